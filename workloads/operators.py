@@ -1,0 +1,97 @@
+"""Finite-difference and kernel operators of the five synthetic workloads.
+
+Every matrix is returned as scipy.sparse CSR in float64.  Index order is
+lexicographic with the first grid coordinate fastest (u[i + N*j] for 2-D,
+u[i + N*j + N*N*k] for 3-D).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def tridiag_laplacian(n: int) -> sp.csr_matrix:
+    """Unscaled 1-D Laplacian: 2 on the diagonal, -1 on both off-diagonals."""
+    main = np.full(n, 2.0)
+    off = np.full(n - 1, -1.0)
+    return sp.diags([off, main, off], [-1, 0, 1], format="csr")
+
+
+def diffusion_2d(N: int, a_xface: np.ndarray, a_yface: np.ndarray, h: float) -> sp.csr_matrix:
+    """5-point discretisation of -div(a grad u) on an N x N interior grid.
+
+    ``a_xface[i, j]`` is the coefficient on the x-face between interior
+    columns i-1 and i (i = 0..N, shape (N+1, N)); ``a_yface[i, j]`` the
+    coefficient on the y-face between rows j-1 and j (shape (N, N+1)).
+    Dirichlet boundary: faces touching the boundary still contribute their
+    coefficient to the diagonal.  Scaled by 1/h^2.
+    """
+    n = N * N
+    idx = np.arange(n).reshape(N, N, order="F")  # idx[i, j] = i + N*j
+    aw = a_xface[:-1, :]  # face west of (i, j)
+    ae = a_xface[1:, :]   # face east
+    as_ = a_yface[:, :-1]  # face south
+    an = a_yface[:, 1:]    # face north
+    diag = (aw + ae + as_ + an).ravel(order="F")
+    rows = [idx.ravel(order="F")]
+    cols = [idx.ravel(order="F")]
+    vals = [diag]
+    # west neighbour (i-1, j)
+    rows.append(idx[1:, :].ravel(order="F")); cols.append(idx[:-1, :].ravel(order="F"))
+    vals.append(-aw[1:, :].ravel(order="F"))
+    # east neighbour (i+1, j)
+    rows.append(idx[:-1, :].ravel(order="F")); cols.append(idx[1:, :].ravel(order="F"))
+    vals.append(-ae[:-1, :].ravel(order="F"))
+    # south neighbour (i, j-1)
+    rows.append(idx[:, 1:].ravel(order="F")); cols.append(idx[:, :-1].ravel(order="F"))
+    vals.append(-as_[:, 1:].ravel(order="F"))
+    # north neighbour (i, j+1)
+    rows.append(idx[:, :-1].ravel(order="F")); cols.append(idx[:, 1:].ravel(order="F"))
+    vals.append(-an[:, :-1].ravel(order="F"))
+    A = sp.csr_matrix(
+        (np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)
+    )
+    A.sort_indices()
+    return (A / (h * h)).tocsr()
+
+
+def gaussian_bump_faces(N: int, centre: np.ndarray, width: float):
+    """Bump psi(x) = exp(-|x - c|^2 / (2 w^2)) sampled exactly at face midpoints.
+
+    Interior node (i, j) sits at ((i+1) h, (j+1) h), h = 1/(N+1).  The x-face
+    between columns i-1 and i sits at ((i + 1/2) h, (j+1) h), i = 0..N.
+    """
+    h = 1.0 / (N + 1)
+    xf = (np.arange(N + 1) + 0.5) * h
+    xn = (np.arange(N) + 1.0) * h
+    cx, cy = float(centre[0]), float(centre[1])
+    gx = np.exp(-((xf - cx) ** 2) / (2 * width * width))
+    gy = np.exp(-((xn - cy) ** 2) / (2 * width * width))
+    a_x = np.outer(gx, gy)  # (N+1, N): x-faces
+    gx_n = np.exp(-((xn - cx) ** 2) / (2 * width * width))
+    gy_f = np.exp(-((xf - cy) ** 2) / (2 * width * width))
+    a_y = np.outer(gx_n, gy_f)  # (N, N+1): y-faces
+    return a_x, a_y
+
+
+def heat_3d(N: int) -> sp.csr_matrix:
+    """A0 = h^-2 * (7-point Laplacian), -6 on the diagonal, +1 on neighbours.
+
+    Dirichlet boundary on an N^3 interior grid, h = 1/(N+1).  -A0 is SPD.
+    """
+    h = 1.0 / (N + 1)
+    T = sp.diags([np.ones(N - 1), np.full(N, -2.0), np.ones(N - 1)], [-1, 0, 1], format="csr")
+    I = sp.identity(N, format="csr")
+    A = sp.kron(I, sp.kron(I, T)) + sp.kron(I, sp.kron(T, I)) + sp.kron(T, sp.kron(I, I))
+    A = A.tocsr()
+    A.sort_indices()
+    return (A / (h * h)).tocsr()
+
+
+def gaussian_kernel_block(Xa: np.ndarray, Xb: np.ndarray, sigma: float) -> np.ndarray:
+    """Gaussian kernel exp(-|x - x'|^2 / (2 sigma^2)) between two point sets.
+
+    Used only to build small dense KRR systems for snapshot generation.
+    """
+    d2 = ((Xa[:, None, :] - Xb[None, :, :]) ** 2).sum(-1)
+    return np.exp(-d2 / (2.0 * sigma * sigma))
