@@ -1,0 +1,389 @@
+"""Benchmark of the SubApSnap online stage on GB300.
+
+Workload: 2-D parametric diffusion, 1024 x 1024 interior grid (n = 1,048,576),
+A(p) = A_0 + sum_k p_k A_k (5 CSR blocks), r = 60, s = 120, m = 4096 new
+parameters per step, full x reconstructed in chunks of 256.  One step = all
+4096 parameters through assembly, least squares and reconstruction.
+
+Metric: new-parameter solves per second (whole job), for the chosen form
+(float32 Householder with float64-residual refinement, float32 x from the
+tf32-split tensor-core reconstruction) next to the plain float64 form; both
+report the subsampled relative residual (max, median) they reach.
+
+Launch: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 it runs under torch.distributed.run, one rank per GPU; every rank
+solves its own 4096 parameters (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+GRID = 1024
+R, S_ROWS, M, CHUNK = 60, 120, 4096, 256
+METRIC = "new-p solves/sec on 1 GB300 at stated rel. residual (chosen vs plain FP64)"
+WORKLOAD = "diffusion_2d_1024x1024_r60_s120_m4096_chunk256"
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def start_clock_sampler(path):
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def stop_clock_sampler(p, f, path, gpu_index):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or parts[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def build_inputs(device, rank):
+    """Problem, snapshot basis (device), row selection and parameter batch."""
+    import torch
+    from paper_2510_04825_gb300.solver import csr_to_device, select_rows
+    from workloads import get_config
+    from workloads import snapshots as wsnap
+
+    prob = get_config("diffusion_2d", N=GRID, r=R, s=S_ROWS, m=M)
+    blocks = [csr_to_device(A, device) for A in prob.blocks]
+    S_rows, snap_res = wsnap.diffusion_basis_torch(prob, device=device)
+    J, gaps = select_rows(prob, S_rows, blocks, prob.sel_param, S_ROWS, device=device)
+    params = prob.test_params
+    if rank > 0:  # weak scaling: every rank solves its own draw of 4096 parameters
+        params = np.random.default_rng(1000 + rank).uniform(0.0, 1.0, params.shape)
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(device)
+    return prob, blocks, S_rows, J, gaps, P, params, snap_res
+
+
+def run_gpu(args):
+    import torch
+    from paper_2510_04825_gb300 import api
+    from paper_2510_04825_gb300.solver import AffineSolver
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    t_setup = time.time()
+    prob, blocks, S_rows, J, gaps, P, params_host, snap_res = build_inputs(device, rank)
+    chosen = AffineSolver(prob, None, J, mode=api.SAS_MODE_MIXED, device=device, S_device=S_rows,
+                          blocks_device=blocks)
+    plain = AffineSolver(prob, None, J, mode=api.SAS_MODE_PLAIN, device=device, S_device=S_rows,
+                         blocks_device=blocks)
+    n = prob.n
+    nchunks = M // CHUNK
+    out32 = torch.empty((CHUNK, n), dtype=torch.float32, device=device)
+    out64 = torch.empty((CHUNK, n), dtype=torch.float64, device=device)
+    rho_c = torch.empty(M, dtype=torch.float64, device=device)
+    rho_p = torch.empty(M, dtype=torch.float64, device=device)
+    flags = torch.empty(M, dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream()
+    setup_s = time.time() - t_setup
+
+    def step(solver, out, rho):
+        for c in range(nchunks):
+            sl = slice(c * CHUNK, (c + 1) * CHUNK)
+            solver.solve(P[sl], api.SAS_OUT_XHAT, out, flags[sl], rho[sl])
+
+    def timed(fn, steps, warmup, sample_clocks=False):
+        clk = None
+        if sample_clocks and rank == 0:
+            # the sampler spans warm-up and timed region (200 ms period)
+            cpath = os.path.join(tempfile.gettempdir(), f"sas_clocks_{os.getpid()}.csv")
+            sp, sf = start_clock_sampler(cpath)
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if sample_clocks and rank == 0:
+            clk = stop_clock_sampler(sp, sf, cpath, local)
+        if pg:
+            pg.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        if pg:
+            t = torch.tensor([ms], device=device)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, clk
+
+    # ---- chosen form (headline), with live per-kernel tracing
+    api.subapsnap_set_tracing(chosen.ctx, True)
+    ms_chosen, clocks = timed(lambda: step(chosen, out32, rho_c), args.steps, args.warmup,
+                              sample_clocks=True)
+    # the tracer also saw the warm-up: discard, then trace the timed region once more
+    api.subapsnap_trace_read(chosen.ctx, api.SAS_KERNEL_LS)
+    api.subapsnap_trace_read(chosen.ctx, api.SAS_KERNEL_RECONSTRUCT)
+    ms_traced, _ = timed(lambda: step(chosen, out32, rho_c), args.steps, 0)
+    rec_ms, rec_n = api.subapsnap_trace_read(chosen.ctx, api.SAS_KERNEL_RECONSTRUCT)
+    ls_ms, ls_n = api.subapsnap_trace_read(chosen.ctx, api.SAS_KERNEL_LS)
+    api.subapsnap_set_tracing(chosen.ctx, False)
+
+    # ---- plain float64 form
+    psteps = max(1, min(args.steps, 3))
+    api.subapsnap_set_tracing(plain.ctx, True)
+    ms_plain, _ = timed(lambda: step(plain, out64, rho_p), psteps, 1)
+    prec_ms, prec_n = api.subapsnap_trace_read(plain.ctx, api.SAS_KERNEL_RECONSTRUCT)
+    pls_ms, pls_n = api.subapsnap_trace_read(plain.ctx, api.SAS_KERNEL_LS)
+    api.subapsnap_set_tracing(plain.ctx, False)
+
+    # ---- accuracy of the chosen form against the plain float64 form (same parameters)
+    Yc = torch.empty((M, R), dtype=torch.float64, device=device)
+    Yp = torch.empty((M, R), dtype=torch.float64, device=device)
+    chosen.solve(P, api.SAS_OUT_Y, Yc, None, rho_c)
+    plain.solve(P, api.SAS_OUT_Y, Yp, None, rho_p)
+    torch.cuda.synchronize()
+    yerr = (torch.linalg.vector_norm(Yc - Yp, dim=1) / torch.linalg.vector_norm(Yp, dim=1)).cpu().numpy()
+    rc, rp = rho_c.cpu().numpy(), rho_p.cpu().numpy()
+    # true residual ||A(p) x - b|| / ||b|| on a sample of 64 parameters (float64 x_hat)
+    sample = slice(0, 64)
+    X64 = torch.empty((64, n), dtype=torch.float64, device=device)
+    plain.solve(P[sample], api.SAS_OUT_XHAT, X64)
+    tr = torch.empty(64, dtype=torch.float64, device=device)
+    plain.true_residual(P[sample], X64, tr)
+    X32 = torch.empty((64, n), dtype=torch.float32, device=device)
+    chosen.solve(P[sample], api.SAS_OUT_XHAT, X32)
+    xerr = (torch.linalg.vector_norm(X32.double() - X64, dim=1) / torch.linalg.vector_norm(X64, dim=1)).cpu().numpy()
+    tr = tr.cpu().numpy()
+    del X64, X32
+
+    # ---- end to end through the C-ABI with host buffers: params H2D, x_hat D2H per chunk
+    host_params = torch.from_numpy(np.ascontiguousarray(params_host)).pin_memory()
+    host_out = torch.empty((CHUNK, n), dtype=torch.float32).pin_memory()
+    Pdev = torch.empty_like(P)
+
+    def e2e_step():
+        Pdev.copy_(host_params, non_blocking=True)
+        for c in range(nchunks):
+            sl = slice(c * CHUNK, (c + 1) * CHUNK)
+            chosen.solve(Pdev[sl], api.SAS_OUT_XHAT, out32, flags[sl], rho_c[sl])
+            host_out.copy_(out32, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 3))
+    ms_e2e, _ = timed(e2e_step, e2e_steps, 1)
+    h2d = int(host_params.numel() * 8)
+    d2h = int(nchunks * CHUNK * n * 4)
+
+    # ---- roofline of the dominant kernel (the reconstruction in the chosen form)
+    hbm, src = peaks()
+    rec_avg_ms = rec_ms / max(rec_n, 1)
+    alg_bytes = 4.0 * n * R + 4.0 * n * CHUNK + 8.0 * CHUNK * R  # S (fp32) once, x_hat (fp32), y
+    achieved = alg_bytes / (rec_avg_ms * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "reconstruct_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as f:
+                tinfo = json.load(f)
+            if tinfo.get("kernel_version") == chosen_kernel_version():
+                traffic = tinfo.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    value = world * M / (ms_chosen * 1e-3)
+    plain_value = world * M / (ms_plain * 1e-3)
+    launches_per_step = 2 * nchunks
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_chosen, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (tf32x3 tensor cores, f32 Householder) + f64 refinement residual",
+        "data": "synthetic (seeded 2-D diffusion workload, snapshot basis from PCG)",
+        "config": {"workload": WORKLOAD, "n": n, "r": R, "s": S_ROWS, "m_per_gpu": M, "chunk": CHUNK,
+                   "parallelism": f"dp{world} (independent parameters)",
+                   "l2": "inputs larger than L2 (S tf32 split 0.54 GB, x_hat chunk 1.07 GB)"},
+        "plain_fp64": {"value": round(plain_value, 2), "unit": "solves/s", "ms_per_step": round(ms_plain, 3),
+                       "reconstruct_ms_per_launch": round(prec_ms / max(prec_n, 1), 4),
+                       "ls_ms_per_launch": round(pls_ms / max(pls_n, 1), 4)},
+        "speedup_chosen_vs_plain": round(value / plain_value, 2),
+        "residual": {"sub_chosen_max": float(rc.max()), "sub_chosen_median": float(np.median(rc)),
+                     "sub_plain_max": float(rp.max()), "sub_plain_median": float(np.median(rp)),
+                     "true_plain_max_64": float(tr.max()), "true_plain_median_64": float(np.median(tr)),
+                     "y_relerr_chosen_vs_plain_max": float(yerr.max()),
+                     "x_relerr_chosen_vs_plain_max_64": float(xerr.max())},
+        "roofline": {"bound": "hbm", "kernel": "reconstruct (chosen form)", "achieved": round(achieved, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                     "traffic": traffic, "peak_source": src,
+                     "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": round(rec_avg_ms, 5),
+                     "ls_avg_launch_ms": round(ls_ms / max(ls_n, 1), 5)},
+        "e2e": {"value": round(world * M / (ms_e2e * 1e-3), 2), "unit": "solves/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "setup_s": round(setup_s, 1),
+        "snapshot_pcg_max_rel_residual": float(np.max(snap_res)),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, S_rows, J, params_host)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def chosen_kernel_version():
+    return "simt-v1"
+
+
+def cpu_baseline(prob, S_rows, J, params, nsample=32, budget_s=20.0):
+    """The oracle, as it stands, on a bounded sample of the same workload."""
+    from oracle import online
+    S = S_rows.cpu().numpy().T.copy()  # n x r on the host
+    t0 = time.time()
+    done = 0
+    for p in params[:nsample]:
+        y, _ = online.solve_one(prob, S, J, p)
+        _ = S @ y  # full reconstruction, as the GPU path does
+        done += 1
+        if time.time() - t0 > budget_s:
+            break
+    dt = time.time() - t0
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": round(done / dt, 3), "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} parameters of the same workload, one at a time (assembly, LS, full x)"}
+
+
+def run_reference(args):
+    """The oracle on the host cores, on this benchmark's workload (bounded sample per step)."""
+    import torch
+    from oracle import online, problem as oproblem, selection
+    from workloads import get_config
+    from workloads import snapshots as wsnap
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    prob = get_config("diffusion_2d", N=GRID, r=R, s=S_ROWS, m=M)
+    if torch.cuda.is_available():
+        S_rows, _ = wsnap.diffusion_basis_torch(prob, device=f"cuda:{local}")
+        S = S_rows.cpu().numpy().T.copy()
+    else:
+        S = wsnap.basis(prob)
+    V = np.asarray(oproblem.full_matrix(prob, prob.sel_param) @ S)
+    J, _ = selection.cpqr_rows(V, S_ROWS)
+    per_step = 8
+    params = prob.test_params
+    for _ in range(args.warmup):
+        y, _ = online.solve_one(prob, S, J, params[0])
+    t0 = time.time()
+    k = 0
+    for st in range(args.steps):
+        for p in params[(st * per_step) % M:(st * per_step) % M + per_step]:
+            y, _ = online.solve_one(prob, S, J, p)
+            _ = S @ y
+            k += 1
+    dt = time.time() - t0
+    value = k / dt
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * dt / max(args.steps, 1), 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": prob.n, "r": R, "s": S_ROWS},
+            "cpu_baseline": {"value": round(value, 3), "unit": "solves/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"{per_step} parameters per step of the same workload (assembly, LS, full x)"},
+            "e2e": {"value": round(value, 3), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

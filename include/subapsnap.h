@@ -1,0 +1,218 @@
+/*
+ * subapsnap.h — C ABI of the GB300 library for the online stage of SubApSnap
+ * (Jones & Nakatsukasa, "SubApSnap", arXiv 2510.04825).
+ *
+ * For a parameter-dependent system A(p) x(p) = b(p), an orthonormal snapshot
+ * basis S (n x r) and a row subsample J (|J| = s, r <= s <= n), every new
+ * parameter p is solved by
+ *     M(p) = A(p)_{J,:} S                       (Alg. 1 step 4; Sec. 3.1)
+ *     y(p) = argmin_y || M(p) y - b_J ||_2      (Alg. 1 step 4; Eq. 3)
+ *     x(p) ~ S y(p)   or   H(p) ~ (c^T S) y(p)  (Alg. 1 step 4; Sec. 5.2.2)
+ *
+ * Conventions for every entry point:
+ *  - Pointers named "device" must be CUDA device (or managed) memory on the
+ *    current device; "host" pointers are ordinary host memory.
+ *  - Matrices are column-major unless stated: entry (i, k) of an n x r matrix
+ *    with leading dimension ld sits at [i + k*ld].  Complex values are
+ *    interleaved (re, im) pairs of double (C99 double _Complex layout).
+ *  - The caller owns every buffer it passes; a context keeps the device
+ *    pointers given at setup (S, CSR arrays, kernel points) and the caller
+ *    must keep them alive and unchanged until subapsnap_destroy.  The
+ *    context owns what it allocates (blocks, copies, scratch).
+ *  - Work is enqueued on the caller's stream (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and is asynchronous unless stated.
+ *    A returned status reports argument checks and launch errors only.
+ *  - No call throws; on failure a call returns a non-zero sas_status and
+ *    subapsnap_last_error() gives a message (per host thread).
+ *  - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef SUBAPSNAP_H
+#define SUBAPSNAP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sas_ctx sas_ctx;
+
+/* Return codes. */
+typedef enum {
+  SAS_OK = 0,
+  SAS_EINVAL = 1,    /* bad argument (sizes, NULL pointer, J out of range or repeated, ...) */
+  SAS_ENOMEM = 2,    /* device allocation failed */
+  SAS_ECUDA = 3,     /* CUDA runtime error (launch or synchronisation) */
+  SAS_ERANK = 4,     /* M(p_sel) is numerically rank deficient at setup */
+  SAS_ETIMEOUT = 5,  /* a bounded device wait ran out (see subapsnap_device_status) */
+  SAS_ENOTSUP = 6    /* combination of options not supported */
+} sas_status;
+
+/* Per-parameter flag bits written to the optional flags[m] array. */
+enum {
+  SAS_FLAG_ILLCOND = 1u,   /* min|R_ii| <= 1e-13 max|R_ii|: M(p) near rank deficient */
+  SAS_FLAG_NONFINITE = 2u, /* a NaN or Inf reached y */
+  SAS_FLAG_REFINE_STALL = 4u /* mixed mode: refinement did not reach its tolerance */
+};
+
+/* Element type of S, b and the outputs. */
+enum { SAS_REAL64 = 0, SAS_COMPLEX128 = 1 };
+
+/* How theta(p) is formed from a parameter vector p (dp doubles per parameter):
+ *  SAS_THETA_LINEAR: theta = (1, p_1, ..., p_{K-1}), dp = K - 1, real.
+ *                    A(p) = A_0 + sum_k p_k A_k.
+ *  SAS_THETA_PENCIL: theta = (-1, i*omega), dp = 1 (p = omega), K = 2,
+ *                    A = (i omega) E - A_0 with blocks (A_0, E): the
+ *                    transfer-function resolvent of Sec. 5.2 (Eq. 9) on the
+ *                    imaginary axis.  Requires SAS_COMPLEX128.            */
+enum { SAS_THETA_LINEAR = 0, SAS_THETA_PENCIL = 1 };
+
+/* Quantity of interest computed from y without any n-vector (Sec. 5.2.2). */
+enum { SAS_QOI_NONE = 0, SAS_QOI_TRANSPOSE = 1 /* c^T x, plain transpose */,
+       SAS_QOI_MEAN = 2 /* (1/n) sum_i x_i */ };
+
+/* Arithmetic of the online solve.
+ *  SAS_MODE_PLAIN: float64 (complex128) assembly, Householder QR and
+ *                  reconstruction.
+ *  SAS_MODE_MIXED: float32 assembly and Householder QR, iterative refinement
+ *                  of y with the subsampled residual b_J - M y formed in
+ *                  float64, float32 reconstruction on the tensor cores
+ *                  (x_hat returned as float32).  Not in the paper.        */
+enum { SAS_MODE_PLAIN = 0, SAS_MODE_MIXED = 1 };
+
+/* What subapsnap_solve_batch writes to `out` for each of its m parameters. */
+enum {
+  SAS_OUT_Y = 0,     /* y: m x r, row j at out + j*r (dtype of S) */
+  SAS_OUT_XHAT = 1,  /* x_hat = S y: m x n, row j at out + j*n; double in
+                        SAS_MODE_PLAIN, float (real) in SAS_MODE_MIXED */
+  SAS_OUT_QOI = 3    /* H = (c^T S) y: m values (dtype of S) */
+};
+
+#define SAS_MAX_TERMS 8
+
+/* Affine operator family A(p) = sum_k theta_k(p) A_k with constant b.
+ * The A_k are real sparse n x n matrices in CSR form (device arrays). */
+typedef struct {
+  int64_t n;            /* order of A(p); rows of S */
+  int32_t r;            /* columns of S (1 <= r <= 128) */
+  int32_t s;            /* rows in the subsample (r <= s <= n, s <= 512) */
+  int32_t K;            /* number of terms, 1..SAS_MAX_TERMS */
+  int32_t dtype;        /* SAS_REAL64 or SAS_COMPLEX128 */
+  int32_t theta_rule;   /* SAS_THETA_LINEAR or SAS_THETA_PENCIL */
+  int32_t mode;         /* SAS_MODE_PLAIN or SAS_MODE_MIXED */
+  const void* S;        /* device, n x r, leading dimension ldS >= n */
+  int64_t ldS;
+  const int64_t* J;     /* host, s distinct row indices in [0, n); order kept */
+  const void* b;        /* device, n entries of dtype */
+  const int64_t* rowptr[SAS_MAX_TERMS]; /* device, n + 1 offsets per term */
+  const int32_t* colind[SAS_MAX_TERMS]; /* device, column indices per term */
+  const double* values[SAS_MAX_TERMS];  /* device, values per term */
+  int32_t qoi_kind;     /* SAS_QOI_* */
+  const double* c;      /* device, n real entries for SAS_QOI_TRANSPOSE, else NULL */
+} sas_affine_desc;
+
+/* Gaussian-kernel ridge regression A(sigma, lambda) = K_sigma + lambda I,
+ * K_sigma(x, x') = exp(-|x - x'|^2 / (2 sigma^2)), b = targets (Sec. 5.3,
+ * Eqs. 10-11).  Parameters are p = (sigma, lambda), dp = 2.  Real only. */
+typedef struct {
+  int64_t n;            /* number of points N */
+  int32_t d;            /* point dimension (1..16) */
+  int32_t r;            /* columns of S (<= 128) */
+  int32_t s;            /* rows in the subsample (r <= s <= 512) */
+  int32_t mode;         /* SAS_MODE_PLAIN or SAS_MODE_MIXED */
+  const double* X;      /* device, N x d row-major (point i at X + i*d) */
+  const double* S;      /* device, N x r, leading dimension ldS >= N */
+  int64_t ldS;
+  const int64_t* J;     /* host, s distinct indices in [0, N) */
+  const double* b;      /* device, N targets */
+} sas_kernel_desc;
+
+/* Build a context for the affine family: gathers b_J, precomputes the blocks
+ * G_k = (A_k)_{J,:} S (s x r each) so that M(p) = sum_k theta_k(p) G_k costs
+ * O(K s r) per parameter (Sec. 3.1, "Computing S A(p*) X"; Sec. 5.2.2), and
+ * the QoI vector c^T S.  Synchronous: returns after the device work is done.
+ * Errors: SAS_EINVAL for inconsistent sizes, NULL pointers or a J that is
+ * out of range or repeated; SAS_ENOMEM; SAS_ECUDA. */
+sas_status subapsnap_setup_affine(const sas_affine_desc* desc, sas_ctx** out);
+
+/* Build a context for the Gaussian-kernel family (Sec. 5.3): keeps X, S and
+ * gathers X_J, S_J and b_J.  The rows K_sigma(X_J, X) are formed on the fly
+ * in every solve.  Synchronous.  Errors as subapsnap_setup_affine. */
+sas_status subapsnap_setup_kernel(const sas_kernel_desc* desc, sas_ctx** out);
+
+/* Solve m new parameters (Alg. 1 step 4).
+ *  params: device, m x dp row-major doubles (dp from the family).
+ *  out:    device, layout per out_kind (see SAS_OUT_*).
+ *  flags:  device, m uint32 (SAS_FLAG_* bits) or NULL.
+ *  rho:    device, m doubles or NULL: the subsampled relative residual
+ *          ||M(p) y - b_J|| / ||b_J|| (Sec. 4.3.1 residual estimate).
+ * Asynchronous on `stream`.  m = 0 is a no-op.  Errors: SAS_EINVAL (bad
+ * pointer, out_kind or family), SAS_ECUDA (launch failure). */
+sas_status subapsnap_solve_batch(sas_ctx* ctx, const double* params, int64_t m,
+                                 int32_t out_kind, void* out, uint32_t* flags,
+                                 double* rho, void* stream);
+
+/* Subsampled relative residual ||M(p) y - b_J|| / ||b_J|| of given
+ * coefficient vectors (Sec. 4.3.1), in float64.
+ *  params: device m x dp; Y: device m x r (dtype of S); rho: device m. */
+sas_status subapsnap_residual(sas_ctx* ctx, const double* params, int64_t m,
+                              const void* Y, double* rho, void* stream);
+
+/* True relative residual ||A(p) x - b|| / ||b|| of full-length vectors
+ * (affine family only; the quantity Tables 3-4 report as (max, median)).
+ *  params: device m x dp; X: device m x n (row j = x for parameter j, dtype
+ *  of S); rho: device m.  Reads every CSR block once per parameter. */
+sas_status subapsnap_true_residual(sas_ctx* ctx, const double* params, int64_t m,
+                                   const void* X, double* rho, void* stream);
+
+/* Row selection by column-pivoted QR on (A(p_sel) S)^T (Sec. 4.3; Alg. 1
+ * step 3), in rounds for s > r: round 1 is CPQR; each later round repeats
+ * CPQR on the same matrix with the earlier picks removed (the union of
+ * pivot sets of Sec. 4.3.2), until s rows are held.  Pivot rule: largest
+ * remaining residual norm in float64, exact ties to the lowest index.
+ *  desc:   as for setup (J, b, qoi fields are ignored).
+ *  p_sel:  host, dp doubles.
+ *  J_out:  host, s indices in pick order.
+ *  gap_out: host, s doubles or NULL: (best - runner-up) / best per step.
+ * Synchronous.  Errors: SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA, SAS_ERANK if a
+ * round runs out of non-zero residuals. */
+sas_status subapsnap_select_rows_affine(const sas_affine_desc* desc, const double* p_sel,
+                                        int64_t* J_out, double* gap_out);
+
+/* Kernel classes reported by the tracer. */
+enum { SAS_KERNEL_LS = 0,           /* assembly + least squares (+ QoI epilogue) */
+       SAS_KERNEL_RECONSTRUCT = 1,  /* x_hat = S y */
+       SAS_KERNEL_RESIDUAL = 2,     /* subsampled / true residual */
+       SAS_KERNEL_CLASSES = 3 };
+
+/* Tracing: when enabled (enable != 0) every kernel the context launches is
+ * bracketed by a pair of CUDA events recorded on the launch stream.  Costs
+ * two event records per launch; off by default.  Not part of the paper. */
+sas_status subapsnap_set_tracing(sas_ctx* ctx, int32_t enable);
+
+/* Sum of traced launch durations (milliseconds, host) and number of traced
+ * launches (host) of one kernel class since the last read; resets that
+ * class.  Synchronises on the recorded events.  Errors: SAS_EINVAL for a
+ * bad class or NULL pointer. */
+sas_status subapsnap_trace_read(sas_ctx* ctx, int32_t kernel_class, double* total_ms,
+                                int64_t* launches);
+
+/* Release a context and everything it allocated.  NULL is a no-op. */
+void subapsnap_destroy(sas_ctx* ctx);
+
+/* Message for the last failed call on this host thread ("" if none). */
+const char* subapsnap_last_error(void);
+
+/* Device status word of a context: 0, or a SAS_* code recorded by a kernel
+ * (e.g. SAS_ETIMEOUT from a bounded wait).  Synchronises the context's
+ * work on `stream` and clears the word. */
+sas_status subapsnap_device_status(sas_ctx* ctx, void* stream);
+
+/* Library version string. */
+const char* subapsnap_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUBAPSNAP_H */

@@ -1,0 +1,197 @@
+"""ctypes binding of libsubapsnap.so (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does
+nothing but check and convert arguments: tensors become device pointers,
+the current torch stream becomes the cudaStream_t, status codes become
+exceptions.  All arithmetic of the online stage runs in the library's CUDA
+kernels.  Importing this module never falls back to anything: if the shared
+library is missing the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libsubapsnap.so")
+
+SAS_OK, SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA, SAS_ERANK, SAS_ETIMEOUT, SAS_ENOTSUP = range(7)
+SAS_FLAG_ILLCOND, SAS_FLAG_NONFINITE, SAS_FLAG_REFINE_STALL = 1, 2, 4
+SAS_REAL64, SAS_COMPLEX128 = 0, 1
+SAS_THETA_LINEAR, SAS_THETA_PENCIL = 0, 1
+SAS_QOI_NONE, SAS_QOI_TRANSPOSE, SAS_QOI_MEAN = 0, 1, 2
+SAS_MODE_PLAIN, SAS_MODE_MIXED = 0, 1
+SAS_OUT_Y, SAS_OUT_XHAT, SAS_OUT_QOI = 0, 1, 3
+SAS_MAX_TERMS = 8
+
+EXPORTED = [
+    "subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
+    "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
+    "subapsnap_destroy", "subapsnap_last_error", "subapsnap_device_status", "subapsnap_version",
+    "subapsnap_set_tracing", "subapsnap_trace_read",
+]
+SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL = 0, 1, 2
+
+
+class SasError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"subapsnap error {code}: {msg}")
+        self.code = code
+
+
+class AffineDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("r", ctypes.c_int32), ("s", ctypes.c_int32),
+        ("K", ctypes.c_int32), ("dtype", ctypes.c_int32), ("theta_rule", ctypes.c_int32),
+        ("mode", ctypes.c_int32), ("S", ctypes.c_void_p), ("ldS", ctypes.c_int64),
+        ("J", ctypes.POINTER(ctypes.c_int64)), ("b", ctypes.c_void_p),
+        ("rowptr", ctypes.c_void_p * SAS_MAX_TERMS), ("colind", ctypes.c_void_p * SAS_MAX_TERMS),
+        ("values", ctypes.c_void_p * SAS_MAX_TERMS), ("qoi_kind", ctypes.c_int32),
+        ("c", ctypes.c_void_p),
+    ]
+
+
+class KernelDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("r", ctypes.c_int32), ("s", ctypes.c_int32),
+        ("mode", ctypes.c_int32), ("X", ctypes.c_void_p), ("S", ctypes.c_void_p),
+        ("ldS", ctypes.c_int64), ("J", ctypes.POINTER(ctypes.c_int64)), ("b", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load the shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        L.subapsnap_setup_affine.argtypes = [ctypes.POINTER(AffineDesc), ctypes.POINTER(vp)]
+        L.subapsnap_setup_kernel.argtypes = [ctypes.POINTER(KernelDesc), ctypes.POINTER(vp)]
+        L.subapsnap_solve_batch.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+        L.subapsnap_residual.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.subapsnap_true_residual.argtypes = [vp, vp, i64, vp, vp, vp]
+        L.subapsnap_select_rows_affine.argtypes = [ctypes.POINTER(AffineDesc),
+                                                   ctypes.POINTER(ctypes.c_double),
+                                                   ctypes.POINTER(ctypes.c_int64),
+                                                   ctypes.POINTER(ctypes.c_double)]
+        L.subapsnap_destroy.argtypes = [vp]
+        L.subapsnap_destroy.restype = None
+        L.subapsnap_last_error.restype = ctypes.c_char_p
+        L.subapsnap_version.restype = ctypes.c_char_p
+        L.subapsnap_device_status.argtypes = [vp, vp]
+        L.subapsnap_set_tracing.argtypes = [vp, i32]
+        L.subapsnap_trace_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_int64)]
+        for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
+                     "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
+                     "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != SAS_OK:
+        raise SasError(code, lib().subapsnap_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _affine_desc(n, r, s, blocks, S, J, b, theta_rule, mode, qoi_kind=SAS_QOI_NONE, c=None,
+                 complex_valued=False):
+    """Fill the C descriptor.  ``blocks`` is a list of (rowptr int64, colind int32,
+    values float64) CUDA tensors; S is (r, n) row-major in memory, i.e. the
+    column-major n x r matrix with ldS = n."""
+    d = AffineDesc()
+    d.n, d.r, d.s, d.K = int(n), int(r), int(s), len(blocks)
+    d.dtype = SAS_COMPLEX128 if complex_valued else SAS_REAL64
+    d.theta_rule, d.mode = theta_rule, mode
+    d.S, d.ldS = _ptr(S), int(n)
+    if J is not None:
+        Jh = np.ascontiguousarray(np.asarray(J, dtype=np.int64))
+        d.J = Jh.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+        d._J_keep = Jh
+    d.b = _ptr(b) if b is not None else None
+    for k, (rp, ci, va) in enumerate(blocks):
+        d.rowptr[k], d.colind[k], d.values[k] = _ptr(rp), _ptr(ci), _ptr(va)
+    d.qoi_kind = qoi_kind
+    d.c = _ptr(c) if c is not None else None
+    return d
+
+
+def subapsnap_version() -> str:
+    return lib().subapsnap_version().decode()
+
+
+def subapsnap_setup_affine(desc: AffineDesc) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(lib().subapsnap_setup_affine(ctypes.byref(desc), ctypes.byref(ctx)))
+    return ctx
+
+
+def subapsnap_select_rows_affine(desc: AffineDesc, p_sel, s: int):
+    ps = np.ascontiguousarray(np.atleast_1d(np.asarray(p_sel, dtype=np.float64)))
+    J = np.zeros(s, dtype=np.int64)
+    gaps = np.zeros(s, dtype=np.float64)
+    _check(lib().subapsnap_select_rows_affine(
+        ctypes.byref(desc), ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        J.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        gaps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return J, gaps
+
+
+def subapsnap_solve_batch(ctx, params, m: int, out_kind: int, out, flags=None, rho=None,
+                          stream=None):
+    _check(lib().subapsnap_solve_batch(ctx, _ptr(params), int(m), int(out_kind), _ptr(out),
+                                       _ptr(flags), _ptr(rho), _stream(stream)))
+
+
+def subapsnap_residual(ctx, params, m: int, Y, rho, stream=None):
+    _check(lib().subapsnap_residual(ctx, _ptr(params), int(m), _ptr(Y), _ptr(rho), _stream(stream)))
+
+
+def subapsnap_true_residual(ctx, params, m: int, X, rho, stream=None):
+    _check(lib().subapsnap_true_residual(ctx, _ptr(params), int(m), _ptr(X), _ptr(rho),
+                                         _stream(stream)))
+
+
+def subapsnap_device_status(ctx, stream=None) -> int:
+    return int(lib().subapsnap_device_status(ctx, _stream(stream)))
+
+
+def subapsnap_set_tracing(ctx, enable: bool):
+    _check(lib().subapsnap_set_tracing(ctx, 1 if enable else 0))
+
+
+def subapsnap_trace_read(ctx, kernel_class: int):
+    """(total milliseconds, launches) of one kernel class since the last read."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int64()
+    _check(lib().subapsnap_trace_read(ctx, kernel_class, ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def subapsnap_destroy(ctx):
+    lib().subapsnap_destroy(ctx)

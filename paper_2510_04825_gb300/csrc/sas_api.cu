@@ -1,0 +1,402 @@
+// C ABI of the SubApSnap online-stage library: argument checks, context
+// set-up and the dispatch of every entry point to its kernels.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "sas_internal.cuh"
+
+namespace sas {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static cudaEvent_t pool_get(sas_ctx* c) {
+  if (!c->event_pool) c->event_pool = new std::vector<cudaEvent_t>();
+  if (!c->event_pool->empty()) {
+    cudaEvent_t e = c->event_pool->back();
+    c->event_pool->pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+TraceScope::TraceScope(sas_ctx* ctx, int k, cudaStream_t s) : c(ctx), cls(k), st(s) {
+  if (c && c->tracing) {
+    a = pool_get(c);
+    cudaEventRecord(a, st);
+  }
+}
+
+TraceScope::~TraceScope() {
+  if (a) {
+    cudaEvent_t b = pool_get(c);
+    cudaEventRecord(b, st);
+    if (!c->trace) c->trace = new std::vector<sas_ctx::TraceRec>();
+    c->trace->push_back({cls, a, b});
+  }
+}
+
+static sas_status fail(sas_status code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+static sas_status cuda_fail(cudaError_t e, const char* where) {
+  set_error(std::string(where) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? SAS_ENOMEM : SAS_ECUDA;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static sas_status check_J(const int64_t* J, int s, int64_t n) {
+  if (!J) return fail(SAS_EINVAL, "J is NULL");
+  std::unordered_set<int64_t> seen;
+  seen.reserve((size_t)s * 2);
+  for (int i = 0; i < s; ++i) {
+    if (J[i] < 0 || J[i] >= n)
+      return fail(SAS_EINVAL, "J[" + std::to_string(i) + "] = " + std::to_string(J[i]) + " is out of range");
+    if (!seen.insert(J[i]).second)
+      return fail(SAS_EINVAL, "J holds the index " + std::to_string(J[i]) + " twice");
+  }
+  return SAS_OK;
+}
+
+static void free_ctx(sas_ctx* c) {
+  if (!c) return;
+  cudaFree(c->J_dev);
+  cudaFree(c->G);
+  cudaFree(c->G32);
+  cudaFree(c->bJ);
+  cudaFree(c->bJ32);
+  cudaFree(c->wq);
+  cudaFree(c->SJ);
+  cudaFree(c->XJ);
+  cudaFree(c->Shi);
+  cudaFree(c->Slo);
+  cudaFree(c->ybuf);
+  cudaFree(c->ysplit);
+  cudaFree(c->dev_status);
+  if (c->trace) {
+    for (auto& t : *c->trace) {
+      cudaEventDestroy(t.a);
+      cudaEventDestroy(t.b);
+    }
+    delete c->trace;
+  }
+  if (c->event_pool) {
+    for (auto e : *c->event_pool) cudaEventDestroy(e);
+    delete c->event_pool;
+  }
+  delete c;
+}
+
+static sas_status check_affine_desc(const sas_affine_desc* d, bool need_J) {
+  if (!d) return fail(SAS_EINVAL, "descriptor is NULL");
+  if (d->n < 1) return fail(SAS_EINVAL, "n must be positive");
+  if (d->r < 1 || d->r > kMaxR) return fail(SAS_EINVAL, "r must be in [1, 128]");
+  if (d->s < d->r || d->s > kMaxS || (int64_t)d->s > d->n)
+    return fail(SAS_EINVAL, "need r <= s <= min(n, 512)");
+  if (d->K < 1 || d->K > SAS_MAX_TERMS) return fail(SAS_EINVAL, "K must be in [1, 8]");
+  if (d->dtype != SAS_REAL64 && d->dtype != SAS_COMPLEX128) return fail(SAS_EINVAL, "bad dtype");
+  if (d->theta_rule == SAS_THETA_PENCIL) {
+    if (d->dtype != SAS_COMPLEX128 || d->K != 2)
+      return fail(SAS_EINVAL, "the pencil rule needs complex128 and K = 2");
+  } else if (d->theta_rule != SAS_THETA_LINEAR) {
+    return fail(SAS_EINVAL, "bad theta rule");
+  }
+  if (d->mode != SAS_MODE_PLAIN && d->mode != SAS_MODE_MIXED) return fail(SAS_EINVAL, "bad mode");
+  if (d->ldS < d->n) return fail(SAS_EINVAL, "ldS < n");
+  if (!is_device_ptr(d->S)) return fail(SAS_EINVAL, "S must be a device pointer");
+  for (int k = 0; k < d->K; ++k) {
+    if (!is_device_ptr(d->rowptr[k]) || !is_device_ptr(d->colind[k]) || !is_device_ptr(d->values[k]))
+      return fail(SAS_EINVAL, "CSR arrays of term " + std::to_string(k) + " must be device pointers");
+  }
+  if (need_J) {
+    if (!is_device_ptr(d->b)) return fail(SAS_EINVAL, "b must be a device pointer");
+    sas_status st = check_J(d->J, d->s, d->n);
+    if (st != SAS_OK) return st;
+    if (d->qoi_kind == SAS_QOI_TRANSPOSE && !is_device_ptr(d->c))
+      return fail(SAS_EINVAL, "c must be a device pointer for SAS_QOI_TRANSPOSE");
+    if (d->qoi_kind != SAS_QOI_NONE && d->qoi_kind != SAS_QOI_TRANSPOSE && d->qoi_kind != SAS_QOI_MEAN)
+      return fail(SAS_EINVAL, "bad qoi kind");
+  }
+  return SAS_OK;
+}
+
+template <typename T>
+static cudaError_t dmalloc(T** p, size_t bytes) {
+  return cudaMalloc((void**)p, bytes);
+}
+
+static sas_status ensure_scratch(sas_ctx* c, int64_t m, bool split, cudaStream_t st) {
+  const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
+  const size_t need = (size_t)m * c->r * es;
+  if (need > c->ybuf_bytes) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+    cudaFree(c->ybuf);
+    c->ybuf = nullptr;
+    c->ybuf_bytes = 0;
+    e = cudaMalloc(&c->ybuf, need);
+    if (e != cudaSuccess) return cuda_fail(e, "solve_batch scratch");
+    c->ybuf_bytes = need;
+  }
+  if (split) {
+    const int rpad = (c->r + 31) / 32 * 32;
+    const size_t need2 = (size_t)2 * m * rpad * sizeof(float);
+    if (need2 > c->ysplit_bytes) {
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+      cudaFree(c->ysplit);
+      c->ysplit = nullptr;
+      c->ysplit_bytes = 0;
+      e = cudaMalloc((void**)&c->ysplit, need2);
+      if (e != cudaSuccess) return cuda_fail(e, "solve_batch scratch");
+      c->ysplit_bytes = need2;
+    }
+  }
+  return SAS_OK;
+}
+
+}  // namespace sas
+
+using namespace sas;
+
+extern "C" {
+
+const char* subapsnap_version(void) { return "subapsnap-gb300 0.1 (sm_103a)"; }
+
+const char* subapsnap_last_error(void) { return g_last_error.c_str(); }
+
+sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
+  if (!out) return fail(SAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  sas_status st = check_affine_desc(d, true);
+  if (st != SAS_OK) return st;
+  sas_ctx* c = new (std::nothrow) sas_ctx();
+  if (!c) return fail(SAS_ENOMEM, "host allocation failed");
+  std::memset((void*)c, 0, sizeof(sas_ctx));
+  c->family = kAffine;
+  c->n = d->n;
+  c->r = d->r;
+  c->s = d->s;
+  c->K = d->K;
+  c->dtype = d->dtype;
+  c->theta_rule = d->theta_rule;
+  c->mode = d->mode;
+  c->dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->K - 1;
+  c->qoi_kind = d->qoi_kind;
+  c->S = d->S;
+  c->ldS = d->ldS;
+  for (int k = 0; k < SAS_MAX_TERMS; ++k) {
+    c->rowptr[k] = k < d->K ? d->rowptr[k] : nullptr;
+    c->colind[k] = k < d->K ? d->colind[k] : nullptr;
+    c->values[k] = k < d->K ? d->values[k] : nullptr;
+  }
+  c->b_full = d->b;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t es = d->dtype == SAS_COMPLEX128 ? 16 : 8;
+  const size_t esl = es / 2;
+  cudaError_t e = cudaSuccess;
+  cudaStream_t sst = nullptr;
+#define TRY(x)                                        \
+  do {                                                \
+    e = (x);                                          \
+    if (e != cudaSuccess) {                           \
+      st = cuda_fail(e, "setup_affine");              \
+      if (sst) cudaStreamDestroy(sst);                \
+      free_ctx(c);                                    \
+      return st;                                      \
+    }                                                 \
+  } while (0)
+  TRY(cudaStreamCreateWithFlags(&sst, cudaStreamNonBlocking));
+  TRY(dmalloc(&c->J_dev, sizeof(int64_t) * d->s));
+  TRY(cudaMemcpy(c->J_dev, d->J, sizeof(int64_t) * d->s, cudaMemcpyHostToDevice));
+  TRY(cudaMalloc(&c->G, (size_t)d->K * d->s * d->r * es));
+  TRY(cudaMalloc(&c->bJ, (size_t)d->s * es));
+  TRY(cudaMalloc(&c->wq, (size_t)d->r * es));
+  TRY(cudaMemset(c->wq, 0, (size_t)d->r * es));
+  TRY(dmalloc(&c->dev_status, sizeof(int)));
+  TRY(cudaMemset(c->dev_status, 0, sizeof(int)));
+  TRY(launch_gather_blocks(c, sst));
+  TRY(launch_gather_vectors(c, d->c, sst));
+  if (d->mode == SAS_MODE_MIXED) {
+    TRY(cudaMalloc(&c->G32, (size_t)d->K * d->s * d->r * esl));
+    TRY(cudaMalloc(&c->bJ32, (size_t)d->s * esl));
+    if (d->dtype == SAS_REAL64) {
+      const int rpad = (d->r + 31) / 32 * 32;
+      TRY(dmalloc(&c->Shi, (size_t)d->n * rpad * sizeof(float)));
+      TRY(dmalloc(&c->Slo, (size_t)d->n * rpad * sizeof(float)));
+    }
+    TRY(launch_make_mixed_copies(c, sst));
+  }
+  TRY(cudaStreamSynchronize(sst));
+  {
+    std::vector<double> hb((size_t)d->s * (es / 8));
+    TRY(cudaMemcpy(hb.data(), c->bJ, (size_t)d->s * es, cudaMemcpyDeviceToHost));
+    double nrm2 = 0.0;
+    for (double v : hb) nrm2 += v * v;
+    c->bJ_norm = std::sqrt(nrm2);
+    if (!(c->bJ_norm > 0.0)) {
+      cudaStreamDestroy(sst);
+      free_ctx(c);
+      return fail(SAS_EINVAL, "b_J is zero: the subsampled system has no right-hand side");
+    }
+  }
+  cudaStreamDestroy(sst);
+#undef TRY
+  *out = c;
+  return SAS_OK;
+}
+
+sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
+  (void)d;
+  if (out) *out = nullptr;
+  return fail(SAS_ENOTSUP, "setup_kernel: the Gaussian-kernel family is not built yet");
+}
+
+sas_status subapsnap_solve_batch(sas_ctx* c, const double* params, int64_t m, int32_t out_kind,
+                                 void* out, uint32_t* flags, double* rho, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (m < 0) return fail(SAS_EINVAL, "m < 0");
+  if (m == 0) return SAS_OK;
+  if (!params || !out) return fail(SAS_EINVAL, "params and out must be non-NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  const bool mixed = c->mode == SAS_MODE_MIXED;
+  if (c->family != kAffine) return fail(SAS_ENOTSUP, "family not supported");
+  switch (out_kind) {
+    case SAS_OUT_Y: {
+      TraceScope ts(c, SAS_KERNEL_LS, st);
+      e = mixed ? launch_ls_mixed(c, params, m, out, nullptr, nullptr, flags, rho, st)
+                : launch_ls_plain(c, params, m, out, nullptr, flags, rho, st);
+      break;
+    }
+    case SAS_OUT_QOI: {
+      if (c->qoi_kind == SAS_QOI_NONE) return fail(SAS_EINVAL, "context was set up without a QoI");
+      TraceScope ts(c, SAS_KERNEL_LS, st);
+      e = mixed ? launch_ls_mixed(c, params, m, nullptr, out, nullptr, flags, rho, st)
+                : launch_ls_plain(c, params, m, nullptr, out, flags, rho, st);
+      break;
+    }
+    case SAS_OUT_XHAT: {
+      if (c->dtype != SAS_REAL64) return fail(SAS_ENOTSUP, "x_hat output is real-only");
+      sas_status s2 = ensure_scratch(c, m, mixed, st);
+      if (s2 != SAS_OK) return s2;
+      {
+        TraceScope ts(c, SAS_KERNEL_LS, st);
+        e = mixed ? launch_ls_mixed(c, params, m, c->ybuf, nullptr, c->ysplit, flags, rho, st)
+                  : launch_ls_plain(c, params, m, c->ybuf, nullptr, flags, rho, st);
+      }
+      if (e == cudaSuccess) {
+        TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
+        e = mixed ? launch_reconstruct_mixed(c, c->ysplit, m, (float*)out, st)
+                  : launch_reconstruct_f64(c, c->ybuf, m, out, st);
+      }
+      break;
+    }
+    default:
+      return fail(SAS_EINVAL, "bad out_kind");
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+  return SAS_OK;
+}
+
+sas_status subapsnap_residual(sas_ctx* c, const double* params, int64_t m, const void* Y,
+                              double* rho, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (m < 0) return fail(SAS_EINVAL, "m < 0");
+  if (m == 0) return SAS_OK;
+  if (!params || !Y || !rho) return fail(SAS_EINVAL, "NULL argument");
+  if (c->family != kAffine) return fail(SAS_ENOTSUP, "family not supported");
+  TraceScope ts(c, SAS_KERNEL_RESIDUAL, (cudaStream_t)stream);
+  cudaError_t e = launch_residual(c, params, m, Y, rho, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "residual");
+  return SAS_OK;
+}
+
+sas_status subapsnap_true_residual(sas_ctx* c, const double* params, int64_t m, const void* X,
+                                   double* rho, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (m < 0) return fail(SAS_EINVAL, "m < 0");
+  if (m == 0) return SAS_OK;
+  if (!params || !X || !rho) return fail(SAS_EINVAL, "NULL argument");
+  if (c->family != kAffine) return fail(SAS_ENOTSUP, "true residual needs the affine family");
+  if (m > 65535) return fail(SAS_EINVAL, "at most 65535 parameters per call");
+  TraceScope ts(c, SAS_KERNEL_RESIDUAL, (cudaStream_t)stream);
+  cudaError_t e = launch_true_residual(c, params, m, X, rho, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "true_residual");
+  return SAS_OK;
+}
+
+sas_status subapsnap_select_rows_affine(const sas_affine_desc* d, const double* p_sel,
+                                        int64_t* J_out, double* gap_out) {
+  sas_status st = check_affine_desc(d, false);
+  if (st != SAS_OK) return st;
+  if (!p_sel || !J_out) return fail(SAS_EINVAL, "p_sel and J_out must be non-NULL");
+  return select_rows_affine(d, p_sel, J_out, gap_out);
+}
+
+void subapsnap_destroy(sas_ctx* c) { free_ctx(c); }
+
+sas_status subapsnap_set_tracing(sas_ctx* c, int32_t enable) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  c->tracing = enable ? 1 : 0;
+  return SAS_OK;
+}
+
+sas_status subapsnap_trace_read(sas_ctx* c, int32_t cls, double* total_ms, int64_t* launches) {
+  if (!c || !total_ms || !launches) return fail(SAS_EINVAL, "NULL argument");
+  if (cls < 0 || cls >= SAS_KERNEL_CLASSES) return fail(SAS_EINVAL, "bad kernel class");
+  *total_ms = 0.0;
+  *launches = 0;
+  if (!c->trace) return SAS_OK;
+  std::vector<sas_ctx::TraceRec> keep;
+  for (auto& t : *c->trace) {
+    if (t.cls != cls) {
+      keep.push_back(t);
+      continue;
+    }
+    cudaError_t e = cudaEventSynchronize(t.b);
+    if (e != cudaSuccess) return cuda_fail(e, "trace_read");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    *total_ms += ms;
+    *launches += 1;
+    c->event_pool->push_back(t.a);
+    c->event_pool->push_back(t.b);
+  }
+  c->trace->swap(keep);
+  return SAS_OK;
+}
+
+sas_status subapsnap_device_status(sas_ctx* c, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "device_status");
+  int v = 0;
+  e = cudaMemcpy(&v, c->dev_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "device_status");
+  cudaMemset(c->dev_status, 0, sizeof(int));
+  return (sas_status)v;
+}
+
+}  // extern "C"

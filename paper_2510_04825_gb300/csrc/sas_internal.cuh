@@ -1,0 +1,218 @@
+// Internal declarations of the SubApSnap online-stage library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "subapsnap.h"
+
+namespace sas {
+
+// ---------------------------------------------------------------- complex
+struct __align__(16) zd {
+  double re, im;
+};
+
+__host__ __device__ inline zd mkz(double a, double b) { zd z; z.re = a; z.im = b; return z; }
+__host__ __device__ inline zd operator+(zd a, zd b) { return mkz(a.re + b.re, a.im + b.im); }
+__host__ __device__ inline zd operator-(zd a, zd b) { return mkz(a.re - b.re, a.im - b.im); }
+__host__ __device__ inline zd operator-(zd a) { return mkz(-a.re, -a.im); }
+__host__ __device__ inline zd operator*(zd a, zd b) {
+  return mkz(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+__host__ __device__ inline zd operator*(double a, zd b) { return mkz(a * b.re, a * b.im); }
+__host__ __device__ inline zd& operator+=(zd& a, zd b) { a = a + b; return a; }
+__host__ __device__ inline zd& operator-=(zd& a, zd b) { a = a - b; return a; }
+
+struct __align__(8) zf {
+  float re, im;
+};
+__host__ __device__ inline zf mkzf(float a, float b) { zf z; z.re = a; z.im = b; return z; }
+__host__ __device__ inline zf operator+(zf a, zf b) { return mkzf(a.re + b.re, a.im + b.im); }
+__host__ __device__ inline zf operator-(zf a, zf b) { return mkzf(a.re - b.re, a.im - b.im); }
+__host__ __device__ inline zf operator-(zf a) { return mkzf(-a.re, -a.im); }
+__host__ __device__ inline zf operator*(zf a, zf b) {
+  return mkzf(fmaf(a.re, b.re, -a.im * b.im), fmaf(a.re, b.im, a.im * b.re));
+}
+__host__ __device__ inline zf operator*(float a, zf b) { return mkzf(a * b.re, a * b.im); }
+__host__ __device__ inline zf& operator+=(zf& a, zf b) { a = a + b; return a; }
+__host__ __device__ inline zf& operator-=(zf& a, zf b) { a = a - b; return a; }
+
+// Uniform helpers so that kernels can be templated on the scalar type.
+__host__ __device__ inline double conjv(double x) { return x; }
+__host__ __device__ inline float conjv(float x) { return x; }
+__host__ __device__ inline zd conjv(zd x) { return mkz(x.re, -x.im); }
+__host__ __device__ inline zf conjv(zf x) { return mkzf(x.re, -x.im); }
+__host__ __device__ inline double absq(double x) { return x * x; }
+__host__ __device__ inline float absq(float x) { return x * x; }
+__host__ __device__ inline double absq(zd x) { return x.re * x.re + x.im * x.im; }
+__host__ __device__ inline float absq(zf x) { return x.re * x.re + x.im * x.im; }
+template <typename T> __host__ __device__ inline T zero();
+template <> __host__ __device__ inline double zero<double>() { return 0.0; }
+template <> __host__ __device__ inline float zero<float>() { return 0.0f; }
+template <> __host__ __device__ inline zd zero<zd>() { return mkz(0.0, 0.0); }
+template <> __host__ __device__ inline zf zero<zf>() { return mkzf(0.0f, 0.0f); }
+// scale by a real number
+__host__ __device__ inline double rscale(double a, double x) { return a * x; }
+__host__ __device__ inline float rscale(float a, float x) { return a * x; }
+__host__ __device__ inline zd rscale(double a, zd x) { return a * x; }
+__host__ __device__ inline zf rscale(float a, zf x) { return a * x; }
+// conversions between precisions
+__host__ __device__ inline float to_lo(double x) { return (float)x; }
+__host__ __device__ inline zf to_lo(zd x) { return mkzf((float)x.re, (float)x.im); }
+__host__ __device__ inline double to_hi(float x) { return (double)x; }
+__host__ __device__ inline zd to_hi(zf x) { return mkz((double)x.re, (double)x.im); }
+// division a / b for b on the complex plane (Smith-free: b is a Householder diagonal)
+__host__ __device__ inline double divv(double a, double b) { return a / b; }
+__host__ __device__ inline float divv(float a, float b) { return a / b; }
+__host__ __device__ inline zd divv(zd a, zd b) {
+  double d = b.re * b.re + b.im * b.im;
+  return mkz((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+__host__ __device__ inline zf divv(zf a, zf b) {
+  float d = b.re * b.re + b.im * b.im;
+  return mkzf((a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d);
+}
+// phase of a number: a/|a| (1 for 0)
+__host__ __device__ inline double phase(double a) { return a < 0.0 ? -1.0 : 1.0; }
+__host__ __device__ inline float phase(float a) { return a < 0.0f ? -1.0f : 1.0f; }
+__host__ __device__ inline zd phase(zd a) {
+  double m = sqrt(absq(a));
+  return m > 0.0 ? mkz(a.re / m, a.im / m) : mkz(1.0, 0.0);
+}
+__host__ __device__ inline zf phase(zf a) {
+  float m = sqrtf(absq(a));
+  return m > 0.0f ? mkzf(a.re / m, a.im / m) : mkzf(1.0f, 0.0f);
+}
+__device__ inline bool finitev(double x) { return isfinite(x); }
+__device__ inline bool finitev(zd x) { return isfinite(x.re) && isfinite(x.im); }
+
+template <typename T> __device__ inline T shfl_down(T v, int o);
+template <> __device__ inline double shfl_down<double>(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+template <> __device__ inline float shfl_down<float>(float v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+template <> __device__ inline zd shfl_down<zd>(zd v, int o) {
+  return mkz(__shfl_down_sync(0xffffffffu, v.re, o), __shfl_down_sync(0xffffffffu, v.im, o));
+}
+template <> __device__ inline zf shfl_down<zf>(zf v, int o) {
+  return mkzf(__shfl_down_sync(0xffffffffu, v.re, o), __shfl_down_sync(0xffffffffu, v.im, o));
+}
+template <typename T> __device__ inline T shfl_idx(T v, int l);
+template <> __device__ inline double shfl_idx<double>(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+template <> __device__ inline float shfl_idx<float>(float v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+template <> __device__ inline zd shfl_idx<zd>(zd v, int l) {
+  return mkz(__shfl_sync(0xffffffffu, v.re, l), __shfl_sync(0xffffffffu, v.im, l));
+}
+template <> __device__ inline zf shfl_idx<zf>(zf v, int l) {
+  return mkzf(__shfl_sync(0xffffffffu, v.re, l), __shfl_sync(0xffffffffu, v.im, l));
+}
+template <typename T> __device__ inline T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_down(v, o);
+  return shfl_idx(v, 0);
+}
+
+// ----------------------------------------------------------------- limits
+constexpr int kMaxR = 128;
+constexpr int kMaxS = 512;
+constexpr int kMaxDp = SAS_MAX_TERMS;
+
+enum Family { kAffine = 0, kKernel = 1 };
+
+// Per-parameter coefficient rule, evaluated on the device.
+struct ThetaRule {
+  int rule;  // SAS_THETA_*
+  int K;
+  int dp;
+};
+
+}  // namespace sas
+
+// ------------------------------------------------------------------ context
+struct sas_ctx {
+  int family;
+  int64_t n;
+  int r, s, K, dtype, theta_rule, mode, dp, qoi_kind;
+  // caller-owned device data
+  const void* S;
+  int64_t ldS;
+  const int64_t* rowptr[SAS_MAX_TERMS];
+  const int32_t* colind[SAS_MAX_TERMS];
+  const double* values[SAS_MAX_TERMS];
+  const void* b_full;
+  const double* X;
+  int d;
+  // owned device data
+  int64_t* J_dev;      // s
+  void* G;             // K blocks, each s x r column-major (ld s), dtype
+  void* G32;           // mixed: float / complex-float copy of G
+  void* bJ;            // s, dtype
+  void* bJ32;          // mixed copy
+  void* wq;            // r, dtype: c^T S (QoI)
+  double* SJ;          // kernel family: s x r (ld s)
+  double* XJ;          // kernel family: s x d
+  float* Shi;          // mixed reconstruction: high tf32 part of S, n x r (ld n)
+  float* Slo;          // low part
+  double bJ_norm;
+  // scratch (grown on demand)
+  void* ybuf;          // m x r dtype
+  size_t ybuf_bytes;
+  float* ysplit;       // mixed: y split into tf32 hi/lo, 2 x m x r
+  size_t ysplit_bytes;
+  int* dev_status;     // device status word
+  int num_sms;
+  int ls_blocks_per_sm;
+  // tracing
+  int tracing;
+  struct TraceRec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<TraceRec>* trace;     // pending records
+  std::vector<cudaEvent_t>* event_pool;
+};
+
+namespace sas {
+
+// Thread-local error text.
+void set_error(const std::string& msg);
+
+// Tracing helpers: begin records an event before a launch, end after it.
+struct TraceScope {
+  sas_ctx* c;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  TraceScope(sas_ctx* ctx, int k, cudaStream_t s);
+  ~TraceScope();
+};
+
+// ------------------------------------------------------- kernel launchers
+// setup
+cudaError_t launch_gather_blocks(const sas_ctx* c, cudaStream_t st);
+cudaError_t launch_gather_vectors(const sas_ctx* c, const double* cvec, cudaStream_t st);
+cudaError_t launch_make_mixed_copies(const sas_ctx* c, cudaStream_t st);
+// solve
+cudaError_t launch_ls_plain(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                            void* qoi_out, uint32_t* flags, double* rho, cudaStream_t st);
+cudaError_t launch_ls_mixed(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                            void* qoi_out, float* ysplit, uint32_t* flags, double* rho,
+                            cudaStream_t st);
+size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block);
+size_t ls_mixed_smem_bytes(const sas_ctx* c);
+cudaError_t launch_reconstruct_f64(const sas_ctx* c, const void* Y, int64_t m, void* out,
+                                   cudaStream_t st);
+cudaError_t launch_reconstruct_mixed(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
+                                     cudaStream_t st);
+cudaError_t launch_residual(const sas_ctx* c, const double* params, int64_t m, const void* Y,
+                            double* rho, cudaStream_t st);
+cudaError_t launch_true_residual(const sas_ctx* c, const double* params, int64_t m, const void* X,
+                                 double* rho, cudaStream_t st);
+// selection
+sas_status select_rows_affine(const sas_affine_desc* d, const double* p_sel, int64_t* J_out,
+                              double* gap_out);
+
+}  // namespace sas

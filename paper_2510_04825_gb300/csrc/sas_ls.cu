@@ -1,0 +1,591 @@
+// Batched subsampled least squares of the SubApSnap online stage.
+//
+// For every parameter p of a batch: assemble M(p) = sum_k theta_k(p) G_k
+// (G_k = (A_k)_{J,:} S precomputed; Sec. 3.1 "Computing S A(p*) X") and
+// solve min_y ||M y - b_J|| (Alg. 1 step 4) by Householder QR, then back
+// substitution.  The residual norm comes for free from the trailing part of
+// Q^H b_J; the QoI (c^T S) y (Sec. 5.2.2) is formed in the epilogue.
+//
+// Plain form: float64 / complex128 throughout, one CTA per parameter.  When
+// s x (r+1) does not fit in shared memory, rows are streamed in blocks of t:
+// the first block is factorised in place, every later block is folded into
+// the r x r triangle by the Householder update of the stacked [R; P] (the
+// row-blocked, sequential form of TSQR).  The result is the same QR up to
+// rounding.
+//
+// Mixed form (not in the paper): float32 assembly and Householder QR with the
+// reflectors kept, then iterative refinement y += R^{-1} Q^H (b_J - M y) where
+// the residual is formed in float64 from the float64 blocks.
+#include "sas_internal.cuh"
+
+namespace sas {
+
+template <typename T> __device__ inline T theta_k(int rule, int k, const double* p);
+template <> __device__ inline double theta_k<double>(int rule, int k, const double* p) {
+  (void)rule;
+  return k == 0 ? 1.0 : p[k - 1];
+}
+template <> __device__ inline zd theta_k<zd>(int rule, int k, const double* p) {
+  if (rule == SAS_THETA_PENCIL) return k == 0 ? mkz(-1.0, 0.0) : mkz(0.0, p[0]);
+  return mkz(k == 0 ? 1.0 : p[k - 1], 0.0);
+}
+
+template <int NT>
+__device__ inline double block_sum(double v, double* red) {
+  constexpr int NW = NT / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double tot = 0.0;
+#pragma unroll
+  for (int w = 0; w < NW; ++w) tot += red[w];
+  __syncthreads();
+  return tot;
+}
+
+// One Householder step on the stacked column [piv_k; tail_k(0..len-1)], applied
+// to columns k+1..ncol-1 (the last column is the right-hand side).  Column j's
+// pivot-row entry sits at piv[j*ldp], its tail at tail + j*ldt.  The reflector is
+// H = I - tau v v^H with v = x - beta e_1, beta = -phase(alpha) ||x||, so that
+// H x = beta e_1 and H = H^H; on return piv[k*ldp] holds beta (= R_kk).
+template <typename T, typename R, int NT>
+__device__ inline void householder_step(int k, int ncol, T* piv, int ldp, T* tail, int ldt, int len,
+                                        R* red, T* v0_out, R* tau_out) {
+  constexpr int NW = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* tk = tail + (size_t)k * ldt;
+  R part = R(0);
+  for (int i = tid; i < len; i += NT) part += absq(tk[i]);
+  // block reduction in the working precision
+  part = warp_sum(part);
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  R tail2 = R(0);
+#pragma unroll
+  for (int w = 0; w < NW; ++w) tail2 += red[w];
+  const T alpha = piv[(size_t)k * ldp];
+  const R a2 = absq(alpha);
+  const R nrm = sqrt(a2 + tail2);
+  const R aa = sqrt(a2);
+  const T beta = rscale(-nrm, phase(alpha));
+  const T v0 = alpha - beta;
+  const R tau = nrm > R(0) ? R(1) / (nrm * (nrm + aa)) : R(0);
+  __syncthreads();  // red and alpha consumed before anyone writes
+  for (int j = k + 1 + warp; j < ncol; j += NW) {
+    T* tj = tail + (size_t)j * ldt;
+    T w = lane == 0 ? conjv(v0) * piv[(size_t)j * ldp] : zero<T>();
+    for (int i = lane; i < len; i += 32) w += conjv(tk[i]) * tj[i];
+    w = warp_sum(w);
+    const T tw = rscale(tau, w);
+    if (lane == 0) piv[(size_t)j * ldp] -= tw * v0;
+    for (int i = lane; i < len; i += 32) tj[i] -= tw * tk[i];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    piv[(size_t)k * ldp] = beta;
+    if (v0_out) v0_out[k] = v0;
+    if (tau_out) tau_out[k] = tau;
+  }
+}
+
+// Back substitution R y = z by one warp: R upper triangular r x r (ld ldr), z
+// in registers distributed as z[lane + 32 c].  Writes y to ys[0..r).  Returns
+// min/max |R_ii| through dmin/dmax (lane 0).
+template <typename T, typename R>
+__device__ inline void backsolve_warp(const T* Rm, int ldr, int r, T* zr /*[4]*/, T* ys, R& dmin,
+                                      R& dmax) {
+  const int lane = threadIdx.x & 31;
+  dmin = R(INFINITY);
+  dmax = R(0);
+  for (int i = r - 1; i >= 0; --i) {
+    const int owner = i & 31, slot = i >> 5;
+    const T rii = Rm[i + (size_t)i * ldr];
+    T zi = zero<T>();
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      if (c == slot) zi = zr[c];
+    zi = shfl_idx(zi, owner);
+    const T yi = divv(zi, rii);
+    if (lane == 0) ys[i] = yi;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = lane + 32 * c;
+      if (j < i) zr[c] -= Rm[j + (size_t)i * ldr] * yi;
+    }
+    const R ad = sqrt(absq(rii));
+    dmin = ad < dmin ? ad : dmin;
+    dmax = ad > dmax ? ad : dmax;
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ plain
+template <typename T>
+struct LsPlainArgs {
+  const T* G;
+  const T* bJ;
+  const T* wq;
+  const double* params;
+  int64_t m;
+  int s, r, K, dp, rule, t, ldt;
+  double bJ_norm;
+  T* yout;
+  T* qoi;
+  uint32_t* flags;
+  double* rho;
+};
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = a.s, r = a.r, t = a.t, ldt = a.ldt, K = a.K;
+  const bool single = t >= s;
+  const int ldr = single ? ldt : r;
+  T* P = reinterpret_cast<T*>(smem_raw);
+  T* Rm = single ? P : P + (size_t)ldt * (r + 1);
+  T* th = P + (size_t)ldt * (r + 1) + (single ? 0 : (size_t)r * (r + 1));
+  T* ys = th + kMaxDp;
+  double* red = reinterpret_cast<double*>(ys + kMaxR);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) {
+    if (tid < K) th[tid] = theta_k<T>(a.rule, tid, a.params + q * a.dp);
+    __syncthreads();
+    double res2 = 0.0;
+    for (int row0 = 0; row0 < s; row0 += t) {
+      const int tb = min(t, s - row0);
+      for (int idx = tid; idx < tb * (r + 1); idx += NT) {
+        const int i = idx % tb, j = idx / tb;
+        T v;
+        if (j < r) {
+          v = zero<T>();
+          const T* g = a.G + (size_t)j * s + row0 + i;
+          for (int k = 0; k < K; ++k) v += th[k] * g[(size_t)k * s * r];
+        } else {
+          v = a.bJ[row0 + i];
+        }
+        P[i + (size_t)j * ldt] = v;
+      }
+      __syncthreads();
+      if (row0 == 0) {
+        for (int k = 0; k < r; ++k)
+          householder_step<T, double, NT>(k, r + 1, P + k, ldt, P + k + 1, ldt, tb - k - 1, red,
+                                          (T*)nullptr, (double*)nullptr);
+        __syncthreads();
+        double part = 0.0;
+        for (int i = r + tid; i < tb; i += NT) part += absq(P[i + (size_t)r * ldt]);
+        res2 += block_sum<NT>(part, red);
+        if (!single) {
+          for (int idx = tid; idx < r * (r + 1); idx += NT) {
+            const int i = idx % r, j = idx / r;
+            Rm[i + (size_t)j * r] = P[i + (size_t)j * ldt];
+          }
+        }
+      } else {
+        for (int k = 0; k < r; ++k)
+          householder_step<T, double, NT>(k, r + 1, Rm + k, r, P, ldt, tb, red, (T*)nullptr,
+                                          (double*)nullptr);
+        __syncthreads();
+        double part = 0.0;
+        for (int i = tid; i < tb; i += NT) part += absq(P[i + (size_t)r * ldt]);
+        res2 += block_sum<NT>(part, red);
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      T zr[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = (tid & 31) + 32 * c;
+        zr[c] = i < r ? Rm[i + (size_t)r * ldr] : zero<T>();
+      }
+      double dmin, dmax;
+      backsolve_warp<T, double>(Rm, ldr, r, zr, ys, dmin, dmax);
+      const int lane = tid & 31;
+      bool fin = true;
+      T h = zero<T>();
+      for (int i = lane; i < r; i += 32) {
+        const T yi = ys[i];
+        fin = fin && finitev(yi);
+        if (a.yout) a.yout[q * r + i] = yi;
+        if (a.qoi) h += a.wq[i] * yi;
+      }
+      fin = __all_sync(0xffffffffu, fin);
+      if (a.qoi) {
+        h = warp_sum(h);
+        if (lane == 0) a.qoi[q] = h;
+      }
+      if (lane == 0) {
+        if (a.rho) a.rho[q] = sqrt(res2) / a.bJ_norm;
+        if (a.flags) {
+          uint32_t f = 0;
+          if (!(dmin > 1e-13 * dmax)) f |= SAS_FLAG_ILLCOND;
+          if (!fin) f |= SAS_FLAG_NONFINITE;
+          a.flags[q] = f;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+constexpr int kLsThreads = 256;
+constexpr size_t kSmemLimit = 227 * 1024 - 1024;
+
+size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block) {
+  const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
+  const size_t extra = (size_t)(kMaxDp + kMaxR) * es + (kLsThreads / 32) * 8;
+  const size_t single = (size_t)c->s * (c->r + 1) * es + extra;
+  if (single <= kSmemLimit) {
+    *rows_per_block = c->s;
+    return single;
+  }
+  const size_t rbuf = (size_t)c->r * (c->r + 1) * es;
+  if (rbuf + extra >= kSmemLimit) return 0;
+  int t = (int)((kSmemLimit - rbuf - extra) / ((c->r + 1) * es));
+  if (t > c->s) t = c->s;
+  if (t < c->r) return 0;
+  *rows_per_block = t;
+  return (size_t)t * (c->r + 1) * es + rbuf + extra;
+}
+
+template <typename T>
+static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                                  void* qoi, uint32_t* flags, double* rho, cudaStream_t st) {
+  int t = 0;
+  const size_t smem = ls_plain_smem_bytes(c, &t);
+  if (smem == 0) return cudaErrorInvalidConfiguration;
+  LsPlainArgs<T> a;
+  a.G = (const T*)c->G;
+  a.bJ = (const T*)c->bJ;
+  a.wq = (const T*)c->wq;
+  a.params = params;
+  a.m = m;
+  a.s = c->s;
+  a.r = c->r;
+  a.K = c->K;
+  a.dp = c->dp;
+  a.rule = c->theta_rule;
+  a.t = t;
+  a.ldt = t;
+  a.bJ_norm = c->bJ_norm;
+  a.yout = (T*)yout;
+  a.qoi = (T*)qoi;
+  a.flags = flags;
+  a.rho = rho;
+  auto kern = ls_plain_affine_kernel<T, kLsThreads>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLsThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)c->num_sms * per_sm;
+  if (grid > m) grid = m;
+  kern<<<(unsigned)grid, kLsThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ls_plain(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                            void* qoi, uint32_t* flags, double* rho, cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  if (c->dtype == SAS_COMPLEX128) return launch_plain_t<zd>(c, params, m, yout, qoi, flags, rho, st);
+  return launch_plain_t<double>(c, params, m, yout, qoi, flags, rho, st);
+}
+
+// ------------------------------------------------------------------ mixed
+template <typename TH, typename TL>
+struct LsMixedArgs {
+  const TH* G;      // float64 blocks (residuals)
+  const TL* G32;    // float32 blocks (factorisation)
+  const TH* bJ;
+  const TL* bJ32;
+  const TH* wq;
+  const double* params;
+  int64_t m;
+  int s, r, K, dp, rule, ldt, rpad, max_refine;
+  double bJ_norm, tol;
+  TH* yout;
+  TH* qoi;
+  float* ysplit;    // real only: [2][m][rpad] tf32 hi / lo parts of y (or null)
+  uint32_t* flags;
+  double* rho;
+};
+
+__device__ inline float tf32_round(float x) {
+  uint32_t u = __float_as_uint(x);
+  u = (u + 0x1000u) & 0xffffe000u;
+  return __uint_as_float(u);
+}
+
+template <typename TH, typename TL, int NT>
+__global__ void __launch_bounds__(NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int s = a.s, r = a.r, ldt = a.ldt, K = a.K;
+  TH* th = reinterpret_cast<TH*>(smem_raw);      // kMaxDp
+  TH* y = th + kMaxDp;                           // kMaxR
+  TH* res = y + kMaxR;                           // kMaxS (float64 residual)
+  double* red = reinterpret_cast<double*>(res + kMaxS);  // NT/32
+  TL* th32 = reinterpret_cast<TL*>(red + NT / 32);
+  TL* v0 = th32 + kMaxDp;                        // kMaxR
+  TL* dl = v0 + kMaxR;                           // kMaxR (correction)
+  float* tau = reinterpret_cast<float*>(dl + kMaxR);  // kMaxR
+  float* redf = tau + kMaxR;                     // NT/32
+  TL* P = reinterpret_cast<TL*>(redf + NT / 32 + 4);   // ldt x (r+1)
+  __shared__ double ctl[2];  // refinement control: stop flag, last relative correction
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) {
+    if (tid < K) {
+      th[tid] = theta_k<TH>(a.rule, tid, a.params + q * a.dp);
+      th32[tid] = to_lo(th[tid]);
+    }
+    __syncthreads();
+    for (int idx = tid; idx < s * (r + 1); idx += NT) {
+      const int i = idx % s, j = idx / s;
+      TL v;
+      if (j < r) {
+        v = zero<TL>();
+        const TL* g = a.G32 + (size_t)j * s + i;
+        for (int k = 0; k < K; ++k) v += th32[k] * g[(size_t)k * s * r];
+      } else {
+        v = a.bJ32[i];
+      }
+      P[i + (size_t)j * ldt] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < r; ++k)
+      householder_step<TL, float, NT>(k, r + 1, P + k, ldt, P + k + 1, ldt, s - k - 1, redf, v0, tau);
+    __syncthreads();
+    // y0 = R^{-1} z
+    float dmin = 0.f, dmax = 0.f;
+    if (warp == 0) {
+      TL zr[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = lane + 32 * c;
+        zr[c] = i < r ? P[i + (size_t)r * ldt] : zero<TL>();
+      }
+      backsolve_warp<TL, float>(P, ldt, r, zr, dl, dmin, dmax);
+      for (int i = lane; i < r; i += 32) y[i] = to_hi(dl[i]);
+    }
+    __syncthreads();
+    double rn2 = 0.0;
+    bool converged = false;
+    double last_rel = 1.0;
+    if (tid == 0) ctl[1] = 1.0;
+    __syncthreads();
+    for (int it = 0;; ++it) {
+      // float64 residual of the subsampled system: res = b_J - M y
+      double part = 0.0;
+      for (int i = tid; i < s; i += NT) {
+        TH acc = zero<TH>();
+        for (int k = 0; k < K; ++k) {
+          const TH* g = a.G + (size_t)k * s * r + i;
+          TH mk = zero<TH>();
+          for (int j = 0; j < r; ++j) mk += g[(size_t)j * s] * y[j];
+          acc += th[k] * mk;
+        }
+        const TH ri = a.bJ[i] - acc;
+        res[i] = ri;
+        part += absq(ri);
+      }
+      rn2 = block_sum<NT>(part, red);
+      if (converged || it >= a.max_refine) break;
+      // correction: delta = R^{-1} [Q^H res]_{0:r} in float32 (warp 0)
+      if (warp == 0) {
+        for (int i = lane; i < s; i += 32) P[i + (size_t)r * ldt] = to_lo(res[i]);
+        __syncwarp();
+        for (int k = 0; k < r; ++k) {
+          const TL* vk = P + (size_t)k * ldt;  // tail entries below the diagonal
+          TL w = lane == 0 ? conjv(v0[k]) * P[k + (size_t)r * ldt] : zero<TL>();
+          for (int i = k + 1 + lane; i < s; i += 32) w += conjv(vk[i]) * P[i + (size_t)r * ldt];
+          w = warp_sum(w);
+          const TL tw = rscale(tau[k], w);
+          __syncwarp();
+          if (lane == 0) P[k + (size_t)r * ldt] -= tw * v0[k];
+          for (int i = k + 1 + lane; i < s; i += 32) P[i + (size_t)r * ldt] -= tw * vk[i];
+          __syncwarp();
+        }
+        TL zr[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int i = lane + 32 * c;
+          zr[c] = i < r ? P[i + (size_t)r * ldt] : zero<TL>();
+        }
+        float d0, d1;
+        backsolve_warp<TL, float>(P, ldt, r, zr, dl, d0, d1);
+        double dn = 0.0, yn = 0.0;
+        for (int i = lane; i < r; i += 32) {
+          const TH di = to_hi(dl[i]);
+          y[i] += di;
+          dn += absq(di);
+          yn += absq(y[i]);
+        }
+        dn = warp_sum(dn);
+        yn = warp_sum(yn);
+        if (lane == 0) {
+          // stop at the tolerance, or once a correction no longer halves: the
+          // iteration has reached the accuracy the float32 factor allows
+          const double rel = sqrt(dn / yn);
+          ctl[0] = (rel <= a.tol || rel > 0.5 * ctl[1]) ? 1.0 : 0.0;
+          ctl[1] = rel;
+        }
+      }
+      __syncthreads();
+      converged = ctl[0] != 0.0;
+      last_rel = ctl[1];
+      __syncthreads();
+    }
+    if (warp == 0) {
+      bool fin = true;
+      TH h = zero<TH>();
+      for (int i = lane; i < r; i += 32) {
+        const TH yi = y[i];
+        fin = fin && finitev(yi);
+        if (a.yout) a.yout[q * r + i] = yi;
+        if (a.qoi) h += a.wq[i] * yi;
+      }
+      fin = __all_sync(0xffffffffu, fin);
+      if (a.qoi) {
+        h = warp_sum(h);
+        if (lane == 0) a.qoi[q] = h;
+      }
+      if (lane == 0) {
+        if (a.rho) a.rho[q] = sqrt(rn2) / a.bJ_norm;
+        if (a.flags) {
+          uint32_t f = 0;
+          if (!(dmin > 1e-6f * dmax)) f |= SAS_FLAG_ILLCOND;
+          if (!fin) f |= SAS_FLAG_NONFINITE;
+          if (!(last_rel <= 1e-8)) f |= SAS_FLAG_REFINE_STALL;
+          a.flags[q] = f;
+        }
+      }
+    }
+    if (a.ysplit) {
+      // tf32 split of y for the tensor-core reconstruction; zero padding to rpad
+      for (int i = tid; i < a.rpad; i += NT) {
+        float hi = 0.f, lo = 0.f;
+        if (i < r) {
+          const float yf = (float)(*reinterpret_cast<const double*>(&y[i]));
+          hi = tf32_round(yf);
+          lo = yf - hi;
+        }
+        a.ysplit[(size_t)q * a.rpad + i] = hi;
+        a.ysplit[(size_t)a.m * a.rpad + (size_t)q * a.rpad + i] = lo;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t ls_mixed_smem_bytes(const sas_ctx* c) {
+  const bool cplx = c->dtype == SAS_COMPLEX128;
+  const size_t eh = cplx ? 16 : 8, el = cplx ? 8 : 4;
+  size_t b = (size_t)(kMaxDp + kMaxR + kMaxS) * eh + (kLsThreads / 32) * 8;
+  b += (size_t)(kMaxDp + 2 * kMaxR) * el + (size_t)kMaxR * 4 + (kLsThreads / 32 + 4) * 4;
+  b = (b + 15) / 16 * 16;
+  b += (size_t)c->s * (c->r + 1) * el;
+  return b + 16;
+}
+
+template <typename TH, typename TL>
+static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                                  void* qoi, float* ysplit, uint32_t* flags, double* rho,
+                                  cudaStream_t st) {
+  const size_t smem = ls_mixed_smem_bytes(c);
+  if (smem > kSmemLimit) return cudaErrorInvalidConfiguration;
+  LsMixedArgs<TH, TL> a;
+  a.G = (const TH*)c->G;
+  a.G32 = (const TL*)c->G32;
+  a.bJ = (const TH*)c->bJ;
+  a.bJ32 = (const TL*)c->bJ32;
+  a.wq = (const TH*)c->wq;
+  a.params = params;
+  a.m = m;
+  a.s = c->s;
+  a.r = c->r;
+  a.K = c->K;
+  a.dp = c->dp;
+  a.rule = c->theta_rule;
+  a.ldt = c->s;
+  a.rpad = (c->r + 31) / 32 * 32;
+  a.max_refine = 4;
+  a.tol = 1e-13;
+  a.bJ_norm = c->bJ_norm;
+  a.yout = (TH*)yout;
+  a.qoi = (TH*)qoi;
+  a.ysplit = ysplit;
+  a.flags = flags;
+  a.rho = rho;
+  auto kern = ls_mixed_affine_kernel<TH, TL, kLsThreads>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLsThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)c->num_sms * per_sm;
+  if (grid > m) grid = m;
+  kern<<<(unsigned)grid, kLsThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ls_mixed(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                            void* qoi, float* ysplit, uint32_t* flags, double* rho,
+                            cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  if (c->dtype == SAS_COMPLEX128)
+    return launch_mixed_t<zd, zf>(c, params, m, yout, qoi, nullptr, flags, rho, st);
+  return launch_mixed_t<double, float>(c, params, m, yout, qoi, ysplit, flags, rho, st);
+}
+
+// ------------------------------------------------- subsampled residual
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) residual_affine_kernel(const T* G, const T* bJ,
+                                                             const double* params, int64_t m,
+                                                             int s, int r, int K, int dp, int rule,
+                                                             const T* Y, double bJ_norm,
+                                                             double* rho) {
+  __shared__ T th[kMaxDp];
+  __shared__ T y[kMaxR];
+  __shared__ double red[NT / 32];
+  const int tid = threadIdx.x;
+  for (int64_t q = blockIdx.x; q < m; q += gridDim.x) {
+    if (tid < K) th[tid] = theta_k<T>(rule, tid, params + q * dp);
+    for (int i = tid; i < r; i += NT) y[i] = Y[q * r + i];
+    __syncthreads();
+    double part = 0.0;
+    for (int i = tid; i < s; i += NT) {
+      T acc = zero<T>();
+      for (int k = 0; k < K; ++k) {
+        const T* g = G + (size_t)k * s * r + i;
+        T mk = zero<T>();
+        for (int j = 0; j < r; ++j) mk += g[(size_t)j * s] * y[j];
+        acc += th[k] * mk;
+      }
+      part += absq(bJ[i] - acc);
+    }
+    const double tot = block_sum<NT>(part, red);
+    if (tid == 0) rho[q] = sqrt(tot) / bJ_norm;
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_residual(const sas_ctx* c, const double* params, int64_t m, const void* Y,
+                            double* rho, cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  int64_t grid = m < (int64_t)c->num_sms * 8 ? m : (int64_t)c->num_sms * 8;
+  if (c->dtype == SAS_COMPLEX128)
+    residual_affine_kernel<zd, 256><<<(unsigned)grid, 256, 0, st>>>(
+        (const zd*)c->G, (const zd*)c->bJ, params, m, c->s, c->r, c->K, c->dp, c->theta_rule,
+        (const zd*)Y, c->bJ_norm, rho);
+  else
+    residual_affine_kernel<double, 256><<<(unsigned)grid, 256, 0, st>>>(
+        (const double*)c->G, (const double*)c->bJ, params, m, c->s, c->r, c->K, c->dp,
+        c->theta_rule, (const double*)Y, c->bJ_norm, rho);
+  return cudaGetLastError();
+}
+
+}  // namespace sas

@@ -1,0 +1,92 @@
+"""Device-side inputs of one context, kept alive next to it.
+
+This is marshalling: it copies a problem's operator blocks (CSR), basis S,
+right-hand side and QoI vector to device tensors, fills the C descriptor and
+owns the context.  No arithmetic of the online stage happens here.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import api
+
+
+def csr_to_device(A, device):
+    A = A.tocsr()
+    A.sort_indices()
+    return (torch.from_numpy(A.indptr.astype(np.int64)).to(device),
+            torch.from_numpy(A.indices.astype(np.int32)).to(device),
+            torch.from_numpy(np.ascontiguousarray(A.data, dtype=np.float64)).to(device))
+
+
+def basis_to_device(S, device, complex_valued=False):
+    """n x r basis -> device tensor of shape (r, n) (column-major n x r, ldS = n)."""
+    if isinstance(S, torch.Tensor):
+        t = S.to(device)
+        return t.T.contiguous()
+    dt = np.complex128 if complex_valued else np.float64
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(S, dtype=dt).T)).to(device)
+
+
+class AffineSolver:
+    """Context for A(p) = sum_k theta_k(p) A_k built from a workload problem."""
+
+    def __init__(self, prob, S, J, mode=api.SAS_MODE_PLAIN, device="cuda", S_device=None,
+                 blocks_device=None, b_device=None, c_device=None):
+        self.prob = prob
+        self.device = device
+        cplx = bool(prob.complex_valued)
+        self.complex_valued = cplx
+        self.blocks = blocks_device or [csr_to_device(A, device) for A in prob.blocks]
+        self.S = S_device if S_device is not None else basis_to_device(S, device, cplx)
+        bdt = np.complex128 if cplx else np.float64
+        self.b = b_device if b_device is not None else \
+            torch.from_numpy(np.ascontiguousarray(prob.b, dtype=bdt)).to(device)
+        qk = api.SAS_QOI_NONE
+        self.c = None
+        if getattr(prob, "qoi_kind", None) == "mean":
+            qk = api.SAS_QOI_MEAN
+        elif getattr(prob, "qoi_kind", None) == "transpose":
+            qk = api.SAS_QOI_TRANSPOSE
+            self.c = c_device if c_device is not None else \
+                torch.from_numpy(np.ascontiguousarray(prob.c, dtype=np.float64)).to(device)
+        rule = api.SAS_THETA_PENCIL if prob.theta_rule == "pencil" else api.SAS_THETA_LINEAR
+        self.J = np.asarray(J, dtype=np.int64)
+        self.desc = api._affine_desc(prob.n, prob.r, len(self.J), self.blocks, self.S, self.J,
+                                     self.b, rule, mode, qk, self.c, cplx)
+        self.mode = mode
+        self.r = prob.r
+        self.s = len(self.J)
+        self.n = prob.n
+        self.ctx = api.subapsnap_setup_affine(self.desc)
+
+    def close(self):
+        if self.ctx is not None:
+            api.subapsnap_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- marshalled calls
+    def solve(self, params, out_kind, out, flags=None, rho=None, stream=None):
+        api.subapsnap_solve_batch(self.ctx, params, params.shape[0], out_kind, out, flags, rho, stream)
+
+    def residual(self, params, Y, rho, stream=None):
+        api.subapsnap_residual(self.ctx, params, params.shape[0], Y, rho, stream)
+
+    def true_residual(self, params, X, rho, stream=None):
+        api.subapsnap_true_residual(self.ctx, params, params.shape[0], X, rho, stream)
+
+
+def select_rows(prob, S_device, blocks_device, p_sel, s, device="cuda"):
+    """CPQR-in-rounds row selection on the device; returns (J, gaps) on the host."""
+    cplx = bool(prob.complex_valued)
+    rule = api.SAS_THETA_PENCIL if prob.theta_rule == "pencil" else api.SAS_THETA_LINEAR
+    desc = api._affine_desc(prob.n, prob.r, s, blocks_device, S_device, None, None, rule,
+                            api.SAS_MODE_PLAIN, api.SAS_QOI_NONE, None, cplx)
+    return api.subapsnap_select_rows_affine(desc, p_sel, s)

@@ -1,0 +1,254 @@
+"""GPU parity of the affine online stage against the oracle, through the C-ABI.
+
+Tolerances
+  plain float64: ||x_gpu - x_oracle|| / ||x_oracle|| <= 1e-10 for every parameter
+    whose kappa(M) * 1.1e-16 <= 1e-11; two backward-stable float64 solvers
+    may differ by ~kappa(M) u, so parameters beyond that bound are checked on
+    the residual instead (the count is reported).  Row sets J must match the
+    oracle exactly, in order.
+  mixed: the float32 factorisation with float64-residual refinement converges
+    to the least-squares solution of the perturbed matrix, so its distance to
+    the float64 answer is bounded by ~kappa^2 u32 ||r*|| / (||M|| ||y||) plus
+    float64 rounding; the test takes 16x that bound plus 1e-11.  The
+    subsampled residual must agree with the plain one to 1e-6 relative
+    (it is quadratic in the error of y).  x_hat is float32 from tf32-split
+    operands: relative error <= 2e-6 per parameter.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU runs deselect with -m "not gpu"
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2510_04825_gb300 import api  # noqa: E402
+from paper_2510_04825_gb300.solver import AffineSolver, basis_to_device, csr_to_device, select_rows  # noqa: E402
+
+from _problems import Case  # noqa: E402
+
+U32 = 2.0 ** -24
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def c0():
+    return Case("reaction_diffusion_1d")
+
+
+@pytest.fixture(scope="module")
+def c1_small():
+    return Case("diffusion_2d", N=48, r=60, s=120, m=257)
+
+
+@pytest.fixture(scope="module")
+def c3_small():
+    return Case("transfer_function", N=9, r=20, s=50, m=300)
+
+
+def run(case, mode, out_kind, params=None, m=None):
+    p = case.prob
+    params = p.test_params if params is None else params
+    m = params.shape[0] if m is None else m
+    solver = AffineSolver(p, case.S, case.J, mode=mode, device=DEV)
+    P = torch.from_numpy(np.ascontiguousarray(params[:m], dtype=np.float64)).to(DEV)
+    cplx = p.complex_valued
+    if out_kind == api.SAS_OUT_Y:
+        out = torch.empty((m, p.r), dtype=torch.complex128 if cplx else torch.float64, device=DEV)
+    elif out_kind == api.SAS_OUT_QOI:
+        out = torch.empty(m, dtype=torch.complex128 if cplx else torch.float64, device=DEV)
+    else:
+        out = torch.empty((m, p.n), dtype=torch.float32 if mode == api.SAS_MODE_MIXED else torch.float64,
+                          device=DEV)
+    flags = torch.zeros(m, dtype=torch.int32, device=DEV)
+    rho = torch.empty(m, dtype=torch.float64, device=DEV)
+    solver.solve(P, out_kind, out, flags, rho)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy(), flags.cpu().numpy(), rho.cpu().numpy()
+    solver.close()
+    return res
+
+
+def rel_err_rows(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+def plain_parity(case, params=None):
+    p = case.prob
+    params = p.test_params if params is None else params
+    Y, flags, rho = run(case, api.SAS_MODE_PLAIN, api.SAS_OUT_Y, params)
+    Yo, rho_o = case.oracle_solve(params)
+    err = rel_err_rows(Y, Yo)
+    kap = case.kappas(params)
+    strict = kap * 1.1e-16 <= 1e-11
+    assert strict.sum() > 0
+    assert err[strict].max() <= 1e-10, (err[strict].max(), kap[strict].max())
+    # beyond the strict range: residual parity
+    if (~strict).any():
+        np.testing.assert_allclose(rho[~strict], rho_o[~strict], rtol=1e-6, atol=1e-14)
+    # rho is relative to ||b_J||: its rounding error is ~kappa(M) u in absolute terms
+    assert (np.abs(rho - rho_o) <= 1e-8 * rho_o + 64 * kap * 1.1e-16).all()
+    assert not (flags & api.SAS_FLAG_NONFINITE).any()
+    return err, kap
+
+
+def test_c0_row_selection_matches_oracle(c0):
+    p = c0.prob
+    S_d = basis_to_device(c0.S, DEV)
+    blocks = [csr_to_device(A, DEV) for A in p.blocks]
+    J, gaps = select_rows(p, S_d, blocks, p.sel_param, p.s)
+    np.testing.assert_array_equal(J, c0.J)
+    np.testing.assert_allclose(gaps, c0.gaps, rtol=1e-6, atol=1e-12)
+
+
+def test_c0_plain_parity(c0):
+    err, kap = plain_parity(c0)
+    print(f"c0 plain: max rel err {err.max():.2e}, kappa max {kap.max():.2e}")
+
+
+def test_c0_plain_xhat(c0):
+    p = c0.prob
+    X, flags, rho = run(c0, api.SAS_MODE_PLAIN, api.SAS_OUT_XHAT)
+    Yo, _ = c0.oracle_solve(p.test_params)
+    Xo = Yo @ c0.S.T
+    err = rel_err_rows(X, Xo)
+    kap = c0.kappas(p.test_params)
+    strict = kap * 1.1e-16 <= 1e-11
+    assert err[strict].max() <= 1e-10
+
+
+def test_c1_small_plain_parity_ragged(c1_small):
+    err, kap = plain_parity(c1_small)
+    print(f"c1-small plain: max rel err {err.max():.2e}, kappa max {kap.max():.2e}")
+
+
+def test_c1_small_plain_xhat_and_qoi(c1_small):
+    p = c1_small.prob
+    X, _, _ = run(c1_small, api.SAS_MODE_PLAIN, api.SAS_OUT_XHAT)
+    H, _, _ = run(c1_small, api.SAS_MODE_PLAIN, api.SAS_OUT_QOI)
+    Yo, _ = c1_small.oracle_solve(p.test_params)
+    Xo = Yo @ c1_small.S.T
+    assert rel_err_rows(X, Xo).max() <= 1e-10
+    Ho = Xo.mean(axis=1)  # grid mean of x_hat
+    np.testing.assert_allclose(H, Ho, rtol=1e-10, atol=1e-14 * np.abs(Ho).max())
+
+
+def mixed_bound(case, params, Yo, rho_o):
+    from oracle import online
+    bounds = []
+    for prm, y, rr in zip(params, Yo, rho_o):
+        M = online.subsampled_matrix(case.prob, case.S, case.J, prm)
+        sv = np.linalg.svd(M, compute_uv=False)
+        kap = sv[0] / sv[-1]
+        bJ = case.prob.b[case.J]
+        rstar = rr * np.linalg.norm(bJ)
+        bounds.append(1e-11 + 16 * (kap ** 2 * U32 * rstar / (sv[0] * np.linalg.norm(y)) + kap * 1.1e-16))
+    return np.array(bounds)
+
+
+@pytest.mark.parametrize("name", ["c0", "c1_small", "c3_small"])
+def test_mixed_error_bound_and_equal_residual(name, request):
+    case = request.getfixturevalue(name)
+    p = case.prob
+    params = p.test_params[:200]
+    Y, flags, rho = run(case, api.SAS_MODE_MIXED, api.SAS_OUT_Y, params)
+    Yo, rho_o = case.oracle_solve(params)
+    err = rel_err_rows(Y, Yo)
+    bound = mixed_bound(case, params, Yo, rho_o)
+    print(f"{name} mixed: max rel err {err.max():.2e}, median {np.median(err):.2e}, "
+          f"max err/bound {(err / bound).max():.2e}, stalled {(flags & api.SAS_FLAG_REFINE_STALL).astype(bool).sum()}")
+    assert (err <= bound).all()
+    kap = case.kappas(params)
+    assert (np.abs(rho - rho_o) <= 1e-6 * rho_o + 64 * kap * 1.1e-16).all()
+    # REFINE_STALL means refinement failed outright (correction still above 1e-8 |y|)
+    assert not (flags & api.SAS_FLAG_REFINE_STALL)[kap < 1e3].any()
+
+
+def test_c1_small_mixed_xhat(c1_small):
+    p = c1_small.prob
+    X, _, _ = run(c1_small, api.SAS_MODE_MIXED, api.SAS_OUT_XHAT)
+    Yo, _ = c1_small.oracle_solve(p.test_params)
+    Xo = Yo @ c1_small.S.T
+    err = rel_err_rows(X.astype(np.float64), Xo)
+    print(f"c1-small mixed x_hat: max rel err {err.max():.2e}")
+    assert err.max() <= 2e-6
+
+
+def test_c3_small_plain_parity_and_qoi(c3_small):
+    p = c3_small.prob
+    err, kap = plain_parity(c3_small)
+    print(f"c3-small plain: max rel err {err.max():.2e}, kappa max {kap.max():.2e}")
+    H, _, _ = run(c3_small, api.SAS_MODE_PLAIN, api.SAS_OUT_QOI)
+    Yo, _ = c3_small.oracle_solve(p.test_params)
+    from oracle import online
+    Ho = online.qoi(p, c3_small.S, Yo)
+    kap_ok = kap * 1.1e-16 <= 1e-11
+    np.testing.assert_allclose(H[kap_ok], Ho[kap_ok], rtol=1e-10, atol=1e-12 * np.abs(Ho).max())
+
+
+def test_c3_small_row_selection_complex(c3_small):
+    p = c3_small.prob
+    S_d = basis_to_device(c3_small.S, DEV, complex_valued=True)
+    blocks = [csr_to_device(A, DEV) for A in p.blocks]
+    J, gaps = select_rows(p, S_d, blocks, p.sel_param, p.s)
+    near = c3_small.gaps < 1e-10
+    assert not near.any()
+    np.testing.assert_array_equal(J, c3_small.J)
+
+
+def test_blocked_householder_path():
+    """s x (r+1) too large for shared memory: the row-blocked QR update runs."""
+    case = Case("diffusion_2d", basis="random", N=24, r=100, s=300, m=40)
+    err, kap = plain_parity(case)
+    print(f"blocked path: max rel err {err.max():.2e}, kappa max {kap.max():.2e}")
+
+
+def test_square_subsample_and_single_parameter():
+    case = Case("reaction_diffusion_1d", n=512, r=12, s=12, m=5)
+    err, _ = plain_parity(case)
+    Y1, _, rho1 = run(case, api.SAS_MODE_PLAIN, api.SAS_OUT_Y, m=1)
+    assert Y1.shape == (1, 12)
+    assert rho1[0] < 1e-12  # s = r interpolates
+
+
+def test_true_residual_matches_oracle(c1_small):
+    from oracle import online
+    p = c1_small.prob
+    params = p.test_params[:16]
+    Yo, _ = c1_small.oracle_solve(params)
+    Xo = np.ascontiguousarray(Yo @ c1_small.S.T)
+    solver = AffineSolver(p, c1_small.S, c1_small.J, device=DEV)
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
+    rho = torch.empty(len(params), dtype=torch.float64, device=DEV)
+    solver.true_residual(P, torch.from_numpy(Xo).to(DEV), rho)
+    Ysub = torch.from_numpy(np.ascontiguousarray(Yo)).to(DEV)
+    rsub = torch.empty(len(params), dtype=torch.float64, device=DEV)
+    solver.residual(P, Ysub, rsub)
+    torch.cuda.synchronize()
+    ref = [online.true_residual(p, prm, x) for prm, x in zip(params, Xo)]
+    ref_sub = [online.subsampled_residual(p, c1_small.S, c1_small.J, prm, y) for prm, y in zip(params, Yo)]
+    np.testing.assert_allclose(rho.cpu().numpy(), ref, rtol=1e-6)
+    np.testing.assert_allclose(rsub.cpu().numpy(), ref_sub, rtol=1e-6, atol=1e-15)
+    solver.close()
+
+
+def test_invalid_arguments_raise():
+    case = Case("reaction_diffusion_1d", n=256, r=8, s=16, m=4)
+    p = case.prob
+    J = case.J.copy()
+    J[3] = J[2]
+    with pytest.raises(api.SasError) as ei:
+        AffineSolver(p, case.S, J, device=DEV)
+    assert ei.value.code == api.SAS_EINVAL
+    J = case.J.copy()
+    J[0] = p.n
+    with pytest.raises(api.SasError):
+        AffineSolver(p, case.S, J, device=DEV)
+    solver = AffineSolver(p, case.S, case.J, device=DEV)
+    P = torch.zeros((0, 1), dtype=torch.float64, device=DEV)
+    out = torch.zeros((1, p.r), dtype=torch.float64, device=DEV)
+    api.subapsnap_solve_batch(solver.ctx, P, 0, api.SAS_OUT_Y, out)  # m = 0: no-op
+    with pytest.raises(api.SasError):
+        api.subapsnap_solve_batch(solver.ctx, P, 1, 7, out)
+    solver.close()

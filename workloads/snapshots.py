@@ -1,0 +1,176 @@
+"""Snapshot bases S for the workloads (inputs of the online stage).
+
+The online stage takes an orthonormal basis S of snapshot solutions
+x(p_1), ..., x(p_r) as given.  This module produces it with generic solvers
+that are neither the oracle nor the product library:
+  * small and medium affine problems: sparse direct solves (scipy);
+  * the 1-D tridiagonal problem: banded LU (scipy.linalg.solve_banded);
+  * large 2-D diffusion problems: preconditioned CG on the GPU with torch,
+    preconditioned by the constant-coefficient Laplacian, inverted with a
+    sine transform (see ``diffusion_pcg``);
+followed by a thin QR (numpy / torch) that orthonormalises the columns.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+def _A(prob, p):
+    p = np.atleast_1d(np.asarray(p, dtype=np.float64))
+    if prob.theta_rule == "linear":
+        A = prob.blocks[0].copy()
+        for k in range(1, len(prob.blocks)):
+            A = A + p[k - 1] * prob.blocks[k]
+        return A.tocsc()
+    if prob.theta_rule == "pencil":
+        return (1j * p[0] * prob.blocks[1] - prob.blocks[0]).tocsc()
+    raise ValueError(prob.theta_rule)
+
+
+def snapshot_solutions(prob) -> np.ndarray:
+    """X = [x(p_1), ..., x(p_r)] (n x r) by direct solves."""
+    if prob.name == "reaction_diffusion_1d":
+        d = prob.meta["d"]
+        cols = []
+        for p in prob.snap_params[:, 0]:
+            ab = np.zeros((3, prob.n))
+            ab[0, 1:] = -1.0
+            ab[1] = 2.0 + p * d
+            ab[2, :-1] = -1.0
+            cols.append(sla.solve_banded((1, 1), ab, prob.b))
+        return np.stack(cols, 1)
+    if hasattr(prob, "X"):  # kernel ridge, small N: dense solves
+        from .operators import gaussian_kernel_block
+        cols = []
+        for sig, lam in prob.snap_params:
+            K = gaussian_kernel_block(prob.X, prob.X, sig) + lam * np.eye(prob.n)
+            cols.append(np.linalg.solve(K, prob.b))
+        return np.stack(cols, 1)
+    cols = [spla.spsolve(_A(prob, p), prob.b) for p in prob.snap_params]
+    return np.stack(cols, 1)
+
+
+def orthonormalise(X: np.ndarray) -> np.ndarray:
+    Q, _ = np.linalg.qr(X, mode="reduced")
+    return np.ascontiguousarray(Q)
+
+
+def basis(prob) -> np.ndarray:
+    """Orthonormal snapshot basis S (n x r) by direct solves."""
+    return orthonormalise(snapshot_solutions(prob))
+
+
+# ---------------------------------------------------------------------------
+# Large 2-D diffusion problems: batched PCG on the GPU (torch).
+# ---------------------------------------------------------------------------
+
+def _dst1_last(v):
+    """Unnormalised DST-I along the last axis: y_k = sum_j v_j sin(pi j k / (N+1))."""
+    import torch
+    N = v.shape[-1]
+    z = torch.zeros(v.shape[:-1] + (2 * (N + 1),), dtype=v.dtype, device=v.device)
+    z[..., 1:N + 1] = v
+    z[..., N + 2:] = -torch.flip(v, dims=(-1,))
+    Z = torch.fft.rfft(z, dim=-1)
+    return -0.5 * Z[..., 1:N + 1].imag
+
+
+def _dst2(u):
+    return _dst1_last(_dst1_last(u).transpose(-1, -2)).transpose(-1, -2)
+
+
+def diffusion_faces_torch(prob, params, device):
+    """Face coefficients a = 1 + sum_k p_k psi_k for a batch of parameters.
+
+    Returns (ax, ay) with ax[b, j, i_face] of shape (B, N, N+1) and
+    ay[b, j_face, i] of shape (B, N+1, N), matching the CSR blocks of
+    ``workloads.operators.diffusion_2d``.
+    """
+    import torch
+    faces = prob.meta["faces"]
+    P = torch.as_tensor(np.asarray(params, dtype=np.float64), device=device)
+    N = prob.grid[0]
+    ax = torch.ones((P.shape[0], N, N + 1), dtype=torch.float64, device=device)
+    ay = torch.ones((P.shape[0], N + 1, N), dtype=torch.float64, device=device)
+    for k, (fx, fy) in enumerate(faces):
+        gx = torch.as_tensor(np.ascontiguousarray(fx.T), device=device)  # (N, N+1)
+        gy = torch.as_tensor(np.ascontiguousarray(fy.T), device=device)  # (N+1, N)
+        ax += P[:, k, None, None] * gx[None]
+        ay += P[:, k, None, None] * gy[None]
+    return ax, ay
+
+
+def diffusion_apply_torch(u, ax, ay, h):
+    """-div(a grad u) / h^2 on (B, N, N) arrays, u[b, j, i] = u_{i + N j}."""
+    import torch.nn.functional as F
+    up = F.pad(u, (1, 1, 1, 1))
+    fx = ax * (up[:, 1:-1, 1:] - up[:, 1:-1, :-1])
+    fy = ay * (up[:, 1:, 1:-1] - up[:, :-1, 1:-1])
+    return -((fx[:, :, 1:] - fx[:, :, :-1]) + (fy[:, 1:, :] - fy[:, :-1, :])) / (h * h)
+
+
+def diffusion_pcg(prob, params, device="cuda", rtol=1e-11, maxit=400, group=None):
+    """Solve A(p) x = b for a batch of parameters with Laplacian-preconditioned CG.
+
+    The preconditioner is the constant-coefficient operator (a = 1), applied
+    exactly through the 2-D sine transform; since 1 <= a(x; p) <= 1 + sum p_k,
+    the preconditioned condition number is at most max a / min a.
+    Returns a torch tensor X of shape (B, n) (float64, on ``device``) and the
+    final relative residuals.
+    """
+    import torch
+    N = prob.grid[0]
+    h = 1.0 / (N + 1)
+    params = np.atleast_2d(np.asarray(params, dtype=np.float64))
+    B = params.shape[0]
+    if group is None:
+        group = max(1, min(B, int(2.0e9 // (N * N * 8 * 12))))
+    k = torch.arange(1, N + 1, dtype=torch.float64, device=device)
+    s2 = torch.sin(np.pi * k / (2 * (N + 1))) ** 2
+    lam = (4.0 / (h * h)) * (s2[:, None] + s2[None, :])
+    scale = (2.0 / (N + 1)) ** 2
+    bvec = torch.as_tensor(np.asarray(prob.b, dtype=np.float64).reshape(N, N), device=device)
+    out = torch.empty((B, N * N), dtype=torch.float64, device=device)
+    finals = []
+    for g0 in range(0, B, group):
+        P = params[g0:g0 + group]
+        ax, ay = diffusion_faces_torch(prob, P, device)
+        b = bvec.expand(P.shape[0], N, N).clone()
+        bn = torch.linalg.vector_norm(b.reshape(len(P), -1), dim=1)
+        x = torch.zeros_like(b)
+        r = b.clone()
+        z = scale * _dst2(_dst2(r) / lam)
+        p = z.clone()
+        rz = (r * z).sum(dim=(1, 2))
+        for _ in range(maxit):
+            Ap = diffusion_apply_torch(p, ax, ay, h)
+            alpha = rz / (p * Ap).sum(dim=(1, 2))
+            x += alpha[:, None, None] * p
+            r -= alpha[:, None, None] * Ap
+            rel = torch.linalg.vector_norm(r.reshape(len(P), -1), dim=1) / bn
+            if bool((rel < rtol).all()):
+                break
+            z = scale * _dst2(_dst2(r) / lam)
+            rz_new = (r * z).sum(dim=(1, 2))
+            p = z + (rz_new / rz)[:, None, None] * p
+            rz = rz_new
+        res = diffusion_apply_torch(x, ax, ay, h) - b
+        finals.append((torch.linalg.vector_norm(res.reshape(len(P), -1), dim=1) / bn).cpu().numpy())
+        out[g0:g0 + len(P)] = x.reshape(len(P), -1)
+        del ax, ay, b, x, r, z, p
+    return out, np.concatenate(finals)
+
+
+def diffusion_basis_torch(prob, device="cuda", **kw):
+    """Orthonormal snapshot basis of a 2-D diffusion workload on the device.
+
+    Returns (S_rows, final_residuals) with S_rows of shape (r, n): row k is
+    column k of S, i.e. the column-major n x r layout with leading dimension n.
+    """
+    import torch
+    X, res = diffusion_pcg(prob, prob.snap_params, device=device, **kw)
+    Q, _ = torch.linalg.qr(X.T, mode="reduced")
+    return Q.T.contiguous(), res
