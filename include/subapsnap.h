@@ -180,6 +180,30 @@ sas_status subapsnap_true_residual(sas_ctx* ctx, const double* params, int64_t m
 sas_status subapsnap_select_rows_affine(const sas_affine_desc* desc, const double* p_sel,
                                         int64_t* J_out, double* gap_out);
 
+/* Capacity, in coefficients (m * r), of the fixed device array used by
+ * subapsnap_solve_batch_xhat_noalloc: 65536 doubles = 512 KiB. */
+#define SAS_NOALLOC_MAX_Y 65536
+
+/* Same result as subapsnap_solve_batch(ctx, params, m, SAS_OUT_XHAT, out,
+ * flags, rho, stream) on the plain float64 path (whatever the context's
+ * mode), for callers that cannot allocate device memory when they solve:
+ * the call calls no cudaMalloc, cudaFree or allocating library routine.  The
+ * m x r coefficient vectors between the least-squares and reconstruction
+ * kernels go to one fixed device array of SAS_NOALLOC_MAX_Y doubles that
+ * every device loading the library holds until the process exits.  No
+ * counterpart in the paper: this is a deployment variant of the online
+ * stage (Alg. 1 step 4).
+ *  params: device m x dp; out: device m x n doubles (row j = x_hat of
+ *  parameter j); flags, rho: device m or NULL, as for solve_batch.
+ * The first call on a device looks the array's address up with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the array and calls that overlap on the GPU race on it.
+ * Errors: SAS_EINVAL if m * r > SAS_NOALLOC_MAX_Y or a pointer is NULL;
+ * SAS_ENOTSUP for a complex or kernel-family context; SAS_ECUDA. */
+sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params, int64_t m,
+                                              double* out, uint32_t* flags, double* rho,
+                                              void* stream);
+
 /* Kernel classes reported by the tracer. */
 enum { SAS_KERNEL_LS = 0,           /* assembly + least squares (+ QoI epilogue) */
        SAS_KERNEL_RECONSTRUCT = 1,  /* x_hat = S y */

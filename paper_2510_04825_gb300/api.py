@@ -30,8 +30,9 @@ EXPORTED = [
     "subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
     "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
     "subapsnap_destroy", "subapsnap_last_error", "subapsnap_device_status", "subapsnap_version",
-    "subapsnap_set_tracing", "subapsnap_trace_read",
+    "subapsnap_set_tracing", "subapsnap_trace_read", "subapsnap_solve_batch_xhat_noalloc",
 ]
+SAS_NOALLOC_MAX_Y = 65536
 SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL = 0, 1, 2
 
 
@@ -88,11 +89,13 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_version.restype = ctypes.c_char_p
         L.subapsnap_device_status.argtypes = [vp, vp]
         L.subapsnap_set_tracing.argtypes = [vp, i32]
+        L.subapsnap_solve_batch_xhat_noalloc.argtypes = [vp, vp, i64, vp, vp, vp, vp]
         L.subapsnap_trace_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
         for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
-                     "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read"):
+                     "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
+                     "subapsnap_solve_batch_xhat_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -166,6 +169,12 @@ def subapsnap_solve_batch(ctx, params, m: int, out_kind: int, out, flags=None, r
                           stream=None):
     _check(lib().subapsnap_solve_batch(ctx, _ptr(params), int(m), int(out_kind), _ptr(out),
                                        _ptr(flags), _ptr(rho), _stream(stream)))
+
+
+def subapsnap_solve_batch_xhat_noalloc(ctx, params, m: int, out, flags=None, rho=None,
+                                       stream=None):
+    _check(lib().subapsnap_solve_batch_xhat_noalloc(ctx, _ptr(params), int(m), _ptr(out),
+                                                    _ptr(flags), _ptr(rho), _stream(stream)))
 
 
 def subapsnap_residual(ctx, params, m: int, Y, rho, stream=None):
