@@ -32,6 +32,7 @@ if ROOT not in sys.path:
 
 GRID = 1024
 R, S_ROWS, M, CHUNK = 60, 120, 4096, 256
+TC_VERSION = "tcgen05-v1"
 METRIC = "new-p solves/sec on 1 GB300 at stated rel. residual (chosen vs plain FP64)"
 WORKLOAD = "diffusion_2d_1024x1024_r60_s120_m4096_chunk256"
 
@@ -95,14 +96,14 @@ def stop_clock_sampler(p, f, path, gpu_index):
             "samples": len(sm)}
 
 
-def build_inputs(device, rank):
+def build_inputs(device, rank, grid=GRID):
     """Problem, snapshot basis (device), row selection and parameter batch."""
     import torch
     from paper_2510_04825_gb300.solver import csr_to_device, select_rows
     from workloads import get_config
     from workloads import snapshots as wsnap
 
-    prob = get_config("diffusion_2d", N=GRID, r=R, s=S_ROWS, m=M)
+    prob = get_config("diffusion_2d", N=grid, r=R, s=S_ROWS, m=M)
     blocks = [csr_to_device(A, device) for A in prob.blocks]
     S_rows, snap_res = wsnap.diffusion_basis_torch(prob, device=device)
     J, gaps = select_rows(prob, S_rows, blocks, prob.sel_param, S_ROWS, device=device)
@@ -127,7 +128,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
         pg = dist
     t_setup = time.time()
-    prob, blocks, S_rows, J, gaps, P, params_host, snap_res = build_inputs(device, rank)
+    prob, blocks, S_rows, J, gaps, P, params_host, snap_res = build_inputs(device, rank, args.grid)
     chosen = AffineSolver(prob, None, J, mode=api.SAS_MODE_MIXED, device=device, S_device=S_rows,
                           blocks_device=blocks)
     plain = AffineSolver(prob, None, J, mode=api.SAS_MODE_PLAIN, device=device, S_device=S_rows,
@@ -191,11 +192,18 @@ def run_gpu(args):
 
     # ---- plain float64 form
     psteps = max(1, min(args.steps, 3))
-    api.subapsnap_set_tracing(plain.ctx, True)
-    ms_plain, _ = timed(lambda: step(plain, out64, rho_p), psteps, 1)
-    prec_ms, prec_n = api.subapsnap_trace_read(plain.ctx, api.SAS_KERNEL_RECONSTRUCT)
-    pls_ms, pls_n = api.subapsnap_trace_read(plain.ctx, api.SAS_KERNEL_LS)
-    api.subapsnap_set_tracing(plain.ctx, False)
+    if args.no_plain:
+        ms_plain, prec_ms, prec_n, pls_ms, pls_n = float("nan"), 0.0, 0, 0.0, 0
+    else:
+        api.subapsnap_set_tracing(plain.ctx, True)
+        ms_plain, _ = timed(lambda: step(plain, out64, rho_p), psteps, 1)
+        prec_ms, prec_n = api.subapsnap_trace_read(plain.ctx, api.SAS_KERNEL_RECONSTRUCT)
+        pls_ms, pls_n = api.subapsnap_trace_read(plain.ctx, api.SAS_KERNEL_LS)
+        api.subapsnap_set_tracing(plain.ctx, False)
+    if args.quick:
+        print(json.dumps({"workload": f"diffusion_2d_{args.grid}", "ms_per_step_chosen": ms_chosen,
+                          "reconstruct_ms": rec_ms / max(rec_n, 1), "ls_ms": ls_ms / max(ls_n, 1)}))
+        return
 
     # ---- accuracy of the chosen form against the plain float64 form (same parameters)
     Yc = torch.empty((M, R), dtype=torch.float64, device=device)
@@ -252,6 +260,10 @@ def run_gpu(args):
 
     value = world * M / (ms_chosen * 1e-3)
     plain_value = world * M / (ms_plain * 1e-3)
+    if args.grid != GRID:
+        line_workload = f"diffusion_2d_{args.grid}x{args.grid}_r60_s120_m4096_chunk256"
+    else:
+        line_workload = WORKLOAD
     launches_per_step = 2 * nchunks
     line = {
         "metric": METRIC,
@@ -266,7 +278,7 @@ def run_gpu(args):
         "vs_baseline": None,
         "dtype": "f32 (tf32x3 tensor cores, f32 Householder) + f64 refinement residual",
         "data": "synthetic (seeded 2-D diffusion workload, snapshot basis from PCG)",
-        "config": {"workload": WORKLOAD, "n": n, "r": R, "s": S_ROWS, "m_per_gpu": M, "chunk": CHUNK,
+        "config": {"workload": line_workload, "n": n, "r": R, "s": S_ROWS, "m_per_gpu": M, "chunk": CHUNK,
                    "parallelism": f"dp{world} (independent parameters)",
                    "l2": "inputs larger than L2 (S tf32 split 0.54 GB, x_hat chunk 1.07 GB)"},
         "plain_fp64": {"value": round(plain_value, 2), "unit": "solves/s", "ms_per_step": round(ms_plain, 3),
@@ -299,7 +311,7 @@ def run_gpu(args):
 
 
 def chosen_kernel_version():
-    return "simt-v1"
+    return TC_VERSION
 
 
 def cpu_baseline(prob, S_rows, J, params, nsample=32, budget_s=20.0):
@@ -378,6 +390,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 form")
+    ap.add_argument("--quick", action="store_true", help="time the chosen form only (profiling runs)")
+    ap.add_argument("--grid", type=int, default=GRID, help="interior grid side (profiling runs use 512)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

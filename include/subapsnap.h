@@ -204,11 +204,26 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
                                               double* out, uint32_t* flags, double* rho,
                                               void* stream);
 
+/* Per-context options (subapsnap_set_option).  Not in the paper.
+ *  SAS_OPT_RECON_KERNEL: mixed-form reconstruction kernel: 0 = automatic
+ *      (tensor cores when r <= 64), 1 = CUDA cores, 2 = tensor cores
+ *      (tcgen05, kind::tf32, three split products).
+ *  SAS_OPT_MAX_REFINE: most refinement steps of the mixed solve (0..16,
+ *      default 4).
+ *  SAS_OPT_REFINE_TOL: refinement stops when ||delta|| <= tol ||y||
+ *      (default 1e-13) or when a step no longer halves the correction. */
+enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2 };
+
+/* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
+ * value out of range. */
+sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
+
 /* Kernel classes reported by the tracer. */
 enum { SAS_KERNEL_LS = 0,           /* assembly + least squares (+ QoI epilogue) */
        SAS_KERNEL_RECONSTRUCT = 1,  /* x_hat = S y */
        SAS_KERNEL_RESIDUAL = 2,     /* subsampled / true residual */
-       SAS_KERNEL_CLASSES = 3 };
+       SAS_KERNEL_ASSEMBLE = 3,     /* Gaussian-kernel rows K_sigma(X_J, X) S */
+       SAS_KERNEL_CLASSES = 4 };
 
 /* Tracing: when enabled (enable != 0) every kernel the context launches is
  * bracketed by a pair of CUDA events recorded on the launch stream.  Costs

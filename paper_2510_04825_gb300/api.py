@@ -31,9 +31,11 @@ EXPORTED = [
     "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
     "subapsnap_destroy", "subapsnap_last_error", "subapsnap_device_status", "subapsnap_version",
     "subapsnap_set_tracing", "subapsnap_trace_read", "subapsnap_solve_batch_xhat_noalloc",
+    "subapsnap_set_option",
 ]
+SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL = 0, 1, 2
 SAS_NOALLOC_MAX_Y = 65536
-SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL = 0, 1, 2
+SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL, SAS_KERNEL_ASSEMBLE = 0, 1, 2, 3
 
 
 class SasError(RuntimeError):
@@ -89,13 +91,14 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_version.restype = ctypes.c_char_p
         L.subapsnap_device_status.argtypes = [vp, vp]
         L.subapsnap_set_tracing.argtypes = [vp, i32]
+        L.subapsnap_set_option.argtypes = [vp, i32, ctypes.c_double]
         L.subapsnap_solve_batch_xhat_noalloc.argtypes = [vp, vp, i64, vp, vp, vp, vp]
         L.subapsnap_trace_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
         for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
-                     "subapsnap_solve_batch_xhat_noalloc"):
+                     "subapsnap_solve_batch_xhat_noalloc", "subapsnap_set_option"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -154,6 +157,25 @@ def subapsnap_setup_affine(desc: AffineDesc) -> ctypes.c_void_p:
     return ctx
 
 
+def _kernel_desc(n, d, r, s, X, S, J, b, mode):
+    """Fill the C descriptor of the Gaussian-kernel family.  X is (N, d) row-major,
+    S is (r, N) row-major in memory (column-major N x r, ldS = N)."""
+    k = KernelDesc()
+    k.n, k.d, k.r, k.s, k.mode = int(n), int(d), int(r), int(s), mode
+    k.X, k.S, k.ldS = _ptr(X), _ptr(S), int(n)
+    Jh = np.ascontiguousarray(np.asarray(J, dtype=np.int64))
+    k.J = Jh.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    k._J_keep = Jh
+    k.b = _ptr(b)
+    return k
+
+
+def subapsnap_setup_kernel(desc: KernelDesc) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(lib().subapsnap_setup_kernel(ctypes.byref(desc), ctypes.byref(ctx)))
+    return ctx
+
+
 def subapsnap_select_rows_affine(desc: AffineDesc, p_sel, s: int):
     ps = np.ascontiguousarray(np.atleast_1d(np.asarray(p_sel, dtype=np.float64)))
     J = np.zeros(s, dtype=np.int64)
@@ -188,6 +210,10 @@ def subapsnap_true_residual(ctx, params, m: int, X, rho, stream=None):
 
 def subapsnap_device_status(ctx, stream=None) -> int:
     return int(lib().subapsnap_device_status(ctx, _stream(stream)))
+
+
+def subapsnap_set_option(ctx, key: int, value: float):
+    _check(lib().subapsnap_set_option(ctx, int(key), float(value)))
 
 
 def subapsnap_set_tracing(ctx, enable: bool):

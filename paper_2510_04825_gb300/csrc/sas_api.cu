@@ -90,6 +90,7 @@ static void free_ctx(sas_ctx* c) {
   cudaFree(c->Slo);
   cudaFree(c->ybuf);
   cudaFree(c->ysplit);
+  cudaFree(c->Mbuf);
   cudaFree(c->dev_status);
   if (c->trace) {
     for (auto& t : *c->trace) {
@@ -209,6 +210,9 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
     c->values[k] = k < d->K ? d->values[k] : nullptr;
   }
   c->b_full = d->b;
+  c->recon_kernel = 0;
+  c->max_refine = 4;
+  c->refine_tol = 1e-13;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -267,10 +271,152 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
 }
 
 sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
-  (void)d;
-  if (out) *out = nullptr;
-  return fail(SAS_ENOTSUP, "setup_kernel: the Gaussian-kernel family is not built yet");
+  if (!out) return fail(SAS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(SAS_EINVAL, "descriptor is NULL");
+  if (d->n < 1) return fail(SAS_EINVAL, "n must be positive");
+  if (d->d < 1 || d->d > 16) return fail(SAS_EINVAL, "d must be in [1, 16]");
+  if (d->r < 1 || d->r > kMaxR) return fail(SAS_EINVAL, "r must be in [1, 128]");
+  if (d->s < d->r || d->s > kMaxS || (int64_t)d->s > d->n)
+    return fail(SAS_EINVAL, "need r <= s <= min(n, 512)");
+  if (d->mode != SAS_MODE_PLAIN && d->mode != SAS_MODE_MIXED) return fail(SAS_EINVAL, "bad mode");
+  if (d->ldS < d->n) return fail(SAS_EINVAL, "ldS < n");
+  if (!is_device_ptr(d->X) || !is_device_ptr(d->S) || !is_device_ptr(d->b))
+    return fail(SAS_EINVAL, "X, S and b must be device pointers");
+  sas_status st = check_J(d->J, d->s, d->n);
+  if (st != SAS_OK) return st;
+  sas_ctx* c = new (std::nothrow) sas_ctx();
+  if (!c) return fail(SAS_ENOMEM, "host allocation failed");
+  std::memset((void*)c, 0, sizeof(sas_ctx));
+  c->family = kKernel;
+  c->n = d->n;
+  c->r = d->r;
+  c->s = d->s;
+  c->K = 0;
+  c->d = d->d;
+  c->dtype = SAS_REAL64;
+  c->theta_rule = -1;
+  c->mode = d->mode;
+  c->dp = 2;
+  c->qoi_kind = SAS_QOI_NONE;
+  c->S = d->S;
+  c->ldS = d->ldS;
+  c->X = d->X;
+  c->b_full = d->b;
+  c->recon_kernel = 0;
+  c->max_refine = 4;
+  c->refine_tol = 1e-13;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaSuccess;
+  cudaStream_t sst = nullptr;
+#define TRYK(x)                              \
+  do {                                       \
+    e = (x);                                 \
+    if (e != cudaSuccess) {                  \
+      st = cuda_fail(e, "setup_kernel");     \
+      if (sst) cudaStreamDestroy(sst);       \
+      free_ctx(c);                           \
+      return st;                             \
+    }                                        \
+  } while (0)
+  TRYK(cudaStreamCreateWithFlags(&sst, cudaStreamNonBlocking));
+  TRYK(dmalloc(&c->J_dev, sizeof(int64_t) * d->s));
+  TRYK(cudaMemcpy(c->J_dev, d->J, sizeof(int64_t) * d->s, cudaMemcpyHostToDevice));
+  TRYK(dmalloc(&c->XJ, sizeof(double) * d->s * d->d));
+  TRYK(dmalloc(&c->SJ, sizeof(double) * d->s * d->r));
+  TRYK(cudaMalloc(&c->bJ, sizeof(double) * d->s));
+  TRYK(cudaMalloc(&c->wq, sizeof(double) * d->r));
+  TRYK(cudaMemset(c->wq, 0, sizeof(double) * d->r));
+  TRYK(dmalloc(&c->dev_status, sizeof(int)));
+  TRYK(cudaMemset(c->dev_status, 0, sizeof(int)));
+  TRYK(launch_gather_kernel_rows(c, sst));
+  if (d->mode == SAS_MODE_MIXED) {
+    TRYK(cudaMalloc(&c->bJ32, sizeof(float) * d->s));
+    const int rpad = (d->r + 31) / 32 * 32;
+    TRYK(dmalloc(&c->Shi, (size_t)d->n * rpad * sizeof(float)));
+    TRYK(dmalloc(&c->Slo, (size_t)d->n * rpad * sizeof(float)));
+    TRYK(launch_make_mixed_copies(c, sst));
+  }
+  TRYK(cudaStreamSynchronize(sst));
+  {
+    std::vector<double> hb((size_t)d->s);
+    TRYK(cudaMemcpy(hb.data(), c->bJ, sizeof(double) * d->s, cudaMemcpyDeviceToHost));
+    double nrm2 = 0.0;
+    for (double v : hb) nrm2 += v * v;
+    c->bJ_norm = std::sqrt(nrm2);
+    if (!(c->bJ_norm > 0.0)) {
+      cudaStreamDestroy(sst);
+      free_ctx(c);
+      return fail(SAS_EINVAL, "b_J is zero: the subsampled system has no right-hand side");
+    }
+  }
+  cudaStreamDestroy(sst);
+#undef TRYK
+  *out = c;
+  return SAS_OK;
 }
+
+namespace sas {
+// Dense-M scratch of the kernel family: room for `cap` parameters.
+static sas_status ensure_mbuf(sas_ctx* c, int64_t cap, cudaStream_t st) {
+  if (c->Mbuf_cap >= cap) return SAS_OK;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel rows scratch");
+  cudaFree(c->Mbuf);
+  c->Mbuf = nullptr;
+  c->Mbuf_cap = 0;
+  e = cudaMalloc((void**)&c->Mbuf, sizeof(double) * (size_t)cap * c->s * c->r);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel rows scratch");
+  c->Mbuf_cap = cap;
+  return SAS_OK;
+}
+constexpr int64_t kKernelSubBatch = 512;
+
+static sas_status solve_kernel_family(sas_ctx* c, const double* params, int64_t m, int32_t out_kind,
+                                      void* out, uint32_t* flags, double* rho, cudaStream_t st) {
+  const bool mixed = c->mode == SAS_MODE_MIXED;
+  if (out_kind != SAS_OUT_Y && out_kind != SAS_OUT_XHAT)
+    return fail(SAS_EINVAL, "the kernel family returns y or x_hat");
+  const int64_t cap = m < kKernelSubBatch ? m : kKernelSubBatch;
+  sas_status s2 = ensure_mbuf(c, cap, st);
+  if (s2 != SAS_OK) return s2;
+  if (out_kind == SAS_OUT_XHAT) {
+    s2 = ensure_scratch(c, cap, mixed, st);
+    if (s2 != SAS_OK) return s2;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int64_t b0 = 0; b0 < m && e == cudaSuccess; b0 += cap) {
+    const int64_t mb = m - b0 < cap ? m - b0 : cap;
+    const double* pb = params + b0 * 2;
+    {
+      TraceScope ts(c, SAS_KERNEL_ASSEMBLE, st);
+      e = launch_krr_assemble(c, pb, mb, c->Mbuf, mixed, st);
+    }
+    if (e != cudaSuccess) break;
+    void* yout = out_kind == SAS_OUT_Y ? (void*)((double*)out + b0 * c->r) : c->ybuf;
+    uint32_t* fb = flags ? flags + b0 : nullptr;
+    double* rb = rho ? rho + b0 : nullptr;
+    {
+      TraceScope ts(c, SAS_KERNEL_LS, st);
+      e = mixed ? launch_ls_mixed(c, pb, mb, yout, nullptr,
+                                  out_kind == SAS_OUT_XHAT ? c->ysplit : nullptr, fb, rb, st, c->Mbuf)
+                : launch_ls_plain(c, pb, mb, yout, nullptr, fb, rb, st, c->Mbuf);
+    }
+    if (e != cudaSuccess || out_kind != SAS_OUT_XHAT) continue;
+    {
+      TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
+      if (mixed)
+        e = launch_reconstruct_mixed(c, c->ysplit, mb, (float*)out + b0 * c->n, st);
+      else
+        e = launch_reconstruct_f64(c, c->ybuf, mb, (double*)out + b0 * c->n, st);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+  return SAS_OK;
+}
+}  // namespace sas
 
 sas_status subapsnap_solve_batch(sas_ctx* c, const double* params, int64_t m, int32_t out_kind,
                                  void* out, uint32_t* flags, double* rho, void* stream) {
@@ -281,6 +427,7 @@ sas_status subapsnap_solve_batch(sas_ctx* c, const double* params, int64_t m, in
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   const bool mixed = c->mode == SAS_MODE_MIXED;
+  if (c->family == kKernel) return solve_kernel_family(c, params, m, out_kind, out, flags, rho, st);
   if (c->family != kAffine) return fail(SAS_ENOTSUP, "family not supported");
   switch (out_kind) {
     case SAS_OUT_Y: {
@@ -325,9 +472,28 @@ sas_status subapsnap_residual(sas_ctx* c, const double* params, int64_t m, const
   if (m < 0) return fail(SAS_EINVAL, "m < 0");
   if (m == 0) return SAS_OK;
   if (!params || !Y || !rho) return fail(SAS_EINVAL, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (c->family == kKernel) {
+    // float64 kernel rows, then the residual of the dense M, sub-batch by sub-batch
+    const int64_t cap = m < kKernelSubBatch ? m : kKernelSubBatch;
+    sas_status s2 = ensure_mbuf(c, cap, st);
+    if (s2 != SAS_OK) return s2;
+    cudaError_t e = cudaSuccess;
+    for (int64_t b0 = 0; b0 < m && e == cudaSuccess; b0 += cap) {
+      const int64_t mb = m - b0 < cap ? m - b0 : cap;
+      e = launch_krr_assemble(c, params + b0 * 2, mb, c->Mbuf, false, st);
+      if (e == cudaSuccess) {
+        TraceScope ts(c, SAS_KERNEL_RESIDUAL, st);
+        e = launch_residual(c, params + b0 * 2, mb, (const double*)Y + b0 * c->r, rho + b0, st,
+                            c->Mbuf);
+      }
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "residual");
+    return SAS_OK;
+  }
   if (c->family != kAffine) return fail(SAS_ENOTSUP, "family not supported");
-  TraceScope ts(c, SAS_KERNEL_RESIDUAL, (cudaStream_t)stream);
-  cudaError_t e = launch_residual(c, params, m, Y, rho, (cudaStream_t)stream);
+  TraceScope ts(c, SAS_KERNEL_RESIDUAL, st);
+  cudaError_t e = launch_residual(c, params, m, Y, rho, st);
   if (e != cudaSuccess) return cuda_fail(e, "residual");
   return SAS_OK;
 }
@@ -355,6 +521,26 @@ sas_status subapsnap_select_rows_affine(const sas_affine_desc* d, const double* 
 }
 
 void subapsnap_destroy(sas_ctx* c) { free_ctx(c); }
+
+sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  switch (key) {
+    case SAS_OPT_RECON_KERNEL:
+      if (value != 0.0 && value != 1.0 && value != 2.0) return fail(SAS_EINVAL, "recon kernel must be 0, 1 or 2");
+      c->recon_kernel = (int)value;
+      return SAS_OK;
+    case SAS_OPT_MAX_REFINE:
+      if (!(value >= 0.0 && value <= 16.0)) return fail(SAS_EINVAL, "max refine must be in [0, 16]");
+      c->max_refine = (int)value;
+      return SAS_OK;
+    case SAS_OPT_REFINE_TOL:
+      if (!(value > 0.0 && value < 1.0)) return fail(SAS_EINVAL, "refine tol must be in (0, 1)");
+      c->refine_tol = value;
+      return SAS_OK;
+    default:
+      return fail(SAS_EINVAL, "unknown option");
+  }
+}
 
 sas_status subapsnap_set_tracing(sas_ctx* c, int32_t enable) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");

@@ -158,6 +158,8 @@ struct sas_ctx {
   float* Slo;          // low part
   double bJ_norm;
   // scratch (grown on demand)
+  double* Mbuf;        // kernel family: dense M for a sub-batch (mcap x s x r)
+  int64_t Mbuf_cap;    // parameters Mbuf holds
   void* ybuf;          // m x r dtype
   size_t ybuf_bytes;
   float* ysplit;       // mixed: y split into tf32 hi/lo, 2 x m x r
@@ -165,6 +167,10 @@ struct sas_ctx {
   int* dev_status;     // device status word
   int num_sms;
   int ls_blocks_per_sm;
+  // options
+  int recon_kernel;    // 0 auto, 1 CUDA cores, 2 tensor cores
+  int max_refine;
+  double refine_tol;
   // tracing
   int tracing;
   struct TraceRec {
@@ -197,18 +203,25 @@ cudaError_t launch_gather_vectors(const sas_ctx* c, const double* cvec, cudaStre
 cudaError_t launch_make_mixed_copies(const sas_ctx* c, cudaStream_t st);
 // solve
 cudaError_t launch_ls_plain(const sas_ctx* c, const double* params, int64_t m, void* yout,
-                            void* qoi_out, uint32_t* flags, double* rho, cudaStream_t st);
+                            void* qoi_out, uint32_t* flags, double* rho, cudaStream_t st,
+                            const void* Mg = nullptr);
 cudaError_t launch_ls_mixed(const sas_ctx* c, const double* params, int64_t m, void* yout,
                             void* qoi_out, float* ysplit, uint32_t* flags, double* rho,
-                            cudaStream_t st);
+                            cudaStream_t st, const void* Mg = nullptr);
 size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block);
 size_t ls_mixed_smem_bytes(const sas_ctx* c);
 cudaError_t launch_reconstruct_f64(const sas_ctx* c, const void* Y, int64_t m, void* out,
                                    cudaStream_t st);
 cudaError_t launch_reconstruct_mixed(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                      cudaStream_t st);
+cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
+                                  cudaStream_t st);
+bool reconstruct_tc_supported(const sas_ctx* c);
 cudaError_t launch_residual(const sas_ctx* c, const double* params, int64_t m, const void* Y,
-                            double* rho, cudaStream_t st);
+                            double* rho, cudaStream_t st, const void* Mg = nullptr);
+cudaError_t launch_krr_assemble(const sas_ctx* c, const double* params, int64_t m, double* M,
+                                bool f32, cudaStream_t st);
+cudaError_t launch_gather_kernel_rows(const sas_ctx* c, cudaStream_t st);
 cudaError_t launch_true_residual(const sas_ctx* c, const double* params, int64_t m, const void* X,
                                  double* rho, cudaStream_t st);
 // selection

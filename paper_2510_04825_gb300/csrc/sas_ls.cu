@@ -49,21 +49,19 @@ __device__ inline double block_sum(double v, double* red) {
 // pivot-row entry sits at piv[j*ldp], its tail at tail + j*ldt.  The reflector is
 // H = I - tau v v^H with v = x - beta e_1, beta = -phase(alpha) ||x||, so that
 // H x = beta e_1 and H = H^H; on return piv[k*ldp] holds beta (= R_kk).
-template <typename T, typename R, int NT>
+//
+// One barrier per step: nrm2[k & 1] must hold ||tail_k||^2 on entry (the
+// caller's pre-pass for k = 0); warp 0, which owns column k+1, writes
+// ||tail_{k+1}[next_off..len)||^2 to nrm2[(k+1) & 1] right after updating it.
+// Each warp updates its columns CB at a time so that the CB dot products and
+// warp reductions overlap.
+template <typename T, typename R, int NT, int CB>
 __device__ inline void householder_step(int k, int ncol, T* piv, int ldp, T* tail, int ldt, int len,
-                                        R* red, T* v0_out, R* tau_out) {
+                                        int next_off, R* nrm2, T* v0_out, R* tau_out) {
   constexpr int NW = NT / 32;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const T* tk = tail + (size_t)k * ldt;
-  R part = R(0);
-  for (int i = tid; i < len; i += NT) part += absq(tk[i]);
-  // block reduction in the working precision
-  part = warp_sum(part);
-  if (lane == 0) red[warp] = part;
-  __syncthreads();
-  R tail2 = R(0);
-#pragma unroll
-  for (int w = 0; w < NW; ++w) tail2 += red[w];
+  const R tail2 = nrm2[k & 1];
   const T alpha = piv[(size_t)k * ldp];
   const R a2 = absq(alpha);
   const R nrm = sqrt(a2 + tail2);
@@ -71,15 +69,44 @@ __device__ inline void householder_step(int k, int ncol, T* piv, int ldp, T* tai
   const T beta = rscale(-nrm, phase(alpha));
   const T v0 = alpha - beta;
   const R tau = nrm > R(0) ? R(1) / (nrm * (nrm + aa)) : R(0);
-  __syncthreads();  // red and alpha consumed before anyone writes
-  for (int j = k + 1 + warp; j < ncol; j += NW) {
-    T* tj = tail + (size_t)j * ldt;
-    T w = lane == 0 ? conjv(v0) * piv[(size_t)j * ldp] : zero<T>();
-    for (int i = lane; i < len; i += 32) w += conjv(tk[i]) * tj[i];
-    w = warp_sum(w);
-    const T tw = rscale(tau, w);
-    if (lane == 0) piv[(size_t)j * ldp] -= tw * v0;
-    for (int i = lane; i < len; i += 32) tj[i] -= tw * tk[i];
+  for (int jb = k + 1 + warp; jb < ncol; jb += NW * CB) {
+    T w[CB];
+    T* tj[CB];
+    bool on[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      const int j = jb + c * NW;
+      on[c] = j < ncol;
+      tj[c] = tail + (size_t)(on[c] ? j : k) * ldt;
+      w[c] = (lane == 0 && on[c]) ? conjv(v0) * piv[(size_t)j * ldp] : zero<T>();
+    }
+    for (int i = lane; i < len; i += 32) {
+      const T vi = conjv(tk[i]);
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        if (on[c]) w[c] += vi * tj[c][i];
+    }
+    T tw[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) tw[c] = rscale(tau, warp_sum(w[c]));
+    if (lane == 0) {
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        if (on[c]) piv[(size_t)(jb + c * NW) * ldp] -= tw[c] * v0;
+    }
+    for (int i = lane; i < len; i += 32) {
+      const T vi = tk[i];
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+        if (on[c]) tj[c][i] -= tw[c] * vi;
+    }
+    if (jb == k + 1) {
+      __syncwarp();
+      R part = R(0);
+      for (int i = next_off + lane; i < len; i += 32) part += absq(tj[0][i]);
+      part = warp_sum(part);
+      if (lane == 0) nrm2[(k + 1) & 1] = part;
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -87,6 +114,17 @@ __device__ inline void householder_step(int k, int ncol, T* piv, int ldp, T* tai
     if (v0_out) v0_out[k] = v0;
     if (tau_out) tau_out[k] = tau;
   }
+}
+
+// ||col[0..len)||^2 by warp 0 into *slot (the caller synchronises afterwards).
+template <typename T, typename R>
+__device__ inline void tail_norm_warp0(const T* col, int len, R* slot) {
+  if ((threadIdx.x >> 5) != 0) return;
+  const int lane = threadIdx.x & 31;
+  R part = R(0);
+  for (int i = lane; i < len; i += 32) part += absq(col[i]);
+  part = warp_sum(part);
+  if (lane == 0) *slot = part;
 }
 
 // Back substitution R y = z by one warp: R upper triangular r x r (ld ldr), z
@@ -123,6 +161,7 @@ __device__ inline void backsolve_warp(const T* Rm, int ldr, int r, T* zr /*[4]*/
 // ------------------------------------------------------------------ plain
 template <typename T>
 struct LsPlainArgs {
+  const T* Mg;  // dense M per parameter (m x s x r, ld s), or null: assemble from G
   const T* G;
   const T* bJ;
   const T* wq;
@@ -147,6 +186,7 @@ __global__ void __launch_bounds__(NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
   T* th = P + (size_t)ldt * (r + 1) + (single ? 0 : (size_t)r * (r + 1));
   T* ys = th + kMaxDp;
   double* red = reinterpret_cast<double*>(ys + kMaxR);
+  __shared__ double nrm2[2];
   const int tid = threadIdx.x, warp = tid >> 5;
 
   for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) {
@@ -159,9 +199,13 @@ __global__ void __launch_bounds__(NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
         const int i = idx % tb, j = idx / tb;
         T v;
         if (j < r) {
-          v = zero<T>();
-          const T* g = a.G + (size_t)j * s + row0 + i;
-          for (int k = 0; k < K; ++k) v += th[k] * g[(size_t)k * s * r];
+          if (a.Mg) {
+            v = a.Mg[(size_t)q * s * r + (size_t)j * s + row0 + i];
+          } else {
+            v = zero<T>();
+            const T* g = a.G + (size_t)j * s + row0 + i;
+            for (int k = 0; k < K; ++k) v += th[k] * g[(size_t)k * s * r];
+          }
         } else {
           v = a.bJ[row0 + i];
         }
@@ -169,9 +213,11 @@ __global__ void __launch_bounds__(NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
       }
       __syncthreads();
       if (row0 == 0) {
+        tail_norm_warp0<T, double>(P + 1, tb - 1, &nrm2[0]);
+        __syncthreads();
         for (int k = 0; k < r; ++k)
-          householder_step<T, double, NT>(k, r + 1, P + k, ldt, P + k + 1, ldt, tb - k - 1, red,
-                                          (T*)nullptr, (double*)nullptr);
+          householder_step<T, double, NT, 4>(k, r + 1, P + k, ldt, P + k + 1, ldt, tb - k - 1, 1,
+                                             nrm2, (T*)nullptr, (double*)nullptr);
         __syncthreads();
         double part = 0.0;
         for (int i = r + tid; i < tb; i += NT) part += absq(P[i + (size_t)r * ldt]);
@@ -183,9 +229,11 @@ __global__ void __launch_bounds__(NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
           }
         }
       } else {
+        tail_norm_warp0<T, double>(P, tb, &nrm2[0]);
+        __syncthreads();
         for (int k = 0; k < r; ++k)
-          householder_step<T, double, NT>(k, r + 1, Rm + k, r, P, ldt, tb, red, (T*)nullptr,
-                                          (double*)nullptr);
+          householder_step<T, double, NT, 4>(k, r + 1, Rm + k, r, P, ldt, tb, 0, nrm2,
+                                             (T*)nullptr, (double*)nullptr);
         __syncthreads();
         double part = 0.0;
         for (int i = tid; i < tb; i += NT) part += absq(P[i + (size_t)r * ldt]);
@@ -252,11 +300,13 @@ size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block) {
 
 template <typename T>
 static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
-                                  void* qoi, uint32_t* flags, double* rho, cudaStream_t st) {
+                                  void* qoi, uint32_t* flags, double* rho, cudaStream_t st,
+                                  const void* Mg) {
   int t = 0;
   const size_t smem = ls_plain_smem_bytes(c, &t);
   if (smem == 0) return cudaErrorInvalidConfiguration;
   LsPlainArgs<T> a;
+  a.Mg = (const T*)Mg;
   a.G = (const T*)c->G;
   a.bJ = (const T*)c->bJ;
   a.wq = (const T*)c->wq;
@@ -288,23 +338,26 @@ static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_
 }
 
 cudaError_t launch_ls_plain(const sas_ctx* c, const double* params, int64_t m, void* yout,
-                            void* qoi, uint32_t* flags, double* rho, cudaStream_t st) {
+                            void* qoi, uint32_t* flags, double* rho, cudaStream_t st,
+                            const void* Mg) {
   if (m == 0) return cudaSuccess;
-  if (c->dtype == SAS_COMPLEX128) return launch_plain_t<zd>(c, params, m, yout, qoi, flags, rho, st);
-  return launch_plain_t<double>(c, params, m, yout, qoi, flags, rho, st);
+  if (c->dtype == SAS_COMPLEX128)
+    return launch_plain_t<zd>(c, params, m, yout, qoi, flags, rho, st, Mg);
+  return launch_plain_t<double>(c, params, m, yout, qoi, flags, rho, st, Mg);
 }
 
 // ------------------------------------------------------------------ mixed
 template <typename TH, typename TL>
 struct LsMixedArgs {
-  const TH* G;      // float64 blocks (residuals)
-  const TL* G32;    // float32 blocks (factorisation)
+  const TH* Mg;     // dense M per parameter (m x s x r, ld s), or null: assemble from G
+  const TH* G;      // float64 blocks
+  const TL* G32;    // float32 blocks (used when M64 is not kept)
   const TH* bJ;
   const TL* bJ32;
   const TH* wq;
   const double* params;
   int64_t m;
-  int s, r, K, dp, rule, ldt, rpad, max_refine;
+  int s, r, K, dp, rule, ldt, rpad, max_refine, keep64;
   double bJ_norm, tol;
   TH* yout;
   TH* qoi;
@@ -319,6 +372,15 @@ __device__ inline float tf32_round(float x) {
   return __uint_as_float(u);
 }
 
+// Mixed-precision solve of one parameter per CTA iteration.
+//  1. theta(p); M assembled once in float64 (kept in shared memory when it
+//     fits, keep64) and rounded to float32 for the factorisation;
+//  2. float32 Householder QR with the reflectors kept below the diagonal;
+//  3. y = R^{-1} [Q^H b_J]_{0:r};
+//  4. refinement: res = b_J - M y in float64, delta = R^{-1} [Q^H res]_{0:r} in
+//     float32, y += delta, until ||delta|| <= tol ||y|| or a step no longer
+//     halves the correction; the last residual evaluated belongs to the
+//     returned y, so rho is exact in float64.
 template <typename TH, typename TL, int NT>
 __global__ void __launch_bounds__(NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -331,8 +393,10 @@ __global__ void __launch_bounds__(NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL>
   TL* v0 = th32 + kMaxDp;                        // kMaxR
   TL* dl = v0 + kMaxR;                           // kMaxR (correction)
   float* tau = reinterpret_cast<float*>(dl + kMaxR);  // kMaxR
-  float* redf = tau + kMaxR;                     // NT/32
-  TL* P = reinterpret_cast<TL*>(redf + NT / 32 + 4);   // ldt x (r+1)
+  float* nrm2 = tau + kMaxR;                     // 2 (+2 padding)
+  TL* P = reinterpret_cast<TL*>(nrm2 + 4);       // ldt x (r+1)
+  TH* M64 = reinterpret_cast<TH*>(
+      (reinterpret_cast<uintptr_t>(P + (size_t)ldt * (r + 1)) + 15) & ~(uintptr_t)15);  // s x r
   __shared__ double ctl[2];  // refinement control: stop flag, last relative correction
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -342,21 +406,44 @@ __global__ void __launch_bounds__(NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL>
       th32[tid] = to_lo(th[tid]);
     }
     __syncthreads();
-    for (int idx = tid; idx < s * (r + 1); idx += NT) {
-      const int i = idx % s, j = idx / s;
-      TL v;
-      if (j < r) {
-        v = zero<TL>();
-        const TL* g = a.G32 + (size_t)j * s + i;
-        for (int k = 0; k < K; ++k) v += th32[k] * g[(size_t)k * s * r];
-      } else {
-        v = a.bJ32[i];
+    if (a.keep64) {
+      for (int idx = tid; idx < s * r; idx += NT) {
+        const int i = idx % s, j = idx / s;
+        TH v = zero<TH>();
+        if (a.Mg) {
+          v = a.Mg[(size_t)q * s * r + idx];
+        } else {
+          const TH* g = a.G + idx;
+          for (int k = 0; k < K; ++k) v += th[k] * g[(size_t)k * s * r];
+        }
+        M64[idx] = v;
+        P[i + (size_t)j * ldt] = to_lo(v);
       }
-      P[i + (size_t)j * ldt] = v;
+      for (int i = tid; i < s; i += NT) P[i + (size_t)r * ldt] = a.bJ32[i];
+    } else {
+      for (int idx = tid; idx < s * (r + 1); idx += NT) {
+        const int i = idx % s, j = idx / s;
+        TL v;
+        if (j < r) {
+          if (a.Mg) {
+            v = to_lo(a.Mg[(size_t)q * s * r + idx]);
+          } else {
+            v = zero<TL>();
+            const TL* g = a.G32 + (size_t)j * s + i;
+            for (int k = 0; k < K; ++k) v += th32[k] * g[(size_t)k * s * r];
+          }
+        } else {
+          v = a.bJ32[i];
+        }
+        P[i + (size_t)j * ldt] = v;
+      }
     }
     __syncthreads();
+    tail_norm_warp0<TL, float>(P + 1, s - 1, &nrm2[0]);
+    __syncthreads();
     for (int k = 0; k < r; ++k)
-      householder_step<TL, float, NT>(k, r + 1, P + k, ldt, P + k + 1, ldt, s - k - 1, redf, v0, tau);
+      householder_step<TL, float, NT, 4>(k, r + 1, P + k, ldt, P + k + 1, ldt, s - k - 1, 1, nrm2,
+                                         v0, tau);
     __syncthreads();
     // y0 = R^{-1} z
     float dmin = 0.f, dmax = 0.f;
@@ -381,11 +468,16 @@ __global__ void __launch_bounds__(NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL>
       double part = 0.0;
       for (int i = tid; i < s; i += NT) {
         TH acc = zero<TH>();
-        for (int k = 0; k < K; ++k) {
-          const TH* g = a.G + (size_t)k * s * r + i;
-          TH mk = zero<TH>();
-          for (int j = 0; j < r; ++j) mk += g[(size_t)j * s] * y[j];
-          acc += th[k] * mk;
+        if (a.keep64 || a.Mg) {
+          const TH* mrow = a.keep64 ? M64 + i : a.Mg + (size_t)q * s * r + i;
+          for (int j = 0; j < r; ++j) acc += mrow[(size_t)j * s] * y[j];
+        } else {
+          for (int k = 0; k < K; ++k) {
+            const TH* g = a.G + (size_t)k * s * r + i;
+            TH mk = zero<TH>();
+            for (int j = 0; j < r; ++j) mk += g[(size_t)j * s] * y[j];
+            acc += th[k] * mk;
+          }
         }
         const TH ri = a.bJ[i] - acc;
         res[i] = ri;
@@ -480,23 +572,34 @@ __global__ void __launch_bounds__(NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL>
   }
 }
 
-size_t ls_mixed_smem_bytes(const sas_ctx* c) {
+static size_t mixed_base_bytes(const sas_ctx* c) {
   const bool cplx = c->dtype == SAS_COMPLEX128;
   const size_t eh = cplx ? 16 : 8, el = cplx ? 8 : 4;
   size_t b = (size_t)(kMaxDp + kMaxR + kMaxS) * eh + (kLsThreads / 32) * 8;
-  b += (size_t)(kMaxDp + 2 * kMaxR) * el + (size_t)kMaxR * 4 + (kLsThreads / 32 + 4) * 4;
-  b = (b + 15) / 16 * 16;
+  b += (size_t)(kMaxDp + 2 * kMaxR) * el + (size_t)kMaxR * 4 + 4 * 4;
   b += (size_t)c->s * (c->r + 1) * el;
-  return b + 16;
+  return (b + 15) / 16 * 16 + 16;
+}
+
+static bool mixed_keep64(const sas_ctx* c) {
+  const size_t eh = c->dtype == SAS_COMPLEX128 ? 16 : 8;
+  // keep M in float64 when it fits and leaves room for two CTAs per SM
+  return mixed_base_bytes(c) + (size_t)c->s * c->r * eh <= kSmemLimit / 2;
+}
+
+size_t ls_mixed_smem_bytes(const sas_ctx* c) {
+  const size_t eh = c->dtype == SAS_COMPLEX128 ? 16 : 8;
+  return mixed_base_bytes(c) + (mixed_keep64(c) ? (size_t)c->s * c->r * eh : 0);
 }
 
 template <typename TH, typename TL>
 static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
                                   void* qoi, float* ysplit, uint32_t* flags, double* rho,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const void* Mg) {
   const size_t smem = ls_mixed_smem_bytes(c);
   if (smem > kSmemLimit) return cudaErrorInvalidConfiguration;
   LsMixedArgs<TH, TL> a;
+  a.Mg = (const TH*)Mg;
   a.G = (const TH*)c->G;
   a.G32 = (const TL*)c->G32;
   a.bJ = (const TH*)c->bJ;
@@ -511,8 +614,9 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
   a.rule = c->theta_rule;
   a.ldt = c->s;
   a.rpad = (c->r + 31) / 32 * 32;
-  a.max_refine = 4;
-  a.tol = 1e-13;
+  a.max_refine = c->max_refine;
+  a.keep64 = mixed_keep64(c) ? 1 : 0;
+  a.tol = c->refine_tol;
   a.bJ_norm = c->bJ_norm;
   a.yout = (TH*)yout;
   a.qoi = (TH*)qoi;
@@ -534,11 +638,11 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
 
 cudaError_t launch_ls_mixed(const sas_ctx* c, const double* params, int64_t m, void* yout,
                             void* qoi, float* ysplit, uint32_t* flags, double* rho,
-                            cudaStream_t st) {
+                            cudaStream_t st, const void* Mg) {
   if (m == 0) return cudaSuccess;
   if (c->dtype == SAS_COMPLEX128)
-    return launch_mixed_t<zd, zf>(c, params, m, yout, qoi, nullptr, flags, rho, st);
-  return launch_mixed_t<double, float>(c, params, m, yout, qoi, ysplit, flags, rho, st);
+    return launch_mixed_t<zd, zf>(c, params, m, yout, qoi, nullptr, flags, rho, st, Mg);
+  return launch_mixed_t<double, float>(c, params, m, yout, qoi, ysplit, flags, rho, st, Mg);
 }
 
 // ------------------------------------------------- subsampled residual
@@ -547,7 +651,7 @@ __global__ void __launch_bounds__(NT) residual_affine_kernel(const T* G, const T
                                                              const double* params, int64_t m,
                                                              int s, int r, int K, int dp, int rule,
                                                              const T* Y, double bJ_norm,
-                                                             double* rho) {
+                                                             double* rho, const T* Mg) {
   __shared__ T th[kMaxDp];
   __shared__ T y[kMaxR];
   __shared__ double red[NT / 32];
@@ -559,11 +663,16 @@ __global__ void __launch_bounds__(NT) residual_affine_kernel(const T* G, const T
     double part = 0.0;
     for (int i = tid; i < s; i += NT) {
       T acc = zero<T>();
-      for (int k = 0; k < K; ++k) {
-        const T* g = G + (size_t)k * s * r + i;
-        T mk = zero<T>();
-        for (int j = 0; j < r; ++j) mk += g[(size_t)j * s] * y[j];
-        acc += th[k] * mk;
+      if (Mg) {
+        const T* mrow = Mg + (size_t)q * s * r + i;
+        for (int j = 0; j < r; ++j) acc += mrow[(size_t)j * s] * y[j];
+      } else {
+        for (int k = 0; k < K; ++k) {
+          const T* g = G + (size_t)k * s * r + i;
+          T mk = zero<T>();
+          for (int j = 0; j < r; ++j) mk += g[(size_t)j * s] * y[j];
+          acc += th[k] * mk;
+        }
       }
       part += absq(bJ[i] - acc);
     }
@@ -574,17 +683,17 @@ __global__ void __launch_bounds__(NT) residual_affine_kernel(const T* G, const T
 }
 
 cudaError_t launch_residual(const sas_ctx* c, const double* params, int64_t m, const void* Y,
-                            double* rho, cudaStream_t st) {
+                            double* rho, cudaStream_t st, const void* Mg) {
   if (m == 0) return cudaSuccess;
   int64_t grid = m < (int64_t)c->num_sms * 8 ? m : (int64_t)c->num_sms * 8;
   if (c->dtype == SAS_COMPLEX128)
     residual_affine_kernel<zd, 256><<<(unsigned)grid, 256, 0, st>>>(
         (const zd*)c->G, (const zd*)c->bJ, params, m, c->s, c->r, c->K, c->dp, c->theta_rule,
-        (const zd*)Y, c->bJ_norm, rho);
+        (const zd*)Y, c->bJ_norm, rho, (const zd*)Mg);
   else
     residual_affine_kernel<double, 256><<<(unsigned)grid, 256, 0, st>>>(
         (const double*)c->G, (const double*)c->bJ, params, m, c->s, c->r, c->K, c->dp,
-        c->theta_rule, (const double*)Y, c->bJ_norm, rho);
+        c->theta_rule, (const double*)Y, c->bJ_norm, rho, (const double*)Mg);
   return cudaGetLastError();
 }
 

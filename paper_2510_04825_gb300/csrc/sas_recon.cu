@@ -85,6 +85,9 @@ __global__ void __launch_bounds__(NT) reconstruct_mixed_simt_kernel(
 cudaError_t launch_reconstruct_mixed(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                      cudaStream_t st) {
   if (m == 0) return cudaSuccess;
+  if (c->recon_kernel != 1 && reconstruct_tc_supported(c))
+    return launch_reconstruct_tc(c, ysplit, m, out, st);
+  if (c->recon_kernel == 2) return cudaErrorNotSupported;
   constexpr int JB = 16, NT = 256;
   const int rpad = (c->r + 31) / 32 * 32;
   if ((m + JB - 1) / JB > 65535) return cudaErrorInvalidValue;

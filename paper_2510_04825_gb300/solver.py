@@ -90,3 +90,38 @@ def select_rows(prob, S_device, blocks_device, p_sel, s, device="cuda"):
     desc = api._affine_desc(prob.n, prob.r, s, blocks_device, S_device, None, None, rule,
                             api.SAS_MODE_PLAIN, api.SAS_QOI_NONE, None, cplx)
     return api.subapsnap_select_rows_affine(desc, p_sel, s)
+
+
+class KernelSolver:
+    """Context for A(sigma, lambda) = K_sigma + lambda I on points X (Gaussian kernel)."""
+
+    def __init__(self, prob, S, J, mode=api.SAS_MODE_PLAIN, device="cuda", S_device=None,
+                 X_device=None, b_device=None):
+        self.prob = prob
+        self.X = X_device if X_device is not None else \
+            torch.from_numpy(np.ascontiguousarray(prob.X, dtype=np.float64)).to(device)
+        self.S = S_device if S_device is not None else basis_to_device(S, device)
+        self.b = b_device if b_device is not None else \
+            torch.from_numpy(np.ascontiguousarray(prob.b, dtype=np.float64)).to(device)
+        self.J = np.asarray(J, dtype=np.int64)
+        self.desc = api._kernel_desc(prob.n, prob.X.shape[1], prob.r, len(self.J), self.X, self.S,
+                                     self.J, self.b, mode)
+        self.r, self.s, self.n, self.mode = prob.r, len(self.J), prob.n, mode
+        self.ctx = api.subapsnap_setup_kernel(self.desc)
+
+    def close(self):
+        if self.ctx is not None:
+            api.subapsnap_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, params, out_kind, out, flags=None, rho=None, stream=None):
+        api.subapsnap_solve_batch(self.ctx, params, params.shape[0], out_kind, out, flags, rho, stream)
+
+    def residual(self, params, Y, rho, stream=None):
+        api.subapsnap_residual(self.ctx, params, params.shape[0], Y, rho, stream)

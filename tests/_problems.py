@@ -26,3 +26,24 @@ class Case:
 
     def kappas(self, params):
         return np.array([online.condition_number(self.prob, self.S, self.J, p) for p in params])
+
+
+U32 = 2.0 ** -24
+
+
+def mixed_bound(prob, S, J, params, Yo, rho_o):
+    """Distance bound of the mixed solve to the float64 answer, per parameter.
+
+    The float32 factorisation with float64-residual refinement converges to
+    the least-squares solution of the perturbed matrix: ~kappa^2 u32 ||r*|| /
+    (||M|| ||y||) plus float64 rounding ~kappa u64; 16x that plus 1e-11.
+    """
+    bounds = []
+    bJ = prob.b[np.asarray(J)]
+    for prm, y, rr in zip(params, Yo, rho_o):
+        M = online.subsampled_matrix(prob, S, J, prm)
+        sv = np.linalg.svd(M, compute_uv=False)
+        kap = sv[0] / sv[-1]
+        rstar = rr * np.linalg.norm(bJ)
+        bounds.append(1e-11 + 16 * (kap ** 2 * U32 * rstar / (sv[0] * np.linalg.norm(y)) + kap * 1.1e-16))
+    return np.array(bounds)

@@ -26,7 +26,7 @@ if not torch.cuda.is_available():  # pragma: no cover - CPU runs deselect with -
 from paper_2510_04825_gb300 import api  # noqa: E402
 from paper_2510_04825_gb300.solver import AffineSolver, basis_to_device, csr_to_device, select_rows  # noqa: E402
 
-from _problems import Case  # noqa: E402
+from _problems import Case, mixed_bound as _mixed_bound  # noqa: E402
 
 U32 = 2.0 ** -24
 DEV = "cuda"
@@ -135,16 +135,7 @@ def test_c1_small_plain_xhat_and_qoi(c1_small):
 
 
 def mixed_bound(case, params, Yo, rho_o):
-    from oracle import online
-    bounds = []
-    for prm, y, rr in zip(params, Yo, rho_o):
-        M = online.subsampled_matrix(case.prob, case.S, case.J, prm)
-        sv = np.linalg.svd(M, compute_uv=False)
-        kap = sv[0] / sv[-1]
-        bJ = case.prob.b[case.J]
-        rstar = rr * np.linalg.norm(bJ)
-        bounds.append(1e-11 + 16 * (kap ** 2 * U32 * rstar / (sv[0] * np.linalg.norm(y)) + kap * 1.1e-16))
-    return np.array(bounds)
+    return _mixed_bound(case.prob, case.S, case.J, params, Yo, rho_o)
 
 
 @pytest.mark.parametrize("name", ["c0", "c1_small", "c3_small"])

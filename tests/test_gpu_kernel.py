@@ -1,0 +1,101 @@
+"""GPU parity of the Gaussian-kernel (kernel ridge regression) family.
+
+M(sigma, lambda) = K_sigma(X_J, X) S + lambda S_J is formed on the device
+from the points, for every parameter (Sec. 5.3), then solved as the affine
+family is.  Tolerances:
+  plain float64: y within 1e-10 relative of the oracle for every parameter
+    with kappa(M) 1.1e-16 <= 1e-11 (the float64 parity rule of the other tests).
+  mixed: the kernel entries are formed in float32 (hi/lo coordinate
+    differences, ex2.approx, per-chunk float32 sums added in float64), so M
+    carries a relative error eps_M ~ 64 u32; the solve is refined against
+    that M, so ||y - y_oracle|| / ||y|| <= 4 kappa(M) eps_M + the refinement
+    bound.  The subsampled residual of the plain path (float64 kernel rows) is
+    checked against the oracle as well.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import krr, selection, snapshots as osnap  # noqa: E402
+from paper_2510_04825_gb300 import api  # noqa: E402
+from paper_2510_04825_gb300.solver import KernelSolver  # noqa: E402
+from workloads import get_config  # noqa: E402
+from workloads import snapshots as wsnap  # noqa: E402
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def krr_case():
+    prob = get_config("kernel_ridge", N=2500, r=16, s=48, m=70)
+    S = wsnap.basis(prob)
+    V = krr.full_matrix(prob.X, prob.sel_param) @ S
+    J, gaps = selection.cpqr_rows(V, prob.s)
+    return prob, S, J
+
+
+def run(prob, S, J, mode, out_kind, params):
+    solver = KernelSolver(prob, S, J, mode=mode, device="cuda")
+    m = params.shape[0]
+    P = torch.from_numpy(np.ascontiguousarray(params)).cuda()
+    if out_kind == api.SAS_OUT_Y:
+        out = torch.empty((m, prob.r), dtype=torch.float64, device="cuda")
+    else:
+        out = torch.empty((m, prob.n), dtype=torch.float32 if mode else torch.float64, device="cuda")
+    flags = torch.zeros(m, dtype=torch.int32, device="cuda")
+    rho = torch.empty(m, dtype=torch.float64, device="cuda")
+    solver.solve(P, out_kind, out, flags, rho)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy(), flags.cpu().numpy(), rho.cpu().numpy(), solver
+    return res
+
+
+def test_kernel_rows_plain_parity(krr_case):
+    prob, S, J = krr_case
+    params = prob.test_params
+    Y, flags, rho, solver = run(prob, S, J, api.SAS_MODE_PLAIN, api.SAS_OUT_Y, params)
+    Yo, rho_o = krr.solve_many(prob, S, J, params)
+    err = np.linalg.norm(Y - Yo, axis=1) / np.linalg.norm(Yo, axis=1)
+    kap = np.array([np.linalg.cond(krr.subsampled_matrix(prob.X, S, J, p)) for p in params])
+    strict = kap * 1.1e-16 <= 1e-11
+    print(f"kernel plain: max rel err {err[strict].max():.2e}, kappa max {kap.max():.2e}, "
+          f"{(~strict).sum()} beyond the strict range")
+    assert strict.sum() > 0
+    assert err[strict].max() <= 1e-10
+    assert (np.abs(rho - rho_o) <= 1e-8 * rho_o + 64 * kap * 1.1e-16).all()
+    # standalone residual entry point on the oracle's y
+    rr = torch.empty(len(params), dtype=torch.float64, device="cuda")
+    solver.residual(torch.from_numpy(np.ascontiguousarray(params)).cuda(),
+                    torch.from_numpy(np.ascontiguousarray(Yo)).cuda(), rr)
+    torch.cuda.synchronize()
+    assert (np.abs(rr.cpu().numpy() - rho_o) <= 1e-8 * rho_o + 64 * kap * 1.1e-16).all()
+    solver.close()
+
+
+def test_kernel_rows_mixed_error(krr_case):
+    prob, S, J = krr_case
+    params = prob.test_params
+    Y, flags, rho, solver = run(prob, S, J, api.SAS_MODE_MIXED, api.SAS_OUT_Y, params)
+    Yo, rho_o = krr.solve_many(prob, S, J, params)
+    err = np.linalg.norm(Y - Yo, axis=1) / np.linalg.norm(Yo, axis=1)
+    kap = np.array([np.linalg.cond(krr.subsampled_matrix(prob.X, S, J, p)) for p in params])
+    bound = 4 * kap * 64 * U32 + 1e-10
+    print(f"kernel mixed: max rel err {err.max():.2e}, median {np.median(err):.2e}, "
+          f"max err/bound {(err / bound).max():.2e}")
+    assert (err <= bound).all()
+    solver.close()
+
+
+def test_kernel_rows_xhat(krr_case):
+    prob, S, J = krr_case
+    params = prob.test_params[:9]
+    X, _, _, solver = run(prob, S, J, api.SAS_MODE_PLAIN, api.SAS_OUT_XHAT, params)
+    Yo, _ = krr.solve_many(prob, S, J, params)
+    Xo = Yo @ S.T
+    assert (np.linalg.norm(X - Xo, axis=1) / np.linalg.norm(Xo, axis=1)).max() <= 1e-10
+    solver.close()

@@ -1,0 +1,51 @@
+"""Mixed-form reconstruction on the tensor cores (tcgen05) against the oracle.
+
+x_hat in float32 from tf32 splits of S and y: three products, relative
+error ~2^-21 per product, so <= 2e-6 relative per parameter is the bound.
+Shapes cover ragged row tiles (n not a multiple of 128), ragged parameter
+tiles (m not a multiple of 128), one and two K boxes (r <= 32, r <= 64).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2510_04825_gb300 import api  # noqa: E402
+from paper_2510_04825_gb300.solver import AffineSolver  # noqa: E402
+
+from _problems import Case  # noqa: E402
+
+
+def xhat(case, kernel, params):
+    solver = AffineSolver(case.prob, case.S, case.J, mode=api.SAS_MODE_MIXED, device="cuda")
+    api.subapsnap_set_option(solver.ctx, api.SAS_OPT_RECON_KERNEL, kernel)
+    m = params.shape[0]
+    P = torch.from_numpy(np.ascontiguousarray(params)).cuda()
+    out = torch.full((m, case.prob.n), float("nan"), dtype=torch.float32, device="cuda")
+    solver.solve(P, api.SAS_OUT_XHAT, out)
+    st = api.subapsnap_device_status(solver.ctx)
+    torch.cuda.synchronize()
+    solver.close()
+    assert st == 0
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("N,r,s,m", [(45, 60, 120, 300), (40, 20, 40, 130), (32, 64, 128, 128),
+                                     (48, 33, 70, 1)])
+def test_tensor_core_reconstruction(N, r, s, m):
+    case = Case("diffusion_2d", basis="random", N=N, r=r, s=s, m=m)
+    params = case.prob.test_params
+    Yo, _ = case.oracle_solve(params)
+    Xo = Yo @ case.S.T
+    Xtc = xhat(case, 2, params)
+    Xcc = xhat(case, 1, params)
+    assert np.isfinite(Xtc).all()
+    e_tc = np.linalg.norm(Xtc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
+    e_cc = np.linalg.norm(Xcc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
+    print(f"N={N} r={r} m={m}: tcgen05 max rel err {e_tc.max():.2e}, CUDA cores {e_cc.max():.2e}")
+    assert e_tc.max() <= 2e-6
+    assert e_cc.max() <= 2e-6
