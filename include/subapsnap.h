@@ -153,6 +153,17 @@ sas_status subapsnap_solve_batch(sas_ctx* ctx, const double* params, int64_t m,
                                  int32_t out_kind, void* out, uint32_t* flags,
                                  double* rho, void* stream);
 
+/* Reconstruction x_hat = S y of given coefficient vectors (Alg. 1 step 4,
+ * "output X c"), in the context's arithmetic: float64 DFMA in
+ * SAS_MODE_PLAIN; in SAS_MODE_MIXED float32 from tf32 splits of S and y on
+ * the tensor cores.  Lets a caller solve a large batch with SAS_OUT_Y once and
+ * reconstruct it in chunks.
+ *  Y:   device, m x r of the dtype of S (row j = y of parameter j).
+ *  out: device, m x n: double (plain) or float (mixed); row j = x_hat_j.
+ * Asynchronous.  Errors: SAS_EINVAL (NULL pointer), SAS_ENOTSUP (complex
+ * context), SAS_ECUDA. */
+sas_status subapsnap_reconstruct(sas_ctx* ctx, const void* Y, int64_t m, void* out, void* stream);
+
 /* Subsampled relative residual ||M(p) y - b_J|| / ||b_J|| of given
  * coefficient vectors (Sec. 4.3.1), in float64.
  *  params: device m x dp; Y: device m x r (dtype of S); rho: device m. */

@@ -31,7 +31,7 @@ EXPORTED = [
     "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
     "subapsnap_destroy", "subapsnap_last_error", "subapsnap_device_status", "subapsnap_version",
     "subapsnap_set_tracing", "subapsnap_trace_read", "subapsnap_solve_batch_xhat_noalloc",
-    "subapsnap_set_option",
+    "subapsnap_set_option", "subapsnap_reconstruct",
 ]
 SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL = 0, 1, 2
 SAS_NOALLOC_MAX_Y = 65536
@@ -92,13 +92,15 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_device_status.argtypes = [vp, vp]
         L.subapsnap_set_tracing.argtypes = [vp, i32]
         L.subapsnap_set_option.argtypes = [vp, i32, ctypes.c_double]
+        L.subapsnap_reconstruct.argtypes = [vp, vp, i64, vp, vp]
         L.subapsnap_solve_batch_xhat_noalloc.argtypes = [vp, vp, i64, vp, vp, vp, vp]
         L.subapsnap_trace_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
         for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
-                     "subapsnap_solve_batch_xhat_noalloc", "subapsnap_set_option"):
+                     "subapsnap_solve_batch_xhat_noalloc", "subapsnap_set_option",
+                     "subapsnap_reconstruct"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -197,6 +199,10 @@ def subapsnap_solve_batch_xhat_noalloc(ctx, params, m: int, out, flags=None, rho
                                        stream=None):
     _check(lib().subapsnap_solve_batch_xhat_noalloc(ctx, _ptr(params), int(m), _ptr(out),
                                                     _ptr(flags), _ptr(rho), _stream(stream)))
+
+
+def subapsnap_reconstruct(ctx, Y, m: int, out, stream=None):
+    _check(lib().subapsnap_reconstruct(ctx, _ptr(Y), int(m), _ptr(out), _stream(stream)))
 
 
 def subapsnap_residual(ctx, params, m: int, Y, rho, stream=None):

@@ -466,6 +466,31 @@ sas_status subapsnap_solve_batch(sas_ctx* c, const double* params, int64_t m, in
   return SAS_OK;
 }
 
+sas_status subapsnap_reconstruct(sas_ctx* c, const void* Y, int64_t m, void* out, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (m < 0) return fail(SAS_EINVAL, "m < 0");
+  if (m == 0) return SAS_OK;
+  if (!Y || !out) return fail(SAS_EINVAL, "Y and out must be non-NULL");
+  if (c->dtype != SAS_REAL64) return fail(SAS_ENOTSUP, "x_hat output is real-only");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (c->mode == SAS_MODE_MIXED) {
+    sas_status s2 = ensure_scratch(c, m, true, st);
+    if (s2 != SAS_OK) return s2;
+    const int rpad = (c->r + 31) / 32 * 32;
+    e = launch_split_y((const double*)Y, m, c->r, rpad, c->ysplit, st);
+    if (e == cudaSuccess) {
+      TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
+      e = launch_reconstruct_mixed(c, c->ysplit, m, (float*)out, st);
+    }
+  } else {
+    TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
+    e = launch_reconstruct_f64(c, Y, m, out, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "reconstruct");
+  return SAS_OK;
+}
+
 sas_status subapsnap_residual(sas_ctx* c, const double* params, int64_t m, const void* Y,
                               double* rho, void* stream) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");

@@ -109,6 +109,19 @@ template <> __device__ inline zd shfl_idx<zd>(zd v, int l) {
 template <> __device__ inline zf shfl_idx<zf>(zf v, int l) {
   return mkzf(__shfl_sync(0xffffffffu, v.re, l), __shfl_sync(0xffffffffu, v.im, l));
 }
+template <typename T> __device__ inline T shfl_xor_m(unsigned mask, T v, int o);
+template <> __device__ inline double shfl_xor_m<double>(unsigned mask, double v, int o) {
+  return __shfl_xor_sync(mask, v, o);
+}
+template <> __device__ inline float shfl_xor_m<float>(unsigned mask, float v, int o) {
+  return __shfl_xor_sync(mask, v, o);
+}
+template <> __device__ inline zd shfl_xor_m<zd>(unsigned mask, zd v, int o) {
+  return mkz(__shfl_xor_sync(mask, v.re, o), __shfl_xor_sync(mask, v.im, o));
+}
+template <> __device__ inline zf shfl_xor_m<zf>(unsigned mask, zf v, int o) {
+  return mkzf(__shfl_xor_sync(mask, v.re, o), __shfl_xor_sync(mask, v.im, o));
+}
 template <typename T> __device__ inline T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += shfl_down(v, o);
@@ -217,6 +230,8 @@ cudaError_t launch_reconstruct_mixed(const sas_ctx* c, const float* ysplit, int6
 cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                   cudaStream_t st);
 bool reconstruct_tc_supported(const sas_ctx* c);
+cudaError_t launch_split_y(const double* Y, int64_t m, int r, int rpad, float* ysplit,
+                           cudaStream_t st);
 cudaError_t launch_residual(const sas_ctx* c, const double* params, int64_t m, const void* Y,
                             double* rho, cudaStream_t st, const void* Mg = nullptr);
 cudaError_t launch_krr_assemble(const sas_ctx* c, const double* params, int64_t m, double* M,

@@ -50,16 +50,18 @@ __device__ inline double block_sum(double v, double* red) {
 // H = I - tau v v^H with v = x - beta e_1, beta = -phase(alpha) ||x||, so that
 // H x = beta e_1 and H = H^H; on return piv[k*ldp] holds beta (= R_kk).
 //
-// One barrier per step: nrm2[k & 1] must hold ||tail_k||^2 on entry (the
-// caller's pre-pass for k = 0); warp 0, which owns column k+1, writes
-// ||tail_{k+1}[next_off..len)||^2 to nrm2[(k+1) & 1] right after updating it.
-// Each warp updates its columns CB at a time so that the CB dot products and
-// warp reductions overlap.
-template <typename T, typename R, int NT, int CB>
+// Thread map: G consecutive lanes share a column; lane g of the group takes the
+// rows g, g + G, ... of the tail, and the G partial dot products are combined
+// with log2(G) shuffles inside the group.  The NT/G groups take columns
+// k+1+slot, k+1+slot+NT/G, ...  One barrier per step: nrm2[k & 1] must hold
+// ||tail_k||^2 on entry (the caller's pre-pass for k = 0); the group that owns
+// column k+1 writes ||tail_{k+1}[next_off..len)||^2 to nrm2[(k+1) & 1].
+template <typename T, typename R, int NT, int G>
 __device__ inline void householder_step(int k, int ncol, T* piv, int ldp, T* tail, int ldt, int len,
                                         int next_off, R* nrm2, T* v0_out, R* tau_out) {
-  constexpr int NW = NT / 32;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NSLOT = NT / G;
+  const int tid = threadIdx.x, g = tid % G, slot = tid / G;
+  const unsigned gmask = ((1u << G) - 1u) << ((tid & 31) & ~(G - 1));
   const T* tk = tail + (size_t)k * ldt;
   const R tail2 = nrm2[k & 1];
   const T alpha = piv[(size_t)k * ldp];
@@ -69,43 +71,22 @@ __device__ inline void householder_step(int k, int ncol, T* piv, int ldp, T* tai
   const T beta = rscale(-nrm, phase(alpha));
   const T v0 = alpha - beta;
   const R tau = nrm > R(0) ? R(1) / (nrm * (nrm + aa)) : R(0);
-  for (int jb = k + 1 + warp; jb < ncol; jb += NW * CB) {
-    T w[CB];
-    T* tj[CB];
-    bool on[CB];
+  for (int j = k + 1 + slot; j < ncol; j += NSLOT) {
+    T* tj = tail + (size_t)j * ldt;
+    T w = g == 0 ? conjv(v0) * piv[(size_t)j * ldp] : zero<T>();
+    for (int i = g; i < len; i += G) w += conjv(tk[i]) * tj[i];
 #pragma unroll
-    for (int c = 0; c < CB; ++c) {
-      const int j = jb + c * NW;
-      on[c] = j < ncol;
-      tj[c] = tail + (size_t)(on[c] ? j : k) * ldt;
-      w[c] = (lane == 0 && on[c]) ? conjv(v0) * piv[(size_t)j * ldp] : zero<T>();
-    }
-    for (int i = lane; i < len; i += 32) {
-      const T vi = conjv(tk[i]);
-#pragma unroll
-      for (int c = 0; c < CB; ++c)
-        if (on[c]) w[c] += vi * tj[c][i];
-    }
-    T tw[CB];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) tw[c] = rscale(tau, warp_sum(w[c]));
-    if (lane == 0) {
-#pragma unroll
-      for (int c = 0; c < CB; ++c)
-        if (on[c]) piv[(size_t)(jb + c * NW) * ldp] -= tw[c] * v0;
-    }
-    for (int i = lane; i < len; i += 32) {
-      const T vi = tk[i];
-#pragma unroll
-      for (int c = 0; c < CB; ++c)
-        if (on[c]) tj[c][i] -= tw[c] * vi;
-    }
-    if (jb == k + 1) {
-      __syncwarp();
+    for (int o = 1; o < G; o <<= 1) w += shfl_xor_m(gmask, w, o);
+    const T tw = rscale(tau, w);
+    if (g == 0) piv[(size_t)j * ldp] -= tw * v0;
+    for (int i = g; i < len; i += G) tj[i] -= tw * tk[i];
+    if (j == k + 1) {
+      __syncwarp(gmask);
       R part = R(0);
-      for (int i = next_off + lane; i < len; i += 32) part += absq(tj[0][i]);
-      part = warp_sum(part);
-      if (lane == 0) nrm2[(k + 1) & 1] = part;
+      for (int i = next_off + g; i < len; i += G) part += absq(tj[i]);
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) part += shfl_xor_m(gmask, part, o);
+      if (g == 0) nrm2[(k + 1) & 1] = part;
     }
   }
   __syncthreads();
@@ -115,6 +96,11 @@ __device__ inline void householder_step(int k, int ncol, T* piv, int ldp, T* tai
     if (tau_out) tau_out[k] = tau;
   }
 }
+
+// Leading dimension of a shared-memory panel with `rows` rows: >= rows and
+// congruent to 4 mod 32, so that the column groups of a warp (4 lanes each, 8
+// groups) fall into distinct banks.
+__host__ __device__ inline int panel_ld(int rows) { return (rows + 31) / 32 * 32 + 4; }
 
 // ||col[0..len)||^2 by warp 0 into *slot (the caller synchronises afterwards).
 template <typename T, typename R>
@@ -176,7 +162,7 @@ struct LsPlainArgs {
 };
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
+__global__ void __launch_bounds__(NT, 2) ls_plain_affine_kernel(LsPlainArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = a.s, r = a.r, t = a.t, ldt = a.ldt, K = a.K;
   const bool single = t >= s;
@@ -284,18 +270,19 @@ constexpr size_t kSmemLimit = 227 * 1024 - 1024;
 size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block) {
   const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
   const size_t extra = (size_t)(kMaxDp + kMaxR) * es + (kLsThreads / 32) * 8;
-  const size_t single = (size_t)c->s * (c->r + 1) * es + extra;
+  const size_t single = (size_t)panel_ld(c->s) * (c->r + 1) * es + extra;
   if (single <= kSmemLimit) {
     *rows_per_block = c->s;
     return single;
   }
   const size_t rbuf = (size_t)c->r * (c->r + 1) * es;
   if (rbuf + extra >= kSmemLimit) return 0;
-  int t = (int)((kSmemLimit - rbuf - extra) / ((c->r + 1) * es));
+  int t = (int)((kSmemLimit - rbuf - extra) / ((c->r + 1) * es)) - 36;
   if (t > c->s) t = c->s;
+  while (t >= c->r && (size_t)panel_ld(t) * (c->r + 1) * es + rbuf + extra > kSmemLimit) --t;
   if (t < c->r) return 0;
   *rows_per_block = t;
-  return (size_t)t * (c->r + 1) * es + rbuf + extra;
+  return (size_t)panel_ld(t) * (c->r + 1) * es + rbuf + extra;
 }
 
 template <typename T>
@@ -318,7 +305,7 @@ static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_
   a.dp = c->dp;
   a.rule = c->theta_rule;
   a.t = t;
-  a.ldt = t;
+  a.ldt = panel_ld(t);
   a.bJ_norm = c->bJ_norm;
   a.yout = (T*)yout;
   a.qoi = (T*)qoi;
@@ -382,7 +369,7 @@ __device__ inline float tf32_round(float x) {
 //     halves the correction; the last residual evaluated belongs to the
 //     returned y, so rho is exact in float64.
 template <typename TH, typename TL, int NT>
-__global__ void __launch_bounds__(NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL> a) {
+__global__ void __launch_bounds__(NT, 2) ls_mixed_affine_kernel(LsMixedArgs<TH, TL> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = a.s, r = a.r, ldt = a.ldt, K = a.K;
   TH* th = reinterpret_cast<TH*>(smem_raw);      // kMaxDp
@@ -577,7 +564,7 @@ static size_t mixed_base_bytes(const sas_ctx* c) {
   const size_t eh = cplx ? 16 : 8, el = cplx ? 8 : 4;
   size_t b = (size_t)(kMaxDp + kMaxR + kMaxS) * eh + (kLsThreads / 32) * 8;
   b += (size_t)(kMaxDp + 2 * kMaxR) * el + (size_t)kMaxR * 4 + 4 * 4;
-  b += (size_t)c->s * (c->r + 1) * el;
+  b += (size_t)panel_ld(c->s) * (c->r + 1) * el;
   return (b + 15) / 16 * 16 + 16;
 }
 
@@ -612,7 +599,7 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
   a.K = c->K;
   a.dp = c->dp;
   a.rule = c->theta_rule;
-  a.ldt = c->s;
+  a.ldt = panel_ld(c->s);
   a.rpad = (c->r + 31) / 32 * 32;
   a.max_refine = c->max_refine;
   a.keep64 = mixed_keep64(c) ? 1 : 0;

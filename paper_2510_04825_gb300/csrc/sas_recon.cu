@@ -97,4 +97,34 @@ cudaError_t launch_reconstruct_mixed(const sas_ctx* c, const float* ysplit, int6
   return cudaGetLastError();
 }
 
+// y (m x r float64) -> tf32 split [2][m][rpad]: the rounded part and the
+// float32 remainder, zero padded to rpad columns.
+__global__ void split_y_kernel(const double* Y, int64_t m, int r, int rpad, float* ys) {
+  const int64_t total = m * rpad;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = idx / rpad;
+    const int i = (int)(idx % rpad);
+    float hi = 0.f, lo = 0.f;
+    if (i < r) {
+      const float yf = (float)Y[q * r + i];
+      uint32_t u = __float_as_uint(yf);
+      u = (u + 0x1000u) & 0xffffe000u;
+      hi = __uint_as_float(u);
+      lo = yf - hi;
+    }
+    ys[idx] = hi;
+    ys[total + idx] = lo;
+  }
+}
+
+cudaError_t launch_split_y(const double* Y, int64_t m, int r, int rpad, float* ysplit,
+                           cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  const int64_t total = m * rpad;
+  const unsigned grid = (unsigned)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  split_y_kernel<<<grid, 256, 0, st>>>(Y, m, r, rpad, ysplit);
+  return cudaGetLastError();
+}
+
 }  // namespace sas

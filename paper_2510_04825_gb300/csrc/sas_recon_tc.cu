@@ -27,6 +27,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
+
 #include "sas_internal.cuh"
 
 namespace sas {
@@ -108,6 +110,22 @@ __device__ inline void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, 
       : "memory");
 }
 
+__device__ inline void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(x), "r"(y), "r"(src)
+      : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ inline void bulk_wait_read1() {
+  asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+}
+__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ inline void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 B, 8-row groups 1024 B apart.
 __device__ inline uint64_t smem_desc(uint32_t addr) {
@@ -169,14 +187,18 @@ struct Params {
   int kboxes;      // rpad / 32 (1 or 2)
   int num_mtiles;
   int num_ntiles;
+  int tma_store;   // 1: epilogue through shared memory and TMA stores
   int* status;
 };
+
+constexpr int kStageFloats = 32 * 32;  // one epilogue staging tile: 32 parameters x 32 rows
 
 __global__ void __launch_bounds__(kThreads, 1)
     reconstruct_tc_kernel(const __grid_constant__ CUtensorMap tmAhi,
                           const __grid_constant__ CUtensorMap tmAlo,
                           const __grid_constant__ CUtensorMap tmBhi,
-                          const __grid_constant__ CUtensorMap tmBlo, Params p) {
+                          const __grid_constant__ CUtensorMap tmBlo,
+                          const __grid_constant__ CUtensorMap tmOut, Params p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
@@ -185,7 +207,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* Bhi = base;
   uint8_t* Blo = Bhi + opbytes;
   uint8_t* Abase = Blo + opbytes;  // stage s: hi at Abase + s*2*opbytes, lo right after
-  uint64_t* bars = reinterpret_cast<uint64_t*>(Abase + (size_t)kStages * 2 * opbytes);
+  float* stage = reinterpret_cast<float*>(Abase + (size_t)kStages * 2 * opbytes);  // 4 warps x 2
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 8 * kStageFloats);
   // bars: full[2], empty[2], tfull[2], tempty[2], bbar
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -300,7 +323,22 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int cb = 0; cb < kBN / 32; ++cb) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + cb * 32), v);
-        if (i < p.n) {
+        if (p.tma_store) {
+          // stage [32 parameters][32 rows] and hand it to the TMA engine
+          const int buf = (it * (kBN / 32) + cb) & 1;
+          float* sb = stage + (q * 2 + buf) * kStageFloats;
+          if (lane == 0) bulk_wait_read1();
+          __syncwarp();
+#pragma unroll
+          for (int c = 0; c < 32; ++c) sb[c * 32 + lane] = v[c];
+          fence_async_smem();
+          __syncwarp();
+          const int64_t xs = (int64_t)mt * kBM + q * 32, ys = j0 + cb * 32;
+          if (lane == 0 && xs < p.n && ys < p.m) {  // boxes wholly past the end are skipped
+            tma_store_2d(&tmOut, smem_u32(sb), (int)xs, (int)ys);
+            bulk_commit();
+          }
+        } else if (i < p.n) {
 #pragma unroll
           for (int c = 0; c < 32; ++c) {
             const int64_t j = j0 + cb * 32 + c;
@@ -312,6 +350,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
     }
+    if (p.tma_store && lane == 0) bulk_wait_all();
   }
   fence_before();
   __syncthreads();
@@ -350,11 +389,26 @@ static bool make_map(CUtensorMap* map, const float* base, int64_t rows, int rpad
   return r == CUDA_SUCCESS;
 }
 
+// Output m x n float32 (row j = x_hat_j), box 32 rows (i) x 32 parameters (j), no swizzle.
+static bool make_out_map(CUtensorMap* map, float* base, int64_t n, int64_t m) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)m};
+  cuuint64_t strides[1] = {(cuuint64_t)n * sizeof(float)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 }  // namespace tc
 
 size_t reconstruct_tc_smem_bytes(int rpad) {
   const size_t op = (size_t)(rpad / 32) * tc::kBoxBytes;
-  return 1024 + 2 * op + (size_t)tc::kStages * 2 * op + 9 * sizeof(uint64_t);
+  return 1024 + 2 * op + (size_t)tc::kStages * 2 * op + 8 * tc::kStageFloats * sizeof(float) +
+         9 * sizeof(uint64_t);
 }
 
 bool reconstruct_tc_supported(const sas_ctx* c) {
@@ -382,7 +436,13 @@ cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t
         !tc::make_map(&mBhi, ysplit + j0 * rpad, mm, rpad) ||
         !tc::make_map(&mBlo, ysplit + (size_t)m * rpad + j0 * rpad, mm, rpad))
       return cudaErrorInvalidValue;
+    // TMA stores need 16-byte aligned rows: n a multiple of 4 and an aligned base
+    CUtensorMap mOut;
+    const bool tma_store = (c->n % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
+                           tc::make_out_map(&mOut, out + j0 * c->n, c->n, mm);
+    if (!tma_store) std::memset(&mOut, 0, sizeof(mOut));
     tc::Params p;
+    p.tma_store = tma_store ? 1 : 0;
     p.out = out + j0 * c->n;
     p.n = c->n;
     p.m = mm;
@@ -394,7 +454,7 @@ cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t
     if (grid < nts) grid = nts;
     const int max_grid = p.num_mtiles * nts;
     if (grid > max_grid) grid = max_grid;
-    tc::reconstruct_tc_kernel<<<grid, tc::kThreads, smem, st>>>(mAhi, mAlo, mBhi, mBlo, p);
+    tc::reconstruct_tc_kernel<<<grid, tc::kThreads, smem, st>>>(mAhi, mAlo, mBhi, mBlo, mOut, p);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

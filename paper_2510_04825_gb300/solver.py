@@ -79,6 +79,9 @@ class AffineSolver:
     def residual(self, params, Y, rho, stream=None):
         api.subapsnap_residual(self.ctx, params, params.shape[0], Y, rho, stream)
 
+    def reconstruct(self, Y, out, stream=None):
+        api.subapsnap_reconstruct(self.ctx, Y, Y.shape[0], out, stream)
+
     def true_residual(self, params, X, rho, stream=None):
         api.subapsnap_true_residual(self.ctx, params, params.shape[0], X, rho, stream)
 

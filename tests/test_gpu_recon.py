@@ -49,3 +49,26 @@ def test_tensor_core_reconstruction(N, r, s, m):
     print(f"N={N} r={r} m={m}: tcgen05 max rel err {e_tc.max():.2e}, CUDA cores {e_cc.max():.2e}")
     assert e_tc.max() <= 2e-6
     assert e_cc.max() <= 2e-6
+
+
+@pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED])
+def test_reconstruct_entry_point_matches_solve(mode):
+    """subapsnap_reconstruct(Y) gives the x_hat that solve_batch(SAS_OUT_XHAT) gives."""
+    case = Case("diffusion_2d", basis="random", N=36, r=60, s=120, m=300)
+    p = case.prob
+    solver = AffineSolver(p, case.S, case.J, mode=mode, device="cuda")
+    P = torch.from_numpy(np.ascontiguousarray(p.test_params)).cuda()
+    m = P.shape[0]
+    odt = torch.float64 if mode == api.SAS_MODE_PLAIN else torch.float32
+    X1 = torch.empty((m, p.n), dtype=odt, device="cuda")
+    solver.solve(P, api.SAS_OUT_XHAT, X1)
+    Y = torch.empty((m, p.r), dtype=torch.float64, device="cuda")
+    solver.solve(P, api.SAS_OUT_Y, Y)
+    X2 = torch.empty((m, p.n), dtype=odt, device="cuda")
+    for c0 in range(0, m, 128):  # chunked, with a ragged last chunk
+        solver.reconstruct(Y[c0:c0 + 128], X2[c0:c0 + 128])
+    torch.cuda.synchronize()
+    a, b = X2.double().cpu().numpy(), X1.double().cpu().numpy()
+    err = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+    assert err.max() <= (1e-12 if mode == api.SAS_MODE_PLAIN else 2e-6)
+    solver.close()
