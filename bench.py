@@ -313,6 +313,197 @@ def run_gpu(args):
         pg.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------
+# Other workloads (measured with the same contract; the driver's default run is
+# the 2-D diffusion workload above)
+# ---------------------------------------------------------------------------
+
+FP64_PEAK = 152 * 2 * 2 * 2.070e9   # 2 DFMA / clk / SM at the 2070 MHz maximum: 1.259 TFLOP/s
+FP32_PEAK = 152 * 128 * 2 * 2.070e9  # 128 FFMA / clk / SM: 80.5 TFLOP/s
+
+
+def householder_flops(s, r, complex_valued):
+    """Algorithmic flops of one Householder least-squares solve (QR, Q^H b, back substitution)."""
+    f = 2.0 * s * r * r - 2.0 * r ** 3 / 3.0 + 4.0 * s * r + r * r
+    return 4.0 * f if complex_valued else f
+
+
+def build_other(args, device, rank):
+    """(problem, chosen solver, plain solver, params (host, device), step spec)."""
+    import torch
+    from paper_2510_04825_gb300 import api
+    from paper_2510_04825_gb300.solver import AffineSolver, KernelSolver, csr_to_device, select_rows
+    from workloads import get_config
+    from workloads import snapshots as wsnap
+
+    wl = args.workload
+    info = {}
+    if wl == "transfer_function":
+        prob = get_config("transfer_function")
+        blocks = [csr_to_device(A, device) for A in prob.blocks]
+        S_rows, res = wsnap.transfer_basis_torch(prob, device=device)
+        info["snapshot_cocg_max_rel_residual"] = float(np.max(res))
+        J, gaps = select_rows(prob, S_rows, blocks, prob.sel_param, prob.s, device=device)
+        mk = lambda mode: AffineSolver(prob, None, J, mode=mode, device=device, S_device=S_rows,
+                                       blocks_device=blocks)
+        out_kind, out_shape, out_dtype = api.SAS_OUT_QOI, (prob.test_params.shape[0],), torch.complex128
+    elif wl == "reaction_diffusion_1d":
+        prob = get_config("reaction_diffusion_1d")
+        blocks = [csr_to_device(A, device) for A in prob.blocks]
+        S = wsnap.basis(prob)
+        from paper_2510_04825_gb300.solver import basis_to_device
+        S_rows = basis_to_device(S, device)
+        J, gaps = select_rows(prob, S_rows, blocks, prob.sel_param, prob.s, device=device)
+        mk = lambda mode: AffineSolver(prob, None, J, mode=mode, device=device, S_device=S_rows,
+                                       blocks_device=blocks)
+        out_kind, out_shape, out_dtype = api.SAS_OUT_XHAT, (prob.test_params.shape[0], prob.n), None
+    elif wl == "kernel_ridge":
+        prob = get_config("kernel_ridge")
+        X = torch.from_numpy(np.ascontiguousarray(prob.X)).to(device)
+        S_rows, res = wsnap.kernel_ridge_basis_torch(prob, X, device=device)
+        info["snapshot_cg_max_rel_residual"] = float(np.max(res))
+        from paper_2510_04825_gb300.solver import select_rows_kernel
+        J, gaps = select_rows_kernel(prob, X, S_rows, prob.sel_param, prob.s)
+        mk = lambda mode: KernelSolver(prob, None, J, mode=mode, device=device, S_device=S_rows,
+                                       X_device=X)
+        out_kind, out_shape, out_dtype = api.SAS_OUT_Y, (prob.test_params.shape[0], prob.r), torch.float64
+    else:
+        raise SystemExit(f"unknown workload {wl}")
+    params = prob.test_params
+    if rank > 0:
+        params = np.random.default_rng(1000 + rank).permutation(params)
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(device)
+    return prob, mk, P, params, out_kind, out_shape, out_dtype, info
+
+
+def run_gpu_other(args):
+    import torch
+    from paper_2510_04825_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    t0 = time.time()
+    prob, mk, P, params_host, out_kind, out_shape, out_dtype, info = build_other(args, device, rank)
+    chosen, plain = mk(api.SAS_MODE_MIXED), mk(api.SAS_MODE_PLAIN)
+    m = P.shape[0]
+    stream = torch.cuda.current_stream()
+    setup_s = time.time() - t0
+
+    def outbuf(mode):
+        dt = out_dtype or (torch.float32 if mode == api.SAS_MODE_MIXED else torch.float64)
+        return torch.empty(out_shape, dtype=dt, device=device)
+
+    out_c, out_p = outbuf(api.SAS_MODE_MIXED), outbuf(api.SAS_MODE_PLAIN)
+    rho_c = torch.empty(m, dtype=torch.float64, device=device)
+    rho_p = torch.empty(m, dtype=torch.float64, device=device)
+    flags = torch.empty(m, dtype=torch.int32, device=device)
+
+    def timed(fn, steps, warmup, sample_clocks=False, sub=None):
+        clk = None
+        if sample_clocks and rank == 0:
+            cpath = os.path.join(tempfile.gettempdir(), f"sas_clocks_{os.getpid()}.csv")
+            sp, sf = start_clock_sampler(cpath)
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if sample_clocks and rank == 0:
+            clk = stop_clock_sampler(sp, sf, cpath, local)
+        ms = e0.elapsed_time(e1) / steps
+        if pg:
+            t = torch.tensor([ms], device=device)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, clk
+
+    # chosen form, whole batch per step
+    api.subapsnap_set_tracing(chosen.ctx, True)
+    ms_c, clocks = timed(lambda: chosen.solve(P, out_kind, out_c, flags, rho_c), args.steps,
+                         args.warmup, sample_clocks=True)
+    for k in range(4):
+        api.subapsnap_trace_read(chosen.ctx, k)
+    timed(lambda: chosen.solve(P, out_kind, out_c, flags, rho_c), 1, 0)
+    traces = {k: api.subapsnap_trace_read(chosen.ctx, k) for k in range(4)}
+    api.subapsnap_set_tracing(chosen.ctx, False)
+    # plain float64 form: the kernel-ridge float64 rows take ~10 ms per parameter, so
+    # that form is timed on a sub-batch and reported per parameter
+    msub = m if args.workload != "kernel_ridge" else min(m, 128)
+    Psub = P[:msub]
+    out_ps = out_p[:msub] if out_p.dim() > 0 else out_p
+    ms_p, _ = timed(lambda: plain.solve(Psub, out_kind, out_ps, None, rho_p[:msub]), 1, 1)
+    plain_value = world * msub / (ms_p * 1e-3)
+    value = world * m / (ms_c * 1e-3)
+    # accuracy of the chosen form against the plain float64 form on the sub-batch
+    torch.cuda.synchronize()
+    Yc = torch.empty((msub, prob.r), dtype=torch.complex128 if prob.complex_valued else torch.float64,
+                     device=device)
+    Yp = torch.empty_like(Yc)
+    chosen.solve(Psub, api.SAS_OUT_Y, Yc, None, rho_c[:msub])
+    plain.solve(Psub, api.SAS_OUT_Y, Yp, None, rho_p[:msub])
+    torch.cuda.synchronize()
+    yerr = (torch.linalg.vector_norm(Yc - Yp, dim=1) / torch.linalg.vector_norm(Yp, dim=1)).cpu().numpy()
+    rc, rp = rho_c[:msub].cpu().numpy(), rho_p[:msub].cpu().numpy()
+    ls_ms, ls_n = traces[api.SAS_KERNEL_LS]
+    asm_ms, asm_n = traces[api.SAS_KERNEL_ASSEMBLE]
+    cplx = prob.complex_valued
+    if args.workload == "kernel_ridge":
+        # dominant kernel: float32 kernel rows (FP32 pipe): 2 s N r fma flops per parameter
+        fl = 2.0 * prob.s * prob.n * prob.r * m
+        roof = {"bound": "alu", "pipe": "fp32", "kernel": "krr_assemble_kernel<float>",
+                "achieved": round(fl / (asm_ms * 1e-3) / 1e12, 3), "peak": round(FP32_PEAK / 1e12, 1),
+                "unit": "TFLOP/s", "peak_source": "derived (128 FFMA/clk/SM x 152 SMs x 2070 MHz)"}
+    else:
+        fl = householder_flops(prob.s, prob.r, cplx) * m
+        roof = {"bound": "alu", "pipe": "fp32 (Householder) + fp64 (refinement)",
+                "kernel": "ls_mixed_affine_kernel",
+                "achieved": round(fl / (ls_ms * 1e-3) / 1e12, 3), "peak": round(FP32_PEAK / 1e12, 1),
+                "unit": "TFLOP/s", "peak_source": "derived (128 FFMA/clk/SM x 152 SMs x 2070 MHz)"}
+    roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
+    roof["traffic"] = None
+    ls_plain_fl = householder_flops(prob.s, prob.r, cplx) * msub
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_c, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 factorisation / f32 kernel rows + f64 refinement residual",
+        "data": "synthetic (seeded workload)",
+        "config": {"workload": args.workload, "n": prob.n, "r": prob.r, "s": prob.s, "m_per_gpu": m,
+                   "output": {api.SAS_OUT_Y: "y", api.SAS_OUT_XHAT: "x_hat", api.SAS_OUT_QOI: "QoI"}[out_kind],
+                   "parallelism": f"dp{world} (independent parameters)"},
+        "plain_fp64": {"value": round(plain_value, 2), "unit": "solves/s", "batch_timed": msub,
+                       "fp64_pipe_frac_ls": round(ls_plain_fl / (ms_p * 1e-3) / FP64_PEAK, 4)
+                       if args.workload != "kernel_ridge" else None},
+        "speedup_chosen_vs_plain": round(value / plain_value, 2),
+        "residual": {"sub_chosen_max": float(rc.max()), "sub_chosen_median": float(np.median(rc)),
+                     "sub_plain_max": float(rp.max()), "sub_plain_median": float(np.median(rp)),
+                     "y_relerr_chosen_vs_plain_max": float(yerr.max()),
+                     "y_relerr_chosen_vs_plain_median": float(np.median(yerr))},
+        "roofline": roof,
+        "kernel_ms": {"ls": round(ls_ms / max(ls_n, 1), 4),
+                      "assemble": round(asm_ms / max(asm_n, 1), 4) if asm_n else None},
+        "gpu_launches": args.steps * ((asm_n + ls_n) + (ls_n if out_kind == api.SAS_OUT_XHAT else 0)),
+        "clocks": clocks, "setup_s": round(setup_s, 1), **info,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
 def chosen_kernel_version():
     return TC_VERSION
 
@@ -396,9 +587,13 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 form")
     ap.add_argument("--quick", action="store_true", help="time the chosen form only (profiling runs)")
     ap.add_argument("--grid", type=int, default=GRID, help="interior grid side (profiling runs use 512)")
+    ap.add_argument("--workload", default="diffusion_2d",
+                    choices=["diffusion_2d", "transfer_function", "reaction_diffusion_1d", "kernel_ridge"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "diffusion_2d":
+        run_gpu_other(args)
     else:
         run_gpu(args)
 

@@ -248,6 +248,14 @@ sas_status subapsnap_set_tracing(sas_ctx* ctx, int32_t enable);
 sas_status subapsnap_trace_read(sas_ctx* ctx, int32_t kernel_class, double* total_ms,
                                 int64_t* launches);
 
+/* Row selection for the Gaussian-kernel family: the same CPQR rounds on
+ * V = (K_sigma + lambda I) S at p_sel = (sigma, lambda) (host, 2 doubles),
+ * with V formed from float64 kernel rows of all N points (O(N^2 r) work,
+ * done once).  desc: as for setup_kernel (J and b are ignored).  Synchronous.
+ * Errors: SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA, SAS_ERANK. */
+sas_status subapsnap_select_rows_kernel(const sas_kernel_desc* desc, const double* p_sel,
+                                        int64_t* J_out, double* gap_out);
+
 /* Release a context and everything it allocated.  NULL is a no-op. */
 void subapsnap_destroy(sas_ctx* ctx);
 

@@ -31,7 +31,7 @@ EXPORTED = [
     "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
     "subapsnap_destroy", "subapsnap_last_error", "subapsnap_device_status", "subapsnap_version",
     "subapsnap_set_tracing", "subapsnap_trace_read", "subapsnap_solve_batch_xhat_noalloc",
-    "subapsnap_set_option", "subapsnap_reconstruct",
+    "subapsnap_set_option", "subapsnap_reconstruct", "subapsnap_select_rows_kernel",
 ]
 SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL = 0, 1, 2
 SAS_NOALLOC_MAX_Y = 65536
@@ -93,6 +93,10 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_set_tracing.argtypes = [vp, i32]
         L.subapsnap_set_option.argtypes = [vp, i32, ctypes.c_double]
         L.subapsnap_reconstruct.argtypes = [vp, vp, i64, vp, vp]
+        L.subapsnap_select_rows_kernel.argtypes = [ctypes.POINTER(KernelDesc),
+                                                   ctypes.POINTER(ctypes.c_double),
+                                                   ctypes.POINTER(ctypes.c_int64),
+                                                   ctypes.POINTER(ctypes.c_double)]
         L.subapsnap_solve_batch_xhat_noalloc.argtypes = [vp, vp, i64, vp, vp, vp, vp]
         L.subapsnap_trace_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
@@ -100,7 +104,7 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
                      "subapsnap_solve_batch_xhat_noalloc", "subapsnap_set_option",
-                     "subapsnap_reconstruct"):
+                     "subapsnap_reconstruct", "subapsnap_select_rows_kernel"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -183,6 +187,17 @@ def subapsnap_select_rows_affine(desc: AffineDesc, p_sel, s: int):
     J = np.zeros(s, dtype=np.int64)
     gaps = np.zeros(s, dtype=np.float64)
     _check(lib().subapsnap_select_rows_affine(
+        ctypes.byref(desc), ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        J.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        gaps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return J, gaps
+
+
+def subapsnap_select_rows_kernel(desc: KernelDesc, p_sel, s: int):
+    ps = np.ascontiguousarray(np.asarray(p_sel, dtype=np.float64).reshape(2))
+    J = np.zeros(s, dtype=np.int64)
+    gaps = np.zeros(s, dtype=np.float64)
+    _check(lib().subapsnap_select_rows_kernel(
         ctypes.byref(desc), ps.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
         J.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
         gaps.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))

@@ -545,6 +545,18 @@ sas_status subapsnap_select_rows_affine(const sas_affine_desc* d, const double* 
   return select_rows_affine(d, p_sel, J_out, gap_out);
 }
 
+sas_status subapsnap_select_rows_kernel(const sas_kernel_desc* d, const double* p_sel,
+                                        int64_t* J_out, double* gap_out) {
+  if (!d || !p_sel || !J_out) return fail(SAS_EINVAL, "NULL argument");
+  if (d->n < 1 || d->d < 1 || d->d > 16 || d->r < 1 || d->r > kMaxR)
+    return fail(SAS_EINVAL, "bad sizes");
+  if (d->s < d->r || (int64_t)d->s > d->n) return fail(SAS_EINVAL, "need r <= s <= n");
+  if (d->ldS != d->n) return fail(SAS_EINVAL, "select_rows_kernel needs ldS = n");
+  if (!is_device_ptr(d->X) || !is_device_ptr(d->S)) return fail(SAS_EINVAL, "X and S must be device pointers");
+  if (!(p_sel[0] > 0.0)) return fail(SAS_EINVAL, "sigma must be positive");
+  return select_rows_kernel(d, p_sel, J_out, gap_out);
+}
+
 void subapsnap_destroy(sas_ctx* c) { free_ctx(c); }
 
 sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {

@@ -242,5 +242,7 @@ cudaError_t launch_true_residual(const sas_ctx* c, const double* params, int64_t
 // selection
 sas_status select_rows_affine(const sas_affine_desc* d, const double* p_sel, int64_t* J_out,
                               double* gap_out);
+sas_status select_rows_kernel(const sas_kernel_desc* d, const double* p_sel, int64_t* J_out,
+                              double* gap_out);
 
 }  // namespace sas

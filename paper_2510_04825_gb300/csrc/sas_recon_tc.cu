@@ -311,6 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ---------------- epilogue: warps 2..5, lane quarter q = warp % 4
     const int q = warp & 3;
+    int issued = 0;  // TMA stores issued by this warp: selects the staging buffer
     for (int it = 0; it < iters; ++it) {
       const int acc = it & 1;
       const uint32_t ph = (uint32_t)(it >> 1) & 1u;
@@ -324,19 +325,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + cb * 32), v);
         if (p.tma_store) {
-          // stage [32 parameters][32 rows] and hand it to the TMA engine
-          const int buf = (it * (kBN / 32) + cb) & 1;
-          float* sb = stage + (q * 2 + buf) * kStageFloats;
-          if (lane == 0) bulk_wait_read1();
-          __syncwarp();
-#pragma unroll
-          for (int c = 0; c < 32; ++c) sb[c * 32 + lane] = v[c];
-          fence_async_smem();
-          __syncwarp();
+          // stage [32 parameters][32 rows] and hand it to the TMA engine; a box
+          // wholly past the end is skipped and touches no staging buffer, so
+          // that "at most one store pending" always means the other buffer
           const int64_t xs = (int64_t)mt * kBM + q * 32, ys = j0 + cb * 32;
-          if (lane == 0 && xs < p.n && ys < p.m) {  // boxes wholly past the end are skipped
-            tma_store_2d(&tmOut, smem_u32(sb), (int)xs, (int)ys);
-            bulk_commit();
+          if (xs < p.n && ys < p.m) {
+            float* sb = stage + (q * 2 + (issued & 1)) * kStageFloats;
+            ++issued;
+            if (lane == 0) bulk_wait_read1();
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < 32; ++c) sb[c * 32 + lane] = v[c];
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(&tmOut, smem_u32(sb), (int)xs, (int)ys);
+              bulk_commit();
+            }
           }
         } else if (i < p.n) {
 #pragma unroll

@@ -10,6 +10,7 @@
 // the t rows already picked in the round.  Every round restarts from V with
 // all earlier picks removed.  The whole loop runs on the device; the host
 // only enqueues launches and reads J back once.
+#include <cstring>
 #include <vector>
 
 #include "sas_internal.cuh"
@@ -202,24 +203,15 @@ __global__ void fill_u8_kernel(uint8_t* a, int64_t count, uint8_t v) {
     a[i] = v;
 }
 
+// CPQR in rounds on V (device, n x r row-major); J_out / gap_out on the host.
 template <typename T>
-static sas_status select_t(const sas_affine_desc* d, const double* p_sel, int64_t* J_out,
-                           double* gap_out) {
+static sas_status cpqr_rounds(const T* V0, int64_t n, int r, int s, int64_t* J_out,
+                              double* gap_out) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t n = d->n;
-  const int r = d->r, s = d->s;
-  const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->K - 1;
-  SelTable h;
-  for (int k = 0; k < SAS_MAX_TERMS; ++k) {
-    h.rp[k] = d->rowptr[k];
-    h.ci[k] = d->colind[k];
-    h.va[k] = d->values[k];
-    h.p[k] = k < dp ? p_sel[k] : 0.0;
-  }
   const int nparts = sms * 4;
-  void *dtab = nullptr, *W = nullptr, *V0 = nullptr, *alive = nullptr, *partial = nullptr;
+  void *W = nullptr, *alive = nullptr, *partial = nullptr;
   void *refl = nullptr, *tau = nullptr, *Jd = nullptr, *gd = nullptr, *stat = nullptr;
   sas_status rc = SAS_OK;
   cudaError_t e = cudaSuccess;
@@ -229,9 +221,7 @@ static sas_status select_t(const sas_affine_desc* d, const double* p_sel, int64_
     e = (x);                        \
     if (e != cudaSuccess) goto done; \
   } while (0)
-  SAS_TRY(cudaMalloc(&dtab, sizeof(SelTable)));
   SAS_TRY(cudaMalloc(&W, vbytes));
-  SAS_TRY(cudaMalloc(&V0, vbytes));
   SAS_TRY(cudaMalloc(&alive, (size_t)n));
   SAS_TRY(cudaMalloc(&partial, sizeof(Top2) * nparts));
   SAS_TRY(cudaMalloc(&refl, sizeof(T) * r));
@@ -240,16 +230,12 @@ static sas_status select_t(const sas_affine_desc* d, const double* p_sel, int64_
   SAS_TRY(cudaMalloc(&gd, sizeof(double) * s));
   SAS_TRY(cudaMalloc(&stat, sizeof(int)));
   SAS_TRY(cudaMemset(stat, 0, sizeof(int)));
-  SAS_TRY(cudaMemcpy(dtab, &h, sizeof(SelTable), cudaMemcpyHostToDevice));
-  apply_operator_kernel<T><<<sms * 8, 256>>>((const SelTable*)dtab, d->K, d->theta_rule,
-                                             (const T*)d->S, d->ldS, n, r, (T*)V0);
-  SAS_TRY(cudaGetLastError());
   fill_u8_kernel<<<sms * 4, 256>>>((uint8_t*)alive, n, 1);
   SAS_TRY(cudaGetLastError());
   {
     int step = 0;
     while (step < s) {
-      copy_kernel<T><<<sms * 8, 256>>>((const T*)V0, (T*)W, (int64_t)n * r);
+      copy_kernel<T><<<sms * 8, 256>>>(V0, (T*)W, (int64_t)n * r);
       const int k = (s - step) < r ? (s - step) : r;
       for (int t = 0; t < k; ++t, ++step) {
         apply_and_norms_kernel<T><<<nparts, kSelThreads>>>((T*)W, n, r, t, (const uint8_t*)alive,
@@ -279,9 +265,7 @@ done:
     rc = e == cudaErrorMemoryAllocation ? SAS_ENOMEM : SAS_ECUDA;
     set_error(std::string("select_rows: ") + cudaGetErrorString(e));
   }
-  cudaFree(dtab);
   cudaFree(W);
-  cudaFree(V0);
   cudaFree(alive);
   cudaFree(partial);
   cudaFree(refl);
@@ -289,6 +273,93 @@ done:
   cudaFree(Jd);
   cudaFree(gd);
   cudaFree(stat);
+  return rc;
+}
+
+template <typename T>
+static sas_status select_t(const sas_affine_desc* d, const double* p_sel, int64_t* J_out,
+                           double* gap_out) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->K - 1;
+  SelTable h;
+  for (int k = 0; k < SAS_MAX_TERMS; ++k) {
+    h.rp[k] = d->rowptr[k];
+    h.ci[k] = d->colind[k];
+    h.va[k] = d->values[k];
+    h.p[k] = k < dp ? p_sel[k] : 0.0;
+  }
+  void *dtab = nullptr, *V0 = nullptr;
+  cudaError_t e = cudaMalloc(&dtab, sizeof(SelTable));
+  if (e == cudaSuccess) e = cudaMalloc(&V0, (size_t)d->n * d->r * sizeof(T));
+  if (e == cudaSuccess) e = cudaMemcpy(dtab, &h, sizeof(SelTable), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    apply_operator_kernel<T><<<sms * 8, 256>>>((const SelTable*)dtab, d->K, d->theta_rule,
+                                               (const T*)d->S, d->ldS, d->n, d->r, (T*)V0);
+    e = cudaGetLastError();
+  }
+  sas_status rc = SAS_OK;
+  if (e != cudaSuccess) {
+    rc = e == cudaErrorMemoryAllocation ? SAS_ENOMEM : SAS_ECUDA;
+    set_error(std::string("select_rows: ") + cudaGetErrorString(e));
+  } else {
+    rc = cpqr_rounds<T>((const T*)V0, d->n, d->r, d->s, J_out, gap_out);
+  }
+  cudaFree(dtab);
+  cudaFree(V0);
+  return rc;
+}
+
+// column-major n x r (ld n) -> row-major n x r
+__global__ void to_row_major_kernel(const double* A, int64_t n, int r, double* B) {
+  const int64_t total = n * r;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / r;
+    const int j = (int)(idx % r);
+    B[idx] = A[i + (int64_t)j * n];
+  }
+}
+
+sas_status select_rows_kernel(const sas_kernel_desc* d, const double* p_sel, int64_t* J_out,
+                              double* gap_out) {
+  // V = (K_sigma + lambda I) S at p_sel, from the float64 kernel rows of every point
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  sas_ctx tmp;
+  std::memset((void*)&tmp, 0, sizeof(tmp));
+  tmp.n = d->n;
+  tmp.r = d->r;
+  tmp.s = (int)d->n;
+  tmp.d = d->d;
+  tmp.X = d->X;
+  tmp.XJ = const_cast<double*>(d->X);
+  tmp.S = d->S;
+  tmp.SJ = const_cast<double*>(d->S);
+  tmp.ldS = d->ldS;
+  void *Vc = nullptr, *Vr = nullptr, *pd = nullptr;
+  cudaError_t e = cudaMalloc(&Vc, (size_t)d->n * d->r * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&Vr, (size_t)d->n * d->r * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&pd, 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemcpy(pd, p_sel, 2 * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && d->ldS != d->n) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) e = launch_krr_assemble(&tmp, (const double*)pd, 1, (double*)Vc, false, 0);
+  if (e == cudaSuccess) {
+    to_row_major_kernel<<<sms * 8, 256>>>((const double*)Vc, d->n, d->r, (double*)Vr);
+    e = cudaGetLastError();
+  }
+  sas_status rc = SAS_OK;
+  if (e != cudaSuccess) {
+    rc = e == cudaErrorMemoryAllocation ? SAS_ENOMEM : SAS_ECUDA;
+    set_error(std::string("select_rows_kernel: ") + cudaGetErrorString(e));
+  } else {
+    rc = cpqr_rounds<double>((const double*)Vr, d->n, d->r, d->s, J_out, gap_out);
+  }
+  cudaFree(Vc);
+  cudaFree(Vr);
+  cudaFree(pd);
   return rc;
 }
 

@@ -128,3 +128,12 @@ class KernelSolver:
 
     def residual(self, params, Y, rho, stream=None):
         api.subapsnap_residual(self.ctx, params, params.shape[0], Y, rho, stream)
+
+
+def select_rows_kernel(prob, X_device, S_device, p_sel, s):
+    """CPQR-in-rounds row selection for the Gaussian-kernel family; (J, gaps) on the host."""
+    J0 = np.arange(s, dtype=np.int64)
+    b = torch.zeros(1, dtype=torch.float64, device=X_device.device)
+    desc = api._kernel_desc(prob.n, prob.X.shape[1], prob.r, s, X_device, S_device, J0, b,
+                            api.SAS_MODE_PLAIN)
+    return api.subapsnap_select_rows_kernel(desc, p_sel, s)

@@ -7,7 +7,7 @@ from workloads import snapshots as wsnap
 
 
 class Case:
-    def __init__(self, name, basis="snapshots", seed_basis=0, **kw):
+    def __init__(self, name, basis="snapshots", seed_basis=0, rows="cpqr", **kw):
         self.prob = get_config(name, **kw)
         p = self.prob
         if basis == "snapshots":
@@ -18,8 +18,12 @@ class Case:
             if p.complex_valued:
                 Z = Z + 1j * rng.standard_normal((p.n, p.r))
             self.S = wsnap.orthonormalise(Z)
-        V = np.asarray(oproblem.full_matrix(p, p.sel_param) @ self.S)
-        self.J, self.gaps = selection.cpqr_rows(V, p.s)
+        if rows == "random":  # the online stage accepts any row set; saves the CPQR at large n
+            self.J = np.sort(np.random.default_rng(seed_basis + 1).choice(p.n, p.s, replace=False))
+            self.gaps = None
+        else:
+            V = np.asarray(oproblem.full_matrix(p, p.sel_param) @ self.S)
+            self.J, self.gaps = selection.cpqr_rows(V, p.s)
 
     def oracle_solve(self, params):
         return online.solve_many(self.prob, self.S, self.J, params)

@@ -72,3 +72,22 @@ def test_reconstruct_entry_point_matches_solve(mode):
     err = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
     assert err.max() <= (1e-12 if mode == api.SAS_MODE_PLAIN else 2e-6)
     solver.close()
+
+
+def test_tensor_core_reconstruction_large_n_many_batch_sizes():
+    """n = 262,144 rows (2048 row tiles) with batch sizes that leave the last
+    parameter tile full, partial or alone: the tcgen05 path against the CUDA-core
+    path (both float32 from the same splits) and against the oracle on samples."""
+    case = Case("diffusion_2d", basis="random", rows="random", N=512, r=60, s=120, m=300)
+    p = case.prob
+    for m in (1, 64, 100, 128, 256, 300):
+        params = p.test_params[:m]
+        Xtc = xhat(case, 2, params)
+        Xcc = xhat(case, 1, params)
+        d = np.linalg.norm(Xtc - Xcc, axis=1) / np.linalg.norm(Xcc, axis=1)
+        bad = np.nonzero(d > 2e-6)[0]
+        assert bad.size == 0, (m, bad[:8], d.max())
+        Yo, _ = case.oracle_solve(params[:3])
+        Xo = Yo @ case.S.T
+        e = np.linalg.norm(Xtc[:3] - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
+        assert e.max() <= 2e-6, (m, e)

@@ -298,3 +298,72 @@ def transfer_basis_torch(prob, device="cuda", **kw):
     X, res = transfer_cocg(prob, prob.snap_params[:, 0], device=device, **kw)
     Q = orthonormalise_torch(X.T)
     return Q.T.contiguous(), res
+
+
+# ---------------------------------------------------------------------------
+# Kernel ridge regression: approximate snapshots (K_sigma + lambda I) x = y by
+# a fixed number of CG iterations on the GPU (torch), the ten lambda values of
+# one sigma sharing every kernel product.
+# ---------------------------------------------------------------------------
+
+def kernel_ridge_cg(prob, X, sigma, lams, iters=40, block=8192):
+    """CG for (K_sigma + lambda_j I) x_j = y, all lambda_j at once.
+
+    The kernel product is formed block by block in float32, so the snapshots
+    are approximate, as Alg. 1 step 1 allows.  Returns (x (N, q) float64, relative residuals of the float32 operator).
+    """
+    import torch
+    N = X.shape[0]
+    Xf = X.float()
+    lam = torch.as_tensor(np.asarray(lams, dtype=np.float64), device=X.device)
+    q = lam.numel()
+    y = torch.as_tensor(np.asarray(prob.b, dtype=np.float64), device=X.device)
+    inv = 1.0 / (2.0 * sigma * sigma)
+
+    def kmat(V):
+        out = torch.empty_like(V)
+        Vf = V.float()
+        for a in range(0, N, block):
+            # squared distances from direct differences (symmetric, no cancellation)
+            D = torch.cdist(Xf[a:a + block], Xf, compute_mode="donot_use_mm_for_euclid_dist")
+            D.square_().mul_(-inv).exp_()
+            out[a:a + block] = (D @ Vf).double()
+        return out
+
+    x = torch.zeros((N, q), dtype=torch.float64, device=X.device)
+    r = y[:, None].expand(N, q).clone()
+    p = r.clone()
+    rr = (r * r).sum(0)
+    bn = torch.sqrt(rr.clone())
+    best = x.clone()
+    best_rr = rr.clone()
+    for _ in range(iters):
+        Ap = kmat(p) + lam[None, :] * p
+        alpha = rr / (p * Ap).sum(0)
+        x += alpha[None, :] * p
+        r -= alpha[None, :] * Ap
+        rr_new = (r * r).sum(0)
+        p = r + (rr_new / rr)[None, :] * p
+        rr = rr_new
+        better = rr < best_rr  # keep the iterate with the smallest residual per column
+        best[:, better] = x[:, better]
+        best_rr = torch.where(better, rr, best_rr)
+    return best, (torch.sqrt(best_rr) / bn).cpu().numpy()
+
+
+def kernel_ridge_basis_torch(prob, X, device="cuda", iters=40):
+    """Orthonormal basis of approximate kernel-ridge snapshots on the sqrt(r) x sqrt(r) grid.
+
+    Returns (S_rows (r, N), relative residuals); row k = column k of S.
+    """
+    import torch
+    sig = np.unique(prob.snap_params[:, 0])
+    cols, res = [], []
+    for sv in sig:
+        lams = prob.snap_params[prob.snap_params[:, 0] == sv, 1]
+        x, rr = kernel_ridge_cg(prob, X, float(sv), lams, iters=iters)
+        cols.append(x)
+        res.append(rr)
+    Xs = torch.cat(cols, dim=1)
+    Q = orthonormalise_torch(Xs)
+    return Q.T.contiguous(), np.concatenate(res)
