@@ -133,6 +133,11 @@ def run_gpu(args):
                           blocks_device=blocks)
     plain = AffineSolver(prob, None, J, mode=api.SAS_MODE_PLAIN, device=device, S_device=S_rows,
                          blocks_device=blocks)
+    # autotune the least-squares launch shape of both forms on this batch
+    tune = {}
+    for name, sv in (("chosen", chosen), ("plain", plain)):
+        v, times = api.subapsnap_autotune(sv.ctx, P, M, 2)
+        tune[name] = {"variant": v, "ms": [round(t, 4) for t in times if t >= 0]}
     n = prob.n
     nchunks = M // CHUNK
     out32 = torch.empty((CHUNK, n), dtype=torch.float32, device=device)
@@ -303,6 +308,7 @@ def run_gpu(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "setup_s": round(setup_s, 1),
+        "autotune": tune,
         "snapshot_pcg_max_rel_residual": float(np.max(snap_res)),
     }
     if rank == 0 and not args.no_cpu_baseline:

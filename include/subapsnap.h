@@ -53,7 +53,9 @@ typedef enum {
 enum {
   SAS_FLAG_ILLCOND = 1u,   /* min|R_ii| <= 1e-13 max|R_ii|: M(p) near rank deficient */
   SAS_FLAG_NONFINITE = 2u, /* a NaN or Inf reached y */
-  SAS_FLAG_REFINE_STALL = 4u /* mixed mode: refinement did not reach its tolerance */
+  SAS_FLAG_REFINE_STALL = 4u, /* mixed mode: refinement did not reach its tolerance */
+  SAS_FLAG_SURROGATE = 8u,     /* gated solve: the network's prediction was accepted */
+  SAS_FLAG_FALLBACK = 16u      /* gated solve: rejected, solved by least squares instead */
 };
 
 /* Element type of S, b and the outputs. */
@@ -222,19 +224,39 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
  *  SAS_OPT_MAX_REFINE: most refinement steps of the mixed solve (0..16,
  *      default 4).
  *  SAS_OPT_REFINE_TOL: refinement stops when ||delta|| <= tol ||y||
- *      (default 1e-13) or when a step no longer halves the correction. */
-enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2 };
+ *      (default 1e-13) or when a step no longer halves the correction.
+ *  SAS_OPT_LS_VARIANT: launch shape of the least-squares kernel of the
+ *      context's mode (the index subapsnap_autotune reports; 0 = default). */
+enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
+       SAS_OPT_LS_VARIANT = 3 };
 
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */
 sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
+
+/* Autotuner (not in the paper): times every launch shape of the context's
+ * least-squares kernel (threads per CTA, lanes per column group, whether M is
+ * kept in float64 shared memory) on the caller's parameters, `reps` timed
+ * launches each after one warm-up, keeps the fastest in the context and
+ * returns it.
+ *  params: device, m x dp (a representative batch; its size matters).
+ *  times_ms: host, room for 16 doubles or NULL: mean time per variant
+ *            (a variant that cannot run for this shape reports -1).
+ *  chosen: host or NULL: index of the kept variant.
+ * If the environment variable SAS_TUNE_CACHE names a file, the choice is
+ * appended there under a key of (family, mode, dtype, s, r, K, m) and later
+ * calls with the same key read it back instead of timing.  Synchronous on
+ * `stream`.  Errors: SAS_EINVAL, SAS_ECUDA. */
+sas_status subapsnap_autotune(sas_ctx* ctx, const double* params, int64_t m, int32_t reps,
+                              double* times_ms, int32_t* chosen, void* stream);
 
 /* Kernel classes reported by the tracer. */
 enum { SAS_KERNEL_LS = 0,           /* assembly + least squares (+ QoI epilogue) */
        SAS_KERNEL_RECONSTRUCT = 1,  /* x_hat = S y */
        SAS_KERNEL_RESIDUAL = 2,     /* subsampled / true residual */
        SAS_KERNEL_ASSEMBLE = 3,     /* Gaussian-kernel rows K_sigma(X_J, X) S */
-       SAS_KERNEL_CLASSES = 4 };
+       SAS_KERNEL_SURROGATE = 4,    /* network inference */
+       SAS_KERNEL_CLASSES = 5 };
 
 /* Tracing: when enabled (enable != 0) every kernel the context launches is
  * bracketed by a pair of CUDA events recorded on the launch stream.  Costs
@@ -255,6 +277,56 @@ sas_status subapsnap_trace_read(sas_ctx* ctx, int32_t kernel_class, double* tota
  * Errors: SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA, SAS_ERANK. */
 sas_status subapsnap_select_rows_kernel(const sas_kernel_desc* desc, const double* p_sel,
                                         int64_t* J_out, double* gap_out);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate (not in the paper).  A network p -> y(p) (d_in -> 256 ->
+ * 256 -> r, exact GELU, bfloat16 weights, float32 accumulation and master
+ * weights, Adam) attached to an affine context, trained by the library's own
+ * kernels on coefficient vectors the online stage produced.  Its predictions
+ * are accepted only when the subsampled relative residual
+ * ||M(p) y_hat - b_J|| / ||b_J|| (the online residual estimate of Sec. 4.3.1,
+ * evaluated in float64) is at most gate_tol; the others are solved exactly.
+ * ---------------------------------------------------------------------- */
+
+/* Train (creating the network with N(0, 1/fan_in) weights from `seed` on the
+ * first call).  P: device ntrain x dp; Y: device ntrain x r (float64).
+ * Inputs are scaled to [-1, 1] and outputs standardised per component from
+ * this training set.  Mini-batches of `batch` rows in a seeded shuffle, Adam
+ * with learning rate lr.  loss_out: host, `epochs` mean losses, or NULL.
+ * Synchronous.  Errors: SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA. */
+sas_status subapsnap_surrogate_train(sas_ctx* ctx, const double* P, const double* Y, int64_t ntrain,
+                                     int32_t epochs, int32_t batch, double lr, uint64_t seed,
+                                     double* loss_out, void* stream);
+
+/* Network predictions y_hat for m parameters (device m x dp -> device m x r). */
+sas_status subapsnap_surrogate_predict(sas_ctx* ctx, const double* params, int64_t m,
+                                       double* Yhat, void* stream);
+
+/* Gated solve: predict, accept the predictions whose float64 subsampled
+ * relative residual is <= gate_tol, solve the rest by the context's least
+ * squares.  out_kind SAS_OUT_Y or SAS_OUT_QOI; flags (device m or NULL) gets
+ * SAS_FLAG_SURROGATE or SAS_FLAG_FALLBACK (plus the solve's own flags); rho
+ * (device m or NULL) the final subsampled residuals; accepted (host or NULL)
+ * the number accepted.  Synchronises once (to size the fallback batch). */
+sas_status subapsnap_solve_batch_surrogate(sas_ctx* ctx, const double* params, int64_t m,
+                                           int32_t out_kind, void* out, uint32_t* flags,
+                                           double* rho, double gate_tol, int64_t* accepted,
+                                           void* stream);
+
+/* Read (get != 0) or write the network: theta (host float32, layout W1 b1 W2
+ * b2 W3 b3, W_l row-major out x in) and norm (host float64: input centre[dp],
+ * input half-width[dp], output mean[r], output sd[r]); either may be NULL.
+ * *nparam (host, may be NULL) receives the parameter count.  Writing creates
+ * the network if needed.  For checkpoints and gradient checks. */
+sas_status subapsnap_surrogate_weights(sas_ctx* ctx, int32_t get, float* theta, double* norm,
+                                       int64_t* nparam);
+
+/* One forward and backward pass on a normalised batch (device float64
+ * X: B x dp, Yn: B x r): loss (host) and gradients (host float32, theta
+ * layout).  The bfloat16 weights of the matrix products are those the
+ * network trains with.  For gradient checks. */
+sas_status subapsnap_surrogate_grad(sas_ctx* ctx, const double* X, const double* Yn, int64_t B,
+                                    double* loss, float* grads);
 
 /* Release a context and everything it allocated.  NULL is a no-op. */
 void subapsnap_destroy(sas_ctx* ctx);

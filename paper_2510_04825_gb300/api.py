@@ -32,8 +32,12 @@ EXPORTED = [
     "subapsnap_destroy", "subapsnap_last_error", "subapsnap_device_status", "subapsnap_version",
     "subapsnap_set_tracing", "subapsnap_trace_read", "subapsnap_solve_batch_xhat_noalloc",
     "subapsnap_set_option", "subapsnap_reconstruct", "subapsnap_select_rows_kernel",
+    "subapsnap_autotune", "subapsnap_surrogate_train", "subapsnap_surrogate_predict",
+    "subapsnap_solve_batch_surrogate", "subapsnap_surrogate_weights", "subapsnap_surrogate_grad",
 ]
-SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL = 0, 1, 2
+SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
+SAS_KERNEL_SURROGATE = 4
+SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL, SAS_OPT_LS_VARIANT = 0, 1, 2, 3
 SAS_NOALLOC_MAX_Y = 65536
 SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL, SAS_KERNEL_ASSEMBLE = 0, 1, 2, 3
 
@@ -93,6 +97,16 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_set_tracing.argtypes = [vp, i32]
         L.subapsnap_set_option.argtypes = [vp, i32, ctypes.c_double]
         L.subapsnap_reconstruct.argtypes = [vp, vp, i64, vp, vp]
+        dp_, fp_, i64p = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64)
+        L.subapsnap_surrogate_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_double,
+                                                ctypes.c_uint64, dp_, vp]
+        L.subapsnap_surrogate_predict.argtypes = [vp, vp, i64, vp, vp]
+        L.subapsnap_solve_batch_surrogate.argtypes = [vp, vp, i64, i32, vp, vp, vp, ctypes.c_double,
+                                                      i64p, vp]
+        L.subapsnap_surrogate_weights.argtypes = [vp, i32, fp_, dp_, i64p]
+        L.subapsnap_surrogate_grad.argtypes = [vp, vp, vp, i64, dp_, fp_]
+        L.subapsnap_autotune.argtypes = [vp, vp, i64, i32, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_int32), vp]
         L.subapsnap_select_rows_kernel.argtypes = [ctypes.POINTER(KernelDesc),
                                                    ctypes.POINTER(ctypes.c_double),
                                                    ctypes.POINTER(ctypes.c_int64),
@@ -104,7 +118,10 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
                      "subapsnap_solve_batch_xhat_noalloc", "subapsnap_set_option",
-                     "subapsnap_reconstruct", "subapsnap_select_rows_kernel"):
+                     "subapsnap_reconstruct", "subapsnap_select_rows_kernel",
+                     "subapsnap_autotune", "subapsnap_surrogate_train",
+                     "subapsnap_surrogate_predict", "subapsnap_solve_batch_surrogate",
+                     "subapsnap_surrogate_weights", "subapsnap_surrogate_grad"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -216,6 +233,15 @@ def subapsnap_solve_batch_xhat_noalloc(ctx, params, m: int, out, flags=None, rho
                                                     _ptr(flags), _ptr(rho), _stream(stream)))
 
 
+def subapsnap_autotune(ctx, params, m: int, reps: int = 3, stream=None):
+    """Time every least-squares launch shape; returns (chosen index, times in ms)."""
+    times = (ctypes.c_double * 16)()
+    chosen = ctypes.c_int32()
+    _check(lib().subapsnap_autotune(ctx, _ptr(params), int(m), int(reps), times,
+                                    ctypes.byref(chosen), _stream(stream)))
+    return chosen.value, [t for t in times]
+
+
 def subapsnap_reconstruct(ctx, Y, m: int, out, stream=None):
     _check(lib().subapsnap_reconstruct(ctx, _ptr(Y), int(m), _ptr(out), _stream(stream)))
 
@@ -247,6 +273,48 @@ def subapsnap_trace_read(ctx, kernel_class: int):
     cnt = ctypes.c_int64()
     _check(lib().subapsnap_trace_read(ctx, kernel_class, ctypes.byref(ms), ctypes.byref(cnt)))
     return ms.value, cnt.value
+
+
+def subapsnap_surrogate_train(ctx, P, Y, epochs: int, batch: int, lr: float, seed: int = 0,
+                              stream=None):
+    """Train the network on (P, Y) device tensors; returns the mean loss of every epoch."""
+    losses = np.zeros(max(epochs, 1), dtype=np.float64)
+    _check(lib().subapsnap_surrogate_train(ctx, _ptr(P), _ptr(Y), int(P.shape[0]), int(epochs),
+                                           int(batch), float(lr), int(seed),
+                                           losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           _stream(stream)))
+    return losses[:epochs]
+
+
+def subapsnap_surrogate_predict(ctx, params, m: int, Yhat, stream=None):
+    _check(lib().subapsnap_surrogate_predict(ctx, _ptr(params), int(m), _ptr(Yhat), _stream(stream)))
+
+
+def subapsnap_solve_batch_surrogate(ctx, params, m: int, out_kind: int, out, flags=None, rho=None,
+                                    gate_tol: float = 1e-6, stream=None) -> int:
+    acc = ctypes.c_int64()
+    _check(lib().subapsnap_solve_batch_surrogate(ctx, _ptr(params), int(m), int(out_kind), _ptr(out),
+                                                 _ptr(flags), _ptr(rho), float(gate_tol),
+                                                 ctypes.byref(acc), _stream(stream)))
+    return acc.value
+
+
+def subapsnap_surrogate_weights(ctx, get: bool, theta=None, norm=None) -> int:
+    """theta: numpy float32 (nparam), norm: numpy float64 (2 (dp + r)); returns nparam."""
+    n = ctypes.c_int64()
+    tp = theta.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if theta is not None else None
+    npp = norm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if norm is not None else None
+    _check(lib().subapsnap_surrogate_weights(ctx, 1 if get else 0, tp, npp, ctypes.byref(n)))
+    return n.value
+
+
+def subapsnap_surrogate_grad(ctx, X, Yn, nparam: int):
+    """One forward/backward on device (X, Yn); returns (loss, gradients float32)."""
+    loss = ctypes.c_double()
+    g = np.zeros(nparam, dtype=np.float32)
+    _check(lib().subapsnap_surrogate_grad(ctx, _ptr(X), _ptr(Yn), int(X.shape[0]), ctypes.byref(loss),
+                                          g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return loss.value, g
 
 
 def subapsnap_destroy(ctx):

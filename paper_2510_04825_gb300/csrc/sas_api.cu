@@ -1,7 +1,11 @@
 // C ABI of the SubApSnap online-stage library: argument checks, context
 // set-up and the dispatch of every entry point to its kernels.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <new>
 #include <string>
 #include <unordered_set>
@@ -92,6 +96,7 @@ static void free_ctx(sas_ctx* c) {
   cudaFree(c->ysplit);
   cudaFree(c->Mbuf);
   cudaFree(c->dev_status);
+  destroy_surrogate(c);
   if (c->trace) {
     for (auto& t : *c->trace) {
       cudaEventDestroy(t.a);
@@ -557,7 +562,162 @@ sas_status subapsnap_select_rows_kernel(const sas_kernel_desc* d, const double* 
   return select_rows_kernel(d, p_sel, J_out, gap_out);
 }
 
+sas_status subapsnap_surrogate_train(sas_ctx* c, const double* P, const double* Y, int64_t ntrain,
+                                     int32_t epochs, int32_t batch, double lr, uint64_t seed,
+                                     double* loss_out, void* stream) {
+  if (!c || !P || !Y) return fail(SAS_EINVAL, "NULL argument");
+  if (c->family != kAffine || c->dtype != SAS_REAL64)
+    return fail(SAS_ENOTSUP, "the surrogate needs a real affine context");
+  if (batch < 1 || ntrain < batch || epochs < 0 || !(lr > 0.0))
+    return fail(SAS_EINVAL, "need 1 <= batch <= ntrain, epochs >= 0, lr > 0");
+  return surrogate_train(c, P, Y, ntrain, epochs, batch, lr, seed, loss_out, (cudaStream_t)stream);
+}
+
+sas_status subapsnap_surrogate_predict(sas_ctx* c, const double* params, int64_t m, double* Yhat,
+                                       void* stream) {
+  if (!c || !params || !Yhat) return fail(SAS_EINVAL, "NULL argument");
+  if (!surrogate_ready(c)) return fail(SAS_EINVAL, "the surrogate is not trained");
+  if (m <= 0) return m == 0 ? SAS_OK : fail(SAS_EINVAL, "m < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  TraceScope ts(c, SAS_KERNEL_SURROGATE, st);
+  cudaError_t e = surrogate_predict(c, params, m, Yhat, st);
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate_predict");
+  return SAS_OK;
+}
+
+sas_status subapsnap_solve_batch_surrogate(sas_ctx* c, const double* params, int64_t m,
+                                           int32_t out_kind, void* out, uint32_t* flags,
+                                           double* rho, double gate_tol, int64_t* accepted,
+                                           void* stream) {
+  if (!c || !params || !out) return fail(SAS_EINVAL, "NULL argument");
+  if (!surrogate_ready(c)) return fail(SAS_EINVAL, "the surrogate is not trained");
+  if (out_kind != SAS_OUT_Y && out_kind != SAS_OUT_QOI)
+    return fail(SAS_EINVAL, "the gated solve returns y or the QoI");
+  if (out_kind == SAS_OUT_QOI && c->qoi_kind == SAS_QOI_NONE)
+    return fail(SAS_EINVAL, "context was set up without a QoI");
+  if (m <= 0) {
+    if (accepted) *accepted = 0;
+    return m == 0 ? SAS_OK : fail(SAS_EINVAL, "m < 0");
+  }
+  return surrogate_solve(c, params, m, out_kind, out, flags, rho, gate_tol, accepted,
+                         (cudaStream_t)stream);
+}
+
+sas_status subapsnap_surrogate_weights(sas_ctx* c, int32_t get, float* theta, double* norm,
+                                       int64_t* nparam) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (c->family != kAffine || c->dtype != SAS_REAL64)
+    return fail(SAS_ENOTSUP, "the surrogate needs a real affine context");
+  if (!c->surrogate) {
+    if (get) return fail(SAS_EINVAL, "no surrogate network in this context");
+    sas_status s2 = surrogate_create(c, 0);
+    if (s2 != SAS_OK) return s2;
+  }
+  if (nparam) *nparam = surrogate_nparam(c);
+  if (!theta && !norm) return SAS_OK;
+  return surrogate_io(c, get, theta, norm);
+}
+
+sas_status subapsnap_surrogate_grad(sas_ctx* c, const double* X, const double* Yn, int64_t B,
+                                    double* loss, float* grads) {
+  if (!c || !X || !Yn || !loss || !grads) return fail(SAS_EINVAL, "NULL argument");
+  if (!c->surrogate) return fail(SAS_EINVAL, "no surrogate network in this context");
+  if (B < 1) return fail(SAS_EINVAL, "B must be positive");
+  return surrogate_grad(c, X, Yn, B, loss, grads, 0);
+}
+
 void subapsnap_destroy(sas_ctx* c) { free_ctx(c); }
+
+namespace sas {
+static std::string tune_key(const sas_ctx* c, int64_t m) {
+  std::ostringstream k;
+  k << "family=" << c->family << " mode=" << c->mode << " dtype=" << c->dtype << " s=" << c->s
+    << " r=" << c->r << " K=" << c->K << " m=" << m;
+  return k.str();
+}
+static int tune_cache_lookup(const std::string& key) {
+  const char* path = std::getenv("SAS_TUNE_CACHE");
+  if (!path) return -1;
+  std::ifstream f(path);
+  std::string line;
+  int found = -1;
+  while (std::getline(f, line)) {
+    const size_t bar = line.rfind(" variant=");
+    if (bar != std::string::npos && line.compare(0, bar, key) == 0)
+      found = std::atoi(line.c_str() + bar + 9);
+  }
+  return found;
+}
+static void tune_cache_store(const std::string& key, int v) {
+  const char* path = std::getenv("SAS_TUNE_CACHE");
+  if (!path) return;
+  std::ofstream f(path, std::ios::app);
+  f << key << " variant=" << v << "\n";
+}
+}  // namespace sas
+
+sas_status subapsnap_autotune(sas_ctx* c, const double* params, int64_t m, int32_t reps,
+                              double* times_ms, int32_t* chosen, void* stream) {
+  if (!c || !params) return fail(SAS_EINVAL, "NULL argument");
+  if (m < 1) return fail(SAS_EINVAL, "m must be positive");
+  if (reps < 1) reps = 1;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool mixed = c->mode == SAS_MODE_MIXED;
+  int* var = mixed ? &c->ls_variant_mixed : &c->ls_variant_plain;
+  const int nv = ls_num_variants(mixed);
+  if (times_ms)
+    for (int v = 0; v < 16; ++v) times_ms[v] = -1.0;
+  const std::string key = tune_key(c, m);
+  const int cached = tune_cache_lookup(key);
+  if (cached >= 0 && cached < nv) {
+    *var = cached;
+    if (chosen) *chosen = cached;
+    return SAS_OK;
+  }
+  void* Y = nullptr;
+  const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
+  cudaError_t e = cudaMalloc(&Y, (size_t)m * c->r * es);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int keep = *var;
+  int best = keep;
+  double best_ms = 1e300;
+  const int tr = c->tracing;
+  c->tracing = 0;
+  for (int v = 0; v < nv; ++v) {
+    *var = v;
+    sas_status s0 = subapsnap_solve_batch(c, params, m, SAS_OUT_Y, Y, nullptr, nullptr, st);
+    if (s0 != SAS_OK || cudaStreamSynchronize(st) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, st);
+    for (int k = 0; k < reps; ++k) subapsnap_solve_batch(c, params, m, SAS_OUT_Y, Y, nullptr, nullptr, st);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double per = ms / reps;
+    if (times_ms && v < 16) times_ms[v] = per;
+    if (per < best_ms) {
+      best_ms = per;
+      best = v;
+    }
+  }
+  c->tracing = tr;
+  *var = best;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(Y);
+  if (chosen) *chosen = best;
+  if (best_ms < 1e300) tune_cache_store(key, best);
+  return SAS_OK;
+}
 
 sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");
@@ -574,6 +734,13 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
       if (!(value > 0.0 && value < 1.0)) return fail(SAS_EINVAL, "refine tol must be in (0, 1)");
       c->refine_tol = value;
       return SAS_OK;
+    case SAS_OPT_LS_VARIANT: {
+      const bool mixed = c->mode == SAS_MODE_MIXED;
+      const int nv = ls_num_variants(mixed);
+      if (!(value >= 0.0 && value < nv)) return fail(SAS_EINVAL, "ls variant out of range");
+      (mixed ? c->ls_variant_mixed : c->ls_variant_plain) = (int)value;
+      return SAS_OK;
+    }
     default:
       return fail(SAS_EINVAL, "unknown option");
   }

@@ -180,8 +180,11 @@ struct sas_ctx {
   int* dev_status;     // device status word
   int num_sms;
   int ls_blocks_per_sm;
+  void* surrogate;     // learned surrogate network (sas_mlp.cu), or null
   // options
   int recon_kernel;    // 0 auto, 1 CUDA cores, 2 tensor cores
+  int ls_variant_plain;  // launch shape of the plain LS kernel (autotuned)
+  int ls_variant_mixed;  // launch shape (+ float64 M kept or not) of the mixed LS kernel
   int max_refine;
   double refine_tol;
   // tracing
@@ -222,6 +225,7 @@ cudaError_t launch_ls_mixed(const sas_ctx* c, const double* params, int64_t m, v
                             void* qoi_out, float* ysplit, uint32_t* flags, double* rho,
                             cudaStream_t st, const void* Mg = nullptr);
 size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block);
+int ls_num_variants(bool mixed);
 size_t ls_mixed_smem_bytes(const sas_ctx* c);
 cudaError_t launch_reconstruct_f64(const sas_ctx* c, const void* Y, int64_t m, void* out,
                                    cudaStream_t st);
@@ -239,6 +243,21 @@ cudaError_t launch_krr_assemble(const sas_ctx* c, const double* params, int64_t 
 cudaError_t launch_gather_kernel_rows(const sas_ctx* c, cudaStream_t st);
 cudaError_t launch_true_residual(const sas_ctx* c, const double* params, int64_t m, const void* X,
                                  double* rho, cudaStream_t st);
+// surrogate
+sas_status surrogate_create(sas_ctx* c, uint64_t seed);
+void destroy_surrogate(sas_ctx* c);
+sas_status surrogate_train(sas_ctx* c, const double* P, const double* Y, int64_t ntrain, int epochs,
+                           int batch, double lr, uint64_t seed, double* loss_out, cudaStream_t st);
+cudaError_t surrogate_predict(sas_ctx* c, const double* params, int64_t m, double* Yhat,
+                              cudaStream_t st);
+sas_status surrogate_grad(sas_ctx* c, const double* X, const double* Yn, int64_t B, double* loss,
+                          float* grads_host, cudaStream_t st);
+sas_status surrogate_io(sas_ctx* c, int get, float* theta, double* norm);
+int64_t surrogate_nparam(const sas_ctx* c);
+bool surrogate_ready(const sas_ctx* c);
+sas_status surrogate_solve(sas_ctx* c, const double* params, int64_t m, int32_t out_kind, void* out,
+                           uint32_t* flags, double* rho_out, double tol, int64_t* accepted,
+                           cudaStream_t st);
 // selection
 sas_status select_rows_affine(const sas_affine_desc* d, const double* p_sel, int64_t* J_out,
                               double* gap_out);

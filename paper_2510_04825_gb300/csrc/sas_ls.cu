@@ -161,8 +161,8 @@ struct LsPlainArgs {
   double* rho;
 };
 
-template <typename T, int NT>
-__global__ void __launch_bounds__(NT, 2) ls_plain_affine_kernel(LsPlainArgs<T> a) {
+template <typename T, int NT, int G>
+__global__ void __launch_bounds__(NT, 512 / NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = a.s, r = a.r, t = a.t, ldt = a.ldt, K = a.K;
   const bool single = t >= s;
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(NT, 2) ls_plain_affine_kernel(LsPlainArgs<T> a
         tail_norm_warp0<T, double>(P + 1, tb - 1, &nrm2[0]);
         __syncthreads();
         for (int k = 0; k < r; ++k)
-          householder_step<T, double, NT, 4>(k, r + 1, P + k, ldt, P + k + 1, ldt, tb - k - 1, 1,
+          householder_step<T, double, NT, G>(k, r + 1, P + k, ldt, P + k + 1, ldt, tb - k - 1, 1,
                                              nrm2, (T*)nullptr, (double*)nullptr);
         __syncthreads();
         double part = 0.0;
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(NT, 2) ls_plain_affine_kernel(LsPlainArgs<T> a
         tail_norm_warp0<T, double>(P, tb, &nrm2[0]);
         __syncthreads();
         for (int k = 0; k < r; ++k)
-          householder_step<T, double, NT, 4>(k, r + 1, Rm + k, r, P, ldt, tb, 0, nrm2,
+          householder_step<T, double, NT, G>(k, r + 1, Rm + k, r, P, ldt, tb, 0, nrm2,
                                              (T*)nullptr, (double*)nullptr);
         __syncthreads();
         double part = 0.0;
@@ -264,8 +264,20 @@ __global__ void __launch_bounds__(NT, 2) ls_plain_affine_kernel(LsPlainArgs<T> a
   }
 }
 
-constexpr int kLsThreads = 256;
+constexpr int kLsThreads = 256;  // largest CTA of any variant (sizes the reduction scratch)
 constexpr size_t kSmemLimit = 227 * 1024 - 1024;
+
+// Launch shapes of the least-squares kernels: threads per CTA and lanes per
+// column group of the Householder step; the mixed kernel also chooses whether
+// to keep M in float64 shared memory (when it fits).  The autotuner times
+// them per context.
+struct LsShape {
+  int nt, g;
+};
+static const LsShape kLsShapes[] = {{256, 4}, {128, 4}, {256, 8}, {128, 2}, {256, 2}};
+constexpr int kNumLsShapes = sizeof(kLsShapes) / sizeof(kLsShapes[0]);
+
+int ls_num_variants(bool mixed) { return mixed ? 2 * kNumLsShapes : kNumLsShapes; }
 
 size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block) {
   const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
@@ -311,16 +323,25 @@ static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_
   a.qoi = (T*)qoi;
   a.flags = flags;
   a.rho = rho;
-  auto kern = ls_plain_affine_kernel<T, kLsThreads>;
+  const int v = c->ls_variant_plain % kNumLsShapes;
+  void (*kern)(LsPlainArgs<T>) = nullptr;
+  switch (v) {
+    case 0: kern = ls_plain_affine_kernel<T, 256, 4>; break;
+    case 1: kern = ls_plain_affine_kernel<T, 128, 4>; break;
+    case 2: kern = ls_plain_affine_kernel<T, 256, 8>; break;
+    case 3: kern = ls_plain_affine_kernel<T, 128, 2>; break;
+    default: kern = ls_plain_affine_kernel<T, 256, 2>; break;
+  }
+  const int nt = kLsShapes[v].nt;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLsThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)c->num_sms * per_sm;
   if (grid > m) grid = m;
-  kern<<<(unsigned)grid, kLsThreads, smem, st>>>(a);
+  kern<<<(unsigned)grid, nt, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -368,8 +389,8 @@ __device__ inline float tf32_round(float x) {
 //     float32, y += delta, until ||delta|| <= tol ||y|| or a step no longer
 //     halves the correction; the last residual evaluated belongs to the
 //     returned y, so rho is exact in float64.
-template <typename TH, typename TL, int NT>
-__global__ void __launch_bounds__(NT, 2) ls_mixed_affine_kernel(LsMixedArgs<TH, TL> a) {
+template <typename TH, typename TL, int NT, int G>
+__global__ void __launch_bounds__(NT, 512 / NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int s = a.s, r = a.r, ldt = a.ldt, K = a.K;
   TH* th = reinterpret_cast<TH*>(smem_raw);      // kMaxDp
@@ -429,7 +450,7 @@ __global__ void __launch_bounds__(NT, 2) ls_mixed_affine_kernel(LsMixedArgs<TH, 
     tail_norm_warp0<TL, float>(P + 1, s - 1, &nrm2[0]);
     __syncthreads();
     for (int k = 0; k < r; ++k)
-      householder_step<TL, float, NT, 4>(k, r + 1, P + k, ldt, P + k + 1, ldt, s - k - 1, 1, nrm2,
+      householder_step<TL, float, NT, G>(k, r + 1, P + k, ldt, P + k + 1, ldt, s - k - 1, 1, nrm2,
                                          v0, tau);
     __syncthreads();
     // y0 = R^{-1} z
@@ -570,7 +591,9 @@ static size_t mixed_base_bytes(const sas_ctx* c) {
 
 static bool mixed_keep64(const sas_ctx* c) {
   const size_t eh = c->dtype == SAS_COMPLEX128 ? 16 : 8;
-  // keep M in float64 when it fits and leaves room for two CTAs per SM
+  // keep M in float64 when the variant asks for it, it fits and leaves room for
+  // two CTAs per SM
+  if (c->ls_variant_mixed >= kNumLsShapes) return false;
   return mixed_base_bytes(c) + (size_t)c->s * c->r * eh <= kSmemLimit / 2;
 }
 
@@ -610,16 +633,25 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
   a.ysplit = ysplit;
   a.flags = flags;
   a.rho = rho;
-  auto kern = ls_mixed_affine_kernel<TH, TL, kLsThreads>;
+  const int v = c->ls_variant_mixed % kNumLsShapes;
+  void (*kern)(LsMixedArgs<TH, TL>) = nullptr;
+  switch (v) {
+    case 0: kern = ls_mixed_affine_kernel<TH, TL, 256, 4>; break;
+    case 1: kern = ls_mixed_affine_kernel<TH, TL, 128, 4>; break;
+    case 2: kern = ls_mixed_affine_kernel<TH, TL, 256, 8>; break;
+    case 3: kern = ls_mixed_affine_kernel<TH, TL, 128, 2>; break;
+    default: kern = ls_mixed_affine_kernel<TH, TL, 256, 2>; break;
+  }
+  const int nt = kLsShapes[v].nt;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kLsThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)c->num_sms * per_sm;
   if (grid > m) grid = m;
-  kern<<<(unsigned)grid, kLsThreads, smem, st>>>(a);
+  kern<<<(unsigned)grid, nt, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -243,3 +243,30 @@ def test_invalid_arguments_raise():
     with pytest.raises(api.SasError):
         api.subapsnap_solve_batch(solver.ctx, P, 1, 7, out)
     solver.close()
+
+
+@pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED])
+def test_every_ls_variant_and_autotune(c1_small, mode):
+    """Every launch shape the autotuner may pick gives the oracle's answer."""
+    case = c1_small
+    p = case.prob
+    params = p.test_params[:100]
+    Yo, rho_o = case.oracle_solve(params)
+    nvar = 5 if mode == api.SAS_MODE_PLAIN else 10
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
+    solver = AffineSolver(p, case.S, case.J, mode=mode, device=DEV)
+    bound = _mixed_bound(p, case.S, case.J, params, Yo, rho_o)
+    for v in range(nvar):
+        api.subapsnap_set_option(solver.ctx, api.SAS_OPT_LS_VARIANT, v)
+        Y = torch.empty((len(params), p.r), dtype=torch.float64, device=DEV)
+        solver.solve(P, api.SAS_OUT_Y, Y)
+        torch.cuda.synchronize()
+        err = rel_err_rows(Y.cpu().numpy(), Yo)
+        if mode == api.SAS_MODE_PLAIN:
+            assert err.max() <= 1e-10, (v, err.max())
+        else:
+            assert (err <= bound).all(), (v, err.max())
+    chosen, times = api.subapsnap_autotune(solver.ctx, P, len(params), 2)
+    print(f"autotune mode {mode}: chosen {chosen}, times {[round(t, 4) for t in times[:nvar]]}")
+    assert 0 <= chosen < nvar and times[chosen] > 0
+    solver.close()
