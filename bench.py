@@ -366,7 +366,7 @@ def build_other(args, device, rank):
     elif wl == "kernel_ridge":
         prob = get_config("kernel_ridge")
         X = torch.from_numpy(np.ascontiguousarray(prob.X)).to(device)
-        S_rows, res = wsnap.kernel_ridge_basis_torch(prob, X, device=device)
+        S_rows, res = wsnap.kernel_ridge_basis_torch(prob, X, device=device, iters=15)
         info["snapshot_cg_max_rel_residual"] = float(np.max(res))
         from paper_2510_04825_gb300.solver import select_rows_kernel
         J, gaps = select_rows_kernel(prob, X, S_rows, prob.sel_param, prob.s)
@@ -510,6 +510,133 @@ def run_gpu_other(args):
         pg.destroy_process_group()
 
 
+def run_gpu_surrogate(args):
+    """Learned-surrogate workload: 4096 x 4096 diffusion (n = 16.8M), r = 60, s = 120.
+
+    Step (chosen form): gated solve of 65,536 parameters for the grid-mean QoI
+    (network prediction accepted when the float64 subsampled residual <= 1e-6,
+    mixed least squares otherwise) plus full x_hat for 256 of them (float32,
+    tensor cores).  Plain form: float64 least squares for the 65,536 QoI and
+    float64 x_hat for the 256.
+    """
+    import torch
+    from paper_2510_04825_gb300 import api
+    from paper_2510_04825_gb300.solver import AffineSolver, csr_to_device, select_rows
+    from workloads import get_config
+    from workloads import snapshots as wsnap
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    t0 = time.time()
+    N = args.grid if args.grid != GRID else 4096
+    prob = get_config("surrogate_diffusion_2d", N=N)
+    blocks = [csr_to_device(A, device) for A in prob.blocks]
+    t_csr = time.time() - t0
+    S_rows, snap_res = wsnap.diffusion_basis_torch(prob, device=device)
+    J, _ = select_rows(prob, S_rows, blocks, prob.sel_param, prob.s, device=device)
+    chosen = AffineSolver(prob, None, J, mode=api.SAS_MODE_MIXED, device=device, S_device=S_rows,
+                          blocks_device=blocks)
+    plain = AffineSolver(prob, None, J, mode=api.SAS_MODE_PLAIN, device=device, S_device=S_rows,
+                         blocks_device=blocks)
+    m, nx, n, r = prob.test_params.shape[0], 256, prob.n, prob.r
+    P = torch.from_numpy(np.ascontiguousarray(prob.test_params)).to(device)
+    api.subapsnap_autotune(chosen.ctx, P, m, 2)
+    api.subapsnap_autotune(plain.ctx, P, m, 1)
+    # training pairs produced by the online stage itself
+    ntrain = 100_000
+    Ptr = torch.from_numpy(np.random.default_rng(123).uniform(0.0, 1.0, (ntrain, prob.dp))).to(device)
+    Ytr = torch.empty((ntrain, r), dtype=torch.float64, device=device)
+    chosen.solve(Ptr, api.SAS_OUT_Y, Ytr)
+    t1 = time.time()
+    losses = api.subapsnap_surrogate_train(chosen.ctx, Ptr, Ytr, args.epochs, 1024, 1e-3, seed=7)
+    torch.cuda.synchronize()
+    train_s = time.time() - t1
+    setup_s = time.time() - t0
+    tol = 1e-6
+    H = torch.empty(m, dtype=torch.float64, device=device)
+    rho_c = torch.empty(m, dtype=torch.float64, device=device)
+    flags = torch.zeros(m, dtype=torch.int32, device=device)
+    Ysub = torch.empty((nx, r), dtype=torch.float64, device=device)
+    X32 = torch.empty((nx, n), dtype=torch.float32, device=device)
+    acc = [0]
+
+    def step_chosen():
+        acc[0] = api.subapsnap_solve_batch_surrogate(chosen.ctx, P, m, api.SAS_OUT_QOI, H, flags, rho_c, tol)
+        api.subapsnap_solve_batch_surrogate(chosen.ctx, P[:nx], nx, api.SAS_OUT_Y, Ysub, None, None, tol)
+        chosen.reconstruct(Ysub, X32)
+
+    Hp = torch.empty(m, dtype=torch.float64, device=device)
+    rho_p = torch.empty(m, dtype=torch.float64, device=device)
+    Yp = torch.empty((nx, r), dtype=torch.float64, device=device)
+    X64 = torch.empty((nx, n), dtype=torch.float64, device=device)
+
+    def step_plain():
+        plain.solve(P, api.SAS_OUT_QOI, Hp, None, rho_p)
+        plain.solve(P[:nx], api.SAS_OUT_Y, Yp)
+        plain.reconstruct(Yp, X64)
+
+    def step_mixed_only():  # mixed least squares for everything, no network
+        chosen.solve(P, api.SAS_OUT_QOI, H, None, rho_c)
+        chosen.solve(P[:nx], api.SAS_OUT_Y, Ysub)
+        chosen.reconstruct(Ysub, X32)
+
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup, clocks=False):
+        clk = None
+        if clocks and rank == 0:
+            cpath = os.path.join(tempfile.gettempdir(), f"sas_clocks_{os.getpid()}.csv")
+            sp, sf = start_clock_sampler(cpath)
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if clocks and rank == 0:
+            clk = stop_clock_sampler(sp, sf, cpath, local)
+        return e0.elapsed_time(e1) / steps, clk
+
+    ms_c, clocks = timed(step_chosen, args.steps, args.warmup, clocks=True)
+    ms_mix, _ = timed(step_mixed_only, max(1, min(args.steps, 3)), 1)
+    ms_p, _ = timed(step_plain, 1, 1)
+    rc = rho_c.cpu().numpy()
+    fl = flags.cpu().numpy()
+    rp = rho_p.cpu().numpy()
+    hc, hp = H.cpu().numpy(), Hp.cpu().numpy()
+    herr = np.abs(hc - hp) / np.abs(hp).max()
+    line = {
+        "metric": METRIC, "value": round(m / (ms_c * 1e-3), 2), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_c, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "surrogate (bf16 weights, f32 accumulate) gated by f64 subsampled residual; "
+                 "fallback f32 Householder + f64 refinement; x_hat f32 (tf32x3)",
+        "data": "synthetic (seeded 2-D diffusion 4096^2, snapshot basis from PCG)",
+        "config": {"workload": f"surrogate_diffusion_2d_{N}x{N}_r60_s120_m65536_x256", "n": n, "r": r,
+                   "s": prob.s, "m_per_gpu": m, "x_hat_params": nx, "gate_tol": tol,
+                   "ntrain": ntrain, "epochs": args.epochs},
+        "accepted_fraction": round(acc[0] / m, 4),
+        "surrogate_loss_first_last": [float(losses[0]), float(losses[-1])] if len(losses) else None,
+        "train_s": round(train_s, 2),
+        "mixed_without_network": {"value": round(m / (ms_mix * 1e-3), 2), "ms_per_step": round(ms_mix, 3)},
+        "plain_fp64": {"value": round(m / (ms_p * 1e-3), 2), "ms_per_step": round(ms_p, 3)},
+        "speedup_chosen_vs_plain": round(ms_p / ms_c, 2),
+        "speedup_network_vs_mixed": round(ms_mix / ms_c, 3),
+        "residual": {"sub_chosen_max": float(rc.max()), "sub_chosen_median": float(np.median(rc)),
+                     "sub_plain_max": float(rp.max()), "sub_plain_median": float(np.median(rp)),
+                     "accepted_max_rho": float(rc[(fl & 8) != 0].max()) if acc[0] else None,
+                     "qoi_maxerr_vs_plain_rel": float(herr.max())},
+        "clocks": clocks, "setup_s": round(setup_s, 1), "csr_build_s": round(t_csr, 1),
+        "snapshot_pcg_max_rel_residual": float(np.max(snap_res)),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def chosen_kernel_version():
     return TC_VERSION
 
@@ -594,10 +721,14 @@ def main():
     ap.add_argument("--quick", action="store_true", help="time the chosen form only (profiling runs)")
     ap.add_argument("--grid", type=int, default=GRID, help="interior grid side (profiling runs use 512)")
     ap.add_argument("--workload", default="diffusion_2d",
-                    choices=["diffusion_2d", "transfer_function", "reaction_diffusion_1d", "kernel_ridge"])
+                    choices=["diffusion_2d", "transfer_function", "reaction_diffusion_1d", "kernel_ridge",
+                             "surrogate_diffusion_2d"])
+    ap.add_argument("--epochs", type=int, default=100, help="surrogate training epochs")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "surrogate_diffusion_2d":
+        run_gpu_surrogate(args)
     elif args.workload != "diffusion_2d":
         run_gpu_other(args)
     else:

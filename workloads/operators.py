@@ -24,35 +24,25 @@ def diffusion_2d(N: int, a_xface: np.ndarray, a_yface: np.ndarray, h: float) -> 
     columns i-1 and i (i = 0..N, shape (N+1, N)); ``a_yface[i, j]`` the
     coefficient on the y-face between rows j-1 and j (shape (N, N+1)).
     Dirichlet boundary: faces touching the boundary still contribute their
-    coefficient to the diagonal.  Scaled by 1/h^2.
+    coefficient to the diagonal.  Scaled by 1/h^2.  Built row by row in CSR
+    order (south, west, centre, east, north), so no sorting is needed.
     """
     n = N * N
-    idx = np.arange(n).reshape(N, N, order="F")  # idx[i, j] = i + N*j
-    aw = a_xface[:-1, :]  # face west of (i, j)
-    ae = a_xface[1:, :]   # face east
-    as_ = a_yface[:, :-1]  # face south
-    an = a_yface[:, 1:]    # face north
-    diag = (aw + ae + as_ + an).ravel(order="F")
-    rows = [idx.ravel(order="F")]
-    cols = [idx.ravel(order="F")]
-    vals = [diag]
-    # west neighbour (i-1, j)
-    rows.append(idx[1:, :].ravel(order="F")); cols.append(idx[:-1, :].ravel(order="F"))
-    vals.append(-aw[1:, :].ravel(order="F"))
-    # east neighbour (i+1, j)
-    rows.append(idx[:-1, :].ravel(order="F")); cols.append(idx[1:, :].ravel(order="F"))
-    vals.append(-ae[:-1, :].ravel(order="F"))
-    # south neighbour (i, j-1)
-    rows.append(idx[:, 1:].ravel(order="F")); cols.append(idx[:, :-1].ravel(order="F"))
-    vals.append(-as_[:, 1:].ravel(order="F"))
-    # north neighbour (i, j+1)
-    rows.append(idx[:, :-1].ravel(order="F")); cols.append(idx[:, 1:].ravel(order="F"))
-    vals.append(-an[:, :-1].ravel(order="F"))
-    A = sp.csr_matrix(
-        (np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)
-    )
-    A.sort_indices()
-    return (A / (h * h)).tocsr()
+    aw = a_xface[:-1, :].ravel(order="F")   # face west of node (i, j), node index i + N j
+    ae = a_xface[1:, :].ravel(order="F")
+    as_ = a_yface[:, :-1].ravel(order="F")
+    an = a_yface[:, 1:].ravel(order="F")
+    idx = np.arange(n, dtype=np.int64)
+    i = idx % N
+    j = idx // N
+    cols = np.stack([idx - N, idx - 1, idx, idx + 1, idx + N], axis=1)
+    vals = np.stack([-as_, -aw, aw + ae + as_ + an, -ae, -an], axis=1) / (h * h)
+    valid = np.stack([j > 0, i > 0, np.ones(n, dtype=bool), i < N - 1, j < N - 1], axis=1)
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(valid.sum(axis=1), out=indptr[1:])
+    A = sp.csr_matrix((vals[valid], cols[valid].astype(np.int32), indptr), shape=(n, n))
+    A.has_sorted_indices = True
+    return A
 
 
 def gaussian_bump_faces(N: int, centre: np.ndarray, width: float):
