@@ -53,6 +53,30 @@ def dist_env():
     return rank, world, local
 
 
+def rank_params(params, rank):
+    """Weak scaling: rank 0 solves the workload's own draw, rank k > 0 an independent
+    seeded draw of the same size and distribution (no data exchanged between ranks)."""
+    if rank == 0:
+        return params
+    lo, hi = params.min(axis=0), params.max(axis=0)
+    return np.random.default_rng(1000 + rank).uniform(lo, hi, params.shape)
+
+
+def max_over_ranks(value, dist_mod, device="cpu"):
+    """Max of a per-rank float over all ranks (the job is as slow as its slowest rank)."""
+    import torch
+    if dist_mod is None:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, ms_per_step):
+    """Whole-job units per second: all ranks' units over the slowest rank's step time."""
+    return world * units_per_rank / (ms_per_step * 1e-3)
+
+
 def start_clock_sampler(path):
     try:
         f = open(path, "w")
@@ -107,9 +131,7 @@ def build_inputs(device, rank, grid=GRID):
     blocks = [csr_to_device(A, device) for A in prob.blocks]
     S_rows, snap_res = wsnap.diffusion_basis_torch(prob, device=device)
     J, gaps = select_rows(prob, S_rows, blocks, prob.sel_param, S_ROWS, device=device)
-    params = prob.test_params
-    if rank > 0:  # weak scaling: every rank solves its own draw of 4096 parameters
-        params = np.random.default_rng(1000 + rank).uniform(0.0, 1.0, params.shape)
+    params = rank_params(prob.test_params, rank)  # weak scaling: one draw of 4096 per rank
     P = torch.from_numpy(np.ascontiguousarray(params)).to(device)
     return prob, blocks, S_rows, J, gaps, P, params, snap_res
 
@@ -179,11 +201,7 @@ def run_gpu(args):
             clk = stop_clock_sampler(sp, sf, cpath, local)
         if pg:
             pg.barrier()
-        ms = e0.elapsed_time(e1) / steps
-        if pg:
-            t = torch.tensor([ms], device=device)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1) / steps, pg, device)
         return ms, clk
 
     # ---- chosen form (headline), with live per-kernel tracing
@@ -266,8 +284,8 @@ def run_gpu(args):
         except Exception:
             traffic = None
 
-    value = world * M / (ms_chosen * 1e-3)
-    plain_value = world * M / (ms_plain * 1e-3)
+    value = job_throughput(world, M, ms_chosen)
+    plain_value = job_throughput(world, M, ms_plain)
     if args.grid != GRID:
         line_workload = f"diffusion_2d_{args.grid}x{args.grid}_r60_s120_m4096_chunk256"
     else:
@@ -375,9 +393,7 @@ def build_other(args, device, rank):
         out_kind, out_shape, out_dtype = api.SAS_OUT_Y, (prob.test_params.shape[0], prob.r), torch.float64
     else:
         raise SystemExit(f"unknown workload {wl}")
-    params = prob.test_params
-    if rank > 0:
-        params = np.random.default_rng(1000 + rank).permutation(params)
+    params = rank_params(prob.test_params, rank)
     P = torch.from_numpy(np.ascontiguousarray(params)).to(device)
     return prob, mk, P, params, out_kind, out_shape, out_dtype, info
 
@@ -398,6 +414,11 @@ def run_gpu_other(args):
     prob, mk, P, params_host, out_kind, out_shape, out_dtype, info = build_other(args, device, rank)
     chosen, plain = mk(api.SAS_MODE_MIXED), mk(api.SAS_MODE_PLAIN)
     m = P.shape[0]
+    tune = {}
+    if args.workload != "kernel_ridge":  # kernel rows dominate there; the LS shape barely matters
+        for name, sv in (("chosen", chosen), ("plain", plain)):
+            v, times = api.subapsnap_autotune(sv.ctx, P, m, 2)
+            tune[name] = {"variant": v, "ms": [round(t, 4) for t in times if t >= 0]}
     stream = torch.cuda.current_stream()
     setup_s = time.time() - t0
 
@@ -502,7 +523,7 @@ def run_gpu_other(args):
         "kernel_ms": {"ls": round(ls_ms / max(ls_n, 1), 4),
                       "assemble": round(asm_ms / max(asm_n, 1), 4) if asm_n else None},
         "gpu_launches": args.steps * ((asm_n + ls_n) + (ls_n if out_kind == api.SAS_OUT_XHAT else 0)),
-        "clocks": clocks, "setup_s": round(setup_s, 1), **info,
+        "clocks": clocks, "setup_s": round(setup_s, 1), "autotune": tune, **info,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -328,6 +328,36 @@ sas_status subapsnap_surrogate_weights(sas_ctx* ctx, int32_t get, float* theta, 
 sas_status subapsnap_surrogate_grad(sas_ctx* ctx, const double* X, const double* Yn, int64_t B,
                                     double* loss, float* grads);
 
+/* ------------------------------------------------------------------------
+ * Persistent batched launch over several contexts (not in the paper).  One
+ * kernel launch drains the parameters of nctx contexts whose s, r and K may
+ * differ (operator families of the same dtype and mode): CTAs take tasks
+ * from a global counter, and each task runs the same per-parameter solve as
+ * subapsnap_solve_batch with the first context's launch shape.  A plan holds
+ * the device descriptors; launching it is capture-safe (no allocation, no
+ * synchronisation) and can replay a CUDA graph the plan captured once.
+ * ---------------------------------------------------------------------- */
+typedef struct sas_multi_plan sas_multi_plan;
+
+/* Build a plan.  ctxs: host array of nctx affine contexts (same dtype and
+ * mode).  params, outs, flags, rho: host arrays of nctx device pointers
+ * (flags and rho may be NULL, or hold NULL entries); m: host array of batch
+ * sizes.  out_kind: SAS_OUT_Y or SAS_OUT_QOI.  The pointed-to buffers must
+ * outlive the plan.  Synchronous.  Errors: SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA. */
+sas_status subapsnap_multi_plan_create(sas_ctx* const* ctxs, int32_t nctx,
+                                       const double* const* params, const int64_t* m,
+                                       int32_t out_kind, void* const* outs,
+                                       uint32_t* const* flags, double* const* rho,
+                                       sas_multi_plan** plan);
+
+/* Enqueue the plan on `stream`: a counter reset and one persistent launch.
+ * use_graph != 0: the first call captures them into a CUDA graph (on a
+ * stream of the plan's own) and every call launches that graph on `stream`. */
+sas_status subapsnap_multi_plan_launch(sas_multi_plan* plan, int32_t use_graph, void* stream);
+
+/* Release a plan (its graph included).  NULL is a no-op. */
+void subapsnap_multi_plan_destroy(sas_multi_plan* plan);
+
 /* Release a context and everything it allocated.  NULL is a no-op. */
 void subapsnap_destroy(sas_ctx* ctx);
 
@@ -338,6 +368,14 @@ const char* subapsnap_last_error(void);
  * (e.g. SAS_ETIMEOUT from a bounded wait).  Synchronises the context's
  * work on `stream` and clears the word. */
 sas_status subapsnap_device_status(sas_ctx* ctx, void* stream);
+
+/* Self-test of the device-side failure path (not in the paper): a kernel waits,
+ * through the bounded wait every pipelined kernel of the library uses, on a
+ * barrier that nothing arrives on; after `seconds` (0 < seconds <= 2) the
+ * wait gives up and records SAS_ETIMEOUT in the context's status word, which
+ * this call then reads (synchronising `stream`) and clears.  Returns
+ * SAS_ETIMEOUT when the mechanism works; the context stays usable. */
+sas_status subapsnap_selftest_wait(sas_ctx* ctx, double seconds, void* stream);
 
 /* Library version string. */
 const char* subapsnap_version(void);

@@ -34,6 +34,8 @@ EXPORTED = [
     "subapsnap_set_option", "subapsnap_reconstruct", "subapsnap_select_rows_kernel",
     "subapsnap_autotune", "subapsnap_surrogate_train", "subapsnap_surrogate_predict",
     "subapsnap_solve_batch_surrogate", "subapsnap_surrogate_weights", "subapsnap_surrogate_grad",
+    "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch", "subapsnap_multi_plan_destroy",
+    "subapsnap_selftest_wait",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
@@ -105,6 +107,13 @@ def lib() -> ctypes.CDLL:
                                                       i64p, vp]
         L.subapsnap_surrogate_weights.argtypes = [vp, i32, fp_, dp_, i64p]
         L.subapsnap_surrogate_grad.argtypes = [vp, vp, vp, i64, dp_, fp_]
+        L.subapsnap_multi_plan_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64p,
+                                                  i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                  ctypes.POINTER(vp), ctypes.POINTER(vp)]
+        L.subapsnap_multi_plan_launch.argtypes = [vp, i32, vp]
+        L.subapsnap_multi_plan_destroy.argtypes = [vp]
+        L.subapsnap_multi_plan_destroy.restype = None
+        L.subapsnap_selftest_wait.argtypes = [vp, ctypes.c_double, vp]
         L.subapsnap_autotune.argtypes = [vp, vp, i64, i32, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(ctypes.c_int32), vp]
         L.subapsnap_select_rows_kernel.argtypes = [ctypes.POINTER(KernelDesc),
@@ -121,7 +130,9 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_reconstruct", "subapsnap_select_rows_kernel",
                      "subapsnap_autotune", "subapsnap_surrogate_train",
                      "subapsnap_surrogate_predict", "subapsnap_solve_batch_surrogate",
-                     "subapsnap_surrogate_weights", "subapsnap_surrogate_grad"):
+                     "subapsnap_surrogate_weights", "subapsnap_surrogate_grad",
+                     "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch",
+                     "subapsnap_selftest_wait"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -315,6 +326,35 @@ def subapsnap_surrogate_grad(ctx, X, Yn, nparam: int):
     _check(lib().subapsnap_surrogate_grad(ctx, _ptr(X), _ptr(Yn), int(X.shape[0]), ctypes.byref(loss),
                                           g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
     return loss.value, g
+
+
+def subapsnap_multi_plan_create(ctxs, params, out_kind: int, outs, flags=None, rho=None):
+    """One persistent launch over several contexts; params/outs/flags/rho are lists of tensors."""
+    n = len(ctxs)
+    VP = ctypes.c_void_p * n
+    arr_ctx = VP(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    arr_p = VP(*[_ptr(t) for t in params])
+    arr_o = VP(*[_ptr(t) for t in outs])
+    arr_f = VP(*[_ptr(t) for t in flags]) if flags is not None else None
+    arr_r = VP(*[_ptr(t) for t in rho]) if rho is not None else None
+    m = (ctypes.c_int64 * n)(*[int(t.shape[0]) for t in params])
+    plan = ctypes.c_void_p()
+    _check(lib().subapsnap_multi_plan_create(arr_ctx, n, arr_p, m, int(out_kind), arr_o, arr_f, arr_r,
+                                             ctypes.byref(plan)))
+    return plan
+
+
+def subapsnap_multi_plan_launch(plan, use_graph: bool = False, stream=None):
+    _check(lib().subapsnap_multi_plan_launch(plan, 1 if use_graph else 0, _stream(stream)))
+
+
+def subapsnap_multi_plan_destroy(plan):
+    lib().subapsnap_multi_plan_destroy(plan)
+
+
+def subapsnap_selftest_wait(ctx, seconds: float = 0.2, stream=None) -> int:
+    """Status the bounded-wait self-test records (SAS_ETIMEOUT when the mechanism works)."""
+    return int(lib().subapsnap_selftest_wait(ctx, float(seconds), _stream(stream)))
 
 
 def subapsnap_destroy(ctx):

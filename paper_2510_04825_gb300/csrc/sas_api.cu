@@ -187,6 +187,15 @@ extern "C" {
 
 const char* subapsnap_version(void) { return "subapsnap-gb300 0.1 (sm_103a)"; }
 
+sas_status subapsnap_selftest_wait(sas_ctx* c, double seconds, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (!(seconds > 0.0 && seconds <= 2.0)) return fail(SAS_EINVAL, "seconds must be in (0, 2]");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = launch_wait_selftest(c->dev_status, seconds, st);
+  if (e != cudaSuccess) return cuda_fail(e, "selftest_wait");
+  return subapsnap_device_status(c, stream);
+}
+
 const char* subapsnap_last_error(void) { return g_last_error.c_str(); }
 
 sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
@@ -624,6 +633,74 @@ sas_status subapsnap_surrogate_grad(sas_ctx* c, const double* X, const double* Y
   if (!c->surrogate) return fail(SAS_EINVAL, "no surrogate network in this context");
   if (B < 1) return fail(SAS_EINVAL, "B must be positive");
   return surrogate_grad(c, X, Yn, B, loss, grads, 0);
+}
+
+struct sas_multi_plan {
+  sas::MultiPlan p;
+};
+
+sas_status subapsnap_multi_plan_create(sas_ctx* const* ctxs, int32_t nctx,
+                                       const double* const* params, const int64_t* m,
+                                       int32_t out_kind, void* const* outs,
+                                       uint32_t* const* flags, double* const* rho,
+                                       sas_multi_plan** plan) {
+  if (!plan) return fail(SAS_EINVAL, "plan is NULL");
+  *plan = nullptr;
+  if (!ctxs || nctx < 1 || !params || !m || !outs) return fail(SAS_EINVAL, "NULL argument");
+  if (out_kind != SAS_OUT_Y && out_kind != SAS_OUT_QOI)
+    return fail(SAS_EINVAL, "multi plans return y or the QoI");
+  for (int i = 0; i < nctx; ++i) {
+    const sas_ctx* c = ctxs[i];
+    if (!c || c->family != kAffine) return fail(SAS_EINVAL, "every context must be affine");
+    if (c->mode != ctxs[0]->mode || c->dtype != ctxs[0]->dtype)
+      return fail(SAS_EINVAL, "every context needs the same mode and dtype");
+    if (m[i] < 0 || (m[i] > 0 && (!params[i] || !outs[i]))) return fail(SAS_EINVAL, "bad batch");
+    if (out_kind == SAS_OUT_QOI && c->qoi_kind == SAS_QOI_NONE)
+      return fail(SAS_EINVAL, "a context was set up without a QoI");
+  }
+  sas_multi_plan* pl = new (std::nothrow) sas_multi_plan();
+  if (!pl) return fail(SAS_ENOMEM, "host allocation failed");
+  cudaError_t e = multi_plan_build(&pl->p, ctxs, nctx, params, m, out_kind, outs, flags, rho);
+  if (e != cudaSuccess) {
+    subapsnap_multi_plan_destroy(pl);
+    return cuda_fail(e, "multi_plan_create");
+  }
+  *plan = pl;
+  return SAS_OK;
+}
+
+sas_status subapsnap_multi_plan_launch(sas_multi_plan* pl, int32_t use_graph, void* stream) {
+  if (!pl) return fail(SAS_EINVAL, "plan is NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (!use_graph) {
+    e = multi_plan_enqueue(&pl->p, st);
+  } else {
+    if (!pl->p.exec) {
+      if (!pl->p.graph_stream) e = cudaStreamCreateWithFlags(&pl->p.graph_stream, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamBeginCapture(pl->p.graph_stream, cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        cudaError_t e2 = multi_plan_enqueue(&pl->p, pl->p.graph_stream);
+        e = cudaStreamEndCapture(pl->p.graph_stream, &pl->p.graph);
+        if (e2 != cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&pl->p.exec, pl->p.graph, 0);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(pl->p.exec, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "multi_plan_launch");
+  return SAS_OK;
+}
+
+void subapsnap_multi_plan_destroy(sas_multi_plan* pl) {
+  if (!pl) return;
+  if (pl->p.exec) cudaGraphExecDestroy(pl->p.exec);
+  if (pl->p.graph) cudaGraphDestroy(pl->p.graph);
+  if (pl->p.graph_stream) cudaStreamDestroy(pl->p.graph_stream);
+  cudaFree(pl->p.d_probs);
+  cudaFree(pl->p.d_offs);
+  cudaFree(pl->p.d_counter);
+  delete pl;
 }
 
 void subapsnap_destroy(sas_ctx* c) { free_ctx(c); }

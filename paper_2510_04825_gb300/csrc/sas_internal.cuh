@@ -234,6 +234,7 @@ cudaError_t launch_reconstruct_mixed(const sas_ctx* c, const float* ysplit, int6
 cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                   cudaStream_t st);
 bool reconstruct_tc_supported(const sas_ctx* c);
+cudaError_t launch_wait_selftest(int* status, double seconds, cudaStream_t st);
 cudaError_t launch_split_y(const double* Y, int64_t m, int r, int rpad, float* ysplit,
                            cudaStream_t st);
 cudaError_t launch_residual(const sas_ctx* c, const double* params, int64_t m, const void* Y,
@@ -258,6 +259,23 @@ bool surrogate_ready(const sas_ctx* c);
 sas_status surrogate_solve(sas_ctx* c, const double* params, int64_t m, int32_t out_kind, void* out,
                            uint32_t* flags, double* rho_out, double tol, int64_t* accepted,
                            cudaStream_t st);
+// persistent multi-problem launch
+struct MultiPlan {
+  const void* kernel = nullptr;
+  void* d_probs = nullptr;
+  int64_t* d_offs = nullptr;
+  unsigned long long* d_counter = nullptr;
+  int nprob = 0, nt = 0, grid = 0;
+  size_t smem = 0;
+  int64_t total = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t graph_stream = nullptr;  // stream the graph was captured on
+};
+cudaError_t multi_plan_build(MultiPlan* pl, sas_ctx* const* ctxs, int n, const double* const* params,
+                             const int64_t* m, int32_t out_kind, void* const* outs,
+                             uint32_t* const* flags, double* const* rho);
+cudaError_t multi_plan_enqueue(MultiPlan* pl, cudaStream_t st);
 // selection
 sas_status select_rows_affine(const sas_affine_desc* d, const double* p_sel, int64_t* J_out,
                               double* gap_out);

@@ -97,10 +97,15 @@ __device__ inline void householder_step(int k, int ncol, T* piv, int ldp, T* tai
   }
 }
 
-// Leading dimension of a shared-memory panel with `rows` rows: >= rows and
-// congruent to 4 mod 32, so that the column groups of a warp (4 lanes each, 8
-// groups) fall into distinct banks.
-__host__ __device__ inline int panel_ld(int rows) { return (rows + 31) / 32 * 32 + 4; }
+// Leading dimension of a shared-memory panel with `rows` rows of elements of
+// `es` bytes: the smallest ld >= rows with ld = 4 (mod 128 / es), so that the
+// column groups of a warp (4 lanes each, 8 groups) spread over the banks with
+// no more wavefronts than the access size needs; at most 128/es - 1 rows of
+// padding.
+__host__ __device__ inline int panel_ld(int rows, int es) {
+  const int mod = 128 / es;
+  return rows + ((4 - rows % mod) % mod + mod) % mod;
+}
 
 // ||col[0..len)||^2 by warp 0 into *slot (the caller synchronises afterwards).
 template <typename T, typename R>
@@ -161,9 +166,12 @@ struct LsPlainArgs {
   double* rho;
 };
 
+// One parameter q of the plain solve (shared by the grid-stride and the
+// persistent multi-problem kernels).
 template <typename T, int NT, int G>
-__global__ void __launch_bounds__(NT, 512 / NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void ls_plain_body(const LsPlainArgs<T>& a, int64_t q,
+                                              unsigned char* smem_raw, double* nrm2) {
+
   const int s = a.s, r = a.r, t = a.t, ldt = a.ldt, K = a.K;
   const bool single = t >= s;
   const int ldr = single ? ldt : r;
@@ -172,10 +180,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) ls_plain_affine_kernel(LsPlainAr
   T* th = P + (size_t)ldt * (r + 1) + (single ? 0 : (size_t)r * (r + 1));
   T* ys = th + kMaxDp;
   double* red = reinterpret_cast<double*>(ys + kMaxR);
-  __shared__ double nrm2[2];
   const int tid = threadIdx.x, warp = tid >> 5;
 
-  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) {
+
     if (tid < K) th[tid] = theta_k<T>(a.rule, tid, a.params + q * a.dp);
     __syncthreads();
     double res2 = 0.0;
@@ -262,6 +269,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) ls_plain_affine_kernel(LsPlainAr
     }
     __syncthreads();
   }
+
+template <typename T, int NT, int G>
+__global__ void __launch_bounds__(NT, 512 / NT) ls_plain_affine_kernel(LsPlainArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double nrm2[2];
+  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) ls_plain_body<T, NT, G>(a, q, smem_raw, nrm2);
 }
 
 constexpr int kLsThreads = 256;  // largest CTA of any variant (sizes the reduction scratch)
@@ -282,29 +295,29 @@ int ls_num_variants(bool mixed) { return mixed ? 2 * kNumLsShapes : kNumLsShapes
 size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block) {
   const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
   const size_t extra = (size_t)(kMaxDp + kMaxR) * es + (kLsThreads / 32) * 8;
-  const size_t single = (size_t)panel_ld(c->s) * (c->r + 1) * es + extra;
+  const int ies = (int)es;
+  const size_t single = (size_t)panel_ld(c->s, ies) * (c->r + 1) * es + extra;
   if (single <= kSmemLimit) {
     *rows_per_block = c->s;
     return single;
   }
   const size_t rbuf = (size_t)c->r * (c->r + 1) * es;
   if (rbuf + extra >= kSmemLimit) return 0;
-  int t = (int)((kSmemLimit - rbuf - extra) / ((c->r + 1) * es)) - 36;
+  int t = (int)((kSmemLimit - rbuf - extra) / ((c->r + 1) * es));
   if (t > c->s) t = c->s;
-  while (t >= c->r && (size_t)panel_ld(t) * (c->r + 1) * es + rbuf + extra > kSmemLimit) --t;
+  while (t >= c->r && (size_t)panel_ld(t, ies) * (c->r + 1) * es + rbuf + extra > kSmemLimit) --t;
   if (t < c->r) return 0;
   *rows_per_block = t;
-  return (size_t)panel_ld(t) * (c->r + 1) * es + rbuf + extra;
+  return (size_t)panel_ld(t, ies) * (c->r + 1) * es + rbuf + extra;
 }
 
 template <typename T>
-static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
-                                  void* qoi, uint32_t* flags, double* rho, cudaStream_t st,
-                                  const void* Mg) {
+static size_t fill_plain_args(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                              void* qoi, uint32_t* flags, double* rho, const void* Mg,
+                              LsPlainArgs<T>& a) {
   int t = 0;
   const size_t smem = ls_plain_smem_bytes(c, &t);
-  if (smem == 0) return cudaErrorInvalidConfiguration;
-  LsPlainArgs<T> a;
+  if (smem == 0) return 0;
   a.Mg = (const T*)Mg;
   a.G = (const T*)c->G;
   a.bJ = (const T*)c->bJ;
@@ -317,12 +330,22 @@ static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_
   a.dp = c->dp;
   a.rule = c->theta_rule;
   a.t = t;
-  a.ldt = panel_ld(t);
+  a.ldt = panel_ld(t, (int)sizeof(T));
   a.bJ_norm = c->bJ_norm;
   a.yout = (T*)yout;
   a.qoi = (T*)qoi;
   a.flags = flags;
   a.rho = rho;
+  return smem;
+}
+
+template <typename T>
+static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                                  void* qoi, uint32_t* flags, double* rho, cudaStream_t st,
+                                  const void* Mg) {
+  LsPlainArgs<T> a;
+  const size_t smem = fill_plain_args<T>(c, params, m, yout, qoi, flags, rho, Mg, a);
+  if (smem == 0) return cudaErrorInvalidConfiguration;
   const int v = c->ls_variant_plain % kNumLsShapes;
   void (*kern)(LsPlainArgs<T>) = nullptr;
   switch (v) {
@@ -389,9 +412,12 @@ __device__ inline float tf32_round(float x) {
 //     float32, y += delta, until ||delta|| <= tol ||y|| or a step no longer
 //     halves the correction; the last residual evaluated belongs to the
 //     returned y, so rho is exact in float64.
+// One parameter q of the mixed solve (shared by the grid-stride and the
+// persistent multi-problem kernels).
 template <typename TH, typename TL, int NT, int G>
-__global__ void __launch_bounds__(NT, 512 / NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int64_t q,
+                                              unsigned char* smem_raw, double* ctl) {
+
   const int s = a.s, r = a.r, ldt = a.ldt, K = a.K;
   TH* th = reinterpret_cast<TH*>(smem_raw);      // kMaxDp
   TH* y = th + kMaxDp;                           // kMaxR
@@ -405,10 +431,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) ls_mixed_affine_kernel(LsMixedAr
   TL* P = reinterpret_cast<TL*>(nrm2 + 4);       // ldt x (r+1)
   TH* M64 = reinterpret_cast<TH*>(
       (reinterpret_cast<uintptr_t>(P + (size_t)ldt * (r + 1)) + 15) & ~(uintptr_t)15);  // s x r
-  __shared__ double ctl[2];  // refinement control: stop flag, last relative correction
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) {
+
     if (tid < K) {
       th[tid] = theta_k<TH>(a.rule, tid, a.params + q * a.dp);
       th32[tid] = to_lo(th[tid]);
@@ -578,6 +603,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) ls_mixed_affine_kernel(LsMixedAr
     }
     __syncthreads();
   }
+
+template <typename TH, typename TL, int NT, int G>
+__global__ void __launch_bounds__(NT, 512 / NT) ls_mixed_affine_kernel(LsMixedArgs<TH, TL> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double ctl[2];  // refinement control: stop flag, last relative correction
+  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) ls_mixed_body<TH, TL, NT, G>(a, q, smem_raw, ctl);
 }
 
 static size_t mixed_base_bytes(const sas_ctx* c) {
@@ -585,7 +616,7 @@ static size_t mixed_base_bytes(const sas_ctx* c) {
   const size_t eh = cplx ? 16 : 8, el = cplx ? 8 : 4;
   size_t b = (size_t)(kMaxDp + kMaxR + kMaxS) * eh + (kLsThreads / 32) * 8;
   b += (size_t)(kMaxDp + 2 * kMaxR) * el + (size_t)kMaxR * 4 + 4 * 4;
-  b += (size_t)panel_ld(c->s) * (c->r + 1) * el;
+  b += (size_t)panel_ld(c->s, (int)el) * (c->r + 1) * el;
   return (b + 15) / 16 * 16 + 16;
 }
 
@@ -603,12 +634,11 @@ size_t ls_mixed_smem_bytes(const sas_ctx* c) {
 }
 
 template <typename TH, typename TL>
-static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
-                                  void* qoi, float* ysplit, uint32_t* flags, double* rho,
-                                  cudaStream_t st, const void* Mg) {
+static size_t fill_mixed_args(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                              void* qoi, float* ysplit, uint32_t* flags, double* rho,
+                              const void* Mg, LsMixedArgs<TH, TL>& a) {
   const size_t smem = ls_mixed_smem_bytes(c);
-  if (smem > kSmemLimit) return cudaErrorInvalidConfiguration;
-  LsMixedArgs<TH, TL> a;
+  if (smem > kSmemLimit) return 0;
   a.Mg = (const TH*)Mg;
   a.G = (const TH*)c->G;
   a.G32 = (const TL*)c->G32;
@@ -622,7 +652,7 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
   a.K = c->K;
   a.dp = c->dp;
   a.rule = c->theta_rule;
-  a.ldt = panel_ld(c->s);
+  a.ldt = panel_ld(c->s, (int)sizeof(TL));
   a.rpad = (c->r + 31) / 32 * 32;
   a.max_refine = c->max_refine;
   a.keep64 = mixed_keep64(c) ? 1 : 0;
@@ -633,6 +663,16 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
   a.ysplit = ysplit;
   a.flags = flags;
   a.rho = rho;
+  return smem;
+}
+
+template <typename TH, typename TL>
+static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
+                                  void* qoi, float* ysplit, uint32_t* flags, double* rho,
+                                  cudaStream_t st, const void* Mg) {
+  LsMixedArgs<TH, TL> a;
+  const size_t smem = fill_mixed_args<TH, TL>(c, params, m, yout, qoi, ysplit, flags, rho, Mg, a);
+  if (smem == 0) return cudaErrorInvalidConfiguration;
   const int v = c->ls_variant_mixed % kNumLsShapes;
   void (*kern)(LsMixedArgs<TH, TL>) = nullptr;
   switch (v) {
@@ -662,6 +702,154 @@ cudaError_t launch_ls_mixed(const sas_ctx* c, const double* params, int64_t m, v
   if (c->dtype == SAS_COMPLEX128)
     return launch_mixed_t<zd, zf>(c, params, m, yout, qoi, nullptr, flags, rho, st, Mg);
   return launch_mixed_t<double, float>(c, params, m, yout, qoi, ysplit, flags, rho, st, Mg);
+}
+
+// ------------------------------------------ persistent multi-problem launch
+// One launch drains a task list spanning several contexts whose (s, r, K)
+// differ: task t belongs to problem p with offs[p] <= t < offs[p+1]; CTAs take
+// tasks from a global counter, so uneven problems balance across the SMs.  The
+// per-task work is the same body the single-problem kernels run.
+template <typename T, int NT, int G>
+__global__ void __launch_bounds__(NT, 512 / NT) ls_plain_multi_kernel(const LsPlainArgs<T>* probs,
+                                                                      const int64_t* offs, int nprob,
+                                                                      unsigned long long* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double nrm2[2];
+  __shared__ long long task;
+  const int64_t total = offs[nprob];
+  while (true) {
+    if (threadIdx.x == 0) task = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t t = task;
+    if (t >= total) break;
+    int p = 0;
+    while (offs[p + 1] <= t) ++p;
+    ls_plain_body<T, NT, G>(probs[p], t - offs[p], smem_raw, nrm2);
+    __syncthreads();
+  }
+}
+
+template <typename TH, typename TL, int NT, int G>
+__global__ void __launch_bounds__(NT, 512 / NT) ls_mixed_multi_kernel(
+    const LsMixedArgs<TH, TL>* probs, const int64_t* offs, int nprob, unsigned long long* counter) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double ctl[2];
+  __shared__ long long task;
+  const int64_t total = offs[nprob];
+  while (true) {
+    if (threadIdx.x == 0) task = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t t = task;
+    if (t >= total) break;
+    int p = 0;
+    while (offs[p + 1] <= t) ++p;
+    ls_mixed_body<TH, TL, NT, G>(probs[p], t - offs[p], smem_raw, ctl);
+    __syncthreads();
+  }
+}
+
+template <typename A>
+static cudaError_t upload(const std::vector<A>& h, void** d) {
+  cudaError_t e = cudaMalloc(d, sizeof(A) * h.size());
+  if (e == cudaSuccess) e = cudaMemcpy(*d, h.data(), sizeof(A) * h.size(), cudaMemcpyHostToDevice);
+  return e;
+}
+
+template <typename T>
+static cudaError_t plan_plain(MultiPlan* pl, sas_ctx* const* ctxs, int n, const double* const* params,
+                              const int64_t* m, int32_t out_kind, void* const* outs,
+                              uint32_t* const* flags, double* const* rho) {
+  std::vector<LsPlainArgs<T>> a(n);
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t sm = fill_plain_args<T>(ctxs[i], params[i], m[i], out_kind == SAS_OUT_Y ? outs[i] : nullptr,
+                                         out_kind == SAS_OUT_QOI ? outs[i] : nullptr,
+                                         flags ? flags[i] : nullptr, rho ? rho[i] : nullptr, nullptr, a[i]);
+    if (sm == 0) return cudaErrorInvalidConfiguration;
+    smem = sm > smem ? sm : smem;
+  }
+  const int v = ctxs[0]->ls_variant_plain % kNumLsShapes;
+  void (*k)(const LsPlainArgs<T>*, const int64_t*, int, unsigned long long*) = nullptr;
+  switch (v) {
+    case 0: k = ls_plain_multi_kernel<T, 256, 4>; break;
+    case 1: k = ls_plain_multi_kernel<T, 128, 4>; break;
+    case 2: k = ls_plain_multi_kernel<T, 256, 8>; break;
+    case 3: k = ls_plain_multi_kernel<T, 128, 2>; break;
+    default: k = ls_plain_multi_kernel<T, 256, 2>; break;
+  }
+  pl->kernel = (const void*)k;
+  pl->nt = kLsShapes[v].nt;
+  pl->smem = smem;
+  return upload(a, &pl->d_probs);
+}
+
+template <typename TH, typename TL>
+static cudaError_t plan_mixed(MultiPlan* pl, sas_ctx* const* ctxs, int n, const double* const* params,
+                              const int64_t* m, int32_t out_kind, void* const* outs,
+                              uint32_t* const* flags, double* const* rho) {
+  std::vector<LsMixedArgs<TH, TL>> a(n);
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t sm = fill_mixed_args<TH, TL>(ctxs[i], params[i], m[i],
+                                              out_kind == SAS_OUT_Y ? outs[i] : nullptr,
+                                              out_kind == SAS_OUT_QOI ? outs[i] : nullptr, nullptr,
+                                              flags ? flags[i] : nullptr, rho ? rho[i] : nullptr,
+                                              nullptr, a[i]);
+    if (sm == 0) return cudaErrorInvalidConfiguration;
+    smem = sm > smem ? sm : smem;
+  }
+  const int v = ctxs[0]->ls_variant_mixed % kNumLsShapes;
+  void (*k)(const LsMixedArgs<TH, TL>*, const int64_t*, int, unsigned long long*) = nullptr;
+  switch (v) {
+    case 0: k = ls_mixed_multi_kernel<TH, TL, 256, 4>; break;
+    case 1: k = ls_mixed_multi_kernel<TH, TL, 128, 4>; break;
+    case 2: k = ls_mixed_multi_kernel<TH, TL, 256, 8>; break;
+    case 3: k = ls_mixed_multi_kernel<TH, TL, 128, 2>; break;
+    default: k = ls_mixed_multi_kernel<TH, TL, 256, 2>; break;
+  }
+  pl->kernel = (const void*)k;
+  pl->nt = kLsShapes[v].nt;
+  pl->smem = smem;
+  return upload(a, &pl->d_probs);
+}
+
+cudaError_t multi_plan_build(MultiPlan* pl, sas_ctx* const* ctxs, int n, const double* const* params,
+                             const int64_t* m, int32_t out_kind, void* const* outs,
+                             uint32_t* const* flags, double* const* rho) {
+  const bool mixed = ctxs[0]->mode == SAS_MODE_MIXED;
+  const bool cplx = ctxs[0]->dtype == SAS_COMPLEX128;
+  cudaError_t e;
+  if (mixed)
+    e = cplx ? plan_mixed<zd, zf>(pl, ctxs, n, params, m, out_kind, outs, flags, rho)
+             : plan_mixed<double, float>(pl, ctxs, n, params, m, out_kind, outs, flags, rho);
+  else
+    e = cplx ? plan_plain<zd>(pl, ctxs, n, params, m, out_kind, outs, flags, rho)
+             : plan_plain<double>(pl, ctxs, n, params, m, out_kind, outs, flags, rho);
+  if (e != cudaSuccess) return e;
+  std::vector<int64_t> offs(n + 1, 0);
+  for (int i = 0; i < n; ++i) offs[i + 1] = offs[i] + m[i];
+  pl->total = offs[n];
+  e = upload(offs, (void**)&pl->d_offs);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&pl->d_counter, sizeof(unsigned long long));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(pl->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl->kernel, pl->nt, pl->smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)ctxs[0]->num_sms * per_sm;
+  if (grid > pl->total) grid = pl->total;
+  pl->grid = (int)grid;
+  pl->nprob = n;
+  return cudaSuccess;
+}
+
+cudaError_t multi_plan_enqueue(MultiPlan* pl, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(pl->d_counter, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess || pl->total == 0) return e;
+  void* args[] = {(void*)&pl->d_probs, (void*)&pl->d_offs, (void*)&pl->nprob, (void*)&pl->d_counter};
+  return cudaLaunchKernel(pl->kernel, dim3(pl->grid), dim3(pl->nt), args, pl->smem, st);
 }
 
 // ------------------------------------------------- subsampled residual

@@ -70,13 +70,13 @@ __device__ inline bool mbar_try(uint32_t bar, uint32_t parity) {
 
 // Bounded wait: true when the phase completed, false on timeout or abort.
 __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                 int* status) {
+                                 int* status, unsigned long long limit_ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kWaitNs) {
+    if (globaltimer() - t0 > limit_ns) {
       *abort_flag = 1;
       atomicExch(status, (int)SAS_ETIMEOUT);
       return false;
@@ -408,7 +408,28 @@ static bool make_out_map(CUtensorMap* map, float* base, int64_t n, int64_t m) {
   return r == CUDA_SUCCESS;
 }
 
+// Self-test of the bounded wait: one warp waits on an mbarrier that nothing
+// arrives on; the wait must give up after limit_ns, record SAS_ETIMEOUT in
+// *status and return.
+__global__ void wait_selftest_kernel(int* status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ volatile int abort_flag;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(smem_u32(&bar), 0, &abort_flag, status, limit_ns);
+  if (threadIdx.x == 0 && ok) atomicExch(status, -1);  // a phase completed that nothing drove
+}
+
 }  // namespace tc
+
+cudaError_t launch_wait_selftest(int* status, double seconds, cudaStream_t st) {
+  tc::wait_selftest_kernel<<<1, 32, 0, st>>>(status, (unsigned long long)(seconds * 1e9));
+  return cudaGetLastError();
+}
 
 size_t reconstruct_tc_smem_bytes(int rpad) {
   const size_t op = (size_t)(rpad / 32) * tc::kBoxBytes;

@@ -306,7 +306,7 @@ def transfer_basis_torch(prob, device="cuda", **kw):
 # one sigma sharing every kernel product.
 # ---------------------------------------------------------------------------
 
-def kernel_ridge_cg(prob, X, sigma, lams, iters=40, block=16384):
+def kernel_ridge_cg(prob, X, sigma, lams, iters=40, block=8192):
     """CG for (K_sigma + lambda_j I) x_j = y, all lambda_j at once.
 
     The kernel product is formed block by block in float32, so the snapshots
