@@ -290,7 +290,9 @@ struct LsShape {
 static const LsShape kLsShapes[] = {{256, 4}, {128, 4}, {256, 8}, {128, 2}, {256, 2}};
 constexpr int kNumLsShapes = sizeof(kLsShapes) / sizeof(kLsShapes[0]);
 
-int ls_num_variants(bool mixed) { return mixed ? 2 * kNumLsShapes : kNumLsShapes; }
+// plain: the smem shapes, then one register-resident variant; mixed: the smem
+// shapes with and without the float64 M, then two register-resident variants
+int ls_num_variants(bool mixed) { return mixed ? 2 * kNumLsShapes + 2 : kNumLsShapes + 1; }
 
 size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block) {
   const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
@@ -346,6 +348,10 @@ static cudaError_t launch_plain_t(const sas_ctx* c, const double* params, int64_
   LsPlainArgs<T> a;
   const size_t smem = fill_plain_args<T>(c, params, m, yout, qoi, flags, rho, Mg, a);
   if (smem == 0) return cudaErrorInvalidConfiguration;
+  if (c->ls_variant_plain >= kNumLsShapes) {
+    if constexpr (sizeof(T) == 8) return launch_plain_reg(c, a, m, st);
+    return cudaErrorInvalidConfiguration;
+  }
   const int v = c->ls_variant_plain % kNumLsShapes;
   void (*kern)(LsPlainArgs<T>) = nullptr;
   switch (v) {
@@ -673,6 +679,11 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
   LsMixedArgs<TH, TL> a;
   const size_t smem = fill_mixed_args<TH, TL>(c, params, m, yout, qoi, ysplit, flags, rho, Mg, a);
   if (smem == 0) return cudaErrorInvalidConfiguration;
+  if (c->ls_variant_mixed >= 2 * kNumLsShapes) {
+    if constexpr (sizeof(TH) == 8)
+      return launch_mixed_reg(c, a, m, c->ls_variant_mixed - 2 * kNumLsShapes, st);
+    return cudaErrorInvalidConfiguration;
+  }
   const int v = c->ls_variant_mixed % kNumLsShapes;
   void (*kern)(LsMixedArgs<TH, TL>) = nullptr;
   switch (v) {
@@ -702,6 +713,391 @@ cudaError_t launch_ls_mixed(const sas_ctx* c, const double* params, int64_t m, v
   if (c->dtype == SAS_COMPLEX128)
     return launch_mixed_t<zd, zf>(c, params, m, yout, qoi, nullptr, flags, rho, st, Mg);
   return launch_mixed_t<double, float>(c, params, m, yout, qoi, ysplit, flags, rho, st, Mg);
+}
+
+// --------------------------------------------- register-resident variants
+// Householder with static column ownership: the G lanes of slot q own the
+// columns j = q, q + NSLOT, ... (up to CPS of them) for the whole
+// factorisation, lane g the rows g, g + G, ... (up to RPT) of each, in
+// registers.  Step k: the owner of column k writes that column (rows >= k) to
+// V[:, k] in shared memory, computes the reflector from it, replaces V[k, k]
+// by v0 and writes R's column k; after one barrier every slot applies
+// H_k = I - tau v v^H to its own columns from V[:, k].  V[:, k] is never
+// overwritten, so one barrier per step suffices, and V is the stored Q of
+// the mixed refinement.
+template <typename TF, typename RF, int NT, int G, int RPT, int CPS>
+__device__ inline void reg_householder(TF (&m)[CPS][RPT], int s, int r, TF* V, int ldv, RF* taus,
+                                       TF* Rs, int ldr, TF* zs, RF* res2) {
+  constexpr int NSLOT = NT / G;
+  const int tid = threadIdx.x, g = tid % G, slot = tid / G;
+  const unsigned gmask = ((1u << G) - 1u) << ((tid & 31) & ~(G - 1));
+  for (int k = 0; k < r; ++k) {
+    const int owner = k % NSLOT, ck = k / NSLOT;
+    if (slot == owner) {
+      RF part = RF(0);
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const int i = g + G * u;
+        const TF val = ck == 0 ? m[0][u] : m[CPS > 1 ? 1 : 0][u];
+        if (i >= k && i < s) V[i + (size_t)k * ldv] = val;
+        if (i > k && i < s) part += absq(val);
+        if (i < k) Rs[i + (size_t)k * ldr] = val;  // rows above k are final
+      }
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) part += shfl_xor_m(gmask, part, o);
+      __syncwarp(gmask);
+      const TF alpha = V[k + (size_t)k * ldv];
+      const RF a2 = absq(alpha);
+      const RF nrm = sqrt(a2 + part);
+      const RF aa = sqrt(a2);
+      const TF beta = rscale(-nrm, phase(alpha));
+      __syncwarp(gmask);
+      if (g == 0) {
+        V[k + (size_t)k * ldv] = alpha - beta;  // v0
+        taus[k] = nrm > RF(0) ? RF(1) / (nrm * (nrm + aa)) : RF(0);
+        Rs[k + (size_t)k * ldr] = beta;
+      }
+    }
+    __syncthreads();
+    const RF tau = taus[k];
+#pragma unroll
+    for (int c = 0; c < CPS; ++c) {
+      const int j = slot + c * NSLOT;
+      if (j > k && j <= r) {
+        TF w = zero<TF>();
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+          const int i = g + G * u;
+          if (i >= k && i < s) w += conjv(V[i + (size_t)k * ldv]) * m[c][u];
+        }
+#pragma unroll
+        for (int o = 1; o < G; o <<= 1) w += shfl_xor_m(gmask, w, o);
+        const TF tw = rscale(tau, w);
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+          const int i = g + G * u;
+          if (i >= k && i < s) m[c][u] -= tw * V[i + (size_t)k * ldv];
+        }
+      }
+    }
+  }
+  // right-hand side column r: z = rows 0..r-1, residual = rows r..s-1
+  {
+    const int owner = r % NSLOT, cr = r / NSLOT;
+    if (slot == owner) {
+      RF part = RF(0);
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const int i = g + G * u;
+        const TF val = cr == 0 ? m[0][u] : m[CPS > 1 ? 1 : 0][u];
+        if (i < r) zs[i] = val;
+        else if (i < s) part += absq(val);
+      }
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) part += shfl_xor_m(gmask, part, o);
+      if (g == 0) *res2 = part;
+    }
+  }
+  __syncthreads();
+}
+
+template <int NT, int G, int RPT, int CPS>
+struct RegShape {
+  static constexpr int nt = NT, g = G, rpt = RPT, cps = CPS;
+  static bool fits(int s, int r) { return s <= G * RPT && r + 1 <= (NT / G) * CPS; }
+};
+
+// Plain float64, register-resident: same outputs as ls_plain_body.
+template <int NT, int G, int RPT, int CPS>
+__global__ void __launch_bounds__(NT, 1) ls_plain_reg_kernel(LsPlainArgs<double> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NSLOT = NT / G;
+  const int s = a.s, r = a.r, K = a.K;
+  const int ldv = s | 1;  // odd stride: the 32 lanes of a column read distinct banks
+  double* V = reinterpret_cast<double*>(smem_raw);          // ldv x r
+  double* Rs = V + (size_t)ldv * r;                         // r x r (ld r)
+  double* zs = Rs + (size_t)r * r;                          // r
+  double* taus = zs + kMaxR;                                // r
+  double* th = taus + kMaxR;                                // K
+  double* ys = th + kMaxDp;                                 // r
+  __shared__ double res2;
+  const int tid = threadIdx.x, g = tid % G, slot = tid / G, warp = tid >> 5;
+  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) {
+    if (tid < K) th[tid] = theta_k<double>(a.rule, tid, a.params + q * a.dp);
+    __syncthreads();
+    double m[CPS][RPT];
+#pragma unroll
+    for (int c = 0; c < CPS; ++c) {
+      const int j = slot + c * NSLOT;
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const int i = g + G * u;
+        double v = 0.0;
+        if (i < s && j < r) {
+          if (a.Mg) {
+            v = a.Mg[(size_t)q * s * r + (size_t)j * s + i];
+          } else {
+            const double* gp = a.G + (size_t)j * s + i;
+            for (int k = 0; k < K; ++k) v += th[k] * gp[(size_t)k * s * r];
+          }
+        } else if (i < s && j == r) {
+          v = a.bJ[i];
+        }
+        m[c][u] = v;
+      }
+    }
+    reg_householder<double, double, NT, G, RPT, CPS>(m, s, r, V, ldv, taus, Rs, r, zs, &res2);
+    if (warp == 0) {
+      double zr[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = (tid & 31) + 32 * c;
+        zr[c] = i < r ? zs[i] : 0.0;
+      }
+      double dmin, dmax;
+      backsolve_warp<double, double>(Rs, r, r, zr, ys, dmin, dmax);
+      const int lane = tid & 31;
+      bool fin = true;
+      double h = 0.0;
+      for (int i = lane; i < r; i += 32) {
+        const double yi = ys[i];
+        fin = fin && isfinite(yi);
+        if (a.yout) a.yout[q * r + i] = yi;
+        if (a.qoi) h += a.wq[i] * yi;
+      }
+      fin = __all_sync(0xffffffffu, fin);
+      if (a.qoi) {
+        h = warp_sum(h);
+        if (lane == 0) a.qoi[q] = h;
+      }
+      if (lane == 0) {
+        if (a.rho) a.rho[q] = sqrt(res2) / a.bJ_norm;
+        if (a.flags) {
+          uint32_t f = 0;
+          if (!(dmin > 1e-13 * dmax)) f |= SAS_FLAG_ILLCOND;
+          if (!fin) f |= SAS_FLAG_NONFINITE;
+          a.flags[q] = f;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static size_t plain_reg_smem(int s, int r) {
+  return sizeof(double) * ((size_t)(s | 1) * r + (size_t)r * r + 3 * kMaxR + kMaxDp) + 64;
+}
+
+// Mixed, register-resident: float32 factorisation in registers, V and R in
+// shared memory, refinement exactly as ls_mixed_body.
+template <int NT, int G, int RPT, int CPS>
+__global__ void __launch_bounds__(NT, 1) ls_mixed_reg_kernel(LsMixedArgs<double, float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int NSLOT = NT / G;
+  const int s = a.s, r = a.r, K = a.K;
+  const int ldv = s | 1;
+  double* th = reinterpret_cast<double*>(smem_raw);   // kMaxDp
+  double* y = th + kMaxDp;                            // kMaxR
+  double* res = y + kMaxR;                            // kMaxS
+  double* red = res + kMaxS;                          // 8
+  float* V = reinterpret_cast<float*>(red + 8);       // ldv x r
+  float* Rs = V + (size_t)ldv * r;                    // r x r
+  float* zs = Rs + (size_t)r * r;                     // kMaxS (also the correction rhs)
+  float* taus = zs + kMaxS;                           // kMaxR
+  float* dl = taus + kMaxR;                           // kMaxR
+  float* th32 = dl + kMaxR;                           // kMaxDp
+  __shared__ float res2f;
+  __shared__ double ctl[2];
+  const int tid = threadIdx.x, g = tid % G, slot = tid / G, lane = tid & 31, warp = tid >> 5;
+  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x) {
+    if (tid < K) {
+      th[tid] = theta_k<double>(a.rule, tid, a.params + q * a.dp);
+      th32[tid] = (float)th[tid];
+    }
+    __syncthreads();
+    float m[CPS][RPT];
+#pragma unroll
+    for (int c = 0; c < CPS; ++c) {
+      const int j = slot + c * NSLOT;
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const int i = g + G * u;
+        float v = 0.f;
+        if (i < s && j < r) {
+          if (a.Mg) {
+            v = (float)a.Mg[(size_t)q * s * r + (size_t)j * s + i];
+          } else {
+            const float* gp = a.G32 + (size_t)j * s + i;
+            for (int k = 0; k < K; ++k) v += th32[k] * gp[(size_t)k * s * r];
+          }
+        } else if (i < s && j == r) {
+          v = a.bJ32[i];
+        }
+        m[c][u] = v;
+      }
+    }
+    reg_householder<float, float, NT, G, RPT, CPS>(m, s, r, V, ldv, taus, Rs, r, zs, &res2f);
+    float dmin = 0.f, dmax = 0.f;
+    if (warp == 0) {
+      float zr[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = lane + 32 * c;
+        zr[c] = i < r ? zs[i] : 0.f;
+      }
+      backsolve_warp<float, float>(Rs, r, r, zr, dl, dmin, dmax);
+      for (int i = lane; i < r; i += 32) y[i] = (double)dl[i];
+    }
+    __syncthreads();
+    double rn2 = 0.0;
+    bool converged = false;
+    double last_rel = 1.0;
+    if (tid == 0) ctl[1] = 1.0;
+    __syncthreads();
+    for (int it = 0;; ++it) {
+      double part = 0.0;
+      for (int i = tid; i < s; i += NT) {
+        double acc = 0.0;
+        if (a.Mg) {
+          const double* mrow = a.Mg + (size_t)q * s * r + i;
+          for (int j = 0; j < r; ++j) acc += mrow[(size_t)j * s] * y[j];
+        } else {
+          for (int k = 0; k < K; ++k) {
+            const double* gp = a.G + (size_t)k * s * r + i;
+            double mk = 0.0;
+            for (int j = 0; j < r; ++j) mk += gp[(size_t)j * s] * y[j];
+            acc += th[k] * mk;
+          }
+        }
+        const double ri = a.bJ[i] - acc;
+        res[i] = ri;
+        part += ri * ri;
+      }
+      rn2 = block_sum<NT>(part, red);
+      if (converged || it >= a.max_refine) break;
+      if (warp == 0) {
+        for (int i = lane; i < s; i += 32) zs[i] = (float)res[i];
+        __syncwarp();
+        for (int k = 0; k < r; ++k) {
+          const float* vk = V + (size_t)k * ldv;  // rows k..s-1 (v0 at row k)
+          float w = 0.f;
+          for (int i = k + lane; i < s; i += 32) w += vk[i] * zs[i];
+          w = warp_sum(w);
+          const float tw = taus[k] * w;
+          __syncwarp();
+          for (int i = k + lane; i < s; i += 32) zs[i] -= tw * vk[i];
+          __syncwarp();
+        }
+        float zr[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int i = lane + 32 * c;
+          zr[c] = i < r ? zs[i] : 0.f;
+        }
+        float d0, d1;
+        backsolve_warp<float, float>(Rs, r, r, zr, dl, d0, d1);
+        double dn = 0.0, yn = 0.0;
+        for (int i = lane; i < r; i += 32) {
+          const double di = (double)dl[i];
+          y[i] += di;
+          dn += di * di;
+          yn += y[i] * y[i];
+        }
+        dn = warp_sum(dn);
+        yn = warp_sum(yn);
+        if (lane == 0) {
+          const double rel = sqrt(dn / yn);
+          ctl[0] = (rel <= a.tol || rel > 0.5 * ctl[1]) ? 1.0 : 0.0;
+          ctl[1] = rel;
+        }
+      }
+      __syncthreads();
+      converged = ctl[0] != 0.0;
+      last_rel = ctl[1];
+      __syncthreads();
+    }
+    if (warp == 0) {
+      bool fin = true;
+      double h = 0.0;
+      for (int i = lane; i < r; i += 32) {
+        const double yi = y[i];
+        fin = fin && isfinite(yi);
+        if (a.yout) a.yout[q * r + i] = yi;
+        if (a.qoi) h += a.wq[i] * yi;
+      }
+      fin = __all_sync(0xffffffffu, fin);
+      if (a.qoi) {
+        h = warp_sum(h);
+        if (lane == 0) a.qoi[q] = h;
+      }
+      if (lane == 0) {
+        if (a.rho) a.rho[q] = sqrt(rn2) / a.bJ_norm;
+        if (a.flags) {
+          uint32_t f = 0;
+          if (!(dmin > 1e-6f * dmax)) f |= SAS_FLAG_ILLCOND;
+          if (!fin) f |= SAS_FLAG_NONFINITE;
+          if (!(last_rel <= 1e-8)) f |= SAS_FLAG_REFINE_STALL;
+          a.flags[q] = f;
+        }
+      }
+    }
+    if (a.ysplit) {
+      for (int i = tid; i < a.rpad; i += NT) {
+        float hi = 0.f, lo = 0.f;
+        if (i < r) {
+          const float yf = (float)y[i];
+          hi = tf32_round(yf);
+          lo = yf - hi;
+        }
+        a.ysplit[(size_t)q * a.rpad + i] = hi;
+        a.ysplit[(size_t)a.m * a.rpad + (size_t)q * a.rpad + i] = lo;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+static size_t mixed_reg_smem(int s, int r) {
+  return sizeof(double) * (kMaxDp + kMaxR + kMaxS + 8) +
+         sizeof(float) * ((size_t)(s | 1) * r + (size_t)r * r + kMaxS + 2 * kMaxR + kMaxDp) + 64;
+}
+
+template <typename K, typename A>
+static cudaError_t launch_persistent(K kern, int nt, size_t smem, const sas_ctx* c, int64_t m, A a,
+                                     cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int64_t grid = (int64_t)c->num_sms * per_sm;
+  if (grid > m) grid = m;
+  kern<<<(unsigned)grid, nt, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Register variants: plain (256 threads, 8 lanes per column, 16 rows, 2 columns);
+// mixed (128 x 4 x 32 x 2) and (256 x 4 x 32 x 1).
+static cudaError_t launch_plain_reg(const sas_ctx* c, const LsPlainArgs<double>& a, int64_t m,
+                                    cudaStream_t st) {
+  using Sh = RegShape<256, 8, 16, 2>;
+  if (!Sh::fits(c->s, c->r)) return cudaErrorInvalidConfiguration;
+  return launch_persistent(ls_plain_reg_kernel<256, 8, 16, 2>, Sh::nt, plain_reg_smem(c->s, c->r),
+                           c, m, a, st);
+}
+
+static cudaError_t launch_mixed_reg(const sas_ctx* c, const LsMixedArgs<double, float>& a, int64_t m,
+                                    int which, cudaStream_t st) {
+  const size_t smem = mixed_reg_smem(c->s, c->r);
+  if (which == 0) {
+    using Sh = RegShape<128, 4, 32, 2>;
+    if (!Sh::fits(c->s, c->r)) return cudaErrorInvalidConfiguration;
+    return launch_persistent(ls_mixed_reg_kernel<128, 4, 32, 2>, Sh::nt, smem, c, m, a, st);
+  }
+  using Sh = RegShape<256, 4, 32, 1>;
+  if (!Sh::fits(c->s, c->r)) return cudaErrorInvalidConfiguration;
+  return launch_persistent(ls_mixed_reg_kernel<256, 4, 32, 1>, Sh::nt, smem, c, m, a, st);
 }
 
 // ------------------------------------------ persistent multi-problem launch

@@ -252,7 +252,7 @@ def test_every_ls_variant_and_autotune(c1_small, mode):
     p = case.prob
     params = p.test_params[:100]
     Yo, rho_o = case.oracle_solve(params)
-    nvar = 5 if mode == api.SAS_MODE_PLAIN else 10
+    nvar = 6 if mode == api.SAS_MODE_PLAIN else 12  # shared-memory and register-resident shapes
     P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
     solver = AffineSolver(p, case.S, case.J, mode=mode, device=DEV)
     bound = _mixed_bound(p, case.S, case.J, params, Yo, rho_o)
@@ -289,3 +289,30 @@ def test_blocked_householder_path_complex():
     case = Case("transfer_function", basis="random", N=9, r=80, s=200, m=40)
     err, kap = plain_parity(case)
     print(f"blocked complex path: max rel err {err.max():.2e}, kappa max {kap.max():.2e}")
+
+
+@pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED])
+def test_register_variants_on_c0_and_multichunk(c0, mode):
+    """The register-resident shapes on the 1-D workload (s = 40, r = 20): ragged row
+    ownership (40 rows over 4 or 8 lanes) and unused column slots."""
+    p = c0.prob
+    params = p.test_params[:300]
+    Yo, rho_o = c0.oracle_solve(params)
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
+    solver = AffineSolver(p, c0.S, c0.J, mode=mode, device=DEV)
+    variants = [5] if mode == api.SAS_MODE_PLAIN else [10, 11]
+    bound = _mixed_bound(p, c0.S, c0.J, params, Yo, rho_o)
+    kap = c0.kappas(params)
+    for v in variants:
+        api.subapsnap_set_option(solver.ctx, api.SAS_OPT_LS_VARIANT, v)
+        Y = torch.empty((len(params), p.r), dtype=torch.float64, device=DEV)
+        rho = torch.empty(len(params), dtype=torch.float64, device=DEV)
+        solver.solve(P, api.SAS_OUT_Y, Y, None, rho)
+        torch.cuda.synchronize()
+        err = rel_err_rows(Y.cpu().numpy(), Yo)
+        if mode == api.SAS_MODE_PLAIN:
+            assert err.max() <= 1e-10, (v, err.max())
+        else:
+            assert (err <= bound).all(), (v, err.max())
+        assert (np.abs(rho.cpu().numpy() - rho_o) <= 1e-6 * rho_o + 64 * kap * 1.1e-16).all()
+    solver.close()

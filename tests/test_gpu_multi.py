@@ -2,9 +2,10 @@
 
 A multi-problem plan solves three contexts (different n, r, s, K) in one launch,
 optionally replayed from a CUDA graph.  Each parameter runs the same per-task
-solve as subapsnap_solve_batch with the same launch shape, so the outputs must
-be bit-identical to the per-context solves, and those are parity-checked against
-the oracle elsewhere (here: against the oracle as well, at the plain tolerance).
+solve as subapsnap_solve_batch with the same launch shape: plain float64 outputs
+must be bit-identical to the per-context solves; mixed outputs (a float32 body
+the compiler may contract differently in another kernel, then refined to float64
+accuracy) within 1e-9.  Both are also checked against the oracle.
 """
 import numpy as np
 import pytest
@@ -47,7 +48,13 @@ def test_multi_plan_matches_single_solves(cases, mode):
         api.subapsnap_multi_plan_launch(plan, use_graph)
         torch.cuda.synchronize()
         for o, r in zip(outs, ref):
-            assert torch.equal(o, r)
+            if mode == api.SAS_MODE_PLAIN:
+                assert torch.equal(o, r)
+            else:
+                # the float32 body inlined into another kernel may contract differently;
+                # both answers are refined to float64 accuracy of the same system
+                rel = (torch.linalg.vector_norm(o - r, dim=1) / torch.linalg.vector_norm(r, dim=1)).max()
+                assert rel.item() <= 1e-9, rel.item()
     for c, o in zip(cases, outs):
         Yo, _ = c.oracle_solve(c.prob.test_params[:20])
         err = np.linalg.norm(o[:20].cpu().numpy() - Yo, axis=1) / np.linalg.norm(Yo, axis=1)

@@ -314,7 +314,8 @@ def kernel_ridge_cg(prob, X, sigma, lams, iters=40, block=8192):
     """
     import torch
     N = X.shape[0]
-    Xf = X.float()
+    Xc = (X - X.mean(dim=0)).float()  # centring shrinks the norms the expansion subtracts
+    nrm = (Xc * Xc).sum(1)
     lam = torch.as_tensor(np.asarray(lams, dtype=np.float64), device=X.device)
     q = lam.numel()
     y = torch.as_tensor(np.asarray(prob.b, dtype=np.float64), device=X.device)
@@ -324,9 +325,9 @@ def kernel_ridge_cg(prob, X, sigma, lams, iters=40, block=8192):
         out = torch.empty_like(V)
         Vf = V.float()
         for a in range(0, N, block):
-            # squared distances from direct differences (symmetric, no cancellation)
-            D = torch.cdist(Xf[a:a + block], Xf, compute_mode="donot_use_mm_for_euclid_dist")
-            D.square_().mul_(-inv).exp_()
+            # squared distances by the norm expansion on centred float32 points
+            D = (nrm[a:a + block, None] + nrm[None, :] - 2.0 * (Xc[a:a + block] @ Xc.T)).clamp_min_(0.0)
+            D.mul_(-inv).exp_()
             out[a:a + block] = (D @ Vf).double()
         return out
 
