@@ -6,21 +6,25 @@
 // rounded to tf32; the low parts are the float32 remainders, truncated to
 // tf32 by the tensor core).  The dropped S_lo y_lo term and the truncation of
 // the low parts leave ~2^-21 relative error per product: float32-class
-// accuracy at tf32 tensor-core rates.  The kernel is bound by HBM (it writes
-// 4 n bytes per parameter and reads S once per 128-parameter tile pair).
+// accuracy at tf32 tensor-core rates.  The kernel is bound by HBM: it writes
+// 4 n bytes per parameter and reads the split S (8 n rpad bytes) once per
+// launch, however many parameters the launch has.
 //
 // Structure (one persistent CTA per SM, 6 warps):
-//   warp 0    TMA producer: B tiles (y_hi, y_lo of this CTA's 128 parameters)
-//             once, then A tiles (S_hi, S_lo rows) into a 2-stage ring;
-//   warp 1    one thread issues tcgen05.mma (kind::tf32, M=128, N=128, K=8)
-//             into a double-buffered TMEM accumulator (2 x 128 columns);
-//   warps 2-5 epilogue: tcgen05.ld 32 lanes x 32 columns at a time and
-//             streaming stores; each warp owns its TMEM lane quarter.
-// Tiles: M = 128 rows of S, N = 128 parameters, K = rpad (32 or 64) in boxes
-// of 32 floats (128 B rows, 128-byte swizzle).  CTA c handles parameter tile
-// c % ntiles and row tiles c / ntiles, c / ntiles + G / ntiles, ... so that
-// the CTAs sharing a row tile run at the same time and the second read of it
-// comes from L2.
+//   warp 0    TMA producer: for each work unit the S tile (S_hi, S_lo of 128
+//             rows) into a 2-stage buffer, then the unit's y tiles (y_hi, y_lo
+//             of 64 parameters, L2-resident) into a 2-stage ring;
+//   warp 1    one thread issues tcgen05.mma (kind::tf32, M=128, N=64, K=8)
+//             into 4 TMEM accumulators of 64 columns;
+//   warps 2-5 epilogue: tcgen05.ld 32 lanes x 32 columns at a time, staged in
+//             shared memory and written by TMA bulk-tensor stores; each warp
+//             owns its TMEM lane quarter.
+// A work unit is one 128-row tile of S and a range of 64-parameter tiles; the
+// S tile stays resident while the unit's y tiles stream past it.  With at
+// least as many row tiles as SMs a unit covers every parameter tile, so S is
+// read from HBM once; with fewer (small n) the parameter tiles are split into
+// ranges so that every SM has work.  K = rpad (32 or 64) in boxes of 32 floats
+// (128 B rows, 128-byte swizzle).
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel
 // records SAS_ETIMEOUT in the status word, stops issuing work, waits (bounded)
 // for its copies and MMAs in flight, frees its TMEM and returns.
@@ -36,11 +40,14 @@ namespace sas {
 namespace tc {
 
 constexpr int kThreads = 192;
-constexpr int kBM = 128;
-constexpr int kBN = 128;
-constexpr int kBoxBytes = 128 * 128;  // 128 rows x 32 floats
-constexpr int kStages = 2;
-constexpr uint32_t kTmemCols = 256;
+constexpr int kBM = 128;              // rows of S per tile (MMA M)
+constexpr int kBN = 64;               // parameters per tile (MMA N)
+constexpr int kABox = 128 * 128;      // A box: 128 rows x 32 floats (128-byte rows)
+constexpr int kBBox = kBN * 128;      // B box: 64 rows x 32 floats
+constexpr int kAStages = 2;
+constexpr int kBStages = 2;
+constexpr int kAcc = 4;               // TMEM accumulators of kBN columns
+constexpr uint32_t kTmemCols = kAcc * kBN;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
 __device__ inline uint32_t smem_u32(const void* p) {
@@ -185,13 +192,25 @@ struct Params {
   int64_t n;
   int64_t m;
   int kboxes;      // rpad / 32 (1 or 2)
-  int num_mtiles;
-  int num_ntiles;
+  int num_mtiles;  // ceil(n / kBM)
+  int num_ntiles;  // ceil(m / kBN)
+  int ngroups;     // parameter tiles of one row tile are split into ngroups ranges
+  int ntpg;        // parameter tiles per range
+  int num_units;   // num_mtiles * ngroups
   int tma_store;   // 1: epilogue through shared memory and TMA stores
   int* status;
 };
 
 constexpr int kStageFloats = 32 * 32;  // one epilogue staging tile: 32 parameters x 32 rows
+
+// Work unit u: row tile u / ngroups, parameter tiles [g ntpg, min((g+1) ntpg, num_ntiles))
+// with g = u % ngroups.  All three roles walk the same units in the same order.
+__device__ inline void unit_range(const Params& p, int u, int& mt, int& nt0, int& nt1) {
+  mt = u / p.ngroups;
+  const int g = u % p.ngroups;
+  nt0 = g * p.ntpg;
+  nt1 = nt0 + p.ntpg < p.num_ntiles ? nt0 + p.ntpg : p.num_ntiles;
+}
 
 __global__ void __launch_bounds__(kThreads, 1)
     reconstruct_tc_kernel(const __grid_constant__ CUtensorMap tmAhi,
@@ -203,30 +222,33 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   const int kb = p.kboxes;
-  const uint32_t opbytes = (uint32_t)kb * kBoxBytes;  // one operand tile (hi or lo)
-  uint8_t* Bhi = base;
-  uint8_t* Blo = Bhi + opbytes;
-  uint8_t* Abase = Blo + opbytes;  // stage s: hi at Abase + s*2*opbytes, lo right after
-  float* stage = reinterpret_cast<float*>(Abase + (size_t)kStages * 2 * opbytes);  // 4 warps x 2
+  const uint32_t aop = (uint32_t)kb * kABox;  // one S tile (hi or lo)
+  const uint32_t bop = (uint32_t)kb * kBBox;  // one y tile (hi or lo)
+  uint8_t* A0 = base;                                 // stage s: hi at A0 + 2 s aop, lo after it
+  uint8_t* B0 = A0 + (size_t)kAStages * 2 * aop;      // stage s: hi at B0 + 2 s bop, lo after it
+  float* stage = reinterpret_cast<float*>(B0 + (size_t)kBStages * 2 * bop);  // 4 warps x 2
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 8 * kStageFloats);
-  // bars: full[2], empty[2], tfull[2], tempty[2], bbar
+  // bars: afull[2], aempty[2], bfull[2], bempty[2], tfull[4], tempty[4]
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[2]);
-  const uint32_t tfull0 = smem_u32(&bars[4]), tempty0 = smem_u32(&bars[6]);
-  const uint32_t bbar = smem_u32(&bars[8]);
+  const uint32_t afull0 = smem_u32(&bars[0]), aempty0 = smem_u32(&bars[2]);
+  const uint32_t bfull0 = smem_u32(&bars[4]), bempty0 = smem_u32(&bars[6]);
+  const uint32_t tfull0 = smem_u32(&bars[8]), tempty0 = smem_u32(&bars[12]);
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, 1);
-      mbar_init(tfull0 + 8 * s, 1);
-      mbar_init(tempty0 + 8 * s, 4);
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(afull0 + 8 * s, 1);
+      mbar_init(aempty0 + 8 * s, 1);
+      mbar_init(bfull0 + 8 * s, 1);
+      mbar_init(bempty0 + 8 * s, 1);
     }
-    mbar_init(bbar, 1);
+    for (int a = 0; a < kAcc; ++a) {
+      mbar_init(tfull0 + 8 * a, 1);
+      mbar_init(tempty0 + 8 * a, 4);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -241,119 +263,152 @@ __global__ void __launch_bounds__(kThreads, 1)
   fence_after();
   const uint32_t tmem = tmem_slot;
 
-  const int ntile = blockIdx.x % p.num_ntiles;
-  const int first = blockIdx.x / p.num_ntiles;
-  const int step = gridDim.x / p.num_ntiles;
-  const int iters = first < p.num_mtiles ? (p.num_mtiles - first + step - 1) / step : 0;
-
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer
-      mbar_expect_tx(bbar, 2 * opbytes);
-      for (int k = 0; k < kb; ++k) {
-        tma_load_2d(smem_u32(Bhi + k * kBoxBytes), &tmBhi, k * 32, ntile * kBN, bbar);
-        tma_load_2d(smem_u32(Blo + k * kBoxBytes), &tmBlo, k * 32, ntile * kBN, bbar);
-      }
-      int issued[kStages] = {-1, -1};
-      for (int it = 0; it < iters; ++it) {
-        const int s = it & 1;
-        const uint32_t ph = (uint32_t)(it >> 1) & 1u;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, &abort_flag, p.status)) break;
-        const int mt = first + it * step;
-        uint8_t* Ahi = Abase + (size_t)s * 2 * opbytes;
-        uint8_t* Alo = Ahi + opbytes;
-        mbar_expect_tx(full0 + 8 * s, 2 * opbytes);
-        for (int k = 0; k < kb; ++k) {
-          tma_load_2d(smem_u32(Ahi + k * kBoxBytes), &tmAhi, k * 32, mt * kBM, full0 + 8 * s);
-          tma_load_2d(smem_u32(Alo + k * kBoxBytes), &tmAlo, k * 32, mt * kBM, full0 + 8 * s);
+      // ---------------- TMA producer: per unit, the S tile once, then its y tiles
+      int bt = 0, at = 0;
+      int b_issued[kBStages] = {-1, -1}, a_issued[kAStages] = {-1, -1};
+      bool stop = false;
+      for (int u = blockIdx.x; u < p.num_units && !stop; u += gridDim.x) {
+        int mt, nt0, nt1;
+        unit_range(p, u, mt, nt0, nt1);
+        for (int nt = nt0; nt < nt1; ++nt) {
+          const int s = bt & 1;
+          if (!mbar_wait(bempty0 + 8 * s, ((uint32_t)(bt >> 1) & 1u) ^ 1u, &abort_flag, p.status)) {
+            stop = true;
+            break;
+          }
+          uint8_t* Bhi = B0 + (size_t)s * 2 * bop;
+          mbar_expect_tx(bfull0 + 8 * s, 2 * bop);
+          for (int k = 0; k < kb; ++k) {
+            tma_load_2d(smem_u32(Bhi + k * kBBox), &tmBhi, k * 32, nt * kBN, bfull0 + 8 * s);
+            tma_load_2d(smem_u32(Bhi + bop + k * kBBox), &tmBlo, k * 32, nt * kBN, bfull0 + 8 * s);
+          }
+          b_issued[s] = bt++;
+          if (nt == nt0) {
+            // the S tile: its stage frees when the last MMA of the unit two back completes
+            const int sa = at & 1;
+            if (!mbar_wait(aempty0 + 8 * sa, ((uint32_t)(at >> 1) & 1u) ^ 1u, &abort_flag,
+                           p.status)) {
+              stop = true;
+              break;
+            }
+            uint8_t* Ahi = A0 + (size_t)sa * 2 * aop;
+            mbar_expect_tx(afull0 + 8 * sa, 2 * aop);
+            for (int k = 0; k < kb; ++k) {
+              tma_load_2d(smem_u32(Ahi + k * kABox), &tmAhi, k * 32, mt * kBM, afull0 + 8 * sa);
+              tma_load_2d(smem_u32(Ahi + aop + k * kABox), &tmAlo, k * 32, mt * kBM,
+                          afull0 + 8 * sa);
+            }
+            a_issued[sa] = at++;
+          }
         }
-        issued[s] = it;
       }
       if (abort_flag) {
-        // drain: wait for the copies in flight of every stage and for B
-        for (int s = 0; s < kStages; ++s)
-          if (issued[s] >= 0) mbar_drain(full0 + 8 * s, (uint32_t)(issued[s] >> 1) & 1u);
-        mbar_drain(bbar, 0);
+        // drain: wait for the copies in flight of every stage
+        for (int s = 0; s < kBStages; ++s)
+          if (b_issued[s] >= 0) mbar_drain(bfull0 + 8 * s, (uint32_t)(b_issued[s] >> 1) & 1u);
+        for (int s = 0; s < kAStages; ++s)
+          if (a_issued[s] >= 0) mbar_drain(afull0 + 8 * s, (uint32_t)(a_issued[s] >> 1) & 1u);
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer
-      int last = -1;
-      if (mbar_wait(bbar, 0, &abort_flag, p.status)) {
-        for (int it = 0; it < iters; ++it) {
-          const int s = it & 1, acc = it & 1;
-          const uint32_t ph = (uint32_t)(it >> 1) & 1u;
-          if (!mbar_wait(full0 + 8 * s, ph, &abort_flag, p.status)) break;
-          if (!mbar_wait(tempty0 + 8 * acc, ph ^ 1u, &abort_flag, p.status)) break;
+      int t = 0, ua = 0, last = -1;
+      bool stop = false;
+      for (int u = blockIdx.x; u < p.num_units && !stop; u += gridDim.x) {
+        int mt, nt0, nt1;
+        unit_range(p, u, mt, nt0, nt1);
+        if (nt0 >= nt1) continue;
+        const int sa = ua & 1;
+        if (!mbar_wait(afull0 + 8 * sa, (uint32_t)(ua >> 1) & 1u, &abort_flag, p.status)) break;
+        const uint8_t* Ahi = A0 + (size_t)sa * 2 * aop;
+        for (int nt = nt0; nt < nt1; ++nt) {
+          const int s = t & 1, acc = t & (kAcc - 1);
+          if (!mbar_wait(bfull0 + 8 * s, (uint32_t)(t >> 1) & 1u, &abort_flag, p.status) ||
+              !mbar_wait(tempty0 + 8 * acc, ((uint32_t)(t >> 2) & 1u) ^ 1u, &abort_flag,
+                         p.status)) {
+            stop = true;
+            break;
+          }
           fence_after();
           const uint32_t d = tmem + (uint32_t)(acc * kBN);
-          const uint8_t* Ahi = Abase + (size_t)s * 2 * opbytes;
-          const uint8_t* Alo = Ahi + opbytes;
-          const uint8_t* Aop[3] = {Alo, Ahi, Ahi};
-          const uint8_t* Bop[3] = {Bhi, Blo, Bhi};
+          const uint8_t* Bhi = B0 + (size_t)s * 2 * bop;
+          const uint8_t* Aop[3] = {Ahi + aop, Ahi, Ahi};  // S_lo y_hi + S_hi y_lo + S_hi y_hi
+          const uint8_t* Bop[3] = {Bhi, Bhi + bop, Bhi};
           uint32_t accum = 0;
           for (int prod = 0; prod < 3; ++prod) {
             for (int ks = 0; ks < kb * 4; ++ks) {
-              const uint32_t off = (uint32_t)(ks >> 2) * kBoxBytes + (uint32_t)(ks & 3) * 32u;
-              mma_tf32(d, smem_desc(smem_u32(Aop[prod]) + off), smem_desc(smem_u32(Bop[prod]) + off),
+              const uint32_t ka = (uint32_t)(ks >> 2) * kABox + (uint32_t)(ks & 3) * 32u;
+              const uint32_t kbo = (uint32_t)(ks >> 2) * kBBox + (uint32_t)(ks & 3) * 32u;
+              mma_tf32(d, smem_desc(smem_u32(Aop[prod]) + ka), smem_desc(smem_u32(Bop[prod]) + kbo),
                        accum);
               accum = 1;
             }
           }
-          mma_commit(empty0 + 8 * s);
+          mma_commit(bempty0 + 8 * s);
+          if (nt == nt1 - 1) mma_commit(aempty0 + 8 * sa);
           mma_commit(tfull0 + 8 * acc);
-          last = it;
+          last = t++;
         }
+        ++ua;
       }
-      if (last >= 0) mbar_drain(tfull0 + 8 * (last & 1), (uint32_t)(last >> 1) & 1u);
+      if (last >= 0) mbar_drain(tfull0 + 8 * (last & (kAcc - 1)), (uint32_t)(last >> 2) & 1u);
     }
   } else {
     // ---------------- epilogue: warps 2..5, lane quarter q = warp % 4
     const int q = warp & 3;
     int issued = 0;  // TMA stores issued by this warp: selects the staging buffer
-    for (int it = 0; it < iters; ++it) {
-      const int acc = it & 1;
-      const uint32_t ph = (uint32_t)(it >> 1) & 1u;
-      const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull0 + 8 * acc, ph, &abort_flag, p.status));
-      if (!ok) break;
-      fence_after();
-      const int mt = first + it * step;
-      const int64_t i = (int64_t)mt * kBM + q * 32 + lane;
-      const int64_t j0 = (int64_t)ntile * kBN;
-      for (int cb = 0; cb < kBN / 32; ++cb) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + cb * 32), v);
-        if (p.tma_store) {
-          // stage [32 parameters][32 rows] and hand it to the TMA engine; a box
-          // wholly past the end is skipped and touches no staging buffer, so
-          // that "at most one store pending" always means the other buffer
-          const int64_t xs = (int64_t)mt * kBM + q * 32, ys = j0 + cb * 32;
-          if (xs < p.n && ys < p.m) {
-            float* sb = stage + (q * 2 + (issued & 1)) * kStageFloats;
-            ++issued;
-            if (lane == 0) bulk_wait_read1();
-            __syncwarp();
+    int t = 0;
+    bool stop = false;
+    for (int u = blockIdx.x; u < p.num_units && !stop; u += gridDim.x) {
+      int mt, nt0, nt1;
+      unit_range(p, u, mt, nt0, nt1);
+      const int64_t xs = (int64_t)mt * kBM + q * 32;
+      for (int nt = nt0; nt < nt1; ++nt, ++t) {
+        const int acc = t & (kAcc - 1);
+        const bool ok = __all_sync(
+            0xffffffffu, mbar_wait(tfull0 + 8 * acc, (uint32_t)(t >> 2) & 1u, &abort_flag, p.status));
+        if (!ok) {
+          stop = true;
+          break;
+        }
+        fence_after();
+        for (int cb = 0; cb < kBN / 32; ++cb) {
+          float v[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + cb * 32), v);
+          const int64_t ys = (int64_t)nt * kBN + cb * 32;
+          if (p.tma_store) {
+            // stage [32 parameters][32 rows] and hand it to the TMA engine; a box
+            // wholly past the end is skipped and touches no staging buffer, so
+            // that "at most one store pending" always means the other buffer
+            if (xs < p.n && ys < p.m) {
+              float* sb = stage + (q * 2 + (issued & 1)) * kStageFloats;
+              ++issued;
+              if (lane == 0) bulk_wait_read1();
+              __syncwarp();
 #pragma unroll
-            for (int c = 0; c < 32; ++c) sb[c * 32 + lane] = v[c];
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0) {
-              tma_store_2d(&tmOut, smem_u32(sb), (int)xs, (int)ys);
-              bulk_commit();
+              for (int c = 0; c < 32; ++c) sb[c * 32 + lane] = v[c];
+              fence_async_smem();
+              __syncwarp();
+              if (lane == 0) {
+                tma_store_2d(&tmOut, smem_u32(sb), (int)xs, (int)ys);
+                bulk_commit();
+              }
+            }
+          } else if (xs + lane < p.n) {
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+              const int64_t j = ys + c;
+              if (j < p.m) __stcs(p.out + j * p.n + xs + lane, v[c]);
             }
           }
-        } else if (i < p.n) {
-#pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            const int64_t j = j0 + cb * 32 + c;
-            if (j < p.m) __stcs(p.out + j * p.n + i, v[c]);
-          }
         }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
       }
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
     }
     if (p.tma_store && lane == 0) bulk_wait_all();
   }
@@ -380,13 +435,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Row-major rows x rpad float32 matrix, box 128 rows x 32 floats, 128-byte swizzle.
-static bool make_map(CUtensorMap* map, const float* base, int64_t rows, int rpad) {
+// Row-major rows x rpad float32 matrix, box box_rows x 32 floats, 128-byte swizzle.
+static bool make_map(CUtensorMap* map, const float* base, int64_t rows, int rpad, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)rpad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)rpad * sizeof(float)};
-  cuuint32_t box[2] = {32, 128};
+  cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -432,9 +487,9 @@ cudaError_t launch_wait_selftest(int* status, double seconds, cudaStream_t st) {
 }
 
 size_t reconstruct_tc_smem_bytes(int rpad) {
-  const size_t op = (size_t)(rpad / 32) * tc::kBoxBytes;
-  return 1024 + 2 * op + (size_t)tc::kStages * 2 * op + 8 * tc::kStageFloats * sizeof(float) +
-         9 * sizeof(uint64_t);
+  const size_t kb = (size_t)(rpad / 32);
+  return 1024 + (size_t)tc::kAStages * 2 * kb * tc::kABox + (size_t)tc::kBStages * 2 * kb * tc::kBBox +
+         8 * tc::kStageFloats * sizeof(float) + (4 * 2 + 2 * tc::kAcc) * sizeof(uint64_t);
 }
 
 bool reconstruct_tc_supported(const sas_ctx* c) {
@@ -442,49 +497,61 @@ bool reconstruct_tc_supported(const sas_ctx* c) {
   return c->dtype == SAS_REAL64 && rpad <= 64 && tc::encode_fn() != nullptr;
 }
 
+// Work split: one unit = one 128-row tile of S and a range of 64-parameter
+// tiles.  When there are fewer row tiles than SMs, the parameter tiles of a
+// row tile are split into ranges so that every SM has work; otherwise each
+// unit covers all parameter tiles and S is read from HBM exactly once.
+void reconstruct_tc_split(int64_t n, int64_t m, int num_sms, int* num_mtiles, int* num_ntiles,
+                          int* ngroups, int* ntpg) {
+  const int64_t mt = (n + tc::kBM - 1) / tc::kBM;
+  const int64_t nt = (m + tc::kBN - 1) / tc::kBN;
+  int64_t ng = 1;
+  if (mt < num_sms) {
+    ng = (num_sms + mt - 1) / mt;
+    if (ng > nt) ng = nt;
+  }
+  const int64_t per = (nt + ng - 1) / ng;
+  ng = (nt + per - 1) / per;  // no empty range
+  *num_mtiles = (int)mt;
+  *num_ntiles = (int)nt;
+  *ngroups = (int)ng;
+  *ntpg = (int)per;
+}
+
 cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                   cudaStream_t st) {
   if (m == 0) return cudaSuccess;
+  if (m > 2147483647 - tc::kBN || c->n > 2147483647 - tc::kBM) return cudaErrorInvalidValue;
   const int rpad = (c->r + 31) / 32 * 32;
-  const int num_ntiles_all = (int)((m + tc::kBN - 1) / tc::kBN);
   const size_t smem = reconstruct_tc_smem_bytes(rpad);
   cudaError_t e = cudaFuncSetAttribute(tc::reconstruct_tc_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // parameter tiles are processed in groups of at most num_sms tiles per launch
-  const int group = c->num_sms;
-  for (int nt0 = 0; nt0 < num_ntiles_all; nt0 += group) {
-    const int nts = num_ntiles_all - nt0 < group ? num_ntiles_all - nt0 : group;
-    const int64_t j0 = (int64_t)nt0 * tc::kBN;
-    const int64_t mm = m - j0 < (int64_t)nts * tc::kBN ? m - j0 : (int64_t)nts * tc::kBN;
-    CUtensorMap mAhi, mAlo, mBhi, mBlo;
-    if (!tc::make_map(&mAhi, c->Shi, c->n, rpad) || !tc::make_map(&mAlo, c->Slo, c->n, rpad) ||
-        !tc::make_map(&mBhi, ysplit + j0 * rpad, mm, rpad) ||
-        !tc::make_map(&mBlo, ysplit + (size_t)m * rpad + j0 * rpad, mm, rpad))
-      return cudaErrorInvalidValue;
-    // TMA stores need 16-byte aligned rows: n a multiple of 4 and an aligned base
-    CUtensorMap mOut;
-    const bool tma_store = (c->n % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
-                           tc::make_out_map(&mOut, out + j0 * c->n, c->n, mm);
-    if (!tma_store) std::memset(&mOut, 0, sizeof(mOut));
-    tc::Params p;
-    p.tma_store = tma_store ? 1 : 0;
-    p.out = out + j0 * c->n;
-    p.n = c->n;
-    p.m = mm;
-    p.kboxes = rpad / 32;
-    p.num_mtiles = (int)((c->n + tc::kBM - 1) / tc::kBM);
-    p.num_ntiles = nts;
-    p.status = c->dev_status;
-    int grid = (c->num_sms / nts) * nts;
-    if (grid < nts) grid = nts;
-    const int max_grid = p.num_mtiles * nts;
-    if (grid > max_grid) grid = max_grid;
-    tc::reconstruct_tc_kernel<<<grid, tc::kThreads, smem, st>>>(mAhi, mAlo, mBhi, mBlo, mOut, p);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  if (!tc::make_map(&mAhi, c->Shi, c->n, rpad, tc::kBM) ||
+      !tc::make_map(&mAlo, c->Slo, c->n, rpad, tc::kBM) ||
+      !tc::make_map(&mBhi, ysplit, m, rpad, tc::kBN) ||
+      !tc::make_map(&mBlo, ysplit + (size_t)m * rpad, m, rpad, tc::kBN))
+    return cudaErrorInvalidValue;
+  // TMA stores need 16-byte aligned rows: n a multiple of 4 and an aligned base
+  CUtensorMap mOut;
+  const bool tma_store = (c->n % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
+                         tc::make_out_map(&mOut, out, c->n, m);
+  if (!tma_store) std::memset(&mOut, 0, sizeof(mOut));
+  tc::Params p;
+  p.tma_store = tma_store ? 1 : 0;
+  p.out = out;
+  p.n = c->n;
+  p.m = m;
+  p.kboxes = rpad / 32;
+  reconstruct_tc_split(c->n, m, c->num_sms, &p.num_mtiles, &p.num_ntiles, &p.ngroups, &p.ntpg);
+  const int64_t units = (int64_t)p.num_mtiles * p.ngroups;
+  if (units > 2147483647) return cudaErrorInvalidValue;
+  p.num_units = (int)units;
+  p.status = c->dev_status;
+  const int grid = (int)(units < c->num_sms ? units : c->num_sms);
+  tc::reconstruct_tc_kernel<<<grid, tc::kThreads, smem, st>>>(mAhi, mAlo, mBhi, mBlo, mOut, p);
+  return cudaGetLastError();
 }
 
 }  // namespace sas

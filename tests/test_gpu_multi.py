@@ -5,7 +5,8 @@ optionally replayed from a CUDA graph.  Each parameter runs the same per-task
 solve as subapsnap_solve_batch with the same launch shape: plain float64 outputs
 must be bit-identical to the per-context solves; mixed outputs (a float32 body
 the compiler may contract differently in another kernel, then refined to float64
-accuracy) within 1e-9.  Both are also checked against the oracle.
+accuracy) within 1e-9.  Both are also checked against the oracle (mixed: the
+conditioning bound of the refined float32 solve).
 """
 import numpy as np
 import pytest
@@ -19,7 +20,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2510_04825_gb300 import api  # noqa: E402
 from paper_2510_04825_gb300.solver import AffineSolver  # noqa: E402
 
-from _problems import Case  # noqa: E402
+from _problems import Case, mixed_bound  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -56,9 +57,15 @@ def test_multi_plan_matches_single_solves(cases, mode):
                 rel = (torch.linalg.vector_norm(o - r, dim=1) / torch.linalg.vector_norm(r, dim=1)).max()
                 assert rel.item() <= 1e-9, rel.item()
     for c, o in zip(cases, outs):
-        Yo, _ = c.oracle_solve(c.prob.test_params[:20])
+        Yo, rho_o = c.oracle_solve(c.prob.test_params[:20])
         err = np.linalg.norm(o[:20].cpu().numpy() - Yo, axis=1) / np.linalg.norm(Yo, axis=1)
-        assert err.max() <= (1e-10 if mode == api.SAS_MODE_PLAIN else 1e-7)
+        if mode == api.SAS_MODE_PLAIN:
+            assert err.max() <= 1e-10
+        else:
+            # the refined float32 solve converges to the LS solution of the
+            # float32-perturbed matrix: bounded per parameter by its conditioning
+            bound = mixed_bound(c.prob, c.S, c.J, c.prob.test_params[:20], Yo, rho_o)
+            assert (err <= bound).all(), (err.max(), bound.min())
     api.subapsnap_multi_plan_destroy(plan)
     for s in solvers:
         s.close()

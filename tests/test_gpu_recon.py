@@ -3,7 +3,9 @@
 x_hat in float32 from tf32 splits of S and y: three products, relative
 error ~2^-21 per product, so <= 2e-6 relative per parameter is the bound.
 Shapes cover ragged row tiles (n not a multiple of 128), ragged parameter
-tiles (m not a multiple of 128), one and two K boxes (r <= 32, r <= 64).
+tiles (m not a multiple of 64), one and two K boxes (r <= 32, r <= 64),
+the split of a row tile's parameter tiles into ranges (fewer row tiles than
+SMs) and units that stream many parameter tiles past one resident S tile.
 """
 import numpy as np
 import pytest
@@ -20,7 +22,7 @@ from paper_2510_04825_gb300.solver import AffineSolver  # noqa: E402
 from _problems import Case  # noqa: E402
 
 
-def xhat(case, kernel, params):
+def xhat(case, kernel, params, on_device=False):
     solver = AffineSolver(case.prob, case.S, case.J, mode=api.SAS_MODE_MIXED, device="cuda")
     api.subapsnap_set_option(solver.ctx, api.SAS_OPT_RECON_KERNEL, kernel)
     m = params.shape[0]
@@ -31,11 +33,13 @@ def xhat(case, kernel, params):
     torch.cuda.synchronize()
     solver.close()
     assert st == 0
+    if on_device:
+        return out
     return out.cpu().numpy().astype(np.float64)
 
 
 @pytest.mark.parametrize("N,r,s,m", [(45, 60, 120, 300), (40, 20, 40, 130), (32, 64, 128, 128),
-                                     (48, 33, 70, 1)])
+                                     (48, 33, 70, 1), (20, 60, 120, 1000), (12, 30, 60, 777)])
 def test_tensor_core_reconstruction(N, r, s, m):
     case = Case("diffusion_2d", basis="random", N=N, r=r, s=s, m=m)
     params = case.prob.test_params
@@ -91,3 +95,23 @@ def test_tensor_core_reconstruction_large_n_many_batch_sizes():
         Xo = Yo @ case.S.T
         e = np.linalg.norm(Xtc[:3] - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
         assert e.max() <= 2e-6, (m, e)
+
+
+def test_tensor_core_reconstruction_long_units():
+    """n = 262,144 (2048 row tiles, more than the SMs: every unit streams all
+    parameter tiles past its S tile) with m = 2100 (33 parameter tiles, the last
+    ragged): tcgen05 against the CUDA-core path on the device, the oracle on samples."""
+    case = Case("diffusion_2d", basis="random", rows="random", N=512, r=60, s=120, m=2100)
+    p = case.prob
+    params = p.test_params
+    Xtc = xhat(case, 2, params, on_device=True)
+    Xcc = xhat(case, 1, params, on_device=True)
+    assert torch.isfinite(Xtc).all().item()
+    d = (torch.linalg.vector_norm(Xtc - Xcc, dim=1) / torch.linalg.vector_norm(Xcc, dim=1)).cpu().numpy()
+    assert d.max() <= 2e-6, (np.argmax(d), d.max())
+    pick = [0, 63, 64, 1000, 2047, 2048, 2099]
+    Yo, _ = case.oracle_solve(params[pick])
+    Xo = Yo @ case.S.T
+    Xs = Xtc[pick].double().cpu().numpy()
+    e = np.linalg.norm(Xs - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
+    assert e.max() <= 2e-6, e

@@ -306,11 +306,15 @@ def transfer_basis_torch(prob, device="cuda", **kw):
 # one sigma sharing every kernel product.
 # ---------------------------------------------------------------------------
 
-def kernel_ridge_cg(prob, X, sigma, lams, iters=40, block=8192):
-    """CG for (K_sigma + lambda_j I) x_j = y, all lambda_j at once.
+def kernel_ridge_cr(prob, X, sigma, lams, iters=40, block=8192):
+    """Conjugate residuals for (K_sigma + lambda_j I) x_j = y, all lambda_j at once.
 
-    The kernel product is formed block by block in float32, so the snapshots
-    are approximate, as Alg. 1 step 1 allows.  Returns (x (N, q) float64, relative residuals of the float32 operator).
+    Conjugate residuals minimise ||y - A x|| over the Krylov space, so the
+    residual falls monotonically (conjugate gradients minimise the energy norm
+    and, on these ill-conditioned kernels, can leave the residual above ||y||
+    for many steps).  The kernel product is formed block by block in float32,
+    so the snapshots are approximate, as Alg. 1 step 1 allows.  Returns
+    (x (N, q) float64, relative residuals of the float32 operator).
     """
     import torch
     N = X.shape[0]
@@ -321,7 +325,7 @@ def kernel_ridge_cg(prob, X, sigma, lams, iters=40, block=8192):
     y = torch.as_tensor(np.asarray(prob.b, dtype=np.float64), device=X.device)
     inv = 1.0 / (2.0 * sigma * sigma)
 
-    def kmat(V):
+    def amul(V):
         out = torch.empty_like(V)
         Vf = V.float()
         for a in range(0, N, block):
@@ -329,27 +333,27 @@ def kernel_ridge_cg(prob, X, sigma, lams, iters=40, block=8192):
             D = (nrm[a:a + block, None] + nrm[None, :] - 2.0 * (Xc[a:a + block] @ Xc.T)).clamp_min_(0.0)
             D.mul_(-inv).exp_()
             out[a:a + block] = (D @ Vf).double()
-        return out
+        return out + lam[None, :] * V
 
     x = torch.zeros((N, q), dtype=torch.float64, device=X.device)
     r = y[:, None].expand(N, q).clone()
     p = r.clone()
-    rr = (r * r).sum(0)
-    bn = torch.sqrt(rr.clone())
-    best = x.clone()
-    best_rr = rr.clone()
+    Ar = amul(r)
+    Ap = Ar.clone()
+    rAr = (r * Ar).sum(0)
+    bn = torch.linalg.vector_norm(y)
     for _ in range(iters):
-        Ap = kmat(p) + lam[None, :] * p
-        alpha = rr / (p * Ap).sum(0)
+        alpha = rAr / (Ap * Ap).sum(0)
         x += alpha[None, :] * p
         r -= alpha[None, :] * Ap
-        rr_new = (r * r).sum(0)
-        p = r + (rr_new / rr)[None, :] * p
-        rr = rr_new
-        better = rr < best_rr  # keep the iterate with the smallest residual per column
-        best[:, better] = x[:, better]
-        best_rr = torch.where(better, rr, best_rr)
-    return best, (torch.sqrt(best_rr) / bn).cpu().numpy()
+        Ar = amul(r)
+        rAr_new = (r * Ar).sum(0)
+        beta = rAr_new / rAr
+        p = r + beta[None, :] * p
+        Ap = Ar + beta[None, :] * Ap
+        rAr = rAr_new
+    res = torch.linalg.vector_norm(y[:, None] - amul(x), dim=0) / bn
+    return x, res.cpu().numpy()
 
 
 def kernel_ridge_basis_torch(prob, X, device="cuda", iters=40):
@@ -362,7 +366,7 @@ def kernel_ridge_basis_torch(prob, X, device="cuda", iters=40):
     cols, res = [], []
     for sv in sig:
         lams = prob.snap_params[prob.snap_params[:, 0] == sv, 1]
-        x, rr = kernel_ridge_cg(prob, X, float(sv), lams, iters=iters)
+        x, rr = kernel_ridge_cr(prob, X, float(sv), lams, iters=iters)
         cols.append(x)
         res.append(rr)
     Xs = torch.cat(cols, dim=1)
