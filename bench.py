@@ -86,8 +86,15 @@ def start_clock_sampler(path):
             ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "25"],
             stdout=f, stderr=subprocess.DEVNULL)
+        # wait (at most 5 s) for the first sample so that the timed region is covered
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and p.poll() is None:
+            f.flush()
+            if os.path.getsize(path) > 0:
+                break
+            time.sleep(0.02)
         return p, f
     except Exception:
         return None, None
@@ -181,7 +188,7 @@ def run_gpu(args):
     def timed(fn, steps, warmup, sample_clocks=False):
         clk = None
         if sample_clocks and rank == 0:
-            # the sampler spans warm-up and timed region (200 ms period)
+            # the sampler spans warm-up and timed region (25 ms period)
             cpath = os.path.join(tempfile.gettempdir(), f"sas_clocks_{os.getpid()}.csv")
             sp, sf = start_clock_sampler(cpath)
         for _ in range(warmup):
@@ -741,7 +748,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

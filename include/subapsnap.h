@@ -220,15 +220,20 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
 /* Per-context options (subapsnap_set_option).  Not in the paper.
  *  SAS_OPT_RECON_KERNEL: mixed-form reconstruction kernel: 0 = automatic
  *      (tensor cores when r <= 64), 1 = CUDA cores, 2 = tensor cores
- *      (tcgen05, kind::tf32, three split products).
+ *      (tcgen05, kind::tf32, three split products, 64-parameter tiles),
+ *      3 = tensor cores with 128-parameter tiles.
  *  SAS_OPT_MAX_REFINE: most refinement steps of the mixed solve (0..16,
  *      default 4).
  *  SAS_OPT_REFINE_TOL: refinement stops when ||delta|| <= tol ||y||
  *      (default 1e-13) or when a step no longer halves the correction.
  *  SAS_OPT_LS_VARIANT: launch shape of the least-squares kernel of the
- *      context's mode (the index subapsnap_autotune reports; 0 = default). */
+ *      context's mode (the index subapsnap_autotune reports; 0 = default).
+ *  SAS_OPT_ASSEMBLY_KERNEL: kernel rows of the mixed kernel-ridge form:
+ *      0 = automatic (tensor cores), 1 = CUDA cores (float32 entries, float64
+ *      chunk sums), 2 = tensor cores (tcgen05, kind::tf32, entries and S in
+ *      three split products, float64 fold every 4096 points). */
 enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
-       SAS_OPT_LS_VARIANT = 3 };
+       SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4 };
 
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */

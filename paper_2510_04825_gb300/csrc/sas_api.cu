@@ -92,6 +92,10 @@ static void free_ctx(sas_ctx* c) {
   cudaFree(c->XJ);
   cudaFree(c->Shi);
   cudaFree(c->Slo);
+  cudaFree(c->StHi);
+  cudaFree(c->StLo);
+  cudaFree(c->Xc32);
+  cudaFree(c->XJ32);
   cudaFree(c->ybuf);
   cudaFree(c->ysplit);
   cudaFree(c->Mbuf);
@@ -352,6 +356,14 @@ sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
     TRYK(dmalloc(&c->Shi, (size_t)d->n * rpad * sizeof(float)));
     TRYK(dmalloc(&c->Slo, (size_t)d->n * rpad * sizeof(float)));
     TRYK(launch_make_mixed_copies(c, sst));
+    // tensor-core kernel rows: S^T split, float32 hi/lo coordinates
+    const int nb = krr_tc_nb(d->r), dp = krr_tc_dp(d->d);
+    const int64_t npad = krr_tc_npad(d->n);
+    TRYK(dmalloc(&c->StHi, (size_t)nb * npad * sizeof(float)));
+    TRYK(dmalloc(&c->StLo, (size_t)nb * npad * sizeof(float)));
+    TRYK(dmalloc(&c->Xc32, (size_t)npad * 2 * dp * sizeof(float)));
+    TRYK(dmalloc(&c->XJ32, (size_t)d->s * 2 * dp * sizeof(float)));
+    TRYK(launch_krr_tc_copies(c, sst));
   }
   TRYK(cudaStreamSynchronize(sst));
   {
@@ -387,13 +399,18 @@ static sas_status ensure_mbuf(sas_ctx* c, int64_t cap, cudaStream_t st) {
   return SAS_OK;
 }
 constexpr int64_t kKernelSubBatch = 512;
+constexpr int64_t kKernelSubBatchTc = 2048;  // tensor-core rows: fewer, fuller waves
 
 static sas_status solve_kernel_family(sas_ctx* c, const double* params, int64_t m, int32_t out_kind,
                                       void* out, uint32_t* flags, double* rho, cudaStream_t st) {
   const bool mixed = c->mode == SAS_MODE_MIXED;
   if (out_kind != SAS_OUT_Y && out_kind != SAS_OUT_XHAT)
     return fail(SAS_EINVAL, "the kernel family returns y or x_hat");
-  const int64_t cap = m < kKernelSubBatch ? m : kKernelSubBatch;
+  const bool tc_rows = mixed && c->krr_kernel != 1 && krr_tc_supported(c);
+  if (mixed && c->krr_kernel == 2 && !tc_rows)
+    return fail(SAS_ENOTSUP, "tensor-core kernel rows are not available for this context");
+  const int64_t sub = tc_rows ? kKernelSubBatchTc : kKernelSubBatch;
+  const int64_t cap = m < sub ? m : sub;
   sas_status s2 = ensure_mbuf(c, cap, st);
   if (s2 != SAS_OK) return s2;
   if (out_kind == SAS_OUT_XHAT) {
@@ -406,7 +423,8 @@ static sas_status solve_kernel_family(sas_ctx* c, const double* params, int64_t 
     const double* pb = params + b0 * 2;
     {
       TraceScope ts(c, SAS_KERNEL_ASSEMBLE, st);
-      e = launch_krr_assemble(c, pb, mb, c->Mbuf, mixed, st);
+      e = tc_rows ? launch_krr_assemble_tc(c, pb, mb, c->Mbuf, st)
+                  : launch_krr_assemble(c, pb, mb, c->Mbuf, mixed, st);
     }
     if (e != cudaSuccess) break;
     void* yout = out_kind == SAS_OUT_Y ? (void*)((double*)out + b0 * c->r) : c->ybuf;
@@ -800,7 +818,8 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");
   switch (key) {
     case SAS_OPT_RECON_KERNEL:
-      if (value != 0.0 && value != 1.0 && value != 2.0) return fail(SAS_EINVAL, "recon kernel must be 0, 1 or 2");
+      if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
+        return fail(SAS_EINVAL, "recon kernel must be 0, 1, 2 or 3");
       c->recon_kernel = (int)value;
       return SAS_OK;
     case SAS_OPT_MAX_REFINE:
@@ -810,6 +829,11 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
     case SAS_OPT_REFINE_TOL:
       if (!(value > 0.0 && value < 1.0)) return fail(SAS_EINVAL, "refine tol must be in (0, 1)");
       c->refine_tol = value;
+      return SAS_OK;
+    case SAS_OPT_ASSEMBLY_KERNEL:
+      if (value != 0.0 && value != 1.0 && value != 2.0)
+        return fail(SAS_EINVAL, "assembly kernel must be 0, 1 or 2");
+      c->krr_kernel = (int)value;
       return SAS_OK;
     case SAS_OPT_LS_VARIANT: {
       const bool mixed = c->mode == SAS_MODE_MIXED;

@@ -169,6 +169,10 @@ struct sas_ctx {
   double* XJ;          // kernel family: s x d
   float* Shi;          // mixed reconstruction: high tf32 part of S, n x r (ld n)
   float* Slo;          // low part
+  float* StHi;         // mixed kernel family: S^T tf32 high part, nb x npad (tensor-core rows)
+  float* StLo;         // low part
+  float* Xc32;         // mixed kernel family: float32 hi/lo coordinates of every point
+  float* XJ32;         // mixed kernel family: float32 hi/lo coordinates of the rows of J
   double bJ_norm;
   // scratch (grown on demand)
   double* Mbuf;        // kernel family: dense M for a sub-batch (mcap x s x r)
@@ -182,7 +186,8 @@ struct sas_ctx {
   int ls_blocks_per_sm;
   void* surrogate;     // learned surrogate network (sas_mlp.cu), or null
   // options
-  int recon_kernel;    // 0 auto, 1 CUDA cores, 2 tensor cores
+  int recon_kernel;    // 0 auto, 1 CUDA cores, 2 tensor cores (64-parameter tiles), 3 (128)
+  int krr_kernel;      // kernel rows of the mixed form: 0 auto, 1 CUDA cores, 2 tensor cores
   int ls_variant_plain;  // launch shape of the plain LS kernel (autotuned)
   int ls_variant_mixed;  // launch shape (+ float64 M kept or not) of the mixed LS kernel
   int max_refine;
@@ -217,6 +222,15 @@ struct TraceScope {
 cudaError_t launch_gather_blocks(const sas_ctx* c, cudaStream_t st);
 cudaError_t launch_gather_vectors(const sas_ctx* c, const double* cvec, cudaStream_t st);
 cudaError_t launch_make_mixed_copies(const sas_ctx* c, cudaStream_t st);
+// tensor-core kernel rows (sas_krr_tc.cu)
+int krr_tc_nb(int r);
+int64_t krr_tc_npad(int64_t n);
+int krr_tc_dp(int d);
+size_t krr_tc_smem_bytes(int r, int d);
+bool krr_tc_supported(const sas_ctx* c);
+cudaError_t launch_krr_tc_copies(const sas_ctx* c, cudaStream_t st);
+cudaError_t launch_krr_assemble_tc(const sas_ctx* c, const double* params, int64_t m, double* M,
+                                   cudaStream_t st);
 // solve
 cudaError_t launch_ls_plain(const sas_ctx* c, const double* params, int64_t m, void* yout,
                             void* qoi_out, uint32_t* flags, double* rho, cudaStream_t st,

@@ -87,7 +87,7 @@ cudaError_t launch_reconstruct_mixed(const sas_ctx* c, const float* ysplit, int6
   if (m == 0) return cudaSuccess;
   if (c->recon_kernel != 1 && reconstruct_tc_supported(c))
     return launch_reconstruct_tc(c, ysplit, m, out, st);
-  if (c->recon_kernel == 2) return cudaErrorNotSupported;
+  if (c->recon_kernel >= 2) return cudaErrorNotSupported;
   constexpr int JB = 16, NT = 256;
   const int rpad = (c->r + 31) / 32 * 32;
   if ((m + JB - 1) / JB > 65535) return cudaErrorInvalidValue;

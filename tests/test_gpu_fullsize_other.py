@@ -8,7 +8,9 @@ solves it (one call for the whole batch):
     float64 within 1e-10 (kappa-filtered as elsewhere), mixed within the
     refinement bound;
   kernel ridge, N = 200,000 points in R^8, r = 100, s = 300, 2048 (sigma,
-    lambda): y for 6 sampled parameters, plain float64 within 1e-10.
+    lambda): y for 6 sampled parameters, plain float64 within 1e-10; the mixed
+    form with tensor-core kernel rows (49 float64 folds per row tile) within
+    4 kappa(M) 64 u32 + 1e-10, solved as part of the whole batch.
 """
 import numpy as np
 import pytest
@@ -97,3 +99,23 @@ def test_kernel_ridge_full_size():
         if kap * 1.1e-16 <= 1e-11:
             assert ey <= 1e-10
     solver.close()
+    # mixed form, tensor-core kernel rows, the whole batch in one call
+    mixed = KernelSolver(prob, None, J, mode=api.SAS_MODE_MIXED, device="cuda", S_device=S_rows,
+                         X_device=X)
+    api.subapsnap_set_option(mixed.ctx, api.SAS_OPT_ASSEMBLY_KERNEL, 2)
+    Ym = torch.empty((m, prob.r), dtype=torch.float64, device="cuda")
+    mixed.solve(P, api.SAS_OUT_Y, Ym)
+    st = api.subapsnap_device_status(mixed.ctx)
+    torch.cuda.synchronize()
+    assert st == 0
+    Ym = Ym.cpu().numpy()
+    assert np.isfinite(Ym).all()
+    for j in pick:
+        yo, _ = krr.solve_one(prob, S, J, prob.test_params[j])
+        M = krr.subsampled_matrix(prob.X, S, J, prob.test_params[j])
+        sv = np.linalg.svd(M, compute_uv=False)
+        kap = sv[0] / sv[-1]
+        ey = np.linalg.norm(Ym[j] - yo) / np.linalg.norm(yo)
+        print(f"kernel ridge full size, mixed tensor-core rows, parameter {j}: rel err {ey:.2e}")
+        assert ey <= 4 * kap * 64 * 2.0 ** -24 + 1e-10
+    mixed.close()

@@ -6,10 +6,13 @@ family is.  Tolerances:
   plain float64: y within 1e-10 relative of the oracle for every parameter
     with kappa(M) 1.1e-16 <= 1e-11 (the float64 parity rule of the other tests).
   mixed: the kernel entries are formed in float32 (hi/lo coordinate
-    differences, ex2.approx, per-chunk float32 sums added in float64), so M
-    carries a relative error eps_M ~ 64 u32; the solve is refined against
-    that M, so ||y - y_oracle|| / ||y|| <= 4 kappa(M) eps_M + the refinement
-    bound.  The subsampled residual of the plain path (float64 kernel rows) is
+    differences, ex2.approx), then either summed on the CUDA cores (float32
+    per chunk, chunks added in float64) or on the tensor cores (entries and S
+    split into tf32 hi/lo, three products, float32 TMEM sums folded into
+    float64 every 4096 points); both leave M with a relative error
+    eps_M <= 64 u32.  The solve is refined against that M, so
+    ||y - y_oracle|| / ||y|| <= 4 kappa(M) eps_M + the refinement bound.
+    The subsampled residual of the plain path (float64 kernel rows) is
     checked against the oracle as well.
 """
 import numpy as np
@@ -39,8 +42,10 @@ def krr_case():
     return prob, S, J
 
 
-def run(prob, S, J, mode, out_kind, params):
+def run(prob, S, J, mode, out_kind, params, assembly=0):
     solver = KernelSolver(prob, S, J, mode=mode, device="cuda")
+    if mode == api.SAS_MODE_MIXED:
+        api.subapsnap_set_option(solver.ctx, api.SAS_OPT_ASSEMBLY_KERNEL, assembly)
     m = params.shape[0]
     P = torch.from_numpy(np.ascontiguousarray(params)).cuda()
     if out_kind == api.SAS_OUT_Y:
@@ -77,15 +82,17 @@ def test_kernel_rows_plain_parity(krr_case):
     solver.close()
 
 
-def test_kernel_rows_mixed_error(krr_case):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_kernel_rows_mixed_error(krr_case, kernel):
     prob, S, J = krr_case
     params = prob.test_params
-    Y, flags, rho, solver = run(prob, S, J, api.SAS_MODE_MIXED, api.SAS_OUT_Y, params)
+    Y, flags, rho, solver = run(prob, S, J, api.SAS_MODE_MIXED, api.SAS_OUT_Y, params, kernel)
     Yo, rho_o = krr.solve_many(prob, S, J, params)
     err = np.linalg.norm(Y - Yo, axis=1) / np.linalg.norm(Yo, axis=1)
     kap = np.array([np.linalg.cond(krr.subsampled_matrix(prob.X, S, J, p)) for p in params])
     bound = 4 * kap * 64 * U32 + 1e-10
-    print(f"kernel mixed: max rel err {err.max():.2e}, median {np.median(err):.2e}, "
+    print(f"kernel mixed ({'tensor' if kernel == 2 else 'CUDA'} cores): max rel err {err.max():.2e}, "
+          f"median {np.median(err):.2e}, "
           f"max err/bound {(err / bound).max():.2e}")
     assert (err <= bound).all()
     solver.close()
@@ -99,3 +106,33 @@ def test_kernel_rows_xhat(krr_case):
     Xo = Yo @ S.T
     assert (np.linalg.norm(X - Xo, axis=1) / np.linalg.norm(Xo, axis=1)).max() <= 1e-10
     solver.close()
+
+
+@pytest.mark.parametrize("N,d,r,s,m", [(9001, 8, 36, 150, 37), (5000, 5, 25, 130, 8),
+                                       (3000, 13, 16, 40, 3), (700, 2, 16, 20, 1)])
+def test_tensor_core_rows_shapes(N, d, r, s, m):
+    """Tensor-core kernel rows on ragged shapes: N not a multiple of the 32-point
+    chunk, several 4096-point float64 folds (N = 9001), J tiles with a ragged
+    last tile (s = 150, 130), coordinate dimensions padded to multiples of 4
+    (d = 5, 13, 2), an odd number of parameters (the last pair has one live
+    member) and a single parameter.  Random orthonormal S and random rows J
+    (the online stage accepts any); both assembly kernels against the oracle."""
+    prob = get_config("kernel_ridge", N=N, d=d, r=r, s=s, m=m)
+    rng = np.random.default_rng(N)
+    S = wsnap.orthonormalise(rng.standard_normal((N, r)))
+    J = np.sort(rng.choice(N, s, replace=False))
+    params = prob.test_params
+    Yo, _ = krr.solve_many(prob, S, J, params)
+    kap = np.array([np.linalg.cond(krr.subsampled_matrix(prob.X, S, J, p)) for p in params])
+    bound = 4 * kap * 64 * U32 + 1e-10
+    errs = {}
+    for kernel in (1, 2):
+        Y, flags, rho, solver = run(prob, S, J, api.SAS_MODE_MIXED, api.SAS_OUT_Y, params, kernel)
+        st = api.subapsnap_device_status(solver.ctx)
+        solver.close()
+        assert st == 0
+        assert np.isfinite(Y).all()
+        errs[kernel] = np.linalg.norm(Y - Yo, axis=1) / np.linalg.norm(Yo, axis=1)
+        assert (errs[kernel] <= bound).all(), (kernel, errs[kernel].max(), bound.min())
+    print(f"N={N} d={d} s={s} m={m}: max rel err CUDA cores {errs[1].max():.2e}, "
+          f"tensor cores {errs[2].max():.2e}, kappa max {kap.max():.2e}")

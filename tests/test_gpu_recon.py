@@ -45,14 +45,16 @@ def test_tensor_core_reconstruction(N, r, s, m):
     params = case.prob.test_params
     Yo, _ = case.oracle_solve(params)
     Xo = Yo @ case.S.T
-    Xtc = xhat(case, 2, params)
     Xcc = xhat(case, 1, params)
-    assert np.isfinite(Xtc).all()
-    e_tc = np.linalg.norm(Xtc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
     e_cc = np.linalg.norm(Xcc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
-    print(f"N={N} r={r} m={m}: tcgen05 max rel err {e_tc.max():.2e}, CUDA cores {e_cc.max():.2e}")
-    assert e_tc.max() <= 2e-6
     assert e_cc.max() <= 2e-6
+    for kernel in (2, 3):  # 64- and 128-parameter tiles
+        Xtc = xhat(case, kernel, params)
+        assert np.isfinite(Xtc).all()
+        e_tc = np.linalg.norm(Xtc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
+        print(f"N={N} r={r} m={m}: tcgen05 ({kernel}) max rel err {e_tc.max():.2e}, "
+              f"CUDA cores {e_cc.max():.2e}")
+        assert e_tc.max() <= 2e-6
 
 
 @pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED])
@@ -86,11 +88,12 @@ def test_tensor_core_reconstruction_large_n_many_batch_sizes():
     p = case.prob
     for m in (1, 64, 100, 128, 256, 300):
         params = p.test_params[:m]
-        Xtc = xhat(case, 2, params)
         Xcc = xhat(case, 1, params)
-        d = np.linalg.norm(Xtc - Xcc, axis=1) / np.linalg.norm(Xcc, axis=1)
-        bad = np.nonzero(d > 2e-6)[0]
-        assert bad.size == 0, (m, bad[:8], d.max())
+        for kernel in (2, 3):
+            Xtc = xhat(case, kernel, params)
+            d = np.linalg.norm(Xtc - Xcc, axis=1) / np.linalg.norm(Xcc, axis=1)
+            bad = np.nonzero(d > 2e-6)[0]
+            assert bad.size == 0, (kernel, m, bad[:8], d.max())
         Yo, _ = case.oracle_solve(params[:3])
         Xo = Yo @ case.S.T
         e = np.linalg.norm(Xtc[:3] - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
@@ -104,11 +107,14 @@ def test_tensor_core_reconstruction_long_units():
     case = Case("diffusion_2d", basis="random", rows="random", N=512, r=60, s=120, m=2100)
     p = case.prob
     params = p.test_params
-    Xtc = xhat(case, 2, params, on_device=True)
     Xcc = xhat(case, 1, params, on_device=True)
-    assert torch.isfinite(Xtc).all().item()
-    d = (torch.linalg.vector_norm(Xtc - Xcc, dim=1) / torch.linalg.vector_norm(Xcc, dim=1)).cpu().numpy()
-    assert d.max() <= 2e-6, (np.argmax(d), d.max())
+    for kernel in (3, 2):
+        Xtc = xhat(case, kernel, params, on_device=True)
+        assert torch.isfinite(Xtc).all().item()
+        d = (torch.linalg.vector_norm(Xtc - Xcc, dim=1) / torch.linalg.vector_norm(Xcc, dim=1)).cpu().numpy()
+        assert d.max() <= 2e-6, (kernel, np.argmax(d), d.max())
+        if kernel == 3:
+            del Xtc
     pick = [0, 63, 64, 1000, 2047, 2048, 2099]
     Yo, _ = case.oracle_solve(params[pick])
     Xo = Yo @ case.S.T
