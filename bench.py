@@ -168,7 +168,7 @@ def run_gpu(args):
     tune = {}
     for name, sv in (("chosen", chosen), ("plain", plain)):
         v, times = api.subapsnap_autotune(sv.ctx, P, M, 2)
-        tune[name] = {"variant": v, "ms": [round(t, 4) for t in times if t >= 0]}
+        tune[name] = {"variant": v, "ms": {str(i): round(t, 4) for i, t in enumerate(times) if t >= 0}}
     n = prob.n
     out32 = torch.empty((M, n), dtype=torch.float32, device=device)
     out64 = torch.empty((M, n), dtype=torch.float64, device=device)
@@ -432,7 +432,7 @@ def run_gpu_other(args):
     if args.workload != "kernel_ridge":  # kernel rows dominate there; the LS shape barely matters
         for name, sv in (("chosen", chosen), ("plain", plain)):
             v, times = api.subapsnap_autotune(sv.ctx, P, m, 2)
-            tune[name] = {"variant": v, "ms": [round(t, 4) for t in times if t >= 0]}
+            tune[name] = {"variant": v, "ms": {str(i): round(t, 4) for i, t in enumerate(times) if t >= 0}}
     stream = torch.cuda.current_stream()
     setup_s = time.time() - t0
 

@@ -219,9 +219,10 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
 
 /* Per-context options (subapsnap_set_option).  Not in the paper.
  *  SAS_OPT_RECON_KERNEL: mixed-form reconstruction kernel: 0 = automatic
- *      (tensor cores when r <= 64), 1 = CUDA cores, 2 = tensor cores
- *      (tcgen05, kind::tf32, three split products, 64-parameter tiles),
- *      3 = tensor cores with 128-parameter tiles.
+ *      (tensor cores when r <= 64, as 4), 1 = CUDA cores, 2 = tensor cores
+ *      (tcgen05, kind::tf32, three split products) with 64-parameter tiles,
+ *      3 = tensor cores with 128-parameter tiles, 4 = as 3 with the parameter
+ *      tiles of each row tile visited in a rotated order.
  *  SAS_OPT_MAX_REFINE: most refinement steps of the mixed solve (0..16,
  *      default 4).
  *  SAS_OPT_REFINE_TOL: refinement stops when ||delta|| <= tol ||y||
@@ -231,27 +232,32 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
  *  SAS_OPT_ASSEMBLY_KERNEL: kernel rows of the mixed kernel-ridge form:
  *      0 = automatic (tensor cores), 1 = CUDA cores (float32 entries, float64
  *      chunk sums), 2 = tensor cores (tcgen05, kind::tf32, entries and S in
- *      three split products, float64 fold every 4096 points). */
+ *      three split products, float32 TMEM sums folded into float64).
+ *  SAS_OPT_ASSEMBLY_SEGMENT: tensor-core kernel rows: points summed in float32
+ *      before each float64 fold (multiple of 32 in [32, 2^20], default 1024);
+ *      shorter segments cost more folds and round less. */
 enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
-       SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4 };
+       SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4, SAS_OPT_ASSEMBLY_SEGMENT = 5 };
 
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */
 sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
 
 /* Autotuner (not in the paper): times every launch shape of the context's
- * least-squares kernel (threads per CTA, lanes per column group, whether M is
- * kept in float64 shared memory) on the caller's parameters, `reps` timed
+ * least-squares kernel (threads per CTA, lanes per column group; for the mixed
+ * form also where the float64 M lives: shared memory, a global slot per CTA,
+ * or recomputed) on the caller's parameters, `reps` timed
  * launches each after one warm-up, keeps the fastest in the context and
  * returns it.
  *  params: device, m x dp (a representative batch; its size matters).
- *  times_ms: host, room for 16 doubles or NULL: mean time per variant
+ *  times_ms: host, room for SAS_MAX_VARIANTS doubles or NULL: mean time per variant
  *            (a variant that cannot run for this shape reports -1).
  *  chosen: host or NULL: index of the kept variant.
  * If the environment variable SAS_TUNE_CACHE names a file, the choice is
  * appended there under a key of (family, mode, dtype, s, r, K, m) and later
  * calls with the same key read it back instead of timing.  Synchronous on
  * `stream`.  Errors: SAS_EINVAL, SAS_ECUDA. */
+#define SAS_MAX_VARIANTS 32
 sas_status subapsnap_autotune(sas_ctx* ctx, const double* params, int64_t m, int32_t reps,
                               double* times_ms, int32_t* chosen, void* stream);
 

@@ -40,7 +40,8 @@ EXPORTED = [
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
 SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL, SAS_OPT_LS_VARIANT = 0, 1, 2, 3
-SAS_OPT_ASSEMBLY_KERNEL = 4
+SAS_OPT_ASSEMBLY_KERNEL, SAS_OPT_ASSEMBLY_SEGMENT = 4, 5
+SAS_MAX_VARIANTS = 32
 SAS_NOALLOC_MAX_Y = 65536
 SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL, SAS_KERNEL_ASSEMBLE = 0, 1, 2, 3
 
@@ -247,7 +248,7 @@ def subapsnap_solve_batch_xhat_noalloc(ctx, params, m: int, out, flags=None, rho
 
 def subapsnap_autotune(ctx, params, m: int, reps: int = 3, stream=None):
     """Time every least-squares launch shape; returns (chosen index, times in ms)."""
-    times = (ctypes.c_double * 16)()
+    times = (ctypes.c_double * SAS_MAX_VARIANTS)()
     chosen = ctypes.c_int32()
     _check(lib().subapsnap_autotune(ctx, _ptr(params), int(m), int(reps), times,
                                     ctypes.byref(chosen), _stream(stream)))

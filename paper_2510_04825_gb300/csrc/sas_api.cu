@@ -92,6 +92,7 @@ static void free_ctx(sas_ctx* c) {
   cudaFree(c->XJ);
   cudaFree(c->Shi);
   cudaFree(c->Slo);
+  cudaFree(c->ls_slots);
   cudaFree(c->StHi);
   cudaFree(c->StLo);
   cudaFree(c->Xc32);
@@ -268,6 +269,9 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
       TRY(dmalloc(&c->Slo, (size_t)d->n * rpad * sizeof(float)));
     }
     TRY(launch_make_mixed_copies(c, sst));
+    // float64 M slots for the least-squares variants that keep M in global memory
+    c->ls_slots_n = ls_mixed_slots(c);
+    TRY(cudaMalloc(&c->ls_slots, (size_t)c->ls_slots_n * d->s * d->r * es));
   }
   TRY(cudaStreamSynchronize(sst));
   {
@@ -324,6 +328,7 @@ sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
   c->recon_kernel = 0;
   c->max_refine = 4;
   c->refine_tol = 1e-13;
+  c->krr_seg_points = 1024;
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -761,7 +766,7 @@ sas_status subapsnap_autotune(sas_ctx* c, const double* params, int64_t m, int32
   int* var = mixed ? &c->ls_variant_mixed : &c->ls_variant_plain;
   const int nv = ls_num_variants(mixed);
   if (times_ms)
-    for (int v = 0; v < 16; ++v) times_ms[v] = -1.0;
+    for (int v = 0; v < SAS_MAX_VARIANTS; ++v) times_ms[v] = -1.0;
   const std::string key = tune_key(c, m);
   const int cached = tune_cache_lookup(key);
   if (cached >= 0 && cached < nv) {
@@ -798,7 +803,7 @@ sas_status subapsnap_autotune(sas_ctx* c, const double* params, int64_t m, int32
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     const double per = ms / reps;
-    if (times_ms && v < 16) times_ms[v] = per;
+    if (times_ms && v < SAS_MAX_VARIANTS) times_ms[v] = per;
     if (per < best_ms) {
       best_ms = per;
       best = v;
@@ -818,8 +823,8 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");
   switch (key) {
     case SAS_OPT_RECON_KERNEL:
-      if (value != 0.0 && value != 1.0 && value != 2.0 && value != 3.0)
-        return fail(SAS_EINVAL, "recon kernel must be 0, 1, 2 or 3");
+      if (!(value == 0.0 || value == 1.0 || value == 2.0 || value == 3.0 || value == 4.0))
+        return fail(SAS_EINVAL, "recon kernel must be 0, 1, 2, 3 or 4");
       c->recon_kernel = (int)value;
       return SAS_OK;
     case SAS_OPT_MAX_REFINE:
@@ -829,6 +834,11 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
     case SAS_OPT_REFINE_TOL:
       if (!(value > 0.0 && value < 1.0)) return fail(SAS_EINVAL, "refine tol must be in (0, 1)");
       c->refine_tol = value;
+      return SAS_OK;
+    case SAS_OPT_ASSEMBLY_SEGMENT:
+      if (!(value >= 32.0 && value <= 1048576.0) || std::fmod(value, 32.0) != 0.0)
+        return fail(SAS_EINVAL, "assembly segment must be a multiple of 32 in [32, 2^20]");
+      c->krr_seg_points = (int)value;
       return SAS_OK;
     case SAS_OPT_ASSEMBLY_KERNEL:
       if (value != 0.0 && value != 1.0 && value != 2.0)

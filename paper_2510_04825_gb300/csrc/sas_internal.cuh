@@ -188,8 +188,11 @@ struct sas_ctx {
   // options
   int recon_kernel;    // 0 auto, 1 CUDA cores, 2 tensor cores (64-parameter tiles), 3 (128)
   int krr_kernel;      // kernel rows of the mixed form: 0 auto, 1 CUDA cores, 2 tensor cores
+  int krr_seg_points;  // tensor-core rows: points per TMEM segment before the float64 fold
   int ls_variant_plain;  // launch shape of the plain LS kernel (autotuned)
-  int ls_variant_mixed;  // launch shape (+ float64 M kept or not) of the mixed LS kernel
+  int ls_variant_mixed;  // launch shape (+ where the float64 M lives) of the mixed LS kernel
+  void* ls_slots;        // mixed affine: global float64-M slots, one per resident CTA
+  int64_t ls_slots_n;
   int max_refine;
   double refine_tol;
   // tracing
@@ -239,6 +242,7 @@ cudaError_t launch_ls_mixed(const sas_ctx* c, const double* params, int64_t m, v
                             void* qoi_out, float* ysplit, uint32_t* flags, double* rho,
                             cudaStream_t st, const void* Mg = nullptr);
 size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block);
+int64_t ls_mixed_slots(const sas_ctx* c);
 int ls_num_variants(bool mixed);
 size_t ls_mixed_smem_bytes(const sas_ctx* c);
 cudaError_t launch_reconstruct_f64(const sas_ctx* c, const void* Y, int64_t m, void* out,

@@ -16,8 +16,9 @@
 // (kind::tf32, float32 accumulation in TMEM): ~2^-21 per product, with the
 // float32 exponent range (entries far below 2^-14, common at small sigma, stay
 // normal numbers, which an f16 split would flush).  The TMEM accumulator is
-// folded into a float64 sum in M every kSegChunks x 32 points, so the float32
-// error does not grow with the number of points N.
+// folded into a float64 sum in M every seg_chunks x 32 points (a context
+// option), so the float32 rounding of the accumulator grows with the segment
+// length, not with the number of points N.
 //
 // Structure (one persistent CTA per SM, 14 warps):
 //   warp 0      TMA producer: per 32-point chunk the S_hi and S_lo boxes (nb
@@ -54,7 +55,6 @@ constexpr int kThreads = 32 * (kFirstGenWarp + kGenWarps);  // 448
 constexpr int kRows = 128;       // rows of J per tile (MMA M)
 constexpr int kChunk = 32;       // points per K box (128 B of tf32)
 constexpr int kQ = 2;            // parameters per work unit
-constexpr int kSegChunks = 128;  // 4096 points per TMEM segment before the float64 fold
 constexpr int kABox = kRows * 128;  // one E operand (hi or lo): 16 KB
 constexpr uint32_t kTmemCols = 512;
 
@@ -69,6 +69,7 @@ struct Params {
   int r, s, nb;          // nb: MMA N, r rounded up to a multiple of 16
   int64_t m;
   int njt;               // ceil(s / 128)
+  int seg_chunks;        // 32-point chunks per TMEM segment before the float64 fold
   int num_units;         // njt * ceil(m / 2)
   uint32_t idesc;
   uint32_t bbox;         // bytes of one S box: nb x 128
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t full0 = smem_u32(&bars[0]), gen0 = smem_u32(&bars[2]);
   const uint32_t empty0 = smem_u32(&bars[4]), accfull0 = smem_u32(&bars[6]);
   const uint32_t accempty0 = smem_u32(&bars[8]);
-  const int nseg = (p.nchunks + kSegChunks - 1) / kSegChunks;
+  const int nseg = (p.nchunks + p.seg_chunks - 1) / p.seg_chunks;
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < p.nchunks; ++c, ++it) {
           const int st = it & 1;
           const uint32_t ph = (uint32_t)(it >> 1) & 1u;
-          const int cin = c % kSegChunks;
+          const int cin = c % p.seg_chunks;
           const int buf = seg & 1;
           if (cin == 0 &&
               !mbar_wait(accempty0 + 8 * buf, ((uint32_t)(seg >> 1) & 1u) ^ 1u, &abort_flag,
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           mma_commit(empty0 + 8 * st);
           last = it;
-          if (cin == kSegChunks - 1 || c == p.nchunks - 1) {
+          if (cin == p.seg_chunks - 1 || c == p.nchunks - 1) {
             mma_commit(accfull0 + 8 * buf);
             ++seg;
           }
@@ -449,6 +450,8 @@ cudaError_t launch_krr_assemble_tc(const sas_ctx* c, const double* params, int64
   p.nb = nb;
   p.m = m;
   p.njt = (c->s + kRows - 1) / kRows;
+  p.seg_chunks = c->krr_seg_points / kChunk;
+  if (p.seg_chunks < 1) p.seg_chunks = 1;
   const int64_t units = (int64_t)p.njt * ((m + kQ - 1) / kQ);
   if (units > 2147483647) return cudaErrorInvalidValue;
   p.num_units = (int)units;

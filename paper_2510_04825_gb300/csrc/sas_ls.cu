@@ -291,8 +291,22 @@ static const LsShape kLsShapes[] = {{256, 4}, {128, 4}, {256, 8}, {128, 2}, {256
 constexpr int kNumLsShapes = sizeof(kLsShapes) / sizeof(kLsShapes[0]);
 
 // plain: the smem shapes, then one register-resident variant; mixed: the smem
-// shapes with and without the float64 M, then two register-resident variants
-int ls_num_variants(bool mixed) { return mixed ? 2 * kNumLsShapes + 2 : kNumLsShapes + 1; }
+// shapes with the float64 M in shared memory, without it, two register-resident
+// variants, then the smem shapes with the float64 M in a global slot per CTA
+int ls_num_variants(bool mixed) { return mixed ? 3 * kNumLsShapes + 2 : kNumLsShapes + 1; }
+
+// Mixed variant index -> (shape, where the float64 M lives); -1 for the
+// register-resident variants.
+static int mixed_shape(int v) {
+  if (v < 2 * kNumLsShapes) return v % kNumLsShapes;
+  if (v < 2 * kNumLsShapes + 2) return -1;
+  return v - (2 * kNumLsShapes + 2);
+}
+static int mixed_keep_kind(int v) {
+  if (v < kNumLsShapes) return 1;
+  if (v < 2 * kNumLsShapes + 2) return 0;
+  return 2;
+}
 
 size_t ls_plain_smem_bytes(const sas_ctx* c, int* rows_per_block) {
   const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
@@ -394,7 +408,10 @@ struct LsMixedArgs {
   const TH* wq;
   const double* params;
   int64_t m;
-  int s, r, K, dp, rule, ldt, rpad, max_refine, keep64;
+  int s, r, K, dp, rule, ldt, rpad, max_refine;
+  int keep64;       // M in float64: 0 recomputed per residual, 1 shared memory, 2 global slot
+  TH* M64g;         // keep64 == 2: nslots slots of s x r, one per CTA (L2-resident)
+  int nslots;
   double bJ_norm, tol;
   TH* yout;
   TH* qoi;
@@ -435,8 +452,14 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
   float* tau = reinterpret_cast<float*>(dl + kMaxR);  // kMaxR
   float* nrm2 = tau + kMaxR;                     // 2 (+2 padding)
   TL* P = reinterpret_cast<TL*>(nrm2 + 4);       // ldt x (r+1)
-  TH* M64 = reinterpret_cast<TH*>(
-      (reinterpret_cast<uintptr_t>(P + (size_t)ldt * (r + 1)) + 15) & ~(uintptr_t)15);  // s x r
+  // float64 M: in shared memory (keep64 1), in this CTA's global slot (keep64 2)
+  // or not kept (recomputed from the blocks for every residual)
+  const bool gslot = a.keep64 == 2 && (int)blockIdx.x < a.nslots;
+  const bool keep = a.keep64 == 1 || gslot;
+  TH* M64 = gslot ? a.M64g + (size_t)blockIdx.x * s * r
+                  : reinterpret_cast<TH*>(
+                        (reinterpret_cast<uintptr_t>(P + (size_t)ldt * (r + 1)) + 15) &
+                        ~(uintptr_t)15);  // s x r
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
 
@@ -445,7 +468,7 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
       th32[tid] = to_lo(th[tid]);
     }
     __syncthreads();
-    if (a.keep64) {
+    if (keep) {
       for (int idx = tid; idx < s * r; idx += NT) {
         const int i = idx % s, j = idx / s;
         TH v = zero<TH>();
@@ -507,9 +530,17 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
       double part = 0.0;
       for (int i = tid; i < s; i += NT) {
         TH acc = zero<TH>();
-        if (a.keep64 || a.Mg) {
-          const TH* mrow = a.keep64 ? M64 + i : a.Mg + (size_t)q * s * r + i;
-          for (int j = 0; j < r; ++j) acc += mrow[(size_t)j * s] * y[j];
+        if (keep || a.Mg) {
+          // four independent partial sums: the row product is a latency chain otherwise
+          const TH* mrow = keep ? M64 + i : a.Mg + (size_t)q * s * r + i;
+          TH acc4[4] = {zero<TH>(), zero<TH>(), zero<TH>(), zero<TH>()};
+          int j = 0;
+          for (; j + 4 <= r; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc4[u] += mrow[(size_t)(j + u) * s] * y[j + u];
+          }
+          for (; j < r; ++j) acc4[0] += mrow[(size_t)j * s] * y[j];
+          acc = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
         } else {
           for (int k = 0; k < K; ++k) {
             const TH* g = a.G + (size_t)k * s * r + i;
@@ -628,15 +659,25 @@ static size_t mixed_base_bytes(const sas_ctx* c) {
 
 static bool mixed_keep64(const sas_ctx* c) {
   const size_t eh = c->dtype == SAS_COMPLEX128 ? 16 : 8;
-  // keep M in float64 when the variant asks for it, it fits and leaves room for
-  // two CTAs per SM
-  if (c->ls_variant_mixed >= kNumLsShapes) return false;
+  // keep M in float64 shared memory when the variant asks for it, it fits and
+  // leaves room for two CTAs per SM
+  if (mixed_keep_kind(c->ls_variant_mixed) != 1) return false;
   return mixed_base_bytes(c) + (size_t)c->s * c->r * eh <= kSmemLimit / 2;
 }
 
 size_t ls_mixed_smem_bytes(const sas_ctx* c) {
   const size_t eh = c->dtype == SAS_COMPLEX128 ? 16 : 8;
   return mixed_base_bytes(c) + (mixed_keep64(c) ? (size_t)c->s * c->r * eh : 0);
+}
+
+// Global float64-M slots of a mixed context: one per CTA that can be resident
+// (bounded by the shared memory each CTA needs at least).
+int64_t ls_mixed_slots(const sas_ctx* c) {
+  const size_t base = mixed_base_bytes(c) + 1024;
+  int64_t per_sm = (int64_t)(228 * 1024) / (int64_t)base;
+  if (per_sm > 16) per_sm = 16;
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * c->num_sms;
 }
 
 template <typename TH, typename TL>
@@ -662,6 +703,13 @@ static size_t fill_mixed_args(const sas_ctx* c, const double* params, int64_t m,
   a.rpad = (c->r + 31) / 32 * 32;
   a.max_refine = c->max_refine;
   a.keep64 = mixed_keep64(c) ? 1 : 0;
+  a.M64g = nullptr;
+  a.nslots = 0;
+  if (mixed_keep_kind(c->ls_variant_mixed) == 2 && c->ls_slots) {
+    a.keep64 = 2;
+    a.M64g = (TH*)c->ls_slots;
+    a.nslots = (int)c->ls_slots_n;
+  }
   a.tol = c->refine_tol;
   a.bJ_norm = c->bJ_norm;
   a.yout = (TH*)yout;
@@ -679,12 +727,12 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
   LsMixedArgs<TH, TL> a;
   const size_t smem = fill_mixed_args<TH, TL>(c, params, m, yout, qoi, ysplit, flags, rho, Mg, a);
   if (smem == 0) return cudaErrorInvalidConfiguration;
-  if (c->ls_variant_mixed >= 2 * kNumLsShapes) {
+  const int v = mixed_shape(c->ls_variant_mixed);
+  if (v < 0) {
     if constexpr (sizeof(TH) == 8)
       return launch_mixed_reg(c, a, m, c->ls_variant_mixed - 2 * kNumLsShapes, st);
     return cudaErrorInvalidConfiguration;
   }
-  const int v = c->ls_variant_mixed % kNumLsShapes;
   void (*kern)(LsMixedArgs<TH, TL>) = nullptr;
   switch (v) {
     case 0: kern = ls_mixed_affine_kernel<TH, TL, 256, 4>; break;
@@ -1194,7 +1242,8 @@ static cudaError_t plan_mixed(MultiPlan* pl, sas_ctx* const* ctxs, int n, const 
     if (sm == 0) return cudaErrorInvalidConfiguration;
     smem = sm > smem ? sm : smem;
   }
-  const int v = ctxs[0]->ls_variant_mixed % kNumLsShapes;
+  int v = mixed_shape(ctxs[0]->ls_variant_mixed);
+  if (v < 0) v = ctxs[0]->ls_variant_mixed - 2 * kNumLsShapes;  // register variants: nearest shape
   void (*k)(const LsMixedArgs<TH, TL>*, const int64_t*, int, unsigned long long*) = nullptr;
   switch (v) {
     case 0: k = ls_mixed_multi_kernel<TH, TL, 256, 4>; break;

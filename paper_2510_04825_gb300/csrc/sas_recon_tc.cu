@@ -62,6 +62,7 @@ struct Params {
   int ngroups;     // parameter tiles of one row tile are split into ngroups ranges
   int ntpg;        // parameter tiles per range
   int num_units;   // num_mtiles * ngroups
+  int rotate;      // 1: each unit starts its parameter tiles at a unit-dependent offset
   int tma_store;   // 1: epilogue through shared memory and TMA stores
   int* status;
 };
@@ -70,11 +71,20 @@ constexpr int kStageFloats = 32 * 32;  // one epilogue staging tile: 32 paramete
 
 // Work unit u: row tile u / ngroups, parameter tiles [g ntpg, min((g+1) ntpg, num_ntiles))
 // with g = u % ngroups.  All three roles walk the same units in the same order.
+// With rotate, unit u visits its len tiles starting at offset (u * 37) % len, so
+// that CTAs running at the same time write different parameters' rows.
 __device__ inline void unit_range(const Params& p, int u, int& mt, int& nt0, int& nt1) {
   mt = u / p.ngroups;
   const int g = u % p.ngroups;
   nt0 = g * p.ntpg;
   nt1 = nt0 + p.ntpg < p.num_ntiles ? nt0 + p.ntpg : p.num_ntiles;
+}
+__device__ inline int unit_tile(const Params& p, int u, int nt0, int nt1, int k) {
+  const int len = nt1 - nt0;
+  if (!p.rotate) return nt0 + k;
+  const int off = (int)(((long long)u * 37) % len);
+  const int t = k + off;
+  return nt0 + (t >= len ? t - len : t);
 }
 
 template <int BN>
@@ -144,7 +154,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int u = blockIdx.x; u < p.num_units && !stop; u += gridDim.x) {
         int mt, nt0, nt1;
         unit_range(p, u, mt, nt0, nt1);
-        for (int nt = nt0; nt < nt1; ++nt) {
+        for (int k = 0; k < nt1 - nt0; ++k) {
+          const int nt = unit_tile(p, u, nt0, nt1, k);
           const int s = bt & (kBStages - 1);
           if (!mbar_wait(bempty0 + 8 * s, ((uint32_t)(bt / kBStages) & 1u) ^ 1u, &abort_flag,
                          p.status)) {
@@ -153,12 +164,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           uint8_t* Bhi = B0 + (size_t)s * 2 * bop;
           mbar_expect_tx(bfull0 + 8 * s, 2 * bop);
-          for (int k = 0; k < kb; ++k) {
-            tma_load_2d(smem_u32(Bhi + k * kBBox), &tmBhi, k * 32, nt * kBN, bfull0 + 8 * s);
-            tma_load_2d(smem_u32(Bhi + bop + k * kBBox), &tmBlo, k * 32, nt * kBN, bfull0 + 8 * s);
+          for (int kx = 0; kx < kb; ++kx) {
+            tma_load_2d(smem_u32(Bhi + kx * kBBox), &tmBhi, kx * 32, nt * kBN, bfull0 + 8 * s);
+            tma_load_2d(smem_u32(Bhi + bop + kx * kBBox), &tmBlo, kx * 32, nt * kBN,
+                        bfull0 + 8 * s);
           }
           b_issued[s] = bt++;
-          if (nt == nt0) {
+          if (k == 0) {
             // the S tile frees when the last MMA of the previous unit completes; the
             // accumulators queued ahead of the epilogue cover the reload
             if (!mbar_wait(aempty, ((uint32_t)at & 1u) ^ 1u, &abort_flag, p.status)) {
@@ -166,9 +178,9 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             mbar_expect_tx(afull, 2 * aop);
-            for (int k = 0; k < kb; ++k) {
-              tma_load_2d(smem_u32(A0 + k * kABox), &tmAhi, k * 32, mt * kBM, afull);
-              tma_load_2d(smem_u32(A0 + aop + k * kABox), &tmAlo, k * 32, mt * kBM, afull);
+            for (int kx = 0; kx < kb; ++kx) {
+              tma_load_2d(smem_u32(A0 + kx * kABox), &tmAhi, kx * 32, mt * kBM, afull);
+              tma_load_2d(smem_u32(A0 + aop + kx * kABox), &tmAlo, kx * 32, mt * kBM, afull);
             }
             a_issued = at++;
           }
@@ -193,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (nt0 >= nt1) continue;
         if (!mbar_wait(afull, (uint32_t)ua & 1u, &abort_flag, p.status)) break;
         const uint8_t* Ahi = A0;
-        for (int nt = nt0; nt < nt1; ++nt) {
+        for (int k = 0; k < nt1 - nt0; ++k) {
           const int s = t & (kBStages - 1), acc = t & (kAcc - 1);
           if (!mbar_wait(bfull0 + 8 * s, (uint32_t)(t / kBStages) & 1u, &abort_flag, p.status) ||
               !mbar_wait(tempty0 + 8 * acc, ((uint32_t)(t >> 2) & 1u) ^ 1u, &abort_flag,
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           mma_commit(bempty0 + 8 * s);
-          if (nt == nt1 - 1) mma_commit(aempty);
+          if (k == nt1 - nt0 - 1) mma_commit(aempty);
           mma_commit(tfull0 + 8 * acc);
           last = t++;
         }
@@ -235,7 +247,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       int mt, nt0, nt1;
       unit_range(p, u, mt, nt0, nt1);
       const int64_t xs = (int64_t)mt * kBM + q * 32;
-      for (int nt = nt0; nt < nt1; ++nt, ++t) {
+      for (int k = 0; k < nt1 - nt0; ++k, ++t) {
+        const int nt = unit_tile(p, u, nt0, nt1, k);
         const int acc = t & (kAcc - 1);
         const bool ok = __all_sync(
             0xffffffffu, mbar_wait(tfull0 + 8 * acc, (uint32_t)(t >> 2) & 1u, &abort_flag, p.status));
@@ -383,7 +396,7 @@ void reconstruct_tc_split(int64_t n, int64_t m, int num_sms, int bn, int* num_mt
 
 template <int BN>
 static cudaError_t launch_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
-                             cudaStream_t st) {
+                             bool rotate, cudaStream_t st) {
   if (m > 2147483647 - BN || c->n > 2147483647 - tc::kBM) return cudaErrorInvalidValue;
   const int rpad = (c->r + 31) / 32 * 32;
   const size_t smem = tc_smem_bytes<BN>(rpad);
@@ -411,18 +424,20 @@ static cudaError_t launch_tc(const sas_ctx* c, const float* ysplit, int64_t m, f
   const int64_t units = (int64_t)p.num_mtiles * p.ngroups;
   if (units > 2147483647) return cudaErrorInvalidValue;
   p.num_units = (int)units;
+  p.rotate = rotate ? 1 : 0;
   p.status = c->dev_status;
   const int grid = (int)(units < c->num_sms ? units : c->num_sms);
   tc::reconstruct_tc_kernel<BN><<<grid, tc::kThreads, smem, st>>>(mAhi, mAlo, mBhi, mBlo, mOut, p);
   return cudaGetLastError();
 }
 
-// recon_kernel 3 selects 128-parameter tiles; otherwise 64-parameter tiles.
+// recon_kernel: 2 = 64-parameter tiles; 3 = 128-parameter tiles; 0 (automatic)
+// and 4 = 128-parameter tiles visited in a unit-dependent rotated order.
 cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                   cudaStream_t st) {
   if (m == 0) return cudaSuccess;
-  return c->recon_kernel == 3 ? launch_tc<128>(c, ysplit, m, out, st)
-                              : launch_tc<64>(c, ysplit, m, out, st);
+  if (c->recon_kernel == 2) return launch_tc<64>(c, ysplit, m, out, false, st);
+  return launch_tc<128>(c, ysplit, m, out, c->recon_kernel != 3, st);
 }
 
 }  // namespace sas

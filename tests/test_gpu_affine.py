@@ -252,7 +252,9 @@ def test_every_ls_variant_and_autotune(c1_small, mode):
     p = case.prob
     params = p.test_params[:100]
     Yo, rho_o = case.oracle_solve(params)
-    nvar = 6 if mode == api.SAS_MODE_PLAIN else 12  # shared-memory and register-resident shapes
+    # plain: 5 shared-memory shapes + 1 register-resident; mixed: 5 shapes with float64 M
+    # in shared memory, 5 without, 2 register-resident, 5 with M in a global slot per CTA
+    nvar = 6 if mode == api.SAS_MODE_PLAIN else 17
     P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
     solver = AffineSolver(p, case.S, case.J, mode=mode, device=DEV)
     bound = _mixed_bound(p, case.S, case.J, params, Yo, rho_o)
@@ -269,6 +271,25 @@ def test_every_ls_variant_and_autotune(c1_small, mode):
     chosen, times = api.subapsnap_autotune(solver.ctx, P, len(params), 2)
     print(f"autotune mode {mode}: chosen {chosen}, times {[round(t, 4) for t in times[:nvar]]}")
     assert 0 <= chosen < nvar and times[chosen] > 0
+    solver.close()
+
+
+def test_global_slot_variants_complex(c3_small):
+    """Mixed complex solve with the float64 M kept in a global slot per CTA."""
+    case = c3_small
+    p = case.prob
+    params = p.test_params[:60]
+    Yo, rho_o = case.oracle_solve(params)
+    bound = _mixed_bound(p, case.S, case.J, params, Yo, rho_o)
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
+    solver = AffineSolver(p, case.S, case.J, mode=api.SAS_MODE_MIXED, device=DEV)
+    for v in range(12, 17):
+        api.subapsnap_set_option(solver.ctx, api.SAS_OPT_LS_VARIANT, v)
+        Y = torch.empty((len(params), p.r), dtype=torch.complex128, device=DEV)
+        solver.solve(P, api.SAS_OUT_Y, Y)
+        torch.cuda.synchronize()
+        err = rel_err_rows(Y.cpu().numpy(), Yo)
+        assert (err <= bound).all(), (v, err.max())
     solver.close()
 
 
