@@ -20,7 +20,7 @@
 // option), so the float32 rounding of the accumulator grows with the segment
 // length, not with the number of points N.
 //
-// Structure (one persistent CTA per SM, 14 warps):
+// Structure (one persistent CTA per SM, 22 warps):
 //   warp 0      TMA producer: per 32-point chunk the S_hi and S_lo boxes (nb
 //               rows x 32 points, K-major, 128-byte swizzle) and the chunk's
 //               coordinates (bulk copy) into a 2-stage ring;
@@ -29,9 +29,10 @@
 //   warps 2-5   fold: at each segment end, tcgen05.ld of the accumulators
 //               (lane quarter = warp % 4) and a float64 read-add-write into M;
 //               the last segment also adds lambda S_J;
-//   warps 6-13  generators: E for the chunk (one row of J and 16 points per
-//               thread, distances shared by the pair of parameters), tf32
-//               split, written in the swizzled K-major operand layout.
+//   warps 6-21  generators: E for the chunk (one row of J and 8 points per
+//               thread, distances shared by the pair of parameters, two points
+//               per packed f32x2 instruction), tf32 split, written in the
+//               swizzled K-major operand layout.
 // Work unit: one 128-row tile of J and a pair of parameters, reduced over all
 // points; the two accumulators of the pair are double-buffered in TMEM (2 x 2
 // x nb <= 512 columns) so that the fold of one segment overlaps the MMAs of
@@ -49,9 +50,9 @@ namespace krrtc {
 
 using namespace tc;
 
-constexpr int kGenWarps = 8;
+constexpr int kGenWarps = 16;
 constexpr int kFirstGenWarp = 6;
-constexpr int kThreads = 32 * (kFirstGenWarp + kGenWarps);  // 448
+constexpr int kThreads = 32 * (kFirstGenWarp + kGenWarps);  // 704
 constexpr int kRows = 128;       // rows of J per tile (MMA M)
 constexpr int kChunk = 32;       // points per K box (128 B of tf32)
 constexpr int kQ = 2;            // parameters per work unit
@@ -60,7 +61,7 @@ constexpr uint32_t kTmemCols = 512;
 
 struct Params {
   const float* xj;       // s x 2dp: hi then lo coordinates of the rows of J (zero padded)
-  const float* xc;       // npad x 2dp: hi then lo coordinates of every point (zero padded)
+  const float* xc;       // per 32-point chunk: hi [dp][32] then lo [dp][32] (zero padded)
   const double* params;  // m x 2: (sigma, lambda)
   const double* SJ;      // s x r (ld s)
   double* M;             // m x (s x r), column-major per parameter (ld s)
@@ -82,6 +83,38 @@ __device__ inline float tf32_hi(float x) {
   uint32_t u = __float_as_uint(x);
   u = (u + 0x1000u) & 0xffffe000u;
   return __uint_as_float(u);
+}
+
+// Packed pairs of float32 (low half = first element) and the f32x2 arithmetic
+// of sm_100-family SMs: two lanes of float32 per instruction.
+typedef unsigned long long f2;
+__device__ inline f2 f2_pack(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ inline void f2_unpack(f2 v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ inline f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ inline f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ inline f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ inline f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
 }
 
 __device__ inline float ex2_approx(float x) {
@@ -256,30 +289,32 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- generators: row i of the J tile, points 16h .. 16h + 15 of each chunk
+    // ---------------- generators: row i of the J tile, points 8 qr .. 8 qr + 7 of each chunk
     const int gt = threadIdx.x - kFirstGenWarp * 32;
-    const int i = gt >> 1, h = gt & 1;
+    const int i = gt >> 2, qr = gt & 3;
     int it = 0;
     bool stop = false;
     for (int u = blockIdx.x; u < p.num_units && !stop; u += gridDim.x) {
       const int jt = u % p.njt, qg = u / p.njt;
       const int row = jt * kRows + i;
       const bool valid = row < p.s;
-      float4 xh[DP4], xl[DP4];
+      // this row's coordinates, each duplicated into both halves of a packed pair
+      f2 xh[4 * DP4], xl[4 * DP4];
 #pragma unroll
-      for (int t = 0; t < DP4; ++t) {
-        xh[t] = valid ? reinterpret_cast<const float4*>(p.xj + (size_t)row * 2 * p.dp)[t]
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
-        xl[t] = valid ? reinterpret_cast<const float4*>(p.xj + (size_t)row * 2 * p.dp + p.dp)[t]
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int t = 0; t < 4 * DP4; ++t) {
+        const float h = valid ? p.xj[(size_t)row * 2 * p.dp + t] : 0.f;
+        const float l = valid ? p.xj[(size_t)row * 2 * p.dp + p.dp + t] : 0.f;
+        xh[t] = f2_pack(h, h);
+        xl[t] = f2_pack(l, l);
       }
-      float cq[kQ];
+      f2 cq[kQ];
 #pragma unroll
       for (int q = 0; q < kQ; ++q) {
         int64_t qi = (int64_t)qg * kQ + q;
         if (qi >= p.m) qi = p.m - 1;  // a lone last parameter: its twin's output is dropped
         const double sg = p.params[qi * 2];
-        cq[q] = (float)(-1.4426950408889634 / (2.0 * sg * sg));  // -log2(e) / (2 sigma^2)
+        const float c = (float)(-1.4426950408889634 / (2.0 * sg * sg));  // -log2(e) / (2 sigma^2)
+        cq[q] = f2_pack(c, c);
       }
       // swizzled K-major offset of this thread's row: 8-row groups of 1024 B, 16-byte
       // chunk index XOR (row % 8)
@@ -294,43 +329,43 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         uint8_t* sb = base + (size_t)st * p.stage_bytes;
-        const float4* C = reinterpret_cast<const float4*>(sb + coff);
-        float dist[16];
+        // chunk coordinates, dimension-major: hi [t][32 points], then lo [t][32 points]
+        const float* C = reinterpret_cast<const float*>(sb + coff) + qr * 8;
+        f2 acc[4] = {0ull, 0ull, 0ull, 0ull};  // squared distances of points (0,1) .. (6,7)
 #pragma unroll
-        for (int pt = 0; pt < 16; ++pt) {
-          const float4* cp = C + (size_t)(h * 16 + pt) * 2 * DP4;
-          float acc = 0.f;
+        for (int t = 0; t < 4 * DP4; ++t) {
+          const ulonglong2 h01 = *reinterpret_cast<const ulonglong2*>(C + t * 32);
+          const ulonglong2 h23 = *reinterpret_cast<const ulonglong2*>(C + t * 32 + 4);
+          const ulonglong2 l01 = *reinterpret_cast<const ulonglong2*>(C + (4 * DP4 + t) * 32);
+          const ulonglong2 l23 = *reinterpret_cast<const ulonglong2*>(C + (4 * DP4 + t) * 32 + 4);
+          const f2 ch[4] = {h01.x, h01.y, h23.x, h23.y};
+          const f2 cl[4] = {l01.x, l01.y, l23.x, l23.y};
 #pragma unroll
-          for (int t = 0; t < DP4; ++t) {
-            const float4 ch = cp[t], cl = cp[DP4 + t];
-            float df;
-            df = (xh[t].x - ch.x) + (xl[t].x - cl.x);
-            acc = fmaf(df, df, acc);
-            df = (xh[t].y - ch.y) + (xl[t].y - cl.y);
-            acc = fmaf(df, df, acc);
-            df = (xh[t].z - ch.z) + (xl[t].z - cl.z);
-            acc = fmaf(df, df, acc);
-            df = (xh[t].w - ch.w) + (xl[t].w - cl.w);
-            acc = fmaf(df, df, acc);
+          for (int j = 0; j < 4; ++j) {
+            const f2 df = f2_add(f2_sub(xh[t], ch[j]), f2_sub(xl[t], cl[j]));
+            acc[j] = f2_fma(df, df, acc[j]);
           }
-          dist[pt] = acc;
         }
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
           uint8_t* ehi = sb + (size_t)(q * 2) * kABox;
           uint8_t* elo = ehi + kABox;
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            float e[4], hi[4], lo[4];
+          for (int v = 0; v < 2; ++v) {
+            float e[4];
+            f2_unpack(f2_mul(acc[2 * v], cq[q]), e[0], e[1]);
+            f2_unpack(f2_mul(acc[2 * v + 1], cq[q]), e[2], e[3]);
+            float hi[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-              e[k] = valid ? ex2_approx(dist[v * 4 + k] * cq[q]) : 0.f;
+              e[k] = valid ? ex2_approx(e[k]) : 0.f;
               hi[k] = tf32_hi(e[k]);
-              lo[k] = e[k] - hi[k];
             }
-            const uint32_t off = rowoff + (uint32_t)(((h * 4 + v) ^ (i & 7)) * 16);
+            const f2 lo01 = f2_sub(f2_pack(e[0], e[1]), f2_pack(hi[0], hi[1]));
+            const f2 lo23 = f2_sub(f2_pack(e[2], e[3]), f2_pack(hi[2], hi[3]));
+            const uint32_t off = rowoff + (uint32_t)(((qr * 2 + v) ^ (i & 7)) * 16);
             *reinterpret_cast<float4*>(ehi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<float4*>(elo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+            *reinterpret_cast<ulonglong2*>(elo + off) = make_ulonglong2(lo01, lo23);
           }
         }
         fence_async_smem();
@@ -364,7 +399,8 @@ static bool make_s_map(CUtensorMap* map, const float* base, int64_t npad, int nb
 }
 
 // Setup copies: S^T split into tf32 hi / float32 lo (nb x npad, zero padded),
-// coordinates of every point and of the rows of J as float32 hi / lo pairs.
+// coordinates of every point (per 32-point chunk, dimension-major) and of the
+// rows of J (row-major) as float32 hi / lo pairs.
 __global__ void krr_tc_copies_kernel(const double* S, int64_t ldS, int64_t n, int r, int nb,
                                      int64_t npad, const double* X, const double* XJ, int d, int dp,
                                      int s, float* sthi, float* stlo, float* xc, float* xj) {
@@ -389,8 +425,10 @@ __global__ void krr_tc_copies_kernel(const double* S, int64_t ldS, int64_t n, in
     const int t = (int)(idx % dp);
     const double x = (k < n && t < d) ? X[k * d + t] : 0.0;
     const float h = (float)x;
-    xc[k * 2 * dp + t] = h;
-    xc[k * 2 * dp + dp + t] = (float)(x - (double)h);
+    // chunk c = k / 32 holds hi [t][32] then lo [t][32]
+    const int64_t cbase = (k / 32) * 64 * dp;
+    xc[cbase + (int64_t)t * 32 + (k % 32)] = h;
+    xc[cbase + (int64_t)(dp + t) * 32 + (k % 32)] = (float)(x - (double)h);
   }
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total_j; idx += stride) {
     const int64_t j = idx / dp;
