@@ -175,9 +175,12 @@ def run_gpu(args):
                          blocks_device=blocks)
     # autotune the least-squares launch shape of both forms on this batch
     tune = {}
-    for name, sv in (("chosen", chosen), ("plain", plain)):
-        v, times = api.subapsnap_autotune(sv.ctx, P, M, 2)
-        tune[name] = {"variant": v, "ms": {str(i): round(t, 4) for i, t in enumerate(times) if t >= 0}}
+    if args.ls_variant is not None:  # profiling runs: a fixed launch shape, no tuning launches
+        api.subapsnap_set_option(chosen.ctx, api.SAS_OPT_LS_VARIANT, args.ls_variant)
+    else:
+        for name, sv in (("chosen", chosen), ("plain", plain)):
+            v, times = api.subapsnap_autotune(sv.ctx, P, M, 2)
+            tune[name] = {"variant": v, "ms": {str(i): round(t, 4) for i, t in enumerate(times) if t >= 0}}
     n = prob.n
     out32 = torch.empty((M, n), dtype=torch.float32, device=device)
     out64 = torch.empty((M, n), dtype=torch.float64, device=device)
@@ -770,6 +773,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 form")
     ap.add_argument("--quick", action="store_true", help="time the chosen form only (profiling runs)")
     ap.add_argument("--grid", type=int, default=GRID, help="interior grid side (profiling runs use 512)")
+    ap.add_argument("--ls-variant", type=int, default=None,
+                    help="fixed least-squares launch shape of the chosen form, no autotuning")
     ap.add_argument("--workload", default="diffusion_2d",
                     choices=["diffusion_2d", "transfer_function", "reaction_diffusion_1d", "kernel_ridge",
                              "surrogate_diffusion_2d"])
