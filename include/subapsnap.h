@@ -219,10 +219,12 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
 
 /* Per-context options (subapsnap_set_option).  Not in the paper.
  *  SAS_OPT_RECON_KERNEL: mixed-form reconstruction kernel: 0 = automatic
- *      (tensor cores when r <= 64, as 4), 1 = CUDA cores, 2 = tensor cores
+ *      (tensor cores when r <= 64, as 5), 1 = CUDA cores, 2 = tensor cores
  *      (tcgen05, kind::tf32, three split products) with 64-parameter tiles,
- *      3 = tensor cores with 128-parameter tiles, 4 = as 3 with the parameter
- *      tiles of each row tile visited in a rotated order.
+ *      3 = as 2 with 128-parameter tiles, 4 = as 3 with the parameter tiles
+ *      of each row tile visited in a rotated order, 5 = tensor cores
+ *      (kind::f16) on power-of-two-scaled f16 splits of S and y, three
+ *      products into two accumulators, 128-parameter tiles.
  *  SAS_OPT_MAX_REFINE: most refinement steps of the mixed solve (0..16,
  *      default 4).
  *  SAS_OPT_REFINE_TOL: refinement stops when ||delta|| <= tol ||y||

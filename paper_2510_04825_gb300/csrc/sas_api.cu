@@ -93,6 +93,9 @@ static void free_ctx(sas_ctx* c) {
   cudaFree(c->Shi);
   cudaFree(c->Slo);
   cudaFree(c->ls_slots);
+  cudaFree(c->S16hi);
+  cudaFree(c->S16lo);
+  cudaFree(c->ysplit16);
   cudaFree(c->StHi);
   cudaFree(c->StLo);
   cudaFree(c->Xc32);
@@ -179,6 +182,18 @@ static sas_status ensure_scratch(sas_ctx* c, int64_t m, bool split, cudaStream_t
       e = cudaMalloc((void**)&c->ysplit, need2);
       if (e != cudaSuccess) return cuda_fail(e, "solve_batch scratch");
       c->ysplit_bytes = need2;
+    }
+    // f16 form of the reconstruction: hi and lo (2 x m x 64 f16) and m float scales
+    const size_t need3 = (size_t)m * (2 * 64 * 2 + 4);
+    if (c->S16hi && need3 > c->ysplit16_bytes) {
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+      cudaFree(c->ysplit16);
+      c->ysplit16 = nullptr;
+      c->ysplit16_bytes = 0;
+      e = cudaMalloc(&c->ysplit16, need3);
+      if (e != cudaSuccess) return cuda_fail(e, "solve_batch scratch");
+      c->ysplit16_bytes = need3;
     }
   }
   return SAS_OK;
@@ -269,6 +284,7 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
       TRY(dmalloc(&c->Slo, (size_t)d->n * rpad * sizeof(float)));
     }
     TRY(launch_make_mixed_copies(c, sst));
+    TRY(setup_f16_basis(c, sst));
     // float64 M slots for the least-squares variants that keep M in global memory
     c->ls_slots_n = ls_mixed_slots(c);
     TRY(cudaMalloc(&c->ls_slots, (size_t)c->ls_slots_n * d->s * d->r * es));
@@ -361,6 +377,7 @@ sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
     TRYK(dmalloc(&c->Shi, (size_t)d->n * rpad * sizeof(float)));
     TRYK(dmalloc(&c->Slo, (size_t)d->n * rpad * sizeof(float)));
     TRYK(launch_make_mixed_copies(c, sst));
+    TRYK(setup_f16_basis(c, sst));
     // tensor-core kernel rows: S^T split, float32 hi/lo coordinates
     const int nb = krr_tc_nb(d->r), dp = krr_tc_dp(d->d);
     const int64_t npad = krr_tc_npad(d->n);
@@ -823,8 +840,8 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");
   switch (key) {
     case SAS_OPT_RECON_KERNEL:
-      if (!(value == 0.0 || value == 1.0 || value == 2.0 || value == 3.0 || value == 4.0))
-        return fail(SAS_EINVAL, "recon kernel must be 0, 1, 2, 3 or 4");
+      if (!(value >= 0.0 && value <= 5.0 && value == (double)(int)value))
+        return fail(SAS_EINVAL, "recon kernel must be 0, 1, 2, 3, 4 or 5");
       c->recon_kernel = (int)value;
       return SAS_OK;
     case SAS_OPT_MAX_REFINE:

@@ -169,6 +169,9 @@ struct sas_ctx {
   double* XJ;          // kernel family: s x d
   float* Shi;          // mixed reconstruction: high tf32 part of S, n x r (ld n)
   float* Slo;          // low part
+  void* S16hi;         // mixed reconstruction, f16 form: 2^shift S high part, n x 64 (f16)
+  void* S16lo;         // 2^11-scaled remainder
+  int s16_shift;       // power-of-two scale of S in the f16 split
   float* StHi;         // mixed kernel family: S^T tf32 high part, nb x npad (tensor-core rows)
   float* StLo;         // low part
   float* Xc32;         // mixed kernel family: float32 hi/lo coordinates of every point
@@ -181,12 +184,14 @@ struct sas_ctx {
   size_t ybuf_bytes;
   float* ysplit;       // mixed: y split into tf32 hi/lo, 2 x m x r
   size_t ysplit_bytes;
+  void* ysplit16;      // mixed, f16 reconstruction: y split into f16 hi/lo (2 x m x 64) + m scales
+  size_t ysplit16_bytes;
   int* dev_status;     // device status word
   int num_sms;
   int ls_blocks_per_sm;
   void* surrogate;     // learned surrogate network (sas_mlp.cu), or null
   // options
-  int recon_kernel;    // 0 auto, 1 CUDA cores, 2 tensor cores (64-parameter tiles), 3 (128)
+  int recon_kernel;    // 0 auto, 1 CUDA cores, 2-4 tensor cores tf32, 5 tensor cores f16
   int krr_kernel;      // kernel rows of the mixed form: 0 auto, 1 CUDA cores, 2 tensor cores
   int krr_seg_points;  // tensor-core rows: points per TMEM segment before the float64 fold
   int ls_variant_plain;  // launch shape of the plain LS kernel (autotuned)
@@ -225,6 +230,7 @@ struct TraceScope {
 cudaError_t launch_gather_blocks(const sas_ctx* c, cudaStream_t st);
 cudaError_t launch_gather_vectors(const sas_ctx* c, const double* cvec, cudaStream_t st);
 cudaError_t launch_make_mixed_copies(const sas_ctx* c, cudaStream_t st);
+cudaError_t setup_f16_basis(sas_ctx* c, cudaStream_t st);  // S16hi / S16lo / s16_shift
 // tensor-core kernel rows (sas_krr_tc.cu)
 int krr_tc_nb(int r);
 int64_t krr_tc_npad(int64_t n);

@@ -20,7 +20,7 @@
 // option), so the float32 rounding of the accumulator grows with the segment
 // length, not with the number of points N.
 //
-// Structure (one persistent CTA per SM, 22 warps):
+// Structure (one persistent CTA per SM, 14 warps):
 //   warp 0      TMA producer: per 32-point chunk the S_hi and S_lo boxes (nb
 //               rows x 32 points, K-major, 128-byte swizzle) and the chunk's
 //               coordinates (bulk copy) into a 2-stage ring;
@@ -29,10 +29,12 @@
 //   warps 2-5   fold: at each segment end, tcgen05.ld of the accumulators
 //               (lane quarter = warp % 4) and a float64 read-add-write into M;
 //               the last segment also adds lambda S_J;
-//   warps 6-21  generators: E for the chunk (one row of J and 8 points per
-//               thread, distances shared by the pair of parameters, two points
-//               per packed f32x2 instruction), tf32 split, written in the
-//               swizzled K-major operand layout.
+//   warps 6-13  generators: E for the chunk (4 rows of J x 4 points per
+//               thread: the rows' coordinates stay in registers as packed row
+//               pairs, each point's coordinates are read once per chunk;
+//               distances shared by the pair of parameters, two rows per f32x2
+//               instruction), tf32 split, written in the swizzled K-major
+//               operand layout.
 // Work unit: one 128-row tile of J and a pair of parameters, reduced over all
 // points; the two accumulators of the pair are double-buffered in TMEM (2 x 2
 // x nb <= 512 columns) so that the fold of one segment overlaps the MMAs of
@@ -50,9 +52,9 @@ namespace krrtc {
 
 using namespace tc;
 
-constexpr int kGenWarps = 16;
+constexpr int kGenWarps = 8;
 constexpr int kFirstGenWarp = 6;
-constexpr int kThreads = 32 * (kFirstGenWarp + kGenWarps);  // 704
+constexpr int kThreads = 32 * (kFirstGenWarp + kGenWarps);  // 448
 constexpr int kRows = 128;       // rows of J per tile (MMA M)
 constexpr int kChunk = 32;       // points per K box (128 B of tf32)
 constexpr int kQ = 2;            // parameters per work unit
@@ -124,7 +126,7 @@ __device__ inline float ex2_approx(float x) {
 }
 
 template <int DP4>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(144)  // 448 threads x 144 registers fit one SM
     krr_tc_kernel(const __grid_constant__ CUtensorMap tmShi,
                   const __grid_constant__ CUtensorMap tmSlo, Params p) {
   extern __shared__ uint8_t smem_raw[];
@@ -289,23 +291,35 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else {
-    // ---------------- generators: row i of the J tile, points 8 qr .. 8 qr + 7 of each chunk
+    // ---------------- generators: rows 4 rg .. 4 rg + 3 of the J tile, points 4 pg .. 4 pg + 3
+    // of each chunk; warp w holds row groups 4w .. 4w + 3 (lane = 8 rgl + pg)
     const int gt = threadIdx.x - kFirstGenWarp * 32;
-    const int i = gt >> 2, qr = gt & 3;
+    const int rg = (gt >> 5) * 4 + ((gt & 31) >> 3), pg = gt & 7;
+    constexpr int DP = 4 * DP4;
     int it = 0;
     bool stop = false;
     for (int u = blockIdx.x; u < p.num_units && !stop; u += gridDim.x) {
       const int jt = u % p.njt, qg = u / p.njt;
-      const int row = jt * kRows + i;
-      const bool valid = row < p.s;
-      // this row's coordinates, each duplicated into both halves of a packed pair
-      f2 xh[4 * DP4], xl[4 * DP4];
+      const int row0 = jt * kRows + 4 * rg;
+      bool valid[4];
 #pragma unroll
-      for (int t = 0; t < 4 * DP4; ++t) {
-        const float h = valid ? p.xj[(size_t)row * 2 * p.dp + t] : 0.f;
-        const float l = valid ? p.xj[(size_t)row * 2 * p.dp + p.dp + t] : 0.f;
-        xh[t] = f2_pack(h, h);
-        xl[t] = f2_pack(l, l);
+      for (int a = 0; a < 4; ++a) valid[a] = row0 + a < p.s;
+      // rows' coordinates as packed pairs: xh[rp][t] = (x_{row 2rp}[t], x_{row 2rp+1}[t])
+      f2 xh[2][DP], xl[2][DP];
+#pragma unroll
+      for (int rp = 0; rp < 2; ++rp) {
+#pragma unroll
+        for (int t = 0; t < DP; ++t) {
+          float h[2], l[2];
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const int a = 2 * rp + b;
+            h[b] = valid[a] ? p.xj[(size_t)(row0 + a) * 2 * p.dp + t] : 0.f;
+            l[b] = valid[a] ? p.xj[(size_t)(row0 + a) * 2 * p.dp + p.dp + t] : 0.f;
+          }
+          xh[rp][t] = f2_pack(h[0], h[1]);
+          xl[rp][t] = f2_pack(l[0], l[1]);
+        }
       }
       f2 cq[kQ];
 #pragma unroll
@@ -316,9 +330,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float c = (float)(-1.4426950408889634 / (2.0 * sg * sg));  // -log2(e) / (2 sigma^2)
         cq[q] = f2_pack(c, c);
       }
-      // swizzled K-major offset of this thread's row: 8-row groups of 1024 B, 16-byte
-      // chunk index XOR (row % 8)
-      const uint32_t rowoff = (uint32_t)(i >> 3) * 1024u + (uint32_t)(i & 7) * 128u;
       for (int c = 0; c < p.nchunks; ++c, ++it) {
         const int st = it & 1;
         const bool ok =
@@ -330,42 +341,51 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         uint8_t* sb = base + (size_t)st * p.stage_bytes;
         // chunk coordinates, dimension-major: hi [t][32 points], then lo [t][32 points]
-        const float* C = reinterpret_cast<const float*>(sb + coff) + qr * 8;
-        f2 acc[4] = {0ull, 0ull, 0ull, 0ull};  // squared distances of points (0,1) .. (6,7)
+        const float* C = reinterpret_cast<const float*>(sb + coff) + pg * 4;
+        f2 acc[2][4];  // acc[rp][e]: squared distances of rows (2rp, 2rp+1) to point e
 #pragma unroll
-        for (int t = 0; t < 4 * DP4; ++t) {
-          const ulonglong2 h01 = *reinterpret_cast<const ulonglong2*>(C + t * 32);
-          const ulonglong2 h23 = *reinterpret_cast<const ulonglong2*>(C + t * 32 + 4);
-          const ulonglong2 l01 = *reinterpret_cast<const ulonglong2*>(C + (4 * DP4 + t) * 32);
-          const ulonglong2 l23 = *reinterpret_cast<const ulonglong2*>(C + (4 * DP4 + t) * 32 + 4);
-          const f2 ch[4] = {h01.x, h01.y, h23.x, h23.y};
-          const f2 cl[4] = {l01.x, l01.y, l23.x, l23.y};
+        for (int rp = 0; rp < 2; ++rp)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const f2 df = f2_add(f2_sub(xh[t], ch[j]), f2_sub(xl[t], cl[j]));
-            acc[j] = f2_fma(df, df, acc[j]);
+          for (int e = 0; e < 4; ++e) acc[rp][e] = 0ull;
+#pragma unroll
+        for (int t = 0; t < DP; ++t) {
+          const float4 ch = *reinterpret_cast<const float4*>(C + t * 32);
+          const float4 cl = *reinterpret_cast<const float4*>(C + (DP + t) * 32);
+          const float chv[4] = {ch.x, ch.y, ch.z, ch.w}, clv[4] = {cl.x, cl.y, cl.z, cl.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const f2 CH = f2_pack(chv[e], chv[e]), CL = f2_pack(clv[e], clv[e]);
+#pragma unroll
+            for (int rp = 0; rp < 2; ++rp) {
+              const f2 df = f2_add(f2_sub(xh[rp][t], CH), f2_sub(xl[rp][t], CL));
+              acc[rp][e] = f2_fma(df, df, acc[rp][e]);
+            }
           }
         }
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
           uint8_t* ehi = sb + (size_t)(q * 2) * kABox;
           uint8_t* elo = ehi + kABox;
+          float ev[4][4];  // ev[row a][point e]
 #pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            float e[4];
-            f2_unpack(f2_mul(acc[2 * v], cq[q]), e[0], e[1]);
-            f2_unpack(f2_mul(acc[2 * v + 1], cq[q]), e[2], e[3]);
-            float hi[4];
+          for (int rp = 0; rp < 2; ++rp)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              e[k] = valid ? ex2_approx(e[k]) : 0.f;
-              hi[k] = tf32_hi(e[k]);
+            for (int e = 0; e < 4; ++e) f2_unpack(f2_mul(acc[rp][e], cq[q]), ev[2 * rp][e], ev[2 * rp + 1][e]);
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = 4 * rg + a;
+            float hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float x = valid[a] ? ex2_approx(ev[a][e]) : 0.f;
+              hi[e] = tf32_hi(x);
+              lo[e] = x - hi[e];
             }
-            const f2 lo01 = f2_sub(f2_pack(e[0], e[1]), f2_pack(hi[0], hi[1]));
-            const f2 lo23 = f2_sub(f2_pack(e[2], e[3]), f2_pack(hi[2], hi[3]));
-            const uint32_t off = rowoff + (uint32_t)(((qr * 2 + v) ^ (i & 7)) * 16);
+            // swizzled K-major: 8-row groups of 1024 B, 16-byte chunk pg XOR (row % 8)
+            const uint32_t off =
+                (uint32_t)(i >> 3) * 1024u + (uint32_t)(i & 7) * 128u + (uint32_t)((pg ^ (i & 7)) * 16);
             *reinterpret_cast<float4*>(ehi + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
-            *reinterpret_cast<ulonglong2*>(elo + off) = make_ulonglong2(lo01, lo23);
+            *reinterpret_cast<float4*>(elo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
           }
         }
         fence_async_smem();

@@ -28,6 +28,8 @@
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel
 // records SAS_ETIMEOUT in the status word, stops issuing work, waits (bounded)
 // for its copies and MMAs in flight, frees its TMEM and returns.
+#include <cuda_fp16.h>
+
 #include <cstring>
 
 #include "sas_internal.cuh"
@@ -40,16 +42,22 @@ namespace tc {
 constexpr int kThreads = 192;
 constexpr int kBM = 128;              // rows of S per tile (MMA M)
 constexpr int kABox = 128 * 128;      // A box: 128 rows x 32 floats (128-byte rows)
-constexpr int kAcc = 4;               // TMEM accumulators of BN columns
 
-// Parameter-tile width BN (MMA N) and the depth of the y-tile ring that keeps
-// the shared-memory budget: 64 x 4 stages or 128 x 2 stages.
-template <int BN>
+// Parameter-tile width BN (MMA N), operand type and the depths that keep the
+// shared-memory and TMEM budgets:
+//   tf32 (three split products into one accumulator): 64 x 4 stages or
+//     128 x 2 stages, 4 accumulator slots of BN columns;
+//   f16 (S_hi y_hi into one accumulator, S_hi y_lo + S_lo y_hi into a second,
+//     the low parts carrying a 2^11 scale): 128 x 4 stages, 2 slots of 2 BN
+//     columns.  Operand rows are 128 B in both: 32 tf32 or 64 f16 values.
+template <int BN, bool F16>
 struct Shape {
-  static constexpr int kBBox = BN * 128;  // B box: BN rows x 32 floats
-  static constexpr int kBStages = BN == 64 ? 4 : 2;
-  static constexpr uint32_t kTmemCols = kAcc * BN;
-  static constexpr uint32_t kIdesc = tf32_idesc(kBM, BN);
+  static constexpr int kBBox = BN * 128;  // B box: BN rows x 128 B
+  static constexpr int kBStages = F16 ? 4 : (BN == 64 ? 4 : 2);
+  static constexpr int kAcc = F16 ? 2 : 4;
+  static constexpr int kSlotCols = F16 ? 2 * BN : BN;
+  static constexpr uint32_t kTmemCols = kAcc * kSlotCols;
+  static constexpr uint32_t kIdesc = F16 ? f16_idesc(kBM, BN) : tf32_idesc(kBM, BN);
 };
 
 struct Params {
@@ -63,6 +71,7 @@ struct Params {
   int ntpg;        // parameter tiles per range
   int num_units;   // num_mtiles * ngroups
   int rotate;      // 1: each unit starts its parameter tiles at a unit-dependent offset
+  const float* yscale;  // f16 form: per-parameter power-of-two scale of the product (m)
   int tma_store;   // 1: epilogue through shared memory and TMA stores
   int* status;
 };
@@ -87,7 +96,7 @@ __device__ inline int unit_tile(const Params& p, int u, int nt0, int nt1, int k)
   return nt0 + (t >= len ? t - len : t);
 }
 
-template <int BN>
+template <int BN, bool F16>
 __global__ void __launch_bounds__(kThreads, 1)
     reconstruct_tc_kernel(const __grid_constant__ CUtensorMap tmAhi,
                           const __grid_constant__ CUtensorMap tmAlo,
@@ -95,10 +104,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                           const __grid_constant__ CUtensorMap tmBlo,
                           const __grid_constant__ CUtensorMap tmOut, Params p) {
   constexpr int kBN = BN;
-  constexpr int kBBox = Shape<BN>::kBBox;
-  constexpr int kBStages = Shape<BN>::kBStages;
-  constexpr uint32_t kTmemCols = Shape<BN>::kTmemCols;
-  constexpr uint32_t kIdesc = Shape<BN>::kIdesc;
+  constexpr int kBBox = Shape<BN, F16>::kBBox;
+  constexpr int kBStages = Shape<BN, F16>::kBStages;
+  constexpr int kAcc = Shape<BN, F16>::kAcc;
+  constexpr int kSlotCols = Shape<BN, F16>::kSlotCols;
+  constexpr uint32_t kTmemCols = Shape<BN, F16>::kTmemCols;
+  constexpr uint32_t kIdesc = Shape<BN, F16>::kIdesc;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
@@ -109,7 +120,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* B0 = A0 + (size_t)2 * aop;                 // stage s: hi at B0 + 2 s bop, lo after it
   float* stage = reinterpret_cast<float*>(B0 + (size_t)kBStages * 2 * bop);  // 4 warps x 2
   uint64_t* bars = reinterpret_cast<uint64_t*>(stage + 8 * kStageFloats);
-  // bars: afull, aempty, bfull[4], bempty[4], tfull[4], tempty[4]
+  // bars: afull, aempty, bfull[kBStages], bempty[kBStages], tfull[kAcc], tempty[kAcc]
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
 
@@ -208,24 +219,40 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int k = 0; k < nt1 - nt0; ++k) {
           const int s = t & (kBStages - 1), acc = t & (kAcc - 1);
           if (!mbar_wait(bfull0 + 8 * s, (uint32_t)(t / kBStages) & 1u, &abort_flag, p.status) ||
-              !mbar_wait(tempty0 + 8 * acc, ((uint32_t)(t >> 2) & 1u) ^ 1u, &abort_flag,
+              !mbar_wait(tempty0 + 8 * acc, ((uint32_t)(t / kAcc) & 1u) ^ 1u, &abort_flag,
                          p.status)) {
             stop = true;
             break;
           }
           fence_after();
-          const uint32_t d = tmem + (uint32_t)(acc * kBN);
+          const uint32_t d = tmem + (uint32_t)(acc * kSlotCols);
           const uint8_t* Bhi = B0 + (size_t)s * 2 * bop;
-          const uint8_t* Aop[3] = {Ahi + aop, Ahi, Ahi};  // S_lo y_hi + S_hi y_lo + S_hi y_hi
-          const uint8_t* Bop[3] = {Bhi, Bhi + bop, Bhi};
-          uint32_t accum = 0;
-          for (int prod = 0; prod < 3; ++prod) {
-            for (int ks = 0; ks < kb * 4; ++ks) {
-              const uint32_t ka = (uint32_t)(ks >> 2) * kABox + (uint32_t)(ks & 3) * 32u;
-              const uint32_t kbo = (uint32_t)(ks >> 2) * kBBox + (uint32_t)(ks & 3) * 32u;
-              mma_tf32(d, smem_desc(smem_u32(Aop[prod]) + ka), smem_desc(smem_u32(Bop[prod]) + kbo),
-                       kIdesc, accum);
-              accum = 1;
+          if constexpr (F16) {
+            // D1 = S_hi y_hi; D2 = S_hi y_lo' + S_lo' y_hi (K = 64 f16 in 4 steps of 16)
+            const uint32_t ah = smem_u32(Ahi), al = smem_u32(Ahi + aop);
+            const uint32_t bh = smem_u32(Bhi), bl = smem_u32(Bhi + bop);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_f16(d, smem_desc(ah + ks * 32), smem_desc(bh + ks * 32), kIdesc, ks > 0 ? 1u : 0u);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_f16(d + kBN, smem_desc(ah + ks * 32), smem_desc(bl + ks * 32), kIdesc,
+                      ks > 0 ? 1u : 0u);
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              mma_f16(d + kBN, smem_desc(al + ks * 32), smem_desc(bh + ks * 32), kIdesc, 1u);
+          } else {
+            const uint8_t* Aop[3] = {Ahi + aop, Ahi, Ahi};  // S_lo y_hi + S_hi y_lo + S_hi y_hi
+            const uint8_t* Bop[3] = {Bhi, Bhi + bop, Bhi};
+            uint32_t accum = 0;
+            for (int prod = 0; prod < 3; ++prod) {
+              for (int ks = 0; ks < kb * 4; ++ks) {
+                const uint32_t ka = (uint32_t)(ks >> 2) * kABox + (uint32_t)(ks & 3) * 32u;
+                const uint32_t kbo = (uint32_t)(ks >> 2) * kBBox + (uint32_t)(ks & 3) * 32u;
+                mma_tf32(d, smem_desc(smem_u32(Aop[prod]) + ka),
+                         smem_desc(smem_u32(Bop[prod]) + kbo), kIdesc, accum);
+                accum = 1;
+              }
             }
           }
           mma_commit(bempty0 + 8 * s);
@@ -235,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         ++ua;
       }
-      if (last >= 0) mbar_drain(tfull0 + 8 * (last & (kAcc - 1)), (uint32_t)(last >> 2) & 1u);
+      if (last >= 0) mbar_drain(tfull0 + 8 * (last & (kAcc - 1)), (uint32_t)(last / kAcc) & 1u);
     }
   } else {
     // ---------------- epilogue: warps 2..5, lane quarter q = warp % 4
@@ -251,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nt = unit_tile(p, u, nt0, nt1, k);
         const int acc = t & (kAcc - 1);
         const bool ok = __all_sync(
-            0xffffffffu, mbar_wait(tfull0 + 8 * acc, (uint32_t)(t >> 2) & 1u, &abort_flag, p.status));
+            0xffffffffu, mbar_wait(tfull0 + 8 * acc, (uint32_t)(t / kAcc) & 1u, &abort_flag, p.status));
         if (!ok) {
           stop = true;
           break;
@@ -259,8 +286,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_after();
         for (int cb = 0; cb < kBN / 32; ++cb) {
           float v[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + cb * 32), v);
+          const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kSlotCols + cb * 32);
+          tmem_ld32(ta, v);
           const int64_t ys = (int64_t)nt * kBN + cb * 32;
+          if constexpr (F16) {
+            // x = scale_j (D1 + 2^-11 D2); lane c of the warp holds column c's scale
+            float v2[32];
+            tmem_ld32(ta + kBN, v2);
+            const float sc = ys + lane < p.m ? p.yscale[ys + lane] : 0.f;
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+              v[c] = fmaf(v2[c], 0x1p-11f, v[c]) * __shfl_sync(0xffffffffu, sc, c);
+          }
           if (p.tma_store) {
             // stage [32 parameters][32 rows] and hand it to the TMA engine; a box
             // wholly past the end is skipped and touches no staging buffer, so
@@ -305,20 +342,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // Row-major rows x rpad float32 matrix, box box_rows x 32 floats, 128-byte swizzle.
-static bool make_map(CUtensorMap* map, const float* base, int64_t rows, int rpad, int box_rows) {
+static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int cols, int box_rows,
+                     bool f16) {
+  // rows x cols row-major, 128-byte rows (32 float32 or 64 f16 values per box row)
   auto fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)rpad, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)rpad * sizeof(float)};
-  cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+  const size_t es = f16 ? 2 : 4;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * es};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = fn(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                  (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
-
-// Output m x n float32 (row j = x_hat_j), box 32 rows (i) x 32 parameters (j), no swizzle.
 static bool make_out_map(CUtensorMap* map, float* base, int64_t n, int64_t m) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -355,17 +394,19 @@ cudaError_t launch_wait_selftest(int* status, double seconds, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int BN>
+template <int BN, bool F16>
 static size_t tc_smem_bytes(int rpad) {
-  const size_t kb = (size_t)(rpad / 32);
-  return 1024 + 2 * kb * tc::kABox + (size_t)tc::Shape<BN>::kBStages * 2 * kb * tc::Shape<BN>::kBBox +
-         8 * tc::kStageFloats * sizeof(float) +
-         (2 + 2 * tc::Shape<BN>::kBStages + 2 * tc::kAcc) * sizeof(uint64_t);
+  using Sh = tc::Shape<BN, F16>;
+  const size_t kb = F16 ? 1 : (size_t)(rpad / 32);
+  return 1024 + 2 * kb * tc::kABox + (size_t)Sh::kBStages * 2 * kb * Sh::kBBox +
+         8 * tc::kStageFloats * sizeof(float) + (2 + 2 * Sh::kBStages + 2 * Sh::kAcc) * sizeof(uint64_t);
 }
 
 size_t reconstruct_tc_smem_bytes(int rpad) {
-  const size_t a = tc_smem_bytes<64>(rpad), b = tc_smem_bytes<128>(rpad);
-  return a > b ? a : b;
+  const size_t a = tc_smem_bytes<64, false>(rpad), b = tc_smem_bytes<128, false>(rpad);
+  const size_t c = tc_smem_bytes<128, true>(rpad);
+  const size_t ab = a > b ? a : b;
+  return ab > c ? ab : c;
 }
 
 bool reconstruct_tc_supported(const sas_ctx* c) {
@@ -394,21 +435,74 @@ void reconstruct_tc_split(int64_t n, int64_t m, int num_sms, int bn, int* num_mt
   *ntpg = (int)per;
 }
 
-template <int BN>
+namespace tc {
+
+// f16 form: y (float32 = tf32 hi + lo of the split) -> per-parameter scale
+// 2^e (|y| 2^-e < 1), f16 high part and 2^11-scaled f16 remainder, zero padded
+// to 64; the product scale 2^(e - shift) goes to ysc.  One warp per parameter.
+__global__ void split_y16_kernel(const float* ys, int64_t m, int rpad, int r, int shift,
+                                 __half* y16, float* ysc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t q = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); q < m; q += warps) {
+    float v[2];
+    float amax = 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      v[h] = k < r ? ys[q * rpad + k] + ys[m * rpad + q * rpad + k] : 0.f;
+      amax = fmaxf(amax, fabsf(v[h]));
+    }
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const int e = amax > 0.f ? ilogbf(amax) + 1 : 0;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      const float yp = ldexpf(v[h], -e);
+      const __half hi = __float2half_rn(yp);
+      const __half lo = __float2half_rn((yp - __half2float(hi)) * 2048.f);
+      y16[q * 64 + k] = hi;
+      y16[m * 64 + q * 64 + k] = lo;
+    }
+    if (lane == 0) ysc[q] = ldexpf(1.f, e - shift);
+  }
+}
+
+}  // namespace tc
+
+template <int BN, bool F16>
 static cudaError_t launch_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                              bool rotate, cudaStream_t st) {
   if (m > 2147483647 - BN || c->n > 2147483647 - tc::kBM) return cudaErrorInvalidValue;
   const int rpad = (c->r + 31) / 32 * 32;
-  const size_t smem = tc_smem_bytes<BN>(rpad);
-  cudaError_t e = cudaFuncSetAttribute(tc::reconstruct_tc_kernel<BN>,
+  const size_t smem = tc_smem_bytes<BN, F16>(rpad);
+  cudaError_t e = cudaFuncSetAttribute(tc::reconstruct_tc_kernel<BN, F16>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
-  if (!tc::make_map(&mAhi, c->Shi, c->n, rpad, tc::kBM) ||
-      !tc::make_map(&mAlo, c->Slo, c->n, rpad, tc::kBM) ||
-      !tc::make_map(&mBhi, ysplit, m, rpad, BN) ||
-      !tc::make_map(&mBlo, ysplit + (size_t)m * rpad, m, rpad, BN))
-    return cudaErrorInvalidValue;
+  const float* ysc = nullptr;
+  if constexpr (F16) {
+    if (!c->S16hi || !c->ysplit16 || c->ysplit16_bytes < (size_t)m * (2 * 64 * 2 + 4))
+      return cudaErrorInvalidValue;
+    __half* y16 = reinterpret_cast<__half*>(c->ysplit16);
+    float* sc = reinterpret_cast<float*>(y16 + (size_t)2 * m * 64);
+    tc::split_y16_kernel<<<(unsigned)((m + 7) / 8 < 4096 ? (m + 7) / 8 : 4096), 256, 0, st>>>(
+        ysplit, m, rpad, c->r, c->s16_shift, y16, sc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ysc = sc;
+    if (!tc::make_map(&mAhi, c->S16hi, c->n, 64, tc::kBM, true) ||
+        !tc::make_map(&mAlo, c->S16lo, c->n, 64, tc::kBM, true) ||
+        !tc::make_map(&mBhi, y16, m, 64, BN, true) ||
+        !tc::make_map(&mBlo, y16 + (size_t)m * 64, m, 64, BN, true))
+      return cudaErrorInvalidValue;
+  } else {
+    if (!tc::make_map(&mAhi, c->Shi, c->n, rpad, tc::kBM, false) ||
+        !tc::make_map(&mAlo, c->Slo, c->n, rpad, tc::kBM, false) ||
+        !tc::make_map(&mBhi, ysplit, m, rpad, BN, false) ||
+        !tc::make_map(&mBlo, ysplit + (size_t)m * rpad, m, rpad, BN, false))
+      return cudaErrorInvalidValue;
+  }
   // TMA stores need 16-byte aligned rows: n a multiple of 4 and an aligned base
   CUtensorMap mOut;
   const bool tma_store = (c->n % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
@@ -419,25 +513,90 @@ static cudaError_t launch_tc(const sas_ctx* c, const float* ysplit, int64_t m, f
   p.out = out;
   p.n = c->n;
   p.m = m;
-  p.kboxes = rpad / 32;
+  p.kboxes = F16 ? 1 : rpad / 32;
   reconstruct_tc_split(c->n, m, c->num_sms, BN, &p.num_mtiles, &p.num_ntiles, &p.ngroups, &p.ntpg);
   const int64_t units = (int64_t)p.num_mtiles * p.ngroups;
   if (units > 2147483647) return cudaErrorInvalidValue;
   p.num_units = (int)units;
   p.rotate = rotate ? 1 : 0;
+  p.yscale = ysc;
   p.status = c->dev_status;
   const int grid = (int)(units < c->num_sms ? units : c->num_sms);
-  tc::reconstruct_tc_kernel<BN><<<grid, tc::kThreads, smem, st>>>(mAhi, mAlo, mBhi, mBlo, mOut, p);
+  tc::reconstruct_tc_kernel<BN, F16><<<grid, tc::kThreads, smem, st>>>(mAhi, mAlo, mBhi, mBlo,
+                                                                       mOut, p);
   return cudaGetLastError();
 }
 
-// recon_kernel: 2 = 64-parameter tiles; 3 = 128-parameter tiles; 0 (automatic)
-// and 4 = 128-parameter tiles visited in a unit-dependent rotated order.
+namespace tc {
+
+// f16 split of S: 2^shift S with max |2^shift S| in [1, 2), the f16 high part
+// and the 2^11-scaled f16 remainder, rows of 64 (zero padded).
+__global__ void maxabs_kernel(const double* S, int64_t ldS, int64_t n, int r, unsigned int* out) {
+  float m = 0.f;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * r;
+       idx += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, (float)fabs(S[(idx % n) + (idx / n) * ldS]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // non-negative floats order as ints
+}
+
+__global__ void split_basis16_kernel(const double* S, int64_t ldS, int64_t n, int r, int shift,
+                                     __half* hi, __half* lo) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * 64;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / 64;
+    const int k = (int)(idx % 64);
+    __half h = __float2half_rn(0.f), l = __float2half_rn(0.f);
+    if (k < r) {
+      const double x = ldexp(S[i + (int64_t)k * ldS], shift);
+      h = __double2half(x);
+      l = __double2half((x - (double)__half2float(h)) * 2048.0);
+    }
+    hi[idx] = h;
+    lo[idx] = l;
+  }
+}
+
+}  // namespace tc
+
+cudaError_t setup_f16_basis(sas_ctx* c, cudaStream_t st) {
+  if (c->dtype != SAS_REAL64 || c->r > 64) return cudaSuccess;
+  unsigned int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) {
+    tc::maxabs_kernel<<<c->num_sms * 4, 256, 0, st>>>((const double*)c->S, c->ldS, c->n, c->r, d);
+    e = cudaGetLastError();
+  }
+  unsigned int bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return e;
+  float amax;
+  std::memcpy(&amax, &bits, sizeof(amax));
+  c->s16_shift = amax > 0.f ? -ilogbf(amax) : 0;
+  e = cudaMalloc(&c->S16hi, (size_t)c->n * 64 * sizeof(__half));
+  if (e == cudaSuccess) e = cudaMalloc(&c->S16lo, (size_t)c->n * 64 * sizeof(__half));
+  if (e != cudaSuccess) return e;
+  tc::split_basis16_kernel<<<c->num_sms * 8, 256, 0, st>>>((const double*)c->S, c->ldS, c->n, c->r,
+                                                           c->s16_shift, (__half*)c->S16hi,
+                                                           (__half*)c->S16lo);
+  return cudaGetLastError();
+}
+
+// recon_kernel: 2 = tf32, 64-parameter tiles; 3 = tf32, 128-parameter tiles;
+// 4 = as 3 in a rotated tile order; 5 and 0 (automatic) = f16 splits,
+// 128-parameter tiles.
 cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                   cudaStream_t st) {
   if (m == 0) return cudaSuccess;
-  if (c->recon_kernel == 2) return launch_tc<64>(c, ysplit, m, out, false, st);
-  return launch_tc<128>(c, ysplit, m, out, c->recon_kernel != 3, st);
+  switch (c->recon_kernel) {
+    case 2: return launch_tc<64, false>(c, ysplit, m, out, false, st);
+    case 3: return launch_tc<128, false>(c, ysplit, m, out, false, st);
+    case 4: return launch_tc<128, false>(c, ysplit, m, out, true, st);
+    default: return launch_tc<128, true>(c, ysplit, m, out, false, st);
+  }
 }
 
 }  // namespace sas

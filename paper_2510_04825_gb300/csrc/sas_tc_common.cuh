@@ -156,6 +156,20 @@ __device__ inline void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_
       : "memory");
 }
 
+// Instruction descriptor of kind::f16 with f16 A and B (both K-major), D f32.
+__host__ __device__ constexpr uint32_t f16_idesc(int m, int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ inline void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                               uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
 // TMEM load of 32 lanes x 16 columns (one value per column for this lane).
 __device__ inline void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];

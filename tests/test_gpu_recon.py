@@ -4,6 +4,8 @@ x_hat in float32 from tf32 splits of S and y: three products, relative
 error ~2^-21 per product, so <= 2e-6 relative per parameter is the bound.
 Shapes cover ragged row tiles (n not a multiple of 128), ragged parameter
 tiles (m not a multiple of 64), one and two K boxes (r <= 32, r <= 64),
+the tf32 forms (64- and 128-parameter tiles) and the f16 form (S and y in
+power-of-two-scaled f16 hi / 2^11 lo splits, three products),
 the split of a row tile's parameter tiles into ranges (fewer row tiles than
 SMs) and units that stream many parameter tiles past one resident S tile.
 """
@@ -48,7 +50,7 @@ def test_tensor_core_reconstruction(N, r, s, m):
     Xcc = xhat(case, 1, params)
     e_cc = np.linalg.norm(Xcc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
     assert e_cc.max() <= 2e-6
-    for kernel in (2, 3):  # 64- and 128-parameter tiles
+    for kernel in (2, 3, 5):  # tf32 64- and 128-parameter tiles, f16 splits
         Xtc = xhat(case, kernel, params)
         assert np.isfinite(Xtc).all()
         e_tc = np.linalg.norm(Xtc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
@@ -89,7 +91,7 @@ def test_tensor_core_reconstruction_large_n_many_batch_sizes():
     for m in (1, 64, 100, 128, 256, 300):
         params = p.test_params[:m]
         Xcc = xhat(case, 1, params)
-        for kernel in (2, 3):
+        for kernel in (2, 3, 5):
             Xtc = xhat(case, kernel, params)
             d = np.linalg.norm(Xtc - Xcc, axis=1) / np.linalg.norm(Xcc, axis=1)
             bad = np.nonzero(d > 2e-6)[0]
@@ -108,12 +110,12 @@ def test_tensor_core_reconstruction_long_units():
     p = case.prob
     params = p.test_params
     Xcc = xhat(case, 1, params, on_device=True)
-    for kernel in (3, 2):
+    for kernel in (3, 2, 5):
         Xtc = xhat(case, kernel, params, on_device=True)
         assert torch.isfinite(Xtc).all().item()
         d = (torch.linalg.vector_norm(Xtc - Xcc, dim=1) / torch.linalg.vector_norm(Xcc, dim=1)).cpu().numpy()
         assert d.max() <= 2e-6, (kernel, np.argmax(d), d.max())
-        if kernel == 3:
+        if kernel != 5:
             del Xtc
     pick = [0, 63, 64, 1000, 2047, 2048, 2099]
     Yo, _ = case.oracle_solve(params[pick])
