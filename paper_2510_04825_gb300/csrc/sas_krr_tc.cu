@@ -126,7 +126,7 @@ __device__ inline float ex2_approx(float x) {
 }
 
 template <int DP4>
-__global__ void __maxnreg__(144)  // 448 threads x 144 registers fit one SM
+__global__ void __maxnreg__(128)  // 448 threads x 128 registers per CTA, one CTA per SM
     krr_tc_kernel(const __grid_constant__ CUtensorMap tmShi,
                   const __grid_constant__ CUtensorMap tmSlo, Params p) {
   extern __shared__ uint8_t smem_raw[];
