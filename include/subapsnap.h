@@ -237,9 +237,14 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
  *      three split products, float32 TMEM sums folded into float64).
  *  SAS_OPT_ASSEMBLY_SEGMENT: tensor-core kernel rows: points summed in float32
  *      before each float64 fold (multiple of 32 in [32, 2^20], default 1024);
- *      shorter segments cost more folds and round less. */
+ *      shorter segments cost more folds and round less.
+ *  SAS_OPT_RECON_STORE: epilogue of the tensor-core reconstruction: 0 = tiles
+ *      staged in shared memory and written by TMA bulk-tensor stores (when n
+ *      is a multiple of 4 and the output 16-byte aligned), 1 = coalesced
+ *      streaming stores straight from registers. */
 enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
-       SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4, SAS_OPT_ASSEMBLY_SEGMENT = 5 };
+       SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4, SAS_OPT_ASSEMBLY_SEGMENT = 5,
+       SAS_OPT_RECON_STORE = 6 };
 
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */

@@ -852,6 +852,10 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
       if (!(value > 0.0 && value < 1.0)) return fail(SAS_EINVAL, "refine tol must be in (0, 1)");
       c->refine_tol = value;
       return SAS_OK;
+    case SAS_OPT_RECON_STORE:
+      if (value != 0.0 && value != 1.0) return fail(SAS_EINVAL, "recon store must be 0 or 1");
+      c->recon_store = (int)value;
+      return SAS_OK;
     case SAS_OPT_ASSEMBLY_SEGMENT:
       if (!(value >= 32.0 && value <= 1048576.0) || std::fmod(value, 32.0) != 0.0)
         return fail(SAS_EINVAL, "assembly segment must be a multiple of 32 in [32, 2^20]");

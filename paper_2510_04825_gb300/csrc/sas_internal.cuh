@@ -192,6 +192,7 @@ struct sas_ctx {
   void* surrogate;     // learned surrogate network (sas_mlp.cu), or null
   // options
   int recon_kernel;    // 0 auto, 1 CUDA cores, 2-4 tensor cores tf32, 5 tensor cores f16
+  int recon_store;     // tensor-core reconstruction epilogue: 0 TMA stores, 1 direct stores
   int krr_kernel;      // kernel rows of the mixed form: 0 auto, 1 CUDA cores, 2 tensor cores
   int krr_seg_points;  // tensor-core rows: points per TMEM segment before the float64 fold
   int ls_variant_plain;  // launch shape of the plain LS kernel (autotuned)

@@ -272,15 +272,21 @@ __global__ void __maxnreg__(128)  // 448 threads x 128 registers per CTA, one CT
             tmem_ld16(tmem + ((uint32_t)(qr * 32) << 16) + (uint32_t)(buf * kQ * p.nb + q * p.nb + cb * 16),
                       v);
             if (live) {
+              // all sixteen loads before any store, so that they are in flight together
+              double prev[16];
 #pragma unroll
               for (int e = 0; e < 16; ++e) {
                 const int col = cb * 16 + e;
+                prev[e] = 0.0;
                 if (col < p.r) {
-                  double* pm = Mq + (int64_t)col * p.s + row;
-                  double a = (g == 0 ? 0.0 : *pm) + (double)v[e];
-                  if (g == nseg - 1) a += lambda * p.SJ[(int64_t)col * p.s + row];
-                  *pm = a;
+                  if (g > 0) prev[e] = Mq[(int64_t)col * p.s + row];
+                  if (g == nseg - 1) prev[e] += lambda * p.SJ[(int64_t)col * p.s + row];
                 }
+              }
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const int col = cb * 16 + e;
+                if (col < p.r) Mq[(int64_t)col * p.s + row] = prev[e] + (double)v[e];
               }
             }
           }

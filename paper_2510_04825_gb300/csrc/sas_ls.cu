@@ -290,18 +290,33 @@ struct LsShape {
 static const LsShape kLsShapes[] = {{256, 4}, {128, 4}, {256, 8}, {128, 2}, {256, 2}};
 constexpr int kNumLsShapes = sizeof(kLsShapes) / sizeof(kLsShapes[0]);
 
+// Blocked Householder variants of the mixed kernel (real only): threads,
+// lanes per column group, registers per lane for a trailing column (s <= G E).
+struct LsBlockedShape {
+  int nt, g, e;
+};
+static const LsBlockedShape kLsBlocked[] = {{128, 4, 32}, {128, 8, 16}, {256, 8, 32}, {128, 8, 32}};
+constexpr int kNumLsBlocked = sizeof(kLsBlocked) / sizeof(kLsBlocked[0]);
+constexpr int kLsPanel = 8;  // columns per panel of the blocked variants
+constexpr int kFirstBlocked = 3 * kNumLsShapes + 2;
+
 // plain: the smem shapes, then one register-resident variant; mixed: the smem
 // shapes with the float64 M in shared memory, without it, two register-resident
-// variants, then the smem shapes with the float64 M in a global slot per CTA
-int ls_num_variants(bool mixed) { return mixed ? 3 * kNumLsShapes + 2 : kNumLsShapes + 1; }
+// variants, the smem shapes with the float64 M in a global slot per CTA, then
+// the blocked variants (M in a global slot)
+int ls_num_variants(bool mixed) {
+  return mixed ? kFirstBlocked + kNumLsBlocked : kNumLsShapes + 1;
+}
 
-// Mixed variant index -> (shape, where the float64 M lives); -1 for the
-// register-resident variants.
+// Mixed variant index -> shape index; -1 for the register-resident variants,
+// -2 for the blocked ones.
 static int mixed_shape(int v) {
   if (v < 2 * kNumLsShapes) return v % kNumLsShapes;
   if (v < 2 * kNumLsShapes + 2) return -1;
-  return v - (2 * kNumLsShapes + 2);
+  if (v < kFirstBlocked) return v - (2 * kNumLsShapes + 2);
+  return -2;
 }
+// Where the float64 M lives: 1 shared memory, 0 recomputed, 2 a global slot.
 static int mixed_keep_kind(int v) {
   if (v < kNumLsShapes) return 1;
   if (v < 2 * kNumLsShapes + 2) return 0;
@@ -437,7 +452,53 @@ __device__ inline float tf32_round(float x) {
 //     returned y, so rho is exact in float64.
 // One parameter q of the mixed solve (shared by the grid-stride and the
 // persistent multi-problem kernels).
-template <typename TH, typename TL, int NT, int G>
+// Blocked form of the Householder sweep (real float32 panel): after the
+// reflectors of panel columns [c0, pe) are formed, each trailing column j in
+// [pe, ncol) is loaded once into registers (rows c0 + g + G e of lane g of its
+// column group), all panel reflectors are applied there in order, and it is
+// stored back.  Vb holds the panel's reflectors as full columns of length s
+// (zero above the diagonal, v0 on it); tau their scales.  The same products as
+// the column-by-column sweep, with one shared-memory pass over the trailing
+// matrix per panel instead of one per reflector.
+template <int NT, int G, int E>
+__device__ inline void blocked_trailing_update(float* P, int ldt, int s, int c0, int pe, int ncol,
+                                               const float* Vb, const float* tau) {
+  constexpr int NSLOT = NT / G;
+  const int tid = threadIdx.x, g = tid % G, slot = tid / G;
+  const unsigned gmask = ((1u << G) - 1u) << ((tid & 31) & ~(G - 1));
+  for (int j = pe + slot; j < ncol; j += NSLOT) {
+    float* pj = P + (size_t)j * ldt;
+    float av[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = c0 + g + G * e;
+      av[e] = i < s ? pj[i] : 0.f;
+    }
+    for (int k = c0; k < pe; ++k) {
+      const float* v = Vb + (size_t)(k - c0) * s;
+      float vv[E];
+      float w = 0.f;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int i = c0 + g + G * e;
+        vv[e] = i < s ? v[i] : 0.f;
+        w = fmaf(vv[e], av[e], w);
+      }
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) w += __shfl_xor_sync(gmask, w, o);
+      const float tw = tau[k] * w;
+#pragma unroll
+      for (int e = 0; e < E; ++e) av[e] = fmaf(-tw, vv[e], av[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int i = c0 + g + G * e;
+      if (i < s) pj[i] = av[e];
+    }
+  }
+}
+
+template <typename TH, typename TL, int NT, int G, int BW = 0, int E = 0>
 __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int64_t q,
                                               unsigned char* smem_raw, double* ctl) {
 
@@ -456,9 +517,12 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
   // or not kept (recomputed from the blocks for every residual)
   const bool gslot = a.keep64 == 2 && (int)blockIdx.x < a.nslots;
   const bool keep = a.keep64 == 1 || gslot;
+  // blocked form: the panel's reflectors as full columns, BW x s, after P
+  float* Vb = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(P + (size_t)ldt * (r + 1)) + 15) & ~(uintptr_t)15);
   TH* M64 = gslot ? a.M64g + (size_t)blockIdx.x * s * r
                   : reinterpret_cast<TH*>(
-                        (reinterpret_cast<uintptr_t>(P + (size_t)ldt * (r + 1)) + 15) &
+                        (reinterpret_cast<uintptr_t>(Vb + (size_t)BW * s) + 15) &
                         ~(uintptr_t)15);  // s x r
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -503,10 +567,33 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
     __syncthreads();
     tail_norm_warp0<TL, float>(P + 1, s - 1, &nrm2[0]);
     __syncthreads();
-    for (int k = 0; k < r; ++k)
-      householder_step<TL, float, NT, G>(k, r + 1, P + k, ldt, P + k + 1, ldt, s - k - 1, 1, nrm2,
-                                         v0, tau);
-    __syncthreads();
+    if constexpr (BW > 0) {
+      // panels of BW columns: reflectors within the panel, then one register pass
+      // over every trailing column (the right-hand side included)
+      for (int c0 = 0; c0 < r; c0 += BW) {
+        const int pe = c0 + BW < r ? c0 + BW : r;
+        for (int k = c0; k < pe; ++k)
+          householder_step<TL, float, NT, G>(k, pe, P + k, ldt, P + k + 1, ldt, s - k - 1, 1, nrm2,
+                                             v0, tau);
+        __syncthreads();
+        for (int idx = tid; idx < (pe - c0) * s; idx += NT) {
+          const int kk = idx / s, i = idx % s, k = c0 + kk;
+          Vb[idx] = i < k ? 0.f : (i == k ? v0[k] : P[i + (size_t)k * ldt]);
+        }
+        __syncthreads();
+        blocked_trailing_update<NT, G, E>(P, ldt, s, c0, pe, r + 1, Vb, tau);
+        __syncthreads();
+        if (pe < r) {
+          tail_norm_warp0<TL, float>(P + (size_t)pe * ldt + pe + 1, s - pe - 1, &nrm2[pe & 1]);
+          __syncthreads();
+        }
+      }
+    } else {
+      for (int k = 0; k < r; ++k)
+        householder_step<TL, float, NT, G>(k, r + 1, P + k, ldt, P + k + 1, ldt, s - k - 1, 1, nrm2,
+                                           v0, tau);
+      __syncthreads();
+    }
     // y0 = R^{-1} z
     float dmin = 0.f, dmax = 0.f;
     if (warp == 0) {
@@ -667,7 +754,8 @@ static bool mixed_keep64(const sas_ctx* c) {
 
 size_t ls_mixed_smem_bytes(const sas_ctx* c) {
   const size_t eh = c->dtype == SAS_COMPLEX128 ? 16 : 8;
-  return mixed_base_bytes(c) + (mixed_keep64(c) ? (size_t)c->s * c->r * eh : 0);
+  const size_t vb = mixed_shape(c->ls_variant_mixed) == -2 ? (size_t)kLsPanel * c->s * 4 + 16 : 0;
+  return mixed_base_bytes(c) + vb + (mixed_keep64(c) ? (size_t)c->s * c->r * eh : 0);
 }
 
 // Global float64-M slots of a mixed context: one per CTA that can be resident
@@ -720,6 +808,38 @@ static size_t fill_mixed_args(const sas_ctx* c, const double* params, int64_t m,
   return smem;
 }
 
+template <int NT, int G, int E>
+__global__ void __launch_bounds__(NT, 512 / NT) ls_mixed_blocked_kernel(LsMixedArgs<double, float> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double ctl[2];
+  for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x)
+    ls_mixed_body<double, float, NT, G, kLsPanel, E>(a, q, smem_raw, ctl);
+}
+
+static cudaError_t launch_mixed_blocked(const sas_ctx* c, const LsMixedArgs<double, float>& a,
+                                        int64_t m, size_t smem, int b, cudaStream_t st) {
+  if (b < 0 || b >= kNumLsBlocked) return cudaErrorInvalidConfiguration;
+  const LsBlockedShape sh = kLsBlocked[b];
+  if (c->s > sh.g * sh.e) return cudaErrorInvalidConfiguration;  // a trailing column must fit
+  void (*kern)(LsMixedArgs<double, float>) = nullptr;
+  switch (b) {
+    case 0: kern = ls_mixed_blocked_kernel<128, 4, 32>; break;
+    case 1: kern = ls_mixed_blocked_kernel<128, 8, 16>; break;
+    case 2: kern = ls_mixed_blocked_kernel<256, 8, 32>; break;
+    default: kern = ls_mixed_blocked_kernel<128, 8, 32>; break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, sh.nt, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)c->num_sms * per_sm;
+  if (grid > m) grid = m;
+  kern<<<(unsigned)grid, sh.nt, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <typename TH, typename TL>
 static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_t m, void* yout,
                                   void* qoi, float* ysplit, uint32_t* flags, double* rho,
@@ -728,6 +848,11 @@ static cudaError_t launch_mixed_t(const sas_ctx* c, const double* params, int64_
   const size_t smem = fill_mixed_args<TH, TL>(c, params, m, yout, qoi, ysplit, flags, rho, Mg, a);
   if (smem == 0) return cudaErrorInvalidConfiguration;
   const int v = mixed_shape(c->ls_variant_mixed);
+  if (v == -2) {
+    if constexpr (sizeof(TH) == 8)
+      return launch_mixed_blocked(c, a, m, smem, c->ls_variant_mixed - kFirstBlocked, st);
+    return cudaErrorInvalidConfiguration;
+  }
   if (v < 0) {
     if constexpr (sizeof(TH) == 8)
       return launch_mixed_reg(c, a, m, c->ls_variant_mixed - 2 * kNumLsShapes, st);

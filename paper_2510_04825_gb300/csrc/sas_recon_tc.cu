@@ -316,11 +316,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 bulk_commit();
               }
             }
-          } else if (xs + lane < p.n) {
+          } else if (xs + lane < p.n && ys < p.m) {
+            // coalesced streaming stores: lane = row, one 128-byte warp store per parameter
+            float* o = p.out + ys * p.n + xs + lane;
+            if (ys + 32 <= p.m) {
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-              const int64_t j = ys + c;
-              if (j < p.m) __stcs(p.out + j * p.n + xs + lane, v[c]);
+              for (int c = 0; c < 32; ++c) __stcs(o + (int64_t)c * p.n, v[c]);
+            } else {
+#pragma unroll
+              for (int c = 0; c < 32; ++c)
+                if (ys + c < p.m) __stcs(o + (int64_t)c * p.n, v[c]);
             }
           }
         }
@@ -505,7 +510,8 @@ static cudaError_t launch_tc(const sas_ctx* c, const float* ysplit, int64_t m, f
   }
   // TMA stores need 16-byte aligned rows: n a multiple of 4 and an aligned base
   CUtensorMap mOut;
-  const bool tma_store = (c->n % 4 == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
+  const bool tma_store = c->recon_store == 0 && (c->n % 4 == 0) &&
+                         ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
                          tc::make_out_map(&mOut, out, c->n, m);
   if (!tma_store) std::memset(&mOut, 0, sizeof(mOut));
   tc::Params p;

@@ -253,8 +253,9 @@ def test_every_ls_variant_and_autotune(c1_small, mode):
     params = p.test_params[:100]
     Yo, rho_o = case.oracle_solve(params)
     # plain: 5 shared-memory shapes + 1 register-resident; mixed: 5 shapes with float64 M
-    # in shared memory, 5 without, 2 register-resident, 5 with M in a global slot per CTA
-    nvar = 6 if mode == api.SAS_MODE_PLAIN else 17
+    # in shared memory, 5 without, 2 register-resident, 5 with M in a global slot per CTA,
+    # 4 blocked (panels of 8 reflectors applied to register-resident trailing columns)
+    nvar = 6 if mode == api.SAS_MODE_PLAIN else 21
     P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
     solver = AffineSolver(p, case.S, case.J, mode=mode, device=DEV)
     bound = _mixed_bound(p, case.S, case.J, params, Yo, rho_o)
@@ -271,6 +272,20 @@ def test_every_ls_variant_and_autotune(c1_small, mode):
     chosen, times = api.subapsnap_autotune(solver.ctx, P, len(params), 2)
     print(f"autotune mode {mode}: chosen {chosen}, times {[round(t, 4) for t in times[:nvar]]}")
     assert 0 <= chosen < nvar and times[chosen] > 0
+    solver.close()
+
+
+def test_blocked_variants_reject_what_does_not_fit():
+    """A blocked variant whose registers cannot hold a trailing column (s > G E) and
+    every blocked variant on a complex context are refused, not run."""
+    case = Case("diffusion_2d", basis="random", rows="random", N=30, r=20, s=300, m=4)
+    P = torch.from_numpy(np.ascontiguousarray(case.prob.test_params)).to(DEV)
+    solver = AffineSolver(case.prob, case.S, case.J, mode=api.SAS_MODE_MIXED, device=DEV)
+    for v in (17, 18, 19, 20):  # s = 300 > 256 >= G E for all four
+        api.subapsnap_set_option(solver.ctx, api.SAS_OPT_LS_VARIANT, v)
+        Y = torch.empty((4, 20), dtype=torch.float64, device=DEV)
+        with pytest.raises(api.SasError):
+            solver.solve(P, api.SAS_OUT_Y, Y)
     solver.close()
 
 
@@ -314,14 +329,15 @@ def test_blocked_householder_path_complex():
 
 @pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED])
 def test_register_variants_on_c0_and_multichunk(c0, mode):
-    """The register-resident shapes on the 1-D workload (s = 40, r = 20): ragged row
-    ownership (40 rows over 4 or 8 lanes) and unused column slots."""
+    """The register-resident and blocked shapes on the 1-D workload (s = 40, r = 20):
+    ragged row ownership (40 rows over 4 or 8 lanes), unused column slots, a last
+    panel of 4 columns."""
     p = c0.prob
     params = p.test_params[:300]
     Yo, rho_o = c0.oracle_solve(params)
     P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
     solver = AffineSolver(p, c0.S, c0.J, mode=mode, device=DEV)
-    variants = [5] if mode == api.SAS_MODE_PLAIN else [10, 11]
+    variants = [5] if mode == api.SAS_MODE_PLAIN else [10, 11, 17, 18, 19, 20]
     bound = _mixed_bound(p, c0.S, c0.J, params, Yo, rho_o)
     kap = c0.kappas(params)
     for v in variants:

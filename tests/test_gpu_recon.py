@@ -24,9 +24,10 @@ from paper_2510_04825_gb300.solver import AffineSolver  # noqa: E402
 from _problems import Case  # noqa: E402
 
 
-def xhat(case, kernel, params, on_device=False):
+def xhat(case, kernel, params, on_device=False, store=0):
     solver = AffineSolver(case.prob, case.S, case.J, mode=api.SAS_MODE_MIXED, device="cuda")
     api.subapsnap_set_option(solver.ctx, api.SAS_OPT_RECON_KERNEL, kernel)
+    api.subapsnap_set_option(solver.ctx, api.SAS_OPT_RECON_STORE, store)
     m = params.shape[0]
     P = torch.from_numpy(np.ascontiguousarray(params)).cuda()
     out = torch.full((m, case.prob.n), float("nan"), dtype=torch.float32, device="cuda")
@@ -50,11 +51,12 @@ def test_tensor_core_reconstruction(N, r, s, m):
     Xcc = xhat(case, 1, params)
     e_cc = np.linalg.norm(Xcc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
     assert e_cc.max() <= 2e-6
-    for kernel in (2, 3, 5):  # tf32 64- and 128-parameter tiles, f16 splits
-        Xtc = xhat(case, kernel, params)
+    # tf32 64- and 128-parameter tiles, f16 splits; TMA-store and direct-store epilogues
+    for kernel, store in ((2, 0), (3, 0), (5, 0), (5, 1), (3, 1)):
+        Xtc = xhat(case, kernel, params, store=store)
         assert np.isfinite(Xtc).all()
         e_tc = np.linalg.norm(Xtc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
-        print(f"N={N} r={r} m={m}: tcgen05 ({kernel}) max rel err {e_tc.max():.2e}, "
+        print(f"N={N} r={r} m={m}: tcgen05 ({kernel}, store {store}) max rel err {e_tc.max():.2e}, "
               f"CUDA cores {e_cc.max():.2e}")
         assert e_tc.max() <= 2e-6
 
@@ -91,11 +93,11 @@ def test_tensor_core_reconstruction_large_n_many_batch_sizes():
     for m in (1, 64, 100, 128, 256, 300):
         params = p.test_params[:m]
         Xcc = xhat(case, 1, params)
-        for kernel in (2, 3, 5):
-            Xtc = xhat(case, kernel, params)
+        for kernel, store in ((2, 0), (3, 0), (5, 0), (5, 1)):
+            Xtc = xhat(case, kernel, params, store=store)
             d = np.linalg.norm(Xtc - Xcc, axis=1) / np.linalg.norm(Xcc, axis=1)
             bad = np.nonzero(d > 2e-6)[0]
-            assert bad.size == 0, (kernel, m, bad[:8], d.max())
+            assert bad.size == 0, (kernel, store, m, bad[:8], d.max())
         Yo, _ = case.oracle_solve(params[:3])
         Xo = Yo @ case.S.T
         e = np.linalg.norm(Xtc[:3] - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
