@@ -219,12 +219,13 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
 
 /* Per-context options (subapsnap_set_option).  Not in the paper.
  *  SAS_OPT_RECON_KERNEL: mixed-form reconstruction kernel: 0 = automatic
- *      (tensor cores when r <= 64, as 5), 1 = CUDA cores, 2 = tensor cores
+ *      (tensor cores when r <= 64, as 3), 1 = CUDA cores, 2 = tensor cores
  *      (tcgen05, kind::tf32, three split products) with 64-parameter tiles,
  *      3 = as 2 with 128-parameter tiles, 4 = as 3 with the parameter tiles
  *      of each row tile visited in a rotated order, 5 = tensor cores
  *      (kind::f16) on power-of-two-scaled f16 splits of S and y, three
- *      products into two accumulators, 128-parameter tiles.
+ *      products into two accumulators, 128-parameter tiles, 6 = as 3 with
+ *      eight epilogue warps (direct stores).
  *  SAS_OPT_MAX_REFINE: most refinement steps of the mixed solve (0..16,
  *      default 4).
  *  SAS_OPT_REFINE_TOL: refinement stops when ||delta|| <= tol ||y||
@@ -241,7 +242,7 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
  *  SAS_OPT_RECON_STORE: epilogue of the tensor-core reconstruction: 0 = tiles
  *      staged in shared memory and written by TMA bulk-tensor stores (when n
  *      is a multiple of 4 and the output 16-byte aligned), 1 = coalesced
- *      streaming stores straight from registers. */
+ *      streaming stores straight from registers (default). */
 enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
        SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4, SAS_OPT_ASSEMBLY_SEGMENT = 5,
        SAS_OPT_RECON_STORE = 6 };

@@ -245,6 +245,7 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
   }
   c->b_full = d->b;
   c->recon_kernel = 0;
+  c->recon_store = 1;
   c->max_refine = 4;
   c->refine_tol = 1e-13;
   int dev = 0;
@@ -342,6 +343,7 @@ sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
   c->X = d->X;
   c->b_full = d->b;
   c->recon_kernel = 0;
+  c->recon_store = 1;
   c->max_refine = 4;
   c->refine_tol = 1e-13;
   c->krr_seg_points = 1024;
@@ -840,8 +842,8 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");
   switch (key) {
     case SAS_OPT_RECON_KERNEL:
-      if (!(value >= 0.0 && value <= 5.0 && value == (double)(int)value))
-        return fail(SAS_EINVAL, "recon kernel must be 0, 1, 2, 3, 4 or 5");
+      if (!(value >= 0.0 && value <= 6.0 && value == (double)(int)value))
+        return fail(SAS_EINVAL, "recon kernel must be an integer in [0, 6]");
       c->recon_kernel = (int)value;
       return SAS_OK;
     case SAS_OPT_MAX_REFINE:

@@ -39,7 +39,10 @@ namespace sas {
 
 namespace tc {
 
-constexpr int kThreads = 192;
+// 2 warps (TMA, MMA) + EW epilogue warps: EW = 4 (one per TMEM lane quarter)
+// or 8 (two per quarter, each taking half of a tile's columns; direct stores)
+template <int EW>
+constexpr int threads_for() { return 64 + 32 * EW; }
 constexpr int kBM = 128;              // rows of S per tile (MMA M)
 constexpr int kABox = 128 * 128;      // A box: 128 rows x 32 floats (128-byte rows)
 
@@ -96,8 +99,8 @@ __device__ inline int unit_tile(const Params& p, int u, int nt0, int nt1, int k)
   return nt0 + (t >= len ? t - len : t);
 }
 
-template <int BN, bool F16>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int BN, bool F16, int EW>
+__global__ void __launch_bounds__(threads_for<EW>(), 1)
     reconstruct_tc_kernel(const __grid_constant__ CUtensorMap tmAhi,
                           const __grid_constant__ CUtensorMap tmAlo,
                           const __grid_constant__ CUtensorMap tmBhi,
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int a = 0; a < kAcc; ++a) {
       mbar_init(tfull0 + 8 * a, 1);
-      mbar_init(tempty0 + 8 * a, 4);
+      mbar_init(tempty0 + 8 * a, EW);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -265,8 +268,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (last >= 0) mbar_drain(tfull0 + 8 * (last & (kAcc - 1)), (uint32_t)(last / kAcc) & 1u);
     }
   } else {
-    // ---------------- epilogue: warps 2..5, lane quarter q = warp % 4
+    // ---------------- epilogue: warps 2 .. 2 + EW - 1, lane quarter q = warp % 4; with
+    // EW = 8 the two warps of a quarter take alternate halves of each tile's columns
     const int q = warp & 3;
+    constexpr int kBoxes = kBN / 32, kMine = EW == 8 ? kBoxes / 2 : kBoxes;
+    const int cb0 = EW == 8 ? ((warp - 2) >> 2) * kMine : 0;
     int issued = 0;  // TMA stores issued by this warp: selects the staging buffer
     int t = 0;
     bool stop = false;
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         fence_after();
-        for (int cb = 0; cb < kBN / 32; ++cb) {
+        for (int cb = cb0; cb < cb0 + kMine; ++cb) {
           float v[32];
           const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kSlotCols + cb * 32);
           tmem_ld32(ta, v);
@@ -475,13 +481,13 @@ __global__ void split_y16_kernel(const float* ys, int64_t m, int rpad, int r, in
 
 }  // namespace tc
 
-template <int BN, bool F16>
+template <int BN, bool F16, int EW>
 static cudaError_t launch_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                              bool rotate, cudaStream_t st) {
   if (m > 2147483647 - BN || c->n > 2147483647 - tc::kBM) return cudaErrorInvalidValue;
   const int rpad = (c->r + 31) / 32 * 32;
   const size_t smem = tc_smem_bytes<BN, F16>(rpad);
-  cudaError_t e = cudaFuncSetAttribute(tc::reconstruct_tc_kernel<BN, F16>,
+  cudaError_t e = cudaFuncSetAttribute(tc::reconstruct_tc_kernel<BN, F16, EW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   CUtensorMap mAhi, mAlo, mBhi, mBlo;
@@ -510,7 +516,8 @@ static cudaError_t launch_tc(const sas_ctx* c, const float* ysplit, int64_t m, f
   }
   // TMA stores need 16-byte aligned rows: n a multiple of 4 and an aligned base
   CUtensorMap mOut;
-  const bool tma_store = c->recon_store == 0 && (c->n % 4 == 0) &&
+  // staging buffers exist for 4 epilogue warps: 8 warps store directly
+  const bool tma_store = EW == 4 && c->recon_store == 0 && (c->n % 4 == 0) &&
                          ((reinterpret_cast<uintptr_t>(out) & 15) == 0) &&
                          tc::make_out_map(&mOut, out, c->n, m);
   if (!tma_store) std::memset(&mOut, 0, sizeof(mOut));
@@ -528,8 +535,8 @@ static cudaError_t launch_tc(const sas_ctx* c, const float* ysplit, int64_t m, f
   p.yscale = ysc;
   p.status = c->dev_status;
   const int grid = (int)(units < c->num_sms ? units : c->num_sms);
-  tc::reconstruct_tc_kernel<BN, F16><<<grid, tc::kThreads, smem, st>>>(mAhi, mAlo, mBhi, mBlo,
-                                                                       mOut, p);
+  tc::reconstruct_tc_kernel<BN, F16, EW><<<grid, tc::threads_for<EW>(), smem, st>>>(
+      mAhi, mAlo, mBhi, mBlo, mOut, p);
   return cudaGetLastError();
 }
 
@@ -591,17 +598,18 @@ cudaError_t setup_f16_basis(sas_ctx* c, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// recon_kernel: 2 = tf32, 64-parameter tiles; 3 = tf32, 128-parameter tiles;
-// 4 = as 3 in a rotated tile order; 5 and 0 (automatic) = f16 splits,
-// 128-parameter tiles.
+// recon_kernel: 2 = tf32, 64-parameter tiles; 3 and 0 (automatic) = tf32,
+// 128-parameter tiles; 4 = as 3 in a rotated tile order; 5 = f16 splits,
+// 128-parameter tiles; 6 = as 3 with 8 epilogue warps (direct stores).
 cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                   cudaStream_t st) {
   if (m == 0) return cudaSuccess;
   switch (c->recon_kernel) {
-    case 2: return launch_tc<64, false>(c, ysplit, m, out, false, st);
-    case 3: return launch_tc<128, false>(c, ysplit, m, out, false, st);
-    case 4: return launch_tc<128, false>(c, ysplit, m, out, true, st);
-    default: return launch_tc<128, true>(c, ysplit, m, out, false, st);
+    case 2: return launch_tc<64, false, 4>(c, ysplit, m, out, false, st);
+    case 4: return launch_tc<128, false, 4>(c, ysplit, m, out, true, st);
+    case 5: return launch_tc<128, true, 4>(c, ysplit, m, out, false, st);
+    case 6: return launch_tc<128, false, 8>(c, ysplit, m, out, false, st);
+    default: return launch_tc<128, false, 4>(c, ysplit, m, out, false, st);
   }
 }
 

@@ -52,7 +52,7 @@ def test_tensor_core_reconstruction(N, r, s, m):
     e_cc = np.linalg.norm(Xcc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
     assert e_cc.max() <= 2e-6
     # tf32 64- and 128-parameter tiles, f16 splits; TMA-store and direct-store epilogues
-    for kernel, store in ((2, 0), (3, 0), (5, 0), (5, 1), (3, 1)):
+    for kernel, store in ((2, 0), (3, 0), (5, 0), (5, 1), (3, 1), (6, 1), (0, 1)):
         Xtc = xhat(case, kernel, params, store=store)
         assert np.isfinite(Xtc).all()
         e_tc = np.linalg.norm(Xtc - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
@@ -93,7 +93,7 @@ def test_tensor_core_reconstruction_large_n_many_batch_sizes():
     for m in (1, 64, 100, 128, 256, 300):
         params = p.test_params[:m]
         Xcc = xhat(case, 1, params)
-        for kernel, store in ((2, 0), (3, 0), (5, 0), (5, 1)):
+        for kernel, store in ((2, 0), (3, 0), (5, 0), (5, 1), (3, 1), (6, 1)):
             Xtc = xhat(case, kernel, params, store=store)
             d = np.linalg.norm(Xtc - Xcc, axis=1) / np.linalg.norm(Xcc, axis=1)
             bad = np.nonzero(d > 2e-6)[0]
@@ -112,7 +112,7 @@ def test_tensor_core_reconstruction_long_units():
     p = case.prob
     params = p.test_params
     Xcc = xhat(case, 1, params, on_device=True)
-    for kernel in (3, 2, 5):
+    for kernel in (3, 2, 5, 6):
         Xtc = xhat(case, kernel, params, on_device=True)
         assert torch.isfinite(Xtc).all().item()
         d = (torch.linalg.vector_norm(Xtc - Xcc, dim=1) / torch.linalg.vector_norm(Xcc, dim=1)).cpu().numpy()
