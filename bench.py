@@ -34,9 +34,28 @@ if ROOT not in sys.path:
 GRID = 1024
 R, S_ROWS, M = 60, 120, 4096
 E2E_CHUNK = 512  # x_hat leaves the device in chunks of 512 parameters
-TC_VERSION = "tcgen05-v2"
+TC_VERSION = "tcgen05-v3-direct-stores"
 METRIC = "new-p solves/sec on 1 GB300 at stated rel. residual (chosen vs plain FP64)"
 WORKLOAD = "diffusion_2d_1024x1024_r60_s120_m4096"
+
+
+def read_traffic(path, version):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary
+    (`key: value` lines), or None when it is missing or was taken on another
+    version of the kernel."""
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_version") != version:
+        return None
+    try:
+        return float(kv["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def bf16_peak():
@@ -299,16 +318,8 @@ def run_gpu(args):
     rec_avg_ms = rec_ms / max(rec_n, 1)
     alg_bytes = 4.0 * n * R + 4.0 * n * M + 8.0 * M * R  # S (fp32) once, x_hat (fp32), y
     achieved = alg_bytes / (rec_avg_ms * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "reconstruct_traffic.json")
-    if os.path.exists(tpath):
-        try:
-            with open(tpath) as f:
-                tinfo = json.load(f)
-            if tinfo.get("kernel_version") == chosen_kernel_version():
-                traffic = tinfo.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = read_traffic(os.path.join(ROOT, "profiles", "reconstruct_tc_diffusion_2d_1024_traffic.txt"),
+                           chosen_kernel_version())
 
     value = job_throughput(world, M, ms_chosen)
     plain_value = job_throughput(world, M, ms_plain)
