@@ -289,24 +289,23 @@ def run_gpu(args):
     tr = tr.cpu().numpy()
     del X64, X32
 
-    # ---- end to end through the C-ABI with host buffers: params H2D, then x_hat
-    # D2H in chunks on a copy stream, overlapped with the next chunk's reconstruction
+    # ---- end to end through the C-ABI with host buffers: params H2D, the batch, then
+    # x_hat D2H in chunks
     host_params = torch.from_numpy(np.ascontiguousarray(params_host)).pin_memory()
     host_out = [torch.empty((E2E_CHUNK, n), dtype=torch.float32).pin_memory() for _ in range(2)]
     Pdev = torch.empty_like(P)
-    copy_stream = torch.cuda.Stream(device=device)
     nchunks = M // E2E_CHUNK
 
     def e2e_step():
+        # the whole batch on the device, then x_hat to the host chunk by chunk: the
+        # copies are bound by the host link (~190 GB/s), and overlapping them with the
+        # reconstruction's 5.8 TB/s of HBM writes only slows them down
         Pdev.copy_(host_params, non_blocking=True)
         chosen.solve(Pdev, api.SAS_OUT_Y, Ystep, flags, rho_c)
+        chosen.reconstruct(Ystep, out32)
         for c in range(nchunks):
             sl = slice(c * E2E_CHUNK, (c + 1) * E2E_CHUNK)
-            chosen.reconstruct(Ystep[sl], out32[sl])
-            copy_stream.wait_stream(stream)
-            with torch.cuda.stream(copy_stream):
-                host_out[c & 1].copy_(out32[sl], non_blocking=True)
-        stream.wait_stream(copy_stream)
+            host_out[c & 1].copy_(out32[sl], non_blocking=True)
 
     e2e_steps = max(1, min(args.steps, 3))
     ms_e2e, _ = timed(e2e_step, e2e_steps, 1)
@@ -421,16 +420,27 @@ def build_other(args, device, rank):
     elif wl == "kernel_ridge":
         prob = get_config("kernel_ridge")
         X = torch.from_numpy(np.ascontiguousarray(prob.X)).to(device)
-        S_rows, res = wsnap.kernel_ridge_basis_torch(prob, X, device=device, iters=15)
-        info["snapshot_cr_max_rel_residual"] = float(np.max(res))
-        from paper_2510_04825_gb300.solver import select_rows_kernel
-        J, gaps = select_rows_kernel(prob, X, S_rows, prob.sel_param, prob.s)
+        if args.random_basis:
+            # profiling runs: a seeded random orthonormal S and random rows J (the online
+            # stage takes any); skips the snapshot solves and the row selection
+            g = torch.Generator(device=device).manual_seed(3)
+            Z = torch.randn(prob.n, prob.r, dtype=torch.float64, device=device, generator=g)
+            S_rows = wsnap.orthonormalise_torch(Z).T.contiguous()
+            J = np.sort(np.random.default_rng(1).choice(prob.n, prob.s, replace=False))
+        else:
+            S_rows, res = wsnap.kernel_ridge_basis_torch(prob, X, device=device, iters=15)
+            info["snapshot_cr_max_rel_residual"] = float(np.max(res))
+            from paper_2510_04825_gb300.solver import select_rows_kernel
+            J, gaps = select_rows_kernel(prob, X, S_rows, prob.sel_param, prob.s)
         mk = lambda mode: KernelSolver(prob, None, J, mode=mode, device=device, S_device=S_rows,
                                        X_device=X)
         out_kind, out_shape, out_dtype = api.SAS_OUT_Y, (prob.test_params.shape[0], prob.r), torch.float64
     else:
         raise SystemExit(f"unknown workload {wl}")
     params = rank_params(prob.test_params, rank)
+    if args.m is not None:
+        params = params[:args.m]
+        out_shape = (args.m,) + tuple(out_shape[1:])
     P = torch.from_numpy(np.ascontiguousarray(params)).to(device)
     return prob, mk, P, params, out_kind, out_shape, out_dtype, info
 
@@ -503,6 +513,12 @@ def run_gpu_other(args):
     timed(lambda: chosen.solve(P, out_kind, out_c, flags, rho_c), 1, 0)
     traces = {k: api.subapsnap_trace_read(chosen.ctx, k) for k in range(4)}
     api.subapsnap_set_tracing(chosen.ctx, False)
+    if args.quick:
+        asm_ms_q, asm_n_q = traces[api.SAS_KERNEL_ASSEMBLE]
+        ls_ms_q, ls_n_q = traces[api.SAS_KERNEL_LS]
+        print(json.dumps({"workload": args.workload, "m": m, "ms_per_step_chosen": ms_c,
+                          "assemble_ms": asm_ms_q / max(asm_n_q, 1), "ls_ms": ls_ms_q / max(ls_n_q, 1)}))
+        return
     # plain float64 form: the kernel-ridge float64 rows take ~10 ms per parameter, so
     # that form is timed on a sub-batch and reported per parameter
     msub = m if args.workload != "kernel_ridge" else min(m, 128)
@@ -784,6 +800,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain float64 form")
     ap.add_argument("--quick", action="store_true", help="time the chosen form only (profiling runs)")
     ap.add_argument("--grid", type=int, default=GRID, help="interior grid side (profiling runs use 512)")
+    ap.add_argument("--random-basis", action="store_true",
+                    help="kernel ridge: random orthonormal S and random rows J (profiling runs)")
+    ap.add_argument("--m", type=int, default=None, help="parameters per step (profiling runs)")
     ap.add_argument("--ls-variant", type=int, default=None,
                     help="fixed least-squares launch shape of the chosen form, no autotuning")
     ap.add_argument("--workload", default="diffusion_2d",
