@@ -407,6 +407,15 @@ def build_other(args, device, rank):
         mk = lambda mode: AffineSolver(prob, None, J, mode=mode, device=device, S_device=S_rows,
                                        blocks_device=blocks)
         out_kind, out_shape, out_dtype = api.SAS_OUT_QOI, (prob.test_params.shape[0],), torch.complex128
+    elif wl == "delay_system":
+        prob = get_config("delay_system")
+        blocks = [csr_to_device(A, device) for A in prob.blocks]
+        S_rows, res = wsnap.delay_basis_torch(prob, device=device)
+        info["snapshot_banded_max_rel_residual"] = float(res)
+        J, gaps = select_rows(prob, S_rows, blocks, prob.sel_param, prob.s, device=device)
+        mk = lambda mode: AffineSolver(prob, None, J, mode=mode, device=device, S_device=S_rows,
+                                       blocks_device=blocks)
+        out_kind, out_shape, out_dtype = api.SAS_OUT_QOI, (prob.test_params.shape[0],), torch.complex128
     elif wl == "reaction_diffusion_1d":
         prob = get_config("reaction_diffusion_1d")
         blocks = [csr_to_device(A, device) for A in prob.blocks]
@@ -807,7 +816,7 @@ def main():
                     help="fixed least-squares launch shape of the chosen form, no autotuning")
     ap.add_argument("--workload", default="diffusion_2d",
                     choices=["diffusion_2d", "transfer_function", "reaction_diffusion_1d", "kernel_ridge",
-                             "surrogate_diffusion_2d"])
+                             "surrogate_diffusion_2d", "delay_system"])
     ap.add_argument("--epochs", type=int, default=100, help="surrogate training epochs")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -67,8 +67,12 @@ enum { SAS_REAL64 = 0, SAS_COMPLEX128 = 1 };
  *  SAS_THETA_PENCIL: theta = (-1, i*omega), dp = 1 (p = omega), K = 2,
  *                    A = (i omega) E - A_0 with blocks (A_0, E): the
  *                    transfer-function resolvent of Sec. 5.2 (Eq. 9) on the
- *                    imaginary axis.  Requires SAS_COMPLEX128.            */
-enum { SAS_THETA_LINEAR = 0, SAS_THETA_PENCIL = 1 };
+ *                    imaginary axis.  Requires SAS_COMPLEX128.
+ *  SAS_THETA_DELAY:  theta = (i*omega, -1, -exp(i*omega*tau)), dp = 2
+ *                    (p = (omega, tau)), K = 3: A = p I - A_0 - e^{tau p} A_1
+ *                    with blocks (I, A_0, A_1) at p = i omega, the delay
+ *                    system of Sec. 5.2.3.  Requires SAS_COMPLEX128.       */
+enum { SAS_THETA_LINEAR = 0, SAS_THETA_PENCIL = 1, SAS_THETA_DELAY = 2 };
 
 /* Quantity of interest computed from y without any n-vector (Sec. 5.2.2). */
 enum { SAS_QOI_NONE = 0, SAS_QOI_TRANSPOSE = 1 /* c^T x, plain transpose */,
@@ -101,7 +105,7 @@ typedef struct {
   int32_t s;            /* rows in the subsample (r <= s <= n, s <= 512) */
   int32_t K;            /* number of terms, 1..SAS_MAX_TERMS */
   int32_t dtype;        /* SAS_REAL64 or SAS_COMPLEX128 */
-  int32_t theta_rule;   /* SAS_THETA_LINEAR or SAS_THETA_PENCIL */
+  int32_t theta_rule;   /* SAS_THETA_LINEAR, SAS_THETA_PENCIL or SAS_THETA_DELAY */
   int32_t mode;         /* SAS_MODE_PLAIN or SAS_MODE_MIXED */
   const void* S;        /* device, n x r, leading dimension ldS >= n */
   int64_t ldS;

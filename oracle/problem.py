@@ -17,13 +17,18 @@ def theta(rule: str, p) -> np.ndarray:
     """Coefficients theta_k(p) of A(p) = sum_k theta_k(p) A_k.
 
     "linear": (1, p_1, ..., p_d).  "pencil": A(s) = s E - A_0 at s = i*omega,
-    so theta = (-1, i*omega) against the blocks (A_0, E).
+    so theta = (-1, i*omega) against the blocks (A_0, E).  "delay": the delay
+    system of Sec. 5.2.3, A(p) = p I - A_0 - e^{tau p} A_1 at p = i*omega, with
+    the parameter vector (omega, tau): theta = (i omega, -1, -e^{i omega tau})
+    against the blocks (I, A_0, A_1).
     """
     p = np.atleast_1d(np.asarray(p, dtype=np.float64))
     if rule == "linear":
         return np.concatenate([[1.0], p])
     if rule == "pencil":
         return np.array([-1.0 + 0j, 1j * p[0]])
+    if rule == "delay":
+        return np.array([1j * p[0], -1.0 + 0j, -np.exp(1j * p[0] * p[1])])
     raise ValueError(f"unknown theta rule {rule!r}")
 
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libsubapsnap.so")
 SAS_OK, SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA, SAS_ERANK, SAS_ETIMEOUT, SAS_ENOTSUP = range(7)
 SAS_FLAG_ILLCOND, SAS_FLAG_NONFINITE, SAS_FLAG_REFINE_STALL = 1, 2, 4
 SAS_REAL64, SAS_COMPLEX128 = 0, 1
-SAS_THETA_LINEAR, SAS_THETA_PENCIL = 0, 1
+SAS_THETA_LINEAR, SAS_THETA_PENCIL, SAS_THETA_DELAY = 0, 1, 2
 SAS_QOI_NONE, SAS_QOI_TRANSPOSE, SAS_QOI_MEAN = 0, 1, 2
 SAS_MODE_PLAIN, SAS_MODE_MIXED = 0, 1
 SAS_OUT_Y, SAS_OUT_XHAT, SAS_OUT_QOI = 0, 1, 3

@@ -130,6 +130,9 @@ static sas_status check_affine_desc(const sas_affine_desc* d, bool need_J) {
   if (d->theta_rule == SAS_THETA_PENCIL) {
     if (d->dtype != SAS_COMPLEX128 || d->K != 2)
       return fail(SAS_EINVAL, "the pencil rule needs complex128 and K = 2");
+  } else if (d->theta_rule == SAS_THETA_DELAY) {
+    if (d->dtype != SAS_COMPLEX128 || d->K != 3)
+      return fail(SAS_EINVAL, "the delay rule needs complex128 and K = 3");
   } else if (d->theta_rule != SAS_THETA_LINEAR) {
     return fail(SAS_EINVAL, "bad theta rule");
   }
@@ -234,7 +237,7 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
   c->dtype = d->dtype;
   c->theta_rule = d->theta_rule;
   c->mode = d->mode;
-  c->dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->K - 1;
+  c->dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->theta_rule == SAS_THETA_DELAY ? 2 : d->K - 1;
   c->qoi_kind = d->qoi_kind;
   c->S = d->S;
   c->ldS = d->ldS;

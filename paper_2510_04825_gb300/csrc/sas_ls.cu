@@ -27,6 +27,13 @@ template <> __device__ inline double theta_k<double>(int rule, int k, const doub
 }
 template <> __device__ inline zd theta_k<zd>(int rule, int k, const double* p) {
   if (rule == SAS_THETA_PENCIL) return k == 0 ? mkz(-1.0, 0.0) : mkz(0.0, p[0]);
+  if (rule == SAS_THETA_DELAY) {  // p = (omega, tau): (i omega, -1, -e^{i omega tau})
+    if (k == 0) return mkz(0.0, p[0]);
+    if (k == 1) return mkz(-1.0, 0.0);
+    double sn, cs;
+    sincos(p[0] * p[1], &sn, &cs);
+    return mkz(-cs, -sn);
+  }
   return mkz(k == 0 ? 1.0 : p[k - 1], 0.0);
 }
 

@@ -24,6 +24,13 @@ template <> __device__ inline double theta_sel<double>(int rule, int k, const do
 }
 template <> __device__ inline zd theta_sel<zd>(int rule, int k, const double* p) {
   if (rule == SAS_THETA_PENCIL) return k == 0 ? mkz(-1.0, 0.0) : mkz(0.0, p[0]);
+  if (rule == SAS_THETA_DELAY) {  // p = (omega, tau): (i omega, -1, -e^{i omega tau})
+    if (k == 0) return mkz(0.0, p[0]);
+    if (k == 1) return mkz(-1.0, 0.0);
+    double sn, cs;
+    sincos(p[0] * p[1], &sn, &cs);
+    return mkz(-cs, -sn);
+  }
   return mkz(k == 0 ? 1.0 : p[k - 1], 0.0);
 }
 
@@ -282,7 +289,7 @@ static sas_status select_t(const sas_affine_desc* d, const double* p_sel, int64_
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->K - 1;
+  const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->theta_rule == SAS_THETA_DELAY ? 2 : d->K - 1;
   SelTable h;
   for (int k = 0; k < SAS_MAX_TERMS; ++k) {
     h.rp[k] = d->rowptr[k];

@@ -29,6 +29,12 @@ def basis_to_device(S, device, complex_valued=False):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(S, dtype=dt).T)).to(device)
 
 
+def theta_rule_code(rule):
+    """C-ABI code of a problem's theta rule."""
+    return {"linear": api.SAS_THETA_LINEAR, "pencil": api.SAS_THETA_PENCIL,
+            "delay": api.SAS_THETA_DELAY}[rule]
+
+
 class AffineSolver:
     """Context for A(p) = sum_k theta_k(p) A_k built from a workload problem."""
 
@@ -51,7 +57,7 @@ class AffineSolver:
             qk = api.SAS_QOI_TRANSPOSE
             self.c = c_device if c_device is not None else \
                 torch.from_numpy(np.ascontiguousarray(prob.c, dtype=np.float64)).to(device)
-        rule = api.SAS_THETA_PENCIL if prob.theta_rule == "pencil" else api.SAS_THETA_LINEAR
+        rule = theta_rule_code(prob.theta_rule)
         self.J = np.asarray(J, dtype=np.int64)
         self.desc = api._affine_desc(prob.n, prob.r, len(self.J), self.blocks, self.S, self.J,
                                      self.b, rule, mode, qk, self.c, cplx)
@@ -89,7 +95,7 @@ class AffineSolver:
 def select_rows(prob, S_device, blocks_device, p_sel, s, device="cuda"):
     """CPQR-in-rounds row selection on the device; returns (J, gaps) on the host."""
     cplx = bool(prob.complex_valued)
-    rule = api.SAS_THETA_PENCIL if prob.theta_rule == "pencil" else api.SAS_THETA_LINEAR
+    rule = theta_rule_code(prob.theta_rule)
     desc = api._affine_desc(prob.n, prob.r, s, blocks_device, S_device, None, None, rule,
                             api.SAS_MODE_PLAIN, api.SAS_QOI_NONE, None, cplx)
     return api.subapsnap_select_rows_affine(desc, p_sel, s)

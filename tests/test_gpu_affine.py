@@ -43,6 +43,11 @@ def c1_small():
 
 
 @pytest.fixture(scope="module")
+def delay_small():
+    return Case("delay_system", n=3000, r=16, s=32, m=120)
+
+
+@pytest.fixture(scope="module")
 def c3_small():
     return Case("transfer_function", N=9, r=20, s=50, m=300)
 
@@ -138,7 +143,7 @@ def mixed_bound(case, params, Yo, rho_o):
     return _mixed_bound(case.prob, case.S, case.J, params, Yo, rho_o)
 
 
-@pytest.mark.parametrize("name", ["c0", "c1_small", "c3_small"])
+@pytest.mark.parametrize("name", ["c0", "c1_small", "c3_small", "delay_small"])
 def test_mixed_error_bound_and_equal_residual(name, request):
     case = request.getfixturevalue(name)
     p = case.prob
@@ -176,6 +181,27 @@ def test_c3_small_plain_parity_and_qoi(c3_small):
     Ho = online.qoi(p, c3_small.S, Yo)
     kap_ok = kap * 1.1e-16 <= 1e-11
     np.testing.assert_allclose(H[kap_ok], Ho[kap_ok], rtol=1e-10, atol=1e-12 * np.abs(Ho).max())
+
+
+def test_delay_system_plain_parity_qoi_and_selection(delay_small):
+    """The delay rule theta = (i omega, -1, -e^{i omega tau}) on (I, A_0, A_1): y, the
+    transfer function H = c^T S y and the device row selection against the oracle."""
+    case = delay_small
+    p = case.prob
+    err, kap = plain_parity(case)
+    print(f"delay system plain: max rel err {err.max():.2e}, kappa max {kap.max():.2e}")
+    H, _, _ = run(case, api.SAS_MODE_PLAIN, api.SAS_OUT_QOI)
+    Yo, _ = case.oracle_solve(p.test_params)
+    from oracle import online
+    Ho = online.qoi(p, case.S, Yo)
+    kap_ok = kap * 1.1e-16 <= 1e-11
+    np.testing.assert_allclose(H[kap_ok], Ho[kap_ok], rtol=1e-10, atol=1e-12 * np.abs(Ho).max())
+    S_d = basis_to_device(case.S, DEV, complex_valued=True)
+    blocks = [csr_to_device(A, DEV) for A in p.blocks]
+    J, gaps = select_rows(p, S_d, blocks, p.sel_param, p.s)
+    near = np.nonzero(case.gaps < 1e-10)[0]
+    upto = near[0] if near.size else p.s
+    np.testing.assert_array_equal(J[:upto], case.J[:upto])
 
 
 def test_c3_small_row_selection_complex(c3_small):

@@ -7,6 +7,9 @@ solves it (one call for the whole batch):
     16,384 frequencies, QoI output: y and H(i w) for 10 sampled w, plain
     float64 within 1e-10 (kappa-filtered as elsewhere), mixed within the
     refinement bound;
+  delay system, n = 10^7 (Sec. 5.2.3), r = 40, s = 80, 5000 frequencies, QoI
+    output: y and H(i w) for 8 sampled w, plain float64 within 1e-10
+    (kappa-filtered), mixed within the refinement bound;
   kernel ridge, N = 200,000 points in R^8, r = 100, s = 300, 2048 (sigma,
     lambda): y for 6 sampled parameters, plain float64 within 1e-10; the mixed
     form with tensor-core kernel rows (49 float64 folds per row tile) within
@@ -70,6 +73,48 @@ def test_transfer_function_full_size():
                 bound = mixed_bound(prob, S, J, [p], [yo], [rho_o])[0]
                 assert ey <= bound, (j, ey, bound)
         print(f"transfer function full size, mode {mode}: max rel err y {worst:.2e}")
+        solver.close()
+
+
+def test_delay_system_full_size():
+    prob = get_config("delay_system")
+    blocks = [csr_to_device(A, "cuda") for A in prob.blocks]
+    S_rows, res = wsnap.delay_basis_torch(prob, device="cuda")
+    assert res < 1e-10
+    J, gaps = select_rows(prob, S_rows, blocks, prob.sel_param, prob.s)
+    assert len(set(J.tolist())) == prob.s
+    S = np.ascontiguousarray(S_rows.cpu().numpy().T)
+    m = prob.test_params.shape[0]
+    P = torch.from_numpy(np.ascontiguousarray(prob.test_params)).cuda()
+    pick = np.unique(np.concatenate([[0, m // 2, m - 1], np.random.default_rng(5).choice(m, 5, replace=False)]))
+    wq = online.qoi_vector(prob, S)
+    for mode in (api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED):
+        solver = AffineSolver(prob, None, J, mode=mode, device="cuda", S_device=S_rows, blocks_device=blocks)
+        H = torch.empty(m, dtype=torch.complex128, device="cuda")
+        Y = torch.empty((m, prob.r), dtype=torch.complex128, device="cuda")
+        solver.solve(P, api.SAS_OUT_QOI, H)
+        solver.solve(P, api.SAS_OUT_Y, Y)
+        torch.cuda.synchronize()
+        H, Y = H.cpu().numpy(), Y.cpu().numpy()
+        assert np.isfinite(H).all()
+        worst = 0.0
+        for j in pick:
+            p = prob.test_params[j]
+            yo, rho_o = online.solve_one(prob, S, J, p)
+            M = online.subsampled_matrix(prob, S, J, p)
+            sv = np.linalg.svd(M, compute_uv=False)
+            kap = sv[0] / sv[-1]
+            ey = np.linalg.norm(Y[j] - yo) / np.linalg.norm(yo)
+            worst = max(worst, ey)
+            if mode == api.SAS_MODE_PLAIN:
+                if kap * 1.1e-16 <= 1e-11:
+                    assert ey <= 1e-10, (j, ey, kap)
+                    ho = wq @ yo
+                    assert abs(H[j] - ho) <= 1e-10 * abs(ho) + 1e-12 * np.abs(wq).max() * np.abs(yo).max()
+            else:
+                bound = mixed_bound(prob, S, J, [p], [yo], [rho_o])[0]
+                assert ey <= bound, (j, ey, bound)
+        print(f"delay system n = 1e7, mode {mode}: max rel err y {worst:.2e}")
         solver.close()
 
 

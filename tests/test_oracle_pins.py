@@ -60,6 +60,7 @@ def test_full_sampling_is_apsnap(cplx):
     ("reaction_diffusion_1d", dict(n=256, r=8, s=16, m=4)),
     ("diffusion_2d", dict(N=12, r=6, s=12, m=4)),
     ("transfer_function", dict(N=5, r=5, s=12, m=4)),
+    ("delay_system", dict(n=300, r=8, s=16, m=4)),
 ])
 def test_snapshot_parameter_recovers_solution(name, kw):
     prob = nonsymmetric_problem() if name == "nonsym" else get_config(name, **kw)
@@ -193,3 +194,23 @@ def test_kernel_ridge_snapshot_recovery():
         sv = np.linalg.svd(M, compute_uv=False)
         kappa = sv[0] / sv[-1]
         assert np.linalg.norm(S @ y - X[:, i]) <= 1e-14 * kappa * np.linalg.norm(X[:, i])
+
+
+def test_delay_theta_rebuilds_the_delay_operator():
+    """A(p) from the delay rule and the blocks equals p I - A_0 - e^{tau p} A_1 written
+    out from its definition in Sec. 5.2.3 (T tridiagonal with unit off-diagonals and
+    T_11 = T_nn = 1, A_1 = (T - kappa I)/tau, A_0 = 3 A_1), at p = i omega; a swapped
+    block, a sign or a missing factor tau in the exponent shows as a mismatch."""
+    n, tau, kappa = 9, 0.1, 2.1
+    prob = get_config("delay_system", n=n, r=4, s=8, m=3, tau=tau, kappa=kappa)
+    T = np.zeros((n, n))
+    for i in range(n - 1):
+        T[i, i + 1] = T[i + 1, i] = 1.0
+    T[0, 0] = T[-1, -1] = 1.0
+    A1 = (T - kappa * np.eye(n)) / tau
+    A0 = 3.0 * A1
+    for omega in (0.37, 12.5, 300.0):
+        p = 1j * omega
+        ref = p * np.eye(n) - A0 - np.exp(tau * p) * A1
+        got = problem.full_matrix(prob, np.array([omega, tau])).toarray()
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())

@@ -9,6 +9,7 @@ Parameter conventions (what the online stage receives per new parameter):
   diffusion_2d          : p in [0, 1]^4           A(p) = A_0 + sum_k p_k A_k
   kernel_ridge          : p = (sigma, lambda)     A(p) = K_sigma + lambda I
   transfer_function     : p = omega, s = i omega  A(s) = s E - A_0
+  delay_system          : p = (omega, tau)        A = i omega I - A_0 - e^{i omega tau} A_1
 """
 from __future__ import annotations
 
@@ -27,6 +28,8 @@ class AffineProblem:
     ``theta_rule`` names how theta(p) is formed from a parameter vector:
       "linear": theta = (1, p_1, ..., p_d)        (real)
       "pencil": theta = (-1, i*omega) for (A_0, E) (complex; p = omega)
+      "delay":  theta = (i omega, -1, -e^{i omega tau}) for (I, A_0, A_1)
+                (complex; p = (omega, tau))
     """
     name: str
     n: int
@@ -188,11 +191,33 @@ def make_kernel_ridge(N=200_000, d=8, ncomp=10, nfreq=5, r=100, s=300, m=2048, s
     )
 
 
+def make_delay_system(n=10_000_000, r=40, s=80, m=5000, tau=0.1, kappa=2.1) -> AffineProblem:
+    """Delay system H(p) = c^T (p I - A_0 - e^{tau p} A_1)^{-1} b on the imaginary axis
+    p = i omega (Sec. 5.2.3, Table 4): A_1 = (T - kappa I)/tau, A_0 = 3 A_1, tau = 0.1,
+    kappa = 2.1.  b = c = ones.  Snapshots at r log-spaced omega in [1e-2, 1e3];
+    test omega = logspace(-2, 3, m) (endpoints shared with the snapshots); selection at
+    the log-midpoint omega = 10^0.5.  Parameters carry tau as their second entry.
+    No random draws.
+    """
+    I, A0, A1 = ops.delay_blocks(n, tau, kappa)
+    snap = np.logspace(-2, 3, r)
+    test = np.logspace(-2, 3, m)
+    return AffineProblem(
+        name="delay_system", n=n, blocks=[I, A0, A1], theta_rule="delay",
+        b=np.ones(n, dtype=np.complex128), r=r, s=s,
+        snap_params=np.stack([snap, np.full(r, tau)], 1),
+        sel_param=np.array([10.0 ** 0.5, tau]),
+        test_params=np.stack([test, np.full(m, tau)], 1), complex_valued=True,
+        c=np.ones(n), qoi_kind="transpose", meta={"tau": tau, "kappa": kappa},
+    )
+
+
 CONFIGS = {
     "reaction_diffusion_1d": make_reaction_diffusion_1d,
     "diffusion_2d": make_diffusion_2d,
     "kernel_ridge": make_kernel_ridge,
     "transfer_function": make_transfer_function,
+    "delay_system": make_delay_system,
     "surrogate_diffusion_2d": make_surrogate_diffusion_2d,
 }
 

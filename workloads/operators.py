@@ -64,6 +64,18 @@ def gaussian_bump_faces(N: int, centre: np.ndarray, width: float):
     return a_x, a_y
 
 
+def delay_blocks(n: int, tau: float, kappa: float):
+    """(I, A_0, A_1) of the delay system: A_1 = (T - kappa I) / tau, A_0 = 3 A_1, where T
+    is tridiagonal with ones on both off-diagonals and T_11 = T_nn = 1 (Sec. 5.2.3)."""
+    off = np.ones(n - 1)
+    diag = np.zeros(n)
+    diag[0] = diag[-1] = 1.0
+    T = sp.diags([off, diag, off], [-1, 0, 1], format="csr")
+    A1 = ((T - kappa * sp.identity(n, format="csr")) / tau).tocsr()
+    A0 = (3.0 * A1).tocsr()
+    return sp.identity(n, format="csr", dtype=np.float64), A0, A1
+
+
 def heat_3d(N: int) -> sp.csr_matrix:
     """A0 = h^-2 * (7-point Laplacian), -6 on the diagonal, +1 on neighbours.
 

@@ -27,7 +27,21 @@ def _A(prob, p):
         return A.tocsc()
     if prob.theta_rule == "pencil":
         return (1j * p[0] * prob.blocks[1] - prob.blocks[0]).tocsc()
+    if prob.theta_rule == "delay":
+        return (1j * p[0] * prob.blocks[0] - prob.blocks[1]
+                - np.exp(1j * p[0] * p[1]) * prob.blocks[2]).tocsc()
     raise ValueError(prob.theta_rule)
+
+
+def _tridiagonal_solve(A, b):
+    """A tridiagonal sparse matrix: banded LU (LAPACK gbsv through scipy)."""
+    A = A.tocsr()
+    n = A.shape[0]
+    ab = np.zeros((3, n), dtype=np.result_type(A.dtype, b.dtype))
+    ab[0, 1:] = A.diagonal(1)
+    ab[1] = A.diagonal(0)
+    ab[2, :-1] = A.diagonal(-1)
+    return sla.solve_banded((1, 1), ab, b)
 
 
 def snapshot_solutions(prob) -> np.ndarray:
@@ -49,8 +63,24 @@ def snapshot_solutions(prob) -> np.ndarray:
             K = gaussian_kernel_block(prob.X, prob.X, sig) + lam * np.eye(prob.n)
             cols.append(np.linalg.solve(K, prob.b))
         return np.stack(cols, 1)
+    if prob.theta_rule == "delay":  # tridiagonal at every parameter
+        return np.stack([_tridiagonal_solve(_A(prob, p), prob.b) for p in prob.snap_params], 1)
     cols = [spla.spsolve(_A(prob, p), prob.b) for p in prob.snap_params]
     return np.stack(cols, 1)
+
+
+def delay_basis_torch(prob, device="cuda"):
+    """Orthonormal snapshot basis of the delay system on the device: banded LU solves
+    on the host (n = 1e7 is a few seconds each), Gram-Schmidt on the device.
+    Returns (S_rows (r, n) complex128, max relative residual of the solves)."""
+    import torch
+    X = snapshot_solutions(prob)
+    res = []
+    for k, p in enumerate(prob.snap_params):
+        A = _A(prob, p)
+        res.append(np.linalg.norm(A @ X[:, k] - prob.b) / np.linalg.norm(prob.b))
+    Q = orthonormalise_torch(torch.from_numpy(X).to(device))
+    return Q.T.contiguous(), float(np.max(res))
 
 
 def orthonormalise(X: np.ndarray) -> np.ndarray:
