@@ -22,21 +22,29 @@ def subsampled_matrix(prob, S: np.ndarray, J, p) -> np.ndarray:
     return np.asarray(R @ S)
 
 
-def solve_one(prob, S, J, p, bJ=None):
-    """(y, rho_sub): subsampled LS solution and its relative residual."""
+def solve_one(prob, S, J, p, bJ=None, w=None):
+    """(y, rho_sub): subsampled LS solution and its relative residual.
+
+    With row weights w (leverage-score sampling, Sec. 4.3.2 footnote) the rows
+    of M and b_J are scaled by w: y = argmin ||W (M y - b_J)||, and rho is
+    ||W (M y - b_J)|| / ||W b_J||.
+    """
     J = np.asarray(J)
     if bJ is None:
         bJ = prob.b[J]
     M = subsampled_matrix(prob, S, J, p)
+    if w is not None:
+        M = M * np.asarray(w)[:, None]
+        bJ = bJ * np.asarray(w)
     y, res = linalg.least_squares(M, bJ)
     return y, res / np.linalg.norm(bJ)
 
 
-def solve_many(prob, S, J, params):
+def solve_many(prob, S, J, params, w=None):
     """Y (m x r) and rho_sub (m) for a list of parameters."""
     ys, rhos = [], []
     for p in params:
-        y, rho = solve_one(prob, S, J, p)
+        y, rho = solve_one(prob, S, J, p, w=w)
         ys.append(y)
         rhos.append(rho)
     return np.array(ys), np.array(rhos)
