@@ -116,6 +116,9 @@ typedef struct {
   const double* values[SAS_MAX_TERMS];  /* device, values per term */
   int32_t qoi_kind;     /* SAS_QOI_* */
   const double* c;      /* device, n real entries for SAS_QOI_TRANSPOSE, else NULL */
+  const double* w;      /* host, s positive row weights (leverage-score sampling,
+                           Sec. 4.3.2 footnote): row i of M(p) and of b_J is scaled
+                           by w[i]; NULL = unweighted */
 } sas_affine_desc;
 
 /* Gaussian-kernel ridge regression A(sigma, lambda) = K_sigma + lambda I,
@@ -254,6 +257,30 @@ enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */
 sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
+
+/* Leverage scores of [A(p_sel) S, b] (Sec. 4.3.2-4.3.3): the squared row norms
+ * of Q in the thin QR of the n x (r+1) matrix, computed on the device in
+ * float64 by CholeskyQR2.  Row selection by leverage-score sampling draws
+ * rows with probability proportional to these scores.
+ *  d: affine descriptor (J, w, mode and QoI fields unused); p_sel: host, dp
+ *     doubles; scores: host, n doubles (sum r + 1 for full column rank).
+ * Synchronous.  Errors: SAS_EINVAL, SAS_ERANK (the matrix is numerically rank
+ * deficient), SAS_ENOMEM, SAS_ECUDA. */
+sas_status subapsnap_leverage_scores_affine(const sas_affine_desc* d, const double* p_sel,
+                                            double* scores);
+
+/* Leverage-score sampling with weights (host only, Sec. 4.3.2 footnote).
+ * s draws with replacement by inverse CDF of pi = scores / total on the
+ * caller's uniforms u[0..s) in [0, 1): the running sums C_i of the scores in
+ * row order give cdf_i = C_i / C_{n-1}, and draw t is the first i with
+ * cdf_i > u[t].  Rows drawn k times are kept once, in increasing order, with
+ * weight sqrt(k / (s pi_i)): pass J_out and w_out (room for s entries) to the
+ * setup (sas_affine_desc.J, .w) with s = *count_out.  The weighted subsampled
+ * residual then estimates the true residual within (1 -/+ eps), eps ~ r log(r)
+ * / s, at p_sel (Sec. 4.3.3).  Errors: SAS_EINVAL. */
+sas_status subapsnap_sample_rows_leverage(const double* scores, int64_t n, int32_t s,
+                                          const double* u, int64_t* J_out, double* w_out,
+                                          int32_t* count_out);
 
 /* Autotuner (not in the paper): times every launch shape of the context's
  * least-squares kernel (threads per CTA, lanes per column group; for the mixed

@@ -11,8 +11,9 @@ eps ~ r log(r) / s, with high probability at p_sel (a heuristic at other p).
 
 Readings (the paper leaves them open):
   * sampling is with replacement, by inverse CDF of the normalised scores on
-    caller-supplied uniforms u in [0, 1): draw t is the first row i with
-    cumsum(pi)[i] > u_t (float64, summed in row order);
+    caller-supplied uniforms u in [0, 1): with C the running sums of the scores
+    in row order (float64) and total = C[-1], draw t is the first row i with
+    C[i] / total > u_t;
   * a row drawn k times is kept once with weight sqrt(k / (s pi_i)), the same
     least-squares objective as k weighted copies;
   * the band uses eps = min(r log(r) / s, 1/2) of Sec. 4.3.3 (r >= 2), r the number of
@@ -31,8 +32,10 @@ def leverage_scores(V: np.ndarray) -> np.ndarray:
 
 def sample_rows(scores: np.ndarray, s: int, u: np.ndarray):
     """(J sorted, weights) from s inverse-CDF draws on the uniforms u (length s)."""
-    pi = scores / scores.sum()
-    cdf = np.cumsum(pi)
+    run = np.cumsum(np.asarray(scores, dtype=np.float64))  # running sums in row order
+    total = run[-1]
+    pi = scores / total
+    cdf = run / total
     draws = []
     for ut in np.asarray(u, dtype=np.float64):
         i = int(np.searchsorted(cdf, ut, side="right"))  # first i with cdf[i] > ut

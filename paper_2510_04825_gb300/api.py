@@ -35,7 +35,7 @@ EXPORTED = [
     "subapsnap_autotune", "subapsnap_surrogate_train", "subapsnap_surrogate_predict",
     "subapsnap_solve_batch_surrogate", "subapsnap_surrogate_weights", "subapsnap_surrogate_grad",
     "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch", "subapsnap_multi_plan_destroy",
-    "subapsnap_selftest_wait",
+    "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine", "subapsnap_sample_rows_leverage",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
@@ -60,7 +60,7 @@ class AffineDesc(ctypes.Structure):
         ("J", ctypes.POINTER(ctypes.c_int64)), ("b", ctypes.c_void_p),
         ("rowptr", ctypes.c_void_p * SAS_MAX_TERMS), ("colind", ctypes.c_void_p * SAS_MAX_TERMS),
         ("values", ctypes.c_void_p * SAS_MAX_TERMS), ("qoi_kind", ctypes.c_int32),
-        ("c", ctypes.c_void_p),
+        ("c", ctypes.c_void_p), ("w", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -125,6 +125,8 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_solve_batch_xhat_noalloc.argtypes = [vp, vp, i64, vp, vp, vp, vp]
         L.subapsnap_trace_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_int64)]
+        L.subapsnap_leverage_scores_affine.argtypes = [ctypes.POINTER(AffineDesc), vp, vp]
+        L.subapsnap_sample_rows_leverage.argtypes = [vp, i64, i32, vp, vp, vp, ctypes.POINTER(ctypes.c_int32)]
         for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
@@ -134,7 +136,8 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_surrogate_predict", "subapsnap_solve_batch_surrogate",
                      "subapsnap_surrogate_weights", "subapsnap_surrogate_grad",
                      "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch",
-                     "subapsnap_selftest_wait"):
+                     "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine",
+                     "subapsnap_sample_rows_leverage"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -162,7 +165,7 @@ def _stream(stream=None):
 
 
 def _affine_desc(n, r, s, blocks, S, J, b, theta_rule, mode, qoi_kind=SAS_QOI_NONE, c=None,
-                 complex_valued=False):
+                 complex_valued=False, w=None):
     """Fill the C descriptor.  ``blocks`` is a list of (rowptr int64, colind int32,
     values float64) CUDA tensors; S is (r, n) row-major in memory, i.e. the
     column-major n x r matrix with ldS = n."""
@@ -180,6 +183,10 @@ def _affine_desc(n, r, s, blocks, S, J, b, theta_rule, mode, qoi_kind=SAS_QOI_NO
         d.rowptr[k], d.colind[k], d.values[k] = _ptr(rp), _ptr(ci), _ptr(va)
     d.qoi_kind = qoi_kind
     d.c = _ptr(c) if c is not None else None
+    if w is not None:
+        wh = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        d.w = wh.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d._w_keep = wh
     return d
 
 
@@ -253,6 +260,29 @@ def subapsnap_autotune(ctx, params, m: int, reps: int = 3, stream=None):
     _check(lib().subapsnap_autotune(ctx, _ptr(params), int(m), int(reps), times,
                                     ctypes.byref(chosen), _stream(stream)))
     return chosen.value, [t for t in times]
+
+
+def subapsnap_leverage_scores_affine(desc: AffineDesc, p_sel) -> np.ndarray:
+    """Leverage scores of [A(p_sel) S, b] (host array of n doubles)."""
+    sc = np.empty(desc.n, dtype=np.float64)
+    ps = np.ascontiguousarray(np.atleast_1d(np.asarray(p_sel, dtype=np.float64)))
+    _check(lib().subapsnap_leverage_scores_affine(ctypes.byref(desc), ps.ctypes.data_as(ctypes.c_void_p),
+                                                  sc.ctypes.data_as(ctypes.c_void_p)))
+    return sc
+
+
+def subapsnap_sample_rows_leverage(scores, s: int, u):
+    """(J, w): s inverse-CDF draws on the uniforms u, duplicates merged into weights."""
+    sc = np.ascontiguousarray(np.asarray(scores, dtype=np.float64))
+    uu = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    J = np.empty(int(s), dtype=np.int64)
+    w = np.empty(int(s), dtype=np.float64)
+    cnt = ctypes.c_int32()
+    _check(lib().subapsnap_sample_rows_leverage(sc.ctypes.data_as(ctypes.c_void_p), int(sc.size), int(s),
+                                                uu.ctypes.data_as(ctypes.c_void_p),
+                                                J.ctypes.data_as(ctypes.c_void_p),
+                                                w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)))
+    return J[:cnt.value].copy(), w[:cnt.value].copy()
 
 
 def subapsnap_reconstruct(ctx, Y, m: int, out, stream=None):

@@ -136,6 +136,10 @@ static sas_status check_affine_desc(const sas_affine_desc* d, bool need_J) {
   } else if (d->theta_rule != SAS_THETA_LINEAR) {
     return fail(SAS_EINVAL, "bad theta rule");
   }
+  if (d->w)
+    for (int i = 0; i < d->s; ++i)
+      if (!(d->w[i] > 0.0) || !std::isfinite(d->w[i]))
+        return fail(SAS_EINVAL, "row weights must be positive and finite");
   if (d->mode != SAS_MODE_PLAIN && d->mode != SAS_MODE_MIXED) return fail(SAS_EINVAL, "bad mode");
   if (d->ldS < d->n) return fail(SAS_EINVAL, "ldS < n");
   if (!is_device_ptr(d->S)) return fail(SAS_EINVAL, "S must be a device pointer");
@@ -279,6 +283,7 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
   TRY(cudaMemset(c->dev_status, 0, sizeof(int)));
   TRY(launch_gather_blocks(c, sst));
   TRY(launch_gather_vectors(c, d->c, sst));
+  if (d->w) TRY(launch_weight_rows(c, d->w, sst));  // weighted rows: W M(p), W b_J
   if (d->mode == SAS_MODE_MIXED) {
     TRY(cudaMalloc(&c->G32, (size_t)d->K * d->s * d->r * esl));
     TRY(cudaMalloc(&c->bJ32, (size_t)d->s * esl));

@@ -232,6 +232,10 @@ cudaError_t launch_gather_blocks(const sas_ctx* c, cudaStream_t st);
 cudaError_t launch_gather_vectors(const sas_ctx* c, const double* cvec, cudaStream_t st);
 cudaError_t launch_make_mixed_copies(const sas_ctx* c, cudaStream_t st);
 cudaError_t setup_f16_basis(sas_ctx* c, cudaStream_t st);  // S16hi / S16lo / s16_shift
+// rows of A(p_sel) S, row-major with row stride ldv (sas_select.cu)
+cudaError_t operator_rows_affine(const sas_affine_desc* d, const double* p_sel, void* V, int ldv);
+// leverage-score weights of the subsampled rows (sas_leverage.cu)
+cudaError_t launch_weight_rows(sas_ctx* c, const double* w_host, cudaStream_t st);
 // tensor-core kernel rows (sas_krr_tc.cu)
 int krr_tc_nb(int r);
 int64_t krr_tc_npad(int64_t n);

@@ -44,7 +44,7 @@ struct SelTable {
 // V[i*r + j] = sum_k theta_k (A_k S)[i, j]
 template <typename T>
 __global__ void apply_operator_kernel(const SelTable* tb, int K, int rule, const T* S, int64_t ldS,
-                                      int64_t n, int r, T* V) {
+                                      int64_t n, int r, T* V, int ldv) {
   const int64_t total = n * r;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
@@ -59,7 +59,7 @@ __global__ void apply_operator_kernel(const SelTable* tb, int K, int rule, const
       for (int64_t e = rp[i]; e < rp[i + 1]; ++e) part += rscale(va[e], S[(int64_t)ci[e] + (int64_t)j * ldS]);
       acc += theta_sel<T>(rule, k, tb->p) * part;
     }
-    V[idx] = acc;
+    V[i * ldv + j] = acc;
   }
 }
 
@@ -303,7 +303,7 @@ static sas_status select_t(const sas_affine_desc* d, const double* p_sel, int64_
   if (e == cudaSuccess) e = cudaMemcpy(dtab, &h, sizeof(SelTable), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     apply_operator_kernel<T><<<sms * 8, 256>>>((const SelTable*)dtab, d->K, d->theta_rule,
-                                               (const T*)d->S, d->ldS, d->n, d->r, (T*)V0);
+                                               (const T*)d->S, d->ldS, d->n, d->r, (T*)V0, d->r);
     e = cudaGetLastError();
   }
   sas_status rc = SAS_OK;
@@ -316,6 +316,38 @@ static sas_status select_t(const sas_affine_desc* d, const double* p_sel, int64_
   cudaFree(dtab);
   cudaFree(V0);
   return rc;
+}
+
+// Rows of A(p_sel) S (row-major, row stride ldv) for the leverage scores.
+template <typename T>
+static cudaError_t operator_rows_t(const sas_affine_desc* d, const double* p_sel, T* V, int ldv) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->theta_rule == SAS_THETA_DELAY ? 2 : d->K - 1;
+  SelTable h;
+  for (int k = 0; k < SAS_MAX_TERMS; ++k) {
+    h.rp[k] = d->rowptr[k];
+    h.ci[k] = d->colind[k];
+    h.va[k] = d->values[k];
+    h.p[k] = k < dp ? p_sel[k] : 0.0;
+  }
+  void* dtab = nullptr;
+  cudaError_t e = cudaMalloc(&dtab, sizeof(SelTable));
+  if (e == cudaSuccess) e = cudaMemcpy(dtab, &h, sizeof(SelTable), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    apply_operator_kernel<T><<<sms * 8, 256>>>((const SelTable*)dtab, d->K, d->theta_rule,
+                                               (const T*)d->S, d->ldS, d->n, d->r, V, ldv);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(dtab);
+  return e;
+}
+
+cudaError_t operator_rows_affine(const sas_affine_desc* d, const double* p_sel, void* V, int ldv) {
+  if (d->dtype == SAS_COMPLEX128) return operator_rows_t<zd>(d, p_sel, (zd*)V, ldv);
+  return operator_rows_t<double>(d, p_sel, (double*)V, ldv);
 }
 
 // column-major n x r (ld n) -> row-major n x r

@@ -39,7 +39,7 @@ class AffineSolver:
     """Context for A(p) = sum_k theta_k(p) A_k built from a workload problem."""
 
     def __init__(self, prob, S, J, mode=api.SAS_MODE_PLAIN, device="cuda", S_device=None,
-                 blocks_device=None, b_device=None, c_device=None):
+                 blocks_device=None, b_device=None, c_device=None, weights=None):
         self.prob = prob
         self.device = device
         cplx = bool(prob.complex_valued)
@@ -60,7 +60,7 @@ class AffineSolver:
         rule = theta_rule_code(prob.theta_rule)
         self.J = np.asarray(J, dtype=np.int64)
         self.desc = api._affine_desc(prob.n, prob.r, len(self.J), self.blocks, self.S, self.J,
-                                     self.b, rule, mode, qk, self.c, cplx)
+                                     self.b, rule, mode, qk, self.c, cplx, weights)
         self.mode = mode
         self.r = prob.r
         self.s = len(self.J)
@@ -99,6 +99,19 @@ def select_rows(prob, S_device, blocks_device, p_sel, s, device="cuda"):
     desc = api._affine_desc(prob.n, prob.r, s, blocks_device, S_device, None, None, rule,
                             api.SAS_MODE_PLAIN, api.SAS_QOI_NONE, None, cplx)
     return api.subapsnap_select_rows_affine(desc, p_sel, s)
+
+
+def leverage_rows(prob, S_device, blocks_device, p_sel, s, u, device="cuda"):
+    """Leverage-score sampling on the device scores of [A(p_sel) S, b]: (J, w, scores)."""
+    cplx = bool(prob.complex_valued)
+    bdt = np.complex128 if cplx else np.float64
+    b = torch.from_numpy(np.ascontiguousarray(prob.b, dtype=bdt)).to(device)
+    desc = api._affine_desc(prob.n, prob.r, s, blocks_device, S_device, None, b,
+                            theta_rule_code(prob.theta_rule), api.SAS_MODE_PLAIN, api.SAS_QOI_NONE,
+                            None, cplx)
+    scores = api.subapsnap_leverage_scores_affine(desc, p_sel)
+    J, w = api.subapsnap_sample_rows_leverage(scores, s, u)
+    return J, w, scores
 
 
 class KernelSolver:

@@ -8,6 +8,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -66,3 +67,22 @@ def test_product_path_has_no_oracle_import():
     for path in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
         src = open(path).read()
         assert "import oracle" not in src and "from oracle" not in src, path
+
+
+def test_host_leverage_sampler_matches_the_oracle(lib):
+    """The library's host-side leverage sampler (no GPU involved) draws the rows and
+    weights the oracle draws from the same scores and uniforms, bit for bit."""
+    from oracle import leverage
+    from paper_2510_04825_gb300 import api
+    rng = np.random.default_rng(9)
+    for n, s in ((50, 20), (1000, 300), (7, 40)):
+        scores = rng.uniform(0.0, 1.0, n) ** 3
+        u = rng.uniform(size=s)
+        J, w = api.subapsnap_sample_rows_leverage(scores, s, u)
+        Jo, wo = leverage.sample_rows(scores, s, u)
+        np.testing.assert_array_equal(J, Jo)
+        np.testing.assert_array_equal(w, wo)
+    with pytest.raises(api.SasError):
+        api.subapsnap_sample_rows_leverage(np.zeros(5), 3, [0.1, 0.2, 0.3])
+    with pytest.raises(api.SasError):
+        api.subapsnap_sample_rows_leverage(np.ones(5), 2, [0.1, 1.0])
