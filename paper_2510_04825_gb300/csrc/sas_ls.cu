@@ -300,9 +300,11 @@ constexpr int kNumLsShapes = sizeof(kLsShapes) / sizeof(kLsShapes[0]);
 // Blocked Householder variants of the mixed kernel (real only): threads,
 // lanes per column group, registers per lane for a trailing column (s <= G E).
 struct LsBlockedShape {
-  int nt, g, e;
+  int nt, g, e, pw;  // pw: panel factorised by warp 0 alone (warp-synchronous)
 };
-static const LsBlockedShape kLsBlocked[] = {{128, 4, 32}, {128, 8, 16}, {256, 8, 32}, {128, 8, 32}};
+static const LsBlockedShape kLsBlocked[] = {{128, 4, 32, 0}, {128, 8, 16, 0}, {256, 8, 32, 0},
+                                            {128, 8, 32, 0}, {128, 8, 16, 1}, {128, 4, 32, 1},
+                                            {256, 8, 32, 1}, {128, 8, 16, 1}};
 constexpr int kNumLsBlocked = sizeof(kLsBlocked) / sizeof(kLsBlocked[0]);
 constexpr int kLsPanel = 8;  // columns per panel of the blocked variants
 constexpr int kFirstBlocked = 3 * kNumLsShapes + 2;
@@ -467,6 +469,41 @@ __device__ inline float tf32_round(float x) {
 // (zero above the diagonal, v0 on it); tau their scales.  The same products as
 // the column-by-column sweep, with one shared-memory pass over the trailing
 // matrix per panel instead of one per reflector.
+// Panel factorisation by warp 0 alone (real float32): reflectors of columns
+// [c0, pe), each applied to the rest of the panel, with warp shuffles and no
+// CTA barrier; the same reflector formulas as householder_step.
+__device__ inline void panel_warp0(float* P, int ldt, int s, int c0, int pe, float* v0s,
+                                   float* taus) {
+  const int lane = threadIdx.x & 31;
+  for (int k = c0; k < pe; ++k) {
+    const float* pk = P + (size_t)k * ldt;
+    float t2 = 0.f;
+    for (int i = k + 1 + lane; i < s; i += 32) t2 = fmaf(pk[i], pk[i], t2);
+    t2 = warp_sum(t2);
+    const float alpha = pk[k];
+    const float nrm = sqrtf(alpha * alpha + t2);
+    const float beta = -nrm * phase(alpha);
+    const float v0 = alpha - beta;
+    const float tau = nrm > 0.f ? 1.f / (nrm * (nrm + fabsf(alpha))) : 0.f;
+    for (int j = k + 1; j < pe; ++j) {
+      float* pj = P + (size_t)j * ldt;
+      float w = lane == 0 ? v0 * pj[k] : 0.f;
+      for (int i = k + 1 + lane; i < s; i += 32) w = fmaf(pk[i], pj[i], w);
+      w = warp_sum(w);
+      const float tw = tau * w;
+      if (lane == 0) pj[k] -= tw * v0;
+      for (int i = k + 1 + lane; i < s; i += 32) pj[i] = fmaf(-tw, pk[i], pj[i]);
+      __syncwarp();
+    }
+    if (lane == 0) {
+      P[k + (size_t)k * ldt] = beta;
+      v0s[k] = v0;
+      taus[k] = tau;
+    }
+    __syncwarp();
+  }
+}
+
 template <int NT, int G, int E>
 __device__ inline void blocked_trailing_update(float* P, int ldt, int s, int c0, int pe, int ncol,
                                                const float* Vb, const float* tau) {
@@ -505,7 +542,7 @@ __device__ inline void blocked_trailing_update(float* P, int ldt, int s, int c0,
   }
 }
 
-template <typename TH, typename TL, int NT, int G, int BW = 0, int E = 0>
+template <typename TH, typename TL, int NT, int G, int BW = 0, int E = 0, int PW = 0>
 __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int64_t q,
                                               unsigned char* smem_raw, double* ctl) {
 
@@ -579,9 +616,13 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
       // over every trailing column (the right-hand side included)
       for (int c0 = 0; c0 < r; c0 += BW) {
         const int pe = c0 + BW < r ? c0 + BW : r;
-        for (int k = c0; k < pe; ++k)
-          householder_step<TL, float, NT, G>(k, pe, P + k, ldt, P + k + 1, ldt, s - k - 1, 1, nrm2,
-                                             v0, tau);
+        if constexpr (PW) {
+          if (warp == 0) panel_warp0(P, ldt, s, c0, pe, v0, tau);
+        } else {
+          for (int k = c0; k < pe; ++k)
+            householder_step<TL, float, NT, G>(k, pe, P + k, ldt, P + k + 1, ldt, s - k - 1, 1, nrm2,
+                                               v0, tau);
+        }
         __syncthreads();
         for (int idx = tid; idx < (pe - c0) * s; idx += NT) {
           const int kk = idx / s, i = idx % s, k = c0 + kk;
@@ -590,7 +631,7 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
         __syncthreads();
         blocked_trailing_update<NT, G, E>(P, ldt, s, c0, pe, r + 1, Vb, tau);
         __syncthreads();
-        if (pe < r) {
+        if (!PW && pe < r) {
           tail_norm_warp0<TL, float>(P + (size_t)pe * ldt + pe + 1, s - pe - 1, &nrm2[pe & 1]);
           __syncthreads();
         }
@@ -815,12 +856,12 @@ static size_t fill_mixed_args(const sas_ctx* c, const double* params, int64_t m,
   return smem;
 }
 
-template <int NT, int G, int E>
-__global__ void __launch_bounds__(NT, 512 / NT) ls_mixed_blocked_kernel(LsMixedArgs<double, float> a) {
+template <int NT, int G, int E, int PW, int MINB>
+__global__ void __launch_bounds__(NT, MINB) ls_mixed_blocked_kernel(LsMixedArgs<double, float> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double ctl[2];
   for (int64_t q = blockIdx.x; q < a.m; q += gridDim.x)
-    ls_mixed_body<double, float, NT, G, kLsPanel, E>(a, q, smem_raw, ctl);
+    ls_mixed_body<double, float, NT, G, kLsPanel, E, PW>(a, q, smem_raw, ctl);
 }
 
 static cudaError_t launch_mixed_blocked(const sas_ctx* c, const LsMixedArgs<double, float>& a,
@@ -830,10 +871,14 @@ static cudaError_t launch_mixed_blocked(const sas_ctx* c, const LsMixedArgs<doub
   if (c->s > sh.g * sh.e) return cudaErrorInvalidConfiguration;  // a trailing column must fit
   void (*kern)(LsMixedArgs<double, float>) = nullptr;
   switch (b) {
-    case 0: kern = ls_mixed_blocked_kernel<128, 4, 32>; break;
-    case 1: kern = ls_mixed_blocked_kernel<128, 8, 16>; break;
-    case 2: kern = ls_mixed_blocked_kernel<256, 8, 32>; break;
-    default: kern = ls_mixed_blocked_kernel<128, 8, 32>; break;
+    case 0: kern = ls_mixed_blocked_kernel<128, 4, 32, 0, 4>; break;
+    case 1: kern = ls_mixed_blocked_kernel<128, 8, 16, 0, 4>; break;
+    case 2: kern = ls_mixed_blocked_kernel<256, 8, 32, 0, 2>; break;
+    case 3: kern = ls_mixed_blocked_kernel<128, 8, 32, 0, 4>; break;
+    case 4: kern = ls_mixed_blocked_kernel<128, 8, 16, 1, 4>; break;
+    case 5: kern = ls_mixed_blocked_kernel<128, 4, 32, 1, 4>; break;
+    case 6: kern = ls_mixed_blocked_kernel<256, 8, 32, 1, 2>; break;
+    default: kern = ls_mixed_blocked_kernel<128, 8, 16, 1, 5>; break;  // 5 CTAs per SM
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

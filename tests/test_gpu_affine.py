@@ -280,8 +280,9 @@ def test_every_ls_variant_and_autotune(c1_small, mode):
     Yo, rho_o = case.oracle_solve(params)
     # plain: 5 shared-memory shapes + 1 register-resident; mixed: 5 shapes with float64 M
     # in shared memory, 5 without, 2 register-resident, 5 with M in a global slot per CTA,
-    # 4 blocked (panels of 8 reflectors applied to register-resident trailing columns)
-    nvar = 6 if mode == api.SAS_MODE_PLAIN else 21
+    # 8 blocked (panels of 8 reflectors applied to register-resident trailing columns;
+    # the panel factorised by the CTA or by warp 0 alone)
+    nvar = 6 if mode == api.SAS_MODE_PLAIN else 25
     P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
     solver = AffineSolver(p, case.S, case.J, mode=mode, device=DEV)
     bound = _mixed_bound(p, case.S, case.J, params, Yo, rho_o)
@@ -307,7 +308,7 @@ def test_blocked_variants_reject_what_does_not_fit():
     case = Case("diffusion_2d", basis="random", rows="random", N=30, r=20, s=300, m=4)
     P = torch.from_numpy(np.ascontiguousarray(case.prob.test_params)).to(DEV)
     solver = AffineSolver(case.prob, case.S, case.J, mode=api.SAS_MODE_MIXED, device=DEV)
-    for v in (17, 18, 19, 20):  # s = 300 > 256 >= G E for all four
+    for v in range(17, 25):  # s = 300 > 256 >= G E for every blocked shape
         api.subapsnap_set_option(solver.ctx, api.SAS_OPT_LS_VARIANT, v)
         Y = torch.empty((4, 20), dtype=torch.float64, device=DEV)
         with pytest.raises(api.SasError):
@@ -363,7 +364,7 @@ def test_register_variants_on_c0_and_multichunk(c0, mode):
     Yo, rho_o = c0.oracle_solve(params)
     P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
     solver = AffineSolver(p, c0.S, c0.J, mode=mode, device=DEV)
-    variants = [5] if mode == api.SAS_MODE_PLAIN else [10, 11, 17, 18, 19, 20]
+    variants = [5] if mode == api.SAS_MODE_PLAIN else [10, 11] + list(range(17, 25))
     bound = _mixed_bound(p, c0.S, c0.J, params, Yo, rho_o)
     kap = c0.kappas(params)
     for v in variants:
