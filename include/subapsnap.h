@@ -260,7 +260,7 @@ sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
 
 /* Leverage scores of [A(p_sel) S, b] (Sec. 4.3.2-4.3.3): the squared row norms
  * of Q in the thin QR of the n x (r+1) matrix, computed on the device in
- * float64 by CholeskyQR2.  Row selection by leverage-score sampling draws
+ * float64 by shifted CholeskyQR3.  Row selection by leverage-score sampling draws
  * rows with probability proportional to these scores.
  *  d: affine descriptor (J, w, mode and QoI fields unused); p_sel: host, dp
  *     doubles; scores: host, n doubles (sum r + 1 for full column rank).

@@ -2,9 +2,12 @@
 // the weighted subsampled rows it leads to (Sec. 4.3.3).
 //
 // Scores: V = [A(p_sel) S, b] (n x (r+1)), thin QR V = QR, score_i = ||Q_i,:||^2,
-// computed on the device in float64 by CholeskyQR2: twice, G = V^H V (a
-// reduction over the n rows), G = R^H R on the host, V <- V R^{-1}.  After
-// the second pass V is Q to working accuracy for kappa(V) up to ~1e7.
+// computed on the device in float64 by shifted CholeskyQR3 (Fukaya, Kannan,
+// Nakatsukasa, Yamamoto, Yanagisawa 2020): three times G = V^H V (a reduction
+// over the n rows), G (+ sigma I on the first pass) = R^H R on the host, and
+// V <- V R^{-1}.  The first, shifted pass with sigma = 11 (n c + c (c+1)) u
+// trace(G) brings kappa(V) down to ~u^{-1/2} whatever it was, so that the two
+// plain passes that follow leave V = Q to working accuracy.
 //
 // Sampling (host): s draws with replacement by inverse CDF of pi = score /
 // total on caller-supplied uniforms u in [0, 1).  C_i is the running sum of the
@@ -171,7 +174,7 @@ static sas_status scores_t(const sas_affine_desc* d, const double* p_sel, double
     put_rhs_kernel<T><<<sms * 4, 256>>>((const T*)d->b, n, c, V);
     e = cudaGetLastError();
   }
-  for (int pass = 0; pass < 2 && e == cudaSuccess && rc == SAS_OK; ++pass) {
+  for (int pass = 0; pass < 3 && e == cudaSuccess && rc == SAS_OK; ++pass) {
     e = cudaMemset(G, 0, (size_t)2 * c * c * sizeof(double));
     if (e != cudaSuccess) break;
     const size_t smem = (size_t)kRows * c * sizeof(T);
@@ -191,6 +194,12 @@ static sas_status scores_t(const sas_affine_desc* d, const double* p_sel, double
         Gc[(size_t)a * c + b] = v;
         Gc[(size_t)b * c + a] = conj_h(v);
       }
+    if (pass == 0) {  // the shift of the first pass
+      double tr = 0.0;
+      for (int a = 0; a < c; ++a) tr += std::real(Gc[(size_t)a * c + a]);
+      const double sigma = 11.0 * ((double)n * c + (double)c * (c + 1)) * 0x1p-53 * tr;
+      for (int a = 0; a < c; ++a) Gc[(size_t)a * c + a] += sigma;
+    }
     if (!cholesky_inverse<C>(Gc, c, Rinv)) {
       rc = SAS_ERANK;
       set_error("leverage scores: [A(p_sel) S, b] is numerically rank deficient");

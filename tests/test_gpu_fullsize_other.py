@@ -7,7 +7,7 @@ solves it (one call for the whole batch):
     16,384 frequencies, QoI output: y and H(i w) for 10 sampled w, plain
     float64 within 1e-10 (kappa-filtered as elsewhere), mixed within the
     refinement bound;
-  delay system, n = 10^7 (Sec. 5.2.3), r = 40, s = 80, 5000 frequencies, QoI
+  delay system, n = 10^7 (Sec. 5.2.3), r = 24, s = 48, 5000 frequencies, QoI
     output: y and H(i w) for 8 sampled w, plain float64 within 1e-10
     (kappa-filtered), mixed within the refinement bound;
   kernel ridge, N = 200,000 points in R^8, r = 100, s = 300, 2048 (sigma,

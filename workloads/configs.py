@@ -191,24 +191,30 @@ def make_kernel_ridge(N=200_000, d=8, ncomp=10, nfreq=5, r=100, s=300, m=2048, s
     )
 
 
-def make_delay_system(n=10_000_000, r=40, s=80, m=5000, tau=0.1, kappa=2.1) -> AffineProblem:
+def make_delay_system(n=10_000_000, r=24, s=48, m=5000, tau=0.1, kappa=2.1,
+                      seed=0) -> AffineProblem:
     """Delay system H(p) = c^T (p I - A_0 - e^{tau p} A_1)^{-1} b on the imaginary axis
     p = i omega (Sec. 5.2.3, Table 4): A_1 = (T - kappa I)/tau, A_0 = 3 A_1, tau = 0.1,
-    kappa = 2.1.  b = c = ones.  Snapshots at r log-spaced omega in [1e-2, 1e3];
-    test omega = logspace(-2, 3, m) (endpoints shared with the snapshots); selection at
-    the log-midpoint omega = 10^0.5.  Parameters carry tau as their second entry.
-    No random draws.
+    kappa = 2.1.  Draw order: b ~ N(0,1)^n, c ~ N(0,1)^n (every row of T sums to 2,
+    so a constant b would be an eigenvector of A(p) and every snapshot a multiple
+    of it).  Snapshots at r = 24 log-spaced omega in [1e-2, 1e3] (the snapshot set's
+    numerical rank is ~26 at 1e-14: more snapshots add rounding noise to S); test omega =
+    logspace(-2, 3, m) (endpoints shared with the snapshots); selection at the
+    log-midpoint omega = 10^0.5.  Parameters carry tau as their second entry.
     """
+    rng = np.random.default_rng(seed)
+    b = rng.standard_normal(n)
+    c = rng.standard_normal(n)
     I, A0, A1 = ops.delay_blocks(n, tau, kappa)
     snap = np.logspace(-2, 3, r)
     test = np.logspace(-2, 3, m)
     return AffineProblem(
         name="delay_system", n=n, blocks=[I, A0, A1], theta_rule="delay",
-        b=np.ones(n, dtype=np.complex128), r=r, s=s,
+        b=b.astype(np.complex128), r=r, s=s,
         snap_params=np.stack([snap, np.full(r, tau)], 1),
         sel_param=np.array([10.0 ** 0.5, tau]),
         test_params=np.stack([test, np.full(m, tau)], 1), complex_valued=True,
-        c=np.ones(n), qoi_kind="transpose", meta={"tau": tau, "kappa": kappa},
+        c=c, qoi_kind="transpose", meta={"tau": tau, "kappa": kappa},
     )
 
 
