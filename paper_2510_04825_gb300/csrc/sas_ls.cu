@@ -661,9 +661,27 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
     if (tid == 0) ctl[1] = 1.0;
     __syncthreads();
     for (int it = 0;; ++it) {
-      // float64 residual of the subsampled system: res = b_J - M y
+      // float64 residual of the subsampled system: res = b_J - M y.  Once the last
+      // correction delta is below 1e-7 |y|, r(y) = r(y - delta) - M delta with M delta
+      // in float32: its rounding, ~u32 |M| |delta| <= 6e-15 |M| |y|, is at the level
+      // of the float64 product, and the float64 pipe is spared.
+      const bool update = (keep || a.Mg) && it > 0 && last_rel <= 1e-7;
       double part = 0.0;
       for (int i = tid; i < s; i += NT) {
+        if (update) {
+          const TH* mrow = keep ? M64 + i : a.Mg + (size_t)q * s * r + i;
+          TL accl[4] = {zero<TL>(), zero<TL>(), zero<TL>(), zero<TL>()};
+          int j = 0;
+          for (; j + 4 <= r; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) accl[u] += to_lo(mrow[(size_t)(j + u) * s]) * dl[j + u];
+          }
+          for (; j < r; ++j) accl[0] += to_lo(mrow[(size_t)j * s]) * dl[j];
+          const TH ri = res[i] - to_hi((accl[0] + accl[1]) + (accl[2] + accl[3]));
+          res[i] = ri;
+          part += absq(ri);
+          continue;
+        }
         TH acc = zero<TH>();
         if (keep || a.Mg) {
           // four independent partial sums: the row product is a latency chain otherwise
