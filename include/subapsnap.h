@@ -258,6 +258,23 @@ enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
  * value out of range. */
 sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
 
+/* Union of pivot sets (Sec. 4.3.4): the CPQR selection of
+ * subapsnap_select_rows_affine with s = s_each at each of t parameters
+ * points[i * dp .. i * dp + dp), the picks merged in order of first
+ * appearance.  J_out: host, room for t * s_each indices; *count_out: how many
+ * distinct rows (between s_each and t * s_each).  Synchronous.  Errors: as for
+ * subapsnap_select_rows_affine. */
+sas_status subapsnap_select_rows_union_affine(const sas_affine_desc* desc, const double* points,
+                                              int32_t t, int32_t s_each, int64_t* J_out,
+                                              int32_t* count_out);
+
+/* Nearest selection point of each parameter (Sec. 4.3.4: the rows chosen at
+ * the snapshot point closest to p): idx_out[q] = argmin_i |params_q -
+ * points_i| in the Euclidean norm of the parameter vector, ties to the lowest
+ * i.  Host arrays: params m x dp, points t x dp, idx_out m.  Errors: SAS_EINVAL. */
+sas_status subapsnap_nearest_points(const double* params, int64_t m, int32_t dp,
+                                    const double* points, int32_t t, int32_t* idx_out);
+
 /* Leverage scores of [A(p_sel) S, b] (Sec. 4.3.2-4.3.3): the squared row norms
  * of Q in the thin QR of the n x (r+1) matrix, computed on the device in
  * float64 by shifted CholeskyQR3.  Row selection by leverage-score sampling draws

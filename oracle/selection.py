@@ -60,3 +60,39 @@ def cpqr_rows(V: np.ndarray, s: int):
         chosen += picks
         gaps += g
     return np.array(chosen, dtype=np.int64), np.array(gaps)
+
+
+def union_rows(V_list, s_each: int):
+    """Union of CPQR picks at several snapshot points (Sec. 4.3.4).
+
+    The variants section proposes choosing rows at t snapshot points and
+    keeping every location any of them chose, which oversamples without a
+    random draw.  Each V_i = A(p_i) S (n x r) is handled by ``cpqr_rows`` with
+    s_each rows; the result lists the distinct rows in order of first
+    appearance (point 0's picks first, then what point 1 adds, ...).
+    """
+    out: list[int] = []
+    seen: set[int] = set()
+    for V in V_list:
+        J, _ = cpqr_rows(np.asarray(V), s_each)
+        for j in J.tolist():
+            if j not in seen:
+                seen.add(j)
+                out.append(j)
+    return np.array(out, dtype=np.int64)
+
+
+def nearest_points(params: np.ndarray, points: np.ndarray) -> np.ndarray:
+    """Index of the snapshot point closest to each parameter (Sec. 4.3.4).
+
+    The other variant of that section takes, for a new p, the rows chosen at
+    its nearest snapshot point.  Distance: Euclidean in the parameter vector;
+    an exact tie goes to the lowest index.
+    """
+    P = np.atleast_2d(np.asarray(params, dtype=np.float64))
+    Q = np.atleast_2d(np.asarray(points, dtype=np.float64))
+    out = np.empty(P.shape[0], dtype=np.int32)
+    for q in range(P.shape[0]):
+        d2 = ((Q - P[q]) ** 2).sum(axis=1)
+        out[q] = int(np.argmin(d2))
+    return out

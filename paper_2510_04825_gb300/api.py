@@ -36,6 +36,7 @@ EXPORTED = [
     "subapsnap_solve_batch_surrogate", "subapsnap_surrogate_weights", "subapsnap_surrogate_grad",
     "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch", "subapsnap_multi_plan_destroy",
     "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine", "subapsnap_sample_rows_leverage",
+    "subapsnap_select_rows_union_affine", "subapsnap_nearest_points",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
@@ -127,6 +128,9 @@ def lib() -> ctypes.CDLL:
                                            ctypes.POINTER(ctypes.c_int64)]
         L.subapsnap_leverage_scores_affine.argtypes = [ctypes.POINTER(AffineDesc), vp, vp]
         L.subapsnap_sample_rows_leverage.argtypes = [vp, i64, i32, vp, vp, vp, ctypes.POINTER(ctypes.c_int32)]
+        L.subapsnap_select_rows_union_affine.argtypes = [ctypes.POINTER(AffineDesc), vp, i32, i32, vp,
+                                                         ctypes.POINTER(ctypes.c_int32)]
+        L.subapsnap_nearest_points.argtypes = [vp, i64, i32, vp, i32, vp]
         for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
@@ -137,7 +141,8 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_surrogate_weights", "subapsnap_surrogate_grad",
                      "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch",
                      "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine",
-                     "subapsnap_sample_rows_leverage"):
+                     "subapsnap_sample_rows_leverage", "subapsnap_select_rows_union_affine",
+                     "subapsnap_nearest_points"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -283,6 +288,29 @@ def subapsnap_sample_rows_leverage(scores, s: int, u):
                                                 J.ctypes.data_as(ctypes.c_void_p),
                                                 w.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cnt)))
     return J[:cnt.value].copy(), w[:cnt.value].copy()
+
+
+def subapsnap_select_rows_union_affine(desc: AffineDesc, points, s_each: int) -> np.ndarray:
+    """Union of the CPQR picks at each row of ``points`` (t x dp), first appearance order."""
+    pts = np.ascontiguousarray(np.atleast_2d(np.asarray(points, dtype=np.float64)))
+    t = pts.shape[0]
+    J = np.empty(t * int(s_each), dtype=np.int64)
+    cnt = ctypes.c_int32()
+    _check(lib().subapsnap_select_rows_union_affine(ctypes.byref(desc), pts.ctypes.data_as(ctypes.c_void_p),
+                                                    int(t), int(s_each), J.ctypes.data_as(ctypes.c_void_p),
+                                                    ctypes.byref(cnt)))
+    return J[:cnt.value].copy()
+
+
+def subapsnap_nearest_points(params, points) -> np.ndarray:
+    """Index of the nearest row of ``points`` for every row of ``params``."""
+    P = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64)))
+    pts = np.ascontiguousarray(np.atleast_2d(np.asarray(points, dtype=np.float64)))
+    idx = np.empty(P.shape[0], dtype=np.int32)
+    _check(lib().subapsnap_nearest_points(P.ctypes.data_as(ctypes.c_void_p), int(P.shape[0]), int(P.shape[1]),
+                                          pts.ctypes.data_as(ctypes.c_void_p), int(pts.shape[0]),
+                                          idx.ctypes.data_as(ctypes.c_void_p)))
+    return idx
 
 
 def subapsnap_reconstruct(ctx, Y, m: int, out, stream=None):

@@ -609,6 +609,55 @@ sas_status subapsnap_select_rows_affine(const sas_affine_desc* d, const double* 
   return select_rows_affine(d, p_sel, J_out, gap_out);
 }
 
+sas_status subapsnap_select_rows_union_affine(const sas_affine_desc* d, const double* points,
+                                              int32_t t, int32_t s_each, int64_t* J_out,
+                                              int32_t* count_out) {
+  if (!d || !points || !J_out || !count_out) return fail(SAS_EINVAL, "NULL argument");
+  if (t < 1 || s_each < d->r) return fail(SAS_EINVAL, "need t >= 1 and s_each >= r");
+  sas_affine_desc one = *d;
+  one.s = s_each;
+  sas_status st = check_affine_desc(&one, false);
+  if (st != SAS_OK) return st;
+  const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->theta_rule == SAS_THETA_DELAY ? 2 : d->K - 1;
+  std::vector<int64_t> picks((size_t)s_each);
+  std::vector<char> seen((size_t)d->n, 0);
+  int32_t k = 0;
+  for (int32_t i = 0; i < t; ++i) {
+    st = select_rows_affine(&one, points + (size_t)i * dp, picks.data(), nullptr);
+    if (st != SAS_OK) return st;
+    for (int64_t j : picks)
+      if (!seen[(size_t)j]) {
+        seen[(size_t)j] = 1;
+        J_out[k++] = j;
+      }
+  }
+  *count_out = k;
+  return SAS_OK;
+}
+
+sas_status subapsnap_nearest_points(const double* params, int64_t m, int32_t dp,
+                                    const double* points, int32_t t, int32_t* idx_out) {
+  if (!params || !points || !idx_out) return fail(SAS_EINVAL, "NULL argument");
+  if (m < 0 || dp < 1 || t < 1) return fail(SAS_EINVAL, "need m >= 0, dp >= 1, t >= 1");
+  for (int64_t q = 0; q < m; ++q) {
+    int32_t best = 0;
+    double bd = INFINITY;
+    for (int32_t i = 0; i < t; ++i) {
+      double d2 = 0.0;
+      for (int32_t k = 0; k < dp; ++k) {
+        const double df = params[q * dp + k] - points[(size_t)i * dp + k];
+        d2 += df * df;
+      }
+      if (d2 < bd) {  // ties go to the lowest index
+        bd = d2;
+        best = i;
+      }
+    }
+    idx_out[q] = best;
+  }
+  return SAS_OK;
+}
+
 sas_status subapsnap_select_rows_kernel(const sas_kernel_desc* d, const double* p_sel,
                                         int64_t* J_out, double* gap_out) {
   if (!d || !p_sel || !J_out) return fail(SAS_EINVAL, "NULL argument");

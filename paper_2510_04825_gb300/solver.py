@@ -114,6 +114,68 @@ def leverage_rows(prob, S_device, blocks_device, p_sel, s, u, device="cuda"):
     return J, w, scores
 
 
+def select_rows_union(prob, S_device, blocks_device, points, s_each):
+    """Union of the device CPQR picks at each row of ``points`` (first appearance order)."""
+    cplx = bool(prob.complex_valued)
+    desc = api._affine_desc(prob.n, prob.r, s_each, blocks_device, S_device, None, None,
+                            theta_rule_code(prob.theta_rule), api.SAS_MODE_PLAIN, api.SAS_QOI_NONE,
+                            None, cplx)
+    return api.subapsnap_select_rows_union_affine(desc, points, s_each)
+
+
+class NearestPointSolver:
+    """Row set chosen per parameter: the CPQR rows of its nearest selection point.
+
+    One AffineSolver per point shares the device basis, blocks, b and c; a
+    batch is split by ``subapsnap_nearest_points`` and each group is solved
+    by its point's context, the results scattered back in input order.
+    """
+
+    def __init__(self, prob, S, points, s, mode=api.SAS_MODE_PLAIN, device="cuda", S_device=None,
+                 blocks_device=None):
+        cplx = bool(prob.complex_valued)
+        self.blocks = blocks_device or [csr_to_device(A, device) for A in prob.blocks]
+        self.S = S_device if S_device is not None else basis_to_device(S, device, cplx)
+        self.points = np.ascontiguousarray(np.atleast_2d(np.asarray(points, dtype=np.float64)))
+        self.J = [select_rows(prob, self.S, self.blocks, pt, s)[0] for pt in self.points]
+        bdt = np.complex128 if cplx else np.float64
+        b = torch.from_numpy(np.ascontiguousarray(prob.b, dtype=bdt)).to(device)
+        c = None if getattr(prob, "c", None) is None else \
+            torch.from_numpy(np.ascontiguousarray(prob.c, dtype=np.float64)).to(device)
+        self.solvers = [AffineSolver(prob, None, J, mode=mode, device=device, S_device=self.S,
+                                     blocks_device=self.blocks, b_device=b, c_device=c) for J in self.J]
+
+    def close(self):
+        for sv in self.solvers:
+            sv.close()
+
+    def assign(self, params):
+        P = params.detach().cpu().numpy() if hasattr(params, "detach") else np.asarray(params)
+        return api.subapsnap_nearest_points(P, self.points)
+
+    def solve(self, params, out_kind, out, flags=None, rho=None, stream=None):
+        if stream is not None:
+            with torch.cuda.stream(stream):
+                return self.solve(params, out_kind, out, flags, rho, None)
+        idx = self.assign(params)
+        for i, sv in enumerate(self.solvers):
+            sel = np.nonzero(idx == i)[0]
+            if sel.size == 0:
+                continue
+            g = torch.from_numpy(sel).to(params.device)
+            Pg = params.index_select(0, g).contiguous()
+            og = out.new_empty((sel.size,) + tuple(out.shape[1:]))
+            fg = None if flags is None else flags.new_zeros(sel.size)
+            rg = None if rho is None else rho.new_empty(sel.size)
+            sv.solve(Pg, out_kind, og, fg, rg, stream)
+            out.index_copy_(0, g, og)
+            if flags is not None:
+                flags.index_copy_(0, g, fg)
+            if rho is not None:
+                rho.index_copy_(0, g, rg)
+        return idx
+
+
 class KernelSolver:
     """Context for A(sigma, lambda) = K_sigma + lambda I on points X (Gaussian kernel)."""
 

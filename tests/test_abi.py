@@ -86,3 +86,22 @@ def test_host_leverage_sampler_matches_the_oracle(lib):
         api.subapsnap_sample_rows_leverage(np.zeros(5), 3, [0.1, 0.2, 0.3])
     with pytest.raises(api.SasError):
         api.subapsnap_sample_rows_leverage(np.ones(5), 2, [0.1, 1.0])
+
+
+def test_host_nearest_points_matches_the_oracle(lib):
+    from oracle import selection
+    from paper_2510_04825_gb300 import api
+
+    rng = np.random.default_rng(3)
+    for m, dp, t in ((200, 1, 5), (500, 4, 7), (0, 2, 3)):
+        pts = rng.uniform(size=(t, dp))
+        P = rng.uniform(size=(m, dp))
+        if m:
+            P[:t] = pts  # exact hits
+        np.testing.assert_array_equal(api.subapsnap_nearest_points(P.reshape(m, dp), pts),
+                                      selection.nearest_points(P.reshape(m, dp), pts))
+    # ties go to the lowest index on both sides
+    pts = np.array([[0.0], [2.0], [1.0], [1.0]])
+    P = np.array([[1.5], [0.5], [1.0]])
+    np.testing.assert_array_equal(api.subapsnap_nearest_points(P, pts), [1, 0, 2])
+    np.testing.assert_array_equal(selection.nearest_points(P, pts), [1, 0, 2])

@@ -75,6 +75,11 @@ def run(case, mode, out_kind, params=None, m=None):
     return res
 
 
+def online_solve(prob, S, J, params):
+    from oracle import online
+    return online.solve_many(prob, S, J, params)
+
+
 def rel_err_rows(a, b):
     return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
 
@@ -212,6 +217,64 @@ def test_c3_small_row_selection_complex(c3_small):
     near = c3_small.gaps < 1e-10
     assert not near.any()
     np.testing.assert_array_equal(J, c3_small.J)
+
+
+def _three_points(p):
+    return p.snap_params[[0, len(p.snap_params) // 2, len(p.snap_params) - 1]]
+
+
+@pytest.mark.parametrize("which", ["c0", "c1_small", "delay_small"])
+def test_union_selection_matches_oracle(which, request):
+    """Union of the CPQR picks at three snapshot points (Sec. 4.3.4), real and complex."""
+    from oracle import problem as oproblem, selection
+    from paper_2510_04825_gb300.solver import select_rows_union
+    case = request.getfixturevalue(which)
+    p = case.prob
+    pts = _three_points(p)
+    S_d = basis_to_device(case.S, DEV, complex_valued=p.complex_valued)
+    blocks = [csr_to_device(A, DEV) for A in p.blocks]
+    Vs = [np.asarray(oproblem.full_matrix(p, pt) @ case.S) for pt in pts]
+    assert min(selection.cpqr_rows(V, p.r)[1].min() for V in Vs) > 1e-8  # no near-ties
+    U = select_rows_union(p, S_d, blocks, pts, p.r)
+    np.testing.assert_array_equal(U, selection.union_rows(Vs, p.r))
+    print(f"{which} union of 3 x {p.r} picks: {len(U)} rows")
+    # the union is itself a row set: the plain solve on it matches the oracle
+    params = p.test_params[:40]
+    solver = AffineSolver(p, None, U, mode=api.SAS_MODE_PLAIN, device=DEV, S_device=S_d, blocks_device=blocks)
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
+    y = torch.empty((len(params), p.r), dtype=torch.complex128 if p.complex_valued else torch.float64, device=DEV)
+    solver.solve(P, api.SAS_OUT_Y, y)
+    Yo, _ = online_solve(p, case.S, U, params)
+    err = rel_err_rows(y.cpu().numpy(), Yo)
+    solver.close()
+    assert err.max() <= 1e-9, err.max()
+
+
+def test_nearest_point_solver_matches_oracle(c0):
+    """Per-parameter rows from the nearest of three selection points (Sec. 4.3.4)."""
+    from oracle import problem as oproblem, selection
+    from paper_2510_04825_gb300.solver import NearestPointSolver
+    p = c0.prob
+    pts = _three_points(p)
+    ns = NearestPointSolver(p, c0.S, pts, p.s, mode=api.SAS_MODE_PLAIN, device=DEV)
+    Js = [selection.cpqr_rows(np.asarray(oproblem.full_matrix(p, pt) @ c0.S), p.s)[0] for pt in pts]
+    for J, Jo in zip(ns.J, Js):
+        np.testing.assert_array_equal(J, Jo)
+    params = p.test_params
+    idx_o = selection.nearest_points(params, pts)
+    assert len(set(idx_o.tolist())) == 3
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
+    y = torch.full((len(params), p.r), float("nan"), dtype=torch.float64, device=DEV)
+    rho = torch.empty(len(params), dtype=torch.float64, device=DEV)
+    idx = ns.solve(P, api.SAS_OUT_Y, y, None, rho)
+    np.testing.assert_array_equal(idx, idx_o)
+    Y = y.cpu().numpy()
+    for i, J in enumerate(Js):
+        g = np.nonzero(idx_o == i)[0]
+        Yo, rho_o = online_solve(p, c0.S, J, params[g])
+        assert rel_err_rows(Y[g], Yo).max() <= 1e-10
+        np.testing.assert_allclose(rho.cpu().numpy()[g], rho_o, rtol=1e-6, atol=1e-14)
+    ns.close()
 
 
 def test_blocked_householder_path():
