@@ -46,7 +46,9 @@ typedef enum {
   SAS_ECUDA = 3,     /* CUDA runtime error (launch or synchronisation) */
   SAS_ERANK = 4,     /* M(p_sel) is numerically rank deficient at setup */
   SAS_ETIMEOUT = 5,  /* a bounded device wait ran out (see subapsnap_device_status) */
-  SAS_ENOTSUP = 6    /* combination of options not supported */
+  SAS_ENOTSUP = 6,   /* combination of options not supported */
+  SAS_ENOCONV = 7    /* an iterative solve stopped (iteration limit or breakdown)
+                        before its tolerance; the outputs hold the last iterates */
 } sas_status;
 
 /* Per-parameter flag bits written to the optional flags[m] array. */
@@ -257,6 +259,48 @@ enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */
 sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
+
+/* ---------------------------------------------------------------- offline stage */
+
+/* Snapshot solves A(p_j) x_j = b, j = 0..B-1, all at once (Alg. 1 step 1,
+ * "fully or approximately"): conjugate gradients in the bilinear form x^T y
+ * (COCG; plain CG for real data) with the diagonal of A(p_j) as
+ * preconditioner.  A(p) must be symmetric (A^T = A; complex symmetric for the
+ * pencil and delay rules) with a non-zero diagonal; the method converges for
+ * positive definite A(p) and in practice for the complex symmetric families
+ * here.  The same call refines given start vectors (warm != 0), e.g. the
+ * SubApSnap output x_hat as the initial guess of Sec. 3.2.
+ *  desc:    the family (n, K, dtype, theta_rule, CSR blocks, b); r, s, S, J,
+ *           mode, qoi and w are ignored.
+ *  params:  host, B x dp.
+ *  X:       device, n x B column-major (column j = x_j, ld n); on entry the
+ *           start vectors if warm != 0 (ignored otherwise: zero start).
+ *  tol:     column j stops once its updated residual ||b - A x_j|| / ||b||
+ *           <= tol; maxit bounds its iterations.
+ *  iters_out:  host, B ints or NULL: iterations per column.
+ *  relres_out: host, B doubles or NULL: the true ||b - A x_j|| / ||b|| of
+ *           the returned x_j, recomputed at the end.
+ * Synchronous (own stream).  Errors: SAS_EINVAL (sizes, pointers, rule, zero
+ * diagonal, b = 0), SAS_ENOMEM, SAS_ECUDA, SAS_ENOCONV (a column stopped at
+ * maxit or broke down; X holds the last iterates). */
+sas_status subapsnap_krylov_affine(const sas_affine_desc* desc, const double* params, int32_t B,
+                                   void* X, int32_t warm, double tol, int32_t maxit,
+                                   int32_t* iters_out, double* relres_out);
+
+/* Thin QR X = Q R of a tall n x r matrix on the device by TSQR (Alg. 1 step
+ * 2: an orthonormal basis Q of the snapshots' range): Householder QR of row
+ * panels in shared memory and of stacks of their R factors up a reduction
+ * tree, Q formed by applying the reflectors top-down.  Column signs are
+ * chosen so that diag(R) >= 0 (R real on its diagonal), which makes Q unique
+ * when X has full rank; a rank-deficient X still gets an orthonormal Q.
+ *  X:  device n x r (ld ldx >= n), dtype SAS_REAL64 or SAS_COMPLEX128.
+ *  Q:  device n x r (ld ldq >= n); may be X itself (ldq == ldx).
+ *  R_out: host r x r column-major or NULL.
+ * Limits: r <= 120 real, r <= 84 complex (a panel of 2r rows in shared
+ * memory).  Synchronous.  Errors: SAS_EINVAL, SAS_ENOTSUP (r too large),
+ * SAS_ENOMEM, SAS_ECUDA. */
+sas_status subapsnap_tsqr(const void* X, int64_t n, int32_t r, int64_t ldx, int32_t dtype,
+                          void* Q, int64_t ldq, void* R_out);
 
 /* Union of pivot sets (Sec. 4.3.4): the CPQR selection of
  * subapsnap_select_rows_affine with s = s_each at each of t parameters

@@ -50,3 +50,19 @@ def orthonormal_basis(X: np.ndarray) -> np.ndarray:
     """Thin-QR Q factor of the snapshot matrix (Alg. 1 step 2)."""
     Q, _ = np.linalg.qr(X, mode="reduced")
     return Q
+
+
+def thin_qr(X: np.ndarray):
+    """Thin QR X = Q R with R's diagonal real and non-negative (Alg. 1 step 2).
+
+    LAPACK's Householder QR, then each column j of Q multiplied by the phase
+    of R_jj and row j of R by its conjugate, which leaves Q R unchanged and
+    makes the factorisation unique when X has full column rank.
+    """
+    Q, R = np.linalg.qr(np.asarray(X), mode="reduced")
+    d = np.diag(R).copy()
+    mag = np.abs(d)
+    ph = np.where(mag > 0, d / np.where(mag > 0, mag, 1.0), 1.0)
+    Q = Q * ph[None, :]
+    R = np.conj(ph)[:, None] * R
+    return Q, R

@@ -17,7 +17,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libsubapsnap.so")
 
-SAS_OK, SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA, SAS_ERANK, SAS_ETIMEOUT, SAS_ENOTSUP = range(7)
+SAS_OK, SAS_EINVAL, SAS_ENOMEM, SAS_ECUDA, SAS_ERANK, SAS_ETIMEOUT, SAS_ENOTSUP, SAS_ENOCONV = range(8)
 SAS_FLAG_ILLCOND, SAS_FLAG_NONFINITE, SAS_FLAG_REFINE_STALL = 1, 2, 4
 SAS_REAL64, SAS_COMPLEX128 = 0, 1
 SAS_THETA_LINEAR, SAS_THETA_PENCIL, SAS_THETA_DELAY = 0, 1, 2
@@ -36,7 +36,8 @@ EXPORTED = [
     "subapsnap_solve_batch_surrogate", "subapsnap_surrogate_weights", "subapsnap_surrogate_grad",
     "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch", "subapsnap_multi_plan_destroy",
     "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine", "subapsnap_sample_rows_leverage",
-    "subapsnap_select_rows_union_affine", "subapsnap_nearest_points",
+    "subapsnap_select_rows_union_affine", "subapsnap_nearest_points", "subapsnap_krylov_affine",
+    "subapsnap_tsqr",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
@@ -131,6 +132,9 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_select_rows_union_affine.argtypes = [ctypes.POINTER(AffineDesc), vp, i32, i32, vp,
                                                          ctypes.POINTER(ctypes.c_int32)]
         L.subapsnap_nearest_points.argtypes = [vp, i64, i32, vp, i32, vp]
+        L.subapsnap_krylov_affine.argtypes = [ctypes.POINTER(AffineDesc), vp, i32, vp, i32, ctypes.c_double,
+                                              i32, vp, vp]
+        L.subapsnap_tsqr.argtypes = [vp, i64, i32, i64, i32, vp, i64, vp]
         for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
@@ -142,7 +146,7 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch",
                      "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine",
                      "subapsnap_sample_rows_leverage", "subapsnap_select_rows_union_affine",
-                     "subapsnap_nearest_points"):
+                     "subapsnap_nearest_points", "subapsnap_krylov_affine", "subapsnap_tsqr"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -311,6 +315,34 @@ def subapsnap_nearest_points(params, points) -> np.ndarray:
                                           pts.ctypes.data_as(ctypes.c_void_p), int(pts.shape[0]),
                                           idx.ctypes.data_as(ctypes.c_void_p)))
     return idx
+
+
+def subapsnap_krylov_affine(desc: AffineDesc, params, X, warm: bool = False, tol: float = 1e-12,
+                            maxit: int = 20000, allow_noconv: bool = False):
+    """Batched snapshot solves A(p_j) x_j = b.  X: CUDA tensor (B, n), row j = x_j
+    (the column-major n x B matrix).  Returns (iterations, true relative residuals)."""
+    P = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64)))
+    B = int(X.shape[0])
+    it = np.zeros(B, dtype=np.int32)
+    rel = np.zeros(B, dtype=np.float64)
+    code = lib().subapsnap_krylov_affine(ctypes.byref(desc), P.ctypes.data_as(ctypes.c_void_p), B, _ptr(X),
+                                         1 if warm else 0, float(tol), int(maxit),
+                                         it.ctypes.data_as(ctypes.c_void_p), rel.ctypes.data_as(ctypes.c_void_p))
+    if not (allow_noconv and code == SAS_ENOCONV):
+        _check(code)
+    return it, rel
+
+
+def subapsnap_tsqr(X, Q=None, complex_valued: bool | None = None) -> np.ndarray:
+    """Thin QR of the column-major n x r matrix held by the CUDA tensor X of shape (r, n).
+    Q (same shape, may be X) receives the orthonormal factor; returns R (r x r, host)."""
+    r, n = int(X.shape[0]), int(X.shape[1])
+    cplx = X.is_complex() if complex_valued is None else complex_valued
+    Q = X if Q is None else Q
+    R = np.zeros((r, r), dtype=np.complex128 if cplx else np.float64)  # R[j, i] = R_ij (column-major)
+    _check(lib().subapsnap_tsqr(_ptr(X), n, r, n, SAS_COMPLEX128 if cplx else SAS_REAL64, _ptr(Q), n,
+                                R.ctypes.data_as(ctypes.c_void_p)))
+    return np.ascontiguousarray(R.T)
 
 
 def subapsnap_reconstruct(ctx, Y, m: int, out, stream=None):

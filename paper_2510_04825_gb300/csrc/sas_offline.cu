@@ -1,0 +1,817 @@
+// Offline stage on the device (Alg. 1 steps 1-2): the snapshot solves
+// A(p_j) x_j = b for a batch of snapshot parameters, and an orthonormal basis
+// of their span.
+//
+// Snapshot solves.  Alg. 1 lets the snapshots be computed "fully or
+// approximately".  Every family here is symmetric in the bilinear sense
+// (A^T = A, complex entries allowed), so one Krylov method covers them:
+// conjugate gradients with the unconjugated form x^T y (COCG; for a real SPD
+// matrix this is plain CG), preconditioned by the diagonal of A(p_j).  The
+// batch runs every column at once: column j has its own theta(p_j), scalars
+// alpha_j, beta_j and stopping test, and one launch of each kernel covers all
+// active columns.  The same routine refines any start vector, e.g. the
+// SubApSnap output x_hat, which Sec. 3.2 names as the initial guess of an
+// outer Krylov solve when x_hat is not accurate enough.
+//
+// Orthonormalisation.  The snapshot matrices are very ill conditioned (the
+// point of Sec. 4: their singular values decay fast), so Cholesky-based QR is
+// out and the basis comes from TSQR: Householder QR of row panels held in
+// shared memory, then of stacks of g of their R factors, level by level up a
+// tree, and Q formed top-down by applying each node's reflectors to the r x r
+// block its parent hands it.  The column signs are fixed so that diag(R) >= 0,
+// which makes Q unique for a full-rank X.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sas_internal.cuh"
+
+namespace sas {
+namespace off {
+
+constexpr int kThreads = 256;
+
+struct Ops {
+  const int64_t* rp[SAS_MAX_TERMS];
+  const int32_t* ci[SAS_MAX_TERMS];
+  const double* va[SAS_MAX_TERMS];
+};
+
+__device__ inline double re_of(double v) { return v; }
+__device__ inline double re_of(zd v) { return v.re; }
+
+template <typename T> __device__ inline T from_re(double v);
+template <> __device__ inline double from_re<double>(double v) { return v; }
+template <> __device__ inline zd from_re<zd>(double v) { return mkz(v, 0.0); }
+
+// Block-wide sum of one value per thread (kThreads threads); result valid in thread 0.
+template <typename T>
+__device__ inline T block_sum(T v, T* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T s = zero<T>();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kThreads / 32; ++k) s += red[k];
+  return s;
+}
+
+// D[k*n + i] = (A_k)_{ii}
+__global__ void diag_kernel(Ops ops, int K, int64_t n, double* D) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int k = 0; k < K; ++k) {
+      double d = 0.0;
+      for (int64_t e = ops.rp[k][i]; e < ops.rp[k][i + 1]; ++e)
+        if (ops.ci[k][e] == i) d += ops.va[k][e];
+      D[k * n + i] = d;
+    }
+}
+
+// invD[b*n + i] = 1 / sum_k theta[b*K + k] D[k*n + i]; a zero diagonal sets *bad.
+template <typename T>
+__global__ void inv_diag_kernel(const double* D, int K, int64_t n, const T* theta, int B, T* invD,
+                                int* bad) {
+  const int b = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T d = zero<T>();
+    for (int k = 0; k < K; ++k) d += rscale(D[k * n + i], theta[b * K + k]);
+    if (absq(d) == 0.0 || !finitev(d)) {
+      atomicExch(bad, 1);
+      invD[b * n + i] = zero<T>();
+    } else {
+      invD[b * n + i] = divv(from_re<T>(1.0), d);
+    }
+  }
+}
+
+// Per-column state of the batched COCG.
+template <typename T>
+struct Col {
+  T rz;          // r^T D^{-1} r of the current residual
+  T alpha, beta;
+  double rr;     // ||r||^2
+  double relres; // ||r|| / ||b|| (recursively updated residual)
+  int active;    // 1 while iterating
+  int iters;
+  int status;    // 0 running, 1 converged, 2 breakdown, 3 iteration limit
+  int pad;
+};
+
+// Y[:, b] = A(theta_b) X[:, b]; part[b*G + g] = sum_i X_ib Y_ib over the CTA's rows.
+// Columns whose state is inactive are skipped (st == nullptr: every column).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) spmv_kernel(Ops ops, int K, int64_t n, const T* theta,
+                                                        const T* X, T* Y, const Col<T>* st,
+                                                        T* part, int64_t rows_per_cta) {
+  __shared__ T red[kThreads / 32];
+  const int b = blockIdx.x, G = gridDim.y;
+  if (st && !st[b].active) return;
+  T th[SAS_MAX_TERMS];
+  for (int k = 0; k < K; ++k) th[k] = theta[b * K + k];
+  const T* x = X + (int64_t)b * n;
+  T* y = Y + (int64_t)b * n;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  T dot = zero<T>();
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    T acc = zero<T>();
+    for (int k = 0; k < K; ++k) {
+      T s = zero<T>();
+      const int64_t e1 = ops.rp[k][i + 1];
+      for (int64_t e = ops.rp[k][i]; e < e1; ++e) s += rscale(ops.va[k][e], x[ops.ci[k][e]]);
+      acc += th[k] * s;
+    }
+    y[i] = acc;
+    dot += x[i] * acc;
+  }
+  if (part) {
+    dot = block_sum(dot, red);
+    if (threadIdx.x == 0) part[(int64_t)b * G + blockIdx.y] = dot;
+  }
+}
+
+// Start: R = b - AX (AX == nullptr: X = 0, R = b); P = D^{-1} R; partials of r^T D^{-1} r and ||r||^2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) start_kernel(const T* bvec, const T* AX, int64_t n,
+                                                         const T* invD, T* X, T* R, T* P, T* prz,
+                                                         double* prr, int64_t rows_per_cta) {
+  __shared__ T red[kThreads / 32];
+  __shared__ double redd[kThreads / 32];
+  const int b = blockIdx.x, G = gridDim.y;
+  const int64_t off = (int64_t)b * n;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  T rz = zero<T>();
+  double rr = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    T r = bvec[i];
+    if (AX) r -= AX[off + i];
+    else X[off + i] = zero<T>();
+    const T z = invD[off + i] * r;
+    R[off + i] = r;
+    P[off + i] = z;
+    rz += r * z;
+    rr += absq(r);
+  }
+  rz = block_sum(rz, red);
+  rr = block_sum(rr, redd);
+  if (threadIdx.x == 0) {
+    prz[(int64_t)b * G + blockIdx.y] = rz;
+    prr[(int64_t)b * G + blockIdx.y] = rr;
+  }
+}
+
+// One CTA per column: sums of the G partials in a fixed order.
+template <typename T>
+__device__ inline T column_sum(const T* part, int b, int G, T* red) {
+  T s = zero<T>();
+  for (int g = threadIdx.x; g < G; g += kThreads) s += part[(int64_t)b * G + g];
+  return block_sum(s, red);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) start_reduce_kernel(const T* prz, const double* prr, int G,
+                                                                double bnorm, double tol, int maxit,
+                                                                Col<T>* st) {
+  __shared__ T red[kThreads / 32];
+  __shared__ double redd[kThreads / 32];
+  const int b = blockIdx.x;
+  const T rz = column_sum(prz, b, G, red);
+  const double rr = column_sum(prr, b, G, redd);
+  if (threadIdx.x == 0) {
+    Col<T> c;
+    c.rz = rz;
+    c.alpha = zero<T>();
+    c.beta = zero<T>();
+    c.rr = rr;
+    c.relres = sqrt(rr) / bnorm;
+    c.iters = 0;
+    c.pad = 0;
+    if (!(c.relres == c.relres)) {
+      c.status = 2;
+      c.active = 0;
+    } else if (c.relres <= tol) {
+      c.status = 1;
+      c.active = 0;
+    } else if (maxit <= 0) {
+      c.status = 3;
+      c.active = 0;
+    } else {
+      c.status = 0;
+      c.active = 1;
+    }
+    st[b] = c;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) alpha_kernel(const T* ppq, int G, Col<T>* st) {
+  __shared__ T red[kThreads / 32];
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  const T pq = column_sum(ppq, b, G, red);
+  if (threadIdx.x == 0) {
+    if (absq(pq) == 0.0 || !finitev(pq)) {
+      st[b].status = 2;
+      st[b].active = 0;
+    } else {
+      st[b].alpha = divv(st[b].rz, pq);
+    }
+  }
+}
+
+// X += alpha P, R -= alpha Q; partials of the new r^T D^{-1} r and ||r||^2.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, T* X, T* R, const T* P, const T* Q,
+                                                          const T* invD, const Col<T>* st, T* prz,
+                                                          double* prr, int64_t rows_per_cta) {
+  __shared__ T red[kThreads / 32];
+  __shared__ double redd[kThreads / 32];
+  const int b = blockIdx.x, G = gridDim.y;
+  if (!st[b].active) return;
+  const T alpha = st[b].alpha;
+  const int64_t off = (int64_t)b * n;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  T rz = zero<T>();
+  double rr = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    X[off + i] += alpha * P[off + i];
+    const T r = R[off + i] - alpha * Q[off + i];
+    R[off + i] = r;
+    rz += r * (invD[off + i] * r);
+    rr += absq(r);
+  }
+  rz = block_sum(rz, red);
+  rr = block_sum(rr, redd);
+  if (threadIdx.x == 0) {
+    prz[(int64_t)b * G + blockIdx.y] = rz;
+    prr[(int64_t)b * G + blockIdx.y] = rr;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) beta_kernel(const T* prz, const double* prr, int G,
+                                                        double bnorm, double tol, int maxit,
+                                                        Col<T>* st) {
+  __shared__ T red[kThreads / 32];
+  __shared__ double redd[kThreads / 32];
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  const T rz = column_sum(prz, b, G, red);
+  const double rr = column_sum(prr, b, G, redd);
+  if (threadIdx.x == 0) {
+    Col<T> c = st[b];
+    c.iters += 1;
+    c.rr = rr;
+    c.relres = sqrt(rr) / bnorm;
+    if (!(c.relres == c.relres) || !finitev(rz)) {
+      c.status = 2;
+      c.active = 0;
+    } else if (c.relres <= tol) {
+      c.status = 1;
+      c.active = 0;
+    } else if (c.iters >= maxit) {
+      c.status = 3;
+      c.active = 0;
+    } else if (absq(c.rz) == 0.0) {
+      c.status = 2;
+      c.active = 0;
+    } else {
+      c.beta = divv(rz, c.rz);
+    }
+    c.rz = rz;
+    st[b] = c;
+  }
+}
+
+// P = D^{-1} R + beta P
+template <typename T>
+__global__ void __launch_bounds__(kThreads) direction_kernel(int64_t n, const T* R, const T* invD, T* P,
+                                                             const Col<T>* st, int64_t rows_per_cta) {
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  const T beta = st[b].beta;
+  const int64_t off = (int64_t)b * n;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads)
+    P[off + i] = invD[off + i] * R[off + i] + beta * P[off + i];
+}
+
+// partial ||b - AX||^2 of every column (the true residual at the end)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) true_res_kernel(const T* bvec, const T* AX, int64_t n,
+                                                            double* prr, int64_t rows_per_cta) {
+  __shared__ double redd[kThreads / 32];
+  const int b = blockIdx.x, G = gridDim.y;
+  const int64_t off = (int64_t)b * n;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  double rr = 0.0;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) rr += absq(bvec[i] - AX[off + i]);
+  rr = block_sum(rr, redd);
+  if (threadIdx.x == 0) prr[(int64_t)b * G + blockIdx.y] = rr;
+}
+
+__global__ void __launch_bounds__(kThreads) norm_partial_kernel(const double* x, int64_t count, double* out) {
+  __shared__ double redd[kThreads / 32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
+    s += x[i] * x[i];
+  s = block_sum(s, redd);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// ------------------------------------------------------------------ TSQR
+//
+// A panel is h x r, column-major in shared memory (entry (i, j) at A[j*h + i]).
+// Level 0 panel p holds rows p*h .. p*h + h - 1 of X (zeros past n).  A panel
+// at level l >= 1 stacks the R factors of g consecutive panels of level l - 1
+// (zeros past the last one).  The kernel leaves, per panel: R (r x r,
+// column-major, zeros below the diagonal), the reflectors' vectors (unit
+// leading entry implied, zeros above it) and their tau.
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) tsqr_panel_kernel(int level0, const T* src, int64_t n,
+                                                              int64_t ldsrc, int64_t nprev, int g,
+                                                              int r, int h, T* V, int64_t ldv,
+                                                              T* tau, T* Rout) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* A = reinterpret_cast<T*>(smraw);
+  __shared__ T s_scale, s_tau, s_beta;
+  const int64_t p = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int idx = threadIdx.x; idx < h * r; idx += kThreads) {
+    const int j = idx / h, i = idx % h;
+    T v = zero<T>();
+    if (level0) {
+      const int64_t row = p * h + i;
+      if (row < n) v = src[(int64_t)j * ldsrc + row];
+    } else {
+      const int64_t blk = p * g + i / r;
+      if (blk < nprev) v = src[blk * r * r + (int64_t)j * r + (i % r)];
+    }
+    A[idx] = v;
+  }
+  __syncthreads();
+  const int steps = r < h ? r : h;
+  for (int j = 0; j < steps; ++j) {
+    T* a = A + (int64_t)j * h;
+    if (warp == 0) {
+      double s2 = 0.0;
+      for (int i = j + 1 + lane; i < h; i += 32) s2 += absq(a[i]);
+      s2 = warp_sum(s2);
+      if (lane == 0) {
+        const T alpha = a[j];
+        const double ai = absq(alpha) - re_of(alpha) * re_of(alpha);  // |Im alpha|^2
+        if (s2 == 0.0 && ai == 0.0) {
+          s_tau = zero<T>();
+          s_beta = alpha;
+          s_scale = zero<T>();
+        } else {
+          const double nrm = sqrt(absq(alpha) + s2);
+          const double beta = re_of(alpha) >= 0.0 ? -nrm : nrm;
+          // tau = (beta - alpha) / beta, scale = 1 / (alpha - beta)
+          s_tau = rscale(1.0 / beta, from_re<T>(beta) - alpha);
+          s_beta = from_re<T>(beta);
+          s_scale = divv(from_re<T>(1.0), alpha - from_re<T>(beta));
+        }
+      }
+    }
+    __syncthreads();
+    const T t = s_tau, sc = s_scale;
+    if (absq(t) != 0.0)
+      for (int i = j + 1 + threadIdx.x; i < h; i += kThreads) a[i] = sc * a[i];
+    __syncthreads();
+    if (absq(t) != 0.0) {
+      const T ct = conjv(t);
+      for (int c = j + 1 + warp; c < r; c += kThreads / 32) {
+        T* ac = A + (int64_t)c * h;
+        T w = zero<T>();
+        for (int i = j + lane; i < h; i += 32) w += (i == j ? ac[i] : conjv(a[i]) * ac[i]);
+        w = warp_sum(w);
+        const T f = ct * w;
+        for (int i = j + lane; i < h; i += 32) ac[i] -= (i == j ? f : f * a[i]);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tau[p * r + j] = t;
+      a[j] = s_beta;
+    }
+    __syncthreads();
+  }
+  for (int j = steps; threadIdx.x == 0 && j < r; ++j) tau[p * r + j] = zero<T>();
+  // R, then the reflectors (the strict lower part; rows past the data are zero anyway)
+  for (int idx = threadIdx.x; idx < r * r; idx += kThreads) {
+    const int j = idx / r, i = idx % r;
+    Rout[p * r * r + idx] = (i <= j && i < h) ? A[(int64_t)j * h + i] : zero<T>();
+  }
+  for (int idx = threadIdx.x; idx < h * r; idx += kThreads) {
+    const int j = idx / h, i = idx % h;
+    const T v = i > j ? A[idx] : zero<T>();
+    if (level0) {
+      const int64_t row = p * h + i;
+      if (row < n) V[(int64_t)j * ldv + row] = v;
+    } else {
+      V[p * (int64_t)h * r + idx] = v;
+    }
+  }
+}
+
+// Q formation at one level: panel p maps its r x r block C_p to
+// H_1 ... H_r [C_p; 0] (h x r).  One warp per column of C; the column lives
+// in registers (row i = lane + 32 k).  Level 0 writes rows of Q; higher
+// levels write the r x r blocks of their children.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) tsqr_apply_kernel(int level0, const T* V, int64_t ldv,
+                                                              const T* tau, int r, int h, int g,
+                                                              const T* Cin, T* out, int64_t ldout,
+                                                              int64_t n, int64_t nchild) {
+  constexpr int KM = 16;  // h <= 512
+  const int64_t p = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.y * (kThreads / 32) + warp;
+  if (c >= r) return;
+  const int kc = (h + 31) / 32;
+  int64_t vrows = h;  // rows of this panel that exist
+  if (level0 && p * h + h > n) vrows = n - p * h;
+  T w[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    const int i = lane + 32 * k;
+    w[k] = (k < kc && i < r) ? Cin[p * r * r + (int64_t)c * r + i] : zero<T>();
+  }
+  for (int j = r - 1; j >= 0; --j) {
+    const T t = tau[p * r + j];
+    if (absq(t) == 0.0) continue;
+    const T* vj = level0 ? V + (int64_t)j * ldv + p * h : V + p * (int64_t)h * r + (int64_t)j * h;
+    T vv[KM];
+    T dot = zero<T>();
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      const int i = lane + 32 * k;
+      vv[k] = zero<T>();
+      if (k < kc && i >= j && i < vrows) {
+        vv[k] = i == j ? from_re<T>(1.0) : vj[i];
+        dot += conjv(vv[k]) * w[k];
+      }
+    }
+    dot = warp_sum(dot);
+    const T f = t * dot;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) w[k] -= f * vv[k];
+  }
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    const int i = lane + 32 * k;
+    if (k >= kc || i >= h) continue;
+    if (level0) {
+      const int64_t row = p * h + i;
+      if (row < n) out[(int64_t)c * ldout + row] = w[k];
+    } else {
+      const int64_t blk = p * g + i / r;
+      if (blk < nchild) out[blk * r * r + (int64_t)c * r + (i % r)] = w[k];
+    }
+  }
+}
+
+}  // namespace off
+
+// ------------------------------------------------------------------ host
+
+namespace {
+
+using off::Col;
+using off::kThreads;
+
+int num_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+bool on_device(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+sas_status fail_off(sas_status code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+sas_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? SAS_ENOMEM : SAS_ECUDA;
+}
+
+// theta_k(p) on the host, the same rules as the online stage.
+void theta_host(int rule, int K, const double* p, std::vector<std::complex<double>>& th) {
+  th.assign(K, 0.0);
+  if (rule == SAS_THETA_PENCIL) {
+    th[0] = -1.0;
+    th[1] = std::complex<double>(0.0, p[0]);
+  } else if (rule == SAS_THETA_DELAY) {
+    th[0] = std::complex<double>(0.0, p[0]);
+    th[1] = -1.0;
+    th[2] = -std::exp(std::complex<double>(0.0, p[0] * p[1]));
+  } else {
+    th[0] = 1.0;
+    for (int k = 1; k < K; ++k) th[k] = p[k - 1];
+  }
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { cudaFree(p); }
+  cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes ? bytes : 16); }
+  template <typename U> U* as() const { return reinterpret_cast<U*>(p); }
+};
+
+template <typename T>
+sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T* X, int warm,
+                    double tol, int32_t maxit, int32_t* iters_out, double* relres_out) {
+  const int64_t n = d->n;
+  const int K = d->K;
+  const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->theta_rule == SAS_THETA_DELAY ? 2 : K - 1;
+  const int sms = num_sms();
+  // rows per CTA: about 16 CTAs per SM over the whole batch, multiples of the block size
+  int64_t rpc = (n * (int64_t)B + (int64_t)sms * 16 - 1) / ((int64_t)sms * 16);
+  rpc = std::max<int64_t>(kThreads, (rpc + kThreads - 1) / kThreads * kThreads);
+  const int G = (int)((n + rpc - 1) / rpc);
+  const dim3 grid(B, G);
+
+  off::Ops ops;
+  for (int k = 0; k < K; ++k) {
+    ops.rp[k] = d->rowptr[k];
+    ops.ci[k] = d->colind[k];
+    ops.va[k] = d->values[k];
+  }
+  std::vector<T> th_h((size_t)B * K);
+  std::vector<std::complex<double>> th;
+  for (int b = 0; b < B; ++b) {
+    theta_host(d->theta_rule, K, params + (size_t)b * dp, th);
+    for (int k = 0; k < K; ++k) {
+      if constexpr (sizeof(T) == 16) {
+        th_h[(size_t)b * K + k] = mkz(th[k].real(), th[k].imag());
+      } else {
+        th_h[(size_t)b * K + k] = th[k].real();
+      }
+    }
+  }
+  DevBuf theta, D, invD, R, P, Q, prz, ppq, prr, st, bad, nb;
+  const size_t vec = (size_t)n * B * sizeof(T);
+  cudaError_t e = theta.alloc(th_h.size() * sizeof(T));
+  if (e == cudaSuccess) e = D.alloc((size_t)K * n * sizeof(double));
+  if (e == cudaSuccess) e = invD.alloc(vec);
+  if (e == cudaSuccess) e = R.alloc(vec);
+  if (e == cudaSuccess) e = P.alloc(vec);
+  if (e == cudaSuccess) e = Q.alloc(vec);
+  if (e == cudaSuccess) e = prz.alloc((size_t)B * G * sizeof(T));
+  if (e == cudaSuccess) e = ppq.alloc((size_t)B * G * sizeof(T));
+  if (e == cudaSuccess) e = prr.alloc((size_t)B * G * sizeof(double));
+  if (e == cudaSuccess) e = st.alloc((size_t)B * sizeof(Col<T>));
+  if (e == cudaSuccess) e = bad.alloc(sizeof(int));
+  if (e == cudaSuccess) e = nb.alloc((size_t)sms * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: allocation");
+  cudaStream_t s = nullptr;
+  e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: stream");
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } guard{s};
+  e = cudaMemcpyAsync(theta.p, th_h.data(), th_h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: setup copies");
+  off::diag_kernel<<<sms * 4, kThreads, 0, s>>>(ops, K, n, D.as<double>());
+  off::inv_diag_kernel<T><<<dim3(sms * 2, B), kThreads, 0, s>>>(D.as<double>(), K, n, theta.as<T>(), B,
+                                                                invD.as<T>(), bad.as<int>());
+  // ||b|| (b viewed as 2n doubles when complex)
+  const int64_t bcount = n * (int64_t)(sizeof(T) / sizeof(double));
+  off::norm_partial_kernel<<<sms, kThreads, 0, s>>>((const double*)d->b, bcount, nb.as<double>());
+  if (warm)
+    off::spmv_kernel<T><<<grid, kThreads, 0, s>>>(ops, K, n, theta.as<T>(), X, Q.as<T>(), nullptr, nullptr, rpc);
+  off::start_kernel<T><<<grid, kThreads, 0, s>>>((const T*)d->b, warm ? Q.as<T>() : nullptr, n, invD.as<T>(), X,
+                                                 R.as<T>(), P.as<T>(), prz.as<T>(), prr.as<double>(), rpc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: start launches");
+  int bad_h = 0;
+  std::vector<double> nb_h((size_t)sms);
+  e = cudaMemcpyAsync(&bad_h, bad.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nb_h.data(), nb.p, nb_h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: start");
+  if (bad_h) return fail_off(SAS_EINVAL, "krylov: A(p) has a zero (or non-finite) diagonal entry; "
+                                         "the Jacobi preconditioner needs a non-zero diagonal");
+  double bn2 = 0.0;
+  for (double v : nb_h) bn2 += v;
+  const double bnorm = std::sqrt(bn2);
+  if (!(bnorm > 0.0)) return fail_off(SAS_EINVAL, "krylov: b = 0");
+  off::start_reduce_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, maxit,
+                                                     st.as<Col<T>>());
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: start reduce");
+
+  // the iteration, captured once as a graph of `chunk` steps and replayed
+  const int chunk = 16;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: capture");
+  for (int it = 0; it < chunk; ++it) {
+    off::spmv_kernel<T><<<grid, kThreads, 0, s>>>(ops, K, n, theta.as<T>(), P.as<T>(), Q.as<T>(), st.as<Col<T>>(),
+                                                  ppq.as<T>(), rpc);
+    off::alpha_kernel<T><<<B, kThreads, 0, s>>>(ppq.as<T>(), G, st.as<Col<T>>());
+    off::update_kernel<T><<<grid, kThreads, 0, s>>>(n, X, R.as<T>(), P.as<T>(), Q.as<T>(), invD.as<T>(),
+                                                    st.as<Col<T>>(), prz.as<T>(), prr.as<double>(), rpc);
+    off::beta_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, maxit,
+                                               st.as<Col<T>>());
+    off::direction_kernel<T><<<grid, kThreads, 0, s>>>(n, R.as<T>(), invD.as<T>(), P.as<T>(), st.as<Col<T>>(), rpc);
+  }
+  e = cudaStreamEndCapture(s, &graph);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e, "krylov: graph");
+  }
+  std::vector<Col<T>> st_h((size_t)B);
+  const int64_t max_chunks = ((int64_t)std::max(maxit, 0) + chunk - 1) / chunk + 1;
+  for (int64_t ch = 0; ch < max_chunks && e == cudaSuccess; ++ch) {
+    e = cudaMemcpyAsync(st_h.data(), st.p, st_h.size() * sizeof(Col<T>), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    bool any = false;
+    for (const auto& c : st_h) any = any || c.active;
+    if (!any) break;
+    e = cudaGraphLaunch(exec, s);
+  }
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: iteration");
+  e = cudaMemcpyAsync(st_h.data(), st.p, st_h.size() * sizeof(Col<T>), cudaMemcpyDeviceToHost, s);
+  // true residual of the final iterates
+  off::spmv_kernel<T><<<grid, kThreads, 0, s>>>(ops, K, n, theta.as<T>(), X, Q.as<T>(), nullptr, nullptr, rpc);
+  off::true_res_kernel<T><<<grid, kThreads, 0, s>>>((const T*)d->b, Q.as<T>(), n, prr.as<double>(), rpc);
+  std::vector<double> prr_h((size_t)B * G);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(prr_h.data(), prr.p, prr_h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: final residual");
+  int failed = 0, broke = 0;
+  for (int b = 0; b < B; ++b) {
+    double rr = 0.0;
+    for (int g = 0; g < G; ++g) rr += prr_h[(size_t)b * G + g];
+    if (iters_out) iters_out[b] = st_h[b].iters;
+    if (relres_out) relres_out[b] = std::sqrt(rr) / bnorm;
+    if (st_h[b].status != 1) ++failed;
+    if (st_h[b].status == 2) ++broke;
+  }
+  if (failed)
+    return fail_off(SAS_ENOCONV, "krylov: " + std::to_string(failed) + " of " + std::to_string(B) +
+                                     " columns did not reach the tolerance (" + std::to_string(broke) +
+                                     " broke down); X holds the last iterates");
+  return SAS_OK;
+}
+
+// panel height for TSQR: a multiple g*r of r with g >= 2, h <= 512, the panel within ~100 KB
+// of shared memory where that allows g >= 2, else the largest that fits the opt-in limit.
+int tsqr_height(int r, size_t elt, int& g) {
+  const size_t soft = 100 * 1024, hard = 227 * 1024 - 1024;
+  g = std::max(2, (int)std::min<size_t>(512 / r, soft / ((size_t)r * r * elt)));
+  while (g > 2 && (size_t)g * r * r * elt > soft) --g;
+  if ((size_t)g * r * r * elt > hard || g * r > 512) return 0;
+  return g * r;
+}
+
+template <typename T>
+sas_status tsqr_t(const T* X, int64_t n, int r, int64_t ldx, T* Qout, int64_t ldq, T* R_host) {
+  int g = 0;
+  const int h = tsqr_height(r, sizeof(T), g);
+  if (h == 0) return fail_off(SAS_ENOTSUP, "tsqr: r too large for a panel in shared memory");
+  const size_t smem = (size_t)h * r * sizeof(T);
+  // level sizes
+  std::vector<int64_t> P{(n + h - 1) / h};
+  while (P.back() > 1) P.push_back((P.back() + g - 1) / g);
+  const int L = (int)P.size();
+  DevBuf V0;
+  std::vector<DevBuf> V(L), tau(L), Rb(L), Cb(L);
+  cudaError_t e = V0.alloc((size_t)n * r * sizeof(T));
+  for (int l = 0; l < L && e == cudaSuccess; ++l) {
+    if (l > 0) e = V[l].alloc((size_t)P[l] * h * r * sizeof(T));
+    if (e == cudaSuccess) e = tau[l].alloc((size_t)P[l] * r * sizeof(T));
+    if (e == cudaSuccess) e = Rb[l].alloc((size_t)P[l] * r * r * sizeof(T));
+    if (e == cudaSuccess) e = Cb[l].alloc((size_t)P[l] * r * r * sizeof(T));
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "tsqr: allocation");
+  e = cudaFuncSetAttribute(off::tsqr_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "tsqr: shared memory");
+  cudaStream_t s = nullptr;
+  e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "tsqr: stream");
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } guard{s};
+  for (int l = 0; l < L; ++l) {
+    const bool lv0 = l == 0;
+    off::tsqr_panel_kernel<T><<<(unsigned)P[l], kThreads, smem, s>>>(
+        lv0 ? 1 : 0, lv0 ? X : Rb[l - 1].as<T>(), n, ldx, lv0 ? 0 : P[l - 1], g, r, h,
+        lv0 ? V0.as<T>() : V[l].as<T>(), n, tau[l].as<T>(), Rb[l].as<T>());
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "tsqr: factor launches");
+  // top R and the column signs
+  std::vector<T> Rt((size_t)r * r);
+  e = cudaMemcpyAsync(Rt.data(), Rb[L - 1].p, Rt.size() * sizeof(T), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "tsqr: top R");
+  std::vector<T> Dg((size_t)r * r, zero<T>());
+  for (int j = 0; j < r; ++j) {
+    double dj;
+    if constexpr (sizeof(T) == 16) dj = Rt[(size_t)j * r + j].re;
+    else dj = Rt[(size_t)j * r + j];
+    const double sg = dj < 0.0 ? -1.0 : 1.0;
+    if constexpr (sizeof(T) == 16) Dg[(size_t)j * r + j] = mkz(sg, 0.0);
+    else Dg[(size_t)j * r + j] = sg;
+    if (R_host)
+      for (int c = 0; c < r; ++c) {  // row j of D R
+        const T v = Rt[(size_t)c * r + j];
+        R_host[(size_t)c * r + j] = c >= j ? rscale(sg, v) : zero<T>();
+      }
+  }
+  e = cudaMemcpyAsync(Cb[L - 1].p, Dg.data(), Dg.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "tsqr: signs");
+  const dim3 cols_grid(1, (r + kThreads / 32 - 1) / (kThreads / 32));
+  for (int l = L - 1; l >= 0; --l) {
+    const bool lv0 = l == 0;
+    off::tsqr_apply_kernel<T><<<dim3((unsigned)P[l], cols_grid.y), kThreads, 0, s>>>(
+        lv0 ? 1 : 0, lv0 ? V0.as<T>() : V[l].as<T>(), n, tau[l].as<T>(), r, h, g, Cb[l].as<T>(),
+        lv0 ? Qout : Cb[l - 1].as<T>(), ldq, n, lv0 ? 0 : P[l - 1]);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "tsqr: Q formation");
+  return SAS_OK;
+}
+
+}  // namespace
+}  // namespace sas
+
+using namespace sas;
+
+sas_status subapsnap_krylov_affine(const sas_affine_desc* d, const double* params, int32_t B, void* X,
+                                   int32_t warm, double tol, int32_t maxit, int32_t* iters_out,
+                                   double* relres_out) {
+  if (!d || !params || !X) return fail_off(SAS_EINVAL, "NULL argument");
+  if (B < 1) return fail_off(SAS_EINVAL, "need B >= 1");
+  if (d->n < 1) return fail_off(SAS_EINVAL, "need n >= 1");
+  if (d->K < 1 || d->K > SAS_MAX_TERMS) return fail_off(SAS_EINVAL, "K must be in [1, 8]");
+  if (d->dtype != SAS_REAL64 && d->dtype != SAS_COMPLEX128) return fail_off(SAS_EINVAL, "bad dtype");
+  if (d->theta_rule == SAS_THETA_PENCIL && (d->K != 2 || d->dtype != SAS_COMPLEX128))
+    return fail_off(SAS_EINVAL, "pencil rule needs K = 2 and complex data");
+  if (d->theta_rule == SAS_THETA_DELAY && (d->K != 3 || d->dtype != SAS_COMPLEX128))
+    return fail_off(SAS_EINVAL, "delay rule needs K = 3 and complex data");
+  if (d->theta_rule != SAS_THETA_LINEAR && d->theta_rule != SAS_THETA_PENCIL &&
+      d->theta_rule != SAS_THETA_DELAY)
+    return fail_off(SAS_EINVAL, "bad theta rule");
+  if (!(tol >= 0.0)) return fail_off(SAS_EINVAL, "tol must be >= 0");
+  if (!on_device(X) || !on_device(d->b)) return fail_off(SAS_EINVAL, "X and b must be device pointers");
+  for (int k = 0; k < d->K; ++k)
+    if (!on_device(d->rowptr[k]) || !on_device(d->colind[k]) || !on_device(d->values[k]))
+      return fail_off(SAS_EINVAL, "CSR arrays must be device pointers");
+  if (d->dtype == SAS_COMPLEX128)
+    return krylov_t<zd>(d, params, B, (zd*)X, warm, tol, maxit, iters_out, relres_out);
+  return krylov_t<double>(d, params, B, (double*)X, warm, tol, maxit, iters_out, relres_out);
+}
+
+sas_status subapsnap_tsqr(const void* X, int64_t n, int32_t r, int64_t ldx, int32_t dtype, void* Q,
+                          int64_t ldq, void* R_out) {
+  if (!X || !Q) return fail_off(SAS_EINVAL, "NULL argument");
+  if (r < 1 || n < r) return fail_off(SAS_EINVAL, "need 1 <= r <= n");
+  if (ldx < n || ldq < n) return fail_off(SAS_EINVAL, "leading dimensions must be >= n");
+  if (dtype != SAS_REAL64 && dtype != SAS_COMPLEX128) return fail_off(SAS_EINVAL, "bad dtype");
+  if (!on_device(X) || !on_device(Q)) return fail_off(SAS_EINVAL, "X and Q must be device pointers");
+  if (dtype == SAS_COMPLEX128)
+    return tsqr_t<zd>((const zd*)X, n, r, ldx, (zd*)Q, ldq, (zd*)R_out);
+  return tsqr_t<double>((const double*)X, n, r, ldx, (double*)Q, ldq, (double*)R_out);
+}

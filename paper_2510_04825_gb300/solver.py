@@ -92,6 +92,38 @@ class AffineSolver:
         api.subapsnap_true_residual(self.ctx, params, params.shape[0], X, rho, stream)
 
 
+def snapshot_solve(prob, params, X, blocks_device=None, b_device=None, warm=False, tol=1e-12,
+                   maxit=20000, device="cuda", allow_noconv=False):
+    """Batched Krylov solves A(p_j) x_j = b on the device into X (B, n); (iterations, true residuals)."""
+    cplx = bool(prob.complex_valued)
+    blocks = blocks_device or [csr_to_device(A, device) for A in prob.blocks]
+    bdt = np.complex128 if cplx else np.float64
+    b = b_device if b_device is not None else \
+        torch.from_numpy(np.ascontiguousarray(prob.b, dtype=bdt)).to(device)
+    P = np.atleast_2d(np.asarray(params, dtype=np.float64))
+    desc = api._affine_desc(prob.n, P.shape[0], P.shape[0], blocks, None, None, b,
+                            theta_rule_code(prob.theta_rule), api.SAS_MODE_PLAIN, api.SAS_QOI_NONE,
+                            None, cplx)
+    return api.subapsnap_krylov_affine(desc, P, X, warm=warm, tol=tol, maxit=maxit,
+                                       allow_noconv=allow_noconv)
+
+
+def snapshot_basis(prob, blocks_device=None, b_device=None, params=None, tol=1e-12, maxit=20000,
+                   device="cuda"):
+    """Offline stage on the device (Alg. 1 steps 1-2): snapshot solves, then TSQR.
+
+    Returns (S, info): S is the (r, n) device tensor of the orthonormal basis
+    (the column-major n x r matrix the online contexts take); info holds the
+    iteration counts, the true residuals of the solves and R."""
+    cplx = bool(prob.complex_valued)
+    P = prob.snap_params if params is None else params
+    P = np.atleast_2d(np.asarray(P, dtype=np.float64))
+    X = torch.empty((P.shape[0], prob.n), dtype=torch.complex128 if cplx else torch.float64, device=device)
+    it, rel = snapshot_solve(prob, P, X, blocks_device, b_device, tol=tol, maxit=maxit, device=device)
+    R = api.subapsnap_tsqr(X)
+    return X, {"iters": it, "relres": rel, "R": R}
+
+
 def select_rows(prob, S_device, blocks_device, p_sel, s, device="cuda"):
     """CPQR-in-rounds row selection on the device; returns (J, gaps) on the host."""
     cplx = bool(prob.complex_valued)

@@ -1,0 +1,169 @@
+"""GPU parity of the offline stage (Alg. 1 steps 1-2) against the oracle, through the C-ABI.
+
+Tolerances
+  Snapshot solves: the batched COCG stops at ||b - A x|| / ||b|| <= tol; the
+    true residual recomputed by the oracle's own matrix must be <= 10 tol (the
+    updated and the true residual drift apart by ~kappa(A) u), and the distance
+    to the oracle's direct solve is bounded by kappa(A) times the residual.
+  TSQR: with diag(R) >= 0 the thin QR of a full-rank X is unique, so Q and R
+    are compared with the oracle's entry by entry: |Q - Q_o| <= 1e-12 and
+    |R - R_o| <= 1e-12 |R| for well-conditioned X (the perturbation of the QR
+    factors is ~kappa(X) u).  For numerically rank-deficient X only what is
+    unique is compared: Q^H Q = I, X = Q R and |R| against the oracle's on the
+    well-determined leading columns.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU runs deselect with -m "not gpu"
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import online, problem as oproblem, selection, snapshots  # noqa: E402
+from paper_2510_04825_gb300 import api  # noqa: E402
+from paper_2510_04825_gb300.solver import (AffineSolver, csr_to_device, select_rows,  # noqa: E402
+                                           snapshot_basis, snapshot_solve)
+from workloads import get_config  # noqa: E402
+
+DEV = "cuda"
+
+SMALL = [("reaction_diffusion_1d", dict(n=1000, r=8, s=16, m=20)),
+         ("diffusion_2d", dict(N=48, r=60, s=120, m=40)),
+         ("transfer_function", dict(N=9, r=20, s=50, m=40)),
+         ("delay_system", dict(n=3000, r=16, s=32, m=40))]
+
+
+def _tensor(a, cplx):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128 if cplx else np.float64)).to(DEV)
+
+
+@pytest.mark.parametrize("name,kw", SMALL, ids=[c[0] for c in SMALL])
+def test_snapshot_solves_match_direct_solves(name, kw):
+    prob = get_config(name, **kw)
+    cplx = prob.complex_valued
+    P = prob.snap_params
+    X = torch.empty((len(P), prob.n), dtype=torch.complex128 if cplx else torch.float64, device=DEV)
+    tol = 1e-10
+    it, rel = snapshot_solve(prob, P, X, tol=tol, maxit=50000)
+    Xg = X.cpu().numpy()
+    worst_err = 0.0
+    for j, p in enumerate(P):
+        A = oproblem.full_matrix(prob, p)
+        xo = snapshots.solve_full(prob, p)
+        res = np.linalg.norm(A @ Xg[j] - prob.b) / np.linalg.norm(prob.b)
+        assert res <= 10 * tol and rel[j] <= 10 * tol, (j, res, rel[j])
+        err = np.linalg.norm(Xg[j] - xo) / np.linalg.norm(xo)
+        worst_err = max(worst_err, err)
+        # forward error <= kappa(A) * residual (kappa from a dense SVD at these sizes)
+        if prob.n <= 2500:
+            sv = np.linalg.svd(A.toarray(), compute_uv=False)
+            assert err <= sv[0] / sv[-1] * 10 * tol, (j, err)
+    print(f"{name}: iterations {it.min()}..{it.max()}, max true residual {rel.max():.2e}, "
+          f"max error vs direct {worst_err:.2e}")
+
+
+def test_warm_start_from_subapsnap_output():
+    """x_hat from the online stage as the start vector (Sec. 3.2): fewer iterations, same bar."""
+    prob = get_config("diffusion_2d", N=48, r=20, s=40, m=8)
+    S = snapshots.orthonormal_basis(snapshots.snapshot_matrix(prob))
+    V = np.asarray(oproblem.full_matrix(prob, prob.sel_param) @ S)
+    J, _ = selection.cpqr_rows(V, prob.s)
+    params = prob.test_params[:8]
+    Y, _ = online.solve_many(prob, S, J, params)
+    Xhat = Y @ S.T
+    tol = 1e-11
+    Xw = _tensor(Xhat, False)
+    it_w, rel_w = snapshot_solve(prob, params, Xw, warm=True, tol=tol)
+    Xc = torch.empty_like(Xw)
+    it_c, rel_c = snapshot_solve(prob, params, Xc, warm=False, tol=tol)
+    assert (rel_w <= 10 * tol).all() and (rel_c <= 10 * tol).all()
+    assert (it_w < it_c).all(), (it_w, it_c)
+    print(f"warm start: {it_w.mean():.0f} iterations against {it_c.mean():.0f} from zero")
+
+
+def test_krylov_iteration_limit_and_bad_arguments():
+    prob = get_config("diffusion_2d", N=32, r=4, s=8, m=4)
+    X = torch.empty((4, prob.n), dtype=torch.float64, device=DEV)
+    with pytest.raises(api.SasError) as ei:
+        snapshot_solve(prob, prob.snap_params, X, tol=1e-14, maxit=3)
+    assert ei.value.code == api.SAS_ENOCONV
+    it, rel = snapshot_solve(prob, prob.snap_params, X, tol=1e-14, maxit=3, allow_noconv=True)
+    assert (it == 3).all() and np.isfinite(rel).all()
+    with pytest.raises(api.SasError):
+        snapshot_solve(prob, prob.snap_params, X, tol=-1.0)
+
+
+@pytest.mark.parametrize("n,r,cplx", [(5000, 37, False), (100_000, 60, False), (5000, 20, True),
+                                      (2000, 80, True), (777, 1, False), (130, 64, False)])
+def test_tsqr_matches_oracle_on_full_rank(n, r, cplx):
+    rng = np.random.default_rng(n + r)
+    Xh = rng.standard_normal((n, r))
+    if cplx:
+        Xh = Xh + 1j * rng.standard_normal((n, r))
+    Xh[:, 0] *= 1e3  # uneven column scales, still well conditioned
+    X = _tensor(Xh.T, cplx)
+    Q = torch.empty_like(X)
+    R = api.subapsnap_tsqr(X, Q)
+    Qo, Ro = snapshots.thin_qr(Xh)
+    Qg = Q.cpu().numpy().T
+    np.testing.assert_allclose(Qg, Qo, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(R, Ro, rtol=0, atol=1e-12 * np.abs(Ro).max())
+    # in place
+    api.subapsnap_tsqr(X)
+    np.testing.assert_array_equal(X.cpu().numpy().T, Qg)
+
+
+@pytest.mark.parametrize("name,kw", SMALL[:1] + SMALL[2:], ids=[c[0] for c in SMALL[:1] + SMALL[2:]])
+def test_tsqr_on_rank_deficient_snapshots(name, kw):
+    """Snapshot matrices with kappa ~ 1e15 .. 1e22: what is unique about their QR."""
+    prob = get_config(name, **kw)
+    Xh = snapshots.snapshot_matrix(prob)
+    cplx = prob.complex_valued
+    X = _tensor(Xh.T, cplx)
+    R = api.subapsnap_tsqr(X, X)
+    Q = X.cpu().numpy().T
+    r = Xh.shape[1]
+    np.testing.assert_allclose(Q.conj().T @ Q, np.eye(r), atol=1e-13)
+    np.testing.assert_allclose(Q @ R, Xh, atol=1e-14 * np.linalg.norm(Xh, 2))
+    assert np.allclose(np.tril(R, -1), 0)
+    d = np.diag(R)
+    assert (d.real >= 0).all() and (d.imag == 0).all()
+    _, Ro = snapshots.thin_qr(Xh)
+    lead = np.abs(np.diag(Ro)) > 1e-8 * np.abs(Ro[0, 0])
+    k = int(np.argmin(lead)) if not lead.all() else r
+    np.testing.assert_allclose(np.abs(np.diag(R))[:k], np.abs(np.diag(Ro))[:k], rtol=1e-6)
+
+
+def test_offline_then_online_pipeline():
+    """Snapshots, basis and rows all on the device, then the online stage; the result
+    has the same quality as the oracle's pipeline (x_hat true residual)."""
+    prob = get_config("diffusion_2d", N=48, r=30, s=60, m=40)
+    blocks = [csr_to_device(A, DEV) for A in prob.blocks]
+    S, info = snapshot_basis(prob, blocks_device=blocks, tol=1e-12)
+    assert (info["relres"] <= 1e-11).all()
+    J, _ = select_rows(prob, S, blocks, prob.sel_param, prob.s)
+    So = snapshots.orthonormal_basis(snapshots.snapshot_matrix(prob))
+    Vo = np.asarray(oproblem.full_matrix(prob, prob.sel_param) @ So)
+    Jo, _ = selection.cpqr_rows(Vo, prob.s)
+    overlap = len(set(J.tolist()) & set(Jo.tolist())) / prob.s
+    sv = AffineSolver(prob, None, J, mode=api.SAS_MODE_PLAIN, device=DEV, S_device=S, blocks_device=blocks)
+    params = prob.test_params
+    Pd = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
+    Xg = torch.empty((len(params), prob.n), dtype=torch.float64, device=DEV)
+    sv.solve(Pd, api.SAS_OUT_XHAT, Xg)
+    Xg = Xg.cpu().numpy()
+    sv.close()
+    Yo, _ = online.solve_many(prob, So, Jo, params)
+    Xo = Yo @ So.T
+    res_g, res_o = [], []
+    for j, p in enumerate(params):
+        A = oproblem.full_matrix(prob, p)
+        nb = np.linalg.norm(prob.b)
+        res_g.append(np.linalg.norm(A @ Xg[j] - prob.b) / nb)
+        res_o.append(np.linalg.norm(A @ Xo[j] - prob.b) / nb)
+    res_g, res_o = np.array(res_g), np.array(res_o)
+    assert (res_g <= 10 * res_o + 1e-9).all(), (res_g.max(), res_o.max())
+    print(f"pipeline: x_hat residual max {res_g.max():.2e} (oracle pipeline {res_o.max():.2e}), "
+          f"rows shared with the oracle's J {overlap:.0%}")
