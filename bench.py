@@ -799,6 +799,90 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_offline(args):
+    """Offline stage (Alg. 1 steps 1-2) on one GPU: the batched snapshot solves of the
+    workload's snapshot parameters, then the TSQR basis, with float32 iterates and
+    float64 residual replacements (chosen) and all in float64 (plain).  One JSON line."""
+    import torch
+    from paper_2510_04825_gb300 import api
+    from paper_2510_04825_gb300.solver import csr_to_device, snapshot_solve
+    from workloads import get_config
+
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    kw = {"N": args.grid} if args.workload == "diffusion_2d" else {}
+    prob = get_config(args.workload, **kw)
+    cplx = bool(prob.complex_valued)
+    dt = torch.complex128 if cplx else torch.float64
+    elt = 16 if cplx else 8
+    blocks = [csr_to_device(A, dev) for A in prob.blocks]
+    b = torch.from_numpy(np.ascontiguousarray(prob.b, dtype=np.complex128 if cplx else np.float64)).to(dev)
+    P = np.atleast_2d(prob.snap_params)
+    B, n = P.shape[0], prob.n
+    X = torch.empty((B, n), dtype=dt, device=dev)
+    # warm-up: a few iterations of two columns in both forms, and a TSQR of them
+    for mixed in (False, True):
+        snapshot_solve(prob, P[:2], X[:2], blocks, b, tol=0.0, maxit=4, allow_noconv=True, mixed=mixed)
+    api.subapsnap_tsqr(X[:2], torch.empty_like(X[:2]))
+    torch.cuda.synchronize()
+    hbm, hbm_kind = peaks()
+    nnz = sum(A.nnz for A in prob.blocks)
+    csr_bytes = sum(A.nnz * 12 + (A.shape[0] + 1) * 8 for A in prob.blocks)
+    clk_path = os.path.join(tempfile.gettempdir(), f"sas_offline_clocks_{os.getpid()}.csv")
+    cp, cf_ = start_clock_sampler(clk_path)
+    forms = {}
+    for mixed in ([True, False] if not args.no_plain else [True]):
+        t0 = time.perf_counter()
+        it, rel = snapshot_solve(prob, P, X, blocks, b, tol=args.tol, maxit=args.maxit, allow_noconv=True,
+                                 mixed=mixed)
+        t_k = time.perf_counter() - t0
+        # per column-iteration: the product reads P and writes Q, the update reads X, P, Q, R,
+        # D^-1 and writes X, R, the direction reads R, D^-1, P and writes P (13 vector passes,
+        # float32 storage in the mixed form); the CSR blocks once per iteration of the batch
+        ve = elt // 2 if mixed else elt
+        col_iters = int(it.sum())
+        alg_bytes = col_iters * 13 * n * ve + int(it.max()) * (csr_bytes if not mixed else csr_bytes * 2 // 3)
+        # float64 work of the plain form per column-iteration: 2 flops per stored entry of
+        # every block, 2 per block and row for theta, 14 per row for the vector updates
+        cf = 4 if cplx else 1
+        flops = col_iters * cf * (2.0 * nnz + 2.0 * len(prob.blocks) * n + 14.0 * n)
+        forms["mixed" if mixed else "plain"] = {
+            "seconds": round(t_k, 4), "iterations_min": int(it.min()), "iterations_max": int(it.max()),
+            "iterations_mean": round(float(it.mean()), 1), "true_rel_residual_max": float(rel.max()),
+            "algorithmic_bytes": alg_bytes, "achieved_gbs": round(alg_bytes / t_k / 1e9, 1),
+            "hbm_frac": round(alg_bytes / t_k / 1e9 / hbm, 4),
+            "fp64_flops": flops, "fp64_pipe_frac": None if mixed else round(flops / t_k / FP64_PEAK, 4)}
+    Q = torch.empty_like(X)
+    t1 = time.perf_counter()
+    R = api.subapsnap_tsqr(X, Q)
+    t_q = time.perf_counter() - t1
+    clocks = stop_clock_sampler(cp, cf_, clk_path, 0)
+    orth = float(torch.linalg.matrix_norm(Q.conj() @ Q.T - torch.eye(B, dtype=dt, device=dev)).item())
+    tsqr_flops = 4.0 * n * B * B * (4.0 if cplx else 1.0)
+    chosen = forms["mixed"]
+    out = {
+        "metric": "snapshot solves + orthonormal basis per second (offline stage, Alg. 1 steps 1-2)",
+        "value": round(B / (chosen["seconds"] + t_q), 3), "unit": "snapshots/s", "n_gpus": 1,
+        "higher_is_better": True, "dtype": "c64 iterates + c128 replacements" if cplx else
+        "f32 iterates + f64 replacements", "data": "synthetic",
+        "config": {"workload": f"{args.workload}_offline", "n": n, "snapshots": B, "tol": args.tol,
+                   "preconditioner": "diagonal (Jacobi)", "method": "COCG" if cplx else "CG"},
+        "krylov": forms,
+        "roofline": {"bound": "hbm", "achieved": chosen["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                     "frac": chosen["hbm_frac"], "peak_kind": hbm_kind,
+                     "note": "whole mixed solve, host wall clock, launch gaps and replacements included"},
+        "tsqr": {"seconds": round(t_q, 4), "flops": tsqr_flops,
+                 "fp64_tflops": round(tsqr_flops / t_q / 1e12, 4),
+                 "fp64_pipe_frac": round(tsqr_flops / t_q / FP64_PEAK, 4),
+                 "orthonormality_fro": orth, "R_diag_min_over_max": float(np.abs(np.diag(R)).min() /
+                                                                          np.abs(np.diag(R)).max())},
+        "clocks": clocks,
+    }
+    if "plain" in forms:
+        out["plain_fp64"] = {"value": round(B / (forms["plain"]["seconds"] + t_q), 3), "unit": "snapshots/s"}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -818,8 +902,14 @@ def main():
                     choices=["diffusion_2d", "transfer_function", "reaction_diffusion_1d", "kernel_ridge",
                              "surrogate_diffusion_2d", "delay_system"])
     ap.add_argument("--epochs", type=int, default=100, help="surrogate training epochs")
+    ap.add_argument("--offline", action="store_true",
+                    help="time the offline stage (snapshot solves + TSQR) of the workload instead")
+    ap.add_argument("--tol", type=float, default=1e-10, help="offline: relative residual of the solves")
+    ap.add_argument("--maxit", type=int, default=50000, help="offline: iteration limit per snapshot")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.offline:
+        run_offline(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "surrogate_diffusion_2d":
         run_gpu_surrogate(args)

@@ -262,21 +262,35 @@ sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
 
 /* ---------------------------------------------------------------- offline stage */
 
+/* Flags of subapsnap_krylov_affine. */
+enum { SAS_KRYLOV_WARM = 1,  /* X holds start vectors (else zero start) */
+       SAS_KRYLOV_MIXED = 2  /* float32 iterates, float64 residual replacements */ };
+
 /* Snapshot solves A(p_j) x_j = b, j = 0..B-1, all at once (Alg. 1 step 1,
  * "fully or approximately"): conjugate gradients in the bilinear form x^T y
  * (COCG; plain CG for real data) with the diagonal of A(p_j) as
  * preconditioner.  A(p) must be symmetric (A^T = A; complex symmetric for the
  * pencil and delay rules) with a non-zero diagonal; the method converges for
  * positive definite A(p) and in practice for the complex symmetric families
- * here.  The same call refines given start vectors (warm != 0), e.g. the
- * SubApSnap output x_hat as the initial guess of Sec. 3.2.
+ * here.  The same call refines given start vectors (SAS_KRYLOV_WARM), e.g.
+ * the SubApSnap output x_hat as the initial guess of Sec. 3.2.  Convergence
+ * is only ever declared on the true residual b - A x computed in float64:
+ * when the iterated residual reaches tol it is replaced by the true one and
+ * the iteration goes on if that is still above tol; a column stops (as not
+ * converged) once four replacements in a row fail to halve the true
+ * residual, i.e. when tol lies below the attainable accuracy.  With SAS_KRYLOV_MIXED
+ * the iterates, directions and matrix values are float32 and the float64
+ * solution takes their corrections, the residual being replaced by the true
+ * float64 one whenever the float32 residual has fallen 10x since the last
+ * replacement (not in the paper; needs kappa(A) well below 1e7).
  *  desc:    the family (n, K, dtype, theta_rule, CSR blocks, b); r, s, S, J,
  *           mode, qoi and w are ignored.
- *  params:  host, B x dp.
- *  X:       device, n x B column-major (column j = x_j, ld n); on entry the
- *           start vectors if warm != 0 (ignored otherwise: zero start).
- *  tol:     column j stops once its updated residual ||b - A x_j|| / ||b||
- *           <= tol; maxit bounds its iterations.
+ *  params:  host, B x dp, 1 <= B <= 256.
+ *  X:       device, n x B column-major (column j = x_j, ld n), float64 or
+ *           complex128; on entry the start vectors with SAS_KRYLOV_WARM.
+ *  flags:   SAS_KRYLOV_* bits.
+ *  tol:     column j stops once ||b - A x_j|| / ||b|| <= tol; maxit bounds
+ *           its iterations.
  *  iters_out:  host, B ints or NULL: iterations per column.
  *  relres_out: host, B doubles or NULL: the true ||b - A x_j|| / ||b|| of
  *           the returned x_j, recomputed at the end.
@@ -284,7 +298,7 @@ sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
  * diagonal, b = 0), SAS_ENOMEM, SAS_ECUDA, SAS_ENOCONV (a column stopped at
  * maxit or broke down; X holds the last iterates). */
 sas_status subapsnap_krylov_affine(const sas_affine_desc* desc, const double* params, int32_t B,
-                                   void* X, int32_t warm, double tol, int32_t maxit,
+                                   void* X, int32_t flags, double tol, int32_t maxit,
                                    int32_t* iters_out, double* relres_out);
 
 /* Thin QR X = Q R of a tall n x r matrix on the device by TSQR (Alg. 1 step

@@ -44,6 +44,7 @@ SAS_KERNEL_SURROGATE = 4
 SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL, SAS_OPT_LS_VARIANT = 0, 1, 2, 3
 SAS_OPT_ASSEMBLY_KERNEL, SAS_OPT_ASSEMBLY_SEGMENT, SAS_OPT_RECON_STORE = 4, 5, 6
 SAS_MAX_VARIANTS = 32
+SAS_KRYLOV_WARM, SAS_KRYLOV_MIXED = 1, 2
 SAS_NOALLOC_MAX_Y = 65536
 SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL, SAS_KERNEL_ASSEMBLE = 0, 1, 2, 3
 
@@ -318,15 +319,16 @@ def subapsnap_nearest_points(params, points) -> np.ndarray:
 
 
 def subapsnap_krylov_affine(desc: AffineDesc, params, X, warm: bool = False, tol: float = 1e-12,
-                            maxit: int = 20000, allow_noconv: bool = False):
+                            maxit: int = 20000, allow_noconv: bool = False, mixed: bool = False):
     """Batched snapshot solves A(p_j) x_j = b.  X: CUDA tensor (B, n), row j = x_j
     (the column-major n x B matrix).  Returns (iterations, true relative residuals)."""
+    flags = (SAS_KRYLOV_WARM if warm else 0) | (SAS_KRYLOV_MIXED if mixed else 0)
     P = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64)))
     B = int(X.shape[0])
     it = np.zeros(B, dtype=np.int32)
     rel = np.zeros(B, dtype=np.float64)
     code = lib().subapsnap_krylov_affine(ctypes.byref(desc), P.ctypes.data_as(ctypes.c_void_p), B, _ptr(X),
-                                         1 if warm else 0, float(tol), int(maxit),
+                                         flags, float(tol), int(maxit),
                                          it.ctypes.data_as(ctypes.c_void_p), rel.ctypes.data_as(ctypes.c_void_p))
     if not (allow_noconv and code == SAS_ENOCONV):
         _check(code)

@@ -25,6 +25,7 @@
 #include <complex>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "sas_internal.cuh"
@@ -38,6 +39,7 @@ struct Ops {
   const int64_t* rp[SAS_MAX_TERMS];
   const int32_t* ci[SAS_MAX_TERMS];
   const double* va[SAS_MAX_TERMS];
+  const float* va32[SAS_MAX_TERMS];  // float copies of the values (mixed iterations)
 };
 
 __device__ inline double re_of(double v) { return v; }
@@ -47,10 +49,41 @@ template <typename T> __device__ inline T from_re(double v);
 template <> __device__ inline double from_re<double>(double v) { return v; }
 template <> __device__ inline zd from_re<zd>(double v) { return mkz(v, 0.0); }
 
+// conversions between the float64 scalar type T and the storage type of the iterates
+template <typename To> __device__ inline To cvt(double x);
+template <typename To> __device__ inline To cvt(float x);
+template <typename To> __device__ inline To cvt(zd x);
+template <typename To> __device__ inline To cvt(zf x);
+template <> __device__ inline double cvt<double>(double x) { return x; }
+template <> __device__ inline double cvt<double>(float x) { return (double)x; }
+template <> __device__ inline float cvt<float>(double x) { return (float)x; }
+template <> __device__ inline float cvt<float>(float x) { return x; }
+template <> __device__ inline zd cvt<zd>(zd x) { return x; }
+template <> __device__ inline zd cvt<zd>(zf x) { return to_hi(x); }
+template <> __device__ inline zf cvt<zf>(zd x) { return to_lo(x); }
+template <> __device__ inline zf cvt<zf>(zf x) { return x; }
+
+template <typename V> __device__ inline const V* vals(const Ops& o, int k);
+template <> __device__ inline const double* vals<double>(const Ops& o, int k) { return o.va[k]; }
+template <> __device__ inline const float* vals<float>(const Ops& o, int k) { return o.va32[k]; }
+
 // Block-wide sum of one value per thread (kThreads threads); result valid in thread 0.
 template <typename T>
 __device__ inline T block_sum(T v, T* red) {
   v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T s = zero<T>();
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kThreads / 32; ++k) s += red[k];
+  return s;
+}
+
+// Block-wide sum of per-warp values held by lane 0 of each warp; result valid in thread 0.
+template <typename T>
+__device__ inline T block_sum_warps(T v, T* red) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) red[w] = v;
@@ -73,10 +106,15 @@ __global__ void diag_kernel(Ops ops, int K, int64_t n, double* D) {
     }
 }
 
-// invD[b*n + i] = 1 / sum_k theta[b*K + k] D[k*n + i]; a zero diagonal sets *bad.
-template <typename T>
-__global__ void inv_diag_kernel(const double* D, int K, int64_t n, const T* theta, int B, T* invD,
-                                int* bad) {
+__global__ void to_float_kernel(const double* a, int64_t count, float* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)a[i];
+}
+
+// invD[b*n + i] = 1 / sum_k theta[b*K + k] D[k*n + i] (stored as TL); a zero diagonal sets *bad.
+template <typename T, typename TL>
+__global__ void inv_diag_kernel(const double* D, int K, int64_t n, const T* theta, TL* invD, int* bad) {
   const int b = blockIdx.y;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -84,9 +122,9 @@ __global__ void inv_diag_kernel(const double* D, int K, int64_t n, const T* thet
     for (int k = 0; k < K; ++k) d += rscale(D[k * n + i], theta[b * K + k]);
     if (absq(d) == 0.0 || !finitev(d)) {
       atomicExch(bad, 1);
-      invD[b * n + i] = zero<T>();
+      invD[b * n + i] = zero<TL>();
     } else {
-      invD[b * n + i] = divv(from_re<T>(1.0), d);
+      invD[b * n + i] = cvt<TL>(divv(from_re<T>(1.0), d));
     }
   }
 }
@@ -94,77 +132,172 @@ __global__ void inv_diag_kernel(const double* D, int K, int64_t n, const T* thet
 // Per-column state of the batched COCG.
 template <typename T>
 struct Col {
-  T rz;          // r^T D^{-1} r of the current residual
+  T rz;           // r^T D^{-1} r of the current residual
   T alpha, beta;
-  double rr;     // ||r||^2
-  double relres; // ||r|| / ||b|| (recursively updated residual)
-  int active;    // 1 while iterating
+  double relres;  // ||r|| / ||b|| of the iterated residual
+  double rmax;    // relres at the last replacement by the true residual
+  int active;     // 1 while iterating
   int iters;
-  int status;    // 0 running, 1 converged, 2 breakdown, 3 iteration limit
-  int pad;
+  int status;     // 0 running, 1 converged, 2 breakdown, 3 iteration limit, 4 stagnation
+  int upd;        // 1: replace the residual by the true one in this iteration
+  int nrel;       // replacements so far
+  int nstag;      // consecutive replacements that did not halve the true residual
 };
 
-// Y[:, b] = A(theta_b) X[:, b]; part[b*G + g] = sum_i X_ib Y_ib over the CTA's rows.
-// Columns whose state is inactive are skipped (st == nullptr: every column).
-template <typename T>
-__global__ void __launch_bounds__(kThreads) spmv_kernel(Ops ops, int K, int64_t n, const T* theta,
-                                                        const T* X, T* Y, const Col<T>* st,
-                                                        T* part, int64_t rows_per_cta) {
-  __shared__ T red[kThreads / 32];
-  const int b = blockIdx.x, G = gridDim.y;
-  if (st && !st[b].active) return;
-  T th[SAS_MAX_TERMS];
-  for (int k = 0; k < K; ++k) th[k] = theta[b * K + k];
-  const T* x = X + (int64_t)b * n;
-  T* y = Y + (int64_t)b * n;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
-  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
-  T dot = zero<T>();
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
-    T acc = zero<T>();
-    for (int k = 0; k < K; ++k) {
-      T s = zero<T>();
-      const int64_t e1 = ops.rp[k][i + 1];
-      for (int64_t e = ops.rp[k][i]; e < e1; ++e) s += rscale(ops.va[k][e], x[ops.ci[k][e]]);
-      acc += th[k] * s;
-    }
-    y[i] = acc;
-    dot += x[i] * acc;
-  }
-  if (part) {
-    dot = block_sum(dot, red);
-    if (threadIdx.x == 0) part[(int64_t)b * G + blockIdx.y] = dot;
-  }
-}
+// Column selection of the tile kernel.
+enum { kSelAll = 0, kSelActive = 1, kSelUpd = 2 };
 
-// Start: R = b - AX (AX == nullptr: X = 0, R = b); P = D^{-1} R; partials of r^T D^{-1} r and ||r||^2.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) start_kernel(const T* bvec, const T* AX, int64_t n,
-                                                         const T* invD, T* X, T* R, T* P, T* prz,
-                                                         double* prr, int64_t rows_per_cta) {
-  __shared__ T red[kThreads / 32];
-  __shared__ double redd[kThreads / 32];
-  const int b = blockIdx.x, G = gridDim.y;
-  const int64_t off = (int64_t)b * n;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
-  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
-  T rz = zero<T>();
-  double rr = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
-    T r = bvec[i];
-    if (AX) r -= AX[off + i];
-    else X[off + i] = zero<T>();
-    const T z = invD[off + i] * r;
-    R[off + i] = r;
-    P[off + i] = z;
-    rz += r * z;
-    rr += absq(r);
-  }
-  rz = block_sum(rz, red);
-  rr = block_sum(rr, redd);
+// For every selected column b, one CTA per tile of kTileRows rows:
+//  MODE 0 (product):  Y = A(theta_b) X;            part0 = sum X_ib Y_ib
+//  MODE 1 (residual): Y = b - A(theta_b) X;        part0 = sum Y_ib D^-1_ib Y_ib, part1 = sum |Y_ib|^2
+// X has storage type TX, Y type TL, the arithmetic and the partials are in
+// the type of X (float64 when X is), the matrix values have type V.  The
+// tile's CSR segments (contiguous in every block) are staged in shared memory
+// once and reused for all columns, so the matrix leaves HBM once per product
+// of the whole batch; two halves of the CTA take alternate columns.  Partials
+// are summed in a fixed order.  Dynamic shared memory: B * 8 values of T and
+// B ints.
+constexpr int kTileRows = 128;
+constexpr int kStage = 4096;
+constexpr int kCB = 4;  // columns per pass of a half CTA
+
+template <typename T, typename TX, typename TL, typename V, int MODE>
+__global__ void __launch_bounds__(kThreads) tile_kernel(Ops ops, int K, int64_t n, int B, const TX* theta,
+                                                        const TX* X, TL* Y, const T* bvec, const TL* invD,
+                                                        const Col<T>* st, int sel, T* part0, double* part1) {
+  __shared__ int32_t ci_s[kStage];
+  __shared__ V va_s[kStage];
+  __shared__ int rps[SAS_MAX_TERMS][kTileRows + 1];  // staged row starts per block
+  __shared__ int seg_off[SAS_MAX_TERMS];
+  __shared__ int64_t seg_base[SAS_MAX_TERMS];
+  __shared__ int s_staged, s_na;
+  __shared__ int alist[256];  // the selected columns, in order
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* wpart = reinterpret_cast<T*>(dyn);
+  double* wpart1 = reinterpret_cast<double*>(wpart + (size_t)B * 4);
+  int* act = reinterpret_cast<int*>(wpart1 + (size_t)B * 4);
+  const int G = gridDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+  const int64_t r1 = r0 + kTileRows < n ? r0 + kTileRows : n;
+  const int rows = (int)(r1 - r0);
+  for (int b = threadIdx.x; b < B; b += kThreads)
+    act[b] = sel == kSelAll ? 1 : sel == kSelActive ? st[b].active : st[b].upd;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    prz[(int64_t)b * G + blockIdx.y] = rz;
-    prr[(int64_t)b * G + blockIdx.y] = rr;
+    int m = 0;
+    for (int b = 0; b < B; ++b)
+      if (act[b]) alist[m++] = b;
+    s_na = m;
+    int64_t total = 0;
+    for (int k = 0; k < K && m > 0; ++k) {
+      seg_base[k] = ops.rp[k][r0];
+      seg_off[k] = (int)(total < kStage ? total : kStage);
+      total += ops.rp[k][r1] - seg_base[k];
+    }
+    s_staged = total <= kStage;
+  }
+  __syncthreads();
+  if (s_na == 0) return;  // no selected column (the same for the whole CTA)
+  const bool staged = s_staged;
+  if (staged)
+    for (int k = 0; k < K; ++k) {
+      const int64_t base = seg_base[k];
+      const int cnt = (int)(ops.rp[k][r1] - base);
+      const V* va = vals<V>(ops, k);
+      for (int e = threadIdx.x; e < cnt; e += kThreads) {
+        ci_s[seg_off[k] + e] = ops.ci[k][base + e];
+        va_s[seg_off[k] + e] = va[base + e];
+      }
+      for (int j = threadIdx.x; j <= rows; j += kThreads)
+        rps[k][j] = (int)(ops.rp[k][r0 + j] - base) + seg_off[k];
+    }
+  const int half = threadIdx.x >> 7, t = threadIdx.x & 127;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = r0 + t;
+  const bool valid = t < rows;
+  __syncthreads();
+  // each half takes kCB of the selected columns at a time: kCB independent gathers per
+  // stored entry; a short last group repeats its last column and discards the copies
+  const int na = s_na;
+  for (int g0 = half * kCB; g0 < na; g0 += 2 * kCB) {
+    const int nj = na - g0 < kCB ? na - g0 : kCB;
+    const TX* xp[kCB];
+    int bj[kCB];
+#pragma unroll
+    for (int j = 0; j < kCB; ++j) {
+      bj[j] = alist[g0 + (j < nj ? j : nj - 1)];
+      xp[j] = X + (int64_t)bj[j] * n;
+    }
+    TX acc[kCB];
+#pragma unroll
+    for (int j = 0; j < kCB; ++j) acc[j] = zero<TX>();
+    if (valid) {
+#pragma unroll 1
+      for (int k = 0; k < K; ++k) {
+        TX sum[kCB];
+#pragma unroll
+        for (int j = 0; j < kCB; ++j) sum[j] = zero<TX>();
+        if (staged) {
+          const int e1 = rps[k][t + 1];
+#pragma unroll 2
+          for (int e = rps[k][t]; e < e1; ++e) {
+            const V v = va_s[e];
+            const int c = ci_s[e];
+#pragma unroll
+            for (int j = 0; j < kCB; ++j) sum[j] += rscale(v, xp[j][c]);
+          }
+        } else {
+          const V* va = vals<V>(ops, k);
+          const int64_t e1 = ops.rp[k][i + 1];
+          for (int64_t e = ops.rp[k][i]; e < e1; ++e) {
+            const V v = va[e];
+            const int c = ops.ci[k][e];
+#pragma unroll
+            for (int j = 0; j < kCB; ++j) sum[j] += rscale(v, xp[j][c]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < kCB; ++j) acc[j] += theta[(int64_t)bj[j] * K + k] * sum[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kCB; ++j) {
+      if (j >= nj) break;  // uniform
+      const int b = bj[j];
+      if (MODE == 0) {
+        // the product's dot is summed over the warp in the arithmetic of X (float32 in the
+        // mixed form: the float64 pipe is 64x narrower), then widened once
+        TX dx = zero<TX>();
+        if (valid) {
+          Y[(int64_t)b * n + i] = cvt<TL>(acc[j]);
+          dx = xp[j][i] * acc[j];
+        }
+        dx = warp_sum(dx);
+        if (lane == 0) wpart[b * 4 + (warp & 3)] = cvt<T>(dx);
+      } else {
+        T d0 = zero<T>();
+        double d1 = 0.0;
+        if (valid) {
+          const T r = bvec[i] - cvt<T>(acc[j]);
+          Y[(int64_t)b * n + i] = cvt<TL>(r);
+          d0 = r * (cvt<T>(invD[(int64_t)b * n + i]) * r);
+          d1 = absq(r);
+        }
+        d0 = warp_sum(d0);
+        d1 = warp_sum(d1);
+        if (lane == 0) {
+          wpart[b * 4 + (warp & 3)] = d0;
+          wpart1[b * 4 + (warp & 3)] = d1;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += kThreads) {
+    if (!act[b]) continue;
+    if (part0) part0[(int64_t)b * G + blockIdx.x] = ((wpart[b * 4] + wpart[b * 4 + 1]) + wpart[b * 4 + 2]) + wpart[b * 4 + 3];
+    if (MODE == 1 && part1)
+      part1[(int64_t)b * G + blockIdx.x] = ((wpart1[b * 4] + wpart1[b * 4 + 1]) + wpart1[b * 4 + 2]) + wpart1[b * 4 + 3];
   }
 }
 
@@ -176,37 +309,57 @@ __device__ inline T column_sum(const T* part, int b, int G, T* red) {
   return block_sum(s, red);
 }
 
+// The start and every replacement of the residual by the true one: the column
+// takes rz and relres of the residual the tile kernel (MODE 1) just wrote.
+// start != 0: every column, iteration count and beta reset; otherwise the
+// columns flagged for replacement, which then get beta from the new rz.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) start_reduce_kernel(const T* prz, const double* prr, int G,
-                                                                double bnorm, double tol, int maxit,
-                                                                Col<T>* st) {
+__global__ void __launch_bounds__(kThreads) replace_kernel(const T* prz, const double* prr, int G, double bnorm,
+                                                           double tol, int maxit, int start, Col<T>* st) {
   __shared__ T red[kThreads / 32];
   __shared__ double redd[kThreads / 32];
   const int b = blockIdx.x;
+  if (!start && !st[b].upd) return;
   const T rz = column_sum(prz, b, G, red);
   const double rr = column_sum(prr, b, G, redd);
   if (threadIdx.x == 0) {
-    Col<T> c;
-    c.rz = rz;
-    c.alpha = zero<T>();
-    c.beta = zero<T>();
-    c.rr = rr;
+    Col<T> c = st[b];
+    const double prev = c.rmax;
+    c.upd = 0;
     c.relres = sqrt(rr) / bnorm;
-    c.iters = 0;
-    c.pad = 0;
-    if (!(c.relres == c.relres)) {
+    c.rmax = c.relres;
+    if (start) {
+      c.alpha = zero<T>();
+      c.iters = 0;
+      c.nrel = 0;
+      c.nstag = 0;
+      c.status = 0;
+      c.active = 1;
+    } else {
+      c.nrel += 1;
+      c.nstag = c.relres > 0.5 * prev ? c.nstag + 1 : 0;
+    }
+    if (!(c.relres == c.relres) || !finitev(rz)) {
       c.status = 2;
       c.active = 0;
     } else if (c.relres <= tol) {
       c.status = 1;
       c.active = 0;
-    } else if (maxit <= 0) {
+    } else if (c.nstag >= 4) {  // the true residual stopped falling: attainable accuracy reached
+      c.status = 4;
+      c.active = 0;
+    } else if (c.iters >= maxit) {
       c.status = 3;
       c.active = 0;
+    } else if (start) {
+      c.beta = zero<T>();
+    } else if (absq(c.rz) == 0.0) {
+      c.status = 2;
+      c.active = 0;
     } else {
-      c.status = 0;
-      c.active = 1;
+      c.beta = divv(rz, c.rz);
     }
+    c.rz = rz;
     st[b] = c;
   }
 }
@@ -227,39 +380,48 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const T* ppq, int G, Co
   }
 }
 
-// X += alpha P, R -= alpha Q; partials of the new r^T D^{-1} r and ||r||^2.
-template <typename T>
-__global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, T* X, T* R, const T* P, const T* Q,
-                                                          const T* invD, const Col<T>* st, T* prz,
+// X += alpha P, R -= alpha Q (storage TL, arithmetic TL); partials (in T) of the
+// new r^T D^{-1} r and ||r||^2.
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, TL* X, TL* R, const TL* P, const TL* Q,
+                                                          const TL* invD, const Col<T>* st, T* prz,
                                                           double* prr, int64_t rows_per_cta) {
   __shared__ T red[kThreads / 32];
   __shared__ double redd[kThreads / 32];
   const int b = blockIdx.x, G = gridDim.y;
   if (!st[b].active) return;
-  const T alpha = st[b].alpha;
+  const TL alpha = cvt<TL>(st[b].alpha);
   const int64_t off = (int64_t)b * n;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
   const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
-  T rz = zero<T>();
-  double rr = 0.0;
+  // per-thread sums in the storage type (a few dozen terms), combined in float64
+  TL rz_t = zero<TL>();
+  decltype(absq(rz_t)) rr_t = 0;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
     X[off + i] += alpha * P[off + i];
-    const T r = R[off + i] - alpha * Q[off + i];
+    const TL r = R[off + i] - alpha * Q[off + i];
     R[off + i] = r;
-    rz += r * (invD[off + i] * r);
-    rr += absq(r);
+    rz_t += r * (invD[off + i] * r);
+    rr_t += absq(r);
   }
-  rz = block_sum(rz, red);
-  rr = block_sum(rr, redd);
+  // warp sums in the storage arithmetic, widened once per warp
+  rz_t = warp_sum(rz_t);
+  rr_t = warp_sum(rr_t);
+  T rz = block_sum_warps(cvt<T>(rz_t), red);
+  double rr = block_sum_warps((double)rr_t, redd);
   if (threadIdx.x == 0) {
     prz[(int64_t)b * G + blockIdx.y] = rz;
     prr[(int64_t)b * G + blockIdx.y] = rr;
   }
 }
 
+// After the update: the iterated residual's norm.  A column whose residual
+// reached the tolerance, or (float32 iterates) fell below delta times the
+// residual at its last replacement, is flagged for replacement by the true
+// residual, which decides convergence and beta; the others take beta here.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) beta_kernel(const T* prz, const double* prr, int G,
-                                                        double bnorm, double tol, int maxit,
+                                                        double bnorm, double tol, double delta, int maxit,
                                                         Col<T>* st) {
   __shared__ T red[kThreads / 32];
   __shared__ double redd[kThreads / 32];
@@ -270,55 +432,50 @@ __global__ void __launch_bounds__(kThreads) beta_kernel(const T* prz, const doub
   if (threadIdx.x == 0) {
     Col<T> c = st[b];
     c.iters += 1;
-    c.rr = rr;
     c.relres = sqrt(rr) / bnorm;
     if (!(c.relres == c.relres) || !finitev(rz)) {
       c.status = 2;
       c.active = 0;
-    } else if (c.relres <= tol) {
-      c.status = 1;
-      c.active = 0;
-    } else if (c.iters >= maxit) {
-      c.status = 3;
-      c.active = 0;
+    } else if (c.relres <= tol || c.relres < delta * c.rmax || c.iters >= maxit) {
+      c.upd = 1;  // rz and beta come from the true residual
     } else if (absq(c.rz) == 0.0) {
       c.status = 2;
       c.active = 0;
     } else {
       c.beta = divv(rz, c.rz);
+      c.rz = rz;
     }
-    c.rz = rz;
     st[b] = c;
   }
 }
 
+// x (float64) += x_lo; x_lo = 0, for the columns flagged for replacement (all != 0: every column)
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) fold_kernel(int64_t n, T* X, TL* Xl, const Col<T>* st, int all,
+                                                        int64_t rows_per_cta) {
+  const int b = blockIdx.x;
+  if (!all && !st[b].upd) return;
+  const int64_t off = (int64_t)b * n;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    X[off + i] += cvt<T>(Xl[off + i]);
+    Xl[off + i] = zero<TL>();
+  }
+}
+
 // P = D^{-1} R + beta P
-template <typename T>
-__global__ void __launch_bounds__(kThreads) direction_kernel(int64_t n, const T* R, const T* invD, T* P,
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) direction_kernel(int64_t n, const TL* R, const TL* invD, TL* P,
                                                              const Col<T>* st, int64_t rows_per_cta) {
   const int b = blockIdx.x;
   if (!st[b].active) return;
-  const T beta = st[b].beta;
+  const TL beta = cvt<TL>(st[b].beta);
   const int64_t off = (int64_t)b * n;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
   const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads)
     P[off + i] = invD[off + i] * R[off + i] + beta * P[off + i];
-}
-
-// partial ||b - AX||^2 of every column (the true residual at the end)
-template <typename T>
-__global__ void __launch_bounds__(kThreads) true_res_kernel(const T* bvec, const T* AX, int64_t n,
-                                                            double* prr, int64_t rows_per_cta) {
-  __shared__ double redd[kThreads / 32];
-  const int b = blockIdx.x, G = gridDim.y;
-  const int64_t off = (int64_t)b * n;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
-  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
-  double rr = 0.0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) rr += absq(bvec[i] - AX[off + i]);
-  rr = block_sum(rr, redd);
-  if (threadIdx.x == 0) prr[(int64_t)b * G + blockIdx.y] = rr;
 }
 
 __global__ void __launch_bounds__(kThreads) norm_partial_kernel(const double* x, int64_t count, double* out) {
@@ -546,24 +703,29 @@ struct DevBuf {
   template <typename U> U* as() const { return reinterpret_cast<U*>(p); }
 };
 
-template <typename T>
-sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T* X, int warm,
-                    double tol, int32_t maxit, int32_t* iters_out, double* relres_out) {
+template <typename T, typename TL>
+sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T* X, bool warm,
+                    bool mixed, double tol, int32_t maxit, int32_t* iters_out, double* relres_out) {
   const int64_t n = d->n;
   const int K = d->K;
   const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->theta_rule == SAS_THETA_DELAY ? 2 : K - 1;
   const int sms = num_sms();
-  // rows per CTA: about 16 CTAs per SM over the whole batch, multiples of the block size
+  // vector kernels: about 16 CTAs per SM over the whole batch, rows per CTA a multiple of the block
   int64_t rpc = (n * (int64_t)B + (int64_t)sms * 16 - 1) / ((int64_t)sms * 16);
   rpc = std::max<int64_t>(kThreads, (rpc + kThreads - 1) / kThreads * kThreads);
   const int G = (int)((n + rpc - 1) / rpc);
   const dim3 grid(B, G);
+  const int Gt = (int)((n + off::kTileRows - 1) / off::kTileRows);  // tiles of the product kernel
+  const int Gp = std::max(G, Gt);
+  const size_t tile_smem = (size_t)B * 4 * sizeof(T) + (size_t)B * 4 * sizeof(double) + (size_t)B * sizeof(int);
+  const double delta = mixed ? 0.1 : 0.0;  // replacement once the float32 residual fell 10x
 
   off::Ops ops;
   for (int k = 0; k < K; ++k) {
     ops.rp[k] = d->rowptr[k];
     ops.ci[k] = d->colind[k];
     ops.va[k] = d->values[k];
+    ops.va32[k] = nullptr;
   }
   std::vector<T> th_h((size_t)B * K);
   std::vector<std::complex<double>> th;
@@ -577,21 +739,36 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
       }
     }
   }
-  DevBuf theta, D, invD, R, P, Q, prz, ppq, prr, st, bad, nb;
-  const size_t vec = (size_t)n * B * sizeof(T);
+  std::vector<TL> thl_h(th_h.size());
+  for (size_t q = 0; q < th_h.size(); ++q) {
+    if constexpr (sizeof(TL) == sizeof(T)) thl_h[q] = th_h[q];
+    else if constexpr (sizeof(T) == 16) thl_h[q] = mkzf((float)th_h[q].re, (float)th_h[q].im);
+    else thl_h[q] = (float)th_h[q];
+  }
+  DevBuf theta, theta_lo, D, invD, R, P, Q, Xl, prz, ppq, prr, st, bad, nb;
+  DevBuf va32[SAS_MAX_TERMS];
+  const size_t vec = (size_t)n * B * sizeof(TL);
   cudaError_t e = theta.alloc(th_h.size() * sizeof(T));
+  if (e == cudaSuccess) e = theta_lo.alloc(thl_h.size() * sizeof(TL));
   if (e == cudaSuccess) e = D.alloc((size_t)K * n * sizeof(double));
   if (e == cudaSuccess) e = invD.alloc(vec);
   if (e == cudaSuccess) e = R.alloc(vec);
   if (e == cudaSuccess) e = P.alloc(vec);
   if (e == cudaSuccess) e = Q.alloc(vec);
-  if (e == cudaSuccess) e = prz.alloc((size_t)B * G * sizeof(T));
-  if (e == cudaSuccess) e = ppq.alloc((size_t)B * G * sizeof(T));
-  if (e == cudaSuccess) e = prr.alloc((size_t)B * G * sizeof(double));
+  if (e == cudaSuccess && mixed) e = Xl.alloc(vec);
+  if (e == cudaSuccess) e = prz.alloc((size_t)B * Gp * sizeof(T));
+  if (e == cudaSuccess) e = ppq.alloc((size_t)B * Gt * sizeof(T));
+  if (e == cudaSuccess) e = prr.alloc((size_t)B * Gp * sizeof(double));
   if (e == cudaSuccess) e = st.alloc((size_t)B * sizeof(Col<T>));
   if (e == cudaSuccess) e = bad.alloc(sizeof(int));
   if (e == cudaSuccess) e = nb.alloc((size_t)sms * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(e, "krylov: allocation");
+  using V = typename std::conditional<sizeof(TL) == sizeof(T), double, float>::type;
+  auto* k_lo = off::tile_kernel<T, TL, TL, V, 0>;
+  auto* k_res = off::tile_kernel<T, T, TL, double, 1>;
+  e = cudaFuncSetAttribute(k_lo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: shared memory");
   cudaStream_t s = nullptr;
   e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: stream");
@@ -599,19 +776,35 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
     cudaStream_t s;
     ~StreamGuard() { cudaStreamDestroy(s); }
   } guard{s};
+  if (mixed)
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+      int64_t nnz = 0;
+      e = cudaMemcpy(&nnz, d->rowptr[k] + n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = va32[k].alloc((size_t)std::max<int64_t>(nnz, 1) * sizeof(float));
+      if (e == cudaSuccess) {
+        off::to_float_kernel<<<sms * 4, kThreads, 0, s>>>(d->values[k], nnz, va32[k].as<float>());
+        ops.va32[k] = va32[k].as<float>();
+      }
+    }
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: float copies of the blocks");
+  TL* Xit = mixed ? Xl.as<TL>() : reinterpret_cast<TL*>(X);  // where the iteration accumulates x
   e = cudaMemcpyAsync(theta.p, th_h.data(), th_h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(theta_lo.p, thl_h.data(), thl_h.size() * sizeof(TL), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, sizeof(int), s);
+  if (e == cudaSuccess && !warm) e = cudaMemsetAsync(X, 0, (size_t)n * B * sizeof(T), s);
+  if (e == cudaSuccess && mixed) e = cudaMemsetAsync(Xl.p, 0, vec, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.p, 0, vec, s);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: setup copies");
   off::diag_kernel<<<sms * 4, kThreads, 0, s>>>(ops, K, n, D.as<double>());
-  off::inv_diag_kernel<T><<<dim3(sms * 2, B), kThreads, 0, s>>>(D.as<double>(), K, n, theta.as<T>(), B,
-                                                                invD.as<T>(), bad.as<int>());
+  off::inv_diag_kernel<T, TL><<<dim3(sms * 2, B), kThreads, 0, s>>>(D.as<double>(), K, n, theta.as<T>(),
+                                                                    invD.as<TL>(), bad.as<int>());
   // ||b|| (b viewed as 2n doubles when complex)
   const int64_t bcount = n * (int64_t)(sizeof(T) / sizeof(double));
   off::norm_partial_kernel<<<sms, kThreads, 0, s>>>((const double*)d->b, bcount, nb.as<double>());
-  if (warm)
-    off::spmv_kernel<T><<<grid, kThreads, 0, s>>>(ops, K, n, theta.as<T>(), X, Q.as<T>(), nullptr, nullptr, rpc);
-  off::start_kernel<T><<<grid, kThreads, 0, s>>>((const T*)d->b, warm ? Q.as<T>() : nullptr, n, invD.as<T>(), X,
-                                                 R.as<T>(), P.as<T>(), prz.as<T>(), prr.as<double>(), rpc);
+  // r = b - A x for every column
+  k_res<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta.as<T>(), X, R.as<TL>(), (const T*)d->b,
+                                        invD.as<TL>(), st.as<Col<T>>(), off::kSelAll, prz.as<T>(), prr.as<double>());
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "krylov: start launches");
   int bad_h = 0;
@@ -626,10 +819,12 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   for (double v : nb_h) bn2 += v;
   const double bnorm = std::sqrt(bn2);
   if (!(bnorm > 0.0)) return fail_off(SAS_EINVAL, "krylov: b = 0");
-  off::start_reduce_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, maxit,
-                                                     st.as<Col<T>>());
+  off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 1,
+                                                st.as<Col<T>>());
+  off::direction_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
+                                                         st.as<Col<T>>(), rpc);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "krylov: start reduce");
+  if (e != cudaSuccess) return cuda_fail(e, "krylov: first direction");
 
   // the iteration, captured once as a graph of `chunk` steps and replayed
   const int chunk = 16;
@@ -638,14 +833,23 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: capture");
   for (int it = 0; it < chunk; ++it) {
-    off::spmv_kernel<T><<<grid, kThreads, 0, s>>>(ops, K, n, theta.as<T>(), P.as<T>(), Q.as<T>(), st.as<Col<T>>(),
-                                                  ppq.as<T>(), rpc);
-    off::alpha_kernel<T><<<B, kThreads, 0, s>>>(ppq.as<T>(), G, st.as<Col<T>>());
-    off::update_kernel<T><<<grid, kThreads, 0, s>>>(n, X, R.as<T>(), P.as<T>(), Q.as<T>(), invD.as<T>(),
-                                                    st.as<Col<T>>(), prz.as<T>(), prr.as<double>(), rpc);
-    off::beta_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, maxit,
+    k_lo<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta_lo.as<TL>(), P.as<TL>(), Q.as<TL>(), nullptr, nullptr,
+                                         st.as<Col<T>>(), off::kSelActive, ppq.as<T>(), nullptr);
+    off::alpha_kernel<T><<<B, kThreads, 0, s>>>(ppq.as<T>(), Gt, st.as<Col<T>>());
+    off::update_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, Xit, R.as<TL>(), P.as<TL>(), Q.as<TL>(),
+                                                        invD.as<TL>(), st.as<Col<T>>(), prz.as<T>(),
+                                                        prr.as<double>(), rpc);
+    off::beta_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, delta, maxit,
                                                st.as<Col<T>>());
-    off::direction_kernel<T><<<grid, kThreads, 0, s>>>(n, R.as<T>(), invD.as<T>(), P.as<T>(), st.as<Col<T>>(), rpc);
+    if (mixed)
+      off::fold_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, X, Xl.as<TL>(), st.as<Col<T>>(), 0, rpc);
+    k_res<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta.as<T>(), X, R.as<TL>(), (const T*)d->b,
+                                          invD.as<TL>(), st.as<Col<T>>(), off::kSelUpd, prz.as<T>(),
+                                          prr.as<double>());
+    off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 0,
+                                                  st.as<Col<T>>());
+    off::direction_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
+                                                           st.as<Col<T>>(), rpc);
   }
   e = cudaStreamEndCapture(s, &graph);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -668,28 +872,32 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: iteration");
   e = cudaMemcpyAsync(st_h.data(), st.p, st_h.size() * sizeof(Col<T>), cudaMemcpyDeviceToHost, s);
-  // true residual of the final iterates
-  off::spmv_kernel<T><<<grid, kThreads, 0, s>>>(ops, K, n, theta.as<T>(), X, Q.as<T>(), nullptr, nullptr, rpc);
-  off::true_res_kernel<T><<<grid, kThreads, 0, s>>>((const T*)d->b, Q.as<T>(), n, prr.as<double>(), rpc);
-  std::vector<double> prr_h((size_t)B * G);
+  // columns that stopped on a breakdown may hold float32 corrections not yet folded
+  if (mixed) off::fold_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, X, Xl.as<TL>(), st.as<Col<T>>(), 1, rpc);
+  // true residual of the returned iterates
+  k_res<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta.as<T>(), X, Q.as<TL>(), (const T*)d->b,
+                                        invD.as<TL>(), st.as<Col<T>>(), off::kSelAll, nullptr, prr.as<double>());
+  std::vector<double> prr_h((size_t)B * Gt);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(prr_h.data(), prr.p, prr_h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: final residual");
-  int failed = 0, broke = 0;
+  int failed = 0, broke = 0, stalled = 0;
   for (int b = 0; b < B; ++b) {
     double rr = 0.0;
-    for (int g = 0; g < G; ++g) rr += prr_h[(size_t)b * G + g];
+    for (int g = 0; g < Gt; ++g) rr += prr_h[(size_t)b * Gt + g];
     if (iters_out) iters_out[b] = st_h[b].iters;
     if (relres_out) relres_out[b] = std::sqrt(rr) / bnorm;
     if (st_h[b].status != 1) ++failed;
     if (st_h[b].status == 2) ++broke;
+    if (st_h[b].status == 4) ++stalled;
   }
   if (failed)
     return fail_off(SAS_ENOCONV, "krylov: " + std::to_string(failed) + " of " + std::to_string(B) +
                                      " columns did not reach the tolerance (" + std::to_string(broke) +
-                                     " broke down); X holds the last iterates");
+                                     " broke down, " + std::to_string(stalled) +
+                                     " stagnated above it); X holds the last iterates");
   return SAS_OK;
 }
 
@@ -780,10 +988,11 @@ sas_status tsqr_t(const T* X, int64_t n, int r, int64_t ldx, T* Qout, int64_t ld
 using namespace sas;
 
 sas_status subapsnap_krylov_affine(const sas_affine_desc* d, const double* params, int32_t B, void* X,
-                                   int32_t warm, double tol, int32_t maxit, int32_t* iters_out,
+                                   int32_t flags, double tol, int32_t maxit, int32_t* iters_out,
                                    double* relres_out) {
+  const bool warm = (flags & SAS_KRYLOV_WARM) != 0, mixed = (flags & SAS_KRYLOV_MIXED) != 0;
   if (!d || !params || !X) return fail_off(SAS_EINVAL, "NULL argument");
-  if (B < 1) return fail_off(SAS_EINVAL, "need B >= 1");
+  if (B < 1 || B > 256) return fail_off(SAS_EINVAL, "need 1 <= B <= 256");
   if (d->n < 1) return fail_off(SAS_EINVAL, "need n >= 1");
   if (d->K < 1 || d->K > SAS_MAX_TERMS) return fail_off(SAS_EINVAL, "K must be in [1, 8]");
   if (d->dtype != SAS_REAL64 && d->dtype != SAS_COMPLEX128) return fail_off(SAS_EINVAL, "bad dtype");
@@ -799,9 +1008,12 @@ sas_status subapsnap_krylov_affine(const sas_affine_desc* d, const double* param
   for (int k = 0; k < d->K; ++k)
     if (!on_device(d->rowptr[k]) || !on_device(d->colind[k]) || !on_device(d->values[k]))
       return fail_off(SAS_EINVAL, "CSR arrays must be device pointers");
+  if (flags & ~(SAS_KRYLOV_WARM | SAS_KRYLOV_MIXED)) return fail_off(SAS_EINVAL, "unknown flag bits");
   if (d->dtype == SAS_COMPLEX128)
-    return krylov_t<zd>(d, params, B, (zd*)X, warm, tol, maxit, iters_out, relres_out);
-  return krylov_t<double>(d, params, B, (double*)X, warm, tol, maxit, iters_out, relres_out);
+    return mixed ? krylov_t<zd, zf>(d, params, B, (zd*)X, warm, true, tol, maxit, iters_out, relres_out)
+                 : krylov_t<zd, zd>(d, params, B, (zd*)X, warm, false, tol, maxit, iters_out, relres_out);
+  return mixed ? krylov_t<double, float>(d, params, B, (double*)X, warm, true, tol, maxit, iters_out, relres_out)
+               : krylov_t<double, double>(d, params, B, (double*)X, warm, false, tol, maxit, iters_out, relres_out);
 }
 
 sas_status subapsnap_tsqr(const void* X, int64_t n, int32_t r, int64_t ldx, int32_t dtype, void* Q,

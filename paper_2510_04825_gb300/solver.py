@@ -93,7 +93,7 @@ class AffineSolver:
 
 
 def snapshot_solve(prob, params, X, blocks_device=None, b_device=None, warm=False, tol=1e-12,
-                   maxit=20000, device="cuda", allow_noconv=False):
+                   maxit=20000, device="cuda", allow_noconv=False, mixed=False):
     """Batched Krylov solves A(p_j) x_j = b on the device into X (B, n); (iterations, true residuals)."""
     cplx = bool(prob.complex_valued)
     blocks = blocks_device or [csr_to_device(A, device) for A in prob.blocks]
@@ -105,11 +105,11 @@ def snapshot_solve(prob, params, X, blocks_device=None, b_device=None, warm=Fals
                             theta_rule_code(prob.theta_rule), api.SAS_MODE_PLAIN, api.SAS_QOI_NONE,
                             None, cplx)
     return api.subapsnap_krylov_affine(desc, P, X, warm=warm, tol=tol, maxit=maxit,
-                                       allow_noconv=allow_noconv)
+                                       allow_noconv=allow_noconv, mixed=mixed)
 
 
 def snapshot_basis(prob, blocks_device=None, b_device=None, params=None, tol=1e-12, maxit=20000,
-                   device="cuda"):
+                   device="cuda", mixed=False):
     """Offline stage on the device (Alg. 1 steps 1-2): snapshot solves, then TSQR.
 
     Returns (S, info): S is the (r, n) device tensor of the orthonormal basis
@@ -119,7 +119,8 @@ def snapshot_basis(prob, blocks_device=None, b_device=None, params=None, tol=1e-
     P = prob.snap_params if params is None else params
     P = np.atleast_2d(np.asarray(P, dtype=np.float64))
     X = torch.empty((P.shape[0], prob.n), dtype=torch.complex128 if cplx else torch.float64, device=device)
-    it, rel = snapshot_solve(prob, P, X, blocks_device, b_device, tol=tol, maxit=maxit, device=device)
+    it, rel = snapshot_solve(prob, P, X, blocks_device, b_device, tol=tol, maxit=maxit, device=device,
+                             mixed=mixed)
     R = api.subapsnap_tsqr(X)
     return X, {"iters": it, "relres": rel, "R": R}
 

@@ -39,28 +39,30 @@ def _tensor(a, cplx):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex128 if cplx else np.float64)).to(DEV)
 
 
+@pytest.mark.parametrize("mixed", [False, True], ids=["plain", "mixed"])
 @pytest.mark.parametrize("name,kw", SMALL, ids=[c[0] for c in SMALL])
-def test_snapshot_solves_match_direct_solves(name, kw):
+def test_snapshot_solves_match_direct_solves(name, kw, mixed):
     prob = get_config(name, **kw)
     cplx = prob.complex_valued
     P = prob.snap_params
     X = torch.empty((len(P), prob.n), dtype=torch.complex128 if cplx else torch.float64, device=DEV)
     tol = 1e-10
-    it, rel = snapshot_solve(prob, P, X, tol=tol, maxit=50000)
+    it, rel = snapshot_solve(prob, P, X, tol=tol, maxit=50000, mixed=mixed)
     Xg = X.cpu().numpy()
     worst_err = 0.0
     for j, p in enumerate(P):
         A = oproblem.full_matrix(prob, p)
         xo = snapshots.solve_full(prob, p)
         res = np.linalg.norm(A @ Xg[j] - prob.b) / np.linalg.norm(prob.b)
-        assert res <= 10 * tol and rel[j] <= 10 * tol, (j, res, rel[j])
+        # convergence is declared on the float64 true residual
+        assert rel[j] <= tol and res <= 2 * tol, (j, res, rel[j])
         err = np.linalg.norm(Xg[j] - xo) / np.linalg.norm(xo)
         worst_err = max(worst_err, err)
         # forward error <= kappa(A) * residual (kappa from a dense SVD at these sizes)
         if prob.n <= 2500:
             sv = np.linalg.svd(A.toarray(), compute_uv=False)
             assert err <= sv[0] / sv[-1] * 10 * tol, (j, err)
-    print(f"{name}: iterations {it.min()}..{it.max()}, max true residual {rel.max():.2e}, "
+    print(f"{name} {'mixed' if mixed else 'plain'}: iterations {it.min()}..{it.max()}, max true residual {rel.max():.2e}, "
           f"max error vs direct {worst_err:.2e}")
 
 
@@ -78,9 +80,13 @@ def test_warm_start_from_subapsnap_output():
     it_w, rel_w = snapshot_solve(prob, params, Xw, warm=True, tol=tol)
     Xc = torch.empty_like(Xw)
     it_c, rel_c = snapshot_solve(prob, params, Xc, warm=False, tol=tol)
-    assert (rel_w <= 10 * tol).all() and (rel_c <= 10 * tol).all()
+    assert (rel_w <= tol).all() and (rel_c <= tol).all()
+    Xm = _tensor(Xhat, False)
+    it_m, rel_m = snapshot_solve(prob, params, Xm, warm=True, tol=tol, mixed=True)
+    assert (rel_m <= tol).all()
     assert (it_w < it_c).all(), (it_w, it_c)
-    print(f"warm start: {it_w.mean():.0f} iterations against {it_c.mean():.0f} from zero")
+    print(f"warm start: {it_w.mean():.0f} iterations against {it_c.mean():.0f} from zero "
+          f"({it_m.mean():.0f} with float32 iterates)")
 
 
 def test_krylov_iteration_limit_and_bad_arguments():
@@ -141,8 +147,8 @@ def test_offline_then_online_pipeline():
     has the same quality as the oracle's pipeline (x_hat true residual)."""
     prob = get_config("diffusion_2d", N=48, r=30, s=60, m=40)
     blocks = [csr_to_device(A, DEV) for A in prob.blocks]
-    S, info = snapshot_basis(prob, blocks_device=blocks, tol=1e-12)
-    assert (info["relres"] <= 1e-11).all()
+    S, info = snapshot_basis(prob, blocks_device=blocks, tol=1e-12, mixed=True)
+    assert (info["relres"] <= 1e-12).all()
     J, _ = select_rows(prob, S, blocks, prob.sel_param, prob.s)
     So = snapshots.orthonormal_basis(snapshots.snapshot_matrix(prob))
     Vo = np.asarray(oproblem.full_matrix(prob, prob.sel_param) @ So)
