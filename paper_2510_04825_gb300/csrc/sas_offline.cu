@@ -112,7 +112,52 @@ __global__ void to_float_kernel(const double* a, int64_t count, float* out) {
     out[i] = (float)a[i];
 }
 
-// invD[b*n + i] = 1 / sum_k theta[b*K + k] D[k*n + i] (stored as TL); a zero diagonal sets *bad.
+// The iteration's vectors (x_lo, r, p, q, D^-1) are stored quad-interleaved:
+// columns 4g .. 4g+3 of row i sit together at ((g * n + i) * 4 + j), so that one
+// 16-byte load gathers a row of four columns (columns past B are zero padding).
+__host__ __device__ inline int64_t qidx(int64_t n, int b, int64_t i) { return (((int64_t)(b >> 2) * n + i) << 2) + (b & 3); }
+
+template <typename TL> struct Quad { TL v[4]; };
+template <typename TL> __device__ inline Quad<TL> ldq(const TL* p);
+template <typename TL> __device__ inline void stq(TL* p, const Quad<TL>& q);
+template <> __device__ inline Quad<float> ldq<float>(const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  return Quad<float>{{a.x, a.y, a.z, a.w}};
+}
+template <> __device__ inline void stq<float>(float* p, const Quad<float>& q) {
+  *reinterpret_cast<float4*>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+}
+template <> __device__ inline Quad<zf> ldq<zf>(const zf* p) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  return Quad<zf>{{mkzf(a.x, a.y), mkzf(a.z, a.w), mkzf(b.x, b.y), mkzf(b.z, b.w)}};
+}
+template <> __device__ inline void stq<zf>(zf* p, const Quad<zf>& q) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(q.v[0].re, q.v[0].im, q.v[1].re, q.v[1].im);
+  reinterpret_cast<float4*>(p)[1] = make_float4(q.v[2].re, q.v[2].im, q.v[3].re, q.v[3].im);
+}
+template <> __device__ inline Quad<double> ldq<double>(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return Quad<double>{{a.x, a.y, b.x, b.y}};
+}
+template <> __device__ inline void stq<double>(double* p, const Quad<double>& q) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(q.v[0], q.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(q.v[2], q.v[3]);
+}
+template <> __device__ inline Quad<zd> ldq<zd>(const zd* p) {
+  Quad<zd> q;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const double2 a = reinterpret_cast<const double2*>(p)[j];
+    q.v[j] = mkz(a.x, a.y);
+  }
+  return q;
+}
+template <> __device__ inline void stq<zd>(zd* p, const Quad<zd>& q) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) reinterpret_cast<double2*>(p)[j] = make_double2(q.v[j].re, q.v[j].im);
+}
+
+// invD (quad layout, TL) = 1 / sum_k theta[b*K + k] D[k*n + i]; a zero diagonal sets *bad.
 template <typename T, typename TL>
 __global__ void inv_diag_kernel(const double* D, int K, int64_t n, const T* theta, TL* invD, int* bad) {
   const int b = blockIdx.y;
@@ -122,9 +167,9 @@ __global__ void inv_diag_kernel(const double* D, int K, int64_t n, const T* thet
     for (int k = 0; k < K; ++k) d += rscale(D[k * n + i], theta[b * K + k]);
     if (absq(d) == 0.0 || !finitev(d)) {
       atomicExch(bad, 1);
-      invD[b * n + i] = zero<TL>();
+      invD[qidx(n, b, i)] = zero<TL>();
     } else {
-      invD[b * n + i] = cvt<TL>(divv(from_re<T>(1.0), d));
+      invD[qidx(n, b, i)] = cvt<TL>(divv(from_re<T>(1.0), d));
     }
   }
 }
@@ -144,113 +189,231 @@ struct Col {
   int nstag;      // consecutive replacements that did not halve the true residual
 };
 
-// Column selection of the tile kernel.
+// Column selection of the product kernels.
 enum { kSelAll = 0, kSelActive = 1, kSelUpd = 2 };
 
-// For every selected column b, one CTA per tile of kTileRows rows:
-//  MODE 0 (product):  Y = A(theta_b) X;            part0 = sum X_ib Y_ib
-//  MODE 1 (residual): Y = b - A(theta_b) X;        part0 = sum Y_ib D^-1_ib Y_ib, part1 = sum |Y_ib|^2
-// X has storage type TX, Y type TL, the arithmetic and the partials are in
-// the type of X (float64 when X is), the matrix values have type V.  The
-// tile's CSR segments (contiguous in every block) are staged in shared memory
-// once and reused for all columns, so the matrix leaves HBM once per product
-// of the whole batch; two halves of the CTA take alternate columns.  Partials
-// are summed in a fixed order.  Dynamic shared memory: B * 8 values of T and
-// B ints.
+// Both product kernels take one CTA per tile of kTileRows rows.  The tile's CSR
+// segments (contiguous in every block) are staged in shared memory once and
+// reused for every column, so the matrix leaves HBM once per product of the
+// whole batch; the two halves of the CTA take alternate column groups.  Dots
+// are summed per warp, then over the four warps of a half in a fixed order.
 constexpr int kTileRows = 128;
 constexpr int kStage = 4096;
-constexpr int kCB = 4;  // columns per pass of a half CTA
 
-template <typename T, typename TX, typename TL, typename V, int MODE>
-__global__ void __launch_bounds__(kThreads) tile_kernel(Ops ops, int K, int64_t n, int B, const TX* theta,
-                                                        const TX* X, TL* Y, const T* bvec, const TL* invD,
-                                                        const Col<T>* st, int sel, T* part0, double* part1) {
-  __shared__ int32_t ci_s[kStage];
-  __shared__ V va_s[kStage];
-  __shared__ int rps[SAS_MAX_TERMS][kTileRows + 1];  // staged row starts per block
-  __shared__ int seg_off[SAS_MAX_TERMS];
-  __shared__ int64_t seg_base[SAS_MAX_TERMS];
-  __shared__ int s_staged, s_na;
-  __shared__ int alist[256];  // the selected columns, in order
-  extern __shared__ __align__(16) unsigned char dyn[];
-  T* wpart = reinterpret_cast<T*>(dyn);
-  double* wpart1 = reinterpret_cast<double*>(wpart + (size_t)B * 4);
-  int* act = reinterpret_cast<int*>(wpart1 + (size_t)B * 4);
-  const int G = gridDim.x;
-  const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
-  const int64_t r1 = r0 + kTileRows < n ? r0 + kTileRows : n;
-  const int rows = (int)(r1 - r0);
+template <typename V>
+struct TileStage {
+  int32_t ci[kStage];
+  V va[kStage];
+  int rps[SAS_MAX_TERMS][kTileRows + 1];  // staged row starts per block
+  int seg_off[SAS_MAX_TERMS];
+  int64_t seg_base[SAS_MAX_TERMS];
+  int staged, nsel;
+  int list[256];
+};
+
+// Selects the columns (or quads of columns) to work on and stages the tile.
+// Returns false when there is nothing to do (the same for the whole CTA).
+template <typename T, typename V>
+__device__ inline bool tile_prologue(const Ops& ops, int K, int64_t r0, int64_t r1, int B, bool quads,
+                                     const Col<T>* st, int sel, int* act, TileStage<V>& ts) {
   for (int b = threadIdx.x; b < B; b += kThreads)
     act[b] = sel == kSelAll ? 1 : sel == kSelActive ? st[b].active : st[b].upd;
   __syncthreads();
   if (threadIdx.x == 0) {
     int m = 0;
-    for (int b = 0; b < B; ++b)
-      if (act[b]) alist[m++] = b;
-    s_na = m;
+    if (quads) {
+      for (int q = 0; 4 * q < B; ++q) {
+        bool any = false;
+        for (int j = 0; j < 4 && 4 * q + j < B; ++j) any = any || act[4 * q + j];
+        if (any) ts.list[m++] = q;
+      }
+    } else {
+      for (int b = 0; b < B; ++b)
+        if (act[b]) ts.list[m++] = b;
+    }
+    ts.nsel = m;
     int64_t total = 0;
     for (int k = 0; k < K && m > 0; ++k) {
-      seg_base[k] = ops.rp[k][r0];
-      seg_off[k] = (int)(total < kStage ? total : kStage);
-      total += ops.rp[k][r1] - seg_base[k];
+      ts.seg_base[k] = ops.rp[k][r0];
+      ts.seg_off[k] = (int)(total < kStage ? total : kStage);
+      total += ops.rp[k][r1] - ts.seg_base[k];
     }
-    s_staged = total <= kStage;
+    ts.staged = total <= kStage;
   }
   __syncthreads();
-  if (s_na == 0) return;  // no selected column (the same for the whole CTA)
-  const bool staged = s_staged;
-  if (staged)
+  if (ts.nsel == 0) return false;
+  if (ts.staged) {
+    const int rows = (int)(r1 - r0);
     for (int k = 0; k < K; ++k) {
-      const int64_t base = seg_base[k];
+      const int64_t base = ts.seg_base[k];
       const int cnt = (int)(ops.rp[k][r1] - base);
       const V* va = vals<V>(ops, k);
       for (int e = threadIdx.x; e < cnt; e += kThreads) {
-        ci_s[seg_off[k] + e] = ops.ci[k][base + e];
-        va_s[seg_off[k] + e] = va[base + e];
+        ts.ci[ts.seg_off[k] + e] = ops.ci[k][base + e];
+        ts.va[ts.seg_off[k] + e] = va[base + e];
       }
       for (int j = threadIdx.x; j <= rows; j += kThreads)
-        rps[k][j] = (int)(ops.rp[k][r0 + j] - base) + seg_off[k];
+        ts.rps[k][j] = (int)(ops.rp[k][r0 + j] - base) + ts.seg_off[k];
     }
+  }
+  __syncthreads();
+  return true;
+}
+
+// Q = A(theta_b) P for the active columns, P and Q quad-interleaved in the
+// storage type TL (the arithmetic too), values of type V; part[b*G + tile] =
+// sum over the tile of P_ib Q_ib.  Each half takes kQ quads per pass: one
+// 16-byte gather serves four columns.  theta is [quad][k][4] in TL.
+// Dynamic shared memory: B * 4 values of T and B ints.
+template <typename T, typename TL, typename V>
+__global__ void __launch_bounds__(kThreads) product_kernel(Ops ops, int K, int64_t n, int B, const TL* theta,
+                                                           const TL* P, TL* Q, const Col<T>* st, T* part) {
+  constexpr int kQ = sizeof(TL) >= 16 ? 1 : 2;
+  __shared__ TileStage<V> ts;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* wpart = reinterpret_cast<T*>(dyn);
+  int* act = reinterpret_cast<int*>(wpart + (size_t)B * 4);
+  const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+  const int64_t r1 = r0 + kTileRows < n ? r0 + kTileRows : n;
+  if (!tile_prologue<T, V>(ops, K, r0, r1, B, true, st, kSelActive, act, ts)) return;
   const int half = threadIdx.x >> 7, t = threadIdx.x & 127;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t i = r0 + t;
-  const bool valid = t < rows;
-  __syncthreads();
-  // each half takes kCB of the selected columns at a time: kCB independent gathers per
-  // stored entry; a short last group repeats its last column and discards the copies
-  const int na = s_na;
-  for (int g0 = half * kCB; g0 < na; g0 += 2 * kCB) {
-    const int nj = na - g0 < kCB ? na - g0 : kCB;
-    const TX* xp[kCB];
-    int bj[kCB];
+  const bool valid = i < r1;
+  const int nq = ts.nsel;
+  for (int g0 = half * kQ; g0 < nq; g0 += 2 * kQ) {
+    const int nj = nq - g0 < kQ ? nq - g0 : kQ;
+    int qa[kQ];
+    const TL* xp[kQ];
 #pragma unroll
-    for (int j = 0; j < kCB; ++j) {
-      bj[j] = alist[g0 + (j < nj ? j : nj - 1)];
-      xp[j] = X + (int64_t)bj[j] * n;
+    for (int u = 0; u < kQ; ++u) {
+      qa[u] = ts.list[g0 + (u < nj ? u : nj - 1)];
+      xp[u] = P + (int64_t)qa[u] * n * 4;
     }
-    TX acc[kCB];
+    Quad<TL> acc[kQ];
 #pragma unroll
-    for (int j = 0; j < kCB; ++j) acc[j] = zero<TX>();
+    for (int u = 0; u < kQ; ++u)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[u].v[j] = zero<TL>();
     if (valid) {
 #pragma unroll 1
       for (int k = 0; k < K; ++k) {
-        TX sum[kCB];
+        Quad<TL> sum[kQ];
 #pragma unroll
-        for (int j = 0; j < kCB; ++j) sum[j] = zero<TX>();
-        if (staged) {
-          const int e1 = rps[k][t + 1];
+        for (int u = 0; u < kQ; ++u)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) sum[u].v[j] = zero<TL>();
+        if (ts.staged) {
+          const int e1 = ts.rps[k][t + 1];
 #pragma unroll 2
-          for (int e = rps[k][t]; e < e1; ++e) {
-            const V v = va_s[e];
-            const int c = ci_s[e];
+          for (int e = ts.rps[k][t]; e < e1; ++e) {
+            const V v = ts.va[e];
+            const int64_t c4 = (int64_t)ts.ci[e] * 4;
 #pragma unroll
-            for (int j = 0; j < kCB; ++j) sum[j] += rscale(v, xp[j][c]);
+            for (int u = 0; u < kQ; ++u) {
+              const Quad<TL> x = ldq<TL>(xp[u] + c4);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) sum[u].v[j] += rscale(v, x.v[j]);
+            }
           }
         } else {
           const V* va = vals<V>(ops, k);
           const int64_t e1 = ops.rp[k][i + 1];
           for (int64_t e = ops.rp[k][i]; e < e1; ++e) {
             const V v = va[e];
+            const int64_t c4 = (int64_t)ops.ci[k][e] * 4;
+#pragma unroll
+            for (int u = 0; u < kQ; ++u) {
+              const Quad<TL> x = ldq<TL>(xp[u] + c4);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) sum[u].v[j] += rscale(v, x.v[j]);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kQ; ++u) {
+          const Quad<TL> th = ldq<TL>(theta + ((int64_t)qa[u] * K + k) * 4);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[u].v[j] += th.v[j] * sum[u].v[j];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kQ; ++u) {
+      if (u >= nj) break;  // uniform
+      Quad<TL> xi;
+      if (valid) {
+        stq<TL>(Q + ((int64_t)qa[u] * n + i) * 4, acc[u]);
+        xi = ldq<TL>(xp[u] + i * 4);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int b = 4 * qa[u] + j;
+        if (b >= B || !act[b]) continue;  // uniform
+        TL d = valid ? xi.v[j] * acc[u].v[j] : zero<TL>();
+        d = warp_sum(d);  // in the storage arithmetic, widened once per warp
+        if (lane == 0) wpart[b * 4 + (warp & 3)] = cvt<T>(d);
+      }
+    }
+  }
+  __syncthreads();
+  const int G = gridDim.x;
+  for (int b = threadIdx.x; b < B; b += kThreads)
+    if (act[b]) part[(int64_t)b * G + blockIdx.x] = ((wpart[b * 4] + wpart[b * 4 + 1]) + wpart[b * 4 + 2]) + wpart[b * 4 + 3];
+}
+
+// R = b - A(theta_b) X in float64 for the selected columns (X column-major,
+// the caller's), written to R in the quad layout as TL; part0[b*G + tile] =
+// sum R_ib D^-1_ib R_ib and part1 = sum |R_ib|^2, both in float64.
+// Dynamic shared memory: B * 4 values of T, B * 4 doubles and B ints.
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) residual_kernel(Ops ops, int K, int64_t n, int B, const T* theta,
+                                                            const T* X, TL* R, const T* bvec, const TL* invD,
+                                                            const Col<T>* st, int sel, T* part0, double* part1) {
+  constexpr int kCB = 4;
+  __shared__ TileStage<double> ts;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* wpart = reinterpret_cast<T*>(dyn);
+  double* wpart1 = reinterpret_cast<double*>(wpart + (size_t)B * 4);
+  int* act = reinterpret_cast<int*>(wpart1 + (size_t)B * 4);
+  const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+  const int64_t r1 = r0 + kTileRows < n ? r0 + kTileRows : n;
+  if (!tile_prologue<T, double>(ops, K, r0, r1, B, false, st, sel, act, ts)) return;
+  const int half = threadIdx.x >> 7, t = threadIdx.x & 127;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = r0 + t;
+  const bool valid = i < r1;
+  const int na = ts.nsel;
+  for (int g0 = half * kCB; g0 < na; g0 += 2 * kCB) {
+    const int nj = na - g0 < kCB ? na - g0 : kCB;
+    const T* xp[kCB];
+    int bj[kCB];
+#pragma unroll
+    for (int j = 0; j < kCB; ++j) {
+      bj[j] = ts.list[g0 + (j < nj ? j : nj - 1)];
+      xp[j] = X + (int64_t)bj[j] * n;
+    }
+    T acc[kCB];
+#pragma unroll
+    for (int j = 0; j < kCB; ++j) acc[j] = zero<T>();
+    if (valid) {
+#pragma unroll 1
+      for (int k = 0; k < K; ++k) {
+        T sum[kCB];
+#pragma unroll
+        for (int j = 0; j < kCB; ++j) sum[j] = zero<T>();
+        if (ts.staged) {
+          const int e1 = ts.rps[k][t + 1];
+          for (int e = ts.rps[k][t]; e < e1; ++e) {
+            const double v = ts.va[e];
+            const int c = ts.ci[e];
+#pragma unroll
+            for (int j = 0; j < kCB; ++j) sum[j] += rscale(v, xp[j][c]);
+          }
+        } else {
+          const int64_t e1 = ops.rp[k][i + 1];
+          for (int64_t e = ops.rp[k][i]; e < e1; ++e) {
+            const double v = ops.va[k][e];
             const int c = ops.ci[k][e];
 #pragma unroll
             for (int j = 0; j < kCB; ++j) sum[j] += rscale(v, xp[j][c]);
@@ -264,39 +427,28 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(Ops ops, int K, int64_t 
     for (int j = 0; j < kCB; ++j) {
       if (j >= nj) break;  // uniform
       const int b = bj[j];
-      if (MODE == 0) {
-        // the product's dot is summed over the warp in the arithmetic of X (float32 in the
-        // mixed form: the float64 pipe is 64x narrower), then widened once
-        TX dx = zero<TX>();
-        if (valid) {
-          Y[(int64_t)b * n + i] = cvt<TL>(acc[j]);
-          dx = xp[j][i] * acc[j];
-        }
-        dx = warp_sum(dx);
-        if (lane == 0) wpart[b * 4 + (warp & 3)] = cvt<T>(dx);
-      } else {
-        T d0 = zero<T>();
-        double d1 = 0.0;
-        if (valid) {
-          const T r = bvec[i] - cvt<T>(acc[j]);
-          Y[(int64_t)b * n + i] = cvt<TL>(r);
-          d0 = r * (cvt<T>(invD[(int64_t)b * n + i]) * r);
-          d1 = absq(r);
-        }
-        d0 = warp_sum(d0);
-        d1 = warp_sum(d1);
-        if (lane == 0) {
-          wpart[b * 4 + (warp & 3)] = d0;
-          wpart1[b * 4 + (warp & 3)] = d1;
-        }
+      T d0 = zero<T>();
+      double d1 = 0.0;
+      if (valid) {
+        const T r = bvec[i] - acc[j];
+        R[qidx(n, b, i)] = cvt<TL>(r);
+        d0 = r * (cvt<T>(invD[qidx(n, b, i)]) * r);
+        d1 = absq(r);
+      }
+      d0 = warp_sum(d0);
+      d1 = warp_sum(d1);
+      if (lane == 0) {
+        wpart[b * 4 + (warp & 3)] = d0;
+        wpart1[b * 4 + (warp & 3)] = d1;
       }
     }
   }
   __syncthreads();
+  const int G = gridDim.x;
   for (int b = threadIdx.x; b < B; b += kThreads) {
     if (!act[b]) continue;
     if (part0) part0[(int64_t)b * G + blockIdx.x] = ((wpart[b * 4] + wpart[b * 4 + 1]) + wpart[b * 4 + 2]) + wpart[b * 4 + 3];
-    if (MODE == 1 && part1)
+    if (part1)
       part1[(int64_t)b * G + blockIdx.x] = ((wpart1[b * 4] + wpart1[b * 4 + 1]) + wpart1[b * 4 + 2]) + wpart1[b * 4 + 3];
   }
 }
@@ -380,41 +532,6 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const T* ppq, int G, Co
   }
 }
 
-// X += alpha P, R -= alpha Q (storage TL, arithmetic TL); partials (in T) of the
-// new r^T D^{-1} r and ||r||^2.
-template <typename T, typename TL>
-__global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, TL* X, TL* R, const TL* P, const TL* Q,
-                                                          const TL* invD, const Col<T>* st, T* prz,
-                                                          double* prr, int64_t rows_per_cta) {
-  __shared__ T red[kThreads / 32];
-  __shared__ double redd[kThreads / 32];
-  const int b = blockIdx.x, G = gridDim.y;
-  if (!st[b].active) return;
-  const TL alpha = cvt<TL>(st[b].alpha);
-  const int64_t off = (int64_t)b * n;
-  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
-  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
-  // per-thread sums in the storage type (a few dozen terms), combined in float64
-  TL rz_t = zero<TL>();
-  decltype(absq(rz_t)) rr_t = 0;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
-    X[off + i] += alpha * P[off + i];
-    const TL r = R[off + i] - alpha * Q[off + i];
-    R[off + i] = r;
-    rz_t += r * (invD[off + i] * r);
-    rr_t += absq(r);
-  }
-  // warp sums in the storage arithmetic, widened once per warp
-  rz_t = warp_sum(rz_t);
-  rr_t = warp_sum(rr_t);
-  T rz = block_sum_warps(cvt<T>(rz_t), red);
-  double rr = block_sum_warps((double)rr_t, redd);
-  if (threadIdx.x == 0) {
-    prz[(int64_t)b * G + blockIdx.y] = rz;
-    prr[(int64_t)b * G + blockIdx.y] = rr;
-  }
-}
-
 // After the update: the iterated residual's norm.  A column whose residual
 // reached the tolerance, or (float32 iterates) fell below delta times the
 // residual at its last replacement, is flagged for replacement by the true
@@ -449,33 +566,129 @@ __global__ void __launch_bounds__(kThreads) beta_kernel(const T* prz, const doub
   }
 }
 
-// x (float64) += x_lo; x_lo = 0, for the columns flagged for replacement (all != 0: every column)
+// Elementwise kernels over the quad layout: grid (quads, row chunks), one row of
+// a quad per thread and step.  Columns that are inactive (or padding) are
+// left untouched.
+template <typename T>
+__device__ inline int quad_flags(const Col<T>* st, int q, int B, int which) {
+  int m = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int b = 4 * q + j;
+    if (b < B && (which == 0 ? st[b].active : st[b].upd)) m |= 1 << j;
+  }
+  return m;
+}
+
+// X += alpha P, R -= alpha Q (arithmetic in TL); partials (in T) of the new
+// r^T D^{-1} r and ||r||^2 per column.
 template <typename T, typename TL>
-__global__ void __launch_bounds__(kThreads) fold_kernel(int64_t n, T* X, TL* Xl, const Col<T>* st, int all,
+__global__ void __launch_bounds__(kThreads) update_kernel(int64_t n, int B, TL* X, TL* R, const TL* P, const TL* Q,
+                                                          const TL* invD, const Col<T>* st, T* prz,
+                                                          double* prr, int64_t rows_per_cta) {
+  __shared__ T red[kThreads / 32][4];
+  __shared__ double redd[kThreads / 32][4];
+  const int q = blockIdx.x, G = gridDim.y;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  TL alpha[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) alpha[j] = (on >> j) & 1 ? cvt<TL>(st[4 * q + j].alpha) : zero<TL>();
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  // per-thread sums in the storage arithmetic (a few dozen terms), widened per warp
+  TL rz[4];
+  decltype(absq(rz[0])) rr[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    rz[j] = zero<TL>();
+    rr[j] = 0;
+  }
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    Quad<TL> x = ldq<TL>(X + o), r = ldq<TL>(R + o);
+    const Quad<TL> p = ldq<TL>(P + o), qq = ldq<TL>(Q + o), d = ldq<TL>(invD + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!((on >> j) & 1)) continue;
+      x.v[j] += alpha[j] * p.v[j];
+      r.v[j] -= alpha[j] * qq.v[j];
+      rz[j] += r.v[j] * (d.v[j] * r.v[j]);
+      rr[j] += absq(r.v[j]);
+    }
+    stq<TL>(X + o, x);
+    stq<TL>(R + o, r);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const TL a = warp_sum(rz[j]);
+    const auto c = warp_sum(rr[j]);
+    if (lane == 0) {
+      red[w][j] = cvt<T>(a);
+      redd[w][j] = (double)c;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && ((on >> threadIdx.x) & 1)) {
+    const int j = threadIdx.x;
+    T a = zero<T>();
+    double c = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) {
+      a += red[k][j];
+      c += redd[k][j];
+    }
+    prz[(int64_t)(4 * q + j) * G + blockIdx.y] = a;
+    prr[(int64_t)(4 * q + j) * G + blockIdx.y] = c;
+  }
+}
+
+// x (float64, column-major) += x_lo (quad layout); x_lo = 0, for the columns
+// flagged for replacement (all != 0: every column)
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) fold_kernel(int64_t n, int B, T* X, TL* Xl, const Col<T>* st, int all,
                                                         int64_t rows_per_cta) {
-  const int b = blockIdx.x;
-  if (!all && !st[b].upd) return;
-  const int64_t off = (int64_t)b * n;
+  const int q = blockIdx.x;
+  int on = quad_flags(st, q, B, 1);
+  if (all)
+    for (int j = 0; j < 4; ++j) on |= (4 * q + j < B) << j;
+  if (!on) return;
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
   const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
   for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
-    X[off + i] += cvt<T>(Xl[off + i]);
-    Xl[off + i] = zero<TL>();
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    Quad<TL> xl = ldq<TL>(Xl + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((on >> j) & 1) {
+        X[(int64_t)(4 * q + j) * n + i] += cvt<T>(xl.v[j]);
+        xl.v[j] = zero<TL>();
+      }
+    stq<TL>(Xl + o, xl);
   }
 }
 
 // P = D^{-1} R + beta P
 template <typename T, typename TL>
-__global__ void __launch_bounds__(kThreads) direction_kernel(int64_t n, const TL* R, const TL* invD, TL* P,
+__global__ void __launch_bounds__(kThreads) direction_kernel(int64_t n, int B, const TL* R, const TL* invD, TL* P,
                                                              const Col<T>* st, int64_t rows_per_cta) {
-  const int b = blockIdx.x;
-  if (!st[b].active) return;
-  const TL beta = cvt<TL>(st[b].beta);
-  const int64_t off = (int64_t)b * n;
+  const int q = blockIdx.x;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  TL beta[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) beta[j] = (on >> j) & 1 ? cvt<TL>(st[4 * q + j].beta) : zero<TL>();
   const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
   const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
-  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads)
-    P[off + i] = invD[off + i] * R[off + i] + beta * P[off + i];
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    const Quad<TL> r = ldq<TL>(R + o), d = ldq<TL>(invD + o);
+    Quad<TL> p = ldq<TL>(P + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((on >> j) & 1) p.v[j] = d.v[j] * r.v[j] + beta[j] * p.v[j];
+    stq<TL>(P + o, p);
+  }
 }
 
 __global__ void __launch_bounds__(kThreads) norm_partial_kernel(const double* x, int64_t count, double* out) {
@@ -714,9 +927,11 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   int64_t rpc = (n * (int64_t)B + (int64_t)sms * 16 - 1) / ((int64_t)sms * 16);
   rpc = std::max<int64_t>(kThreads, (rpc + kThreads - 1) / kThreads * kThreads);
   const int G = (int)((n + rpc - 1) / rpc);
-  const dim3 grid(B, G);
+
   const int Gt = (int)((n + off::kTileRows - 1) / off::kTileRows);  // tiles of the product kernel
   const int Gp = std::max(G, Gt);
+  const int B4 = (B + 3) / 4;  // quads of columns
+  const dim3 qgrid(B4, G);
   const size_t tile_smem = (size_t)B * 4 * sizeof(T) + (size_t)B * 4 * sizeof(double) + (size_t)B * sizeof(int);
   const double delta = mixed ? 0.1 : 0.0;  // replacement once the float32 residual fell 10x
 
@@ -739,15 +954,20 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
       }
     }
   }
-  std::vector<TL> thl_h(th_h.size());
-  for (size_t q = 0; q < th_h.size(); ++q) {
-    if constexpr (sizeof(TL) == sizeof(T)) thl_h[q] = th_h[q];
-    else if constexpr (sizeof(T) == 16) thl_h[q] = mkzf((float)th_h[q].re, (float)th_h[q].im);
-    else thl_h[q] = (float)th_h[q];
-  }
+  // theta in the iterates' arithmetic, laid out [quad][k][4] (zero for padding columns)
+  std::vector<TL> thl_h((size_t)B4 * K * 4, TL{});
+  for (int b = 0; b < B; ++b)
+    for (int k = 0; k < K; ++k) {
+      const T v = th_h[(size_t)b * K + k];
+      TL w;
+      if constexpr (sizeof(TL) == sizeof(T)) w = v;
+      else if constexpr (sizeof(T) == 16) w = mkzf((float)v.re, (float)v.im);
+      else w = (float)v;
+      thl_h[((size_t)(b / 4) * K + k) * 4 + (b % 4)] = w;
+    }
   DevBuf theta, theta_lo, D, invD, R, P, Q, Xl, prz, ppq, prr, st, bad, nb;
   DevBuf va32[SAS_MAX_TERMS];
-  const size_t vec = (size_t)n * B * sizeof(TL);
+  const size_t vec = (size_t)n * B4 * 4 * sizeof(TL);
   cudaError_t e = theta.alloc(th_h.size() * sizeof(T));
   if (e == cudaSuccess) e = theta_lo.alloc(thl_h.size() * sizeof(TL));
   if (e == cudaSuccess) e = D.alloc((size_t)K * n * sizeof(double));
@@ -755,7 +975,7 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   if (e == cudaSuccess) e = R.alloc(vec);
   if (e == cudaSuccess) e = P.alloc(vec);
   if (e == cudaSuccess) e = Q.alloc(vec);
-  if (e == cudaSuccess && mixed) e = Xl.alloc(vec);
+  if (e == cudaSuccess) e = Xl.alloc(vec);
   if (e == cudaSuccess) e = prz.alloc((size_t)B * Gp * sizeof(T));
   if (e == cudaSuccess) e = ppq.alloc((size_t)B * Gt * sizeof(T));
   if (e == cudaSuccess) e = prr.alloc((size_t)B * Gp * sizeof(double));
@@ -764,8 +984,8 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   if (e == cudaSuccess) e = nb.alloc((size_t)sms * sizeof(double));
   if (e != cudaSuccess) return cuda_fail(e, "krylov: allocation");
   using V = typename std::conditional<sizeof(TL) == sizeof(T), double, float>::type;
-  auto* k_lo = off::tile_kernel<T, TL, TL, V, 0>;
-  auto* k_res = off::tile_kernel<T, T, TL, double, 1>;
+  auto* k_lo = off::product_kernel<T, TL, V>;
+  auto* k_res = off::residual_kernel<T, TL>;
   e = cudaFuncSetAttribute(k_lo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: shared memory");
@@ -787,14 +1007,13 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
       }
     }
   if (e != cudaSuccess) return cuda_fail(e, "krylov: float copies of the blocks");
-  TL* Xit = mixed ? Xl.as<TL>() : reinterpret_cast<TL*>(X);  // where the iteration accumulates x
   e = cudaMemcpyAsync(theta.p, th_h.data(), th_h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(theta_lo.p, thl_h.data(), thl_h.size() * sizeof(TL), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(bad.p, 0, sizeof(int), s);
   if (e == cudaSuccess && !warm) e = cudaMemsetAsync(X, 0, (size_t)n * B * sizeof(T), s);
-  if (e == cudaSuccess && mixed) e = cudaMemsetAsync(Xl.p, 0, vec, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(P.p, 0, vec, s);
+  for (DevBuf* v : {&Xl, &P, &R, &Q, &invD})  // the padding columns stay zero
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->p, 0, vec, s);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: setup copies");
   off::diag_kernel<<<sms * 4, kThreads, 0, s>>>(ops, K, n, D.as<double>());
   off::inv_diag_kernel<T, TL><<<dim3(sms * 2, B), kThreads, 0, s>>>(D.as<double>(), K, n, theta.as<T>(),
@@ -821,8 +1040,8 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   if (!(bnorm > 0.0)) return fail_off(SAS_EINVAL, "krylov: b = 0");
   off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 1,
                                                 st.as<Col<T>>());
-  off::direction_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
-                                                         st.as<Col<T>>(), rpc);
+  off::direction_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
+                                                          st.as<Col<T>>(), rpc);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "krylov: first direction");
 
@@ -833,23 +1052,22 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: capture");
   for (int it = 0; it < chunk; ++it) {
-    k_lo<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta_lo.as<TL>(), P.as<TL>(), Q.as<TL>(), nullptr, nullptr,
-                                         st.as<Col<T>>(), off::kSelActive, ppq.as<T>(), nullptr);
+    k_lo<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta_lo.as<TL>(), P.as<TL>(), Q.as<TL>(), st.as<Col<T>>(),
+                                         ppq.as<T>());
     off::alpha_kernel<T><<<B, kThreads, 0, s>>>(ppq.as<T>(), Gt, st.as<Col<T>>());
-    off::update_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, Xit, R.as<TL>(), P.as<TL>(), Q.as<TL>(),
-                                                        invD.as<TL>(), st.as<Col<T>>(), prz.as<T>(),
-                                                        prr.as<double>(), rpc);
+    off::update_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, Xl.as<TL>(), R.as<TL>(), P.as<TL>(), Q.as<TL>(),
+                                                         invD.as<TL>(), st.as<Col<T>>(), prz.as<T>(),
+                                                         prr.as<double>(), rpc);
     off::beta_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, delta, maxit,
                                                st.as<Col<T>>());
-    if (mixed)
-      off::fold_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, X, Xl.as<TL>(), st.as<Col<T>>(), 0, rpc);
+    off::fold_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, X, Xl.as<TL>(), st.as<Col<T>>(), 0, rpc);
     k_res<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta.as<T>(), X, R.as<TL>(), (const T*)d->b,
                                           invD.as<TL>(), st.as<Col<T>>(), off::kSelUpd, prz.as<T>(),
                                           prr.as<double>());
     off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 0,
                                                   st.as<Col<T>>());
-    off::direction_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
-                                                           st.as<Col<T>>(), rpc);
+    off::direction_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
+                                                            st.as<Col<T>>(), rpc);
   }
   e = cudaStreamEndCapture(s, &graph);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -872,8 +1090,8 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: iteration");
   e = cudaMemcpyAsync(st_h.data(), st.p, st_h.size() * sizeof(Col<T>), cudaMemcpyDeviceToHost, s);
-  // columns that stopped on a breakdown may hold float32 corrections not yet folded
-  if (mixed) off::fold_kernel<T, TL><<<grid, kThreads, 0, s>>>(n, X, Xl.as<TL>(), st.as<Col<T>>(), 1, rpc);
+  // columns that stopped on a breakdown or the iteration limit may hold corrections not yet folded
+  off::fold_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, X, Xl.as<TL>(), st.as<Col<T>>(), 1, rpc);
   // true residual of the returned iterates
   k_res<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta.as<T>(), X, Q.as<TL>(), (const T*)d->b,
                                         invD.as<TL>(), st.as<Col<T>>(), off::kSelAll, nullptr, prr.as<double>());

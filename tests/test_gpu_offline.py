@@ -173,3 +173,50 @@ def test_offline_then_online_pipeline():
     assert (res_g <= 10 * res_o + 1e-9).all(), (res_g.max(), res_o.max())
     print(f"pipeline: x_hat residual max {res_g.max():.2e} (oracle pipeline {res_o.max():.2e}), "
           f"rows shared with the oracle's J {overlap:.0%}")
+
+
+def test_dense_rows_take_the_unstaged_path():
+    """Eight blocks of 9-point stencils: ~70 stored entries per row, more than a tile's
+    shared-memory stage holds, so the product reads the CSR arrays from global memory."""
+    import types
+    import scipy.sparse as sp
+    N = 40
+    n = N * N
+    rng = np.random.default_rng(11)
+    one = np.ones(N)
+    T1 = sp.diags([-one[1:], 2 * one, -one[1:]], [-1, 0, 1])
+    I = sp.identity(N)
+    lap = (sp.kron(I, T1) + sp.kron(T1, I)).tocsr()
+    blocks = [lap + sp.identity(n) * 0.1]
+    for k in range(7):  # SPD 9-point blocks with random positive weights
+        w = rng.uniform(0.5, 1.5, n)
+        W = sp.diags(w)
+        Tp = sp.diags([one[1:], 2 * one, one[1:]], [-1, 0, 1])  # positive semidefinite
+        M = sp.kron(Tp, Tp)
+        blocks.append((W @ M @ W * 0.05 + sp.identity(n) * 2.0).tocsr())
+    prob = types.SimpleNamespace(name="dense_rows", n=n, blocks=blocks, theta_rule="linear",
+                                 b=rng.standard_normal(n), complex_valued=False)
+    per_row = sum(B.nnz for B in blocks) / n
+    assert per_row * 128 > 4096, per_row
+    P = rng.uniform(0.0, 1.0, (5, 7))
+    for mixed in (False, True):
+        X = torch.empty((5, n), dtype=torch.float64, device=DEV)
+        it, rel = snapshot_solve(prob, P, X, tol=1e-10, mixed=mixed)
+        Xg = X.cpu().numpy()
+        for j, p in enumerate(P):
+            xo = snapshots.solve_full(prob, p)
+            A = oproblem.full_matrix(prob, p)
+            assert np.linalg.norm(A @ Xg[j] - prob.b) / np.linalg.norm(prob.b) <= 2e-10
+            assert np.linalg.norm(Xg[j] - xo) / np.linalg.norm(xo) <= 1e-7
+        print(f"unstaged rows ({per_row:.0f} per row), {'mixed' if mixed else 'plain'}: iterations {it.max()}")
+
+
+def test_batch_limits_and_single_column():
+    prob = get_config("diffusion_2d", N=20, r=3, s=6, m=4)
+    X = torch.empty((1, prob.n), dtype=torch.float64, device=DEV)
+    it, rel = snapshot_solve(prob, prob.snap_params[:1], X, tol=1e-12)
+    xo = snapshots.solve_full(prob, prob.snap_params[0])
+    assert np.linalg.norm(X.cpu().numpy()[0] - xo) / np.linalg.norm(xo) <= 1e-9
+    with pytest.raises(api.SasError):
+        Xb = torch.empty((257, prob.n), dtype=torch.float64, device=DEV)
+        snapshot_solve(prob, np.tile(prob.snap_params[:1], (257, 1)), Xb)
