@@ -164,6 +164,21 @@ sas_status subapsnap_solve_batch(sas_ctx* ctx, const double* params, int64_t m,
                                  int32_t out_kind, void* out, uint32_t* flags,
                                  double* rho, void* stream);
 
+/* subapsnap_solve_batch with HOST buffers: params (m x dp), out (layout per
+ * out_kind), flags and rho (or NULL) are ordinary host memory.  The call
+ * copies params to the device, solves, and returns after the outputs are in
+ * the host buffers (synchronous on `stream`).  x_hat is written straight
+ * into `out` by the reconstruction when `out` is page-locked host memory
+ * mapped into the device's address space (cudaHostAlloc or
+ * cudaHostRegister; every such allocation is mapped under unified
+ * addressing), so the transfer overlaps the computation; pageable `out`
+ * goes through a device buffer in chunks of at most 1 GiB.  Device staging
+ * is owned by the context.  Errors: as subapsnap_solve_batch, SAS_EINVAL for
+ * a device pointer. */
+sas_status subapsnap_solve_batch_host(sas_ctx* ctx, const double* params, int64_t m,
+                                      int32_t out_kind, void* out, uint32_t* flags,
+                                      double* rho, void* stream);
+
 /* Reconstruction x_hat = S y of given coefficient vectors (Alg. 1 step 4,
  * "output X c"), in the context's arithmetic: float64 DFMA in
  * SAS_MODE_PLAIN; in SAS_MODE_MIXED float32 from tf32 splits of S and y on

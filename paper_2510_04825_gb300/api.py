@@ -37,7 +37,7 @@ EXPORTED = [
     "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch", "subapsnap_multi_plan_destroy",
     "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine", "subapsnap_sample_rows_leverage",
     "subapsnap_select_rows_union_affine", "subapsnap_nearest_points", "subapsnap_krylov_affine",
-    "subapsnap_tsqr",
+    "subapsnap_tsqr", "subapsnap_solve_batch_host",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
@@ -136,6 +136,7 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_krylov_affine.argtypes = [ctypes.POINTER(AffineDesc), vp, i32, vp, i32, ctypes.c_double,
                                               i32, vp, vp]
         L.subapsnap_tsqr.argtypes = [vp, i64, i32, i64, i32, vp, i64, vp]
+        L.subapsnap_solve_batch_host.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
         for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
@@ -147,7 +148,8 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch",
                      "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine",
                      "subapsnap_sample_rows_leverage", "subapsnap_select_rows_union_affine",
-                     "subapsnap_nearest_points", "subapsnap_krylov_affine", "subapsnap_tsqr"):
+                     "subapsnap_nearest_points", "subapsnap_krylov_affine", "subapsnap_tsqr",
+                     "subapsnap_solve_batch_host"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -345,6 +347,27 @@ def subapsnap_tsqr(X, Q=None, complex_valued: bool | None = None) -> np.ndarray:
     _check(lib().subapsnap_tsqr(_ptr(X), n, r, n, SAS_COMPLEX128 if cplx else SAS_REAL64, _ptr(Q), n,
                                 R.ctypes.data_as(ctypes.c_void_p)))
     return np.ascontiguousarray(R.T)
+
+
+def _hptr(a):
+    """Host pointer of a CPU tensor or a numpy array (None passes through)."""
+    if a is None:
+        return None
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda:
+            raise ValueError("expected a host (CPU) tensor")
+        if not a.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a contiguous array")
+    return a.ctypes.data
+
+
+def subapsnap_solve_batch_host(ctx, params, m: int, out_kind: int, out, flags=None, rho=None, stream=None):
+    """solve_batch with host buffers (CPU tensors or numpy arrays); returns when out is filled."""
+    _check(lib().subapsnap_solve_batch_host(ctx, _hptr(params), int(m), int(out_kind), _hptr(out),
+                                            _hptr(flags), _hptr(rho), _stream(stream)))
 
 
 def subapsnap_reconstruct(ctx, Y, m: int, out, stream=None):

@@ -103,6 +103,7 @@ static void free_ctx(sas_ctx* c) {
   cudaFree(c->ybuf);
   cudaFree(c->ysplit);
   cudaFree(c->Mbuf);
+  cudaFree(c->hstage);
   cudaFree(c->dev_status);
   destroy_surrogate(c);
   if (c->trace) {
@@ -527,6 +528,89 @@ sas_status subapsnap_solve_batch(sas_ctx* c, const double* params, int64_t m, in
       return fail(SAS_EINVAL, "bad out_kind");
   }
   if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+  return SAS_OK;
+}
+
+namespace {
+// device staging for host-buffer calls, grown on demand (256-byte aligned pieces)
+cudaError_t host_stage(sas_ctx* c, size_t bytes, cudaStream_t st) {
+  if (bytes <= c->hstage_bytes) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  cudaFree(c->hstage);
+  c->hstage = nullptr;
+  c->hstage_bytes = 0;
+  e = cudaMalloc(&c->hstage, bytes);
+  if (e == cudaSuccess) c->hstage_bytes = bytes;
+  return e;
+}
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+}  // namespace
+
+sas_status subapsnap_solve_batch_host(sas_ctx* c, const double* params, int64_t m, int32_t out_kind,
+                                      void* out, uint32_t* flags, double* rho, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (m < 0) return fail(SAS_EINVAL, "m < 0");
+  if (m == 0) return SAS_OK;
+  if (!params || !out) return fail(SAS_EINVAL, "params and out must be non-NULL");
+  if (is_device_ptr(params) || is_device_ptr(out) || (flags && is_device_ptr(flags)) ||
+      (rho && is_device_ptr(rho)))
+    return fail(SAS_EINVAL, "solve_batch_host takes host buffers (use subapsnap_solve_batch for device ones)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool mixed = c->mode == SAS_MODE_MIXED;
+  const size_t elt = c->dtype == SAS_COMPLEX128 ? 16 : 8;
+  size_t out_row;  // bytes of one parameter's output
+  if (out_kind == SAS_OUT_Y) out_row = (size_t)c->r * elt;
+  else if (out_kind == SAS_OUT_QOI) out_row = elt;
+  else if (out_kind == SAS_OUT_XHAT) out_row = (size_t)c->n * (mixed ? 4 : 8);
+  else return fail(SAS_EINVAL, "bad out_kind");
+  // x_hat goes straight into the caller's memory when it is page-locked and mapped: the
+  // reconstruction's stores then stream over the host link, which is what bounds this path
+  void* out_mapped = nullptr;
+  if (out_kind == SAS_OUT_XHAT) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost)
+      out_mapped = at.devicePointer;
+    cudaGetLastError();
+  }
+  // x_hat into pageable memory: chunks of at most 1 GiB through a device buffer
+  int64_t chunk = m;
+  if (out_kind == SAS_OUT_XHAT && !out_mapped)
+    chunk = std::max<int64_t>(1, std::min<int64_t>(m, ((int64_t)1 << 30) / (int64_t)out_row));
+  const size_t pb = align256((size_t)m * c->dp * sizeof(double));
+  const size_t fb = align256((size_t)m * sizeof(uint32_t));
+  const size_t rb = align256((size_t)m * sizeof(double));
+  const size_t ob = out_mapped ? 0 : align256((size_t)chunk * out_row);
+  cudaError_t e = host_stage(c, pb + fb + rb + ob, st);
+  if (e != cudaSuccess) return cuda_fail(e, "solve_batch_host: staging");
+  char* base = (char*)c->hstage;
+  double* p_d = (double*)base;
+  uint32_t* f_d = flags ? (uint32_t*)(base + pb) : nullptr;
+  double* r_d = rho ? (double*)(base + pb + fb) : nullptr;
+  void* o_d = out_mapped ? nullptr : (void*)(base + pb + fb + rb);
+  e = cudaMemcpyAsync(p_d, params, (size_t)m * c->dp * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && f_d) e = cudaMemsetAsync(f_d, 0, (size_t)m * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "solve_batch_host: parameters");
+  const int saved_store = c->recon_store;
+  if (out_mapped) c->recon_store = 1;  // direct stores: no tensor map over host memory
+  sas_status rc = SAS_OK;
+  for (int64_t q0 = 0; q0 < m && rc == SAS_OK; q0 += chunk) {
+    const int64_t mq = std::min<int64_t>(chunk, m - q0);
+    void* dst = out_mapped ? (void*)((char*)out_mapped + (size_t)q0 * out_row) : o_d;
+    rc = subapsnap_solve_batch(c, p_d + q0 * c->dp, mq, out_kind, dst, f_d ? f_d + q0 : nullptr,
+                               r_d ? r_d + q0 : nullptr, stream);
+    if (rc == SAS_OK && !out_mapped) {
+      e = cudaMemcpyAsync((char*)out + (size_t)q0 * out_row, o_d, (size_t)mq * out_row,
+                          cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "solve_batch_host: output copy");
+    }
+  }
+  c->recon_store = saved_store;
+  if (rc != SAS_OK) return rc;
+  if (f_d) e = cudaMemcpyAsync(flags, f_d, (size_t)m * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && r_d) e = cudaMemcpyAsync(rho, r_d, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "solve_batch_host");
   return SAS_OK;
 }
 

@@ -186,6 +186,8 @@ struct sas_ctx {
   size_t ysplit_bytes;
   void* ysplit16;      // mixed, f16 reconstruction: y split into f16 hi/lo (2 x m x 64) + m scales
   size_t ysplit16_bytes;
+  void* hstage;        // host-buffer calls: device staging of params, small outputs, x_hat chunks
+  size_t hstage_bytes;
   int* dev_status;     // device status word
   int num_sms;
   int ls_blocks_per_sm;
