@@ -563,6 +563,15 @@ def run_gpu_other(args):
     roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
     roof["traffic"] = None
     ls_plain_fl = householder_flops(prob.s, prob.r, cplx) * msub
+    # end to end through the C-ABI with host buffers: params from pinned host memory, the
+    # outputs (x_hat straight from the reconstruction) into pinned host memory
+    host_params = torch.from_numpy(np.ascontiguousarray(params_host)).pin_memory()
+    host_out = torch.empty(tuple(out_c.shape), dtype=out_c.dtype).pin_memory()
+    ms_e2e, _ = timed(lambda: api.subapsnap_solve_batch_host(chosen.ctx, host_params, m, out_kind, host_out),
+                      max(1, min(args.steps, 5)), 1)
+    e2e = {"value": round(world * m / (ms_e2e * 1e-3), 2), "unit": "solves/s",
+           "h2d_bytes_per_step": int(host_params.numel() * 8),
+           "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size())}
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_c, 4),
@@ -582,6 +591,7 @@ def run_gpu_other(args):
                      "sub_plain_max": float(rp.max()), "sub_plain_median": float(np.median(rp)),
                      "y_relerr_chosen_vs_plain_max": float(yerr.max()),
                      "y_relerr_chosen_vs_plain_median": float(np.median(yerr))},
+        "e2e": e2e,
         "roofline": roof,
         "kernel_ms": {"ls": round(ls_ms / max(ls_n, 1), 4),
                       "assemble": round(asm_ms / max(asm_n, 1), 4) if asm_n else None},
