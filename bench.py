@@ -864,18 +864,24 @@ def run_offline(args):
     clocks = stop_clock_sampler(cp, cf_, clk_path, 0)
     orth = float(torch.linalg.matrix_norm(Q.conj() @ Q.T - torch.eye(B, dtype=dt, device=dev)).item())
     tsqr_flops = 4.0 * n * B * B * (4.0 if cplx else 1.0)
-    chosen = forms["mixed"]
+    # the chosen form: the faster of the forms that reached the tolerance on every snapshot
+    # (float32 iterates stall where kappa(A) 2^-24 is not small, e.g. the 1-D system)
+    ok = [k for k, f in forms.items() if f["true_rel_residual_max"] <= args.tol * (1 + 1e-9)]
+    chosen_name = min(ok, key=lambda k: forms[k]["seconds"]) if ok else "mixed"
+    chosen = forms[chosen_name]
+    mixed_dtype = "c64 iterates + c128 replacements" if cplx else "f32 iterates + f64 replacements"
     out = {
         "metric": "snapshot solves + orthonormal basis per second (offline stage, Alg. 1 steps 1-2)",
         "value": round(B / (chosen["seconds"] + t_q), 3), "unit": "snapshots/s", "n_gpus": 1,
-        "higher_is_better": True, "dtype": "c64 iterates + c128 replacements" if cplx else
-        "f32 iterates + f64 replacements", "data": "synthetic",
+        "higher_is_better": True, "chosen": chosen_name,
+        "dtype": mixed_dtype if chosen_name == "mixed" else ("c128" if cplx else "f64"), "data": "synthetic",
         "config": {"workload": f"{args.workload}_offline", "n": n, "snapshots": B, "tol": args.tol,
                    "preconditioner": "diagonal (Jacobi)", "method": "COCG" if cplx else "CG"},
         "krylov": forms,
         "roofline": {"bound": "hbm", "achieved": chosen["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                      "frac": chosen["hbm_frac"], "peak_kind": hbm_kind,
-                     "note": "whole mixed solve, host wall clock, launch gaps and replacements included"},
+                     "note": "whole solve of the chosen form, host wall clock, launch gaps and "
+                             "replacements included"},
         "tsqr": {"seconds": round(t_q, 4), "flops": tsqr_flops,
                  "fp64_tflops": round(tsqr_flops / t_q / 1e12, 4),
                  "fp64_pipe_frac": round(tsqr_flops / t_q / FP64_PEAK, 4),

@@ -59,6 +59,18 @@ def test_argument_checks_without_device(lib):
     assert b"r <= s" in lib.subapsnap_last_error()
     assert lib.subapsnap_solve_batch(None, None, 0, 0, None, None, None, None) == api.SAS_EINVAL
     assert api.subapsnap_version().startswith("subapsnap")
+    # the host-buffer, offline-stage and selection-variant entry points check before any device work
+    assert lib.subapsnap_solve_batch_host(None, None, 4, 0, None, None, None, None) == api.SAS_EINVAL
+    x = np.zeros(8)
+    assert lib.subapsnap_krylov_affine(None, x.ctypes.data, 1, None, 0, 1e-8, 10, None, None) == api.SAS_EINVAL
+    assert lib.subapsnap_krylov_affine(ctypes.byref(d), x.ctypes.data, 0, x.ctypes.data, 0, 1e-8, 10,
+                                       None, None) == api.SAS_EINVAL
+    assert b"B" in lib.subapsnap_last_error()
+    assert lib.subapsnap_tsqr(None, 10, 2, 10, 0, None, 10, None) == api.SAS_EINVAL
+    assert lib.subapsnap_tsqr(x.ctypes.data, 1, 2, 1, 0, x.ctypes.data, 1, None) == api.SAS_EINVAL
+    cnt = ctypes.c_int32()
+    assert lib.subapsnap_select_rows_union_affine(None, None, 1, 1, None, ctypes.byref(cnt)) == api.SAS_EINVAL
+    assert lib.subapsnap_nearest_points(x.ctypes.data, 2, 0, x.ctypes.data, 1, x.ctypes.data) == api.SAS_EINVAL
 
 
 def test_product_path_has_no_oracle_import():
