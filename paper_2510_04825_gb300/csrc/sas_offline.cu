@@ -21,6 +21,7 @@
 // block its parent hands it.  The column signs are fixed so that diag(R) >= 0,
 // which makes Q unique for a full-rank X.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -354,6 +355,175 @@ __global__ void __launch_bounds__(kThreads) product_kernel(Ops ops, int K, int64
         d = warp_sum(d);  // in the storage arithmetic, widened once per warp
         if (lane == 0) wpart[b * 4 + (warp & 3)] = cvt<T>(d);
       }
+    }
+  }
+  __syncthreads();
+  const int G = gridDim.x;
+  for (int b = threadIdx.x; b < B; b += kThreads)
+    if (act[b]) part[(int64_t)b * G + blockIdx.x] = ((wpart[b * 4] + wpart[b * 4 + 1]) + wpart[b * 4 + 2]) + wpart[b * 4 + 3];
+}
+
+// ---------------------------------------------------------------- merged blocks
+// The K blocks merged into one pattern: row i lists the union of the blocks'
+// column indices (each block's row sorted, no repeats), with K values per
+// stored entry (zero where a block has none).  The product then gathers each x
+// entry once for all K blocks; per column the entry's coefficient
+// sum_k theta_k v_k costs K multiply-adds, against one gather per block
+// without merging.
+
+// per row: the number of distinct columns; *bad set when a block row is unsorted
+// or repeats a column (the product then keeps the blocks apart)
+__global__ void merge_count_kernel(Ops ops, int K, int64_t n, int* cnt, int* bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t cur[SAS_MAX_TERMS], end[SAS_MAX_TERMS];
+    for (int k = 0; k < K; ++k) {
+      cur[k] = ops.rp[k][i];
+      end[k] = ops.rp[k][i + 1];
+      for (int64_t e = cur[k] + 1; e < end[k]; ++e)
+        if (ops.ci[k][e] <= ops.ci[k][e - 1]) atomicExch(bad, 1);
+    }
+    int count = 0;
+    for (;;) {
+      int cmin = INT_MAX;
+      for (int k = 0; k < K; ++k)
+        if (cur[k] < end[k] && ops.ci[k][cur[k]] < cmin) cmin = ops.ci[k][cur[k]];
+      if (cmin == INT_MAX) break;
+      ++count;
+      for (int k = 0; k < K; ++k)
+        while (cur[k] < end[k] && ops.ci[k][cur[k]] <= cmin) ++cur[k];
+    }
+    cnt[i] = count;
+  }
+}
+
+// fills the merged pattern: mci[e], mva[e*K + k] (float32 values)
+__global__ void merge_fill_kernel(Ops ops, int K, int64_t n, const int64_t* mrp, int32_t* mci, float* mva) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t cur[SAS_MAX_TERMS], end[SAS_MAX_TERMS];
+    for (int k = 0; k < K; ++k) {
+      cur[k] = ops.rp[k][i];
+      end[k] = ops.rp[k][i + 1];
+    }
+    int64_t o = mrp[i];
+    for (;;) {
+      int cmin = INT_MAX;
+      for (int k = 0; k < K; ++k)
+        if (cur[k] < end[k] && ops.ci[k][cur[k]] < cmin) cmin = ops.ci[k][cur[k]];
+      if (cmin == INT_MAX) break;
+      mci[o] = cmin;
+      for (int k = 0; k < K; ++k) {
+        float v = 0.0f;
+        if (cur[k] < end[k] && ops.ci[k][cur[k]] == cmin) v = (float)ops.va[k][cur[k]++];
+        mva[o * K + k] = v;
+      }
+      ++o;
+    }
+  }
+}
+
+struct Merged {
+  const int64_t* rp;
+  const int32_t* ci;
+  const float* va;  // K values per entry
+};
+
+constexpr int kStageM = 1024;  // merged entries staged per tile (K values each, at most 4096 values)
+
+// Q = A(theta_b) P over the merged pattern, float32 (TL = float or zf), one quad of
+// columns per pass of a half CTA; otherwise as product_kernel.
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) product_merged_kernel(Merged mg, int K, int64_t n, int B,
+                                                                  const TL* theta, const TL* P, TL* Q,
+                                                                  const Col<T>* st, T* part) {
+  __shared__ int32_t ci_s[kStageM];
+  __shared__ float va_s[4096];
+  __shared__ int rps_s[kTileRows + 1];
+  __shared__ int s_staged, s_nq;
+  __shared__ int qlist[64];
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* wpart = reinterpret_cast<T*>(dyn);
+  int* act = reinterpret_cast<int*>(wpart + (size_t)B * 4);
+  const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+  const int64_t r1 = r0 + kTileRows < n ? r0 + kTileRows : n;
+  const int rows = (int)(r1 - r0);
+  for (int b = threadIdx.x; b < B; b += kThreads) act[b] = st[b].active;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int q = 0; 4 * q < B; ++q) {
+      bool any = false;
+      for (int j = 0; j < 4 && 4 * q + j < B; ++j) any = any || act[4 * q + j];
+      if (any) qlist[m++] = q;
+    }
+    s_nq = m;
+    const int64_t cnt = mg.rp[r1] - mg.rp[r0];
+    s_staged = cnt <= kStageM && cnt * K <= 4096;
+  }
+  __syncthreads();
+  if (s_nq == 0) return;
+  const bool staged = s_staged;
+  const int64_t base = mg.rp[r0];
+  if (staged) {
+    const int cnt = (int)(mg.rp[r1] - base);
+    for (int e = threadIdx.x; e < cnt; e += kThreads) ci_s[e] = mg.ci[base + e];
+    for (int e = threadIdx.x; e < cnt * K; e += kThreads) va_s[e] = mg.va[base * K + e];
+    for (int j = threadIdx.x; j <= rows; j += kThreads) rps_s[j] = (int)(mg.rp[r0 + j] - base);
+  }
+  __syncthreads();
+  const int half = threadIdx.x >> 7, t = threadIdx.x & 127;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = r0 + t;
+  const bool valid = t < rows;
+  const int nq = s_nq;
+  for (int g = half; g < nq; g += 2) {
+    const int qa = qlist[g];
+    const TL* xp = P + (int64_t)qa * n * 4;
+    TL th[SAS_MAX_TERMS][4];
+#pragma unroll
+    for (int k = 0; k < SAS_MAX_TERMS; ++k) {
+      Quad<TL> tq;
+      if (k < K) tq = ldq<TL>(theta + ((int64_t)qa * K + k) * 4);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) th[k][j] = k < K ? tq.v[j] : zero<TL>();
+    }
+    Quad<TL> acc;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc.v[j] = zero<TL>();
+    if (valid) {
+      const int64_t e0 = staged ? rps_s[t] : mg.rp[i] - base;
+      const int64_t e1 = staged ? rps_s[t + 1] : mg.rp[i + 1] - base;
+      for (int64_t e = e0; e < e1; ++e) {
+        const int c = staged ? ci_s[e] : mg.ci[base + e];
+        const float* v = staged ? va_s + e * K : mg.va + (base + e) * K;
+        const Quad<TL> x = ldq<TL>(xp + (int64_t)c * 4);
+        TL coef[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) coef[j] = zero<TL>();
+#pragma unroll
+        for (int k = 0; k < SAS_MAX_TERMS; ++k) {
+          if (k >= K) break;
+          const float vk = v[k];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) coef[j] += rscale(vk, th[k][j]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc.v[j] += coef[j] * x.v[j];
+      }
+    }
+    Quad<TL> xi;
+    if (valid) {
+      stq<TL>(Q + ((int64_t)qa * n + i) * 4, acc);
+      xi = ldq<TL>(xp + i * 4);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = 4 * qa + j;
+      if (b >= B || !act[b]) continue;  // uniform
+      TL d = valid ? xi.v[j] * acc.v[j] : zero<TL>();
+      d = warp_sum(d);
+      if (lane == 0) wpart[b * 4 + (warp & 3)] = cvt<T>(d);
     }
   }
   __syncthreads();
@@ -916,6 +1086,14 @@ struct DevBuf {
   template <typename U> U* as() const { return reinterpret_cast<U*>(p); }
 };
 
+// the merged product exists for float32 iterates only
+template <typename T, typename TL>
+void launch_product_merged(const off::Merged& mg, int K, int64_t n, int B, const TL* theta, const TL* P, TL* Q,
+                           const Col<T>* st, T* part, int Gt, size_t smem, cudaStream_t s) {
+  if constexpr (sizeof(TL) < sizeof(T))
+    off::product_merged_kernel<T, TL><<<Gt, kThreads, smem, s>>>(mg, K, n, B, theta, P, Q, st, part);
+}
+
 template <typename T, typename TL>
 sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T* X, bool warm,
                     bool mixed, double tol, int32_t maxit, int32_t* iters_out, double* relres_out) {
@@ -1007,6 +1185,52 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
       }
     }
   if (e != cudaSuccess) return cuda_fail(e, "krylov: float copies of the blocks");
+  // float32 iterates: merge the blocks into one pattern when they overlap enough that
+  // gathering each x entry once for all blocks saves work
+  DevBuf mcnt, mbad, mrp, mci, mva;
+  off::Merged mg{nullptr, nullptr, nullptr};
+  if (mixed && K > 1) {
+    e = mcnt.alloc((size_t)n * sizeof(int));
+    if (e == cudaSuccess) e = mbad.alloc(sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(mbad.p, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+      off::merge_count_kernel<<<sms * 4, kThreads, 0, s>>>(ops, K, n, mcnt.as<int>(), mbad.as<int>());
+      e = cudaGetLastError();
+    }
+    std::vector<int> cnt_h((size_t)n);
+    int bad_m = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cnt_h.data(), mcnt.p, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad_m, mbad.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "krylov: merged pattern");
+    int64_t nnz_sum = 0;
+    for (int k = 0; k < K; ++k) {
+      int64_t v = 0;
+      e = cudaMemcpy(&v, d->rowptr[k] + n, sizeof(int64_t), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(e, "krylov: block sizes");
+      nnz_sum += v;
+    }
+    std::vector<int64_t> rp_h((size_t)n + 1);
+    rp_h[0] = 0;
+    for (int64_t i = 0; i < n; ++i) rp_h[(size_t)i + 1] = rp_h[(size_t)i] + cnt_h[(size_t)i];
+    const int64_t nnz_m = rp_h[(size_t)n];
+    if (!bad_m && nnz_m > 0 && 2 * nnz_sum >= 3 * nnz_m) {
+      e = mrp.alloc(rp_h.size() * sizeof(int64_t));
+      if (e == cudaSuccess) e = mci.alloc((size_t)nnz_m * sizeof(int32_t));
+      if (e == cudaSuccess) e = mva.alloc((size_t)nnz_m * K * sizeof(float));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mrp.p, rp_h.data(), rp_h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) {
+        off::merge_fill_kernel<<<sms * 4, kThreads, 0, s>>>(ops, K, n, mrp.as<int64_t>(), mci.as<int32_t>(),
+                                                            mva.as<float>());
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // rp_h leaves scope
+      if (e != cudaSuccess) return cuda_fail(e, "krylov: merged pattern");
+      mg = off::Merged{mrp.as<int64_t>(), mci.as<int32_t>(), mva.as<float>()};
+    }
+  }
+  const size_t merged_smem = (size_t)B * 4 * sizeof(T) + (size_t)B * sizeof(int);
   e = cudaMemcpyAsync(theta.p, th_h.data(), th_h.size() * sizeof(T), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(theta_lo.p, thl_h.data(), thl_h.size() * sizeof(TL), cudaMemcpyHostToDevice, s);
@@ -1052,8 +1276,12 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: capture");
   for (int it = 0; it < chunk; ++it) {
-    k_lo<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta_lo.as<TL>(), P.as<TL>(), Q.as<TL>(), st.as<Col<T>>(),
-                                         ppq.as<T>());
+    if (mg.rp)
+      launch_product_merged<T, TL>(mg, K, n, B, theta_lo.as<TL>(), P.as<TL>(), Q.as<TL>(), st.as<Col<T>>(),
+                                   ppq.as<T>(), Gt, merged_smem, s);
+    else
+      k_lo<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta_lo.as<TL>(), P.as<TL>(), Q.as<TL>(),
+                                           st.as<Col<T>>(), ppq.as<T>());
     off::alpha_kernel<T><<<B, kThreads, 0, s>>>(ppq.as<T>(), Gt, st.as<Col<T>>());
     off::update_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, Xl.as<TL>(), R.as<TL>(), P.as<TL>(), Q.as<TL>(),
                                                          invD.as<TL>(), st.as<Col<T>>(), prz.as<T>(),
