@@ -9,17 +9,20 @@
 // matrix this is plain CG), preconditioned by the diagonal of A(p_j).  The
 // batch runs every column at once: column j has its own theta(p_j), scalars
 // alpha_j, beta_j and stopping test, and one launch of each kernel covers all
-// active columns.  The same routine refines any start vector, e.g. the
-// SubApSnap output x_hat, which Sec. 3.2 names as the initial guess of an
-// outer Krylov solve when x_hat is not accurate enough.
+// active columns.  Convergence is declared on the float64 true residual only.
+// In the mixed form the iterates are float32 and the residual is replaced by
+// the float64 true one whenever it has fallen 10x.  The same routine refines
+// any start vector, e.g. the SubApSnap output x_hat, which Sec. 3.2 names as
+// the initial guess of an outer Krylov solve when x_hat is not accurate
+// enough.
 //
-// Orthonormalisation.  The snapshot matrices are very ill conditioned (the
-// point of Sec. 4: their singular values decay fast), so Cholesky-based QR is
-// out and the basis comes from TSQR: Householder QR of row panels held in
-// shared memory, then of stacks of g of their R factors, level by level up a
-// tree, and Q formed top-down by applying each node's reflectors to the r x r
-// block its parent hands it.  The column signs are fixed so that diag(R) >= 0,
-// which makes Q unique for a full-rank X.
+// Orthonormalisation.  The snapshot matrices are very ill conditioned: their
+// singular values decay fast, and condition numbers reach 1e22 on these
+// workloads.  Cholesky-based QR is out, and the basis comes from TSQR:
+// Householder QR of row panels held in shared memory, then of stacks of g of
+// their R factors, level by level up a tree; Q is formed top-down by applying
+// each node's reflectors to the r x r block its parent hands it.  The column
+// signs are fixed so that diag(R) >= 0, which makes Q unique for a full-rank X.
 #include <algorithm>
 #include <climits>
 #include <cmath>
