@@ -316,6 +316,33 @@ sas_status subapsnap_krylov_affine(const sas_affine_desc* desc, const double* pa
                                    void* X, int32_t flags, double tol, int32_t maxit,
                                    int32_t* iters_out, double* relres_out);
 
+/* Preconditioners of subapsnap_krylov_affine_ex. */
+enum { SAS_PRECOND_JACOBI = 0, SAS_PRECOND_POISSON = 1 };
+
+/* SAS_PRECOND_POISSON: M_j = alpha_j L + beta_j I with L the unit-spacing
+ * Dirichlet Laplacian of an nx x ny x nz grid (the sum over the axes of
+ * tridiag(-1, 2, -1)), point i = ix + nx (iy + ny iz).  M_j^-1 is applied
+ * exactly by the discrete sine transform along each axis (dense float32
+ * transforms on the tensor cores).  For the 2-D diffusion family A(p) =
+ * A_0 + sum p_k A_k with A_0 = h^-2 L, alpha = h^-2 and beta = 0 make A_0 the
+ * preconditioner; for the transfer function i omega E - A_0 with
+ * A_0 = -h^-2 L, alpha = h^-2 and beta = i omega mean(E). */
+typedef struct {
+  int32_t kind;        /* SAS_PRECOND_* */
+  int32_t ndim;        /* POISSON: 1, 2 or 3 axes */
+  int64_t dims[3];     /* POISSON: grid size per axis (each <= 8192), product = n */
+  const double* coef;  /* POISSON: host, B x 4 doubles per column:
+                          alpha_re, alpha_im, beta_re, beta_im (imaginary parts 0 for real data) */
+} sas_krylov_precond;
+
+/* subapsnap_krylov_affine with a choice of preconditioner (NULL = Jacobi).
+ * Errors: as subapsnap_krylov_affine; SAS_EINVAL for a grid that does not
+ * have n points, an axis above 8192 or complex coefficients on real data. */
+sas_status subapsnap_krylov_affine_ex(const sas_affine_desc* desc, const double* params, int32_t B,
+                                      void* X, int32_t flags, double tol, int32_t maxit,
+                                      const sas_krylov_precond* precond, int32_t* iters_out,
+                                      double* relres_out);
+
 /* Thin QR X = Q R of a tall n x r matrix on the device by TSQR (Alg. 1 step
  * 2: an orthonormal basis Q of the snapshots' range): Householder QR of row
  * panels in shared memory and of stacks of their R factors up a reduction

@@ -37,7 +37,7 @@ EXPORTED = [
     "subapsnap_multi_plan_create", "subapsnap_multi_plan_launch", "subapsnap_multi_plan_destroy",
     "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine", "subapsnap_sample_rows_leverage",
     "subapsnap_select_rows_union_affine", "subapsnap_nearest_points", "subapsnap_krylov_affine",
-    "subapsnap_tsqr", "subapsnap_solve_batch_host",
+    "subapsnap_tsqr", "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
@@ -45,6 +45,7 @@ SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL, SAS_OPT_LS_VARIANT
 SAS_OPT_ASSEMBLY_KERNEL, SAS_OPT_ASSEMBLY_SEGMENT, SAS_OPT_RECON_STORE = 4, 5, 6
 SAS_MAX_VARIANTS = 32
 SAS_KRYLOV_WARM, SAS_KRYLOV_MIXED = 1, 2
+SAS_PRECOND_JACOBI, SAS_PRECOND_POISSON = 0, 1
 SAS_NOALLOC_MAX_Y = 65536
 SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL, SAS_KERNEL_ASSEMBLE = 0, 1, 2, 3
 
@@ -53,6 +54,11 @@ class SasError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"subapsnap error {code}: {msg}")
         self.code = code
+
+
+class KrylovPrecond(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("ndim", ctypes.c_int32), ("dims", ctypes.c_int64 * 3),
+                ("coef", ctypes.c_void_p)]
 
 
 class AffineDesc(ctypes.Structure):
@@ -137,6 +143,8 @@ def lib() -> ctypes.CDLL:
                                               i32, vp, vp]
         L.subapsnap_tsqr.argtypes = [vp, i64, i32, i64, i32, vp, i64, vp]
         L.subapsnap_solve_batch_host.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
+        L.subapsnap_krylov_affine_ex.argtypes = [ctypes.POINTER(AffineDesc), vp, i32, vp, i32, ctypes.c_double,
+                                                 i32, ctypes.POINTER(KrylovPrecond), vp, vp]
         for name in ("subapsnap_setup_affine", "subapsnap_setup_kernel", "subapsnap_solve_batch",
                      "subapsnap_residual", "subapsnap_true_residual", "subapsnap_select_rows_affine",
                      "subapsnap_device_status", "subapsnap_set_tracing", "subapsnap_trace_read",
@@ -149,7 +157,7 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine",
                      "subapsnap_sample_rows_leverage", "subapsnap_select_rows_union_affine",
                      "subapsnap_nearest_points", "subapsnap_krylov_affine", "subapsnap_tsqr",
-                     "subapsnap_solve_batch_host"):
+                     "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -321,17 +329,31 @@ def subapsnap_nearest_points(params, points) -> np.ndarray:
 
 
 def subapsnap_krylov_affine(desc: AffineDesc, params, X, warm: bool = False, tol: float = 1e-12,
-                            maxit: int = 20000, allow_noconv: bool = False, mixed: bool = False):
+                            maxit: int = 20000, allow_noconv: bool = False, mixed: bool = False,
+                            precond=None):
     """Batched snapshot solves A(p_j) x_j = b.  X: CUDA tensor (B, n), row j = x_j
-    (the column-major n x B matrix).  Returns (iterations, true relative residuals)."""
+    (the column-major n x B matrix).  precond: None (Jacobi) or a dict with keys
+    "dims" (grid sizes) and "coef" (B x 4: alpha re/im, beta re/im) for the fast
+    Poisson preconditioner.  Returns (iterations, true relative residuals)."""
     flags = (SAS_KRYLOV_WARM if warm else 0) | (SAS_KRYLOV_MIXED if mixed else 0)
     P = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64)))
     B = int(X.shape[0])
     it = np.zeros(B, dtype=np.int32)
     rel = np.zeros(B, dtype=np.float64)
-    code = lib().subapsnap_krylov_affine(ctypes.byref(desc), P.ctypes.data_as(ctypes.c_void_p), B, _ptr(X),
-                                         flags, float(tol), int(maxit),
-                                         it.ctypes.data_as(ctypes.c_void_p), rel.ctypes.data_as(ctypes.c_void_p))
+    pc = None
+    if precond is not None:
+        coef = np.ascontiguousarray(np.asarray(precond["coef"], dtype=np.float64).reshape(B, 4))
+        dims = list(precond["dims"])
+        pc = KrylovPrecond()
+        pc.kind, pc.ndim = SAS_PRECOND_POISSON, len(dims)
+        for a, v in enumerate(dims):
+            pc.dims[a] = int(v)
+        pc.coef = coef.ctypes.data
+        pc._coef_keep = coef
+    code = lib().subapsnap_krylov_affine_ex(ctypes.byref(desc), P.ctypes.data_as(ctypes.c_void_p), B, _ptr(X),
+                                            flags, float(tol), int(maxit),
+                                            ctypes.byref(pc) if pc is not None else None,
+                                            it.ctypes.data_as(ctypes.c_void_p), rel.ctypes.data_as(ctypes.c_void_p))
     if not (allow_noconv and code == SAS_ENOCONV):
         _check(code)
     return it, rel

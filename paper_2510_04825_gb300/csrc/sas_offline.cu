@@ -32,6 +32,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "sas_internal.cuh"
 
 namespace sas {
@@ -640,7 +642,8 @@ __device__ inline T column_sum(const T* part, int b, int G, T* red) {
 // columns flagged for replacement, which then get beta from the new rz.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) replace_kernel(const T* prz, const double* prr, int G, double bnorm,
-                                                           double tol, int maxit, int start, Col<T>* st) {
+                                                           double tol, int maxit, int start, int defer,
+                                                           Col<T>* st) {
   __shared__ T red[kThreads / 32];
   __shared__ double redd[kThreads / 32];
   const int b = blockIdx.x;
@@ -664,7 +667,7 @@ __global__ void __launch_bounds__(kThreads) replace_kernel(const T* prz, const d
       c.nrel += 1;
       c.nstag = c.relres > 0.5 * prev ? c.nstag + 1 : 0;
     }
-    if (!(c.relres == c.relres) || !finitev(rz)) {
+    if (!(c.relres == c.relres) || (!defer && !finitev(rz))) {
       c.status = 2;
       c.active = 0;
     } else if (c.relres <= tol) {
@@ -676,6 +679,8 @@ __global__ void __launch_bounds__(kThreads) replace_kernel(const T* prz, const d
     } else if (c.iters >= maxit) {
       c.status = 3;
       c.active = 0;
+    } else if (defer) {
+      // rz and beta come after the preconditioner (rz_kernel)
     } else if (start) {
       c.beta = zero<T>();
     } else if (absq(c.rz) == 0.0) {
@@ -684,7 +689,7 @@ __global__ void __launch_bounds__(kThreads) replace_kernel(const T* prz, const d
     } else {
       c.beta = divv(rz, c.rz);
     }
-    c.rz = rz;
+    if (!defer) c.rz = rz;
     st[b] = c;
   }
 }
@@ -712,7 +717,7 @@ __global__ void __launch_bounds__(kThreads) alpha_kernel(const T* ppq, int G, Co
 template <typename T>
 __global__ void __launch_bounds__(kThreads) beta_kernel(const T* prz, const double* prr, int G,
                                                         double bnorm, double tol, double delta, int maxit,
-                                                        Col<T>* st) {
+                                                        int defer, Col<T>* st) {
   __shared__ T red[kThreads / 32];
   __shared__ double redd[kThreads / 32];
   const int b = blockIdx.x;
@@ -723,11 +728,13 @@ __global__ void __launch_bounds__(kThreads) beta_kernel(const T* prz, const doub
     Col<T> c = st[b];
     c.iters += 1;
     c.relres = sqrt(rr) / bnorm;
-    if (!(c.relres == c.relres) || !finitev(rz)) {
+    if (!(c.relres == c.relres) || (!defer && !finitev(rz))) {
       c.status = 2;
       c.active = 0;
     } else if (c.relres <= tol || c.relres < delta * c.rmax || c.iters >= maxit) {
       c.upd = 1;  // rz and beta come from the true residual
+    } else if (defer) {
+      // rz and beta come after the preconditioner (rz_kernel)
     } else if (absq(c.rz) == 0.0) {
       c.status = 2;
       c.active = 0;
@@ -860,6 +867,185 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(int64_t n, int B, c
 #pragma unroll
     for (int j = 0; j < 4; ++j)
       if ((on >> j) & 1) p.v[j] = d.v[j] * r.v[j] + beta[j] * p.v[j];
+    stq<TL>(P + o, p);
+  }
+}
+
+// ------------------------------------------------- fast Poisson preconditioner
+// M_b = alpha_b L + beta_b I with L the unit-spacing Dirichlet Laplacian of an
+// nx x ny x nz grid (sum over the axes of tridiag(-1, 2, -1)), i = ix + nx (iy + ny iz).
+// The discrete sine transform (DST-I) diagonalises L: with S_N[j][k] =
+// sin(pi (j+1)(k+1) / (N+1)), S_N S_N = (N+1)/2 I and S_N T_N S_N = (N+1)/2 diag(mu),
+// mu_j = 2 - 2 cos(pi (j+1) / (N+1)).  So M_b^-1 r = c S (S r ./ (alpha_b (mu_x + mu_y + mu_z)
+// + beta_b)) with c = prod 2/(N+1) and S the tensor product of the axes' S_N.  The
+// transforms are dense matrix products along each axis (library GEMMs, float32
+// accuracy); the kernels here build the matrices and eigenvalues, move data
+// between the quad layout and planar float32 columns, and scale.
+
+__global__ void dst_matrix_kernel(int N, float* S, float* mu) {
+  const int64_t NN = (int64_t)N * N;
+  const double pi = 3.14159265358979323846;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < NN;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = idx % N, k = idx / N;
+    const int64_t a = ((j + 1) * (k + 1)) % (2 * (int64_t)(N + 1));  // sin has period 2(N+1) in a
+    S[idx] = (float)sin(pi * (double)a / (double)(N + 1));
+    if (k == 0) mu[j] = (float)(2.0 - 2.0 * cos(pi * (double)(j + 1) / (double)(N + 1)));
+  }
+}
+
+// planar float32 columns: plane 0 (real parts) then plane 1 (imaginary parts), column b
+// of plane p at U + (p * B + b) * n
+template <typename TL> __host__ __device__ constexpr bool is_cplx() {
+  return std::is_same<TL, zf>::value || std::is_same<TL, zd>::value;
+}
+template <typename TL> __device__ inline float re_f(TL v);
+template <> __device__ inline float re_f<float>(float v) { return v; }
+template <> __device__ inline float re_f<zf>(zf v) { return v.re; }
+template <> __device__ inline float re_f<double>(double v) { return (float)v; }
+template <> __device__ inline float re_f<zd>(zd v) { return (float)v.re; }
+template <typename TL> __device__ inline float im_f(TL v);
+template <> __device__ inline float im_f<float>(float) { return 0.0f; }
+template <> __device__ inline float im_f<zf>(zf v) { return v.im; }
+template <> __device__ inline float im_f<double>(double) { return 0.0f; }
+template <> __device__ inline float im_f<zd>(zd v) { return (float)v.im; }
+template <typename TL> __device__ inline TL mk_f(float re, float im);
+template <> __device__ inline float mk_f<float>(float re, float) { return re; }
+template <> __device__ inline zf mk_f<zf>(float re, float im) { return mkzf(re, im); }
+template <> __device__ inline double mk_f<double>(float re, float) { return (double)re; }
+template <> __device__ inline zd mk_f<zd>(float re, float im) { return mkz((double)re, (double)im); }
+
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) unpack_kernel(int64_t n, int B, const TL* R, float* U, const Col<T>* st,
+                                                          int64_t rows_per_cta) {
+  const int q = blockIdx.x;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  const bool cplx = is_cplx<TL>();
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const Quad<TL> r = ldq<TL>(R + ((int64_t)q * n + i) * 4);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!((on >> j) & 1)) continue;
+      const int b = 4 * q + j;
+      U[(int64_t)b * n + i] = re_f<TL>(r.v[j]);
+      if (cplx) U[((int64_t)B + b) * n + i] = im_f<TL>(r.v[j]);
+    }
+  }
+}
+
+// U_b(i) /= alpha_b (mu_x[ix] + mu_y[iy] + mu_z[iz]) + beta_b, times c; coef is B x 4
+// (alpha re, im, beta re, im) on the device
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) poisson_scale_kernel(int64_t nx, int64_t ny, int64_t nz, int B,
+                                                                 float* U, const float* mux, const float* muy,
+                                                                 const float* muz, const double* coef, double c,
+                                                                 const Col<T>* st) {
+  const int b = blockIdx.y;
+  if (!st[b].active) return;
+  const bool cplx = is_cplx<TL>();
+  const int64_t n = nx * ny * nz;
+  const double ar = coef[4 * b], ai = coef[4 * b + 1], br = coef[4 * b + 2], bi = coef[4 * b + 3];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = i % nx, iy = (i / nx) % ny, iz = i / (nx * ny);
+    const double lam = (double)mux[ix] + (double)muy[iy] + (double)muz[iz];
+    const double dr = ar * lam + br, di = ai * lam + bi;
+    const double den = dr * dr + di * di;
+    float* ur = U + (int64_t)b * n + i;
+    if (cplx) {
+      float* ui = U + ((int64_t)B + b) * n + i;
+      const double xr = *ur, xi = *ui;
+      *ur = (float)(c * (xr * dr + xi * di) / den);
+      *ui = (float)(c * (xi * dr - xr * di) / den);
+    } else {
+      *ur = (float)(c * (double)*ur * dr / den);
+    }
+  }
+}
+
+// Z (quad layout) = the planar result; partials of r^T z per column (bilinear)
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) pack_rz_kernel(int64_t n, int B, const float* U, const TL* R, TL* Z,
+                                                           const Col<T>* st, T* prz, int64_t rows_per_cta) {
+  __shared__ T red[kThreads / 32][4];
+  const int q = blockIdx.x, G = gridDim.y;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  const bool cplx = is_cplx<TL>();
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  TL rz[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) rz[j] = zero<TL>();
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    const Quad<TL> r = ldq<TL>(R + o);
+    Quad<TL> z = ldq<TL>(Z + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!((on >> j) & 1)) continue;
+      const int b = 4 * q + j;
+      z.v[j] = mk_f<TL>(U[(int64_t)b * n + i], cplx ? U[((int64_t)B + b) * n + i] : 0.0f);
+      rz[j] += r.v[j] * z.v[j];
+    }
+    stq<TL>(Z + o, z);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const TL a = warp_sum(rz[j]);
+    if (lane == 0) red[w][j] = cvt<T>(a);
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && ((on >> threadIdx.x) & 1)) {
+    const int j = threadIdx.x;
+    T a = zero<T>();
+    for (int k = 0; k < kThreads / 32; ++k) a += red[k][j];
+    prz[(int64_t)(4 * q + j) * G + blockIdx.y] = a;
+  }
+}
+
+// beta from the preconditioned residual: rz = r^T M^-1 r (start: beta = 0)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) rz_kernel(const T* prz, int G, int start, Col<T>* st) {
+  __shared__ T red[kThreads / 32];
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  const T rz = column_sum(prz, b, G, red);
+  if (threadIdx.x == 0) {
+    Col<T> c = st[b];
+    if (!finitev(rz) || (!start && absq(c.rz) == 0.0)) {
+      c.status = 2;
+      c.active = 0;
+    } else {
+      c.beta = start ? zero<T>() : divv(rz, c.rz);
+      c.rz = rz;
+    }
+    st[b] = c;
+  }
+}
+
+// P = Z + beta P
+template <typename T, typename TL>
+__global__ void __launch_bounds__(kThreads) direction_z_kernel(int64_t n, int B, const TL* Z, TL* P,
+                                                               const Col<T>* st, int64_t rows_per_cta) {
+  const int q = blockIdx.x;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  TL beta[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) beta[j] = (on >> j) & 1 ? cvt<TL>(st[4 * q + j].beta) : zero<TL>();
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    const Quad<TL> z = ldq<TL>(Z + o);
+    Quad<TL> p = ldq<TL>(P + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((on >> j) & 1) p.v[j] = z.v[j] + beta[j] * p.v[j];
     stq<TL>(P + o, p);
   }
 }
@@ -1097,9 +1283,46 @@ void launch_product_merged(const off::Merged& mg, int K, int64_t n, int B, const
     off::product_merged_kernel<T, TL><<<Gt, kThreads, smem, s>>>(mg, K, n, B, theta, P, Q, st, part);
 }
 
+// The fast Poisson preconditioner's state: DST matrices and eigenvalues per axis,
+// planar work buffers, the per-column coefficients and a cuBLAS handle whose
+// workspace is fixed so that its GEMMs can be captured in the iteration graph.
+struct PoissonPre {
+  int ndim = 0;
+  int64_t N[3] = {1, 1, 1};
+  cublasHandle_t h = nullptr;
+  cublasComputeType_t ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
+  DevBuf S[3], mu[3], U, W, coef, ws;
+  PoissonPre() = default;
+  PoissonPre(const PoissonPre&) = delete;
+  PoissonPre& operator=(const PoissonPre&) = delete;
+  ~PoissonPre() {
+    if (h) cublasDestroy(h);
+  }
+};
+
+// one axis of the separable transform, out = in transformed along axis a, for C planar columns
+cublasStatus_t dst_axis(PoissonPre& pp, int a, int64_t C, const float* in, float* out) {
+  const float one = 1.0f, zero = 0.0f;
+  const int64_t nx = pp.N[0], ny = pp.N[1], nz = pp.N[2], n = nx * ny * nz;
+  const float* Sa = pp.S[a].as<float>();
+  if (a == 0)  // S_x (nx x nx) times the nx x (n / nx * C) matrix of all columns
+    return cublasGemmEx(pp.h, CUBLAS_OP_N, CUBLAS_OP_N, (int)nx, (int)(n / nx * C), (int)nx, &one, Sa, CUDA_R_32F,
+                        (int)nx, in, CUDA_R_32F, (int)nx, &zero, out, CUDA_R_32F, (int)nx, pp.ct, CUBLAS_GEMM_DEFAULT);
+  if (a == 1)  // every nx x ny slab times S_y
+    return cublasGemmStridedBatchedEx(pp.h, CUBLAS_OP_N, CUBLAS_OP_N, (int)nx, (int)ny, (int)ny, &one, in,
+                                      CUDA_R_32F, (int)nx, nx * ny, Sa, CUDA_R_32F, (int)ny, 0, &zero, out,
+                                      CUDA_R_32F, (int)nx, nx * ny, (int)(nz * C), pp.ct, CUBLAS_GEMM_DEFAULT);
+  // every column's (nx ny) x nz matrix times S_z
+  return cublasGemmStridedBatchedEx(pp.h, CUBLAS_OP_N, CUBLAS_OP_N, (int)(nx * ny), (int)nz, (int)nz, &one, in,
+                                    CUDA_R_32F, (int)(nx * ny), n, Sa, CUDA_R_32F, (int)nz, 0, &zero, out,
+                                    CUDA_R_32F, (int)(nx * ny), n, (int)C, pp.ct, CUBLAS_GEMM_DEFAULT);
+}
+
 template <typename T, typename TL>
 sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T* X, bool warm,
-                    bool mixed, double tol, int32_t maxit, int32_t* iters_out, double* relres_out) {
+                    bool mixed, double tol, int32_t maxit, const sas_krylov_precond* pc, int32_t* iters_out,
+                    double* relres_out) {
+  const bool poisson = pc && pc->kind == SAS_PRECOND_POISSON;
   const int64_t n = d->n;
   const int K = d->K;
   const int dp = d->theta_rule == SAS_THETA_PENCIL ? 1 : d->theta_rule == SAS_THETA_DELAY ? 2 : K - 1;
@@ -1259,16 +1482,78 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   if (e == cudaSuccess) e = cudaMemcpyAsync(nb_h.data(), nb.p, nb_h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: start");
-  if (bad_h) return fail_off(SAS_EINVAL, "krylov: A(p) has a zero (or non-finite) diagonal entry; "
-                                         "the Jacobi preconditioner needs a non-zero diagonal");
+  if (bad_h && !poisson)
+    return fail_off(SAS_EINVAL, "krylov: A(p) has a zero (or non-finite) diagonal entry; "
+                                "the Jacobi preconditioner needs a non-zero diagonal");
   double bn2 = 0.0;
   for (double v : nb_h) bn2 += v;
   const double bnorm = std::sqrt(bn2);
   if (!(bnorm > 0.0)) return fail_off(SAS_EINVAL, "krylov: b = 0");
-  off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 1,
+
+  // fast Poisson preconditioner: z = M^-1 r for every active column, written to Q (free between
+  // the update and the next product), with the partial sums of r^T z
+  PoissonPre pp;
+  const int64_t Cpl = (int64_t)B * (off::is_cplx<T>() ? 2 : 1);  // planar float32 columns
+  if (poisson) {
+    pp.ndim = pc->ndim;
+    for (int a = 0; a < 3; ++a) pp.N[a] = a < pc->ndim ? pc->dims[a] : 1;
+    for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
+      const int64_t Na = pp.N[a];
+      e = pp.S[a].alloc((size_t)Na * Na * sizeof(float));
+      if (e == cudaSuccess) e = pp.mu[a].alloc((size_t)Na * sizeof(float));
+      if (e == cudaSuccess && a < pp.ndim)
+        off::dst_matrix_kernel<<<sms * 2, kThreads, 0, s>>>((int)Na, pp.S[a].as<float>(), pp.mu[a].as<float>());
+      else if (e == cudaSuccess)
+        e = cudaMemsetAsync(pp.mu[a].p, 0, sizeof(float), s);  // an absent axis adds nothing to L
+    }
+    if (e == cudaSuccess) e = pp.U.alloc((size_t)Cpl * n * sizeof(float));
+    if (e == cudaSuccess) e = pp.W.alloc((size_t)Cpl * n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(pp.U.p, 0, (size_t)Cpl * n * sizeof(float), s);
+    if (e == cudaSuccess) e = pp.coef.alloc((size_t)B * 4 * sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(pp.coef.p, pc->coef, (size_t)B * 4 * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = pp.ws.alloc((size_t)32 << 20);
+    if (e != cudaSuccess) return cuda_fail(e, "krylov: preconditioner buffers");
+    if (cublasCreate(&pp.h) != CUBLAS_STATUS_SUCCESS || cublasSetStream(pp.h, s) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetWorkspace(pp.h, pp.ws.p, (size_t)32 << 20) != CUBLAS_STATUS_SUCCESS)
+      return fail_off(SAS_ECUDA, "krylov: cuBLAS handle");
+  }
+  double pc_scale = 1.0;
+  for (int a = 0; a < pp.ndim; ++a) pc_scale *= 2.0 / (double)(pp.N[a] + 1);
+  auto precondition = [&]() -> bool {
+    off::unpack_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, R.as<TL>(), pp.U.as<float>(), st.as<Col<T>>(), rpc);
+    float* cur = pp.U.as<float>();
+    float* oth = pp.W.as<float>();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int a = 0; a < pp.ndim; ++a) {
+        if (dst_axis(pp, a, Cpl, cur, oth) != CUBLAS_STATUS_SUCCESS) return false;
+        std::swap(cur, oth);
+      }
+      if (pass == 0)
+        off::poisson_scale_kernel<T, TL><<<dim3(sms * 2, B), kThreads, 0, s>>>(
+            pp.N[0], pp.N[1], pp.N[2], B, cur, pp.mu[0].as<float>(), pp.mu[1].as<float>(), pp.mu[2].as<float>(),
+            pp.coef.as<double>(), pc_scale, st.as<Col<T>>());
+    }
+    off::pack_rz_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, cur, R.as<TL>(), Q.as<TL>(), st.as<Col<T>>(),
+                                                          prz.as<T>(), rpc);
+    return true;
+  };
+
+  const int defer = poisson ? 1 : 0;
+  off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 1, defer,
                                                 st.as<Col<T>>());
-  off::direction_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
-                                                          st.as<Col<T>>(), rpc);
+  if (poisson) {
+    // the emulated-float32 tensor-core GEMM where the library has it, plain float32 otherwise
+    if (!precondition()) {
+      pp.ct = CUBLAS_COMPUTE_32F;
+      if (!precondition()) return fail_off(SAS_ECUDA, "krylov: preconditioner GEMM failed");
+    }
+    off::rz_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), G, 1, st.as<Col<T>>());
+    off::direction_z_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, Q.as<TL>(), P.as<TL>(), st.as<Col<T>>(), rpc);
+  } else {
+    off::direction_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
+                                                            st.as<Col<T>>(), rpc);
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "krylov: first direction");
 
@@ -1289,16 +1574,28 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
     off::update_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, Xl.as<TL>(), R.as<TL>(), P.as<TL>(), Q.as<TL>(),
                                                          invD.as<TL>(), st.as<Col<T>>(), prz.as<T>(),
                                                          prr.as<double>(), rpc);
-    off::beta_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, delta, maxit,
+    off::beta_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, delta, maxit, defer,
                                                st.as<Col<T>>());
     off::fold_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, X, Xl.as<TL>(), st.as<Col<T>>(), 0, rpc);
     k_res<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta.as<T>(), X, R.as<TL>(), (const T*)d->b,
                                           invD.as<TL>(), st.as<Col<T>>(), off::kSelUpd, prz.as<T>(),
                                           prr.as<double>());
-    off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 0,
+    off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 0, defer,
                                                   st.as<Col<T>>());
-    off::direction_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
-                                                            st.as<Col<T>>(), rpc);
+    if (poisson) {
+      if (!precondition()) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        return fail_off(SAS_ECUDA, "krylov: preconditioner GEMM failed in capture");
+      }
+      off::rz_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), G, 0, st.as<Col<T>>());
+      off::direction_z_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, Q.as<TL>(), P.as<TL>(), st.as<Col<T>>(),
+                                                                rpc);
+    } else {
+      off::direction_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, R.as<TL>(), invD.as<TL>(), P.as<TL>(),
+                                                              st.as<Col<T>>(), rpc);
+    }
   }
   e = cudaStreamEndCapture(s, &graph);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -1436,9 +1733,9 @@ sas_status tsqr_t(const T* X, int64_t n, int r, int64_t ldx, T* Qout, int64_t ld
 
 using namespace sas;
 
-sas_status subapsnap_krylov_affine(const sas_affine_desc* d, const double* params, int32_t B, void* X,
-                                   int32_t flags, double tol, int32_t maxit, int32_t* iters_out,
-                                   double* relres_out) {
+sas_status subapsnap_krylov_affine_ex(const sas_affine_desc* d, const double* params, int32_t B, void* X,
+                                      int32_t flags, double tol, int32_t maxit, const sas_krylov_precond* pc,
+                                      int32_t* iters_out, double* relres_out) {
   const bool warm = (flags & SAS_KRYLOV_WARM) != 0, mixed = (flags & SAS_KRYLOV_MIXED) != 0;
   if (!d || !params || !X) return fail_off(SAS_EINVAL, "NULL argument");
   if (B < 1 || B > 256) return fail_off(SAS_EINVAL, "need 1 <= B <= 256");
@@ -1453,16 +1750,45 @@ sas_status subapsnap_krylov_affine(const sas_affine_desc* d, const double* param
       d->theta_rule != SAS_THETA_DELAY)
     return fail_off(SAS_EINVAL, "bad theta rule");
   if (!(tol >= 0.0)) return fail_off(SAS_EINVAL, "tol must be >= 0");
+  if (flags & ~(SAS_KRYLOV_WARM | SAS_KRYLOV_MIXED)) return fail_off(SAS_EINVAL, "unknown flag bits");
+  if (pc) {
+    if (pc->kind != SAS_PRECOND_JACOBI && pc->kind != SAS_PRECOND_POISSON)
+      return fail_off(SAS_EINVAL, "unknown preconditioner");
+    if (pc->kind == SAS_PRECOND_POISSON) {
+      if (pc->ndim < 1 || pc->ndim > 3) return fail_off(SAS_EINVAL, "Poisson preconditioner: ndim must be 1, 2 or 3");
+      int64_t prod = 1;
+      for (int a = 0; a < pc->ndim; ++a) {
+        if (pc->dims[a] < 1 || pc->dims[a] > 8192)
+          return fail_off(SAS_EINVAL, "Poisson preconditioner: every axis needs 1 <= N <= 8192");
+        prod *= pc->dims[a];
+      }
+      if (prod != d->n) return fail_off(SAS_EINVAL, "Poisson preconditioner: the grid does not have n points");
+      if (!pc->coef) return fail_off(SAS_EINVAL, "Poisson preconditioner: coef is NULL");
+      for (int b = 0; b < B; ++b) {
+        const double* c = pc->coef + 4 * b;
+        if (!std::isfinite(c[0]) || !std::isfinite(c[1]) || !std::isfinite(c[2]) || !std::isfinite(c[3]))
+          return fail_off(SAS_EINVAL, "Poisson preconditioner: coefficients must be finite");
+        if (d->dtype == SAS_REAL64 && (c[1] != 0.0 || c[3] != 0.0))
+          return fail_off(SAS_EINVAL, "Poisson preconditioner: real data needs real alpha and beta");
+      }
+    }
+  }
   if (!on_device(X) || !on_device(d->b)) return fail_off(SAS_EINVAL, "X and b must be device pointers");
   for (int k = 0; k < d->K; ++k)
     if (!on_device(d->rowptr[k]) || !on_device(d->colind[k]) || !on_device(d->values[k]))
       return fail_off(SAS_EINVAL, "CSR arrays must be device pointers");
-  if (flags & ~(SAS_KRYLOV_WARM | SAS_KRYLOV_MIXED)) return fail_off(SAS_EINVAL, "unknown flag bits");
   if (d->dtype == SAS_COMPLEX128)
-    return mixed ? krylov_t<zd, zf>(d, params, B, (zd*)X, warm, true, tol, maxit, iters_out, relres_out)
-                 : krylov_t<zd, zd>(d, params, B, (zd*)X, warm, false, tol, maxit, iters_out, relres_out);
-  return mixed ? krylov_t<double, float>(d, params, B, (double*)X, warm, true, tol, maxit, iters_out, relres_out)
-               : krylov_t<double, double>(d, params, B, (double*)X, warm, false, tol, maxit, iters_out, relres_out);
+    return mixed ? krylov_t<zd, zf>(d, params, B, (zd*)X, warm, true, tol, maxit, pc, iters_out, relres_out)
+                 : krylov_t<zd, zd>(d, params, B, (zd*)X, warm, false, tol, maxit, pc, iters_out, relres_out);
+  return mixed ? krylov_t<double, float>(d, params, B, (double*)X, warm, true, tol, maxit, pc, iters_out, relres_out)
+               : krylov_t<double, double>(d, params, B, (double*)X, warm, false, tol, maxit, pc, iters_out,
+                                          relres_out);
+}
+
+sas_status subapsnap_krylov_affine(const sas_affine_desc* d, const double* params, int32_t B, void* X,
+                                   int32_t flags, double tol, int32_t maxit, int32_t* iters_out,
+                                   double* relres_out) {
+  return subapsnap_krylov_affine_ex(d, params, B, X, flags, tol, maxit, nullptr, iters_out, relres_out);
 }
 
 sas_status subapsnap_tsqr(const void* X, int64_t n, int32_t r, int64_t ldx, int32_t dtype, void* Q,

@@ -92,8 +92,31 @@ class AffineSolver:
         api.subapsnap_true_residual(self.ctx, params, params.shape[0], X, rho, stream)
 
 
+def poisson_precond(prob, params):
+    """Fast Poisson preconditioner for the grid workloads: M = alpha L + beta I per column.
+
+    2-D diffusion, A(p) = A_0 + sum p_k A_k with A_0 = h^-2 L: alpha = h^-2, beta = 0.
+    Transfer function, A = i omega E - A_0 with A_0 = -h^-2 L: alpha = h^-2,
+    beta = i omega mean(E).  Returns None for the other workloads."""
+    P = np.atleast_2d(np.asarray(params, dtype=np.float64))
+    grid = tuple(getattr(prob, "grid", ()) or ())
+    if prob.name in ("diffusion_2d", "surrogate_diffusion_2d") and len(grid) == 2:
+        h = 1.0 / (grid[0] + 1)
+        coef = np.zeros((P.shape[0], 4))
+        coef[:, 0] = 1.0 / (h * h)
+        return {"dims": grid, "coef": coef}
+    if prob.name == "transfer_function" and len(grid) == 3:
+        h = 1.0 / (grid[0] + 1)
+        ebar = float(prob.blocks[1].diagonal().mean())
+        coef = np.zeros((P.shape[0], 4))
+        coef[:, 0] = 1.0 / (h * h)
+        coef[:, 3] = P[:, 0] * ebar
+        return {"dims": grid, "coef": coef}
+    return None
+
+
 def snapshot_solve(prob, params, X, blocks_device=None, b_device=None, warm=False, tol=1e-12,
-                   maxit=20000, device="cuda", allow_noconv=False, mixed=False):
+                   maxit=20000, device="cuda", allow_noconv=False, mixed=False, precond=None):
     """Batched Krylov solves A(p_j) x_j = b on the device into X (B, n); (iterations, true residuals)."""
     cplx = bool(prob.complex_valued)
     blocks = blocks_device or [csr_to_device(A, device) for A in prob.blocks]
@@ -105,11 +128,11 @@ def snapshot_solve(prob, params, X, blocks_device=None, b_device=None, warm=Fals
                             theta_rule_code(prob.theta_rule), api.SAS_MODE_PLAIN, api.SAS_QOI_NONE,
                             None, cplx)
     return api.subapsnap_krylov_affine(desc, P, X, warm=warm, tol=tol, maxit=maxit,
-                                       allow_noconv=allow_noconv, mixed=mixed)
+                                       allow_noconv=allow_noconv, mixed=mixed, precond=precond)
 
 
 def snapshot_basis(prob, blocks_device=None, b_device=None, params=None, tol=1e-12, maxit=20000,
-                   device="cuda", mixed=False):
+                   device="cuda", mixed=False, precond=None):
     """Offline stage on the device (Alg. 1 steps 1-2): snapshot solves, then TSQR.
 
     Returns (S, info): S is the (r, n) device tensor of the orthonormal basis
@@ -120,7 +143,7 @@ def snapshot_basis(prob, blocks_device=None, b_device=None, params=None, tol=1e-
     P = np.atleast_2d(np.asarray(P, dtype=np.float64))
     X = torch.empty((P.shape[0], prob.n), dtype=torch.complex128 if cplx else torch.float64, device=device)
     it, rel = snapshot_solve(prob, P, X, blocks_device, b_device, tol=tol, maxit=maxit, device=device,
-                             mixed=mixed)
+                             mixed=mixed, precond=precond)
     R = api.subapsnap_tsqr(X)
     return X, {"iters": it, "relres": rel, "R": R}
 

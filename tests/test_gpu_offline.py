@@ -220,3 +220,45 @@ def test_batch_limits_and_single_column():
     with pytest.raises(api.SasError):
         Xb = torch.empty((257, prob.n), dtype=torch.float64, device=DEV)
         snapshot_solve(prob, np.tile(prob.snap_params[:1], (257, 1)), Xb)
+
+
+@pytest.mark.parametrize("mixed", [False, True], ids=["plain", "mixed"])
+@pytest.mark.parametrize("name,kw", [("diffusion_2d", dict(N=48, r=20, s=40, m=4)),
+                                     ("transfer_function", dict(N=9, r=20, s=50, m=4))],
+                         ids=["diffusion_2d", "transfer_function"])
+def test_poisson_preconditioner(name, kw, mixed):
+    """Fast Poisson preconditioner (DST along each axis): same answers as the direct
+    solves, in far fewer iterations than the diagonal preconditioner."""
+    from paper_2510_04825_gb300.solver import poisson_precond
+    prob = get_config(name, **kw)
+    cplx = prob.complex_valued
+    P = prob.snap_params
+    dt = torch.complex128 if cplx else torch.float64
+    tol = 1e-10
+    Xp = torch.empty((len(P), prob.n), dtype=dt, device=DEV)
+    it_p, rel_p = snapshot_solve(prob, P, Xp, tol=tol, mixed=mixed, precond=poisson_precond(prob, P))
+    Xj = torch.empty_like(Xp)
+    it_j, _ = snapshot_solve(prob, P, Xj, tol=tol, mixed=mixed)
+    assert (rel_p <= tol).all()
+    Xg = Xp.cpu().numpy()
+    for j, p in enumerate(P):
+        xo = snapshots.solve_full(prob, p)
+        A = oproblem.full_matrix(prob, p)
+        assert np.linalg.norm(A @ Xg[j] - prob.b) / np.linalg.norm(prob.b) <= 2 * tol
+        assert np.linalg.norm(Xg[j] - xo) / np.linalg.norm(xo) <= 1e-7
+    assert it_p.max() < it_j.max(), (it_p.max(), it_j.max())
+    print(f"{name} {'mixed' if mixed else 'plain'}: Poisson-preconditioned iterations {it_p.min()}..{it_p.max()}, "
+          f"diagonal {it_j.min()}..{it_j.max()}")
+
+
+def test_poisson_preconditioner_arguments():
+    from paper_2510_04825_gb300.solver import poisson_precond
+    prob = get_config("diffusion_2d", N=20, r=3, s=6, m=4)
+    X = torch.empty((3, prob.n), dtype=torch.float64, device=DEV)
+    pc = poisson_precond(prob, prob.snap_params)
+    bad = dict(pc, dims=(20, 21))
+    with pytest.raises(api.SasError):
+        snapshot_solve(prob, prob.snap_params, X, precond=bad)
+    cplx = dict(pc, coef=pc["coef"] + np.array([0, 1.0, 0, 0]))
+    with pytest.raises(api.SasError):
+        snapshot_solve(prob, prob.snap_params, X, precond=cplx)
