@@ -1160,12 +1160,11 @@ __global__ void __launch_bounds__(kThreads) tsqr_panel_kernel(int level0, const 
 // H_1 ... H_r [C_p; 0] (h x r).  One warp per column of C; the column lives
 // in registers (row i = lane + 32 k).  Level 0 writes rows of Q; higher
 // levels write the r x r blocks of their children.
-template <typename T>
+template <typename T, int KM>  // KM >= ceil(h / 32): register chunks of the column, no idle ones
 __global__ void __launch_bounds__(kThreads) tsqr_apply_kernel(int level0, const T* V, int64_t ldv,
                                                               const T* tau, int r, int h, int g,
                                                               const T* Cin, T* out, int64_t ldout,
                                                               int64_t n, int64_t nchild) {
-  constexpr int KM = 16;  // h <= 512
   const int64_t p = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.y * (kThreads / 32) + warp;
@@ -1718,9 +1717,20 @@ sas_status tsqr_t(const T* X, int64_t n, int r, int64_t ldx, T* Qout, int64_t ld
   const dim3 cols_grid(1, (r + kThreads / 32 - 1) / (kThreads / 32));
   for (int l = L - 1; l >= 0; --l) {
     const bool lv0 = l == 0;
-    off::tsqr_apply_kernel<T><<<dim3((unsigned)P[l], cols_grid.y), kThreads, 0, s>>>(
-        lv0 ? 1 : 0, lv0 ? V0.as<T>() : V[l].as<T>(), n, tau[l].as<T>(), r, h, g, Cb[l].as<T>(),
-        lv0 ? Qout : Cb[l - 1].as<T>(), ldq, n, lv0 ? 0 : P[l - 1]);
+    const int kc = (h + 31) / 32;
+    const dim3 ag((unsigned)P[l], cols_grid.y);
+    const T* Vl = lv0 ? V0.as<T>() : V[l].as<T>();
+    T* outl = lv0 ? Qout : Cb[l - 1].as<T>();
+    const int64_t nch = lv0 ? 0 : P[l - 1];
+#define SAS_TSQR_APPLY(KMV) off::tsqr_apply_kernel<T, KMV><<<ag, kThreads, 0, s>>>( \
+        lv0 ? 1 : 0, Vl, n, tau[l].as<T>(), r, h, g, Cb[l].as<T>(), outl, ldq, n, nch)
+    if (kc <= 2) SAS_TSQR_APPLY(2);
+    else if (kc <= 4) SAS_TSQR_APPLY(4);
+    else if (kc <= 6) SAS_TSQR_APPLY(6);
+    else if (kc <= 8) SAS_TSQR_APPLY(8);
+    else if (kc <= 12) SAS_TSQR_APPLY(12);
+    else SAS_TSQR_APPLY(16);
+#undef SAS_TSQR_APPLY
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
