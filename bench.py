@@ -804,6 +804,86 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_selection_variants(args):
+    """The subsampling variants of Sec. 4.3.4 on the headline workload: rows chosen at the
+    median point (the default), the union of the CPQR picks at three snapshot points, and
+    per-parameter rows from the nearest of three points.  Each is timed on the headline
+    step (the float32 form, y of the whole batch then x_hat) and scored by the true
+    residual of its float64 x_hat on 64 parameters.  One JSON line."""
+    import torch
+    from paper_2510_04825_gb300 import api
+    from paper_2510_04825_gb300.solver import AffineSolver, NearestPointSolver, select_rows_union
+
+    torch.cuda.set_device(0)
+    device = "cuda:0"
+    prob, blocks, S_rows, J, gaps, P, params_host, _ = build_inputs(device, 0, args.grid)
+    n = prob.n
+    snaps = prob.snap_params
+    pts = snaps[[0, len(snaps) // 2, len(snaps) - 1]]
+    nearest_idx = None
+    variants = {}
+    Jset = {"median_point": J, "union_3_points": select_rows_union(prob, S_rows, blocks, pts, R)}
+    out32 = torch.empty((M, n), dtype=torch.float32, device=device)
+    Y = torch.empty((M, R), dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def true_residuals(make_plain, Psample):
+        sv = make_plain()
+        X64 = torch.empty((Psample.shape[0], n), dtype=torch.float64, device=device)
+        sv.solve(Psample, api.SAS_OUT_XHAT, X64)
+        tr = torch.empty(Psample.shape[0], dtype=torch.float64, device=device)
+        first = sv.solvers[0] if hasattr(sv, "solvers") else sv
+        first.true_residual(Psample, X64, tr)
+        torch.cuda.synchronize()
+        sv.close()
+        return tr.cpu().numpy()
+
+    for name in ("median_point", "union_3_points", "nearest_of_3_points"):
+        if name == "nearest_of_3_points":
+            mk = lambda mode: NearestPointSolver(prob, None, pts, S_ROWS, mode=mode, device=device,
+                                                 S_device=S_rows, blocks_device=blocks)
+            # group the batch by nearest point (the order of independent parameters is free)
+            nearest_idx = api.subapsnap_nearest_points(params_host, pts)
+            order = np.argsort(nearest_idx, kind="stable")
+            Pv = torch.from_numpy(np.ascontiguousarray(params_host[order])).to(device)
+        else:
+            Jv = Jset[name]
+            mk = lambda mode, Jv=Jv: AffineSolver(prob, None, Jv, mode=mode, device=device, S_device=S_rows,
+                                                  blocks_device=blocks)
+            Pv = P
+        chosen = mk(api.SAS_MODE_MIXED)
+        s_rows = [len(j) for j in chosen.J] if hasattr(chosen, "solvers") else [len(chosen.J)]
+        if not hasattr(chosen, "solvers"):
+            api.subapsnap_autotune(chosen.ctx, Pv, M, 2)
+
+        def step():
+            chosen.solve(Pv, api.SAS_OUT_Y, Y)
+            chosen.reconstruct(Y, out32)
+
+        ms = timed(step, max(3, args.steps // 3), args.warmup)
+        chosen.close()
+        tr = true_residuals(lambda: mk(api.SAS_MODE_PLAIN), Pv[::M // 64].contiguous())
+        variants[name] = {"solves_per_s": round(M / (ms * 1e-3), 1), "ms_per_step": round(ms, 4),
+                          "s": s_rows, "true_rel_residual_max_64": float(tr.max()),
+                          "true_rel_residual_median_64": float(np.median(tr))}
+    if nearest_idx is not None:
+        variants["nearest_of_3_points"]["parameters_per_point"] = np.bincount(nearest_idx, minlength=3).tolist()
+    print(json.dumps({"metric": "subsampling variants (Sec. 4.3.4) on the headline workload",
+                      "config": {"workload": WORKLOAD, "points": pts.tolist()}, "variants": variants}))
+
+
 def run_offline(args):
     """Offline stage (Alg. 1 steps 1-2) on one GPU: the batched snapshot solves of the
     workload's snapshot parameters, then the TSQR basis, with float32 iterates and
@@ -935,6 +1015,8 @@ def main():
                     choices=["diffusion_2d", "transfer_function", "reaction_diffusion_1d", "kernel_ridge",
                              "surrogate_diffusion_2d", "delay_system"])
     ap.add_argument("--epochs", type=int, default=100, help="surrogate training epochs")
+    ap.add_argument("--selection-variants", action="store_true",
+                    help="time the subsampling variants of Sec. 4.3.4 on the headline workload")
     ap.add_argument("--offline", action="store_true",
                     help="time the offline stage (snapshot solves + TSQR) of the workload instead")
     ap.add_argument("--tol", type=float, default=1e-10, help="offline: relative residual of the solves")
@@ -942,6 +1024,8 @@ def main():
     args = ap.parse_args()
     if args.offline:
         run_offline(args)
+    elif args.selection_variants:
+        run_selection_variants(args)
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "surrogate_diffusion_2d":

@@ -205,6 +205,10 @@ class NearestPointSolver:
         for sv in self.solvers:
             sv.close()
 
+    def reconstruct(self, Y, out, stream=None):
+        """x_hat = S y: every point's context holds the same basis."""
+        self.solvers[0].reconstruct(Y, out, stream)
+
     def assign(self, params):
         P = params.detach().cpu().numpy() if hasattr(params, "detach") else np.asarray(params)
         return api.subapsnap_nearest_points(P, self.points)
@@ -214,6 +218,15 @@ class NearestPointSolver:
             with torch.cuda.stream(stream):
                 return self.solve(params, out_kind, out, flags, rho, None)
         idx = self.assign(params)
+        if np.all(np.diff(idx) >= 0):
+            # parameters already grouped by point: every group is a contiguous slice
+            bounds = np.searchsorted(idx, np.arange(len(self.solvers) + 1))
+            for i, sv in enumerate(self.solvers):
+                lo, hi = int(bounds[i]), int(bounds[i + 1])
+                if hi > lo:
+                    sv.solve(params[lo:hi], out_kind, out[lo:hi], None if flags is None else flags[lo:hi],
+                             None if rho is None else rho[lo:hi], stream)
+            return idx
         for i, sv in enumerate(self.solvers):
             sel = np.nonzero(idx == i)[0]
             if sel.size == 0:
