@@ -274,6 +274,13 @@ def test_nearest_point_solver_matches_oracle(c0):
         Yo, rho_o = online_solve(p, c0.S, J, params[g])
         assert rel_err_rows(Y[g], Yo).max() <= 1e-10
         np.testing.assert_allclose(rho.cpu().numpy()[g], rho_o, rtol=1e-6, atol=1e-14)
+    # parameters grouped by point take the slice path: the same answers
+    order = np.argsort(idx_o, kind="stable")
+    Ps = torch.from_numpy(np.ascontiguousarray(params[order])).to(DEV)
+    ys = torch.full_like(y, float("nan"))
+    ns.solve(Ps, api.SAS_OUT_Y, ys)
+    torch.cuda.synchronize()
+    assert torch.equal(ys.cpu(), y.cpu()[torch.from_numpy(order)])
     ns.close()
 
 
