@@ -172,7 +172,8 @@ sas_status subapsnap_solve_batch(sas_ctx* ctx, const double* params, int64_t m,
  * mapped into the device's address space (cudaHostAlloc or
  * cudaHostRegister; every such allocation is mapped under unified
  * addressing), so the transfer overlaps the computation; pageable `out`
- * goes through a device buffer in chunks of at most 1 GiB.  Device staging
+ * goes through a device buffer in chunks (SAS_OPT_HOST_CHUNK, default
+ * 1 GiB).  Device staging
  * is owned by the context.  Errors: as subapsnap_solve_batch, SAS_EINVAL for
  * a device pointer. */
 sas_status subapsnap_solve_batch_host(sas_ctx* ctx, const double* params, int64_t m,
@@ -266,10 +267,13 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
  *  SAS_OPT_RECON_STORE: epilogue of the tensor-core reconstruction: 0 = tiles
  *      staged in shared memory and written by TMA bulk-tensor stores (when n
  *      is a multiple of 4 and the output 16-byte aligned), 1 = coalesced
- *      streaming stores straight from registers (default). */
+ *      streaming stores straight from registers (default).
+ *  SAS_OPT_HOST_CHUNK: subapsnap_solve_batch_host with pageable x_hat: bytes
+ *      of the device chunk x_hat goes through (at least one parameter's row;
+ *      default 2^30). */
 enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
        SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4, SAS_OPT_ASSEMBLY_SEGMENT = 5,
-       SAS_OPT_RECON_STORE = 6 };
+       SAS_OPT_RECON_STORE = 6, SAS_OPT_HOST_CHUNK = 7 };
 
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */

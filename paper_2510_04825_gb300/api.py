@@ -43,6 +43,7 @@ SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
 SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL, SAS_OPT_LS_VARIANT = 0, 1, 2, 3
 SAS_OPT_ASSEMBLY_KERNEL, SAS_OPT_ASSEMBLY_SEGMENT, SAS_OPT_RECON_STORE = 4, 5, 6
+SAS_OPT_HOST_CHUNK = 7
 SAS_MAX_VARIANTS = 32
 SAS_KRYLOV_WARM, SAS_KRYLOV_MIXED = 1, 2
 SAS_PRECOND_JACOBI, SAS_PRECOND_POISSON = 0, 1

@@ -576,7 +576,8 @@ sas_status subapsnap_solve_batch_host(sas_ctx* c, const double* params, int64_t 
   // x_hat into pageable memory: chunks of at most 1 GiB through a device buffer
   int64_t chunk = m;
   if (out_kind == SAS_OUT_XHAT && !out_mapped)
-    chunk = std::max<int64_t>(1, std::min<int64_t>(m, ((int64_t)1 << 30) / (int64_t)out_row));
+    chunk = std::max<int64_t>(1, std::min<int64_t>(m, (int64_t)(c->host_chunk ? c->host_chunk : (size_t)1 << 30) /
+                                                             (int64_t)out_row));
   const size_t pb = align256((size_t)m * c->dp * sizeof(double));
   const size_t fb = align256((size_t)m * sizeof(uint32_t));
   const size_t rb = align256((size_t)m * sizeof(double));
@@ -998,6 +999,10 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
     case SAS_OPT_RECON_STORE:
       if (value != 0.0 && value != 1.0) return fail(SAS_EINVAL, "recon store must be 0 or 1");
       c->recon_store = (int)value;
+      return SAS_OK;
+    case SAS_OPT_HOST_CHUNK:
+      if (!(value >= 1.0 && value <= 1099511627776.0)) return fail(SAS_EINVAL, "host chunk must be in [1, 2^40] bytes");
+      c->host_chunk = (size_t)value;
       return SAS_OK;
     case SAS_OPT_ASSEMBLY_SEGMENT:
       if (!(value >= 32.0 && value <= 1048576.0) || std::fmod(value, 32.0) != 0.0)

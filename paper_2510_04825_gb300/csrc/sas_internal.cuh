@@ -188,6 +188,7 @@ struct sas_ctx {
   size_t ysplit16_bytes;
   void* hstage;        // host-buffer calls: device staging of params, small outputs, x_hat chunks
   size_t hstage_bytes;
+  size_t host_chunk;   // bytes of one pageable x_hat chunk (0 = 1 GiB)
   int* dev_status;     // device status word
   int num_sms;
   int ls_blocks_per_sm;

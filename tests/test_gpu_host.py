@@ -42,10 +42,13 @@ def _device_reference(sv, P, kind, shape, dtype):
 
 
 @pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED], ids=["plain", "mixed"])
-@pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
+@pytest.mark.parametrize("pinned", [True, False, "chunked"], ids=["pinned", "pageable", "pageable-chunks"])
 def test_host_buffers_match_device_buffers(c2d, mode, pinned):
     p = c2d.prob
     sv = AffineSolver(p, c2d.S, c2d.J, mode=mode, device=DEV)
+    if pinned == "chunked":  # pageable x_hat through 17-parameter chunks, the last one ragged
+        api.subapsnap_set_option(sv.ctx, api.SAS_OPT_HOST_CHUNK, 17 * p.n * 8)
+        pinned = False
     params = np.ascontiguousarray(p.test_params)
     m = params.shape[0]
     P = torch.from_numpy(params).to(DEV)
