@@ -282,8 +282,11 @@ sas_status subapsnap_set_option(sas_ctx* ctx, int32_t key, double value);
 /* ---------------------------------------------------------------- offline stage */
 
 /* Flags of subapsnap_krylov_affine. */
-enum { SAS_KRYLOV_WARM = 1,  /* X holds start vectors (else zero start) */
-       SAS_KRYLOV_MIXED = 2  /* float32 iterates, float64 residual replacements */ };
+enum { SAS_KRYLOV_WARM = 1,     /* X holds start vectors (else zero start) */
+       SAS_KRYLOV_MIXED = 2,    /* float32 iterates, float64 residual replacements */
+       SAS_KRYLOV_BICGSTAB = 4  /* BiCGStab for nonsymmetric A(p): float64 iterates, diagonal
+                                   preconditioner; when its iterated residual reaches tol the
+                                   true residual decides, and it restarts from that one */ };
 
 /* Snapshot solves A(p_j) x_j = b, j = 0..B-1, all at once (Alg. 1 step 1,
  * "fully or approximately"): conjugate gradients in the bilinear form x^T y

@@ -45,7 +45,7 @@ SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL, SAS_OPT_LS_VARIANT
 SAS_OPT_ASSEMBLY_KERNEL, SAS_OPT_ASSEMBLY_SEGMENT, SAS_OPT_RECON_STORE = 4, 5, 6
 SAS_OPT_HOST_CHUNK = 7
 SAS_MAX_VARIANTS = 32
-SAS_KRYLOV_WARM, SAS_KRYLOV_MIXED = 1, 2
+SAS_KRYLOV_WARM, SAS_KRYLOV_MIXED, SAS_KRYLOV_BICGSTAB = 1, 2, 4
 SAS_PRECOND_JACOBI, SAS_PRECOND_POISSON = 0, 1
 SAS_NOALLOC_MAX_Y = 65536
 SAS_KERNEL_LS, SAS_KERNEL_RECONSTRUCT, SAS_KERNEL_RESIDUAL, SAS_KERNEL_ASSEMBLE = 0, 1, 2, 3
@@ -331,12 +331,16 @@ def subapsnap_nearest_points(params, points) -> np.ndarray:
 
 def subapsnap_krylov_affine(desc: AffineDesc, params, X, warm: bool = False, tol: float = 1e-12,
                             maxit: int = 20000, allow_noconv: bool = False, mixed: bool = False,
-                            precond=None):
+                            precond=None, method: str = "cg"):
     """Batched snapshot solves A(p_j) x_j = b.  X: CUDA tensor (B, n), row j = x_j
     (the column-major n x B matrix).  precond: None (Jacobi) or a dict with keys
     "dims" (grid sizes) and "coef" (B x 4: alpha re/im, beta re/im) for the fast
     Poisson preconditioner.  Returns (iterations, true relative residuals)."""
     flags = (SAS_KRYLOV_WARM if warm else 0) | (SAS_KRYLOV_MIXED if mixed else 0)
+    if method == "bicgstab":
+        flags |= SAS_KRYLOV_BICGSTAB
+    elif method != "cg":
+        raise ValueError("method must be 'cg' or 'bicgstab'")
     P = np.ascontiguousarray(np.atleast_2d(np.asarray(params, dtype=np.float64)))
     B = int(X.shape[0])
     it = np.zeros(B, dtype=np.int32)

@@ -183,8 +183,9 @@ __global__ void inv_diag_kernel(const double* D, int K, int64_t n, const T* thet
 // Per-column state of the batched COCG.
 template <typename T>
 struct Col {
-  T rz;           // r^T D^{-1} r of the current residual
+  T rz;           // r^T D^{-1} r of the current residual (BiCGStab: rho = <r_hat, r>)
   T alpha, beta;
+  T omega;        // BiCGStab only
   double relres;  // ||r|| / ||b|| of the iterated residual
   double rmax;    // relres at the last replacement by the true residual
   int active;     // 1 while iterating
@@ -193,6 +194,7 @@ struct Col {
   int upd;        // 1: replace the residual by the true one in this iteration
   int nrel;       // replacements so far
   int nstag;      // consecutive replacements that did not halve the true residual
+  int restart;    // BiCGStab: restart from the current residual in this iteration
 };
 
 // Column selection of the product kernels.
@@ -871,6 +873,311 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(int64_t n, int B, c
   }
 }
 
+// ------------------------------------------------------------------ BiCGStab
+// For nonsymmetric A(p) (BiCGStab, van der Vorst 1992) with the diagonal as right
+// preconditioner, float64 / complex128 iterates in the quad layout.  Per iteration:
+//   p = r + beta (p - omega v), p^ = D^-1 p, v = A p^, alpha = rho / <r_hat, v>,
+//   s = r - alpha v, s^ = D^-1 s, t = A s^, omega = <t, s> / <t, t>,
+//   x += alpha p^ + omega s^, r = s - omega t, rho' = <r_hat, r>, beta = (rho'/rho)(alpha/omega),
+// with <a, b> = sum conj(a) b.  When the iterated residual reaches the tolerance
+// the true residual decides; if it is still above, the iteration restarts from it
+// (r_hat = r, p = r), which is also how it starts.
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bicg_dir_kernel(int64_t n, int B, const T* R, T* Rh, T* P, const T* V,
+                                                            const T* invD, T* Ph, const Col<T>* st,
+                                                            int64_t rows_per_cta) {
+  const int q = blockIdx.x;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  T beta[4], omega[4];
+  int rs = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const bool a = (on >> j) & 1;
+    beta[j] = a ? st[4 * q + j].beta : zero<T>();
+    omega[j] = a ? st[4 * q + j].omega : zero<T>();
+    if (a && st[4 * q + j].restart) rs |= 1 << j;
+  }
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    const Quad<T> r = ldq<T>(R + o), v = ldq<T>(V + o), d = ldq<T>(invD + o);
+    Quad<T> p = ldq<T>(P + o), ph = ldq<T>(Ph + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!((on >> j) & 1)) continue;
+      p.v[j] = (rs >> j) & 1 ? r.v[j] : r.v[j] + beta[j] * (p.v[j] - omega[j] * v.v[j]);
+      ph.v[j] = d.v[j] * p.v[j];
+    }
+    stq<T>(P + o, p);
+    stq<T>(Ph + o, ph);
+    if (rs) {
+      Quad<T> rh = ldq<T>(Rh + o);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if ((rs >> j) & 1) rh.v[j] = r.v[j];
+      stq<T>(Rh + o, rh);
+    }
+  }
+}
+
+// partials of <A, Bv> (and of <C, D> when C is given) per active column
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bicg_dot_kernel(int64_t n, int B, const T* A, const T* Bv, const T* C,
+                                                            const T* D, const Col<T>* st, T* part0, T* part1,
+                                                            int64_t rows_per_cta) {
+  __shared__ T red0[kThreads / 32][4];
+  __shared__ T red1[kThreads / 32][4];
+  const int q = blockIdx.x, G = gridDim.y;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  T s0[4], s1[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) s0[j] = s1[j] = zero<T>();
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    const Quad<T> a = ldq<T>(A + o), b = ldq<T>(Bv + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s0[j] += conjv(a.v[j]) * b.v[j];
+    if (C) {
+      const Quad<T> c = ldq<T>(C + o), dd = ldq<T>(D + o);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s1[j] += conjv(c.v[j]) * dd.v[j];
+    }
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T a = warp_sum(s0[j]);
+    const T c = warp_sum(s1[j]);
+    if (lane == 0) {
+      red0[w][j] = a;
+      red1[w][j] = c;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && ((on >> threadIdx.x) & 1)) {
+    const int j = threadIdx.x;
+    T a = zero<T>(), c = zero<T>();
+    for (int k = 0; k < kThreads / 32; ++k) {
+      a += red0[k][j];
+      c += red1[k][j];
+    }
+    part0[(int64_t)(4 * q + j) * G + blockIdx.y] = a;
+    if (C) part1[(int64_t)(4 * q + j) * G + blockIdx.y] = c;
+  }
+}
+
+// s = r - alpha v, s^ = D^-1 s
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bicg_s_kernel(int64_t n, int B, const T* R, const T* V, const T* invD,
+                                                          T* Sv, T* Sh, const Col<T>* st, int64_t rows_per_cta) {
+  const int q = blockIdx.x;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  T alpha[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) alpha[j] = (on >> j) & 1 ? st[4 * q + j].alpha : zero<T>();
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    const Quad<T> r = ldq<T>(R + o), v = ldq<T>(V + o), d = ldq<T>(invD + o);
+    Quad<T> sv = ldq<T>(Sv + o), sh = ldq<T>(Sh + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!((on >> j) & 1)) continue;
+      sv.v[j] = r.v[j] - alpha[j] * v.v[j];
+      sh.v[j] = d.v[j] * sv.v[j];
+    }
+    stq<T>(Sv + o, sv);
+    stq<T>(Sh + o, sh);
+  }
+}
+
+// x += alpha p^ + omega s^, r = s - omega t; partials of rho' = <r_hat, r> and |r|^2
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bicg_xr_kernel(int64_t n, int B, T* X, const T* Ph, const T* Sh,
+                                                           const T* Sv, const T* Tv, const T* Rh, T* R,
+                                                           const Col<T>* st, T* prz, double* prr,
+                                                           int64_t rows_per_cta) {
+  __shared__ T red[kThreads / 32][4];
+  __shared__ double redd[kThreads / 32][4];
+  const int q = blockIdx.x, G = gridDim.y;
+  const int on = quad_flags(st, q, B, 0);
+  if (!on) return;
+  T alpha[4], omega[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    alpha[j] = (on >> j) & 1 ? st[4 * q + j].alpha : zero<T>();
+    omega[j] = (on >> j) & 1 ? st[4 * q + j].omega : zero<T>();
+  }
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_cta;
+  const int64_t r1 = r0 + rows_per_cta < n ? r0 + rows_per_cta : n;
+  T rho[4];
+  double rr[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    rho[j] = zero<T>();
+    rr[j] = 0.0;
+  }
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += kThreads) {
+    const int64_t o = ((int64_t)q * n + i) * 4;
+    Quad<T> x = ldq<T>(X + o), r = ldq<T>(R + o);
+    const Quad<T> ph = ldq<T>(Ph + o), sh = ldq<T>(Sh + o), sv = ldq<T>(Sv + o), tv = ldq<T>(Tv + o),
+                  rh = ldq<T>(Rh + o);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (!((on >> j) & 1)) continue;
+      x.v[j] += alpha[j] * ph.v[j] + omega[j] * sh.v[j];
+      r.v[j] = sv.v[j] - omega[j] * tv.v[j];
+      rho[j] += conjv(rh.v[j]) * r.v[j];
+      rr[j] += absq(r.v[j]);
+    }
+    stq<T>(X + o, x);
+    stq<T>(R + o, r);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T a = warp_sum(rho[j]);
+    const double c = warp_sum(rr[j]);
+    if (lane == 0) {
+      red[w][j] = a;
+      redd[w][j] = c;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 4 && ((on >> threadIdx.x) & 1)) {
+    const int j = threadIdx.x;
+    T a = zero<T>();
+    double c = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) {
+      a += red[k][j];
+      c += redd[k][j];
+    }
+    prz[(int64_t)(4 * q + j) * G + blockIdx.y] = a;
+    prr[(int64_t)(4 * q + j) * G + blockIdx.y] = c;
+  }
+}
+
+// alpha = rho / <r_hat, v>
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bicg_alpha_kernel(const T* pd, int G, Col<T>* st) {
+  __shared__ T red[kThreads / 32];
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  const T d = column_sum(pd, b, G, red);
+  if (threadIdx.x == 0) {
+    if (absq(d) == 0.0 || !finitev(d)) {
+      st[b].status = 2;
+      st[b].active = 0;
+    } else {
+      st[b].alpha = divv(st[b].rz, d);
+    }
+  }
+}
+
+// omega = <t, s> / <t, t> (omega = 0 when t = 0: then s = 0 and r is already s)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bicg_omega_kernel(const T* pts, const T* ptt, int G, Col<T>* st) {
+  __shared__ T red[kThreads / 32];
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  const T ts = column_sum(pts, b, G, red);
+  const T tt = column_sum(ptt, b, G, red);
+  if (threadIdx.x == 0) {
+    if (!finitev(ts) || !finitev(tt)) {
+      st[b].status = 2;
+      st[b].active = 0;
+    } else {
+      st[b].omega = absq(tt) == 0.0 ? zero<T>() : divv(ts, tt);
+    }
+  }
+}
+
+// after x and r: the iterated residual; tolerance or limit -> the true residual decides
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bicg_beta_kernel(const T* prho, const double* prr, int G, double bnorm,
+                                                             double tol, int maxit, Col<T>* st) {
+  __shared__ T red[kThreads / 32];
+  __shared__ double redd[kThreads / 32];
+  const int b = blockIdx.x;
+  if (!st[b].active) return;
+  const T rho = column_sum(prho, b, G, red);
+  const double rr = column_sum(prr, b, G, redd);
+  if (threadIdx.x == 0) {
+    Col<T> c = st[b];
+    c.iters += 1;
+    c.restart = 0;
+    c.relres = sqrt(rr) / bnorm;
+    if (!(c.relres == c.relres) || !finitev(rho)) {
+      c.status = 2;
+      c.active = 0;
+    } else if (c.relres <= tol || c.iters >= maxit) {
+      c.upd = 1;
+    } else if (absq(c.rz) == 0.0 || absq(c.omega) == 0.0) {
+      c.upd = 1;  // breakdown of the recurrences: restart from the true residual
+    } else {
+      c.beta = divv(rho, c.rz) * divv(c.alpha, c.omega);
+      c.rz = rho;
+    }
+    st[b] = c;
+  }
+}
+
+// the true residual (written to R by the residual kernel) decides; otherwise restart
+// from it: r_hat = r, p = r, rho = <r, r>
+template <typename T>
+__global__ void __launch_bounds__(kThreads) bicg_replace_kernel(const double* prr, int G, double bnorm, double tol,
+                                                                int maxit, int start, Col<T>* st) {
+  __shared__ double redd[kThreads / 32];
+  const int b = blockIdx.x;
+  if (!start && !st[b].upd) return;
+  const double rr = column_sum(prr, b, G, redd);
+  if (threadIdx.x == 0) {
+    Col<T> c = st[b];
+    const double prev = c.rmax;
+    c.upd = 0;
+    c.relres = sqrt(rr) / bnorm;
+    c.rmax = c.relres;
+    if (start) {
+      c.iters = 0;
+      c.nrel = 0;
+      c.nstag = 0;
+      c.status = 0;
+      c.active = 1;
+    } else {
+      c.nrel += 1;
+      c.nstag = c.relres > 0.5 * prev ? c.nstag + 1 : 0;
+    }
+    if (!(c.relres == c.relres)) {
+      c.status = 2;
+      c.active = 0;
+    } else if (c.relres <= tol) {
+      c.status = 1;
+      c.active = 0;
+    } else if (c.nstag >= 4) {
+      c.status = 4;
+      c.active = 0;
+    } else if (c.iters >= maxit) {
+      c.status = 3;
+      c.active = 0;
+    } else {
+      c.restart = 1;
+      c.rz = from_re<T>(rr);
+      c.beta = zero<T>();
+      c.omega = zero<T>();
+      c.alpha = zero<T>();
+    }
+    st[b] = c;
+  }
+}
+
 // ------------------------------------------------- fast Poisson preconditioner
 // M_b = alpha_b L + beta_b I with L the unit-spacing Dirichlet Laplacian of an
 // nx x ny x nz grid (sum over the axes of tridiag(-1, 2, -1)), i = ix + nx (iy + ny iz).
@@ -1319,8 +1626,8 @@ cublasStatus_t dst_axis(PoissonPre& pp, int a, int64_t C, const float* in, float
 
 template <typename T, typename TL>
 sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T* X, bool warm,
-                    bool mixed, double tol, int32_t maxit, const sas_krylov_precond* pc, int32_t* iters_out,
-                    double* relres_out) {
+                    bool mixed, bool bicg, double tol, int32_t maxit, const sas_krylov_precond* pc,
+                    int32_t* iters_out, double* relres_out) {
   const bool poisson = pc && pc->kind == SAS_PRECOND_POISSON;
   const int64_t n = d->n;
   const int K = d->K;
@@ -1539,9 +1846,25 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   };
 
   const int defer = poisson ? 1 : 0;
-  off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 1, defer,
-                                                st.as<Col<T>>());
-  if (poisson) {
+  // BiCGStab's extra vectors (float64 iterates only): r_hat, p^, s, s^, t; v lives in Q
+  DevBuf Rh, Ph, Sv, Sh, Tv, pz2;
+  if (bicg) {
+    for (DevBuf* v : {&Rh, &Ph, &Sv, &Sh, &Tv}) {
+      if (e == cudaSuccess) e = v->alloc(vec);
+      if (e == cudaSuccess) e = cudaMemsetAsync(v->p, 0, vec, s);
+    }
+    if (e == cudaSuccess) e = pz2.alloc((size_t)B * Gp * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "krylov: BiCGStab buffers");
+  }
+  if (bicg) {
+    off::bicg_replace_kernel<T><<<B, kThreads, 0, s>>>(prr.as<double>(), Gt, bnorm, tol, maxit, 1, st.as<Col<T>>());
+  } else {
+    off::replace_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), Gt, bnorm, tol, maxit, 1, defer,
+                                                  st.as<Col<T>>());
+  }
+  if (bicg) {
+    // the first iteration starts from r (restart flag set by bicg_replace_kernel)
+  } else if (poisson) {
     // the emulated-float32 tensor-core GEMM where the library has it, plain float32 otherwise
     if (!precondition()) {
       pp.ct = CUBLAS_COMPUTE_32F;
@@ -1562,7 +1885,37 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   cudaGraphExec_t exec = nullptr;
   e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: capture");
-  for (int it = 0; it < chunk; ++it) {
+  for (int it = 0; it < chunk && bicg; ++it) {
+    if constexpr (sizeof(TL) == sizeof(T)) {
+      T* V = reinterpret_cast<T*>(Q.p);
+      off::bicg_dir_kernel<T><<<qgrid, kThreads, 0, s>>>(n, B, (const T*)R.p, Rh.as<T>(), (T*)P.p, V,
+                                                         (const T*)invD.p, Ph.as<T>(), st.as<Col<T>>(), rpc);
+      k_lo<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta_lo.as<TL>(), (const TL*)Ph.p, Q.as<TL>(),
+                                           st.as<Col<T>>(), ppq.as<T>());
+      off::bicg_dot_kernel<T><<<qgrid, kThreads, 0, s>>>(n, B, Rh.as<T>(), V, nullptr, nullptr, st.as<Col<T>>(),
+                                                         prz.as<T>(), nullptr, rpc);
+      off::bicg_alpha_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), G, st.as<Col<T>>());
+      off::bicg_s_kernel<T><<<qgrid, kThreads, 0, s>>>(n, B, (const T*)R.p, V, (const T*)invD.p, Sv.as<T>(),
+                                                       Sh.as<T>(), st.as<Col<T>>(), rpc);
+      k_lo<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta_lo.as<TL>(), (const TL*)Sh.p, (TL*)Tv.p,
+                                           st.as<Col<T>>(), ppq.as<T>());
+      off::bicg_dot_kernel<T><<<qgrid, kThreads, 0, s>>>(n, B, Tv.as<T>(), Sv.as<T>(), Tv.as<T>(), Tv.as<T>(),
+                                                         st.as<Col<T>>(), prz.as<T>(), pz2.as<T>(), rpc);
+      off::bicg_omega_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), pz2.as<T>(), G, st.as<Col<T>>());
+      off::bicg_xr_kernel<T><<<qgrid, kThreads, 0, s>>>(n, B, (T*)Xl.p, Ph.as<T>(), Sh.as<T>(), Sv.as<T>(),
+                                                        Tv.as<T>(), Rh.as<T>(), (T*)R.p, st.as<Col<T>>(),
+                                                        prz.as<T>(), prr.as<double>(), rpc);
+      off::bicg_beta_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), prr.as<double>(), G, bnorm, tol, maxit,
+                                                      st.as<Col<T>>());
+      off::fold_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, X, Xl.as<TL>(), st.as<Col<T>>(), 0, rpc);
+      k_res<<<Gt, kThreads, tile_smem, s>>>(ops, K, n, B, theta.as<T>(), X, R.as<TL>(), (const T*)d->b,
+                                            invD.as<TL>(), st.as<Col<T>>(), off::kSelUpd, prz.as<T>(),
+                                            prr.as<double>());
+      off::bicg_replace_kernel<T><<<B, kThreads, 0, s>>>(prr.as<double>(), Gt, bnorm, tol, maxit, 0,
+                                                         st.as<Col<T>>());
+    }
+  }
+  for (int it = 0; it < chunk && !bicg; ++it) {
     if (mg.rp)
       launch_product_merged<T, TL>(mg, K, n, B, theta_lo.as<TL>(), P.as<TL>(), Q.as<TL>(), st.as<Col<T>>(),
                                    ppq.as<T>(), Gt, merged_smem, s);
@@ -1747,6 +2100,7 @@ sas_status subapsnap_krylov_affine_ex(const sas_affine_desc* d, const double* pa
                                       int32_t flags, double tol, int32_t maxit, const sas_krylov_precond* pc,
                                       int32_t* iters_out, double* relres_out) {
   const bool warm = (flags & SAS_KRYLOV_WARM) != 0, mixed = (flags & SAS_KRYLOV_MIXED) != 0;
+  const bool bicg = (flags & SAS_KRYLOV_BICGSTAB) != 0;
   if (!d || !params || !X) return fail_off(SAS_EINVAL, "NULL argument");
   if (B < 1 || B > 256) return fail_off(SAS_EINVAL, "need 1 <= B <= 256");
   if (d->n < 1) return fail_off(SAS_EINVAL, "need n >= 1");
@@ -1760,7 +2114,10 @@ sas_status subapsnap_krylov_affine_ex(const sas_affine_desc* d, const double* pa
       d->theta_rule != SAS_THETA_DELAY)
     return fail_off(SAS_EINVAL, "bad theta rule");
   if (!(tol >= 0.0)) return fail_off(SAS_EINVAL, "tol must be >= 0");
-  if (flags & ~(SAS_KRYLOV_WARM | SAS_KRYLOV_MIXED)) return fail_off(SAS_EINVAL, "unknown flag bits");
+  if (flags & ~(SAS_KRYLOV_WARM | SAS_KRYLOV_MIXED | SAS_KRYLOV_BICGSTAB))
+    return fail_off(SAS_EINVAL, "unknown flag bits");
+  if (bicg && (mixed || (pc && pc->kind != SAS_PRECOND_JACOBI)))
+    return fail_off(SAS_ENOTSUP, "BiCGStab runs float64 iterates with the diagonal preconditioner");
   if (pc) {
     if (pc->kind != SAS_PRECOND_JACOBI && pc->kind != SAS_PRECOND_POISSON)
       return fail_off(SAS_EINVAL, "unknown preconditioner");
@@ -1788,10 +2145,12 @@ sas_status subapsnap_krylov_affine_ex(const sas_affine_desc* d, const double* pa
     if (!on_device(d->rowptr[k]) || !on_device(d->colind[k]) || !on_device(d->values[k]))
       return fail_off(SAS_EINVAL, "CSR arrays must be device pointers");
   if (d->dtype == SAS_COMPLEX128)
-    return mixed ? krylov_t<zd, zf>(d, params, B, (zd*)X, warm, true, tol, maxit, pc, iters_out, relres_out)
-                 : krylov_t<zd, zd>(d, params, B, (zd*)X, warm, false, tol, maxit, pc, iters_out, relres_out);
-  return mixed ? krylov_t<double, float>(d, params, B, (double*)X, warm, true, tol, maxit, pc, iters_out, relres_out)
-               : krylov_t<double, double>(d, params, B, (double*)X, warm, false, tol, maxit, pc, iters_out,
+    return mixed ? krylov_t<zd, zf>(d, params, B, (zd*)X, warm, true, false, tol, maxit, pc, iters_out, relres_out)
+                 : krylov_t<zd, zd>(d, params, B, (zd*)X, warm, false, bicg, tol, maxit, pc, iters_out,
+                                    relres_out);
+  return mixed ? krylov_t<double, float>(d, params, B, (double*)X, warm, true, false, tol, maxit, pc, iters_out,
+                                         relres_out)
+               : krylov_t<double, double>(d, params, B, (double*)X, warm, false, bicg, tol, maxit, pc, iters_out,
                                           relres_out);
 }
 

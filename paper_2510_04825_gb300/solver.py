@@ -116,7 +116,7 @@ def poisson_precond(prob, params):
 
 
 def snapshot_solve(prob, params, X, blocks_device=None, b_device=None, warm=False, tol=1e-12,
-                   maxit=20000, device="cuda", allow_noconv=False, mixed=False, precond=None):
+                   maxit=20000, device="cuda", allow_noconv=False, mixed=False, precond=None, method="cg"):
     """Batched Krylov solves A(p_j) x_j = b on the device into X (B, n); (iterations, true residuals)."""
     cplx = bool(prob.complex_valued)
     blocks = blocks_device or [csr_to_device(A, device) for A in prob.blocks]
@@ -128,7 +128,7 @@ def snapshot_solve(prob, params, X, blocks_device=None, b_device=None, warm=Fals
                             theta_rule_code(prob.theta_rule), api.SAS_MODE_PLAIN, api.SAS_QOI_NONE,
                             None, cplx)
     return api.subapsnap_krylov_affine(desc, P, X, warm=warm, tol=tol, maxit=maxit,
-                                       allow_noconv=allow_noconv, mixed=mixed, precond=precond)
+                                       allow_noconv=allow_noconv, mixed=mixed, precond=precond, method=method)
 
 
 def snapshot_basis(prob, blocks_device=None, b_device=None, params=None, tol=1e-12, maxit=20000,

@@ -262,3 +262,65 @@ def test_poisson_preconditioner_arguments():
     cplx = dict(pc, coef=pc["coef"] + np.array([0, 1.0, 0, 0]))
     with pytest.raises(api.SasError):
         snapshot_solve(prob, prob.snap_params, X, precond=cplx)
+
+
+def _convection_diffusion(N, cplx):
+    """Nonsymmetric family: 2-D convection-diffusion (upwind convection), A(p) = A_0 + p A_1
+    with A_1 a positive reaction term; complex version: the pencil i omega E - A_0 on the
+    same nonsymmetric A_0 (negated)."""
+    import types
+    import scipy.sparse as sp
+    rng = np.random.default_rng(21)
+    n = N * N
+    h = 1.0 / (N + 1)
+    one = np.ones(N)
+    T1 = sp.diags([-one[1:], 2 * one, -one[1:]], [-1, 0, 1])
+    Dx = sp.diags([-one[1:], one], [-1, 0])  # upwind first difference
+    I = sp.identity(N)
+    L = (sp.kron(I, T1) + sp.kron(T1, I)) / h ** 2
+    C = 40.0 * (sp.kron(I, Dx) + 0.5 * sp.kron(Dx, I)) / h
+    A0 = (L + C).tocsr()
+    b = rng.standard_normal(n)
+    if not cplx:
+        A1 = sp.diags(rng.uniform(0.5, 1.5, n)).tocsr()
+        return types.SimpleNamespace(name="convection_diffusion", n=n, blocks=[A0, A1], theta_rule="linear",
+                                     b=b, complex_valued=False), rng.uniform(0.0, 10.0, (6, 1))
+    E = sp.diags(rng.uniform(0.5, 1.5, n)).tocsr()
+    return types.SimpleNamespace(name="convection_diffusion_pencil", n=n, blocks=[(-A0).tocsr(), E],
+                                 theta_rule="pencil", b=b.astype(np.complex128), complex_valued=True), \
+        np.logspace(0, 3, 6)[:, None]
+
+
+@pytest.mark.parametrize("cplx", [False, True], ids=["real", "complex"])
+def test_bicgstab_on_a_nonsymmetric_family(cplx):
+    prob, P = _convection_diffusion(30, cplx)
+    dt = torch.complex128 if cplx else torch.float64
+    X = torch.empty((len(P), prob.n), dtype=dt, device=DEV)
+    tol = 1e-10
+    it, rel = snapshot_solve(prob, P, X, tol=tol, maxit=5000, method="bicgstab")
+    assert (rel <= tol).all()
+    Xg = X.cpu().numpy()
+    for j, p in enumerate(P):
+        xo = snapshots.solve_full(prob, p)
+        A = oproblem.full_matrix(prob, p)
+        assert np.linalg.norm(A @ Xg[j] - prob.b) / np.linalg.norm(prob.b) <= 2 * tol
+        assert np.linalg.norm(Xg[j] - xo) / np.linalg.norm(xo) <= 1e-6
+    # warm start from the solution's neighbourhood takes fewer iterations
+    Xw = torch.from_numpy(np.ascontiguousarray(Xg * (1 + 1e-6))).to(DEV)
+    it_w, rel_w = snapshot_solve(prob, P, Xw, tol=tol, maxit=5000, method="bicgstab", warm=True)
+    assert (rel_w <= tol).all() and (it_w < it).all()
+    print(f"BiCGStab {'complex' if cplx else 'real'} nonsymmetric: iterations {it.min()}..{it.max()}, "
+          f"warm {it_w.min()}..{it_w.max()}")
+
+
+def test_bicgstab_on_a_symmetric_workload_and_arguments():
+    prob = get_config("diffusion_2d", N=32, r=6, s=12, m=4)
+    X = torch.empty((6, prob.n), dtype=torch.float64, device=DEV)
+    it, rel = snapshot_solve(prob, prob.snap_params, X, tol=1e-10, maxit=5000, method="bicgstab")
+    assert (rel <= 1e-10).all()
+    for j, p in enumerate(prob.snap_params):
+        xo = snapshots.solve_full(prob, p)
+        assert np.linalg.norm(X.cpu().numpy()[j] - xo) / np.linalg.norm(xo) <= 1e-8
+    with pytest.raises(api.SasError) as ei:
+        snapshot_solve(prob, prob.snap_params, X, method="bicgstab", mixed=True)
+    assert ei.value.code == api.SAS_ENOTSUP
