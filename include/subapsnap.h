@@ -294,7 +294,7 @@ enum { SAS_KRYLOV_WARM = 1,     /* X holds start vectors (else zero start) */
  * preconditioner.  A(p) must be symmetric (A^T = A; complex symmetric for the
  * pencil and delay rules) with a non-zero diagonal; the method converges for
  * positive definite A(p) and in practice for the complex symmetric families
- * here.  The same call refines given start vectors (SAS_KRYLOV_WARM), e.g.
+ * here.  Nonsymmetric A(p) take SAS_KRYLOV_BICGSTAB.  The same call refines given start vectors (SAS_KRYLOV_WARM), e.g.
  * the SubApSnap output x_hat as the initial guess of Sec. 3.2.  Convergence
  * is only ever declared on the true residual b - A x computed in float64:
  * when the iterated residual reaches tol it is replaced by the true one and

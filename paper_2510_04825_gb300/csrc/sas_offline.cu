@@ -6,7 +6,8 @@
 // approximately".  Every family here is symmetric in the bilinear sense
 // (A^T = A, complex entries allowed), so one Krylov method covers them:
 // conjugate gradients with the unconjugated form x^T y (COCG; for a real SPD
-// matrix this is plain CG), preconditioned by the diagonal of A(p_j).  The
+// matrix this is plain CG), preconditioned by the diagonal of A(p_j) or, on
+// grid families, by a fast Poisson solve; BiCGStab serves nonsymmetric A(p).  The
 // batch runs every column at once: column j has its own theta(p_j), scalars
 // alpha_j, beta_j and stopping test, and one launch of each kernel covers all
 // active columns.  Convergence is declared on the float64 true residual only.
