@@ -164,18 +164,17 @@ sas_status subapsnap_solve_batch(sas_ctx* ctx, const double* params, int64_t m,
                                  int32_t out_kind, void* out, uint32_t* flags,
                                  double* rho, void* stream);
 
-/* subapsnap_solve_batch with HOST buffers: params (m x dp), out (layout per
- * out_kind), flags and rho (or NULL) are ordinary host memory.  The call
- * copies params to the device, solves, and returns after the outputs are in
- * the host buffers (synchronous on `stream`).  x_hat is written straight
- * into `out` by the reconstruction when `out` is page-locked host memory
- * mapped into the device's address space (cudaHostAlloc or
+/* subapsnap_solve_batch (Alg. 1 step 4) with HOST buffers: params (m x dp),
+ * out (layout per out_kind), flags and rho (or NULL) are ordinary host
+ * memory.  The call copies params to the device, solves, and returns after
+ * the outputs are in the host buffers (synchronous on `stream`).  x_hat is
+ * written straight into `out` by the reconstruction when `out` is page-locked
+ * host memory mapped into the device's address space (cudaHostAlloc or
  * cudaHostRegister; every such allocation is mapped under unified
- * addressing), so the transfer overlaps the computation; pageable `out`
- * goes through a device buffer in chunks (SAS_OPT_HOST_CHUNK, default
- * 1 GiB).  Device staging
- * is owned by the context.  Errors: as subapsnap_solve_batch, SAS_EINVAL for
- * a device pointer. */
+ * addressing), so the transfer overlaps the computation; pageable `out` goes
+ * through a device buffer in chunks (SAS_OPT_HOST_CHUNK, default 1 GiB).
+ * Device staging is owned by the context.  Errors: as subapsnap_solve_batch,
+ * SAS_EINVAL for a device pointer. */
 sas_status subapsnap_solve_batch_host(sas_ctx* ctx, const double* params, int64_t m,
                                       int32_t out_kind, void* out, uint32_t* flags,
                                       double* rho, void* stream);
@@ -326,7 +325,8 @@ sas_status subapsnap_krylov_affine(const sas_affine_desc* desc, const double* pa
 /* Preconditioners of subapsnap_krylov_affine_ex. */
 enum { SAS_PRECOND_JACOBI = 0, SAS_PRECOND_POISSON = 1 };
 
-/* SAS_PRECOND_POISSON: M_j = alpha_j L + beta_j I with L the unit-spacing
+/* SAS_PRECOND_POISSON (not in the paper; a classical preconditioner for its
+ * grid problems): M_j = alpha_j L + beta_j I with L the unit-spacing
  * Dirichlet Laplacian of an nx x ny x nz grid (the sum over the axes of
  * tridiag(-1, 2, -1)), point i = ix + nx (iy + ny iz).  M_j^-1 is applied
  * exactly by the discrete sine transform along each axis (dense float32
