@@ -85,15 +85,21 @@ enum { SAS_QOI_NONE = 0, SAS_QOI_TRANSPOSE = 1 /* c^T x, plain transpose */,
  *                  reconstruction.
  *  SAS_MODE_MIXED: float32 assembly and Householder QR, iterative refinement
  *                  of y with the subsampled residual b_J - M y formed in
- *                  float64, float32 reconstruction on the tensor cores
- *                  (x_hat returned as float32).  Not in the paper.        */
+ *                  float64, and a float64-accurate reconstruction on the
+ *                  tensor cores: 9-bit fixed-point digits of S and y, their
+ *                  products summed exactly in the f32 accumulators and
+ *                  assembled as int64 (x_hat returned as float64, within
+ *                  ~2^-43 of the scale max_k|S_ik| ||y||_1 of each entry;
+ *                  r <= 64, otherwise the float64 CUDA-core product).  With
+ *                  SAS_OPT_XHAT_F32 = 1, x_hat is float32 from three tf32
+ *                  products instead.  Not in the paper.                     */
 enum { SAS_MODE_PLAIN = 0, SAS_MODE_MIXED = 1 };
 
 /* What subapsnap_solve_batch writes to `out` for each of its m parameters. */
 enum {
   SAS_OUT_Y = 0,     /* y: m x r, row j at out + j*r (dtype of S) */
-  SAS_OUT_XHAT = 1,  /* x_hat = S y: m x n, row j at out + j*n; double in
-                        SAS_MODE_PLAIN, float (real) in SAS_MODE_MIXED */
+  SAS_OUT_XHAT = 1,  /* x_hat = S y: m x n, row j at out + j*n; double (real),
+                        float when SAS_MODE_MIXED and SAS_OPT_XHAT_F32 = 1 */
   SAS_OUT_QOI = 3    /* H = (c^T S) y: m values (dtype of S) */
 };
 
@@ -241,9 +247,19 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
                                               double* out, uint32_t* flags, double* rho,
                                               void* stream);
 
+/* Bytes that subapsnap_solve_batch / subapsnap_solve_batch_host write per
+ * parameter for out_kind (and subapsnap_reconstruct for SAS_OUT_XHAT) under the
+ * context's current mode and options: r elements for SAS_OUT_Y, n for
+ * SAS_OUT_XHAT (8-byte double, or 4-byte float when SAS_OPT_XHAT_F32 = 1 in
+ * SAS_MODE_MIXED), one for SAS_OUT_QOI.  A caller sizes `out` as m times this.
+ * Not in the paper.  Errors: SAS_EINVAL (NULL argument or bad out_kind). */
+sas_status subapsnap_output_row_bytes(const sas_ctx* ctx, int32_t out_kind, int64_t* bytes);
+
 /* Per-context options (subapsnap_set_option).  Not in the paper.
- *  SAS_OPT_RECON_KERNEL: mixed-form reconstruction kernel: 0 = automatic
- *      (tensor cores when r <= 64, as 3), 1 = CUDA cores, 2 = tensor cores
+ *  SAS_OPT_RECON_KERNEL: mixed-form reconstruction kernel.  float64 x_hat:
+ *      1 = float64 CUDA-core product, any other value = the digit products on
+ *      the tensor cores (when r <= 64).  float32 x_hat (SAS_OPT_XHAT_F32): 0 =
+ *      automatic (tensor cores when r <= 64, as 3), 1 = CUDA cores, 2 = tensor cores
  *      (tcgen05, kind::tf32, three split products) with 64-parameter tiles,
  *      3 = as 2 with 128-parameter tiles, 4 = as 3 with the parameter tiles
  *      of each row tile visited in a rotated order, 5 = tensor cores
@@ -269,10 +285,13 @@ sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params
  *      streaming stores straight from registers (default).
  *  SAS_OPT_HOST_CHUNK: subapsnap_solve_batch_host with pageable x_hat: bytes
  *      of the device chunk x_hat goes through (at least one parameter's row;
- *      default 2^30). */
+ *      default 2^30).
+ *  SAS_OPT_XHAT_F32: mixed form only: 1 = x_hat returned as float32 (three
+ *      tf32 products, ~2^-21 relative; not residual-equivalent to float64
+ *      for an operator with large ||A||), 0 = float64 (default). */
 enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
        SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4, SAS_OPT_ASSEMBLY_SEGMENT = 5,
-       SAS_OPT_RECON_STORE = 6, SAS_OPT_HOST_CHUNK = 7 };
+       SAS_OPT_RECON_STORE = 6, SAS_OPT_HOST_CHUNK = 7, SAS_OPT_XHAT_F32 = 8 };
 
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */

@@ -38,12 +38,13 @@ EXPORTED = [
     "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine", "subapsnap_sample_rows_leverage",
     "subapsnap_select_rows_union_affine", "subapsnap_nearest_points", "subapsnap_krylov_affine",
     "subapsnap_tsqr", "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex",
+    "subapsnap_output_row_bytes",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
 SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL, SAS_OPT_LS_VARIANT = 0, 1, 2, 3
 SAS_OPT_ASSEMBLY_KERNEL, SAS_OPT_ASSEMBLY_SEGMENT, SAS_OPT_RECON_STORE = 4, 5, 6
-SAS_OPT_HOST_CHUNK = 7
+SAS_OPT_HOST_CHUNK, SAS_OPT_XHAT_F32 = 7, 8
 SAS_MAX_VARIANTS = 32
 SAS_KRYLOV_WARM, SAS_KRYLOV_MIXED, SAS_KRYLOV_BICGSTAB = 1, 2, 4
 SAS_PRECOND_JACOBI, SAS_PRECOND_POISSON = 0, 1
@@ -111,6 +112,7 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_set_tracing.argtypes = [vp, i32]
         L.subapsnap_set_option.argtypes = [vp, i32, ctypes.c_double]
         L.subapsnap_reconstruct.argtypes = [vp, vp, i64, vp, vp]
+        L.subapsnap_output_row_bytes.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64)]
         dp_, fp_, i64p = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int64)
         L.subapsnap_surrogate_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_double,
                                                 ctypes.c_uint64, dp_, vp]
@@ -262,8 +264,32 @@ def subapsnap_select_rows_kernel(desc: KernelDesc, p_sel, s: int):
     return J, gaps
 
 
+def subapsnap_output_row_bytes(ctx, out_kind: int) -> int:
+    b = ctypes.c_int64()
+    _check(lib().subapsnap_output_row_bytes(ctx, int(out_kind), ctypes.byref(b)))
+    return b.value
+
+
+def _check_out(ctx, out_kind, out, m):
+    """The output buffer must hold m rows of what the context writes for out_kind;
+    a 2-D buffer's rows must be exactly one parameter's output (so that a float32
+    x_hat buffer is never handed to a context that writes float64)."""
+    row = subapsnap_output_row_bytes(ctx, out_kind)
+    if hasattr(out, "element_size"):
+        esize, shape = out.element_size(), tuple(out.shape)
+    else:
+        arr = np.asarray(out)
+        esize, shape = arr.itemsize, arr.shape
+    nbytes = esize * int(np.prod(shape)) if shape else esize
+    if nbytes < int(m) * row:
+        raise ValueError(f"output buffer holds {nbytes} bytes; {int(m)} rows need {int(m) * row}")
+    if len(shape) == 2 and shape[1] * esize != row:
+        raise ValueError(f"output rows are {shape[1] * esize} bytes; the context writes {row} per row")
+
+
 def subapsnap_solve_batch(ctx, params, m: int, out_kind: int, out, flags=None, rho=None,
                           stream=None):
+    _check_out(ctx, out_kind, out, m)
     _check(lib().subapsnap_solve_batch(ctx, _ptr(params), int(m), int(out_kind), _ptr(out),
                                        _ptr(flags), _ptr(rho), _stream(stream)))
 
@@ -393,11 +419,13 @@ def _hptr(a):
 
 def subapsnap_solve_batch_host(ctx, params, m: int, out_kind: int, out, flags=None, rho=None, stream=None):
     """solve_batch with host buffers (CPU tensors or numpy arrays); returns when out is filled."""
+    _check_out(ctx, out_kind, out, m)
     _check(lib().subapsnap_solve_batch_host(ctx, _hptr(params), int(m), int(out_kind), _hptr(out),
                                             _hptr(flags), _hptr(rho), _stream(stream)))
 
 
 def subapsnap_reconstruct(ctx, Y, m: int, out, stream=None):
+    _check_out(ctx, SAS_OUT_XHAT, out, m)
     _check(lib().subapsnap_reconstruct(ctx, _ptr(Y), int(m), _ptr(out), _stream(stream)))
 
 
@@ -448,6 +476,7 @@ def subapsnap_surrogate_predict(ctx, params, m: int, Yhat, stream=None):
 def subapsnap_solve_batch_surrogate(ctx, params, m: int, out_kind: int, out, flags=None, rho=None,
                                     gate_tol: float = 1e-6, stream=None) -> int:
     acc = ctypes.c_int64()
+    _check_out(ctx, out_kind, out, m)
     _check(lib().subapsnap_solve_batch_surrogate(ctx, _ptr(params), int(m), int(out_kind), _ptr(out),
                                                  _ptr(flags), _ptr(rho), float(gate_tol),
                                                  ctypes.byref(acc), _stream(stream)))

@@ -96,6 +96,9 @@ static void free_ctx(sas_ctx* c) {
   cudaFree(c->S16hi);
   cudaFree(c->S16lo);
   cudaFree(c->ysplit16);
+  cudaFree(c->Sx64);
+  cudaFree(c->Sx64_exp);
+  cudaFree(c->yx64);
   cudaFree(c->StHi);
   cudaFree(c->StLo);
   cudaFree(c->Xc32);
@@ -165,7 +168,7 @@ static cudaError_t dmalloc(T** p, size_t bytes) {
   return cudaMalloc((void**)p, bytes);
 }
 
-static sas_status ensure_scratch(sas_ctx* c, int64_t m, bool split, cudaStream_t st) {
+static sas_status ensure_scratch(sas_ctx* c, int64_t m, bool mixed, cudaStream_t st) {
   const size_t es = c->dtype == SAS_COMPLEX128 ? 16 : 8;
   const size_t need = (size_t)m * c->r * es;
   if (need > c->ybuf_bytes) {
@@ -178,7 +181,21 @@ static sas_status ensure_scratch(sas_ctx* c, int64_t m, bool split, cudaStream_t
     if (e != cudaSuccess) return cuda_fail(e, "solve_batch scratch");
     c->ybuf_bytes = need;
   }
-  if (split) {
+  if (mixed && !c->xhat_f32) {
+    // float64-accurate x_hat: digit planes of y and their exponents
+    const size_t need4 = reconstruct_x64_supported(c) ? x64_coeff_bytes(m) : 0;
+    if (need4 > c->yx64_bytes) {
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "solve_batch");
+      cudaFree(c->yx64);
+      c->yx64 = nullptr;
+      c->yx64_bytes = 0;
+      e = cudaMalloc(&c->yx64, need4);
+      if (e != cudaSuccess) return cuda_fail(e, "solve_batch scratch");
+      c->yx64_bytes = need4;
+    }
+  }
+  if (mixed && c->xhat_f32) {
     const int rpad = (c->r + 31) / 32 * 32;
     const size_t need2 = (size_t)2 * m * rpad * sizeof(float);
     if (need2 > c->ysplit_bytes) {
@@ -205,6 +222,15 @@ static sas_status ensure_scratch(sas_ctx* c, int64_t m, bool split, cudaStream_t
     }
   }
   return SAS_OK;
+}
+
+// x_hat of the mixed form from the float64 coefficients in c->ybuf: float64 from
+// the digit products on the tensor cores (or the float64 CUDA-core product where
+// the digit split does not apply: r > 64, or SAS_OPT_RECON_KERNEL = 1).
+static cudaError_t reconstruct_mixed_f64(sas_ctx* c, int64_t m, double* out, cudaStream_t st) {
+  if (c->recon_kernel != 1 && reconstruct_x64_supported(c))
+    return launch_reconstruct_x64(c, (const double*)c->ybuf, m, out, c->yx64, st);
+  return launch_reconstruct_f64(c, c->ybuf, m, out, st);
 }
 
 }  // namespace sas
@@ -295,6 +321,7 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
     }
     TRY(launch_make_mixed_copies(c, sst));
     TRY(setup_f16_basis(c, sst));
+    TRY(setup_x64_basis(c, sst));
     // float64 M slots for the least-squares variants that keep M in global memory
     c->ls_slots_n = ls_mixed_slots(c);
     TRY(cudaMalloc(&c->ls_slots, (size_t)c->ls_slots_n * d->s * d->r * es));
@@ -389,6 +416,7 @@ sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
     TRYK(dmalloc(&c->Slo, (size_t)d->n * rpad * sizeof(float)));
     TRYK(launch_make_mixed_copies(c, sst));
     TRYK(setup_f16_basis(c, sst));
+    TRYK(setup_x64_basis(c, sst));
     // tensor-core kernel rows: S^T split, float32 hi/lo coordinates
     const int nb = krr_tc_nb(d->r), dp = krr_tc_dp(d->d);
     const int64_t npad = krr_tc_npad(d->n);
@@ -466,14 +494,17 @@ static sas_status solve_kernel_family(sas_ctx* c, const double* params, int64_t 
     {
       TraceScope ts(c, SAS_KERNEL_LS, st);
       e = mixed ? launch_ls_mixed(c, pb, mb, yout, nullptr,
-                                  out_kind == SAS_OUT_XHAT ? c->ysplit : nullptr, fb, rb, st, c->Mbuf)
+                                  out_kind == SAS_OUT_XHAT && c->xhat_f32 ? c->ysplit : nullptr, fb,
+                                  rb, st, c->Mbuf)
                 : launch_ls_plain(c, pb, mb, yout, nullptr, fb, rb, st, c->Mbuf);
     }
     if (e != cudaSuccess || out_kind != SAS_OUT_XHAT) continue;
     {
       TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
-      if (mixed)
+      if (mixed && c->xhat_f32)
         e = launch_reconstruct_mixed(c, c->ysplit, mb, (float*)out + b0 * c->n, st);
+      else if (mixed)
+        e = reconstruct_mixed_f64(c, mb, (double*)out + b0 * c->n, st);
       else
         e = launch_reconstruct_f64(c, c->ybuf, mb, (double*)out + b0 * c->n, st);
     }
@@ -514,13 +545,18 @@ sas_status subapsnap_solve_batch(sas_ctx* c, const double* params, int64_t m, in
       if (s2 != SAS_OK) return s2;
       {
         TraceScope ts(c, SAS_KERNEL_LS, st);
-        e = mixed ? launch_ls_mixed(c, params, m, c->ybuf, nullptr, c->ysplit, flags, rho, st)
+        e = mixed ? launch_ls_mixed(c, params, m, c->ybuf, nullptr,
+                                    c->xhat_f32 ? c->ysplit : nullptr, flags, rho, st)
                   : launch_ls_plain(c, params, m, c->ybuf, nullptr, flags, rho, st);
       }
       if (e == cudaSuccess) {
         TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
-        e = mixed ? launch_reconstruct_mixed(c, c->ysplit, m, (float*)out, st)
-                  : launch_reconstruct_f64(c, c->ybuf, m, out, st);
+        if (mixed && c->xhat_f32)
+          e = launch_reconstruct_mixed(c, c->ysplit, m, (float*)out, st);
+        else if (mixed)
+          e = reconstruct_mixed_f64(c, m, (double*)out, st);
+        else
+          e = launch_reconstruct_f64(c, c->ybuf, m, out, st);
       }
       break;
     }
@@ -562,7 +598,7 @@ sas_status subapsnap_solve_batch_host(sas_ctx* c, const double* params, int64_t 
   size_t out_row;  // bytes of one parameter's output
   if (out_kind == SAS_OUT_Y) out_row = (size_t)c->r * elt;
   else if (out_kind == SAS_OUT_QOI) out_row = elt;
-  else if (out_kind == SAS_OUT_XHAT) out_row = (size_t)c->n * (mixed ? 4 : 8);
+  else if (out_kind == SAS_OUT_XHAT) out_row = (size_t)c->n * (mixed && c->xhat_f32 ? 4 : 8);
   else return fail(SAS_EINVAL, "bad out_kind");
   // x_hat goes straight into the caller's memory when it is page-locked and mapped: the
   // reconstruction's stores then stream over the host link, which is what bounds this path
@@ -623,7 +659,7 @@ sas_status subapsnap_reconstruct(sas_ctx* c, const void* Y, int64_t m, void* out
   if (c->dtype != SAS_REAL64) return fail(SAS_ENOTSUP, "x_hat output is real-only");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
-  if (c->mode == SAS_MODE_MIXED) {
+  if (c->mode == SAS_MODE_MIXED && c->xhat_f32) {
     sas_status s2 = ensure_scratch(c, m, true, st);
     if (s2 != SAS_OK) return s2;
     const int rpad = (c->r + 31) / 32 * 32;
@@ -632,6 +668,14 @@ sas_status subapsnap_reconstruct(sas_ctx* c, const void* Y, int64_t m, void* out
       TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
       e = launch_reconstruct_mixed(c, c->ysplit, m, (float*)out, st);
     }
+  } else if (c->mode == SAS_MODE_MIXED) {
+    sas_status s2 = ensure_scratch(c, m, true, st);
+    if (s2 != SAS_OK) return s2;
+    TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
+    if (c->recon_kernel != 1 && reconstruct_x64_supported(c))
+      e = launch_reconstruct_x64(c, (const double*)Y, m, (double*)out, c->yx64, st);
+    else
+      e = launch_reconstruct_f64(c, Y, m, out, st);
   } else {
     TraceScope ts(c, SAS_KERNEL_RECONSTRUCT, st);
     e = launch_reconstruct_f64(c, Y, m, out, st);
@@ -980,6 +1024,20 @@ sas_status subapsnap_autotune(sas_ctx* c, const double* params, int64_t m, int32
   return SAS_OK;
 }
 
+sas_status subapsnap_output_row_bytes(const sas_ctx* c, int32_t out_kind, int64_t* bytes) {
+  if (!c || !bytes) return fail(SAS_EINVAL, "NULL argument");
+  const int64_t elt = c->dtype == SAS_COMPLEX128 ? 16 : 8;
+  switch (out_kind) {
+    case SAS_OUT_Y: *bytes = (int64_t)c->r * elt; return SAS_OK;
+    case SAS_OUT_QOI: *bytes = elt; return SAS_OK;
+    case SAS_OUT_XHAT:
+      *bytes = c->n * (c->mode == SAS_MODE_MIXED && c->xhat_f32 ? 4 : elt);
+      return SAS_OK;
+    default:
+      return fail(SAS_EINVAL, "bad out_kind");
+  }
+}
+
 sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");
   switch (key) {
@@ -999,6 +1057,12 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
     case SAS_OPT_RECON_STORE:
       if (value != 0.0 && value != 1.0) return fail(SAS_EINVAL, "recon store must be 0 or 1");
       c->recon_store = (int)value;
+      return SAS_OK;
+    case SAS_OPT_XHAT_F32:
+      if (value != 0.0 && value != 1.0) return fail(SAS_EINVAL, "xhat f32 must be 0 or 1");
+      if (value == 1.0 && c->mode == SAS_MODE_MIXED && c->dtype == SAS_REAL64 && !c->Shi)
+        return fail(SAS_ENOTSUP, "this context has no float32 copy of S");
+      c->xhat_f32 = (int)value;
       return SAS_OK;
     case SAS_OPT_HOST_CHUNK:
       if (!(value >= 1.0 && value <= 1099511627776.0)) return fail(SAS_EINVAL, "host chunk must be in [1, 2^40] bytes");

@@ -172,6 +172,9 @@ struct sas_ctx {
   void* S16hi;         // mixed reconstruction, f16 form: 2^shift S high part, n x 64 (f16)
   void* S16lo;         // 2^11-scaled remainder
   int s16_shift;       // power-of-two scale of S in the f16 split
+  void* Sx64;          // mixed reconstruction, float64-accurate form: 5 planes of 9-bit
+                       // digits of the max-scaled rows of S (f16, rows of 64, n rounded to 128)
+  int* Sx64_exp;       // per-row exponent e_i of that split (n)
   float* StHi;         // mixed kernel family: S^T tf32 high part, nb x npad (tensor-core rows)
   float* StLo;         // low part
   float* Xc32;         // mixed kernel family: float32 hi/lo coordinates of every point
@@ -186,6 +189,8 @@ struct sas_ctx {
   size_t ysplit_bytes;
   void* ysplit16;      // mixed, f16 reconstruction: y split into f16 hi/lo (2 x m x 64) + m scales
   size_t ysplit16_bytes;
+  void* yx64;          // mixed, float64-accurate reconstruction: digit planes of y + exponents
+  size_t yx64_bytes;
   void* hstage;        // host-buffer calls: device staging of params, small outputs, x_hat chunks
   size_t hstage_bytes;
   size_t host_chunk;   // bytes of one pageable x_hat chunk (0 = 1 GiB)
@@ -195,6 +200,7 @@ struct sas_ctx {
   void* surrogate;     // learned surrogate network (sas_mlp.cu), or null
   // options
   int recon_kernel;    // 0 auto, 1 CUDA cores, 2-4 tensor cores tf32, 5 tensor cores f16
+  int xhat_f32;        // mixed form: 1 = x_hat in float32 (tf32 x 3), 0 = float64-accurate
   int recon_store;     // tensor-core reconstruction epilogue: 0 TMA stores, 1 direct stores
   int krr_kernel;      // kernel rows of the mixed form: 0 auto, 1 CUDA cores, 2 tensor cores
   int krr_seg_points;  // tensor-core rows: points per TMEM segment before the float64 fold
@@ -266,6 +272,15 @@ cudaError_t launch_reconstruct_mixed(const sas_ctx* c, const float* ysplit, int6
 cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t m, float* out,
                                   cudaStream_t st);
 bool reconstruct_tc_supported(const sas_ctx* c);
+void reconstruct_tc_split(int64_t n, int64_t m, int num_sms, int bn, int* num_mtiles,
+                          int* num_ntiles, int* ngroups, int* ntpg);
+// float64-accurate tensor-core reconstruction (sas_recon_x64.cu)
+cudaError_t setup_x64_basis(sas_ctx* c, cudaStream_t st);
+bool reconstruct_x64_supported(const sas_ctx* c);
+int64_t x64_plane_rows(int64_t rows);
+size_t x64_coeff_bytes(int64_t m);
+cudaError_t launch_reconstruct_x64(const sas_ctx* c, const double* Y, int64_t m, double* out,
+                                   void* scratch, cudaStream_t st);
 cudaError_t launch_wait_selftest(int* status, double seconds, cudaStream_t st);
 cudaError_t launch_split_y(const double* Y, int64_t m, int r, int rpad, float* ysplit,
                            cudaStream_t st);

@@ -170,6 +170,15 @@ __device__ inline void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t
       : "memory");
 }
 
+// kind::f16 MMA that first scales the accumulator: D = A B + 2^-9 D.
+__device__ inline void mma_f16_scale9(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, 9;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc)
+      : "memory");
+}
+
 // TMEM load of 32 lanes x 16 columns (one value per column for this lane).
 __device__ inline void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];

@@ -41,18 +41,22 @@ def _device_reference(sv, P, kind, shape, dtype):
     return out.cpu(), flags.cpu(), rho.cpu()
 
 
-@pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED], ids=["plain", "mixed"])
+@pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED, "mixed-f32"],
+                         ids=["plain", "mixed", "mixed-f32"])
 @pytest.mark.parametrize("pinned", [True, False, "chunked"], ids=["pinned", "pageable", "pageable-chunks"])
 def test_host_buffers_match_device_buffers(c2d, mode, pinned):
     p = c2d.prob
-    sv = AffineSolver(p, c2d.S, c2d.J, mode=mode, device=DEV)
+    f32 = mode == "mixed-f32"
+    sv = AffineSolver(p, c2d.S, c2d.J, mode=api.SAS_MODE_MIXED if f32 else mode, device=DEV)
+    if f32:
+        api.subapsnap_set_option(sv.ctx, api.SAS_OPT_XHAT_F32, 1)
     if pinned == "chunked":  # pageable x_hat through 17-parameter chunks, the last one ragged
         api.subapsnap_set_option(sv.ctx, api.SAS_OPT_HOST_CHUNK, 17 * p.n * 8)
         pinned = False
     params = np.ascontiguousarray(p.test_params)
     m = params.shape[0]
     P = torch.from_numpy(params).to(DEV)
-    xdt = torch.float32 if mode == api.SAS_MODE_MIXED else torch.float64
+    xdt = torch.float32 if f32 else torch.float64
     for kind, shape, dt in ((api.SAS_OUT_Y, (m, p.r), torch.float64), (api.SAS_OUT_XHAT, (m, p.n), xdt)):
         ref, fref, rref = _device_reference(sv, P, kind, shape, dt)
         out = torch.full(shape, float("nan"), dtype=dt)

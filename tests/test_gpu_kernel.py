@@ -51,7 +51,7 @@ def run(prob, S, J, mode, out_kind, params, assembly=0):
     if out_kind == api.SAS_OUT_Y:
         out = torch.empty((m, prob.r), dtype=torch.float64, device="cuda")
     else:
-        out = torch.empty((m, prob.n), dtype=torch.float32 if mode else torch.float64, device="cuda")
+        out = torch.empty((m, prob.n), dtype=torch.float64, device="cuda")
     flags = torch.zeros(m, dtype=torch.int32, device="cuda")
     rho = torch.empty(m, dtype=torch.float64, device="cuda")
     solver.solve(P, out_kind, out, flags, rho)

@@ -1,4 +1,5 @@
-"""Mixed-form reconstruction on the tensor cores (tcgen05) against the oracle.
+"""Mixed-form float32 reconstruction (SAS_OPT_XHAT_F32 = 1) on the tensor cores
+(tcgen05) against the oracle.
 
 x_hat in float32 from tf32 splits of S and y: three products, relative
 error ~2^-21 per product, so <= 2e-6 relative per parameter is the bound.
@@ -26,6 +27,7 @@ from _problems import Case  # noqa: E402
 
 def xhat(case, kernel, params, on_device=False, store=0):
     solver = AffineSolver(case.prob, case.S, case.J, mode=api.SAS_MODE_MIXED, device="cuda")
+    api.subapsnap_set_option(solver.ctx, api.SAS_OPT_XHAT_F32, 1)
     api.subapsnap_set_option(solver.ctx, api.SAS_OPT_RECON_KERNEL, kernel)
     api.subapsnap_set_option(solver.ctx, api.SAS_OPT_RECON_STORE, store)
     m = params.shape[0]
@@ -61,15 +63,18 @@ def test_tensor_core_reconstruction(N, r, s, m):
         assert e_tc.max() <= 2e-6
 
 
-@pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED])
+@pytest.mark.parametrize("mode", [api.SAS_MODE_PLAIN, api.SAS_MODE_MIXED, "mixed-f32"])
 def test_reconstruct_entry_point_matches_solve(mode):
     """subapsnap_reconstruct(Y) gives the x_hat that solve_batch(SAS_OUT_XHAT) gives."""
     case = Case("diffusion_2d", basis="random", N=36, r=60, s=120, m=300)
     p = case.prob
-    solver = AffineSolver(p, case.S, case.J, mode=mode, device="cuda")
+    f32 = mode == "mixed-f32"
+    solver = AffineSolver(p, case.S, case.J, mode=api.SAS_MODE_MIXED if f32 else mode, device="cuda")
+    if f32:
+        api.subapsnap_set_option(solver.ctx, api.SAS_OPT_XHAT_F32, 1)
     P = torch.from_numpy(np.ascontiguousarray(p.test_params)).cuda()
     m = P.shape[0]
-    odt = torch.float64 if mode == api.SAS_MODE_PLAIN else torch.float32
+    odt = torch.float32 if f32 else torch.float64
     X1 = torch.empty((m, p.n), dtype=odt, device="cuda")
     solver.solve(P, api.SAS_OUT_XHAT, X1)
     Y = torch.empty((m, p.r), dtype=torch.float64, device="cuda")
@@ -80,7 +85,7 @@ def test_reconstruct_entry_point_matches_solve(mode):
     torch.cuda.synchronize()
     a, b = X2.double().cpu().numpy(), X1.double().cpu().numpy()
     err = np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
-    assert err.max() <= (1e-12 if mode == api.SAS_MODE_PLAIN else 2e-6)
+    assert err.max() <= (2e-6 if f32 else 1e-12)
     solver.close()
 
 
