@@ -2,14 +2,16 @@
 
 Workload: 2-D parametric diffusion, 1024 x 1024 interior grid (n = 1,048,576),
 A(p) = A_0 + sum_k p_k A_k (5 CSR blocks), r = 60, s = 120, m = 4096 new
-parameters per step, the full x of every parameter reconstructed into HBM
-(17.2 GB in float32).  One step = all 4096 parameters through assembly, least
+parameters per step, the full x of every parameter reconstructed into HBM in
+float64 (34.4 GB).  One step = all 4096 parameters through assembly, least
 squares and reconstruction.
 
 Metric: new-parameter solves per second (whole job), for the chosen form
-(float32 Householder with float64-residual refinement, float32 x from the
-tf32-split tensor-core reconstruction) next to the plain float64 form; both
-report the subsampled relative residual (max, median) they reach.
+(float32 Householder with float64-residual refinement, float64 x from the
+fixed-point digit products on the tensor cores) next to the plain float64
+form, at equal relative residual: both report the true relative residual
+||A(p) x - b|| / ||b|| (max, median) of their x on 64 parameters and the
+subsampled residual of every parameter.
 
 Launch: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 it runs under torch.distributed.run, one rank per GPU; every rank
@@ -34,7 +36,7 @@ if ROOT not in sys.path:
 GRID = 1024
 R, S_ROWS, M = 60, 120, 4096
 E2E_CHUNK = 512  # x_hat leaves the device in chunks of 512 parameters
-TC_VERSION = "tcgen05-v3-direct-stores"
+TC_VERSION = "x64-digits-v1"
 METRIC = "new-p solves/sec on 1 GB300 at stated rel. residual (chosen vs plain FP64)"
 WORKLOAD = "diffusion_2d_1024x1024_r60_s120_m4096"
 
@@ -188,6 +190,8 @@ def run_gpu(args):
         pg = dist
     t_setup = time.time()
     prob, blocks, S_rows, J, gaps, P, params_host, snap_res = build_inputs(device, rank, args.grid)
+    Mb = M if args.m is None else int(args.m)  # parameters per step (profiling runs use fewer)
+    P, params_host = P[:Mb].contiguous(), params_host[:Mb]
     chosen = AffineSolver(prob, None, J, mode=api.SAS_MODE_MIXED, device=device, S_device=S_rows,
                           blocks_device=blocks)
     plain = AffineSolver(prob, None, J, mode=api.SAS_MODE_PLAIN, device=device, S_device=S_rows,
@@ -198,18 +202,18 @@ def run_gpu(args):
         api.subapsnap_set_option(chosen.ctx, api.SAS_OPT_LS_VARIANT, args.ls_variant)
     else:
         for name, sv in (("chosen", chosen), ("plain", plain)):
-            v, times = api.subapsnap_autotune(sv.ctx, P, M, 2)
+            v, times = api.subapsnap_autotune(sv.ctx, P, Mb, 2)
             tune[name] = {"variant": v, "ms": {str(i): round(t, 4) for i, t in enumerate(times) if t >= 0}}
     n = prob.n
-    out32 = torch.empty((M, n), dtype=torch.float32, device=device)
-    out64 = torch.empty((M, n), dtype=torch.float64, device=device)
-    rho_c = torch.empty(M, dtype=torch.float64, device=device)
-    rho_p = torch.empty(M, dtype=torch.float64, device=device)
-    flags = torch.empty(M, dtype=torch.int32, device=device)
+    out64c = torch.empty((Mb, n), dtype=torch.float64, device=device)
+    out64 = torch.empty((Mb, n), dtype=torch.float64, device=device)
+    rho_c = torch.empty(Mb, dtype=torch.float64, device=device)
+    rho_p = torch.empty(Mb, dtype=torch.float64, device=device)
+    flags = torch.empty(Mb, dtype=torch.int32, device=device)
     stream = torch.cuda.current_stream()
     setup_s = time.time() - t_setup
 
-    Ystep = torch.empty((M, R), dtype=torch.float64, device=device)
+    Ystep = torch.empty((Mb, R), dtype=torch.float64, device=device)
 
     def step(solver, out, rho):
         # one least-squares launch for the whole batch, then x_hat of the whole batch
@@ -244,15 +248,27 @@ def run_gpu(args):
 
     # ---- chosen form (headline), with live per-kernel tracing
     api.subapsnap_set_tracing(chosen.ctx, True)
-    ms_chosen, clocks = timed(lambda: step(chosen, out32, rho_c), args.steps, args.warmup,
+    ms_chosen, clocks = timed(lambda: step(chosen, out64c, rho_c), args.steps, args.warmup,
                               sample_clocks=True)
     # the tracer also saw the warm-up: discard, then trace the timed region once more
     api.subapsnap_trace_read(chosen.ctx, api.SAS_KERNEL_LS)
     api.subapsnap_trace_read(chosen.ctx, api.SAS_KERNEL_RECONSTRUCT)
-    ms_traced, _ = timed(lambda: step(chosen, out32, rho_c), args.steps, 0)
+    ms_traced, _ = timed(lambda: step(chosen, out64c, rho_c), args.steps, 0)
     rec_ms, rec_n = api.subapsnap_trace_read(chosen.ctx, api.SAS_KERNEL_RECONSTRUCT)
     ls_ms, ls_n = api.subapsnap_trace_read(chosen.ctx, api.SAS_KERNEL_LS)
     api.subapsnap_set_tracing(chosen.ctx, False)
+
+    # ---- the same step with float32 x_hat (SAS_OPT_XHAT_F32): faster, not residual-equivalent
+    ms_f32 = float("nan")
+    if not args.quick:
+        del out64c
+        torch.cuda.empty_cache()
+        out32 = torch.empty((Mb, n), dtype=torch.float32, device=device)
+        api.subapsnap_set_option(chosen.ctx, api.SAS_OPT_XHAT_F32, 1)
+        ms_f32, _ = timed(lambda: step(chosen, out32, rho_c), max(3, args.steps // 2), 2)
+        api.subapsnap_set_option(chosen.ctx, api.SAS_OPT_XHAT_F32, 0)
+        del out32
+        torch.cuda.empty_cache()
 
     # ---- plain float64 form
     psteps = max(1, min(args.steps, 3))
@@ -270,31 +286,42 @@ def run_gpu(args):
         return
 
     # ---- accuracy of the chosen form against the plain float64 form (same parameters)
-    Yc = torch.empty((M, R), dtype=torch.float64, device=device)
-    Yp = torch.empty((M, R), dtype=torch.float64, device=device)
+    Yc = torch.empty((Mb, R), dtype=torch.float64, device=device)
+    Yp = torch.empty((Mb, R), dtype=torch.float64, device=device)
     chosen.solve(P, api.SAS_OUT_Y, Yc, None, rho_c)
     plain.solve(P, api.SAS_OUT_Y, Yp, None, rho_p)
     torch.cuda.synchronize()
     yerr = (torch.linalg.vector_norm(Yc - Yp, dim=1) / torch.linalg.vector_norm(Yp, dim=1)).cpu().numpy()
     rc, rp = rho_c.cpu().numpy(), rho_p.cpu().numpy()
-    # true residual ||A(p) x - b|| / ||b|| on a sample of 64 parameters (float64 x_hat)
-    sample = slice(0, 64)
-    X64 = torch.empty((64, n), dtype=torch.float64, device=device)
-    plain.solve(P[sample], api.SAS_OUT_XHAT, X64)
-    tr = torch.empty(64, dtype=torch.float64, device=device)
-    plain.true_residual(P[sample], X64, tr)
-    X32 = torch.empty((64, n), dtype=torch.float32, device=device)
-    chosen.solve(P[sample], api.SAS_OUT_XHAT, X32)
-    xerr = (torch.linalg.vector_norm(X32.double() - X64, dim=1) / torch.linalg.vector_norm(X64, dim=1)).cpu().numpy()
-    tr = tr.cpu().numpy()
-    del X64, X32
+    # true residual ||A(p) x - b|| / ||b|| on 64 parameters spread over the batch, for the
+    # plain form's x, the chosen form's x and (context) the float32 x of SAS_OPT_XHAT_F32
+    Ps = P[::max(1, Mb // 64)][:64].contiguous()
+    ns = Ps.shape[0]
+    X64 = torch.empty((ns, n), dtype=torch.float64, device=device)
+    plain.solve(Ps, api.SAS_OUT_XHAT, X64)
+    tr = torch.empty(ns, dtype=torch.float64, device=device)
+    plain.true_residual(Ps, X64, tr)
+    Xc = torch.empty((ns, n), dtype=torch.float64, device=device)
+    chosen.solve(Ps, api.SAS_OUT_XHAT, Xc)
+    trc = torch.empty(ns, dtype=torch.float64, device=device)
+    plain.true_residual(Ps, Xc, trc)
+    xerr = (torch.linalg.vector_norm(Xc - X64, dim=1) / torch.linalg.vector_norm(X64, dim=1)).cpu().numpy()
+    api.subapsnap_set_option(chosen.ctx, api.SAS_OPT_XHAT_F32, 1)
+    X32 = torch.empty((ns, n), dtype=torch.float32, device=device)
+    chosen.solve(Ps, api.SAS_OUT_XHAT, X32)
+    api.subapsnap_set_option(chosen.ctx, api.SAS_OPT_XHAT_F32, 0)
+    tr32 = torch.empty(ns, dtype=torch.float64, device=device)
+    X32d = X32.double()
+    plain.true_residual(Ps, X32d, tr32)
+    tr, trc, tr32 = tr.cpu().numpy(), trc.cpu().numpy(), tr32.cpu().numpy()
+    del X64, Xc, X32, X32d
 
     # ---- end to end through the C-ABI with host buffers: subapsnap_solve_batch_host per
     # chunk of 512 parameters, params from pinned host memory, x_hat written by the
     # reconstruction straight into pinned host memory (the host link, ~190 GB/s, bounds it)
     host_params = torch.from_numpy(np.ascontiguousarray(params_host)).pin_memory()
-    host_out = [torch.empty((E2E_CHUNK, n), dtype=torch.float32).pin_memory() for _ in range(2)]
-    nchunks = M // E2E_CHUNK
+    host_out = [torch.empty((E2E_CHUNK, n), dtype=torch.float64).pin_memory() for _ in range(2)]
+    nchunks = max(1, Mb // E2E_CHUNK)
 
     def e2e_step():
         for c in range(nchunks):
@@ -305,23 +332,24 @@ def run_gpu(args):
     e2e_steps = max(1, min(args.steps, 3))
     ms_e2e, _ = timed(e2e_step, e2e_steps, 1)
     h2d = int(host_params.numel() * 8)
-    d2h = int(nchunks * E2E_CHUNK * n * 4)
+    d2h = int(nchunks * E2E_CHUNK * n * 8)
 
     # ---- roofline of the dominant kernel (the reconstruction in the chosen form)
     hbm, src = peaks()
     rec_avg_ms = rec_ms / max(rec_n, 1)
-    alg_bytes = 4.0 * n * R + 4.0 * n * M + 8.0 * M * R  # S (fp32) once, x_hat (fp32), y
+    # the method's bytes: S read once (float64), x_hat written (float64), y read
+    alg_bytes = 8.0 * n * R + 8.0 * n * Mb + 8.0 * Mb * R
     achieved = alg_bytes / (rec_avg_ms * 1e-3) / 1e9
-    traffic = read_traffic(os.path.join(ROOT, "profiles", "reconstruct_tc_diffusion_2d_1024_traffic.txt"),
+    traffic = read_traffic(os.path.join(ROOT, "profiles", "reconstruct_x64_diffusion_2d_1024_traffic.txt"),
                            chosen_kernel_version())
 
-    value = job_throughput(world, M, ms_chosen)
-    plain_value = job_throughput(world, M, ms_plain)
+    value = job_throughput(world, Mb, ms_chosen)
+    plain_value = job_throughput(world, Mb, ms_plain)
     if args.grid != GRID:
         line_workload = f"diffusion_2d_{args.grid}x{args.grid}_r60_s120_m4096"
     else:
         line_workload = WORKLOAD
-    launches_per_step = 3  # least squares, y split, reconstruction
+    launches_per_step = 3  # least squares, digit split of y, reconstruction
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -333,26 +361,34 @@ def run_gpu(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 (tf32x3 tensor cores, f32 Householder) + f64 refinement residual",
+        "dtype": "f64 x_hat (9-bit digit products on f16 tensor cores, exact int64 assembly); "
+                 "f32 Householder + f64 refinement residual",
         "data": "synthetic (seeded 2-D diffusion workload, snapshot basis from PCG)",
-        "config": {"workload": line_workload, "n": n, "r": R, "s": S_ROWS, "m_per_gpu": M, "e2e_chunk": E2E_CHUNK,
+        "config": {"workload": line_workload, "n": n, "r": R, "s": S_ROWS, "m_per_gpu": Mb, "e2e_chunk": E2E_CHUNK,
                    "parallelism": f"dp{world} (independent parameters)",
-                   "l2": "inputs larger than L2 (S tf32 split 0.54 GB, x_hat 17.2 GB per step)"},
+                   "l2": "inputs larger than L2 (S digit planes 0.67 GB, x_hat 34.4 GB per step)"},
         "plain_fp64": {"value": round(plain_value, 2), "unit": "solves/s", "ms_per_step": round(ms_plain, 3),
                        "reconstruct_ms_per_launch": round(prec_ms / max(prec_n, 1), 4),
                        "ls_ms_per_launch_4096": round(pls_ms / max(pls_n, 1), 4)},
         "speedup_chosen_vs_plain": round(value / plain_value, 2),
-        "residual": {"sub_chosen_max": float(rc.max()), "sub_chosen_median": float(np.median(rc)),
-                     "sub_plain_max": float(rp.max()), "sub_plain_median": float(np.median(rp)),
+        "equal_true_residual": bool(trc.max() <= 1.1 * tr.max() and np.median(trc) <= 1.1 * np.median(tr)),
+        "residual": {"true_chosen_max_64": float(trc.max()), "true_chosen_median_64": float(np.median(trc)),
                      "true_plain_max_64": float(tr.max()), "true_plain_median_64": float(np.median(tr)),
+                     "sub_chosen_max": float(rc.max()), "sub_chosen_median": float(np.median(rc)),
+                     "sub_plain_max": float(rp.max()), "sub_plain_median": float(np.median(rp)),
                      "y_relerr_chosen_vs_plain_max": float(yerr.max()),
                      "x_relerr_chosen_vs_plain_max_64": float(xerr.max())},
-        "roofline": {"bound": "hbm", "kernel": "reconstruct (chosen form)", "achieved": round(achieved, 1),
+        "float32_x_hat_option": {"value": round(job_throughput(world, Mb, ms_f32), 2),
+                                 "ms_per_step": round(ms_f32, 4),
+                                 "true_max_64": float(tr32.max()), "true_median_64": float(np.median(tr32)),
+                                 "note": "SAS_OPT_XHAT_F32: float32 x_hat, not residual-equivalent"},
+        "roofline": {"bound": "hbm", "kernel": "reconstruct_x64_kernel (chosen form)",
+                     "achieved": round(achieved, 1),
                      "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
                      "traffic": traffic, "peak_source": src,
                      "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": round(rec_avg_ms, 5),
                      "ls_avg_launch_ms_4096": round(ls_ms / max(ls_n, 1), 5)},
-        "e2e": {"value": round(world * M / (ms_e2e * 1e-3), 2), "unit": "solves/s",
+        "e2e": {"value": round(world * Mb / (ms_e2e * 1e-3), 2), "unit": "solves/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
@@ -474,7 +510,7 @@ def run_gpu_other(args):
     setup_s = time.time() - t0
 
     def outbuf(mode):
-        dt = out_dtype or (torch.float32 if mode == api.SAS_MODE_MIXED else torch.float64)
+        dt = out_dtype or torch.float64
         return torch.empty(out_shape, dtype=dt, device=device)
 
     out_c, out_p = outbuf(api.SAS_MODE_MIXED), outbuf(api.SAS_MODE_PLAIN)
@@ -609,8 +645,8 @@ def run_gpu_surrogate(args):
 
     Step (chosen form): gated solve of 65,536 parameters for the grid-mean QoI
     (network prediction accepted when the float64 subsampled residual <= 1e-6,
-    mixed least squares otherwise) plus full x_hat for 256 of them (float32,
-    tensor cores).  Plain form: float64 least squares for the 65,536 QoI and
+    mixed least squares otherwise) plus full x_hat for 256 of them (float64
+    from the tensor-core digit products).  Plain form: float64 least squares for the 65,536 QoI and
     float64 x_hat for the 256.
     """
     import torch
@@ -652,13 +688,13 @@ def run_gpu_surrogate(args):
     rho_c = torch.empty(m, dtype=torch.float64, device=device)
     flags = torch.zeros(m, dtype=torch.int32, device=device)
     Ysub = torch.empty((nx, r), dtype=torch.float64, device=device)
-    X32 = torch.empty((nx, n), dtype=torch.float32, device=device)
+    Xc = torch.empty((nx, n), dtype=torch.float64, device=device)
     acc = [0]
 
     def step_chosen():
         acc[0] = api.subapsnap_solve_batch_surrogate(chosen.ctx, P, m, api.SAS_OUT_QOI, H, flags, rho_c, tol)
         api.subapsnap_solve_batch_surrogate(chosen.ctx, P[:nx], nx, api.SAS_OUT_Y, Ysub, None, None, tol)
-        chosen.reconstruct(Ysub, X32)
+        chosen.reconstruct(Ysub, Xc)
 
     Hp = torch.empty(m, dtype=torch.float64, device=device)
     rho_p = torch.empty(m, dtype=torch.float64, device=device)
@@ -673,7 +709,7 @@ def run_gpu_surrogate(args):
     def step_mixed_only():  # mixed least squares for everything, no network
         chosen.solve(P, api.SAS_OUT_QOI, H, None, rho_c)
         chosen.solve(P[:nx], api.SAS_OUT_Y, Ysub)
-        chosen.reconstruct(Ysub, X32)
+        chosen.reconstruct(Ysub, Xc)
 
     stream = torch.cuda.current_stream()
 
@@ -708,7 +744,7 @@ def run_gpu_surrogate(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_c, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "surrogate (bf16 weights, f32 accumulate) gated by f64 subsampled residual; "
-                 "fallback f32 Householder + f64 refinement; x_hat f32 (tf32x3)",
+                 "fallback f32 Householder + f64 refinement; x_hat f64 (tensor-core digit products)",
         "data": "synthetic (seeded 2-D diffusion 4096^2, snapshot basis from PCG)",
         "config": {"workload": f"surrogate_diffusion_2d_{N}x{N}_r60_s120_m65536_x256", "n": n, "r": r,
                    "s": prob.s, "m_per_gpu": m, "x_hat_params": nx, "gate_tol": tol,
@@ -808,7 +844,7 @@ def run_selection_variants(args):
     """The subsampling variants of Sec. 4.3.4 on the headline workload: rows chosen at the
     median point (the default), the union of the CPQR picks at three snapshot points, and
     per-parameter rows from the nearest of three points.  Each is timed on the headline
-    step (the float32 form, y of the whole batch then x_hat) and scored by the true
+    step (the mixed form, y of the whole batch then float64 x_hat) and scored by the true
     residual of its float64 x_hat on 64 parameters.  One JSON line."""
     import torch
     from paper_2510_04825_gb300 import api
@@ -823,7 +859,7 @@ def run_selection_variants(args):
     nearest_idx = None
     variants = {}
     Jset = {"median_point": J, "union_3_points": select_rows_union(prob, S_rows, blocks, pts, R)}
-    out32 = torch.empty((M, n), dtype=torch.float32, device=device)
+    outc = torch.empty((M, n), dtype=torch.float64, device=device)
     Y = torch.empty((M, R), dtype=torch.float64, device=device)
     stream = torch.cuda.current_stream()
 
@@ -870,7 +906,7 @@ def run_selection_variants(args):
 
         def step():
             chosen.solve(Pv, api.SAS_OUT_Y, Y)
-            chosen.reconstruct(Y, out32)
+            chosen.reconstruct(Y, outc)
 
         ms = timed(step, max(3, args.steps // 3), args.warmup)
         chosen.close()

@@ -94,6 +94,32 @@ __device__ inline int cvt_rni(float x) {
   return r;
 }
 
+// One entry of the fast path: V = a 2^18 + rint(P_2) 2^9 + rint(T) as an exact
+// int64, converted once to float64, with the scale 2^E applied as an integer add of
+// add = E 2^20 to the high word (V = 0 keeps its all-zero bits).
+__device__ __forceinline__ double assemble(int a, float p2, float t, int add) {
+  double x;
+  asm("{\n"
+      " .reg .s32 i2, it, lo, hi;\n"
+      " .reg .s64 t64, v;\n"
+      " .reg .f64 d;\n"
+      " .reg .pred pz;\n"
+      " cvt.rni.s32.f32 i2, %2;\n"
+      " cvt.rni.s32.f32 it, %3;\n"
+      " cvt.s64.s32 t64, it;\n"
+      " mad.wide.s32 v, i2, 512, t64;\n"
+      " mad.wide.s32 v, %1, 262144, v;\n"
+      " cvt.rn.f64.s64 d, v;\n"
+      " mov.b64 {lo, hi}, d;\n"
+      " setp.ne.s32 pz, hi, 0;\n"
+      " @pz add.s32 hi, hi, %4;\n"
+      " mov.b64 %0, {lo, hi};\n"
+      "}\n"
+      : "=d"(x)
+      : "r"(a), "f"(p2), "f"(t), "r"(add));
+  return x;
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
     reconstruct_x64_kernel(const __grid_constant__ CUtensorMap tmS,
                            const __grid_constant__ CUtensorMap tmY, Params p) {
@@ -281,10 +307,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       int mt, nt0, nt1;
       unit_range(p, u, mt, nt0, nt1);
       const int64_t row = (int64_t)mt * kBM + q * 32 + lane;
-      const int erow = row < p.n ? p.erow[row] : 0;
+      const bool row_ok = row < p.n;
+      const int erow = row_ok ? p.erow[row] : 0;
+      const int emin = __reduce_min_sync(0xffffffffu, erow);
+      const int emax = __reduce_max_sync(0xffffffffu, erow);
       for (int k = 0; k < nt1 - nt0; ++k, ++t) {
         const int64_t j0 = (int64_t)(nt0 + k) * kBN + cb * 32;
         const int fcol = j0 + lane < p.m ? p.ecol[j0 + lane] : 0;
+        // fast path (warp-uniform): all 32 columns present and every E = e_i + f_j - 45 such
+        // that V 2^E with 1 <= |V| < 2^46 stays a normal float64; then the scaling is one
+        // integer add to the high word.  Otherwise every entry takes the checked path.
+        const int fmin = __reduce_min_sync(0xffffffffu, fcol);
+        const int fmax = __reduce_max_sync(0xffffffffu, fcol);
+        const bool fast = j0 + 32 <= p.m && emin + fmin - 45 >= -1022 && emax + fmax - 45 <= 977;
+        const int ehi = erow * (1 << 20);              // e_i in the exponent field of the high word
+        const int fhi = (fcol - 45) * (1 << 20);       // f_j - 45, lane c holds column c's
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
         const uint32_t par = (uint32_t)t & 1u;
         int acol[32];
@@ -326,21 +363,38 @@ __global__ void __launch_bounds__(kThreads, 1)
               mbar_arrive(tempty0 + 24);
             }
           }
+          if (fast) {
+            double* o = orow + (int64_t)(16 * h) * p.n;
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int cc = 16 * h + c;
-            const long long V = (long long)acol[cc] * 262144ll + (long long)cvt_rni(w2[c]) * 512ll +
-                                (long long)cvt_rni(w3[c]);
-            const int E = erow + __shfl_sync(0xffffffffu, fcol, cc) - 45;
-            const long long bits = __double_as_longlong((double)V);
-            const int ex = (int)((bits >> 52) & 0x7ff) + E;
-            // V 2^E: the exponent field moves by E; below the normal range the entry is
-            // flushed to zero, above it overflows to +-inf
-            double x = __longlong_as_double(bits + ((long long)E << 52));
-            if (V == 0 || ex <= 0) x = 0.0;
-            if (ex >= 2047) x = V > 0 ? __longlong_as_double(0x7ff0000000000000ll)
-                                      : __longlong_as_double((long long)0xfff0000000000000ull);
-            if (row < p.n && j0 + cc < p.m) __stcs(orow + (int64_t)cc * p.n, x);
+            for (int c = 0; c < 16; ++c) {
+              // the shuffle runs on every lane (a full-mask shuffle must not sit under a
+              // lane-dependent condition)
+              const int add = ehi + __shfl_sync(0xffffffffu, fhi, 16 * h + c);
+              const double x = assemble(acol[16 * h + c], w2[c], w3[c], add);
+              if (row_ok) __stcs(o, x);
+              o += p.n;
+            }
+          } else {
+            // checked: V 2^E tested against the float64 range (below it the entry is
+            // flushed to zero, above it it overflows to +-inf), ragged columns skipped
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int cc = 16 * h + c;
+              const int E = erow + __shfl_sync(0xffffffffu, fcol, cc) - 45;
+              const double d = assemble(acol[cc], w2[c], w3[c], 0);
+              int hi = __double2hiint(d), lo = __double2loint(d);
+              const int ex = ((hi >> 20) & 0x7ff) + E;
+              if (hi == 0 || ex <= 0) {
+                hi = 0;
+                lo = 0;
+              } else if (ex >= 2047) {
+                hi = (hi & (int)0x80000000) | 0x7ff00000;
+                lo = 0;
+              } else {
+                hi += E * (1 << 20);
+              }
+              if (row_ok && j0 + cc < p.m) __stcs(orow + (int64_t)cc * p.n, __hiloint2double(hi, lo));
+            }
           }
         }
       }

@@ -163,3 +163,32 @@ def test_digit_reconstruction_long_units_against_float64_product():
     assert bool((err <= BOUND * scale + 1e-15 * scale).all().item()), float((err / scale).max())
     pick = [0, 127, 128, 1000, 2047, 2048, 2099]
     check_entries(case.S, Y[pick], Xtc[pick].cpu().numpy(), "long units, sampled parameters")
+
+
+def test_digit_reconstruction_beyond_float64_range():
+    """Entries whose scale 2^{e_i + f_j} puts x outside the normal float64 range take
+    the checked path: below it they are flushed to zero (the float64 product is a
+    subnormal there), above it they overflow to +-inf as the float64 product does;
+    entries of the same launch inside the range stay within the bound."""
+    case = Case("diffusion_2d", basis="random", N=16, r=20, s=40, m=8)
+    n, r = case.prob.n, 20
+    rng = np.random.default_rng(11)
+    S = rng.standard_normal((n, r))
+    band = np.arange(n) % 3  # 0: normal rows, 1: tiny rows, 2: huge rows
+    S[band == 1] *= 1e-250
+    S[band == 2] = np.abs(S[band == 2]) * 1e250  # one sign, so that the float64 sum is +inf, not nan
+    m = 200
+    Y = rng.standard_normal((m, r))
+    Y[: m // 2] *= 1e-80   # tiny rows x tiny coefficients underflow
+    Y[m // 2:] = np.abs(Y[m // 2:]) * 1e80  # huge rows x huge coefficients overflow
+    with np.errstate(over="ignore", invalid="ignore", under="ignore"):
+        ref = online.reconstruct(S, Y)
+    X = reconstruct(case, S, Y)
+    with np.errstate(over="ignore", invalid="ignore", under="ignore"):
+        scale = np.abs(S).max(axis=1)[None, :] * np.abs(Y).sum(axis=1)[:, None]
+    normal = np.isfinite(scale) & (scale > 1e-290) & (scale < 1e290)
+    assert (np.abs(X - ref)[normal] <= BOUND * scale[normal]).all()
+    tiny = (scale <= 1e-320)
+    assert tiny.any() and (X[tiny] == 0.0).all()
+    huge = ~np.isfinite(ref) & ~np.isnan(ref)
+    assert huge.any() and (X[huge] == ref[huge]).all()
