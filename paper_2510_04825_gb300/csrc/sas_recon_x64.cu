@@ -29,21 +29,27 @@
 //   x[i,j] = 2^{e_i + f_j - 45} (P_0 2^27 + P_1 2^18 + P_2 2^9 + rint(T))
 // is formed as an exact int64 (below 2^46) and converted to float64 once.
 //
-// Structure (one persistent CTA per SM, 18 warps):
+// Structure (one persistent CTA per SM, 18 warps; tiles of 128 rows x 128 parameters):
 //   warp 0     TMA producer: per work unit the five S digit tiles of 128 rows
-//              (80 KB, resident for the unit), then for every 128-parameter
-//              tile its five y digit tiles (16 KB each, L2-resident) into an
-//              8-slot ring;
-//   warp 1     one thread issues tcgen05.mma (kind::f16, M = N = 128, K = 16):
-//              per tile 15 digit products x 4 K-steps into 4 TMEM accumulators
-//              of 128 columns, level by level;
+//              (80 KB, resident for the unit), then for every parameter tile its
+//              five y digit tiles (16 KB each, L2-resident) into an 8-slot ring;
+//   warp 1     MMA issuer: the whole warp runs the loop (descriptors stay
+//              warp-uniform) and the elected lane issues tcgen05.mma (kind::f16,
+//              M = N = 128, K = 16): per tile 15 digit products x 4 K-steps into 4
+//              TMEM accumulators of 128 columns (all 512), in the order L0, L1,
+//              tail (L4, then L3 on the scaled sum), L2;
 //   warps 2-17 epilogue, 4 per TMEM lane quarter, 32 columns each.  They drain
-//              P_0 and P_1 as soon as their levels complete (releasing them to
-//              the next tile's first products), then P_2 and T once the tile's
-//              last products complete; they assemble the int64, convert, scale
-//              and store 8 bytes per lane (one coalesced 256-byte warp store per
-//              parameter).  18 warps put 5 on some SM sub-partitions, which caps
-//              registers at 96 per thread: hence the staged drain.
+//              P_0, P_1 (into a = P_0 2^9 + P_1) and the tail (into rint(T)) as
+//              each completes and release it at once, so that the next tile's
+//              first 48 MMAs run while they assemble this tile from P_2; then
+//              they convert (alternating the int64 -> float64 conversion unit and
+//              an integer-only normalisation, so that both work side by side),
+//              scale and store 8 bytes per lane (one coalesced 256-byte warp
+//              store per parameter).  18 warps put 5 on some SM sub-partitions,
+//              which caps registers at 96 per thread.
+// A shared-memory operand pair of f16 at N = 128 reads 8 KB per 64-clock MMA,
+// the SM's shared-memory bandwidth: 128-parameter tiles keep the MMA at its
+// full rate, narrower ones would not.
 // Every mbarrier wait is bounded (2 s of %globaltimer); on expiry the kernel
 // records SAS_ETIMEOUT, stops issuing work, waits (bounded) for its copies and
 // MMAs in flight, frees its TMEM and returns.
@@ -65,8 +71,9 @@ constexpr int kDigits = 5;                // 9-bit digits per operand
 constexpr int kSlots = 8;                 // y digit ring
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr uint32_t kTileBytes = 128 * 128;  // one digit tile: 128 rows x 64 f16 (128-byte rows)
-constexpr uint32_t kTmemCols = 512;         // 4 accumulators x 128 columns
+constexpr uint32_t kATileBytes = kBM * 128;  // one S digit tile: 128 rows x 64 f16 (128-byte rows)
+constexpr uint32_t kBTileBytes = kBN * 128;  // one y digit tile: 128 rows x 64 f16
+constexpr uint32_t kTmemCols = 512;          // 4 accumulators x 128 columns
 constexpr uint32_t kIdesc = f16_idesc(kBM, kBN);
 constexpr int kNumBars = 2 + 2 * kSlots + 8;
 
@@ -94,19 +101,18 @@ __device__ inline int cvt_rni(float x) {
   return r;
 }
 
-// One entry of the fast path: V = a 2^18 + rint(P_2) 2^9 + rint(T) as an exact
-// int64, converted once to float64, with the scale 2^E applied as an integer add of
+// One entry of the fast path: V = a 2^18 + rint(P_2) 2^9 + t as an exact int64,
+// converted once to float64, with the scale 2^E applied as an integer add of
 // add = E 2^20 to the high word (V = 0 keeps its all-zero bits).
-__device__ __forceinline__ double assemble(int a, float p2, float t, int add) {
+__device__ __forceinline__ double assemble(int a, float p2, int t, int add) {
   double x;
   asm("{\n"
-      " .reg .s32 i2, it, lo, hi;\n"
+      " .reg .s32 i2, lo, hi;\n"
       " .reg .s64 t64, v;\n"
       " .reg .f64 d;\n"
       " .reg .pred pz;\n"
       " cvt.rni.s32.f32 i2, %2;\n"
-      " cvt.rni.s32.f32 it, %3;\n"
-      " cvt.s64.s32 t64, it;\n"
+      " cvt.s64.s32 t64, %3;\n"
       " mad.wide.s32 v, i2, 512, t64;\n"
       " mad.wide.s32 v, %1, 262144, v;\n"
       " cvt.rn.f64.s64 d, v;\n"
@@ -116,8 +122,27 @@ __device__ __forceinline__ double assemble(int a, float p2, float t, int add) {
       " mov.b64 %0, {lo, hi};\n"
       "}\n"
       : "=d"(x)
-      : "r"(a), "f"(p2), "f"(t), "r"(add));
+      : "r"(a), "f"(p2), "r"(t), "r"(add));
   return x;
+}
+
+// The same entry converted with integer operations only (no int64 -> float64
+// conversion unit): sign and magnitude of V, leading-zero count, the mantissa shifted
+// to bit 52 and the exponent 1086 - lz + E built in the high word.  The fast path
+// alternates this with assemble() so that the slow conversion unit and the integer
+// pipes work side by side.
+__device__ __forceinline__ double assemble_int(int a, float p2, int t, int add) {
+  const int i2 = cvt_rni(p2);
+  const long long v = (long long)a * 262144ll + (long long)i2 * 512ll + (long long)t;
+  const long long s = v >> 63;
+  unsigned long long u = (unsigned long long)((v ^ s) - s);
+  const int lz = __clzll((long long)u);
+  u <<= (lz - 11);  // leading bit at 52 (|V| < 2^47, so lz >= 17)
+  unsigned h = ((unsigned)(u >> 32) & 0xFFFFFu) | ((unsigned)(1086 - lz) << 20);
+  h += (unsigned)add;
+  h |= (unsigned)s & 0x80000000u;
+  if (lz == 64) h = 0;  // V = 0
+  return __hiloint2double((int)h, (int)(unsigned)u);
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -127,8 +152,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   uint8_t* A0 = base;                                    // sigma_0..4 of the unit's row tile
-  uint8_t* B0 = A0 + (size_t)kDigits * kTileBytes;       // ring of y digit tiles
-  uint64_t* bars = reinterpret_cast<uint64_t*>(B0 + (size_t)kSlots * kTileBytes);
+  uint8_t* B0 = A0 + (size_t)kDigits * kATileBytes;      // ring of y digit tiles
+  uint64_t* bars = reinterpret_cast<uint64_t*>(B0 + (size_t)kSlots * kBTileBytes);
   // bars: afull, aempty, bfull[kSlots], bempty[kSlots], tfull[4], tempty[4]
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -177,24 +202,24 @@ __global__ void __launch_bounds__(kThreads, 1)
           const int nt = nt0 + k;
           for (int b = 0; b < kDigits; ++b) {
             const int s = g % kSlots;
-            if (!mbar_wait(bempty0 + 8 * s, ((uint32_t)(g / kSlots) & 1u) ^ 1u, &abort_flag,
+            if (!mbar_wait_idle(bempty0 + 8 * s, ((uint32_t)(g / kSlots) & 1u) ^ 1u, &abort_flag,
                            p.status)) {
               stop = true;
               break;
             }
-            mbar_expect_tx(bfull0 + 8 * s, kTileBytes);
-            tma_load_2d(smem_u32(B0 + (size_t)s * kTileBytes), &tmY, 0, b * p.y_plane + nt * kBN,
-                        bfull0 + 8 * s);
+            mbar_expect_tx(bfull0 + 8 * s, kBTileBytes);
+            tma_load_2d(smem_u32(B0 + (size_t)s * kBTileBytes), &tmY, 0,
+                        b * p.y_plane + nt * kBN, bfull0 + 8 * s);
             ++g;
             if (k == 0 && b == 0) {
               // the S digit tiles free when the last MMA of the previous unit completes
-              if (!mbar_wait(aempty, ((uint32_t)at & 1u) ^ 1u, &abort_flag, p.status)) {
+              if (!mbar_wait_idle(aempty, ((uint32_t)at & 1u) ^ 1u, &abort_flag, p.status)) {
                 stop = true;
                 break;
               }
-              mbar_expect_tx(afull, kDigits * kTileBytes);
+              mbar_expect_tx(afull, kDigits * kATileBytes);
               for (int a = 0; a < kDigits; ++a)
-                tma_load_2d(smem_u32(A0 + (size_t)a * kTileBytes), &tmS, 0,
+                tma_load_2d(smem_u32(A0 + (size_t)a * kATileBytes), &tmS, 0,
                             a * p.s_plane + mt * kBM, afull);
               a_issued = at++;
             }
@@ -211,92 +236,121 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      // ---------------- MMA issuer
-      int t = 0, ua = 0;
-      uint32_t last_bar = 0, last_par = 0;
-      bool any = false, stop = false;
-      const uint32_t a_base = smem_u32(A0), b_base = smem_u32(B0);
-      for (int u = blockIdx.x; u < p.num_units && !stop; u += gridDim.x) {
-        int mt, nt0, nt1;
-        unit_range(p, u, mt, nt0, nt1);
-        if (nt0 >= nt1) continue;
-        if (!mbar_wait(afull, (uint32_t)ua & 1u, &abort_flag, p.status)) break;
-        for (int k = 0; k < nt1 - nt0; ++k) {
-          const int gb = kDigits * t;  // ring index of this tile's tau_0
-          // digit tile addresses and their readiness
-          auto bslot = [&](int b) -> uint32_t {
-            return b_base + (uint32_t)((gb + b) % kSlots) * kTileBytes;
-          };
-          auto wait_digit = [&](int b) -> bool {
-            const int gg = gb + b;
-            const bool ok = mbar_wait(bfull0 + 8 * (gg % kSlots), (uint32_t)(gg / kSlots) & 1u,
-                                      &abort_flag, p.status);
-            fence_after();
-            return ok;
-          };
-          auto wait_acc = [&](int acc) -> bool {
-            const bool ok = mbar_wait(tempty0 + 8 * acc, ((uint32_t)t & 1u) ^ 1u, &abort_flag,
-                                      p.status);
-            fence_after();
-            return ok;
-          };
-          // one digit product sigma_a tau_b (K = 64 in four steps of 16) into accumulator acc
-          auto prod = [&](int acc, int a, int b, bool first) {
-            const uint32_t d = tmem + (uint32_t)(acc * kBN);
-            const uint32_t aa = a_base + (uint32_t)a * kTileBytes, bb = bslot(b);
+    // ---------------- MMA issuer: the whole warp runs the loop, so that descriptors and
+    // counters are warp-uniform; the elected lane issues the MMAs and their commits.
+    // Per tile the levels go in the order L0, L1, tail (L4 then L3), L2: the epilogue
+    // drains the first three as they complete, so that while it assembles the tile
+    // from P_2 the next tile's first 48 MMAs already run.
+    const bool leader = elect_one();
+    int t = 0, ua = 0;
+    uint32_t last_bar = 0, last_par = 0;
+    bool any = false, stop = false;
+    const uint32_t a_base = smem_u32(A0), b_base = smem_u32(B0);
+    uint64_t ad[kDigits];  // descriptors of the resident S digit tiles
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              mma_f16(d, smem_desc(aa + ks * 32), smem_desc(bb + ks * 32), kIdesc,
-                      (first && ks == 0) ? 0u : 1u);
-          };
-          auto prod_scaled = [&](int acc, int a, int b) {
-            const uint32_t d = tmem + (uint32_t)(acc * kBN);
-            const uint32_t aa = a_base + (uint32_t)a * kTileBytes, bb = bslot(b);
-            mma_f16_scale9(d, smem_desc(aa), smem_desc(bb), kIdesc);
+    for (int a = 0; a < kDigits; ++a) ad[a] = smem_desc(a_base + (uint32_t)a * kATileBytes);
+    auto wait_all = [&](uint32_t bar, uint32_t par) -> bool {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_idle(bar, par, &abort_flag, p.status));
+      fence_after();
+      return ok;
+    };
+    for (int u = blockIdx.x; u < p.num_units && !stop; u += gridDim.x) {
+      int mt, nt0, nt1;
+      unit_range(p, u, mt, nt0, nt1);
+      if (nt0 >= nt1) continue;
+      if (!wait_all(afull, (uint32_t)ua & 1u)) break;
+      for (int k = 0; k < nt1 - nt0; ++k) {
+        const int gb = kDigits * t;  // ring index of this tile's tau_0
+        const uint32_t free_par = ((uint32_t)t & 1u) ^ 1u;  // accumulators drained for tile t - 1
+        // descriptors of this tile's y digits; a K step of 16 f16 advances the start
+        // address field (16-byte units) by 2
+        uint64_t bd[kDigits];
+        uint32_t bfull_b[kDigits], bpar[kDigits];
 #pragma unroll
-            for (int ks = 1; ks < 4; ++ks)
-              mma_f16(d, smem_desc(aa + ks * 32), smem_desc(bb + ks * 32), kIdesc, 1u);
-          };
-          // level 0: sigma_0 tau_0
-          if (!wait_digit(0) || !wait_acc(0)) { stop = true; break; }
+        for (int b = 0; b < kDigits; ++b) {
+          const int gg = gb + b, sl = gg % kSlots;
+          bd[b] = smem_desc(b_base + (uint32_t)sl * kBTileBytes);
+          bfull_b[b] = bfull0 + 8 * sl;
+          bpar[b] = (uint32_t)(gg / kSlots) & 1u;
+        }
+        // one digit product sigma_a tau_b (K = 64 in four steps of 16) into accumulator acc
+        auto prod = [&](int acc, int a, int b, bool first) {
+          const uint32_t d = tmem + (uint32_t)(acc * kBN);
+          if (first)
+            mma_f16_c<false>(d, ad[a], bd[b], kIdesc);
+          else
+            mma_f16_c<true>(d, ad[a], bd[b], kIdesc);
+#pragma unroll
+          for (int ks = 1; ks < 4; ++ks) mma_f16_c<true>(d, ad[a] + 2 * ks, bd[b] + 2 * ks, kIdesc);
+        };
+        auto prod_scaled = [&](int acc, int a, int b) {
+          const uint32_t d = tmem + (uint32_t)(acc * kBN);
+          mma_f16_scale9(d, ad[a], bd[b], kIdesc);
+#pragma unroll
+          for (int ks = 1; ks < 4; ++ks) mma_f16_c<true>(d, ad[a] + 2 * ks, bd[b] + 2 * ks, kIdesc);
+        };
+        // levels 0 and 1
+        if (!wait_all(bfull_b[0], bpar[0]) || !wait_all(bfull_b[1], bpar[1]) ||
+            !wait_all(tempty0, free_par) || !wait_all(tempty0 + 8, free_par)) {
+          stop = true;
+          break;
+        }
+        if (leader) {
           prod(0, 0, 0, true);
           mma_commit(tfull0);
-          // level 1
-          if (!wait_digit(1) || !wait_acc(1)) { stop = true; break; }
           prod(1, 0, 1, true);
           prod(1, 1, 0, false);
           mma_commit(tfull0 + 8);
-          // level 2
-          if (!wait_digit(2) || !wait_acc(2)) { stop = true; break; }
-          prod(2, 0, 2, true);
-          prod(2, 1, 1, false);
-          prod(2, 2, 0, false);
-          // levels 4 then 3 into the tail accumulator: T = P_3 + 2^-9 P_4
-          if (!wait_acc(3)) { stop = true; break; }
+        }
+        __syncwarp();
+        // the tail, T = P_3 + 2^-9 P_4: level 4 first, then level 3 on the scaled sum
+        if (!wait_all(tempty0 + 24, free_par) || !wait_all(bfull_b[2], bpar[2])) {
+          stop = true;
+          break;
+        }
+        if (leader) {
           prod(3, 4, 0, true);
           prod(3, 3, 1, false);
           prod(3, 2, 2, false);
-          if (!wait_digit(3)) { stop = true; break; }
+        }
+        __syncwarp();
+        if (!wait_all(bfull_b[3], bpar[3]) || !wait_all(bfull_b[4], bpar[4])) {
+          stop = true;
+          break;
+        }
+        if (leader) {
           prod(3, 1, 3, false);
-          if (!wait_digit(4)) { stop = true; break; }
           prod(3, 0, 4, false);
           prod_scaled(3, 3, 0);
           prod(3, 2, 1, false);
           prod(3, 1, 2, false);
           prod(3, 0, 3, false);
           mma_commit(tfull0 + 24);
-          for (int b = 0; b < kDigits; ++b) mma_commit(bempty0 + 8 * ((gb + b) % kSlots));
-          if (k == nt1 - nt0 - 1) mma_commit(aempty);
-          last_bar = tfull0 + 24;
-          last_par = (uint32_t)t & 1u;
-          any = true;
-          ++t;
         }
-        ++ua;
+        __syncwarp();
+        // level 2 last
+        if (!wait_all(tempty0 + 16, free_par)) {
+          stop = true;
+          break;
+        }
+        if (leader) {
+          prod(2, 0, 2, true);
+          prod(2, 1, 1, false);
+          prod(2, 2, 0, false);
+          mma_commit(tfull0 + 16);
+#pragma unroll
+          for (int b = 0; b < kDigits; ++b) mma_commit(bfull_b[b] + 8 * kSlots);  // bempty of the slot
+          if (k == nt1 - nt0 - 1) mma_commit(aempty);
+        }
+        __syncwarp();
+        last_bar = tfull0 + 16;
+        last_par = (uint32_t)t & 1u;
+        any = true;
+        ++t;
       }
-      if (any) mbar_drain(last_bar, last_par);
+      ++ua;
     }
+    if (any && leader) mbar_drain(last_bar, last_par);
   } else {
     // ---------------- epilogue: warps 2 .. 17; lane quarter q = warp % 4 (the TMEM lanes
     // this warp may read), column block cb of 32 of the tile's 128 parameters
@@ -311,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int erow = row_ok ? p.erow[row] : 0;
       const int emin = __reduce_min_sync(0xffffffffu, erow);
       const int emax = __reduce_max_sync(0xffffffffu, erow);
+      const int ehi = erow * (1 << 20);  // e_i in the exponent field of the high word
       for (int k = 0; k < nt1 - nt0; ++k, ++t) {
         const int64_t j0 = (int64_t)(nt0 + k) * kBN + cb * 32;
         const int fcol = j0 + lane < p.m ? p.ecol[j0 + lane] : 0;
@@ -320,49 +375,50 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int fmin = __reduce_min_sync(0xffffffffu, fcol);
         const int fmax = __reduce_max_sync(0xffffffffu, fcol);
         const bool fast = j0 + 32 <= p.m && emin + fmin - 45 >= -1022 && emax + fmax - 45 <= 977;
-        const int ehi = erow * (1 << 20);              // e_i in the exponent field of the high word
-        const int fhi = (fcol - 45) * (1 << 20);       // f_j - 45, lane c holds column c's
+        const int fhi = (fcol - 45) * (1 << 20);  // f_j - 45, lane c holds column c's
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
         const uint32_t par = (uint32_t)t & 1u;
-        int acol[32];
+        int acol[32], itail[32];
         float v[32];
-        // P_0 and P_1: a = P_0 2^9 + P_1 (|a| < 2^28); both accumulators are released
-        // as soon as they are read, so that the next tile's first levels can start
-        if (!__all_sync(0xffffffffu, mbar_wait(tfull0, par, &abort_flag, p.status))) { stop = true; break; }
-        fence_after();
+        auto wait_acc = [&](int acc) -> bool {
+          const bool ok = __all_sync(0xffffffffu, mbar_wait_idle(tfull0 + 8 * acc, par, &abort_flag,
+                                                                p.status));
+          fence_after();
+          return ok;
+        };
+        auto release = [&](int acc) {
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
+        };
+        // P_0 and P_1 -> a = P_0 2^9 + P_1 (|a| < 2^28); T -> rint(T); each accumulator is
+        // released as soon as it is read, for the next tile's first 48 MMAs
+        if (!wait_acc(0)) { stop = true; break; }
         tmem_ld32(ta, v);
+        release(0);
 #pragma unroll
         for (int c = 0; c < 32; ++c) acol[c] = cvt_rni(v[c]);
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty0);
-        if (!__all_sync(0xffffffffu, mbar_wait(tfull0 + 8, par, &abort_flag, p.status))) { stop = true; break; }
-        fence_after();
+        if (!wait_acc(1)) { stop = true; break; }
         tmem_ld32(ta + kBN, v);
+        release(1);
 #pragma unroll
         for (int c = 0; c < 32; ++c) acol[c] = acol[c] * 512 + cvt_rni(v[c]);
-        fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(tempty0 + 8);
-        // P_2 and T once the tile's last products completed (the commit after the tail
-        // covers every earlier MMA), 16 columns at a time;
-        // x = 2^{e_i + f_j - 45} (a 2^18 + P_2 2^9 + rint(T))
-        if (!__all_sync(0xffffffffu, mbar_wait(tfull0 + 24, par, &abort_flag, p.status))) { stop = true; break; }
-        fence_after();
+        if (!wait_acc(3)) { stop = true; break; }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tmem_ld16(ta + 3 * kBN + 16 * h, v);
+          if (h == 1) release(3);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) itail[16 * h + c] = cvt_rni(v[c]);
+        }
+        // P_2 last, 16 columns at a time: x = 2^{e_i + f_j - 45} (a 2^18 + P_2 2^9 + rint(T))
+        if (!wait_acc(2)) { stop = true; break; }
         double* orow = p.out + j0 * p.n + row;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          float w2[16], w3[16];
-          tmem_ld16(ta + 2 * kBN + 16 * h, w2);
-          tmem_ld16(ta + 3 * kBN + 16 * h, w3);
-          if (h == 1) {
-            fence_before();
-            __syncwarp();
-            if (lane == 0) {
-              mbar_arrive(tempty0 + 16);
-              mbar_arrive(tempty0 + 24);
-            }
-          }
+          float w[16];
+          tmem_ld16(ta + 2 * kBN + 16 * h, w);
+          if (h == 1) release(2);
           if (fast) {
             double* o = orow + (int64_t)(16 * h) * p.n;
 #pragma unroll
@@ -370,7 +426,8 @@ __global__ void __launch_bounds__(kThreads, 1)
               // the shuffle runs on every lane (a full-mask shuffle must not sit under a
               // lane-dependent condition)
               const int add = ehi + __shfl_sync(0xffffffffu, fhi, 16 * h + c);
-              const double x = assemble(acol[16 * h + c], w2[c], w3[c], add);
+              const double x = (c & 1) ? assemble(acol[16 * h + c], w[c], itail[16 * h + c], add)
+                                       : assemble_int(acol[16 * h + c], w[c], itail[16 * h + c], add);
               if (row_ok) __stcs(o, x);
               o += p.n;
             }
@@ -381,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = 0; c < 16; ++c) {
               const int cc = 16 * h + c;
               const int E = erow + __shfl_sync(0xffffffffu, fcol, cc) - 45;
-              const double d = assemble(acol[cc], w2[c], w3[c], 0);
+              const double d = assemble(acol[cc], w[c], itail[cc], 0);
               int hi = __double2hiint(d), lo = __double2loint(d);
               const int ex = ((hi >> 20) & 0x7ff) + E;
               if (hi == 0 || ex <= 0) {
@@ -410,8 +467,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-constexpr size_t kSmemBytes =
-    1024 + (size_t)(kDigits + kSlots) * kTileBytes + (size_t)kNumBars * sizeof(uint64_t);
+constexpr size_t kSmemBytes = 1024 + (size_t)kDigits * kATileBytes + (size_t)kSlots * kBTileBytes +
+                               (size_t)kNumBars * sizeof(uint64_t);
 
 // Digit planes of an operand: `plane` rows of 64 f16 per digit, plane a at
 // D + a*plane*64.  One warp per row of 64 values v (zero beyond r): exponent
@@ -478,12 +535,12 @@ __global__ void split_coeff_kernel(const double* __restrict__ Y, int64_t m, int 
   }
 }
 
-static bool make_map(CUtensorMap* map, const void* base, int64_t rows) {
+static bool make_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {64, (cuuint64_t)rows};
   cuuint64_t strides[1] = {64 * sizeof(__half)};
-  cuuint32_t box[2] = {64, 128};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -546,8 +603,8 @@ cudaError_t launch_reconstruct_x64(const sas_ctx* c, const double* Y, int64_t m,
   }
   CUtensorMap mS, mY;
   const int64_t splane = x64_plane_rows(c->n);
-  if (!x64::make_map(&mS, c->Sx64, x64::kDigits * splane) ||
-      !x64::make_map(&mY, Yd, x64::kDigits * yplane))
+  if (!x64::make_map(&mS, c->Sx64, x64::kDigits * splane, x64::kBM) ||
+      !x64::make_map(&mY, Yd, x64::kDigits * yplane, x64::kBN))
     return cudaErrorInvalidValue;
   x64::Params p;
   p.out = out;

@@ -58,6 +58,34 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* ab
   }
 }
 
+// As mbar_wait, for waiters with nothing else to do: each try may suspend the
+// thread for up to hint_ns (it resumes as soon as the phase completes), so that
+// idle warps do not take issue slots from the warps doing work.
+__device__ inline bool mbar_try_hint(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+__device__ inline bool mbar_wait_idle(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                      int* status, uint32_t hint_ns = 20000) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_hint(bar, parity, hint_ns)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kWaitNs) {
+      *abort_flag = 1;
+      atomicExch(status, (int)SAS_ETIMEOUT);
+      return false;
+    }
+  }
+}
+
 // Bounded wait that ignores the abort flag (used to drain work in flight).
 __device__ inline void mbar_drain(uint32_t bar, uint32_t parity) {
   const unsigned long long t0 = globaltimer();
@@ -177,6 +205,33 @@ __device__ inline void mma_f16_scale9(uint32_t d_tmem, uint64_t a, uint64_t b, u
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, 9;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc)
       : "memory");
+}
+
+// kind::f16 MMA with a compile-time choice of accumulate (ACC = false starts the
+// accumulator): no predicate is formed at run time.
+template <bool ACC>
+__device__ inline void mma_f16_c(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc) {
+  if constexpr (ACC)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.eq.u32 p, 1, 1;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.eq.u32 p, 1, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc)
+        : "memory");
+}
+
+// One lane of the (fully active) warp: the leader elected by elect.sync.
+__device__ inline bool elect_one() {
+  uint32_t pred = 0;
+  asm volatile(
+      "{\n .reg .pred P1;\n elect.sync _|P1, 0xffffffff;\n selp.b32 %0, 1, 0, P1;\n}\n"
+      : "+r"(pred));
+  return pred != 0;
 }
 
 // TMEM load of 32 lanes x 16 columns (one value per column for this lane).
