@@ -214,3 +214,81 @@ def test_delay_theta_rebuilds_the_delay_operator():
         ref = p * np.eye(n) - A0 - np.exp(tau * p) * A1
         got = problem.full_matrix(prob, np.array([omega, tau])).toarray()
         np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_pencil_theta_rebuilds_the_transfer_function_operator():
+    """A(i omega) from the pencil rule and the blocks equals i omega E - A_0 written out
+    from its definition (Sec. 5.2, A(s) = s E - A_0 on the imaginary axis): A_0 the
+    h^-2-scaled 7-point heat operator on an N^3 grid with zero Dirichlet values (-6 on
+    the diagonal, +1 per neighbour, index i + N j + N^2 k), E = diag(e).  A sign slip
+    (A_0 + i omega E), a swapped pair of blocks or a missing i fails."""
+    N = 3
+    prob = get_config("transfer_function", N=N, r=4, s=8, m=3)
+    n, h = N ** 3, 1.0 / (N + 1)
+    A0 = np.zeros((n, n))
+    for k in range(N):
+        for j in range(N):
+            for i in range(N):
+                row = i + N * j + N * N * k
+                A0[row, row] = -6.0 / h ** 2
+                for di, dj, dk in ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)):
+                    ii, jj, kk = i + di, j + dj, k + dk
+                    if 0 <= ii < N and 0 <= jj < N and 0 <= kk < N:
+                        A0[row, ii + N * jj + N * N * kk] = 1.0 / h ** 2
+    E = np.diag(prob.meta["e"])
+    for omega in (0.01, 3.0, 2500.0):
+        ref = 1j * omega * E - A0
+        got = problem.full_matrix(prob, np.array([omega])).toarray()
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_linear_theta_rebuilds_the_diffusion_operator():
+    """A(p) from the linear rule and the blocks equals -div(a(x;p) grad .) / h^2 written
+    out node by node from a(x;p) = 1 + sum_k p_k psi_k(x), psi_k(x) =
+    exp(-|x - c_k|^2 / (2 w^2)) evaluated at the four face midpoints of every node
+    (node (i, j) at ((i+1) h, (j+1) h), index i + N j, zero Dirichlet values).  A
+    dropped leading 1 (no A_0), a wrong sign on a p_k or a shifted face fails."""
+    N = 5
+    prob = get_config("diffusion_2d", N=N, r=4, s=8, m=3)
+    h, w = prob.meta["h"], prob.meta["width"]
+    centres = prob.meta["centres"]
+
+    def a(x, y, p):
+        return 1.0 + sum(pk * np.exp(-((x - c[0]) ** 2 + (y - c[1]) ** 2) / (2 * w * w))
+                         for pk, c in zip(p, centres))
+
+    rng = np.random.default_rng(5)
+    for p in (np.zeros(4), np.array([1.0, 0.0, 0.0, 0.0]), rng.uniform(0, 1, 4), rng.uniform(0, 1, 4)):
+        ref = np.zeros((N * N, N * N))
+        for j in range(N):
+            for i in range(N):
+                row = i + N * j
+                x, y = (i + 1) * h, (j + 1) * h
+                for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                    af = a(x + di * h / 2, y + dj * h / 2, p)
+                    ref[row, row] += af / h ** 2
+                    ii, jj = i + di, j + dj
+                    if 0 <= ii < N and 0 <= jj < N:
+                        ref[row, ii + N * jj] = -af / h ** 2
+        got = problem.full_matrix(prob, p).toarray()
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_qoi_hand_worked_transpose_and_mean():
+    """The QoI H = c^T x_hat = (c^T S) y with the plain transpose (Sec. 5.2.2, H ~ (c^T X) c_hat;
+    Sec. 5.2, Eq. 9), worked by hand on complex S, c and y, and the grid mean
+    (1/n) 1^T x_hat.  A conjugated c, the wrong axis of the mean or a transposed
+    product gives another number."""
+    from types import SimpleNamespace
+    S = np.array([[1 + 2j, 0], [3, -1j], [0, 2]])
+    c = np.array([1, 2j, -1])
+    prob = SimpleNamespace(qoi_kind="transpose", c=c, n=3)
+    # c^T S = [1 (1+2j) + 2j 3 + (-1) 0, 1 0 + 2j (-1j) + (-1) 2] = [1 + 8j, 0]
+    np.testing.assert_allclose(online.qoi_vector(prob, S), [1 + 8j, 0], rtol=0, atol=1e-15)
+    # (1 + 8j)(2 - 1j) + 0 * 5 = 10 + 15j
+    np.testing.assert_allclose(online.qoi(prob, S, np.array([[2 - 1j, 5]])), [10 + 15j], rtol=0, atol=1e-14)
+    Sr = np.array([[1.0, 2.0], [3.0, 4.0], [5.0, 9.0]])
+    mean = SimpleNamespace(qoi_kind="mean", c=None, n=3)
+    np.testing.assert_allclose(online.qoi_vector(mean, Sr), [3.0, 5.0], rtol=0, atol=1e-15)
+    # x_hat = S [1, -1] = [-1, -1, -4], mean -2
+    np.testing.assert_allclose(online.qoi(mean, Sr, np.array([[1.0, -1.0]])), [-2.0], rtol=0, atol=1e-15)
