@@ -85,13 +85,40 @@ def dist_env():
     return rank, world, local
 
 
-def rank_params(params, rank):
-    """Weak scaling: rank 0 solves the workload's own draw, rank k > 0 an independent
-    seeded draw of the same size and distribution (no data exchanged between ranks)."""
-    if rank == 0:
+def global_batch(params, world):
+    """The whole job's parameters: the workload's own draw followed by (world - 1)
+    seeded draws of the same size and distribution (weak scaling: every rank keeps
+    a batch of the workload's size)."""
+    if world == 1:
         return params
     lo, hi = params.min(axis=0), params.max(axis=0)
-    return np.random.default_rng(1000 + rank).uniform(lo, hi, params.shape)
+    extra = np.random.default_rng(1000).uniform(lo, hi, ((world - 1) * params.shape[0],) + params.shape[1:])
+    return np.concatenate([params, extra])
+
+
+def rank_slice(m_total, rank, world):
+    """Contiguous block of the global batch that rank owns (blocks differ by at most one)."""
+    base, extra = divmod(m_total, world)
+    lo = rank * base + min(rank, extra)
+    return slice(lo, lo + base + (1 if rank < extra else 0))
+
+
+def rank_params(params, rank, world=None):
+    """This rank's block of the global batch (no data exchanged between ranks)."""
+    world = int(os.environ.get("WORLD_SIZE", "1")) if world is None else world
+    world = max(world, rank + 1)
+    g = global_batch(params, world)
+    return g[rank_slice(g.shape[0], rank, world)]
+
+
+def gather_rows(local, dist_mod, world):
+    """Reassemble the ranks' output blocks (equal sizes) into the global batch's order."""
+    import torch
+    if dist_mod is None or world == 1:
+        return local
+    parts = [torch.empty_like(local) for _ in range(world)]
+    dist_mod.all_gather(parts, local.contiguous())
+    return torch.cat(parts)
 
 
 def max_over_ranks(value, dist_mod, device="cpu"):

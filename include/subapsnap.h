@@ -234,13 +234,13 @@ sas_status subapsnap_select_rows_affine(const sas_affine_desc* desc, const doubl
  * m x r coefficient vectors between the least-squares and reconstruction
  * kernels go to one fixed device array of SAS_NOALLOC_MAX_Y doubles that
  * every device loading the library holds until the process exits.  No
- * counterpart in the paper: this is a deployment variant of the online
- * stage (Alg. 1 step 4).
+ * counterpart in the paper.
  *  params: device m x dp; out: device m x n doubles (row j = x_hat of
  *  parameter j); flags, rho: device m or NULL, as for solve_batch.
- * The first call on a device looks the array's address up with that device
- * current; make that first call before any stream capture.  All calls share
- * the array and calls that overlap on the GPU race on it.
+ * Context set-up looks the array's address up (and brings the array onto the
+ * device); every call looks it up again, so the address stays right after a
+ * device reset.  Make the first call before any stream capture.  All calls
+ * share the array and calls that overlap on the GPU race on it.
  * Errors: SAS_EINVAL if m * r > SAS_NOALLOC_MAX_Y or a pointer is NULL;
  * SAS_ENOTSUP for a complex or kernel-family context; SAS_ECUDA. */
 sas_status subapsnap_solve_batch_xhat_noalloc(sas_ctx* ctx, const double* params, int64_t m,

@@ -310,6 +310,7 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
   TRY(cudaMemset(c->dev_status, 0, sizeof(int)));
   TRY(launch_gather_blocks(c, sst));
   TRY(launch_gather_vectors(c, d->c, sst));
+  TRY(noalloc_prepare());  // the fixed array of the no-allocation entry point
   if (d->w) TRY(launch_weight_rows(c, d->w, sst));  // weighted rows: W M(p), W b_J
   if (d->mode == SAS_MODE_MIXED) {
     TRY(cudaMalloc(&c->G32, (size_t)d->K * d->s * d->r * esl));

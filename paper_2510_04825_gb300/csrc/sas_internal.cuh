@@ -274,6 +274,8 @@ cudaError_t launch_reconstruct_tc(const sas_ctx* c, const float* ysplit, int64_t
 bool reconstruct_tc_supported(const sas_ctx* c);
 void reconstruct_tc_split(int64_t n, int64_t m, int num_sms, int bn, int* num_mtiles,
                           int* num_ntiles, int* ngroups, int* ntpg);
+// fixed device array of subapsnap_solve_batch_xhat_noalloc: address lookup at set-up
+cudaError_t noalloc_prepare();
 // float64-accurate tensor-core reconstruction (sas_recon_x64.cu)
 cudaError_t setup_x64_basis(sas_ctx* c, cudaStream_t st);
 bool reconstruct_x64_supported(const sas_ctx* c);

@@ -13,39 +13,34 @@
 // The array lives in every device that loads the library until the process
 // exits (SAS_NOALLOC_MAX_Y doubles = 512 KiB).  Host code only ever sees the
 // array's name as a host-side stand-in, so its device address is looked up
-// once per device with cudaGetSymbolAddress, with that device current, on the
-// first call made on that device; that first call should come before any
-// stream capture.  All calls share the array and it keeps the last call's
-// contents; every call overwrites the m x r entries it uses before reading
-// them, so nothing has to start at zero.  Calls whose work overlaps on the
-// GPU (other streams, other host threads) race on the array.
-#include <mutex>
-
+// with cudaGetSymbolAddress, with the device current: once at context set-up
+// (which also brings the array onto the device, so that no later call makes
+// the driver load it) and again at every call, which allocates nothing and
+// stays right after a device reset or a new primary context.  Make the first
+// call after set-up and before any stream capture.  All calls share the array
+// and it keeps the last call's contents; every call overwrites the m x r
+// entries it uses before reading them, so nothing has to start at zero.
+// Calls whose work overlaps on the GPU (other streams, other host threads)
+// race on the array.
 #include "sas_internal.cuh"
 
 namespace sas {
 
 static __device__ __align__(256) double g_noalloc_y[SAS_NOALLOC_MAX_Y];
 
-constexpr int kNoallocMaxDevices = 64;
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_addr[kNoallocMaxDevices];
-
-// Device address of g_noalloc_y on the current device (set-up on first use).
+// Device address of g_noalloc_y on the current device.
 static cudaError_t noalloc_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_y);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_y);
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_addr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
+}
+
+// Context set-up: look the array up once on the current device.
+cudaError_t noalloc_prepare() {
+  double* p = nullptr;
+  return noalloc_address(&p);
 }
 
 }  // namespace sas

@@ -1,9 +1,14 @@
 """The multi-rank path of bench.py on CPU: two gloo ranks, no GPU.
 
-Every rank solves its own parameters (weak scaling, no data-path collective);
-the only exchange is the max-reduction of the step time.  The test checks the
-sharding (distinct draws of the same distribution), the max-over-ranks timing
-and the whole-job throughput every rank would report.
+The job's parameters form one global batch that the ranks partition into
+contiguous blocks (weak scaling: each block has the workload's size); every
+rank solves its block with no data-path collective, and the only exchanges are
+the max-reduction of the step time and, for checking, the gather of the
+outputs.  The test runs the solve on each rank's block with the oracle (the
+CUDA path needs a GPU), reassembles the blocks with the bench's gather and
+requires the result to be bit-identical to one unsplit solve of the whole
+batch; it also checks the max-over-ranks timing and the whole-job throughput
+every rank reports.
 """
 import os
 import socket
@@ -15,6 +20,8 @@ torch = pytest.importorskip("torch")
 import torch.distributed as dist  # noqa: E402
 import torch.multiprocessing as mp  # noqa: E402
 
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
 
 def _free_port():
     with socket.socket() as s:
@@ -22,34 +29,67 @@ def _free_port():
         return s.getsockname()[1]
 
 
+def _problem():
+    from oracle import problem, selection
+    from workloads import get_config
+    from workloads import snapshots as wsnap
+    prob = get_config("reaction_diffusion_1d", n=200, r=8, s=16, m=12)
+    S = wsnap.basis(prob)
+    J, _ = selection.cpqr_rows(np.asarray(problem.full_matrix(prob, prob.sel_param) @ S), prob.s)
+    return prob, S, J
+
+
 def _worker(rank, world, port, out):
     import sys
-    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    sys.path.insert(0, ROOT)
     import bench
-    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    from oracle import online
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    base = np.random.default_rng(0).uniform(0.0, 1.0, (64, 4))
-    mine = bench.rank_params(base, rank)
+    prob, S, J = _problem()
+    mine = bench.rank_params(prob.test_params, rank, world)
+    Y, _ = online.solve_many(prob, S, J, mine)
+    X = torch.from_numpy(np.ascontiguousarray(Y @ S.T))
+    whole = bench.gather_rows(X, dist, world).numpy()
     ms = 10.0 + 5.0 * rank  # rank 1 is the slower one
     slowest = bench.max_over_ranks(ms, dist)
     value = bench.job_throughput(world, mine.shape[0], slowest)
-    gathered = [torch.zeros(64 * 4, dtype=torch.float64) for _ in range(world)]
-    dist.all_gather(gathered, torch.from_numpy(mine.reshape(-1).copy()))
-    out[rank] = (slowest, value, [g.numpy().copy() for g in gathered])
+    out[rank] = (slowest, value, mine.copy(), whole)
     dist.barrier()
     dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_shard_and_reduce():
+def test_two_gloo_ranks_partition_solve_and_reassemble():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import online
     world = 2
     port = _free_port()
     manager = mp.Manager()
     out = manager.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+    prob, S, J = _problem()
+    glob = bench.global_batch(prob.test_params, world)
+    Yg, _ = online.solve_many(prob, S, J, glob)
+    Xg = Yg @ S.T
+    blocks = []
     for r in range(world):
-        slowest, value, gathered = out[r]
-        assert slowest == 15.0                     # max over ranks
-        assert value == pytest.approx(2 * 64 / 15e-3)
-        p0, p1 = (g.reshape(64, 4) for g in gathered)
-        assert not np.allclose(p0, p1)             # every rank has its own parameters
-        assert p1.min() >= p0.min() - 1e-12 and p1.max() <= p0.max() + 1e-12
+        slowest, value, mine, whole = out[r]
+        assert slowest == 15.0                              # max over ranks
+        assert value == pytest.approx(world * prob.test_params.shape[0] / 15e-3)
+        assert mine.shape == prob.test_params.shape         # weak scaling: the workload's size per rank
+        np.testing.assert_array_equal(whole, Xg)            # reassembled = one unsplit solve, bit for bit
+        blocks.append(mine)
+    np.testing.assert_array_equal(blocks[0], prob.test_params)  # rank 0 keeps the workload's draw
+    np.testing.assert_array_equal(np.concatenate(blocks), glob)  # the blocks partition the batch
+
+
+def test_rank_slices_partition_any_batch():
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    for m in (1, 7, 64, 4097):
+        for world in (1, 2, 3, 8):
+            idx = np.concatenate([np.arange(m)[bench.rank_slice(m, r, world)] for r in range(world)])
+            np.testing.assert_array_equal(idx, np.arange(m))

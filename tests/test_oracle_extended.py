@@ -8,8 +8,6 @@ allows 1e-13 kappa(M) relative error (plus a small floor).
 import numpy as np
 import pytest
 
-mpmath = pytest.importorskip("mpmath")
-
 from oracle import online, problem, selection, snapshots  # noqa: E402
 from workloads import get_config  # noqa: E402
 
@@ -20,6 +18,9 @@ CASES = [("reaction_diffusion_1d", dict(n=40, r=6, s=12, m=5)),
 
 
 def _exact_ls(M, bJ, digits=50):
+    # imported here, not at module level: an image without mpmath then skips these
+    # tests when they run instead of skipping the module at collection
+    mpmath = pytest.importorskip("mpmath")
     with mpmath.workdps(digits):
         Mm = mpmath.matrix([[mpmath.mpc(complex(v)) for v in row] for row in M])
         bm = mpmath.matrix([mpmath.mpc(complex(v)) for v in bJ])
