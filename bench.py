@@ -705,10 +705,36 @@ def run_gpu_surrogate(args):
     Ptr = torch.from_numpy(np.random.default_rng(123).uniform(0.0, 1.0, (ntrain, prob.dp))).to(device)
     Ytr = torch.empty((ntrain, r), dtype=torch.float64, device=device)
     chosen.solve(Ptr, api.SAS_OUT_Y, Ytr)
-    t1 = time.time()
-    losses = api.subapsnap_surrogate_train(chosen.ctx, Ptr, Ytr, args.epochs, 1024, 1e-3, seed=7)
-    torch.cuda.synchronize()
-    train_s = time.time() - t1
+    # anchors: the snapshot parameters with the online stage's coefficient vectors there
+    Pa = torch.from_numpy(np.ascontiguousarray(prob.snap_params)).to(device)
+    Ya = torch.empty((Pa.shape[0], r), dtype=torch.float64, device=device)
+    chosen.solve(Pa, api.SAS_OUT_Y, Ya)
+    # acceptance versus threshold for the network variants: bfloat16 output layer; float32
+    # output layer; float32 output layer learning the deviation from the nearest snapshot's y
+    thresholds = [1e-6, 1e-5, 1e-4, 1e-3, 1e-2]
+    variants = [("bf16_output_layer", 0, False), ("f32_output_layer_nearest_snapshot_deviation", 1, True),
+                ("f32_output_layer", 1, False)]  # the last one is the network of the timed step
+    Yh = torch.empty((m, r), dtype=torch.float64, device=device)
+    rho_h = torch.empty(m, dtype=torch.float64, device=device)
+    table = []
+    for name, f32_out, anchored in variants:
+        api.subapsnap_surrogate_reset(chosen.ctx)
+        api.subapsnap_set_option(chosen.ctx, api.SAS_OPT_SURROGATE_F32_OUT, f32_out)
+        if anchored:
+            api.subapsnap_surrogate_set_anchors(chosen.ctx, Pa, Ya)
+        else:
+            api.subapsnap_surrogate_set_anchors(chosen.ctx)
+        t1 = time.time()
+        losses = api.subapsnap_surrogate_train(chosen.ctx, Ptr, Ytr, args.epochs, 1024, 1e-3, seed=7)
+        torch.cuda.synchronize()
+        train_s = time.time() - t1
+        api.subapsnap_surrogate_predict(chosen.ctx, P, m, Yh)
+        api.subapsnap_residual(chosen.ctx, P, m, Yh, rho_h)
+        rh = rho_h.cpu().numpy()
+        table.append({"variant": name, "train_s": round(train_s, 2),
+                      "loss_first_last": [float(losses[0]), float(losses[-1])] if len(losses) else None,
+                      "rho_median": float(np.median(rh)), "rho_min": float(rh.min()),
+                      "accepted": {f"{t:.0e}": round(float((rh <= t).mean()), 4) for t in thresholds}})
     setup_s = time.time() - t0
     tol = 1e-6
     H = torch.empty(m, dtype=torch.float64, device=device)
@@ -770,15 +796,18 @@ def run_gpu_surrogate(args):
         "metric": METRIC, "value": round(m / (ms_c * 1e-3), 2), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_c, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "surrogate (bf16 weights, f32 accumulate) gated by f64 subsampled residual; "
+        "dtype": "surrogate (tcgen05 bf16 products, f32 accumulate, f32 output layer) "
+                 "gated by f64 subsampled residual; "
                  "fallback f32 Householder + f64 refinement; x_hat f64 (tensor-core digit products)",
         "data": "synthetic (seeded 2-D diffusion 4096^2, snapshot basis from PCG)",
         "config": {"workload": f"surrogate_diffusion_2d_{N}x{N}_r60_s120_m65536_x256", "n": n, "r": r,
                    "s": prob.s, "m_per_gpu": m, "x_hat_params": nx, "gate_tol": tol,
                    "ntrain": ntrain, "epochs": args.epochs},
         "accepted_fraction": round(acc[0] / m, 4),
+        "surrogate_variant": variants[-1][0],
         "surrogate_loss_first_last": [float(losses[0]), float(losses[-1])] if len(losses) else None,
         "train_s": round(train_s, 2),
+        "acceptance_vs_threshold": table,
         "mixed_without_network": {"value": round(m / (ms_mix * 1e-3), 2), "ms_per_step": round(ms_mix, 3)},
         "plain_fp64": {"value": round(m / (ms_p * 1e-3), 2), "ms_per_step": round(ms_p, 3)},
         "speedup_chosen_vs_plain": round(ms_p / ms_c, 2),
@@ -790,6 +819,77 @@ def run_gpu_surrogate(args):
         "clocks": clocks, "setup_s": round(setup_s, 1), "csr_build_s": round(t_csr, 1),
         "snapshot_pcg_max_rel_residual": float(np.max(snap_res)),
     }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_gpu_surrogate_mlp(args):
+    """The surrogate network's inference on the tensor cores, alone: d_in = 4 -> 256 -> 256 -> r = 60
+    (exact GELU, float32 output layer), m = 262,144 parameters per step (four chunks of 65,536
+    rows), seeded random weights; L2 flushed between timed iterations.  Every product is a
+    tcgen05 kind::f16 MMA chain with bfloat16 operands: the float32 activations enter as two
+    bfloat16 terms (hi, lo) and the float32 output-layer weights as two more, so the tensor
+    cores execute 2x the algorithmic FLOPs of the hidden layers and 3x those of the output layer."""
+    import torch
+    from paper_2510_04825_gb300 import api
+    from paper_2510_04825_gb300.solver import AffineSolver
+    from workloads import get_config
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    prob = get_config("surrogate_diffusion_2d", N=64)  # only d_in and r matter here
+    rng = np.random.default_rng(0)
+    S = np.linalg.qr(rng.standard_normal((prob.n, prob.r)))[0]
+    J = np.sort(rng.choice(prob.n, prob.s, replace=False))
+    solver = AffineSolver(prob, S, J, mode=api.SAS_MODE_MIXED, device=device)
+    ctx = solver.ctx
+    api.subapsnap_set_option(ctx, api.SAS_OPT_SURROGATE_F32_OUT, 1)
+    nparam = api.subapsnap_surrogate_weights(ctx, False)
+    theta = (rng.standard_normal(nparam) / 16.0).astype(np.float32)
+    dp, r, h = prob.dp, prob.r, 256
+    norm = np.concatenate([np.full(dp, 0.5), np.full(dp, 0.5), np.zeros(r), np.ones(r)])
+    api.subapsnap_surrogate_weights(ctx, False, theta, norm)
+    m = args.m or 262144
+    P = torch.from_numpy(rng.uniform(0.0, 1.0, (m, dp))).to(device)
+    Yh = torch.empty((m, r), dtype=torch.float64, device=device)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        api.subapsnap_surrogate_predict(ctx, P, m, Yh)
+    torch.cuda.synchronize()
+    cpath = os.path.join(tempfile.gettempdir(), f"sas_clocks_{os.getpid()}.csv")
+    sp, sf = start_clock_sampler(cpath)
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        api.subapsnap_surrogate_predict(ctx, P, m, Yh)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    clocks = stop_clock_sampler(sp, sf, cpath, local)
+    ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    alg = 2.0 * m * (dp * h + h * h + h * r)
+    executed = 2.0 * m * (2 * dp * h + 2 * h * h + 3 * h * r)
+    peak, kind = bf16_peak()
+    line = {
+        "metric": "surrogate network predictions per second (tensor-core inference)",
+        "value": round(m / (ms * 1e-3), 1), "unit": "predictions/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+        "dtype": "bf16 tensor-core products (f32 operands as hi + lo bf16), f32 accumulate",
+        "data": "synthetic (seeded random weights and parameters)",
+        "config": {"workload": f"surrogate_mlp_{dp}x{h}x{h}x{r}_m{m}", "l2": "flushed between steps"},
+        "roofline": {"bound": "tensor", "achieved": round(executed / (ms * 1e-3) / 1e12, 2),
+                     "peak": peak, "unit": "TFLOP/s",
+                     "frac": round(executed / (ms * 1e-3) / 1e12 / peak, 4), "peak_kind": kind,
+                     "algorithmic_tflops": round(alg / (ms * 1e-3) / 1e12, 2),
+                     "note": "executed tensor FLOPs (hi/lo terms) over the whole predict call: "
+                             "three GEMM launches plus normalise / denormalise"},
+        "clocks": clocks,
+    }
+    solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -1076,7 +1176,7 @@ def main():
                     help="fixed least-squares launch shape of the chosen form, no autotuning")
     ap.add_argument("--workload", default="diffusion_2d",
                     choices=["diffusion_2d", "transfer_function", "reaction_diffusion_1d", "kernel_ridge",
-                             "surrogate_diffusion_2d", "delay_system"])
+                             "surrogate_diffusion_2d", "delay_system", "surrogate_mlp"])
     ap.add_argument("--epochs", type=int, default=100, help="surrogate training epochs")
     ap.add_argument("--selection-variants", action="store_true",
                     help="time the subsampling variants of Sec. 4.3.4 on the headline workload")
@@ -1093,6 +1193,8 @@ def main():
         run_reference(args)
     elif args.workload == "surrogate_diffusion_2d":
         run_gpu_surrogate(args)
+    elif args.workload == "surrogate_mlp":
+        run_gpu_surrogate_mlp(args)
     elif args.workload != "diffusion_2d":
         run_gpu_other(args)
     else:

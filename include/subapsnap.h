@@ -288,10 +288,15 @@ sas_status subapsnap_output_row_bytes(const sas_ctx* ctx, int32_t out_kind, int6
  *      default 2^30).
  *  SAS_OPT_XHAT_F32: mixed form only: 1 = x_hat returned as float32 (three
  *      tf32 products, ~2^-21 relative; not residual-equivalent to float64
- *      for an operator with large ||A||), 0 = float64 (default). */
+ *      for an operator with large ||A||), 0 = float64 (default). *  SAS_OPT_SURROGATE_F32_OUT: 1 = the surrogate's output layer uses its float32
+ *      weights (each entered as two bfloat16 terms on the tensor cores) instead
+ *      of the bfloat16 copy; training, prediction and gradients use the current
+ *      setting (default 0).
+ */
 enum { SAS_OPT_RECON_KERNEL = 0, SAS_OPT_MAX_REFINE = 1, SAS_OPT_REFINE_TOL = 2,
        SAS_OPT_LS_VARIANT = 3, SAS_OPT_ASSEMBLY_KERNEL = 4, SAS_OPT_ASSEMBLY_SEGMENT = 5,
-       SAS_OPT_RECON_STORE = 6, SAS_OPT_HOST_CHUNK = 7, SAS_OPT_XHAT_F32 = 8 };
+       SAS_OPT_RECON_STORE = 6, SAS_OPT_HOST_CHUNK = 7, SAS_OPT_XHAT_F32 = 8,
+       SAS_OPT_SURROGATE_F32_OUT = 9 };
 
 /* Set one option of a context.  Errors: SAS_EINVAL for an unknown key or a
  * value out of range. */
@@ -473,8 +478,8 @@ sas_status subapsnap_select_rows_kernel(const sas_kernel_desc* desc, const doubl
 
 /* ------------------------------------------------------------------------
  * Learned surrogate (not in the paper).  A network p -> y(p) (d_in -> 256 ->
- * 256 -> r, exact GELU, bfloat16 weights, float32 accumulation and master
- * weights, Adam) attached to an affine context, trained by the library's own
+ * 256 -> r, exact GELU, bfloat16 weights, tensor-core products with float32
+ * accumulation, float32 master weights, Adam) attached to an affine context, trained by the library's own
  * kernels on coefficient vectors the online stage produced.  Its predictions
  * are accepted only when the subsampled relative residual
  * ||M(p) y_hat - b_J|| / ||b_J|| (the online residual estimate of Sec. 4.3.1,
@@ -505,6 +510,21 @@ sas_status subapsnap_solve_batch_surrogate(sas_ctx* ctx, const double* params, i
                                            int32_t out_kind, void* out, uint32_t* flags,
                                            double* rho, double gate_tol, int64_t* accepted,
                                            void* stream);
+
+/* Discard the network (weights, optimiser state and its copy of the anchors);
+ * the next subapsnap_surrogate_train creates a fresh one from its seed.
+ * Synchronises the device first.  Errors: SAS_EINVAL, SAS_ECUDA. */
+sas_status subapsnap_surrogate_reset(sas_ctx* ctx);
+
+/* Anchors for the next subapsnap_surrogate_train: n parameter points P
+ * (device n x dp, float64) with their coefficient vectors Y (device n x r), for
+ * instance the snapshot parameters with the online solution there.  A network
+ * trained with anchors learns y(p) - Y[a(p)], a(p) the anchor nearest to p in
+ * the network's input scaling (sum_k ((p_k - P[a]_k) / half-width_k)^2, lowest
+ * index on ties), and predicts Y[a(p)] plus its output; it keeps its own copy
+ * of the anchors.  The context copies P and Y (the caller keeps ownership);
+ * n = 0 clears them.  Errors: SAS_EINVAL, SAS_ENOTSUP, SAS_ENOMEM, SAS_ECUDA. */
+sas_status subapsnap_surrogate_set_anchors(sas_ctx* ctx, const double* P, const double* Y, int64_t n);
 
 /* Read (get != 0) or write the network: theta (host float32, layout W1 b1 W2
  * b2 W3 b3, W_l row-major out x in) and norm (host float64: input centre[dp],

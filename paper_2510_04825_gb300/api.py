@@ -38,13 +38,13 @@ EXPORTED = [
     "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine", "subapsnap_sample_rows_leverage",
     "subapsnap_select_rows_union_affine", "subapsnap_nearest_points", "subapsnap_krylov_affine",
     "subapsnap_tsqr", "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex",
-    "subapsnap_output_row_bytes",
+    "subapsnap_output_row_bytes", "subapsnap_surrogate_set_anchors", "subapsnap_surrogate_reset",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
 SAS_OPT_RECON_KERNEL, SAS_OPT_MAX_REFINE, SAS_OPT_REFINE_TOL, SAS_OPT_LS_VARIANT = 0, 1, 2, 3
 SAS_OPT_ASSEMBLY_KERNEL, SAS_OPT_ASSEMBLY_SEGMENT, SAS_OPT_RECON_STORE = 4, 5, 6
-SAS_OPT_HOST_CHUNK, SAS_OPT_XHAT_F32 = 7, 8
+SAS_OPT_HOST_CHUNK, SAS_OPT_XHAT_F32, SAS_OPT_SURROGATE_F32_OUT = 7, 8, 9
 SAS_MAX_VARIANTS = 32
 SAS_KRYLOV_WARM, SAS_KRYLOV_MIXED, SAS_KRYLOV_BICGSTAB = 1, 2, 4
 SAS_PRECOND_JACOBI, SAS_PRECOND_POISSON = 0, 1
@@ -121,6 +121,8 @@ def lib() -> ctypes.CDLL:
                                                       i64p, vp]
         L.subapsnap_surrogate_weights.argtypes = [vp, i32, fp_, dp_, i64p]
         L.subapsnap_surrogate_grad.argtypes = [vp, vp, vp, i64, dp_, fp_]
+        L.subapsnap_surrogate_set_anchors.argtypes = [vp, vp, vp, i64]
+        L.subapsnap_surrogate_reset.argtypes = [vp]
         L.subapsnap_multi_plan_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64p,
                                                   i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                   ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -160,7 +162,8 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_selftest_wait", "subapsnap_leverage_scores_affine",
                      "subapsnap_sample_rows_leverage", "subapsnap_select_rows_union_affine",
                      "subapsnap_nearest_points", "subapsnap_krylov_affine", "subapsnap_tsqr",
-                     "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex"):
+                     "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex",
+                     "subapsnap_surrogate_set_anchors", "subapsnap_surrogate_reset"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -481,6 +484,17 @@ def subapsnap_solve_batch_surrogate(ctx, params, m: int, out_kind: int, out, fla
                                                  _ptr(flags), _ptr(rho), float(gate_tol),
                                                  ctypes.byref(acc), _stream(stream)))
     return acc.value
+
+
+def subapsnap_surrogate_reset(ctx):
+    """Discard the network; the next training starts from a fresh one."""
+    _check(lib().subapsnap_surrogate_reset(ctx))
+
+
+def subapsnap_surrogate_set_anchors(ctx, P=None, Y=None):
+    """Anchors (device float64 P: n x dp, Y: n x r) for the next training; None clears."""
+    n = 0 if P is None else int(P.shape[0])
+    _check(lib().subapsnap_surrogate_set_anchors(ctx, _ptr(P) if n else None, _ptr(Y) if n else None, n))
 
 
 def subapsnap_surrogate_weights(ctx, get: bool, theta=None, norm=None) -> int:

@@ -108,6 +108,8 @@ static void free_ctx(sas_ctx* c) {
   cudaFree(c->Mbuf);
   cudaFree(c->hstage);
   cudaFree(c->dev_status);
+  cudaFree(c->surr_aP);
+  cudaFree(c->surr_aY);
   destroy_surrogate(c);
   if (c->trace) {
     for (auto& t : *c->trace) {
@@ -841,6 +843,22 @@ sas_status subapsnap_solve_batch_surrogate(sas_ctx* c, const double* params, int
                          (cudaStream_t)stream);
 }
 
+sas_status subapsnap_surrogate_reset(sas_ctx* c) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  cudaError_t e = cudaDeviceSynchronize();  // no launch of this context may still read the network
+  destroy_surrogate(c);
+  if (e != cudaSuccess) return cuda_fail(e, "surrogate_reset");
+  return SAS_OK;
+}
+
+sas_status subapsnap_surrogate_set_anchors(sas_ctx* c, const double* P, const double* Y, int64_t n) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (c->family != kAffine || c->dtype != SAS_REAL64)
+    return fail(SAS_ENOTSUP, "the surrogate needs a real affine context");
+  if (n < 0 || (n > 0 && (!P || !Y))) return fail(SAS_EINVAL, "anchors: n < 0 or NULL buffers");
+  return surrogate_set_anchors(c, P, Y, n);
+}
+
 sas_status subapsnap_surrogate_weights(sas_ctx* c, int32_t get, float* theta, double* norm,
                                        int64_t* nparam) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");
@@ -1064,6 +1082,10 @@ sas_status subapsnap_set_option(sas_ctx* c, int32_t key, double value) {
       if (value == 1.0 && c->mode == SAS_MODE_MIXED && c->dtype == SAS_REAL64 && !c->Shi)
         return fail(SAS_ENOTSUP, "this context has no float32 copy of S");
       c->xhat_f32 = (int)value;
+      return SAS_OK;
+    case SAS_OPT_SURROGATE_F32_OUT:
+      if (value != 0.0 && value != 1.0) return fail(SAS_EINVAL, "surrogate f32 out must be 0 or 1");
+      c->surr_f32_out = (int)value;
       return SAS_OK;
     case SAS_OPT_HOST_CHUNK:
       if (!(value >= 1.0 && value <= 1099511627776.0)) return fail(SAS_EINVAL, "host chunk must be in [1, 2^40] bytes");

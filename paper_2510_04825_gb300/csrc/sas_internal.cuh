@@ -201,6 +201,10 @@ struct sas_ctx {
   // options
   int recon_kernel;    // 0 auto, 1 CUDA cores, 2-4 tensor cores tf32, 5 tensor cores f16
   int xhat_f32;        // mixed form: 1 = x_hat in float32 (tf32 x 3), 0 = float64-accurate
+  int surr_f32_out;    // surrogate: 1 = output layer with float32 weights (hi + lo bfloat16)
+  double* surr_aP;     // surrogate anchors for the next training (device, surr_na x dp)
+  double* surr_aY;     // and their coefficient vectors (device, surr_na x r)
+  int64_t surr_na;
   int recon_store;     // tensor-core reconstruction epilogue: 0 TMA stores, 1 direct stores
   int krr_kernel;      // kernel rows of the mixed form: 0 auto, 1 CUDA cores, 2 tensor cores
   int krr_seg_points;  // tensor-core rows: points per TMEM segment before the float64 fold
@@ -308,6 +312,13 @@ bool surrogate_ready(const sas_ctx* c);
 sas_status surrogate_solve(sas_ctx* c, const double* params, int64_t m, int32_t out_kind, void* out,
                            uint32_t* flags, double* rho_out, double tol, int64_t* accepted,
                            cudaStream_t st);
+sas_status surrogate_set_anchors(sas_ctx* c, const double* P, const double* Y, int64_t n);
+// tensor-core GEMM of the surrogate (sas_mlp_tc.cu): operand types of A and B
+enum { kMlpF32 = 0, kMlpBF16 = 1 };
+cudaError_t mlp_gemm_tc(cudaStream_t st, float* part, int64_t part_cap, int* status, int M, int N,
+                        int K, const void* A, int ta, int64_t lai, int64_t lak, const void* B, int tb,
+                        int64_t lbk, int64_t lbj, float* C, int64_t ldc, int epi, const float* bias,
+                        float* H);
 // persistent multi-problem launch
 struct MultiPlan {
   const void* kernel = nullptr;

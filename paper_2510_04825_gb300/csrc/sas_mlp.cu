@@ -5,14 +5,19 @@
 // ||M(p) y_hat - b_J|| / ||b_J|| (Sec. 4.3.1's online estimate) is below a
 // threshold; the rest fall back to the exact least-squares solve.
 //
-// Arithmetic: float32 master weights and Adam moments; the matrix products
-// read bfloat16 copies of the weights and accumulate in float32.  Inputs are
-// normalised to [-1, 1] per parameter, outputs standardised per component,
-// both from the training set.
+// Arithmetic: float32 master weights and Adam moments; every matrix product
+// (forward, input gradients, weight gradients) runs on the tensor cores
+// (tcgen05 kind::f16, bfloat16 operands, float32 accumulation; sas_mlp_tc.cu)
+// with bfloat16 copies of the weights and float32 activations split into two
+// bfloat16 terms.  Option: the output layer takes its float32 weights (split
+// the same way).  Inputs are normalised to [-1, 1] per parameter, outputs
+// standardised per component, both from the training set.  Optional anchors
+// (parameter points with their coefficient vectors, e.g. the snapshots): the
+// network then learns the deviation of y(p) from the coefficient vector of the
+// nearest anchor, and predicts that anchor's vector plus its output.
 //
-// Kernels: one tiled GEMM with strided operands (forward, input gradients and
-// weight gradients), bias+GELU epilogue, GELU backward, column sums, MSE loss,
-// Adam with the bfloat16 cast, and the gather/normalisation helpers.
+// Kernels here: GELU backward, column sums, MSE loss, Adam with the bfloat16
+// cast, nearest anchor, and the gather/normalisation helpers.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -27,83 +32,9 @@ namespace sas {
 
 namespace mlp {
 
-constexpr int kTile = 64;
-constexpr int kBK = 16;
-constexpr int kThreads = 256;
-
-__device__ inline float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ inline float gelu_grad_f(float x) {
   return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) +
          x * expf(-0.5f * x * x) * 0.39894228040143268f;
-}
-
-template <typename T> __device__ inline float ld(const T* p, int64_t i);
-template <> __device__ inline float ld<float>(const float* p, int64_t i) { return p[i]; }
-template <> __device__ inline float ld<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
-  return __bfloat162float(p[i]);
-}
-
-// C[i*ldc + j] (epilogue) = sum_k A(i,k) B(k,j), A(i,k) = A[i*lai + k*lak],
-// B(k,j) = B[k*lbk + j*lbj].  Epilogues: 0 store, 1 Z = acc + bias, H = gelu(Z),
-// 2 store acc + bias.
-template <typename TA, typename TB>
-__global__ void __launch_bounds__(kThreads) gemm_kernel(int M, int N, int K, const TA* A, int64_t lai,
-                                                        int64_t lak, const TB* B, int64_t lbk,
-                                                        int64_t lbj, float* C, int64_t ldc, int epi,
-                                                        const float* bias, float* H) {
-  __shared__ float As[kBK][kTile + 1];
-  __shared__ float Bs[kBK][kTile + 1];
-  const int tid = threadIdx.x;
-  const int ty = tid / 16, tx = tid % 16;
-  const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += kBK) {
-    for (int idx = tid; idx < kBK * kTile; idx += kThreads) {
-      const int kk = idx / kTile, ii = idx % kTile;
-      const int i = i0 + ii, k = k0 + kk;
-      As[kk][ii] = (i < M && k < K) ? ld<TA>(A, (int64_t)i * lai + (int64_t)k * lak) : 0.f;
-      const int j = j0 + ii;
-      Bs[kk][ii] = (j < N && k < K) ? ld<TB>(B, (int64_t)k * lbk + (int64_t)j * lbj) : 0.f;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kBK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) a[u] = As[kk][ty + 16 * u];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) b[v] = Bs[kk][tx + 16 * v];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int i = i0 + ty + 16 * u;
-    if (i >= M) continue;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int j = j0 + tx + 16 * v;
-      if (j >= N) continue;
-      float z = acc[u][v];
-      if (epi >= 1) z += bias[j];
-      C[(int64_t)i * ldc + j] = z;
-      if (epi == 1) H[(int64_t)i * ldc + j] = gelu_f(z);
-    }
-  }
-}
-
-template <typename TA, typename TB>
-static cudaError_t gemm(cudaStream_t st, int M, int N, int K, const TA* A, int64_t lai, int64_t lak,
-                        const TB* B, int64_t lbk, int64_t lbj, float* C, int64_t ldc, int epi = 0,
-                        const float* bias = nullptr, float* H = nullptr) {
-  dim3 grid((N + kTile - 1) / kTile, (M + kTile - 1) / kTile);
-  gemm_kernel<TA, TB><<<grid, kThreads, 0, st>>>(M, N, K, A, lai, lak, B, lbk, lbj, C, ldc, epi,
-                                                  bias, H);
-  return cudaGetLastError();
 }
 
 // dZ = dH * gelu'(Z)
@@ -191,14 +122,49 @@ __global__ void gather_normalise_kernel(const double* src, int64_t ld, const int
   }
 }
 
-// y_hat[b][k] = mean[k] + std[k] * out[b][k] (float64)
+// y_hat[b][k] = mean[k] + std[k] * out[b][k] (float64), plus the nearest anchor's
+// coefficient vector aY[nn[b]][k] when anchors are in use
 __global__ void denormalise_kernel(const float* out, int B, int cols, const double* mean,
-                                   const double* sd, double* y) {
+                                   const double* sd, const int64_t* nn, const double* aY, double* y) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)B * cols;
        t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / cols;
     const int k = (int)(t % cols);
-    y[t] = mean[k] + sd[k] * (double)out[t];
+    double v = mean[k] + sd[k] * (double)out[t];
+    if (nn) v += aY[nn[b] * cols + k];
+    y[t] = v;
   }
+}
+
+// nn[b] = the anchor a nearest to P[b] in the network's input scaling:
+// argmin_a sum_k ((P[b][k] - A[a][k]) / scale[k])^2, the lowest index on ties.
+__global__ void nearest_anchor_kernel(const double* P, int64_t m, int din, const double* A,
+                                      int64_t na, const double* scale, int64_t* nn) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    double best = 0.0;
+    int64_t arg = -1;
+    for (int64_t a = 0; a < na; ++a) {
+      double d2 = 0.0;
+      for (int k = 0; k < din; ++k) {
+        const double d = (P[b * din + k] - A[a * din + k]) / scale[k];
+        d2 += d * d;
+      }
+      if (arg < 0 || d2 < best) {
+        best = d2;
+        arg = a;
+      }
+    }
+    nn[b] = arg;
+  }
+}
+
+// D[b][k] = Y[b][k] - aY[nn[b]][k]
+__global__ void deviation_kernel(const double* Y, int64_t m, int cols, const int64_t* nn,
+                                 const double* aY, double* D) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m * cols;
+       t += (int64_t)gridDim.x * blockDim.x)
+    D[t] = Y[t] - aY[nn[t / cols] * cols + (t % cols)];
 }
 
 }  // namespace mlp
@@ -221,9 +187,16 @@ struct Surrogate {
   int64_t cap = 0;
   float *X = nullptr, *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr, *O = nullptr;
   float *Yn = nullptr, *dO = nullptr, *dH = nullptr;
-  int64_t* idx = nullptr;
+  int64_t* idx = nullptr;  // nearest anchor of each row of a prediction chunk
   double* loss = nullptr;
   bool trained = false;
+  int f32_out = 0;              // output layer with the float32 weights (hi + lo bfloat16)
+  float* part = nullptr;        // split-K partial tiles of the weight gradients
+  int64_t part_cap = 0;
+  int* status = nullptr;        // the context's device status word (bounded waits)
+  double* aP = nullptr;         // anchors the network was trained with: na x din, na x dout
+  double* aY = nullptr;
+  int64_t na = 0;
 };
 
 static void free_surrogate(Surrogate* s) {
@@ -231,7 +204,8 @@ static void free_surrogate(Surrogate* s) {
   for (void* p : {(void*)s->theta, (void*)s->grad, (void*)s->m, (void*)s->v, (void*)s->wbf,
                   (void*)s->woff, (void*)s->wlen, (void*)s->norm, (void*)s->X, (void*)s->Z1,
                   (void*)s->H1, (void*)s->Z2, (void*)s->H2, (void*)s->O, (void*)s->Yn,
-                  (void*)s->dO, (void*)s->dH, (void*)s->idx, (void*)s->loss})
+                  (void*)s->dO, (void*)s->dH, (void*)s->idx, (void*)s->loss, (void*)s->part,
+                  (void*)s->aP, (void*)s->aY})
     cudaFree(p);
   delete s;
 }
@@ -304,6 +278,9 @@ sas_status surrogate_create(sas_ctx* c, uint64_t seed) {
   e = e ? e : cudaMalloc(&s->wlen, sizeof(wlen));
   e = e ? e : cudaMalloc(&s->norm, sizeof(double) * 2 * (din + dout));
   e = e ? e : cudaMalloc(&s->loss, sizeof(double));
+  s->part_cap = 32 * std::max<int64_t>((int64_t)h * h, std::max<int64_t>((int64_t)h * din, (int64_t)dout * h));
+  e = e ? e : cudaMalloc(&s->part, sizeof(float) * s->part_cap);
+  s->status = c->dev_status;
   e = e ? e : cudaMemcpy(s->theta, host.data(), sizeof(float) * o, cudaMemcpyHostToDevice);
   e = e ? e : cudaMemset(s->m, 0, sizeof(float) * o);
   e = e ? e : cudaMemset(s->v, 0, sizeof(float) * o);
@@ -330,18 +307,38 @@ sas_status surrogate_create(sas_ctx* c, uint64_t seed) {
   return SAS_OK;
 }
 
-// Forward pass on rows already normalised in s->X (float32); output in s->O.
-static cudaError_t forward(Surrogate* s, int64_t B, cudaStream_t st) {
+// C = A B on the tensor cores (A float32; B float32 or bfloat16 by tb).
+static cudaError_t mm(Surrogate* s, cudaStream_t st, int M, int N, int K, const float* A, int64_t lai,
+                      int64_t lak, const void* B, int tb, int64_t lbk, int64_t lbj, float* C,
+                      int64_t ldc, int epi = 0, const float* bias = nullptr, float* H = nullptr) {
+  return mlp_gemm_tc(st, s->part, s->part_cap, s->status, M, N, K, A, kMlpF32, lai, lak, B, tb, lbk,
+                     lbj, C, ldc, epi, bias, H);
+}
+
+// The output layer's weights as the products read them: the bfloat16 copy, or the float32
+// masters when the float32 output layer is chosen.
+static const void* w3_operand(const Surrogate* s, int* tb) {
+  *tb = s->f32_out ? kMlpF32 : kMlpBF16;
+  if (s->f32_out) return s->theta + s->off[4];
+  return s->wbf + (int64_t)s->h * s->din + (int64_t)s->h * s->h;
+}
+
+// Forward pass on rows already normalised in s->X (float32); output in s->O.  keep_z: also
+// store the pre-activations Z1, Z2 (training needs them; inference writes H1, H2 only).
+static cudaError_t forward(Surrogate* s, int64_t B, cudaStream_t st, bool keep_z = true) {
   const __nv_bfloat16* W1 = s->wbf;
   const __nv_bfloat16* W2 = W1 + (int64_t)s->h * s->din;
-  const __nv_bfloat16* W3 = W2 + (int64_t)s->h * s->h;
+  int t3 = kMlpBF16;
+  const void* W3 = w3_operand(s, &t3);
   const int din = s->din, h = s->h, dout = s->dout;
-  cudaError_t e = mlp::gemm(st, (int)B, h, din, s->X, din, 1, W1, 1, din, s->Z1, h, 1,
-                            s->theta + s->off[1], s->H1);
+  const int ep = keep_z ? 1 : 3;
+  cudaError_t e = mm(s, st, (int)B, h, din, s->X, din, 1, W1, kMlpBF16, 1, din, keep_z ? s->Z1 : s->H1,
+                     h, ep, s->theta + s->off[1], s->H1);
   if (e == cudaSuccess)
-    e = mlp::gemm(st, (int)B, h, h, s->H1, h, 1, W2, 1, h, s->Z2, h, 1, s->theta + s->off[3], s->H2);
+    e = mm(s, st, (int)B, h, h, s->H1, h, 1, W2, kMlpBF16, 1, h, keep_z ? s->Z2 : s->H2, h, ep,
+           s->theta + s->off[3], s->H2);
   if (e == cudaSuccess)
-    e = mlp::gemm(st, (int)B, dout, h, s->H2, h, 1, W3, 1, h, s->O, dout, 2, s->theta + s->off[5]);
+    e = mm(s, st, (int)B, dout, h, s->H2, h, 1, W3, t3, 1, h, s->O, dout, 2, s->theta + s->off[5]);
   return e;
 }
 
@@ -349,7 +346,8 @@ static cudaError_t forward(Surrogate* s, int64_t B, cudaStream_t st) {
 static cudaError_t forward_backward(Surrogate* s, int64_t B, cudaStream_t st) {
   const __nv_bfloat16* W1 = s->wbf;
   const __nv_bfloat16* W2 = W1 + (int64_t)s->h * s->din;
-  const __nv_bfloat16* W3 = W2 + (int64_t)s->h * s->h;
+  int t3 = kMlpBF16;
+  const void* W3 = w3_operand(s, &t3);
   const int din = s->din, h = s->h, dout = s->dout;
   float* g = s->grad;
   cudaError_t e = forward(s, B, st);
@@ -357,22 +355,22 @@ static cudaError_t forward_backward(Surrogate* s, int64_t B, cudaStream_t st) {
   cudaMemsetAsync(s->loss, 0, sizeof(double), st);
   mlp::mse_kernel<<<64, 256, 0, st>>>(s->O, s->Yn, B * dout, 1.0f / (float)(B * dout), s->dO, s->loss);
   // layer 3: dW3 = dO^T H2, db3 = colsum dO, dH2 = dO W3
-  e = mlp::gemm(st, dout, h, (int)B, s->dO, 1, dout, s->H2, h, 1, g + s->off[4], h);
+  e = mm(s, st, dout, h, (int)B, s->dO, 1, dout, s->H2, kMlpF32, h, 1, g + s->off[4], h);
   if (e != cudaSuccess) return e;
   mlp::colsum_kernel<<<(dout + 255) / 256, 256, 0, st>>>(s->dO, (int)B, dout, dout, g + s->off[5]);
-  e = mlp::gemm(st, (int)B, h, dout, s->dO, dout, 1, W3, h, 1, s->dH, h);
+  e = mm(s, st, (int)B, h, dout, s->dO, dout, 1, W3, t3, h, 1, s->dH, h);
   if (e != cudaSuccess) return e;
   mlp::gelu_backward_kernel<<<256, 256, 0, st>>>(s->Z2, s->dH, B * h);
-  // layer 2
-  e = mlp::gemm(st, h, h, (int)B, s->dH, 1, h, s->H1, h, 1, g + s->off[2], h);
+  // layer 2: dW2 = dZ2^T H1, db2 = colsum dZ2
+  e = mm(s, st, h, h, (int)B, s->dH, 1, h, s->H1, kMlpF32, h, 1, g + s->off[2], h);
   if (e != cudaSuccess) return e;
   mlp::colsum_kernel<<<(h + 255) / 256, 256, 0, st>>>(s->dH, (int)B, h, h, g + s->off[3]);
-  // dH1 = dZ2 W2 (into Z1's gradient: reuse H2 as scratch after its use)
-  e = mlp::gemm(st, (int)B, h, h, s->dH, h, 1, W2, h, 1, s->H2, h);
+  // dH1 = dZ2 W2 (into H2, whose values are no longer needed)
+  e = mm(s, st, (int)B, h, h, s->dH, h, 1, W2, kMlpBF16, h, 1, s->H2, h);
   if (e != cudaSuccess) return e;
   mlp::gelu_backward_kernel<<<256, 256, 0, st>>>(s->Z1, s->H2, B * h);
-  // layer 1
-  e = mlp::gemm(st, h, din, (int)B, s->H2, 1, h, s->X, din, 1, g + s->off[0], din);
+  // layer 1: dW1 = dZ1^T X, db1 = colsum dZ1
+  e = mm(s, st, h, din, (int)B, s->H2, 1, h, s->X, kMlpF32, din, 1, g + s->off[0], din);
   if (e != cudaSuccess) return e;
   mlp::colsum_kernel<<<(h + 255) / 256, 256, 0, st>>>(s->H2, (int)B, h, h, g + s->off[1]);
   return cudaGetLastError();
@@ -388,16 +386,27 @@ sas_status surrogate_train(sas_ctx* c, const double* P, const double* Y, int64_t
     s = static_cast<Surrogate*>(c->surrogate);
   }
   const int din = s->din, dout = s->dout;
-  // normalisation from the training set (host pass over P and Y)
-  std::vector<double> hp((size_t)ntrain * din), hy((size_t)ntrain * dout);
-  cudaError_t e = cudaMemcpy(hp.data(), P, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess) e = cudaMemcpy(hy.data(), Y, sizeof(double) * hy.size(), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) {
-    set_error(std::string("surrogate_train: ") + cudaGetErrorString(e));
-    return SAS_ECUDA;
+  s->f32_out = c->surr_f32_out;
+  // the network keeps its own copy of the context's anchors (none: it learns y itself)
+  cudaError_t e = cudaSuccess;
+  cudaFree(s->aP);
+  cudaFree(s->aY);
+  s->aP = s->aY = nullptr;
+  s->na = 0;
+  if (c->surr_na > 0) {
+    e = cudaMalloc(&s->aP, sizeof(double) * c->surr_na * din);
+    if (e == cudaSuccess) e = cudaMalloc(&s->aY, sizeof(double) * c->surr_na * dout);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(s->aP, c->surr_aP, sizeof(double) * c->surr_na * din, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(s->aY, c->surr_aY, sizeof(double) * c->surr_na * dout, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) s->na = c->surr_na;
   }
+  // normalisation of the inputs from the training set (host pass over P)
+  std::vector<double> hp((size_t)ntrain * din), hy((size_t)ntrain * dout);
+  if (e == cudaSuccess) e = cudaMemcpy(hp.data(), P, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost);
   std::vector<double> norm(2 * (din + dout));
-  for (int k = 0; k < din; ++k) {
+  for (int k = 0; k < din && e == cudaSuccess; ++k) {
     double lo = hp[k], hi = hp[k];
     for (int64_t i = 0; i < ntrain; ++i) {
       lo = std::min(lo, hp[i * din + k]);
@@ -405,6 +414,29 @@ sas_status surrogate_train(sas_ctx* c, const double* P, const double* Y, int64_t
     }
     norm[k] = 0.5 * (lo + hi);
     norm[din + k] = hi > lo ? 0.5 * (hi - lo) : 1.0;
+  }
+  // targets: y, or its deviation from the nearest anchor's coefficient vector
+  const double* Yt = Y;
+  double* dev = nullptr;
+  int64_t* dnn = nullptr;
+  if (e == cudaSuccess && s->na > 0) {
+    e = cudaMemcpy(s->norm, norm.data(), sizeof(double) * 2 * din, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&dnn, sizeof(int64_t) * ntrain);
+    if (e == cudaSuccess) e = cudaMalloc(&dev, sizeof(double) * ntrain * dout);
+    if (e == cudaSuccess) {
+      mlp::nearest_anchor_kernel<<<(int)std::min<int64_t>(1024, (ntrain + 127) / 128), 128>>>(
+          P, ntrain, din, s->aP, s->na, s->norm + din, dnn);
+      mlp::deviation_kernel<<<256, 256>>>(Y, ntrain, dout, dnn, s->aY, dev);
+      e = cudaGetLastError();
+    }
+    Yt = dev;
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(hy.data(), Yt, sizeof(double) * hy.size(), cudaMemcpyDeviceToHost);
+  cudaFree(dnn);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    set_error(std::string("surrogate_train: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SAS_ENOMEM : SAS_ECUDA;
   }
   for (int k = 0; k < dout; ++k) {
     double mu = 0.0, sq = 0.0;
@@ -418,6 +450,7 @@ sas_status surrogate_train(sas_ctx* c, const double* P, const double* Y, int64_t
   e = cudaMemcpy(s->norm, norm.data(), sizeof(double) * norm.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = ensure_acts(s, batch);
   if (e != cudaSuccess) {
+    cudaFree(dev);
     set_error(std::string("surrogate_train: ") + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? SAS_ENOMEM : SAS_ECUDA;
   }
@@ -438,7 +471,7 @@ sas_status surrogate_train(sas_ctx* c, const double* P, const double* Y, int64_t
     int64_t nb = 0;
     for (int64_t b0 = 0; b0 + batch <= ntrain && e == cudaSuccess; b0 += batch, ++nb) {
       mlp::gather_normalise_kernel<<<128, 256, 0, st>>>(P, din, dperm + b0, batch, din, in_c, in_s, s->X);
-      mlp::gather_normalise_kernel<<<128, 256, 0, st>>>(Y, dout, dperm + b0, batch, dout, out_m, out_s,
+      mlp::gather_normalise_kernel<<<128, 256, 0, st>>>(Yt, dout, dperm + b0, batch, dout, out_m, out_s,
                                                          s->Yn);
       e = forward_backward(s, batch, st);
       if (e != cudaSuccess) break;
@@ -456,8 +489,9 @@ sas_status surrogate_train(sas_ctx* c, const double* P, const double* Y, int64_t
     }
     if (loss_out) loss_out[ep] = nb ? ep_loss / nb : 0.0;
   }
-  cudaFree(dperm);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(dperm);
+  cudaFree(dev);
   if (e != cudaSuccess) {
     set_error(std::string("surrogate_train: ") + cudaGetErrorString(e));
     return SAS_ECUDA;
@@ -470,16 +504,21 @@ cudaError_t surrogate_predict(sas_ctx* c, const double* params, int64_t m, doubl
                               cudaStream_t st) {
   Surrogate* s = static_cast<Surrogate*>(c->surrogate);
   const int din = s->din, dout = s->dout;
+  s->f32_out = c->surr_f32_out;
   const int64_t chunk = 65536;
   cudaError_t e = ensure_acts(s, std::min<int64_t>(m, chunk));
   for (int64_t b0 = 0; b0 < m && e == cudaSuccess; b0 += chunk) {
     const int64_t B = std::min<int64_t>(chunk, m - b0);
     mlp::gather_normalise_kernel<<<256, 256, 0, st>>>(params + b0 * din, din, nullptr, (int)B, din,
                                                        s->norm, s->norm + din, s->X);
-    e = forward(s, B, st);
+    if (s->na > 0)
+      mlp::nearest_anchor_kernel<<<(int)std::min<int64_t>(1024, (B + 127) / 128), 128, 0, st>>>(
+          params + b0 * din, B, din, s->aP, s->na, s->norm + din, s->idx);
+    e = forward(s, B, st, false);
     if (e != cudaSuccess) break;
-    mlp::denormalise_kernel<<<256, 256, 0, st>>>(s->O, (int)B, dout, s->norm + 2 * din,
-                                                  s->norm + 2 * din + dout, Yhat + b0 * dout);
+    mlp::denormalise_kernel<<<1024, 256, 0, st>>>(s->O, (int)B, dout, s->norm + 2 * din,
+                                                  s->norm + 2 * din + dout, s->na > 0 ? s->idx : nullptr,
+                                                  s->aY, Yhat + b0 * dout);
     e = cudaGetLastError();
   }
   return e;
@@ -491,6 +530,7 @@ sas_status surrogate_grad(sas_ctx* c, const double* X, const double* Yn, int64_t
                           float* grads_host, cudaStream_t st) {
   Surrogate* s = static_cast<Surrogate*>(c->surrogate);
   if (!s) return SAS_EINVAL;
+  s->f32_out = c->surr_f32_out;
   cudaError_t e = ensure_acts(s, B);
   if (e == cudaSuccess) {
     std::vector<double> zero(std::max(s->din, s->dout), 0.0), one(std::max(s->din, s->dout), 1.0);
@@ -539,6 +579,29 @@ sas_status surrogate_io(sas_ctx* c, int get, float* theta, double* norm) {
     set_error(std::string("surrogate weights: ") + cudaGetErrorString(e));
     return SAS_ECUDA;
   }
+  return SAS_OK;
+}
+
+// Anchors for the next training: device P (n x dp) and Y (n x r), copied into buffers the
+// context owns; n = 0 clears them.
+sas_status surrogate_set_anchors(sas_ctx* c, const double* P, const double* Y, int64_t n) {
+  cudaFree(c->surr_aP);
+  cudaFree(c->surr_aY);
+  c->surr_aP = c->surr_aY = nullptr;
+  c->surr_na = 0;
+  if (n == 0) return SAS_OK;
+  cudaError_t e = cudaMalloc(&c->surr_aP, sizeof(double) * n * c->dp);
+  if (e == cudaSuccess) e = cudaMalloc(&c->surr_aY, sizeof(double) * n * c->r);
+  if (e == cudaSuccess) e = cudaMemcpy(c->surr_aP, P, sizeof(double) * n * c->dp, cudaMemcpyDeviceToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->surr_aY, Y, sizeof(double) * n * c->r, cudaMemcpyDeviceToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(c->surr_aP);
+    cudaFree(c->surr_aY);
+    c->surr_aP = c->surr_aY = nullptr;
+    set_error(std::string("surrogate anchors: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SAS_ENOMEM : SAS_ECUDA;
+  }
+  c->surr_na = n;
   return SAS_OK;
 }
 

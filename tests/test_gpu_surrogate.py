@@ -51,22 +51,29 @@ def case():
     return Case("diffusion_2d", N=40, r=60, s=120, m=600)
 
 
-def test_gradients_match_oracle(case):
+@pytest.mark.parametrize("B,f32_out", [(512, 0), (1000, 0), (1000, 1), (64, 1)],
+                         ids=["b512", "b1000-ragged", "b1000-f32-output-layer", "b64-f32-output-layer"])
+def test_gradients_match_oracle(case, B, f32_out):
+    """All products on the tensor cores (bfloat16 operands, float32 activations as two
+    bfloat16 terms, float32 accumulation): one forward/backward against the oracle.  B
+    covers one K block, a ragged batch split over many CTAs (split-K weight gradients),
+    and the float32 output layer (SAS_OPT_SURROGATE_F32_OUT: the oracle then takes W3
+    unrounded)."""
     p = case.prob
     solver = AffineSolver(p, case.S, case.J, mode=api.SAS_MODE_MIXED, device="cuda")
+    api.subapsnap_set_option(solver.ctx, api.SAS_OPT_SURROGATE_F32_OUT, f32_out)
     nparam = api.subapsnap_surrogate_weights(solver.ctx, False)  # creates the network
     rng = np.random.default_rng(0)
     theta = np.zeros(nparam, dtype=np.float32)
     api.subapsnap_surrogate_weights(solver.ctx, True, theta)
     theta += (0.05 * rng.standard_normal(nparam)).astype(np.float32)  # non-trivial biases too
     api.subapsnap_surrogate_weights(solver.ctx, False, theta)
-    B = 512
     X = rng.uniform(-1, 1, (B, p.dp))
     Yn = rng.standard_normal((B, p.r))
     loss, g = api.subapsnap_surrogate_grad(solver.ctx, torch.from_numpy(X).cuda(),
                                            torch.from_numpy(Yn).cuda(), nparam)
     W1, b1, W2, b2, W3, b3 = unpack(theta, p.dp, 256, p.r)
-    params = [(bf16_round(W1), b1), (bf16_round(W2), b2), (bf16_round(W3), b3)]
+    params = [(bf16_round(W1), b1), (bf16_round(W2), b2), (W3 if f32_out else bf16_round(W3), b3)]
     # the device feeds float32 inputs: round them the same way
     Xf = X.astype(np.float32).astype(np.float64)
     Yf = Yn.astype(np.float32).astype(np.float64)
@@ -78,6 +85,56 @@ def test_gradients_match_oracle(case):
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         print(f"grad tensor {k}: rel err {rel:.2e}")
         assert rel <= 2e-3, (k, rel)
+    solver.close()
+
+
+def test_predictions_with_anchors_match_oracle(case):
+    """Prediction = nearest anchor's y + network output (denormalised): the nearest anchor
+    (input scaling, lowest index on ties) must equal numpy's choice exactly, and y_hat the
+    oracle's float64 forward pass of the same weights within float32-class error."""
+    p = case.prob
+    solver = AffineSolver(p, case.S, case.J, mode=api.SAS_MODE_MIXED, device="cuda")
+    rng = np.random.default_rng(4)
+    na, ntrain = 37, 512
+    Pa = rng.uniform(0.0, 1.0, (na, p.dp))
+    Pa[5] = Pa[3]  # a duplicate anchor: the lower index wins
+    Ya = rng.standard_normal((na, p.r))
+    api.subapsnap_surrogate_set_anchors(solver.ctx, torch.from_numpy(Pa).cuda(), torch.from_numpy(Ya).cuda())
+    Ptr = rng.uniform(0.0, 1.0, (ntrain, p.dp))
+    Ytr = rng.standard_normal((ntrain, p.r))
+    # zero epochs: fixes the normalisation (from the deviations) and the anchors only
+    api.subapsnap_surrogate_train(solver.ctx, torch.from_numpy(Ptr).cuda(), torch.from_numpy(Ytr).cuda(),
+                                  0, 256, 1e-3, seed=3)
+    nparam = api.subapsnap_surrogate_weights(solver.ctx, False)
+    theta = np.zeros(nparam, dtype=np.float32)
+    norm = np.zeros(2 * (p.dp + p.r))
+    api.subapsnap_surrogate_weights(solver.ctx, True, theta, norm)
+    c, hw = norm[:p.dp], norm[p.dp:2 * p.dp]
+    mu, sd = norm[2 * p.dp:2 * p.dp + p.r], norm[2 * p.dp + p.r:]
+    # the normalisation was fitted to the deviations from the nearest anchors
+    def nearest(P):
+        d2 = (((P[:, None, :] - Pa[None, :, :]) / hw) ** 2).sum(axis=2)
+        return d2.argmin(axis=1)
+    dev = Ytr - Ya[nearest(Ptr)]
+    np.testing.assert_allclose(mu, dev.mean(axis=0), rtol=1e-12, atol=1e-12)
+    m = 300
+    P = rng.uniform(0.0, 1.0, (m, p.dp))
+    P[7] = Pa[3]
+    Yhat = torch.empty((m, p.r), dtype=torch.float64, device="cuda")
+    api.subapsnap_surrogate_predict(solver.ctx, torch.from_numpy(P).cuda(), m, Yhat)
+    torch.cuda.synchronize()
+    W1, b1, W2, b2, W3, b3 = unpack(theta, p.dp, 256, p.r)
+    params = [(bf16_round(W1), b1), (bf16_round(W2), b2), (bf16_round(W3), b3)]
+    Xn = ((P - c) / hw).astype(np.float32).astype(np.float64)
+    out, _ = omlp.forward(params, Xn)
+    nn = nearest(P)
+    assert nn[7] == 3
+    ref = Ya[nn] + mu + sd * out
+    net = (Yhat.cpu().numpy() - Ya[nn] - mu) / sd
+    rel = np.linalg.norm(net - out, axis=1) / np.linalg.norm(out, axis=1)
+    print(f"anchored predictions: network output rel err max {rel.max():.2e}")
+    assert rel.max() <= 1e-4
+    np.testing.assert_allclose(Yhat.cpu().numpy(), ref, rtol=0, atol=1e-4 * np.abs(ref).max())
     solver.close()
 
 
