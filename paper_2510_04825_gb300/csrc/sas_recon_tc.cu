@@ -10,16 +10,23 @@
 // 4 n bytes per parameter and reads the split S (8 n rpad bytes) once per
 // launch, however many parameters the launch has.
 //
-// Structure (one persistent CTA per SM, 6 warps):
+// Structure (one persistent CTA per SM; 2 + EW warps):
 //   warp 0    TMA producer: for each work unit the S tile (S_hi, S_lo of 128
-//             rows), then the unit's y tiles (y_hi, y_lo of 64 parameters,
-//             L2-resident) into a 4-stage ring;
-//   warp 1    one thread issues tcgen05.mma (kind::tf32, M=128, N=64, K=8)
-//             into 4 TMEM accumulators of 64 columns;
-//   warps 2-5 epilogue: tcgen05.ld 32 lanes x 32 columns at a time, staged in
-//             shared memory and written by TMA bulk-tensor stores; each warp
-//             owns its TMEM lane quarter.
-// A work unit is one 128-row tile of S and a range of 64-parameter tiles; the
+//             rows), then the unit's y tiles (y_hi, y_lo of BN parameters,
+//             L2-resident) into a ring of stages;
+//   warp 1    one thread issues tcgen05.mma (M = 128, N = BN) into TMEM
+//             accumulator slots of BN columns;
+//   epilogue  EW = 4 warps (one per TMEM lane quarter) or 8 (two per quarter,
+//             alternate column halves): tcgen05.ld 32 lanes x 32 columns at a
+//             time, then either direct coalesced streaming stores (lane = row,
+//             one 128-byte warp store per parameter; the default) or, with
+//             SAS_OPT_RECON_STORE = 0 and 4 warps, staging in shared memory and
+//             TMA bulk-tensor stores.
+// The default launch (SAS_OPT_RECON_KERNEL 0 or 3) is kind::tf32 with BN = 128,
+// 2 stages, 4 accumulator slots, 4 epilogue warps and direct stores; option 2
+// takes 64-parameter tiles, 4 rotates the order of the parameter tiles, 5 is
+// the f16 variant and 6 the 8-warp epilogue.
+// A work unit is one 128-row tile of S and a range of BN-parameter tiles; the
 // S tile stays resident while the unit's y tiles stream past it.  With at
 // least as many row tiles as SMs a unit covers every parameter tile, so S is
 // read from HBM once; with fewer (small n) the parameter tiles are split into

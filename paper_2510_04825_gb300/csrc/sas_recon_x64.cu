@@ -39,14 +39,16 @@
 //              TMEM accumulators of 128 columns (all 512), in the order L0, L1,
 //              tail (L4, then L3 on the scaled sum), L2;
 //   warps 2-17 epilogue, 4 per TMEM lane quarter, 32 columns each.  They drain
-//              P_0, P_1 (into a = P_0 2^9 + P_1) and the tail (into rint(T)) as
-//              each completes and release it at once, so that the next tile's
-//              first 48 MMAs run while they assemble this tile from P_2; then
-//              they convert (alternating the int64 -> float64 conversion unit and
-//              an integer-only normalisation, so that both work side by side),
-//              scale and store 8 bytes per lane (one coalesced 256-byte warp
-//              store per parameter).  18 warps put 5 on some SM sub-partitions,
-//              which caps registers at 96 per thread.
+//              P_0 and P_1 (into a = P_0 2^9 + P_1) as each completes and release
+//              it at once, so that the next tile's first 12 MMAs run while they
+//              assemble this tile; then, 16 columns at a time, rint(T) and P_2
+//              (both released once the second half is loaded, for the next
+//              tile's remaining 48 MMAs); they convert (alternating the int64 ->
+//              float64 conversion, which runs on the float64 pipe, and an
+//              integer-only normalisation, so that both work side by side), scale
+//              and store 8 bytes per lane (one coalesced 256-byte warp store per
+//              parameter).  18 warps put 5 on some SM sub-partitions, which caps
+//              registers at 96 per thread.
 // A shared-memory operand pair of f16 at N = 128 reads 8 KB per 64-clock MMA,
 // the SM's shared-memory bandwidth: 128-parameter tiles keep the MMA at its
 // full rate, narrower ones would not.
@@ -239,8 +241,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- MMA issuer: the whole warp runs the loop, so that descriptors and
     // counters are warp-uniform; the elected lane issues the MMAs and their commits.
     // Per tile the levels go in the order L0, L1, tail (L4 then L3), L2: the epilogue
-    // drains the first three as they complete, so that while it assembles the tile
-    // from P_2 the next tile's first 48 MMAs already run.
+    // drains the first two as they complete, so that while it assembles the tile the
+    // next tile's first 12 MMAs already run, and the tail and L2 half-way through.
     const bool leader = elect_one();
     int t = 0, ua = 0;
     uint32_t last_bar = 0, last_par = 0;
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row = (int64_t)mt * kBM + q * 32 + lane;
       const bool row_ok = row < p.n;
       const int erow = row_ok ? p.erow[row] : 0;
+      const bool rows_full = __all_sync(0xffffffffu, row_ok);  // the fast path stores unguarded
       const int emin = __reduce_min_sync(0xffffffffu, erow);
       const int emax = __reduce_max_sync(0xffffffffu, erow);
       const int ehi = erow * (1 << 20);  // e_i in the exponent field of the high word
@@ -374,11 +377,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         // integer add to the high word.  Otherwise every entry takes the checked path.
         const int fmin = __reduce_min_sync(0xffffffffu, fcol);
         const int fmax = __reduce_max_sync(0xffffffffu, fcol);
-        const bool fast = j0 + 32 <= p.m && emin + fmin - 45 >= -1022 && emax + fmax - 45 <= 977;
+        const bool fast = rows_full && j0 + 32 <= p.m && emin + fmin - 45 >= -1022 &&
+                          emax + fmax - 45 <= 977;
         const int fhi = (fcol - 45) * (1 << 20);  // f_j - 45, lane c holds column c's
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
         const uint32_t par = (uint32_t)t & 1u;
-        int acol[32], itail[32];
+        int acol[32];
         float v[32];
         auto wait_acc = [&](int acc) -> bool {
           const bool ok = __all_sync(0xffffffffu, mbar_wait_idle(tfull0 + 8 * acc, par, &abort_flag,
@@ -391,8 +395,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
         };
-        // P_0 and P_1 -> a = P_0 2^9 + P_1 (|a| < 2^28); T -> rint(T); each accumulator is
-        // released as soon as it is read, for the next tile's first 48 MMAs
+        // P_0 and P_1 -> a = P_0 2^9 + P_1 (|a| < 2^28); each accumulator is released as soon
+        // as it is read, for the next tile's first 12 MMAs
         if (!wait_acc(0)) { stop = true; break; }
         tmem_ld32(ta, v);
         release(0);
@@ -403,33 +407,34 @@ __global__ void __launch_bounds__(kThreads, 1)
         release(1);
 #pragma unroll
         for (int c = 0; c < 32; ++c) acol[c] = acol[c] * 512 + cvt_rni(v[c]);
-        if (!wait_acc(3)) { stop = true; break; }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          tmem_ld16(ta + 3 * kBN + 16 * h, v);
-          if (h == 1) release(3);
-#pragma unroll
-          for (int c = 0; c < 16; ++c) itail[16 * h + c] = cvt_rni(v[c]);
-        }
-        // P_2 last, 16 columns at a time: x = 2^{e_i + f_j - 45} (a 2^18 + P_2 2^9 + rint(T))
-        if (!wait_acc(2)) { stop = true; break; }
+        // then 16 columns at a time: rint(T) and P_2, and x = 2^{e_i + f_j - 45} (a 2^18 +
+        // P_2 2^9 + rint(T)); the tail and P_2 accumulators are released once the second
+        // half is loaded (16 live tail values instead of 32 relieve the register cap)
+        if (!wait_acc(3) || !wait_acc(2)) { stop = true; break; }
         double* orow = p.out + j0 * p.n + row;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
+          int itail[16];
           float w[16];
+          tmem_ld16(ta + 3 * kBN + 16 * h, w);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) itail[c] = cvt_rni(w[c]);
           tmem_ld16(ta + 2 * kBN + 16 * h, w);
-          if (h == 1) release(2);
+          if (h == 1) {
+            release(3);
+            release(2);
+          }
           if (fast) {
             double* o = orow + (int64_t)(16 * h) * p.n;
+            const int64_t ns = p.n;
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
               // the shuffle runs on every lane (a full-mask shuffle must not sit under a
               // lane-dependent condition)
               const int add = ehi + __shfl_sync(0xffffffffu, fhi, 16 * h + c);
-              const double x = (c & 1) ? assemble(acol[16 * h + c], w[c], itail[16 * h + c], add)
-                                       : assemble_int(acol[16 * h + c], w[c], itail[16 * h + c], add);
-              if (row_ok) __stcs(o, x);
-              o += p.n;
+              const double x = (c & 1) ? assemble(acol[16 * h + c], w[c], itail[c], add)
+                                       : assemble_int(acol[16 * h + c], w[c], itail[c], add);
+              __stcs(o + c * ns, x);
             }
           } else {
             // checked: V 2^E tested against the float64 range (below it the entry is
@@ -438,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int c = 0; c < 16; ++c) {
               const int cc = 16 * h + c;
               const int E = erow + __shfl_sync(0xffffffffu, fcol, cc) - 45;
-              const double d = assemble(acol[cc], w[c], itail[cc], 0);
+              const double d = assemble(acol[cc], w[c], itail[c], 0);
               int hi = __double2hiint(d), lo = __double2loint(d);
               const int ex = ((hi >> 20) & 0x7ff) + E;
               if (hi == 0 || ex <= 0) {
