@@ -407,41 +407,42 @@ __global__ void __launch_bounds__(kThreads, 1)
         release(1);
 #pragma unroll
         for (int c = 0; c < 32; ++c) acol[c] = acol[c] * 512 + cvt_rni(v[c]);
-        // then 16 columns at a time: rint(T) and P_2, and x = 2^{e_i + f_j - 45} (a 2^18 +
-        // P_2 2^9 + rint(T)); the tail and P_2 accumulators are released once the second
-        // half is loaded (16 live tail values instead of 32 relieve the register cap)
+        // then kSub columns at a time: rint(T) and P_2, and x = 2^{e_i + f_j - 45} (a 2^18 +
+        // P_2 2^9 + rint(T)); the tail and P_2 accumulators are released once the last
+        // sub-block is loaded (kSub live tail values instead of 32 relieve the register cap)
         if (!wait_acc(3) || !wait_acc(2)) { stop = true; break; }
         double* orow = p.out + j0 * p.n + row;
+        constexpr int kSub = 8;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          int itail[16];
-          float w[16];
-          tmem_ld16(ta + 3 * kBN + 16 * h, w);
+        for (int h = 0; h < 32 / kSub; ++h) {
+          int itail[kSub];
+          float w[kSub];
+          tmem_ld8(ta + 3 * kBN + kSub * h, w);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) itail[c] = cvt_rni(w[c]);
-          tmem_ld16(ta + 2 * kBN + 16 * h, w);
-          if (h == 1) {
+          for (int c = 0; c < kSub; ++c) itail[c] = cvt_rni(w[c]);
+          tmem_ld8(ta + 2 * kBN + kSub * h, w);
+          if (h == 32 / kSub - 1) {
             release(3);
             release(2);
           }
           if (fast) {
-            double* o = orow + (int64_t)(16 * h) * p.n;
+            double* o = orow + (int64_t)(kSub * h) * p.n;
             const int64_t ns = p.n;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < kSub; ++c) {
               // the shuffle runs on every lane (a full-mask shuffle must not sit under a
               // lane-dependent condition)
-              const int add = ehi + __shfl_sync(0xffffffffu, fhi, 16 * h + c);
-              const double x = (c & 1) ? assemble(acol[16 * h + c], w[c], itail[c], add)
-                                       : assemble_int(acol[16 * h + c], w[c], itail[c], add);
+              const int add = ehi + __shfl_sync(0xffffffffu, fhi, kSub * h + c);
+              const double x = (c & 1) ? assemble(acol[kSub * h + c], w[c], itail[c], add)
+                                       : assemble_int(acol[kSub * h + c], w[c], itail[c], add);
               __stcs(o + c * ns, x);
             }
           } else {
             // checked: V 2^E tested against the float64 range (below it the entry is
             // flushed to zero, above it it overflows to +-inf), ragged columns skipped
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int cc = 16 * h + c;
+            for (int c = 0; c < kSub; ++c) {
+              const int cc = kSub * h + c;
               const int E = erow + __shfl_sync(0xffffffffu, fcol, cc) - 45;
               const double d = assemble(acol[cc], w[c], itail[c], 0);
               int hi = __double2hiint(d), lo = __double2loint(d);
