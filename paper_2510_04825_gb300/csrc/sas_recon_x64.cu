@@ -159,6 +159,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   // bars: afull, aempty, bfull[kSlots], bempty[kSlots], tfull[4], tempty[4]
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
+  __shared__ __align__(16) int colexp[kEpiWarps][32];  // per epilogue warp: (f_j - 45) 2^20
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t afull = smem_u32(&bars[0]), aempty = smem_u32(&bars[1]);
@@ -379,7 +380,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int fmax = __reduce_max_sync(0xffffffffu, fcol);
         const bool fast = rows_full && j0 + 32 <= p.m && emin + fmin - 45 >= -1022 &&
                           emax + fmax - 45 <= 977;
-        const int fhi = (fcol - 45) * (1 << 20);  // f_j - 45, lane c holds column c's
+        // (f_j - 45) in the exponent field, column c's at colexp[.][c]: read back as
+        // broadcast 16-byte loads (one per 4 entries) instead of a shuffle per entry
+        int* fsh = colexp[warp - 2];
+        __syncwarp();  // the previous tile's reads are done
+        fsh[lane] = (fcol - 45) * (1 << 20);
+        __syncwarp();
         const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32);
         const uint32_t par = (uint32_t)t & 1u;
         int acol[32];
@@ -428,11 +434,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (fast) {
             double* o = orow + (int64_t)(kSub * h) * p.n;
             const int64_t ns = p.n;
+            int fc[kSub];
+#pragma unroll
+            for (int c = 0; c < kSub; c += 4)
+              *reinterpret_cast<int4*>(fc + c) = *reinterpret_cast<const int4*>(fsh + kSub * h + c);
 #pragma unroll
             for (int c = 0; c < kSub; ++c) {
-              // the shuffle runs on every lane (a full-mask shuffle must not sit under a
-              // lane-dependent condition)
-              const int add = ehi + __shfl_sync(0xffffffffu, fhi, kSub * h + c);
+              const int add = ehi + fc[c];
               const double x = (c & 1) ? assemble(acol[kSub * h + c], w[c], itail[c], add)
                                        : assemble_int(acol[kSub * h + c], w[c], itail[c], add);
               __stcs(o + c * ns, x);
