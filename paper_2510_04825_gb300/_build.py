@@ -57,7 +57,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
             if verbose and log.strip():
                 print(f"[{os.path.basename(src)}]\n{log}", file=sys.stderr)
     if jobs or not os.path.exists(LIB):
-        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs, "-lcublas"]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stderr}")

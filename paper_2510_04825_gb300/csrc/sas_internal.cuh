@@ -313,12 +313,18 @@ sas_status surrogate_solve(sas_ctx* c, const double* params, int64_t m, int32_t 
                            uint32_t* flags, double* rho_out, double tol, int64_t* accepted,
                            cudaStream_t st);
 sas_status surrogate_set_anchors(sas_ctx* c, const double* P, const double* Y, int64_t n);
-// tensor-core GEMM of the surrogate (sas_mlp_tc.cu): operand types of A and B
+// tensor-core GEMM with bfloat16-split operands (sas_mlp_tc.cu): operand types of A and B
 enum { kMlpF32 = 0, kMlpBF16 = 1 };
 cudaError_t mlp_gemm_tc(cudaStream_t st, float* part, int64_t part_cap, int* status, int M, int N,
                         int K, const void* A, int ta, int64_t lai, int64_t lak, const void* B, int tb,
                         int64_t lbk, int64_t lbj, float* C, int64_t ldc, int epi, const float* bias,
                         float* H);
+// the same kernel with ns-term splits (2 or 3: float32-accurate) and a batch of nbatch entries
+cudaError_t gemm_split_tc(cudaStream_t st, int ns, float* part, int64_t part_cap, int* status, int M,
+                          int N, int K, const void* A, int ta, int64_t lai, int64_t lak, int64_t bsa,
+                          const void* B, int tb, int64_t lbk, int64_t lbj, int64_t bsb, float* C,
+                          int64_t ldc, int64_t bsc, int nbatch, int epi, const float* bias, float* H);
+cudaError_t gemm_f32_tc_prepare();
 // persistent multi-problem launch
 struct MultiPlan {
   const void* kernel = nullptr;

@@ -33,8 +33,6 @@
 #include <type_traits>
 #include <vector>
 
-#include <cublas_v2.h>
-
 #include "sas_internal.cuh"
 
 namespace sas {
@@ -1590,39 +1588,33 @@ void launch_product_merged(const off::Merged& mg, int K, int64_t n, int B, const
     off::product_merged_kernel<T, TL><<<Gt, kThreads, smem, s>>>(mg, K, n, B, theta, P, Q, st, part);
 }
 
-// The fast Poisson preconditioner's state: DST matrices and eigenvalues per axis,
-// planar work buffers, the per-column coefficients and a cuBLAS handle whose
-// workspace is fixed so that its GEMMs can be captured in the iteration graph.
+// The fast Poisson preconditioner's state: DST matrices and eigenvalues per axis, planar
+// work buffers, the per-column coefficients and the status word of the transform kernels.
 struct PoissonPre {
   int ndim = 0;
   int64_t N[3] = {1, 1, 1};
-  cublasHandle_t h = nullptr;
-  cublasComputeType_t ct = CUBLAS_COMPUTE_32F_EMULATED_16BFX9;
-  DevBuf S[3], mu[3], U, W, coef, ws;
-  PoissonPre() = default;
-  PoissonPre(const PoissonPre&) = delete;
-  PoissonPre& operator=(const PoissonPre&) = delete;
-  ~PoissonPre() {
-    if (h) cublasDestroy(h);
-  }
+  DevBuf S[3], mu[3], U, W, coef, status;
 };
 
-// one axis of the separable transform, out = in transformed along axis a, for C planar columns
-cublasStatus_t dst_axis(PoissonPre& pp, int a, int64_t C, const float* in, float* out) {
-  const float one = 1.0f, zero = 0.0f;
-  const int64_t nx = pp.N[0], ny = pp.N[1], nz = pp.N[2], n = nx * ny * nz;
+// One axis of the separable transform, out = in transformed along axis a, for C planar
+// columns (x fastest, then y, then z, then the column): float32-accurate tensor-core
+// products (three-term bfloat16 splits of both operands, float32 accumulation).
+cudaError_t dst_axis(PoissonPre& pp, int a, int64_t C, const float* in, float* out, cudaStream_t s) {
+  const int64_t nx = pp.N[0], ny = pp.N[1], nz = pp.N[2], n = nx * ny * nz, nxy = nx * ny;
   const float* Sa = pp.S[a].as<float>();
-  if (a == 0)  // S_x (nx x nx) times the nx x (n / nx * C) matrix of all columns
-    return cublasGemmEx(pp.h, CUBLAS_OP_N, CUBLAS_OP_N, (int)nx, (int)(n / nx * C), (int)nx, &one, Sa, CUDA_R_32F,
-                        (int)nx, in, CUDA_R_32F, (int)nx, &zero, out, CUDA_R_32F, (int)nx, pp.ct, CUBLAS_GEMM_DEFAULT);
-  if (a == 1)  // every nx x ny slab times S_y
-    return cublasGemmStridedBatchedEx(pp.h, CUBLAS_OP_N, CUBLAS_OP_N, (int)nx, (int)ny, (int)ny, &one, in,
-                                      CUDA_R_32F, (int)nx, nx * ny, Sa, CUDA_R_32F, (int)ny, 0, &zero, out,
-                                      CUDA_R_32F, (int)nx, nx * ny, (int)(nz * C), pp.ct, CUBLAS_GEMM_DEFAULT);
-  // every column's (nx ny) x nz matrix times S_z
-  return cublasGemmStridedBatchedEx(pp.h, CUBLAS_OP_N, CUBLAS_OP_N, (int)(nx * ny), (int)nz, (int)nz, &one, in,
-                                    CUDA_R_32F, (int)(nx * ny), n, Sa, CUDA_R_32F, (int)nz, 0, &zero, out,
-                                    CUDA_R_32F, (int)(nx * ny), n, (int)C, pp.ct, CUBLAS_GEMM_DEFAULT);
+  int* status = pp.status.as<int>();
+  if (a == 0) {  // out[l nx + i] = sum_x in[l nx + x] S_x[i + x nx] over the n / nx * C lines l
+    const int64_t L = n / nx * C;
+    if (L > (int64_t)65535 * 128) return cudaErrorInvalidValue;
+    return gemm_split_tc(s, 3, nullptr, 0, status, (int)L, (int)nx, (int)nx, in, kMlpF32, nx, 1, 0, Sa,
+                         kMlpF32, nx, 1, 0, out, nx, 0, 1, 0, nullptr, nullptr);
+  }
+  if (a == 1)  // per x-y slab b: out_b[y' nx + x] = sum_y S_y[y + y' ny] in_b[y nx + x]
+    return gemm_split_tc(s, 3, nullptr, 0, status, (int)ny, (int)nx, (int)ny, Sa, kMlpF32, ny, 1, 0, in,
+                         kMlpF32, nx, 1, nxy, out, nx, nxy, (int)(nz * C), 0, nullptr, nullptr);
+  // per column c: out_c[z' nxy + xy] = sum_z S_z[z + z' nz] in_c[z nxy + xy]
+  return gemm_split_tc(s, 3, nullptr, 0, status, (int)nz, (int)nxy, (int)nz, Sa, kMlpF32, nz, 1, 0, in,
+                       kMlpF32, nxy, 1, n, out, nxy, n, (int)C, 0, nullptr, nullptr);
 }
 
 template <typename T, typename TL>
@@ -1819,11 +1811,10 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
     if (e == cudaSuccess) e = pp.coef.alloc((size_t)B * 4 * sizeof(double));
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(pp.coef.p, pc->coef, (size_t)B * 4 * sizeof(double), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = pp.ws.alloc((size_t)32 << 20);
+    if (e == cudaSuccess) e = pp.status.alloc(sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(pp.status.p, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = gemm_f32_tc_prepare();  // before the iteration is captured
     if (e != cudaSuccess) return cuda_fail(e, "krylov: preconditioner buffers");
-    if (cublasCreate(&pp.h) != CUBLAS_STATUS_SUCCESS || cublasSetStream(pp.h, s) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetWorkspace(pp.h, pp.ws.p, (size_t)32 << 20) != CUBLAS_STATUS_SUCCESS)
-      return fail_off(SAS_ECUDA, "krylov: cuBLAS handle");
   }
   double pc_scale = 1.0;
   for (int a = 0; a < pp.ndim; ++a) pc_scale *= 2.0 / (double)(pp.N[a] + 1);
@@ -1833,7 +1824,7 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
     float* oth = pp.W.as<float>();
     for (int pass = 0; pass < 2; ++pass) {
       for (int a = 0; a < pp.ndim; ++a) {
-        if (dst_axis(pp, a, Cpl, cur, oth) != CUBLAS_STATUS_SUCCESS) return false;
+        if (dst_axis(pp, a, Cpl, cur, oth, s) != cudaSuccess) return false;
         std::swap(cur, oth);
       }
       if (pass == 0)
@@ -1866,11 +1857,7 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   if (bicg) {
     // the first iteration starts from r (restart flag set by bicg_replace_kernel)
   } else if (poisson) {
-    // the emulated-float32 tensor-core GEMM where the library has it, plain float32 otherwise
-    if (!precondition()) {
-      pp.ct = CUBLAS_COMPUTE_32F;
-      if (!precondition()) return fail_off(SAS_ECUDA, "krylov: preconditioner GEMM failed");
-    }
+    if (!precondition()) return fail_off(SAS_ECUDA, "krylov: preconditioner GEMM failed");
     off::rz_kernel<T><<<B, kThreads, 0, s>>>(prz.as<T>(), G, 1, st.as<Col<T>>());
     off::direction_z_kernel<T, TL><<<qgrid, kThreads, 0, s>>>(n, B, Q.as<TL>(), P.as<TL>(), st.as<Col<T>>(), rpc);
   } else {
@@ -1980,8 +1967,12 @@ sas_status krylov_t(const sas_affine_desc* d, const double* params, int32_t B, T
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(prr_h.data(), prr.p, prr_h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  int tstat = 0;
+  if (e == cudaSuccess && poisson)
+    e = cudaMemcpyAsync(&tstat, pp.status.p, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "krylov: final residual");
+  if (tstat != 0) return fail_off(SAS_ETIMEOUT, "krylov: a preconditioner transform timed out");
   int failed = 0, broke = 0, stalled = 0;
   for (int b = 0; b < B; ++b) {
     double rr = 0.0;
