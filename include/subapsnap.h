@@ -374,6 +374,31 @@ sas_status subapsnap_krylov_affine_ex(const sas_affine_desc* desc, const double*
                                       const sas_krylov_precond* precond, int32_t* iters_out,
                                       double* relres_out);
 
+/* Snapshots of the Gaussian-kernel family (Alg. 1 step 1 for Sec. 5.3): the
+ * solutions x of (K_sigma + lambda I) x = b on the grid of nsigma sigma values
+ * times nlambda lambda values, by multishift conjugate gradients: for each
+ * sigma one CG on the smallest lambda, every other lambda from the shifted
+ * recurrences of the same Krylov space (one kernel product per sigma and
+ * iteration for all lambda).  All sigma advance together.  A system stops once
+ * its recurrence residual is at most tol ||b||.  float64 throughout: distances
+ * from direct coordinate differences, entries by exp.
+ *  desc:   X (device N x d), n, d and b (device N) are used; S, J, r, s, mode
+ *          are ignored.
+ *  sigma:  host, nsigma values > 0 (1 <= nsigma <= 16).
+ *  lambda: host, nlambda values > 0 (1 <= nlambda <= 32).
+ *  X_out:  device, N x (nsigma nlambda) column-major (ld ldx >= N); column
+ *          a nlambda + b solves (sigma_a, lambda_b).
+ *  iters_out (host or NULL): iterations per system; relres_out (host or
+ *  NULL): true float64 residuals ||(K + lambda I) x - b|| / ||b||.
+ * Allocates device work space (about N (nsigma nlambda + 2 nsigma + 32)
+ * doubles).  Synchronous on `stream`.  Errors: SAS_EINVAL, SAS_ENOMEM,
+ * SAS_ECUDA, SAS_ENOCONV (a system did not reach tol within maxit iterations
+ * or broke down; X_out holds the last iterates). */
+sas_status subapsnap_krr_snapshots(const sas_kernel_desc* desc, const double* sigma, int32_t nsigma,
+                                   const double* lambda, int32_t nlambda, double tol, int32_t maxit,
+                                   double* X_out, int64_t ldx, int32_t* iters_out, double* relres_out,
+                                   void* stream);
+
 /* Thin QR X = Q R of a tall n x r matrix on the device by TSQR (Alg. 1 step
  * 2: an orthonormal basis Q of the snapshots' range): Householder QR of row
  * panels in shared memory and of stacks of their R factors up a reduction

@@ -39,6 +39,7 @@ EXPORTED = [
     "subapsnap_select_rows_union_affine", "subapsnap_nearest_points", "subapsnap_krylov_affine",
     "subapsnap_tsqr", "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex",
     "subapsnap_output_row_bytes", "subapsnap_surrogate_set_anchors", "subapsnap_surrogate_reset",
+    "subapsnap_krr_snapshots",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
@@ -123,6 +124,8 @@ def lib() -> ctypes.CDLL:
         L.subapsnap_surrogate_grad.argtypes = [vp, vp, vp, i64, dp_, fp_]
         L.subapsnap_surrogate_set_anchors.argtypes = [vp, vp, vp, i64]
         L.subapsnap_surrogate_reset.argtypes = [vp]
+        L.subapsnap_krr_snapshots.argtypes = [ctypes.POINTER(KernelDesc), dp_, i32, dp_, i32, ctypes.c_double,
+                                              i32, vp, i64, ctypes.POINTER(ctypes.c_int32), dp_, vp]
         L.subapsnap_multi_plan_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp), i64p,
                                                   i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                   ctypes.POINTER(vp), ctypes.POINTER(vp)]
@@ -163,7 +166,8 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_sample_rows_leverage", "subapsnap_select_rows_union_affine",
                      "subapsnap_nearest_points", "subapsnap_krylov_affine", "subapsnap_tsqr",
                      "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex",
-                     "subapsnap_surrogate_set_anchors", "subapsnap_surrogate_reset"):
+                     "subapsnap_surrogate_set_anchors", "subapsnap_surrogate_reset",
+                     "subapsnap_krr_snapshots"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -391,6 +395,29 @@ def subapsnap_krylov_affine(desc: AffineDesc, params, X, warm: bool = False, tol
     if not (allow_noconv and code == SAS_ENOCONV):
         _check(code)
     return it, rel
+
+
+def subapsnap_krr_snapshots(X, b, sigma, lam, Xout, tol: float = 1e-10, maxit: int = 10000, stream=None):
+    """Kernel-ridge snapshots by multishift CG: X (N, d) and b (N,) float64 CUDA tensors, sigma and
+    lam host sequences; Xout a float64 CUDA tensor of shape (len(sigma) * len(lam), N) whose row
+    a * len(lam) + b receives the solution for (sigma[a], lam[b]).  Returns (iterations, true
+    relative residuals) as numpy arrays."""
+    import torch
+    N, d = int(X.shape[0]), int(X.shape[1])
+    sig = np.ascontiguousarray(sigma, dtype=np.float64)
+    lm = np.ascontiguousarray(lam, dtype=np.float64)
+    nc = len(sig) * len(lm)
+    if tuple(Xout.shape) != (nc, N) or Xout.dtype != torch.float64 or not Xout.is_contiguous():
+        raise ValueError(f"Xout must be a contiguous float64 tensor of shape ({nc}, {N})")
+    desc = KernelDesc(n=N, d=d, r=0, s=0, mode=0, X=_ptr(X), S=None, ldS=0, J=None, b=_ptr(b))
+    its = np.zeros(nc, dtype=np.int32)
+    res = np.zeros(nc, dtype=np.float64)
+    _check(lib().subapsnap_krr_snapshots(
+        ctypes.byref(desc), sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(sig),
+        lm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(lm), float(tol), int(maxit), _ptr(Xout), N,
+        its.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), res.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        _stream(stream)))
+    return its, res
 
 
 def subapsnap_tsqr(X, Q=None, complex_valued: bool | None = None) -> np.ndarray:

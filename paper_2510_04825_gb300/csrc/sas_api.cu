@@ -11,6 +11,8 @@
 #include <unordered_set>
 #include <vector>
 
+#include <cmath>
+
 #include "sas_internal.cuh"
 
 namespace sas {
@@ -800,6 +802,25 @@ sas_status subapsnap_select_rows_kernel(const sas_kernel_desc* d, const double* 
   if (!is_device_ptr(d->X) || !is_device_ptr(d->S)) return fail(SAS_EINVAL, "X and S must be device pointers");
   if (!(p_sel[0] > 0.0)) return fail(SAS_EINVAL, "sigma must be positive");
   return select_rows_kernel(d, p_sel, J_out, gap_out);
+}
+
+sas_status subapsnap_krr_snapshots(const sas_kernel_desc* d, const double* sigma, int32_t ns,
+                                   const double* lambda, int32_t nl, double tol, int32_t maxit, double* X,
+                                   int64_t ldx, int32_t* iters_out, double* relres_out, void* stream) {
+  if (!d || !sigma || !lambda || !X) return fail(SAS_EINVAL, "NULL argument");
+  if (d->n < 1 || d->d < 1 || d->d > 16) return fail(SAS_EINVAL, "need n >= 1 and 1 <= d <= 16");
+  if (!is_device_ptr(d->X) || !is_device_ptr(d->b) || !is_device_ptr(X))
+    return fail(SAS_EINVAL, "X, b and X_out must be device pointers");
+  if (ns < 1 || ns > 16 || nl < 1 || nl > 32) return fail(SAS_EINVAL, "need 1 <= nsigma <= 16, 1 <= nlambda <= 32");
+  if (ldx < d->n) return fail(SAS_EINVAL, "ldx < N");
+  if (!(tol > 0.0) || maxit < 1) return fail(SAS_EINVAL, "need tol > 0 and maxit >= 1");
+  for (int i = 0; i < ns; ++i)
+    if (!(sigma[i] > 0.0) || !std::isfinite(sigma[i])) return fail(SAS_EINVAL, "sigma must be positive and finite");
+  for (int i = 0; i < nl; ++i)
+    if (!(lambda[i] > 0.0) || !std::isfinite(lambda[i]))
+      return fail(SAS_EINVAL, "lambda must be positive and finite");
+  return krr_snapshots(d, sigma, ns, lambda, nl, tol, maxit, X, ldx, iters_out, relres_out,
+                       (cudaStream_t)stream);
 }
 
 sas_status subapsnap_surrogate_train(sas_ctx* c, const double* P, const double* Y, int64_t ntrain,

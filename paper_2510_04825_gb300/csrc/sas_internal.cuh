@@ -313,6 +313,10 @@ sas_status surrogate_solve(sas_ctx* c, const double* params, int64_t m, int32_t 
                            uint32_t* flags, double* rho_out, double tol, int64_t* accepted,
                            cudaStream_t st);
 sas_status surrogate_set_anchors(sas_ctx* c, const double* P, const double* Y, int64_t n);
+// kernel-ridge snapshots by multishift CG (sas_krr_snap.cu)
+sas_status krr_snapshots(const sas_kernel_desc* d, const double* sigma, int32_t ns, const double* lambda,
+                         int32_t nl, double tol, int32_t maxit, double* Xout, int64_t ldx, int32_t* iters_out,
+                         double* relres_out, cudaStream_t st);
 // tensor-core GEMM with bfloat16-split operands (sas_mlp_tc.cu): operand types of A and B
 enum { kMlpF32 = 0, kMlpBF16 = 1 };
 cudaError_t mlp_gemm_tc(cudaStream_t st, float* part, int64_t part_cap, int* status, int M, int N,
