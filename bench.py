@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 GRID = 1024
 R, S_ROWS, M = 60, 120, 4096
 E2E_CHUNK = 512  # x_hat leaves the device in chunks of 512 parameters
-TC_VERSION = "x64-digits-v1"
+TC_VERSION = "x64-digits-v2"
 METRIC = "new-p solves/sec on 1 GB300 at stated rel. residual (chosen vs plain FP64)"
 WORKLOAD = "diffusion_2d_1024x1024_r60_s120_m4096"
 
