@@ -145,6 +145,19 @@ typedef struct {
   const double* b;      /* device, N targets */
 } sas_kernel_desc;
 
+/* One shard of the points of a Gaussian-kernel problem (the data-parallel
+ * split of Sec. 5.3's rows over N for several GPUs): base.X and base.S hold
+ * this shard's N_g points and rows of S (base.n = N_g; base.J and base.b are
+ * ignored), and the subsample's rows come from the caller, so that every shard
+ * uses the same J of the full problem. */
+typedef struct {
+  sas_kernel_desc base;
+  const double* XJ;  /* device, s x d row-major: coordinates of the points at J */
+  const double* SJ;  /* device, s x r column-major (ld s): S's rows at J on ONE shard, zeros on
+                        the others, so that the lambda S_J term enters the sum once */
+  const double* bJ;  /* device, s: b at J */
+} sas_kernel_shard_desc;
+
 /* Build a context for the affine family: gathers b_J, precomputes the blocks
  * G_k = (A_k)_{J,:} S (s x r each) so that M(p) = sum_k theta_k(p) G_k costs
  * O(K s r) per parameter (Sec. 3.1, "Computing S A(p*) X"; Sec. 5.2.2), and
@@ -157,6 +170,31 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* desc, sas_ctx** out);
  * gathers X_J, S_J and b_J.  The rows K_sigma(X_J, X) are formed on the fly
  * in every solve.  Synchronous.  Errors as subapsnap_setup_affine. */
 sas_status subapsnap_setup_kernel(const sas_kernel_desc* desc, sas_ctx** out);
+
+/* Context over one point shard (see sas_kernel_shard_desc).  Its rows are
+ * partial: subapsnap_kernel_rows gives M_g = K_sigma(X_J, X_g) S_g + lambda
+ * S_J^(g); the caller sums them over the shards (one all-reduce of m x s x r
+ * doubles) and solves with subapsnap_solve_batch_rows.  subapsnap_solve_batch
+ * refuses a shard context (SAS_ENOTSUP).  Not in the paper.  Synchronous.
+ * Errors as subapsnap_setup_kernel. */
+sas_status subapsnap_setup_kernel_shard(const sas_kernel_shard_desc* desc, sas_ctx** out);
+
+/* Kernel rows of a Gaussian-kernel context (Sec. 5.3, Sec. 3.1's rows at J):
+ * M_q = K_sigma(X_J, X) S + lambda S_J for m parameters (sigma, lambda), by
+ * the context's assembly (float64 in the plain form, the tensor-core rows in
+ * the mixed form).  M: device, m x (s x r) doubles, each parameter's block
+ * column-major with ld s.  Asynchronous on `stream`.  Errors: SAS_EINVAL,
+ * SAS_ENOTSUP (not a kernel context), SAS_ECUDA. */
+sas_status subapsnap_kernel_rows(sas_ctx* ctx, const double* params, int64_t m, double* M,
+                                 void* stream);
+
+/* Least squares min ||M_q y - b_J|| from given rows (Alg. 1 step 4), e.g. the
+ * shard sums of subapsnap_kernel_rows: the context's solver (plain float64
+ * Householder, or the mixed form with float64 refinement against M).  Y:
+ * device m x r; flags, rho as in subapsnap_solve_batch.  Asynchronous.
+ * Errors: SAS_EINVAL, SAS_ENOTSUP (not a kernel context), SAS_ECUDA. */
+sas_status subapsnap_solve_batch_rows(sas_ctx* ctx, const double* params, int64_t m, const double* M,
+                                      double* Y, uint32_t* flags, double* rho, void* stream);
 
 /* Solve m new parameters (Alg. 1 step 4).
  *  params: device, m x dp row-major doubles (dp from the family).

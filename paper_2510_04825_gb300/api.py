@@ -39,7 +39,8 @@ EXPORTED = [
     "subapsnap_select_rows_union_affine", "subapsnap_nearest_points", "subapsnap_krylov_affine",
     "subapsnap_tsqr", "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex",
     "subapsnap_output_row_bytes", "subapsnap_surrogate_set_anchors", "subapsnap_surrogate_reset",
-    "subapsnap_krr_snapshots",
+    "subapsnap_krr_snapshots", "subapsnap_setup_kernel_shard", "subapsnap_kernel_rows",
+    "subapsnap_solve_batch_rows",
 ]
 SAS_FLAG_SURROGATE, SAS_FLAG_FALLBACK = 8, 16
 SAS_KERNEL_SURROGATE = 4
@@ -84,6 +85,11 @@ class KernelDesc(ctypes.Structure):
     ]
 
 
+class KernelShardDesc(ctypes.Structure):
+    _fields_ = [("base", KernelDesc), ("XJ", ctypes.c_void_p), ("SJ", ctypes.c_void_p),
+                ("bJ", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -98,6 +104,9 @@ def lib() -> ctypes.CDLL:
         vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
         L.subapsnap_setup_affine.argtypes = [ctypes.POINTER(AffineDesc), ctypes.POINTER(vp)]
         L.subapsnap_setup_kernel.argtypes = [ctypes.POINTER(KernelDesc), ctypes.POINTER(vp)]
+        L.subapsnap_setup_kernel_shard.argtypes = [ctypes.POINTER(KernelShardDesc), ctypes.POINTER(vp)]
+        L.subapsnap_kernel_rows.argtypes = [vp, vp, i64, vp, vp]
+        L.subapsnap_solve_batch_rows.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
         L.subapsnap_solve_batch.argtypes = [vp, vp, i64, i32, vp, vp, vp, vp]
         L.subapsnap_residual.argtypes = [vp, vp, i64, vp, vp, vp]
         L.subapsnap_true_residual.argtypes = [vp, vp, i64, vp, vp, vp]
@@ -167,7 +176,8 @@ def lib() -> ctypes.CDLL:
                      "subapsnap_nearest_points", "subapsnap_krylov_affine", "subapsnap_tsqr",
                      "subapsnap_solve_batch_host", "subapsnap_krylov_affine_ex",
                      "subapsnap_surrogate_set_anchors", "subapsnap_surrogate_reset",
-                     "subapsnap_krr_snapshots"):
+                     "subapsnap_krr_snapshots", "subapsnap_setup_kernel_shard",
+                     "subapsnap_kernel_rows", "subapsnap_solve_batch_rows"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -247,6 +257,22 @@ def subapsnap_setup_kernel(desc: KernelDesc) -> ctypes.c_void_p:
     ctx = ctypes.c_void_p()
     _check(lib().subapsnap_setup_kernel(ctypes.byref(desc), ctypes.byref(ctx)))
     return ctx
+
+
+def subapsnap_setup_kernel_shard(desc: KernelShardDesc) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(lib().subapsnap_setup_kernel_shard(ctypes.byref(desc), ctypes.byref(ctx)))
+    return ctx
+
+
+def subapsnap_kernel_rows(ctx, params, m: int, M, stream=None):
+    """M (device, m x s x r doubles; each parameter's block column-major) = the context's rows."""
+    _check(lib().subapsnap_kernel_rows(ctx, _ptr(params), int(m), _ptr(M), _stream(stream)))
+
+
+def subapsnap_solve_batch_rows(ctx, params, m: int, M, Y, flags=None, rho=None, stream=None):
+    _check(lib().subapsnap_solve_batch_rows(ctx, _ptr(params), int(m), _ptr(M), _ptr(Y), _ptr(flags),
+                                            _ptr(rho), _stream(stream)))
 
 
 def subapsnap_select_rows_affine(desc: AffineDesc, p_sel, s: int):

@@ -350,21 +350,32 @@ sas_status subapsnap_setup_affine(const sas_affine_desc* d, sas_ctx** out) {
   return SAS_OK;
 }
 
-sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
+// Kernel-family context.  ext == NULL: the rows at J are gathered from X, S and b.  ext != NULL
+// (a point shard): X and S hold this shard's points only, and the rows X_J, S_J, b_J come from
+// the caller (device arrays, copied).
+static sas_status setup_kernel_impl(const sas_kernel_desc* d, const sas_kernel_shard_desc* ext,
+                                    sas_ctx** out) {
   if (!out) return fail(SAS_EINVAL, "out is NULL");
   *out = nullptr;
   if (!d) return fail(SAS_EINVAL, "descriptor is NULL");
   if (d->n < 1) return fail(SAS_EINVAL, "n must be positive");
   if (d->d < 1 || d->d > 16) return fail(SAS_EINVAL, "d must be in [1, 16]");
   if (d->r < 1 || d->r > kMaxR) return fail(SAS_EINVAL, "r must be in [1, 128]");
-  if (d->s < d->r || d->s > kMaxS || (int64_t)d->s > d->n)
+  if (d->s < d->r || d->s > kMaxS || (!ext && (int64_t)d->s > d->n))
     return fail(SAS_EINVAL, "need r <= s <= min(n, 512)");
   if (d->mode != SAS_MODE_PLAIN && d->mode != SAS_MODE_MIXED) return fail(SAS_EINVAL, "bad mode");
   if (d->ldS < d->n) return fail(SAS_EINVAL, "ldS < n");
-  if (!is_device_ptr(d->X) || !is_device_ptr(d->S) || !is_device_ptr(d->b))
-    return fail(SAS_EINVAL, "X, S and b must be device pointers");
-  sas_status st = check_J(d->J, d->s, d->n);
-  if (st != SAS_OK) return st;
+  if (!is_device_ptr(d->X) || !is_device_ptr(d->S))
+    return fail(SAS_EINVAL, "X and S must be device pointers");
+  sas_status st = SAS_OK;
+  if (ext) {
+    if (!is_device_ptr(ext->XJ) || !is_device_ptr(ext->SJ) || !is_device_ptr(ext->bJ))
+      return fail(SAS_EINVAL, "XJ, SJ and bJ must be device pointers");
+  } else {
+    if (!is_device_ptr(d->b)) return fail(SAS_EINVAL, "b must be a device pointer");
+    st = check_J(d->J, d->s, d->n);
+    if (st != SAS_OK) return st;
+  }
   sas_ctx* c = new (std::nothrow) sas_ctx();
   if (!c) return fail(SAS_ENOMEM, "host allocation failed");
   std::memset((void*)c, 0, sizeof(sas_ctx));
@@ -404,8 +415,6 @@ sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
     }                                        \
   } while (0)
   TRYK(cudaStreamCreateWithFlags(&sst, cudaStreamNonBlocking));
-  TRYK(dmalloc(&c->J_dev, sizeof(int64_t) * d->s));
-  TRYK(cudaMemcpy(c->J_dev, d->J, sizeof(int64_t) * d->s, cudaMemcpyHostToDevice));
   TRYK(dmalloc(&c->XJ, sizeof(double) * d->s * d->d));
   TRYK(dmalloc(&c->SJ, sizeof(double) * d->s * d->r));
   TRYK(cudaMalloc(&c->bJ, sizeof(double) * d->s));
@@ -413,7 +422,16 @@ sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
   TRYK(cudaMemset(c->wq, 0, sizeof(double) * d->r));
   TRYK(dmalloc(&c->dev_status, sizeof(int)));
   TRYK(cudaMemset(c->dev_status, 0, sizeof(int)));
-  TRYK(launch_gather_kernel_rows(c, sst));
+  if (ext) {
+    c->kernel_shard = 1;
+    TRYK(cudaMemcpy(c->XJ, ext->XJ, sizeof(double) * d->s * d->d, cudaMemcpyDeviceToDevice));
+    TRYK(cudaMemcpy(c->SJ, ext->SJ, sizeof(double) * d->s * d->r, cudaMemcpyDeviceToDevice));
+    TRYK(cudaMemcpy(c->bJ, ext->bJ, sizeof(double) * d->s, cudaMemcpyDeviceToDevice));
+  } else {
+    TRYK(dmalloc(&c->J_dev, sizeof(int64_t) * d->s));
+    TRYK(cudaMemcpy(c->J_dev, d->J, sizeof(int64_t) * d->s, cudaMemcpyHostToDevice));
+    TRYK(launch_gather_kernel_rows(c, sst));
+  }
   if (d->mode == SAS_MODE_MIXED) {
     TRYK(cudaMalloc(&c->bJ32, sizeof(float) * d->s));
     const int rpad = (d->r + 31) / 32 * 32;
@@ -448,6 +466,18 @@ sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
 #undef TRYK
   *out = c;
   return SAS_OK;
+}
+
+sas_status subapsnap_setup_kernel(const sas_kernel_desc* d, sas_ctx** out) {
+  return setup_kernel_impl(d, nullptr, out);
+}
+
+sas_status subapsnap_setup_kernel_shard(const sas_kernel_shard_desc* d, sas_ctx** out) {
+  if (!d) {
+    if (out) *out = nullptr;
+    return fail(SAS_EINVAL, "descriptor is NULL");
+  }
+  return setup_kernel_impl(&d->base, d, out);
 }
 
 namespace sas {
@@ -519,9 +549,52 @@ static sas_status solve_kernel_family(sas_ctx* c, const double* params, int64_t 
 }
 }  // namespace sas
 
+sas_status subapsnap_kernel_rows(sas_ctx* c, const double* params, int64_t m, double* M, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (c->family != kKernel) return fail(SAS_ENOTSUP, "kernel rows need a Gaussian-kernel context");
+  if (m < 0) return fail(SAS_EINVAL, "m < 0");
+  if (m == 0) return SAS_OK;
+  if (!params || !M) return fail(SAS_EINVAL, "params and M must be non-NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool mixed = c->mode == SAS_MODE_MIXED;
+  const bool tc_rows = mixed && c->krr_kernel != 1 && krr_tc_supported(c);
+  if (mixed && c->krr_kernel == 2 && !tc_rows)
+    return fail(SAS_ENOTSUP, "tensor-core kernel rows are not available for this context");
+  const int64_t sub = tc_rows ? kKernelSubBatchTc : kKernelSubBatch;
+  cudaError_t e = cudaSuccess;
+  for (int64_t b0 = 0; b0 < m && e == cudaSuccess; b0 += sub) {
+    const int64_t mb = m - b0 < sub ? m - b0 : sub;
+    double* Mb = M + b0 * (int64_t)c->s * c->r;
+    TraceScope ts(c, SAS_KERNEL_ASSEMBLE, st);
+    e = tc_rows ? launch_krr_assemble_tc(c, params + b0 * 2, mb, Mb, st)
+                : launch_krr_assemble(c, params + b0 * 2, mb, Mb, mixed, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "kernel_rows");
+  return SAS_OK;
+}
+
+sas_status subapsnap_solve_batch_rows(sas_ctx* c, const double* params, int64_t m, const double* M,
+                                      double* Y, uint32_t* flags, double* rho, void* stream) {
+  if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (c->family != kKernel) return fail(SAS_ENOTSUP, "solve from rows needs a Gaussian-kernel context");
+  if (m < 0) return fail(SAS_EINVAL, "m < 0");
+  if (m == 0) return SAS_OK;
+  if (!params || !M || !Y) return fail(SAS_EINVAL, "params, M and Y must be non-NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  TraceScope ts(c, SAS_KERNEL_LS, st);
+  const cudaError_t e = c->mode == SAS_MODE_MIXED
+                            ? launch_ls_mixed(c, params, m, Y, nullptr, nullptr, flags, rho, st, M)
+                            : launch_ls_plain(c, params, m, Y, nullptr, flags, rho, st, M);
+  if (e != cudaSuccess) return cuda_fail(e, "solve_batch_rows");
+  return SAS_OK;
+}
+
 sas_status subapsnap_solve_batch(sas_ctx* c, const double* params, int64_t m, int32_t out_kind,
                                  void* out, uint32_t* flags, double* rho, void* stream) {
   if (!c) return fail(SAS_EINVAL, "context is NULL");
+  if (c->kernel_shard)
+    return fail(SAS_ENOTSUP, "a point-shard context forms partial rows only: sum them over the shards "
+                             "and call subapsnap_solve_batch_rows");
   if (m < 0) return fail(SAS_EINVAL, "m < 0");
   if (m == 0) return SAS_OK;
   if (!params || !out) return fail(SAS_EINVAL, "params and out must be non-NULL");

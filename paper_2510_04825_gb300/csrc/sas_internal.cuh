@@ -202,6 +202,7 @@ struct sas_ctx {
   int recon_kernel;    // 0 auto, 1 CUDA cores, 2-4 tensor cores tf32, 5 tensor cores f16
   int xhat_f32;        // mixed form: 1 = x_hat in float32 (tf32 x 3), 0 = float64-accurate
   int surr_f32_out;    // surrogate: 1 = output layer with float32 weights (hi + lo bfloat16)
+  int kernel_shard;    // kernel family: 1 = this context holds one shard of the points
   double* surr_aP;     // surrogate anchors for the next training (device, surr_na x dp)
   double* surr_aY;     // and their coefficient vectors (device, surr_na x r)
   int64_t surr_na;

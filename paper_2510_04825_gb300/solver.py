@@ -280,6 +280,71 @@ class KernelSolver:
         api.subapsnap_residual(self.ctx, params, params.shape[0], Y, rho, stream)
 
 
+def point_shard(n, rank, world):
+    """Contiguous block of the n points that rank owns (blocks differ by at most one)."""
+    base, extra = divmod(int(n), int(world))
+    lo = rank * base + min(rank, extra)
+    return slice(lo, lo + base + (1 if rank < extra else 0))
+
+
+def allreduce_rows(M, dist_mod):
+    """Sum the shards' partial kernel rows in place: the one exchange of the point split."""
+    if dist_mod is not None and dist_mod.get_world_size() > 1:
+        dist_mod.all_reduce(M, op=dist_mod.ReduceOp.SUM)
+    return M
+
+
+class KernelShard:
+    """One shard of the points of a Gaussian-kernel problem: its context forms the partial rows
+    M_g = K_sigma(X_J, X_g) S_g (+ lambda S_J on the shard that owns it); the sum over the shards
+    is the full M, which any shard's context then solves."""
+
+    def __init__(self, X, S, XJ, SJ, bJ, shard, r, s, mode=api.SAS_MODE_PLAIN, owns_lambda=False):
+        n_all = X.shape[0]
+        self.X = X[shard].contiguous()
+        self.S = S  # (r, N) row-major: the shard's rows start at shard.start with ldS = N
+        self.SJ = SJ if owns_lambda else torch.zeros_like(SJ)
+        self.XJ, self.bJ = XJ, bJ
+        ng = shard.stop - shard.start
+        base = api.KernelDesc()
+        base.n, base.d, base.r, base.s, base.mode = int(ng), int(X.shape[1]), int(r), int(s), mode
+        base.X = api._ptr(self.X)
+        base.S = S.data_ptr() + 8 * shard.start
+        base.ldS = int(n_all)
+        base.J = None
+        base.b = None
+        self.desc = api.KernelShardDesc(base=base, XJ=api._ptr(self.XJ), SJ=api._ptr(self.SJ),
+                                        bJ=api._ptr(self.bJ))
+        self.r, self.s = r, s
+        self.ctx = api.subapsnap_setup_kernel_shard(self.desc)
+
+    @classmethod
+    def from_full(cls, X, S, b, J, rank, world, r, mode=api.SAS_MODE_PLAIN):
+        Jd = torch.as_tensor(np.asarray(J, dtype=np.int64), device=X.device)
+        XJ = X.index_select(0, Jd).contiguous()
+        SJ = S.index_select(1, Jd).contiguous()  # (r, s): column-major s x r with ld s
+        bJ = b.index_select(0, Jd).contiguous()
+        return cls(X, S, XJ, SJ, bJ, point_shard(X.shape[0], rank, world), r, len(J), mode,
+                   owns_lambda=rank == 0)
+
+    def rows(self, params, M, stream=None):
+        api.subapsnap_kernel_rows(self.ctx, params, params.shape[0], M, stream)
+
+    def solve_rows(self, params, M, Y, flags=None, rho=None, stream=None):
+        api.subapsnap_solve_batch_rows(self.ctx, params, params.shape[0], M, Y, flags, rho, stream)
+
+    def close(self):
+        if self.ctx is not None:
+            api.subapsnap_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def select_rows_kernel(prob, X_device, S_device, p_sel, s):
     """CPQR-in-rounds row selection for the Gaussian-kernel family; (J, gaps) on the host."""
     J0 = np.arange(s, dtype=np.int64)
