@@ -71,6 +71,15 @@ def test_argument_checks_without_device(lib):
     cnt = ctypes.c_int32()
     assert lib.subapsnap_select_rows_union_affine(None, None, 1, 1, None, ctypes.byref(cnt)) == api.SAS_EINVAL
     assert lib.subapsnap_nearest_points(x.ctypes.data, 2, 0, x.ctypes.data, 1, x.ctypes.data) == api.SAS_EINVAL
+    # entry points of the kernel-ridge snapshots, the point shards and the surrogate
+    assert lib.subapsnap_krr_snapshots(None, None, 1, None, 1, 1e-8, 10, None, 1, None, None,
+                                       None) == api.SAS_EINVAL
+    assert lib.subapsnap_setup_kernel_shard(None, ctypes.byref(ctx)) == api.SAS_EINVAL
+    assert lib.subapsnap_kernel_rows(None, None, 1, None, None) == api.SAS_EINVAL
+    assert lib.subapsnap_solve_batch_rows(None, None, 1, None, None, None, None, None) == api.SAS_EINVAL
+    assert lib.subapsnap_surrogate_set_anchors(None, None, None, 0) == api.SAS_EINVAL
+    assert lib.subapsnap_surrogate_reset(None) == api.SAS_EINVAL
+    assert lib.subapsnap_set_option(None, api.SAS_OPT_SURROGATE_F32_OUT, 1.0) == api.SAS_EINVAL
 
 
 def test_product_path_has_no_oracle_import():
