@@ -15,15 +15,16 @@
 // Epilogues: 0 = store C; 1 = Z = C + bias and H = gelu(Z) (exact erf form); 2 = C + bias;
 // 3 = gelu(C + bias) only (inference, where Z is not needed).
 //
-// Structure: one CTA of 256 threads per 128 x BN tile of C (BN = 16 .. 256) and K range
-// (split-K for the surrogate's weight gradients, whose K is the batch) or batch entry: K in
-// blocks of 64 (128-byte K-major rows, 128-byte swizzle), two shared-memory stages.  All
-// threads load, split and store a K block; one elected thread issues its MMAs (K = 16 each)
-// and commits them to the stage's mbarrier, which the threads wait on before they overwrite
-// that stage.  Eight warps drain TMEM (warp w reads lane quarter w % 4 and half w / 4 of the
-// columns).  A split-K launch writes float32 partial tiles that a second kernel sums in a
-// fixed order.  Every wait is bounded (2 s of %globaltimer); on expiry the kernel records
-// SAS_ETIMEOUT, stops, waits (bounded) for its MMAs, frees its TMEM and returns.
+// Structure: one CTA (256 threads for two-term splits, 512 for three-term ones) per 128 x BN
+// tile of C (BN = 16 .. 256) and K range (split-K for the surrogate's weight gradients, whose K
+// is the batch) or batch entry: K in blocks of 64 (128-byte K-major rows, 128-byte swizzle),
+// two shared-memory stages.  All threads load, split and store a K block; one elected thread
+// issues its MMAs (K = 16 each) and commits them to the stage's mbarrier, which the threads
+// wait on before they overwrite that stage.  The warps drain TMEM: warp w reads lane quarter
+// w % 4 and every (threads / 128)-th 16-column chunk from chunk w / 4.  A split-K launch writes
+// float32 partial tiles that a second kernel sums in a fixed order.  Every wait is bounded (2 s
+// of %globaltimer); on expiry the kernel records SAS_ETIMEOUT, stops, waits (bounded) for its
+// MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -37,7 +38,9 @@ namespace mlptc {
 
 using namespace tc;
 
-constexpr int kThreads = 256;
+// threads per CTA: 256 for two-term kernels (two CTAs per SM), 512 for three-term ones (one CTA
+// per SM by shared memory: twice the warps to hide the staging latency)
+__host__ __device__ constexpr int threads_for(int ns) { return ns == 3 ? 512 : 256; }
 constexpr int kBM = 128;
 constexpr int kKB = 64;  // K per block: 64 bfloat16 = one 128-byte swizzled row
 
@@ -96,11 +99,11 @@ __device__ inline uint32_t bits(__nv_bfloat162 h) { return *reinterpret_cast<con
 // Operand tile: rows x 64 (K block at k0) as NT bfloat16 term tiles (term i at tile + i *
 // tstride) in the swizzled K-major layout.  Each thread takes a (row, k, k + 1) pair; the
 // pair index runs along the operand's unit-stride direction so that loads coalesce.
-template <typename T, int NT, int ROWS>
+template <typename T, int NT, int ROWS, int NTH>
 __device__ inline void stage_tile(const T* src, int64_t lrow, int64_t lk, int row0, int nrows,
                                   int k0, int K, uint8_t* tile, uint32_t tstride) {
   const bool k_fast = lk == 1;
-  for (int idx = threadIdx.x; idx < ROWS * 32; idx += kThreads) {
+  for (int idx = threadIdx.x; idx < ROWS * 32; idx += NTH) {
     const int r = k_fast ? idx >> 5 : idx % ROWS;
     const int kp = k_fast ? idx & 31 : idx / ROWS;
     const int k = k0 + 2 * kp;
@@ -123,20 +126,20 @@ __device__ inline void stage_tile(const T* src, int64_t lrow, int64_t lk, int ro
 // before it converts and stores any of them, and writes whole swizzle units (bfloat16) or
 // 8-byte halves of them (float32 terms).  Chunks past K or past the valid rows are filled
 // element by element (zeros outside).
-template <typename T, int NT, int ROWS>
+template <typename T, int NT, int ROWS, int NTH>
 __device__ inline void stage_tile_vec(const T* src, int64_t lrow, int row0, int nrows, int k0, int K,
                                       uint8_t* tile, uint32_t tstride) {
   constexpr int kPer = 16 / sizeof(T);          // elements per 16-byte chunk
   constexpr int kChunks = kKB / kPer;           // chunks per row
-  constexpr int kIters = ROWS * kChunks / kThreads;
-  static_assert(ROWS * kChunks % kThreads == 0 || ROWS * kChunks < kThreads, "tile and block");
+  constexpr int kIters = ROWS * kChunks / NTH;
+  static_assert(ROWS * kChunks % NTH == 0 || ROWS * kChunks < NTH, "tile and block");
   constexpr int kBatch = kIters < 8 ? (kIters < 1 ? 1 : kIters) : 8;
 #pragma unroll 1
   for (int it0 = 0; it0 < (kIters < 1 ? 1 : kIters); it0 += kBatch) {
     uint4 v[kBatch];
 #pragma unroll
     for (int b = 0; b < kBatch; ++b) {
-      const int idx = threadIdx.x + (it0 + b) * kThreads;
+      const int idx = threadIdx.x + (it0 + b) * NTH;
       const int r = idx / kChunks, c = idx % kChunks;
       const int k = k0 + c * kPer;
       v[b] = make_uint4(0u, 0u, 0u, 0u);
@@ -153,7 +156,7 @@ __device__ inline void stage_tile_vec(const T* src, int64_t lrow, int row0, int 
     }
 #pragma unroll
     for (int b = 0; b < kBatch; ++b) {
-      const int idx = threadIdx.x + (it0 + b) * kThreads;
+      const int idx = threadIdx.x + (it0 + b) * NTH;
       if (idx >= ROWS * kChunks) continue;
       const int r = idx / kChunks, c = idx % kChunks;
       if (sizeof(T) == 2) {  // 8 bfloat16: one swizzle unit
@@ -177,16 +180,16 @@ __device__ inline void stage_tile_vec(const T* src, int64_t lrow, int row0, int 
 // as 8-byte row pieces of every term.  Lanes of a warp cover 8 K-quads x 4 row-quads, so that
 // each load instruction reads 64 contiguous bytes at each of 8 k and the 8-byte stores spread
 // over the banks.  Blocks that cross the valid rows or K are filled element by element.
-template <int NT, int ROWS>
+template <int NT, int ROWS, int NTH>
 __device__ inline void stage_tile_vec_t(const float* src, int64_t lk, int row0, int nrows, int k0,
                                         int K, uint8_t* tile, uint32_t tstride) {
   constexpr int kRQ = ROWS / 4;                 // row-quads
   constexpr int kRQhi = kRQ >= 4 ? kRQ / 4 : 1;  // row-quad groups of 4 per warp
   constexpr int kUnits = 16 * kRQ;              // 16 K-quads per K block
-  constexpr int kIters = (kUnits + kThreads - 1) / kThreads;
+  constexpr int kIters = (kUnits + NTH - 1) / NTH;
 #pragma unroll 1
   for (int it = 0; it < kIters; ++it) {
-    const int idx = threadIdx.x + it * kThreads;
+    const int idx = threadIdx.x + it * NTH;
     if (idx >= kUnits) break;
     const int kq_lo = idx & 7, rq_lo = kRQ >= 4 ? (idx >> 3) & 3 : (idx >> 3) % kRQ;
     const int rest = kRQ >= 4 ? idx >> 5 : (idx >> 3) / kRQ;
@@ -229,15 +232,15 @@ __device__ inline void stage_tile_vec_t(const float* src, int64_t lk, int row0, 
 // them into the NT term tiles.  Work units as in stage_tile_vec (mode 1: 4 floats of a row)
 // and stage_tile_vec_t (mode 2: a 4 x 4 block).
 constexpr int kPF = 8;
-template <int ROWS>
+template <int ROWS, int NTH>
 __device__ inline void load_vec(int mode, const float* src, int64_t lrow, int64_t lk, int row0, int nrows,
                                 int k0, int K, uint4 (&rg)[kPF]) {
   if (mode == 1) {
-    constexpr int kUnits = ROWS * 16, kIt = kUnits / kThreads > 0 ? kUnits / kThreads : 1;
+    constexpr int kUnits = ROWS * 16, kIt = kUnits / NTH > 0 ? kUnits / NTH : 1;
     static_assert(kIt <= kPF, "prefetch registers");
 #pragma unroll
     for (int i = 0; i < kIt; ++i) {
-      const int idx = threadIdx.x + i * kThreads;
+      const int idx = threadIdx.x + i * NTH;
       const int r = idx >> 4, k = k0 + 4 * (idx & 15);
       rg[i] = make_uint4(0u, 0u, 0u, 0u);
       if (idx >= kUnits || r >= nrows) continue;
@@ -254,11 +257,11 @@ __device__ inline void load_vec(int mode, const float* src, int64_t lrow, int64_
     }
   } else {
     constexpr int kRQ = ROWS / 4, kRQhi = kRQ / 4, kUnits = 16 * kRQ;
-    constexpr int kIt = (kUnits + kThreads - 1) / kThreads;
+    constexpr int kIt = (kUnits + NTH - 1) / NTH;
     static_assert(4 * kIt <= kPF && kRQ >= 4, "prefetch registers");
 #pragma unroll
     for (int i = 0; i < kIt; ++i) {
-      const int idx = threadIdx.x + i * kThreads;
+      const int idx = threadIdx.x + i * NTH;
       const int rest = idx >> 5;
       const int r = 4 * ((rest % kRQhi) * 4 + ((idx >> 3) & 3));
       const int k = k0 + 4 * ((rest / kRQhi) * 8 + (idx & 7));
@@ -282,13 +285,13 @@ __device__ inline void load_vec(int mode, const float* src, int64_t lrow, int64_
   }
 }
 
-template <int NT, int ROWS>
+template <int NT, int ROWS, int NTH>
 __device__ inline void store_vec(int mode, const uint4 (&rg)[kPF], uint8_t* tile, uint32_t tstride) {
   if (mode == 1) {
-    constexpr int kUnits = ROWS * 16, kIt = kUnits / kThreads > 0 ? kUnits / kThreads : 1;
+    constexpr int kUnits = ROWS * 16, kIt = kUnits / NTH > 0 ? kUnits / NTH : 1;
 #pragma unroll
     for (int i = 0; i < kIt; ++i) {
-      const int idx = threadIdx.x + i * kThreads;
+      const int idx = threadIdx.x + i * NTH;
       if (idx >= kUnits) continue;
       __nv_bfloat162 t01[NT], t23[NT];
       split_pair<NT>(__uint_as_float(rg[i].x), __uint_as_float(rg[i].y), t01);
@@ -300,10 +303,10 @@ __device__ inline void store_vec(int mode, const uint4 (&rg)[kPF], uint8_t* tile
     }
   } else {
     constexpr int kRQ = ROWS / 4, kRQhi = kRQ / 4, kUnits = 16 * kRQ;
-    constexpr int kIt = (kUnits + kThreads - 1) / kThreads;
+    constexpr int kIt = (kUnits + NTH - 1) / NTH;
 #pragma unroll
     for (int i = 0; i < kIt; ++i) {
-      const int idx = threadIdx.x + i * kThreads;
+      const int idx = threadIdx.x + i * NTH;
       if (idx >= kUnits) continue;
       const int rest = idx >> 5;
       const int r = 4 * ((rest % kRQhi) * 4 + ((idx >> 3) & 3));
@@ -323,16 +326,16 @@ __device__ inline void store_vec(int mode, const uint4 (&rg)[kPF], uint8_t* tile
   }
 }
 
-template <typename T, int NT, int ROWS>
+template <typename T, int NT, int ROWS, int NTH>
 __device__ inline void stage(int mode, const T* src, int64_t lrow, int64_t lk, int row0, int nrows,
                              int k0, int K, uint8_t* tile, uint32_t tstride) {
   if (mode == 1) {
-    stage_tile_vec<T, NT, ROWS>(src, lrow, row0, nrows, k0, K, tile, tstride);
+    stage_tile_vec<T, NT, ROWS, NTH>(src, lrow, row0, nrows, k0, K, tile, tstride);
   } else if (mode == 2) {
     if constexpr (std::is_same<T, float>::value)
-      stage_tile_vec_t<NT, ROWS>(src, lk, row0, nrows, k0, K, tile, tstride);
+      stage_tile_vec_t<NT, ROWS, NTH>(src, lk, row0, nrows, k0, K, tile, tstride);
   } else {
-    stage_tile<T, NT, ROWS>(src, lrow, lk, row0, nrows, k0, K, tile, tstride);
+    stage_tile<T, NT, ROWS, NTH>(src, lrow, lk, row0, nrows, k0, K, tile, tstride);
   }
 }
 
@@ -349,8 +352,9 @@ struct Shape {
 // Three-term kernels run one CTA per SM (shared memory), so they can spend registers on
 // prefetching the next K block; two-term kernels keep two CTAs per SM instead.
 template <typename TA, typename TB, int BN, int NS>
-__global__ void __launch_bounds__(kThreads, NS == 3 ? 1 : 2) gemm_bf16_kernel(GemmArgs g) {
+__global__ void __launch_bounds__(threads_for(NS), NS == 3 ? 1 : 2) gemm_bf16_kernel(GemmArgs g) {
   using S = Shape<TA, TB, BN, NS>;
+  constexpr int NTH = threads_for(NS);
   constexpr bool kPrefetch = NS == 3 && std::is_same<TA, float>::value && std::is_same<TB, float>::value;
   constexpr uint32_t kIdesc = bf16_idesc(kBM, BN);
   constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
@@ -399,8 +403,8 @@ __global__ void __launch_bounds__(kThreads, NS == 3 ? 1 : 2) gemm_bf16_kernel(Ge
   uint4 ra[kPF], rb[kPF];
   if constexpr (kPrefetch) {
     if (pf && kb0 < kb1) {
-      load_vec<kBM>(g.a_vec, reinterpret_cast<const float*>(Ab), g.lai, g.lak, m0, mv, kb0 * kKB, g.K, ra);
-      load_vec<BN>(g.b_vec, reinterpret_cast<const float*>(Bb), g.lbj, g.lbk, n0, nv, kb0 * kKB, g.K, rb);
+      load_vec<kBM, NTH>(g.a_vec, reinterpret_cast<const float*>(Ab), g.lai, g.lak, m0, mv, kb0 * kKB, g.K, ra);
+      load_vec<BN, NTH>(g.b_vec, reinterpret_cast<const float*>(Bb), g.lbj, g.lbk, n0, nv, kb0 * kKB, g.K, rb);
     }
   }
   for (int kb = kb0; kb < kb1; ++kb, ++issued) {
@@ -416,20 +420,20 @@ __global__ void __launch_bounds__(kThreads, NS == 3 ? 1 : 2) gemm_bf16_kernel(Ge
     bool staged = false;
     if constexpr (kPrefetch) {
       if (pf) {
-        store_vec<S::kNA, kBM>(g.a_vec, ra, at, S::kATile);
-        store_vec<S::kNB, BN>(g.b_vec, rb, bt, S::kBTile);
+        store_vec<S::kNA, kBM, NTH>(g.a_vec, ra, at, S::kATile);
+        store_vec<S::kNB, BN, NTH>(g.b_vec, rb, bt, S::kBTile);
         if (kb + 1 < kb1) {
-          load_vec<kBM>(g.a_vec, reinterpret_cast<const float*>(Ab), g.lai, g.lak, m0, mv, (kb + 1) * kKB, g.K,
-                        ra);
-          load_vec<BN>(g.b_vec, reinterpret_cast<const float*>(Bb), g.lbj, g.lbk, n0, nv, (kb + 1) * kKB, g.K,
-                       rb);
+          load_vec<kBM, NTH>(g.a_vec, reinterpret_cast<const float*>(Ab), g.lai, g.lak, m0, mv, (kb + 1) * kKB,
+                             g.K, ra);
+          load_vec<BN, NTH>(g.b_vec, reinterpret_cast<const float*>(Bb), g.lbj, g.lbk, n0, nv, (kb + 1) * kKB,
+                            g.K, rb);
         }
         staged = true;
       }
     }
     if (!staged) {
-      stage<TA, S::kNA, kBM>(g.a_vec, Ab, g.lai, g.lak, m0, mv, kb * kKB, g.K, at, S::kATile);
-      stage<TB, S::kNB, BN>(g.b_vec, Bb, g.lbj, g.lbk, n0, nv, kb * kKB, g.K, bt, S::kBTile);
+      stage<TA, S::kNA, kBM, NTH>(g.a_vec, Ab, g.lai, g.lak, m0, mv, kb * kKB, g.K, at, S::kATile);
+      stage<TB, S::kNB, BN, NTH>(g.b_vec, Bb, g.lbj, g.lbk, n0, nv, kb * kKB, g.K, bt, S::kBTile);
     }
     fence_async_smem();
     fence_before();
@@ -461,9 +465,10 @@ __global__ void __launch_bounds__(kThreads, NS == 3 ? 1 : 2) gemm_bf16_kernel(Ge
   }
   if (done) {
     fence_after();
-    const int q = warp & 3, half = warp >> 2;
+    // warp w reads TMEM lane quarter w % 4 and the 16-column chunks part, part + parts, ...
+    constexpr int kParts = NTH / 128, kChunks16 = BN / 16;
+    const int q = warp & 3, part = warp >> 2;
     const int row = q * 32 + (threadIdx.x & 31);
-    constexpr int kHalf = BN / 2;
     const bool split = !batched && gridDim.z > 1;
     float* C = split ? g.C + (int64_t)blockIdx.z * g.M * g.N : g.C + bz * g.bsc;
     const int64_t ldc = split ? g.N : g.ldc;
@@ -471,7 +476,8 @@ __global__ void __launch_bounds__(kThreads, NS == 3 ? 1 : 2) gemm_bf16_kernel(Ge
     const bool vec = ((ldc & 3) == 0) && ((reinterpret_cast<uintptr_t>(C) & 15) == 0) &&
                      (epi != 1 || (reinterpret_cast<uintptr_t>(g.H) & 15) == 0);
 #pragma unroll 1
-    for (int c0 = half * kHalf; c0 < half * kHalf + kHalf; c0 += 16) {
+    for (int ch = part; ch < kChunks16; ch += kParts) {
+      const int c0 = ch * 16;
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
       if (row >= mv || c0 >= nv) continue;
@@ -546,7 +552,7 @@ cudaError_t launch_bn(cudaStream_t st, dim3 grid, const mlptc::GemmArgs& g) {
   cudaError_t e = set_smem_attr<TA, TB, BN, NS>();
   if (e != cudaSuccess) return e;
   mlptc::gemm_bf16_kernel<TA, TB, BN, NS>
-      <<<grid, mlptc::kThreads, mlptc::Shape<TA, TB, BN, NS>::kSmem, st>>>(g);
+      <<<grid, mlptc::threads_for(NS), mlptc::Shape<TA, TB, BN, NS>::kSmem, st>>>(g);
   return cudaGetLastError();
 }
 
