@@ -196,6 +196,27 @@ def test_kernel_ridge_snapshot_recovery():
         assert np.linalg.norm(S @ y - X[:, i]) <= 1e-14 * kappa * np.linalg.norm(X[:, i])
 
 
+def test_kernel_ridge_snapshots_closed_form():
+    """Two points at distance d on a line: K_sigma = [[1, e], [e, 1]] with e = exp(-d^2 / (2
+    sigma^2)), so (K + lambda I) x = b has the closed form x = [(1 + lambda) b_1 - e b_2,
+    (1 + lambda) b_2 - e b_1] / ((1 + lambda)^2 - e^2).  Pins full_matrix (a dropped or squared
+    lambda, or sigma for sigma^2, shows) and snapshot_matrix's column order."""
+    from types import SimpleNamespace
+    d = 0.7
+    X = np.array([[0.0], [d]])
+    b = np.array([1.3, -0.4])
+    grid = [(0.5, 1e-3), (0.5, 0.2), (1.7, 1e-3), (1.7, 0.2)]
+    prob = SimpleNamespace(X=X, b=b, snap_params=np.array(grid))
+    Xs = krr.snapshot_matrix(prob)
+    for c, (sigma, lam) in enumerate(grid):
+        e = np.exp(-d * d / (2.0 * sigma * sigma))
+        A = krr.full_matrix(X, (sigma, lam))
+        np.testing.assert_allclose(A, [[1.0 + lam, e], [e, 1.0 + lam]], rtol=0, atol=1e-16)
+        det = (1.0 + lam) ** 2 - e * e
+        x = np.array([(1.0 + lam) * b[0] - e * b[1], (1.0 + lam) * b[1] - e * b[0]]) / det
+        np.testing.assert_allclose(Xs[:, c], x, rtol=1e-13)
+
+
 def test_delay_theta_rebuilds_the_delay_operator():
     """A(p) from the delay rule and the blocks equals p I - A_0 - e^{tau p} A_1 written
     out from its definition in Sec. 5.2.3 (T tridiagonal with unit off-diagonals and
