@@ -309,7 +309,8 @@ def run_gpu(args):
         api.subapsnap_set_tracing(plain.ctx, False)
     if args.quick:
         print(json.dumps({"workload": f"diffusion_2d_{args.grid}", "ms_per_step_chosen": ms_chosen,
-                          "reconstruct_ms": rec_ms / max(rec_n, 1), "ls_ms": ls_ms / max(ls_n, 1)}))
+                          "reconstruct_ms": rec_ms / max(rec_n, 1), "ls_ms": ls_ms / max(ls_n, 1),
+                          "autotune": tune}))
         return
 
     # ---- accuracy of the chosen form against the plain float64 form (same parameters)

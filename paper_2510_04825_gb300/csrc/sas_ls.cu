@@ -300,11 +300,14 @@ constexpr int kNumLsShapes = sizeof(kLsShapes) / sizeof(kLsShapes[0]);
 // Blocked Householder variants of the mixed kernel (real only): threads,
 // lanes per column group, registers per lane for a trailing column (s <= G E).
 struct LsBlockedShape {
-  int nt, g, e, pw;  // pw: panel factorised by warp 0 alone (warp-synchronous)
+  // pw: 0 panel factorised by the CTA; 1 by warp 0 alone (warp-synchronous); 2 by
+  // warp 0 with the panel in registers, and the refinement corrections too (s <= 128)
+  int nt, g, e, pw;
 };
 static const LsBlockedShape kLsBlocked[] = {{128, 4, 32, 0}, {128, 8, 16, 0}, {256, 8, 32, 0},
                                             {128, 8, 32, 0}, {128, 8, 16, 1}, {128, 4, 32, 1},
-                                            {256, 8, 32, 1}, {128, 8, 16, 1}};
+                                            {256, 8, 32, 1}, {128, 8, 16, 1}, {128, 8, 16, 2}};
+constexpr int kLsRegRows = 128;  // largest s of the register-panel variant (4 rows per lane)
 constexpr int kNumLsBlocked = sizeof(kLsBlocked) / sizeof(kLsBlocked[0]);
 constexpr int kLsPanel = 8;  // columns per panel of the blocked variants
 constexpr int kFirstBlocked = 3 * kNumLsShapes + 2;
@@ -504,6 +507,152 @@ __device__ inline void panel_warp0(float* P, int ldt, int s, int c0, int pe, flo
   }
 }
 
+// Sum over the warp, every lane receiving it (xor butterfly).
+__device__ inline float butterfly_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Element (i & 3) of a lane's four rows, taken from lane i >> 2.
+__device__ inline float row_of(const float (&x)[4], int i) {
+  float v = x[0];
+  v = (i & 3) == 1 ? x[1] : v;
+  v = (i & 3) == 2 ? x[2] : v;
+  v = (i & 3) == 3 ? x[3] : v;
+  return __shfl_sync(0xffffffffu, v, i >> 2);
+}
+
+// Rows 4 lane .. 4 lane + 3 of column c of P (16 bytes: the panel and its leading
+// dimension are 16-byte aligned), rows >= s as zeros.
+__device__ inline void load_rows4(const float* P, int ldt, int s, int c, float (&x)[4]) {
+  const int i0 = 4 * (threadIdx.x & 31);
+  float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i0 < s) q = *reinterpret_cast<const float4*>(P + (size_t)c * ldt + i0);
+  x[0] = q.x;
+  x[1] = i0 + 1 < s ? q.y : 0.f;
+  x[2] = i0 + 2 < s ? q.z : 0.f;
+  x[3] = i0 + 3 < s ? q.w : 0.f;
+}
+
+// Panel factorisation by one warp with the panel in registers (s <= 128): lane l
+// holds rows 4l .. 4l+3 of the panel's nb <= BW columns, loaded and stored with one
+// 16-byte access per column.  Each reflector costs a few multiply-adds per column
+// and one butterfly for all of the panel's remaining columns together; the
+// reflector formulas are those of householder_step.
+template <int BW>
+__device__ inline void panel_regs(float* P, int ldt, int s, int c0, int nb, float* v0s,
+                                  float* taus) {
+  const int lane = threadIdx.x & 31, i0 = 4 * lane;
+  float col[BW][4];
+#pragma unroll
+  for (int a = 0; a < BW; ++a) {
+    if (a < nb) {
+      load_rows4(P, ldt, s, c0 + a, col[a]);
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) col[a][t] = 0.f;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < BW; ++a) {
+    if (a < nb) {
+      const int k = c0 + a;
+      float t2 = 0.f;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float x = i0 + t > k ? col[a][t] : 0.f;
+        t2 = fmaf(x, x, t2);
+      }
+      t2 = butterfly_sum(t2);
+      const float alpha = row_of(col[a], k);
+      const float nrm = sqrtf(alpha * alpha + t2);
+      const float beta = -nrm * phase(alpha);
+      const float v0 = alpha - beta;
+      const float tau = nrm > 0.f ? 1.f / (nrm * (nrm + fabsf(alpha))) : 0.f;
+      float vv[4];  // this lane's rows of the reflector (v0 at row k, zero above)
+#pragma unroll
+      for (int t = 0; t < 4; ++t) vv[t] = i0 + t > k ? col[a][t] : (i0 + t == k ? v0 : 0.f);
+      float w[BW];
+#pragma unroll
+      for (int j = 0; j < BW; ++j) {
+        w[j] = 0.f;
+        if (j > a && j < nb) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) w[j] = fmaf(vv[t], col[j][t], w[j]);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int j = a + 1; j < BW; ++j)
+          if (j < nb) w[j] += __shfl_xor_sync(0xffffffffu, w[j], o);
+      }
+#pragma unroll
+      for (int j = a + 1; j < BW; ++j) {
+        if (j < nb) {
+          const float tw = tau * w[j];
+#pragma unroll
+          for (int t = 0; t < 4; ++t) col[j][t] = fmaf(-tw, vv[t], col[j][t]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (i0 + t == k) col[a][t] = beta;
+      if (lane == 0) {
+        v0s[k] = v0;
+        taus[k] = tau;
+      }
+    }
+  }
+  if (i0 < s) {
+#pragma unroll
+    for (int a = 0; a < BW; ++a)
+      if (a < nb)
+        *reinterpret_cast<float4*>(P + (size_t)(c0 + a) * ldt + i0) =
+            make_float4(col[a][0], col[a][1], col[a][2], col[a][3]);
+  }
+  __syncwarp();
+}
+
+// One refinement correction by one warp with the vector in registers (s <= 128;
+// lane l holds rows 4l .. 4l+3): x = Q^T res (float32) one reflector at a time, each a
+// 16-byte load of its column, four multiply-adds, a butterfly and four more; then
+// R delta = x_{0:r} by back substitution with the reciprocal diagonal rinv.  Writes
+// delta to dl[0..r).
+__device__ inline void correction_regs(const float* P, int ldt, int s, int r, const double* res,
+                                       const float* v0, const float* tau, const float* rinv,
+                                       float* dl) {
+  const int lane = threadIdx.x & 31, i0 = 4 * lane;
+  float x[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) x[t] = i0 + t < s ? (float)res[i0 + t] : 0.f;
+#pragma unroll 2
+  for (int k = 0; k < r; ++k) {
+    float vv[4];
+    load_rows4(P, ldt, s, k, vv);
+    const float vk0 = v0[k], tk = tau[k];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) vv[t] = i0 + t > k ? vv[t] : (i0 + t == k ? vk0 : 0.f);
+    float w = 0.f;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) w = fmaf(vv[t], x[t], w);
+    const float tw = tk * butterfly_sum(w);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) x[t] = fmaf(-tw, vv[t], x[t]);
+  }
+  for (int i = r - 1; i >= 0; --i) {
+    const float yi = row_of(x, i) * rinv[i];
+    if (lane == 0) dl[i] = yi;
+    float rc[4];
+    load_rows4(P, ldt, s, i, rc);
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (i0 + t < i) x[t] = fmaf(-rc[t], yi, x[t]);
+  }
+  __syncwarp();
+}
+
 template <int NT, int G, int E>
 __device__ inline void blocked_trailing_update(float* P, int ldt, int s, int c0, int pe, int ncol,
                                                const float* Vb, const float* tau) {
@@ -557,6 +706,10 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
   float* tau = reinterpret_cast<float*>(dl + kMaxR);  // kMaxR
   float* nrm2 = tau + kMaxR;                     // 2 (+2 padding)
   TL* P = reinterpret_cast<TL*>(nrm2 + 4);       // ldt x (r+1)
+  // the register-panel variant moves rows of P four at a time in 16-byte accesses
+  static_assert(PW != 2 || ((kMaxDp + kMaxR + kMaxS + NT / 32) * sizeof(TH) +
+                            (kMaxDp + 3 * kMaxR + 4) * sizeof(TL)) % 16 == 0,
+                "P must start on a 16-byte boundary");
   // float64 M: in shared memory (keep64 1), in this CTA's global slot (keep64 2)
   // or not kept (recomputed from the blocks for every residual)
   const bool gslot = a.keep64 == 2 && (int)blockIdx.x < a.nslots;
@@ -616,7 +769,9 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
       // over every trailing column (the right-hand side included)
       for (int c0 = 0; c0 < r; c0 += BW) {
         const int pe = c0 + BW < r ? c0 + BW : r;
-        if constexpr (PW) {
+        if constexpr (PW == 2) {
+          if (warp == 0) panel_regs<BW>(P, ldt, s, c0, pe - c0, v0, tau);
+        } else if constexpr (PW) {
           if (warp == 0) panel_warp0(P, ldt, s, c0, pe, v0, tau);
         } else {
           for (int k = c0; k < pe; ++k)
@@ -653,6 +808,8 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
       }
       backsolve_warp<TL, float>(P, ldt, r, zr, dl, dmin, dmax);
       for (int i = lane; i < r; i += 32) y[i] = to_hi(dl[i]);
+      if constexpr (PW == 2)
+        for (int i = lane; i < r; i += 32) Vb[i] = 1.f / P[i + (size_t)i * ldt];
     }
     __syncthreads();
     double rn2 = 0.0;
@@ -710,27 +867,31 @@ __device__ __forceinline__ void ls_mixed_body(const LsMixedArgs<TH, TL>& a, int6
       if (converged || it >= a.max_refine) break;
       // correction: delta = R^{-1} [Q^H res]_{0:r} in float32 (warp 0)
       if (warp == 0) {
-        for (int i = lane; i < s; i += 32) P[i + (size_t)r * ldt] = to_lo(res[i]);
-        __syncwarp();
-        for (int k = 0; k < r; ++k) {
-          const TL* vk = P + (size_t)k * ldt;  // tail entries below the diagonal
-          TL w = lane == 0 ? conjv(v0[k]) * P[k + (size_t)r * ldt] : zero<TL>();
-          for (int i = k + 1 + lane; i < s; i += 32) w += conjv(vk[i]) * P[i + (size_t)r * ldt];
-          w = warp_sum(w);
-          const TL tw = rscale(tau[k], w);
+        if constexpr (PW == 2) {
+          correction_regs(P, ldt, s, r, res, v0, tau, Vb, dl);
+        } else {
+          for (int i = lane; i < s; i += 32) P[i + (size_t)r * ldt] = to_lo(res[i]);
           __syncwarp();
-          if (lane == 0) P[k + (size_t)r * ldt] -= tw * v0[k];
-          for (int i = k + 1 + lane; i < s; i += 32) P[i + (size_t)r * ldt] -= tw * vk[i];
-          __syncwarp();
-        }
-        TL zr[4];
+          for (int k = 0; k < r; ++k) {
+            const TL* vk = P + (size_t)k * ldt;  // tail entries below the diagonal
+            TL w = lane == 0 ? conjv(v0[k]) * P[k + (size_t)r * ldt] : zero<TL>();
+            for (int i = k + 1 + lane; i < s; i += 32) w += conjv(vk[i]) * P[i + (size_t)r * ldt];
+            w = warp_sum(w);
+            const TL tw = rscale(tau[k], w);
+            __syncwarp();
+            if (lane == 0) P[k + (size_t)r * ldt] -= tw * v0[k];
+            for (int i = k + 1 + lane; i < s; i += 32) P[i + (size_t)r * ldt] -= tw * vk[i];
+            __syncwarp();
+          }
+          TL zr[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int i = lane + 32 * c;
-          zr[c] = i < r ? P[i + (size_t)r * ldt] : zero<TL>();
+          for (int c = 0; c < 4; ++c) {
+            const int i = lane + 32 * c;
+            zr[c] = i < r ? P[i + (size_t)r * ldt] : zero<TL>();
+          }
+          float d0, d1;
+          backsolve_warp<TL, float>(P, ldt, r, zr, dl, d0, d1);
         }
-        float d0, d1;
-        backsolve_warp<TL, float>(P, ldt, r, zr, dl, d0, d1);
         double dn = 0.0, yn = 0.0;
         for (int i = lane; i < r; i += 32) {
           const TH di = to_hi(dl[i]);
@@ -887,6 +1048,7 @@ static cudaError_t launch_mixed_blocked(const sas_ctx* c, const LsMixedArgs<doub
   if (b < 0 || b >= kNumLsBlocked) return cudaErrorInvalidConfiguration;
   const LsBlockedShape sh = kLsBlocked[b];
   if (c->s > sh.g * sh.e) return cudaErrorInvalidConfiguration;  // a trailing column must fit
+  if (sh.pw == 2 && c->s > kLsRegRows) return cudaErrorInvalidConfiguration;
   void (*kern)(LsMixedArgs<double, float>) = nullptr;
   switch (b) {
     case 0: kern = ls_mixed_blocked_kernel<128, 4, 32, 0, 4>; break;
@@ -896,7 +1058,8 @@ static cudaError_t launch_mixed_blocked(const sas_ctx* c, const LsMixedArgs<doub
     case 4: kern = ls_mixed_blocked_kernel<128, 8, 16, 1, 4>; break;
     case 5: kern = ls_mixed_blocked_kernel<128, 4, 32, 1, 4>; break;
     case 6: kern = ls_mixed_blocked_kernel<256, 8, 32, 1, 2>; break;
-    default: kern = ls_mixed_blocked_kernel<128, 8, 16, 1, 5>; break;  // 5 CTAs per SM
+    case 7: kern = ls_mixed_blocked_kernel<128, 8, 16, 1, 5>; break;  // 5 CTAs per SM
+    default: kern = ls_mixed_blocked_kernel<128, 8, 16, 2, 4>; break;  // panel in registers
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

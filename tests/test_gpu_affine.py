@@ -351,9 +351,10 @@ def test_every_ls_variant_and_autotune(c1_small, mode):
     Yo, rho_o = case.oracle_solve(params)
     # plain: 5 shared-memory shapes + 1 register-resident; mixed: 5 shapes with float64 M
     # in shared memory, 5 without, 2 register-resident, 5 with M in a global slot per CTA,
-    # 8 blocked (panels of 8 reflectors applied to register-resident trailing columns;
-    # the panel factorised by the CTA or by warp 0 alone)
-    nvar = 6 if mode == api.SAS_MODE_PLAIN else 25
+    # 9 blocked (panels of 8 reflectors applied to register-resident trailing columns;
+    # the panel factorised by the CTA, by warp 0 alone, or by warp 0 with the panel and
+    # the refinement corrections in registers)
+    nvar = 6 if mode == api.SAS_MODE_PLAIN else 26
     P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
     solver = AffineSolver(p, case.S, case.J, mode=mode, device=DEV)
     bound = _mixed_bound(p, case.S, case.J, params, Yo, rho_o)
@@ -379,7 +380,7 @@ def test_blocked_variants_reject_what_does_not_fit():
     case = Case("diffusion_2d", basis="random", rows="random", N=30, r=20, s=300, m=4)
     P = torch.from_numpy(np.ascontiguousarray(case.prob.test_params)).to(DEV)
     solver = AffineSolver(case.prob, case.S, case.J, mode=api.SAS_MODE_MIXED, device=DEV)
-    for v in range(17, 25):  # s = 300 > 256 >= G E for every blocked shape
+    for v in range(17, 26):  # s = 300 > 256 >= G E for every blocked shape
         api.subapsnap_set_option(solver.ctx, api.SAS_OPT_LS_VARIANT, v)
         Y = torch.empty((4, 20), dtype=torch.float64, device=DEV)
         with pytest.raises(api.SasError):
@@ -435,7 +436,7 @@ def test_register_variants_on_c0_and_multichunk(c0, mode):
     Yo, rho_o = c0.oracle_solve(params)
     P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
     solver = AffineSolver(p, c0.S, c0.J, mode=mode, device=DEV)
-    variants = [5] if mode == api.SAS_MODE_PLAIN else [10, 11] + list(range(17, 25))
+    variants = [5] if mode == api.SAS_MODE_PLAIN else [10, 11] + list(range(17, 26))
     bound = _mixed_bound(p, c0.S, c0.J, params, Yo, rho_o)
     kap = c0.kappas(params)
     for v in variants:
@@ -450,4 +451,29 @@ def test_register_variants_on_c0_and_multichunk(c0, mode):
         else:
             assert (err <= bound).all(), (v, err.max())
         assert (np.abs(rho.cpu().numpy() - rho_o) <= 1e-6 * rho_o + 64 * kap * 1.1e-16).all()
+    solver.close()
+
+
+@pytest.mark.parametrize("N,r,s", [(24, 29, 97), (30, 60, 128)], ids=["s97_r29", "s128_r60"])
+def test_register_panel_variant_edges(N, r, s):
+    """The register-panel variant (each lane holding four rows of the panel and of the
+    correction vector) at its edges: s = 97 leaves one valid row in the last owning lane
+    and r = 29 a last panel of 5 columns; s = 128 fills all 32 lanes."""
+    case = Case("diffusion_2d", basis="random", N=N, r=r, s=s, m=40)
+    p = case.prob
+    params = p.test_params
+    Yo, rho_o = case.oracle_solve(params)
+    P = torch.from_numpy(np.ascontiguousarray(params)).to(DEV)
+    solver = AffineSolver(p, case.S, case.J, mode=api.SAS_MODE_MIXED, device=DEV)
+    api.subapsnap_set_option(solver.ctx, api.SAS_OPT_LS_VARIANT, 25)
+    Y = torch.empty((len(params), p.r), dtype=torch.float64, device=DEV)
+    rho = torch.empty(len(params), dtype=torch.float64, device=DEV)
+    solver.solve(P, api.SAS_OUT_Y, Y, None, rho)
+    torch.cuda.synchronize()
+    err = rel_err_rows(Y.cpu().numpy(), Yo)
+    bound = _mixed_bound(p, case.S, case.J, params, Yo, rho_o)
+    kap = case.kappas(params)
+    print(f"register panel s={s} r={r}: max rel err {err.max():.2e}, kappa max {kap.max():.2e}")
+    assert (err <= bound).all(), err.max()
+    assert (np.abs(rho.cpu().numpy() - rho_o) <= 1e-6 * rho_o + 64 * kap * 1.1e-16).all()
     solver.close()
