@@ -496,7 +496,10 @@ sas_status subapsnap_sample_rows_leverage(const double* scores, int64_t n, int32
 /* Autotuner (not in the paper): times every launch shape of the context's
  * least-squares kernel (threads per CTA, lanes per column group; for the mixed
  * form also where the float64 M lives: shared memory, a global slot per CTA,
- * or recomputed) on the caller's parameters, `reps` timed
+ * or recomputed, and how the Householder panels run: column by column, blocked
+ * with the panel on the CTA or on one warp, or, for s <= 128, blocked with the
+ * panel and the refinement corrections in one warp's registers) on the caller's
+ * parameters, `reps` timed
  * launches each after one warm-up, keeps the fastest in the context and
  * returns it.
  *  params: device, m x dp (a representative batch; its size matters).
