@@ -126,3 +126,89 @@ def test_host_nearest_points_matches_the_oracle(lib):
     P = np.array([[1.5], [0.5], [1.0]])
     np.testing.assert_array_equal(api.subapsnap_nearest_points(P, pts), [1, 0, 2])
     np.testing.assert_array_equal(selection.nearest_points(P, pts), [1, 0, 2])
+
+
+def _affine_desc(**fields):
+    from paper_2510_04825_gb300 import api
+    d = api.AffineDesc()
+    d.n, d.r, d.s, d.K, d.ldS = 100, 10, 20, 2, 100
+    d.dtype, d.theta_rule, d.mode = api.SAS_REAL64, api.SAS_THETA_LINEAR, api.SAS_MODE_PLAIN
+    for k, v in fields.items():
+        setattr(d, k, v)
+    return d
+
+
+@pytest.mark.parametrize("fields,msg", [
+    ({"n": 0}, b"n must be positive"),
+    ({"r": 0}, b"r must be in [1, 128]"),
+    ({"r": 129, "s": 200, "n": 300, "ldS": 300}, b"r must be in [1, 128]"),
+    ({"s": 9}, b"need r <= s"),
+    ({"s": 513, "n": 600, "ldS": 600}, b"need r <= s"),
+    ({"s": 101}, b"need r <= s"),  # s > n
+    ({"K": 0}, b"K must be in [1, 8]"),
+    ({"K": 9}, b"K must be in [1, 8]"),
+    ({"dtype": 7}, b"bad dtype"),
+    ({"theta_rule": 1}, b"pencil rule needs complex128 and K = 2"),  # real dtype
+    ({"theta_rule": 1, "dtype": 1, "K": 3}, b"pencil rule needs complex128 and K = 2"),
+    ({"theta_rule": 2, "dtype": 1, "K": 2}, b"delay rule needs complex128 and K = 3"),
+    ({"theta_rule": 9}, b"bad theta rule"),
+    ({"mode": 5}, b"bad mode"),
+    ({"ldS": 99}, b"ldS < n"),
+    ({}, b"S must be a device pointer"),  # every field valid, S NULL
+], ids=lambda v: v.decode() if isinstance(v, bytes) else None)
+def test_affine_descriptor_checks(lib, fields, msg):
+    """Each invalid field of the affine descriptor is refused with SAS_EINVAL and its
+    message before any device work, and the context stays NULL."""
+    from paper_2510_04825_gb300 import api
+    d = _affine_desc(**fields)
+    ctx = ctypes.c_void_p(1)
+    assert lib.subapsnap_setup_affine(ctypes.byref(d), ctypes.byref(ctx)) == api.SAS_EINVAL
+    assert msg in lib.subapsnap_last_error(), lib.subapsnap_last_error()
+    assert ctx.value is None
+
+
+@pytest.mark.parametrize("bad", [0.0, -1.0, float("nan"), float("inf")])
+def test_affine_row_weights_must_be_positive_and_finite(lib, bad):
+    """Row weights (leverage sampling, Sec. 4.3.3) are checked on the host before the
+    device pointers."""
+    from paper_2510_04825_gb300 import api
+    w = np.ones(20)
+    w[7] = bad
+    d = _affine_desc()
+    d.w = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    ctx = ctypes.c_void_p(1)
+    assert lib.subapsnap_setup_affine(ctypes.byref(d), ctypes.byref(ctx)) == api.SAS_EINVAL
+    assert b"row weights must be positive and finite" in lib.subapsnap_last_error()
+    assert ctx.value is None
+
+
+@pytest.mark.parametrize("fields,msg", [
+    ({"n": 0}, b"n must be positive"),
+    ({"d": 0}, b"d must be in [1, 16]"),
+    ({"d": 17}, b"d must be in [1, 16]"),
+    ({"r": 0}, b"r must be in [1, 128]"),
+    ({"s": 9}, b"need r <= s"),
+    ({"s": 101}, b"need r <= s"),  # s > n
+    ({"mode": 5}, b"bad mode"),
+    ({"ldS": 99}, b"ldS < n"),
+    ({}, b"X and S must be device pointers"),
+], ids=lambda v: v.decode() if isinstance(v, bytes) else None)
+def test_kernel_descriptor_checks(lib, fields, msg):
+    """The Gaussian-kernel descriptor's fields, as for the affine one."""
+    from paper_2510_04825_gb300 import api
+    d = api.KernelDesc()
+    d.n, d.d, d.r, d.s, d.ldS, d.mode = 100, 8, 10, 20, 100, api.SAS_MODE_PLAIN
+    for k, v in fields.items():
+        setattr(d, k, v)
+    ctx = ctypes.c_void_p(1)
+    assert lib.subapsnap_setup_kernel(ctypes.byref(d), ctypes.byref(ctx)) == api.SAS_EINVAL
+    assert msg in lib.subapsnap_last_error(), lib.subapsnap_last_error()
+    assert ctx.value is None
+    # a shard context skips the s <= n check (its n is the shard's points), not the others
+    if fields and "s" not in fields and "n" not in fields:
+        sd = api.KernelShardDesc()
+        sd.base = d
+        ctx2 = ctypes.c_void_p(1)
+        assert lib.subapsnap_setup_kernel_shard(ctypes.byref(sd), ctypes.byref(ctx2)) == api.SAS_EINVAL
+        assert msg in lib.subapsnap_last_error()
+        assert ctx2.value is None
